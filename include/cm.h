@@ -1,0 +1,145 @@
+/*
+ * cm.h -- C ABI of the GB300 NTT randomness-extractor library (libcm.so).
+ *
+ * The library computes the Toeplitz, Circulant and Dodis et al. extractors of
+ * Cryptomite (arXiv 2402.09481) on one NVIDIA GB300 GPU.  Each output is a
+ * GF(2) matrix-vector product, computed exactly as an integer convolution by a
+ * number-theoretic transform over the Goldilocks prime p = 2^64 - 2^32 + 1
+ * (Def. ntt and Thm. convolution of the paper), then reduced mod 2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Bit strings are arrays of uint64_t words: bit i is bit (i & 63) of word
+ * i >> 6 (least significant first).  Bit 0 is the paper's x_0 / y_0.  A string
+ * of k bits occupies ceil(k / 64) words.  Input bits past the length are
+ * ignored; output bits past m are written as 0.
+ *
+ * Unless stated otherwise, data pointers are DEVICE pointers on the context's
+ * GPU, the caller owns every buffer, and calls are asynchronous and
+ * stream-ordered on `stream` (a cudaStream_t; NULL is the legacy default
+ * stream).  The library keeps no pointer to caller memory after the stream
+ * work of the call completes.  Scratch memory comes from a memory pool owned by
+ * the context (stream-ordered allocation on the same stream), so concurrent
+ * calls on different streams do not share scratch.
+ *
+ * Errors: every call returns a cm_status.  Argument errors are detected on the
+ * host before anything is enqueued; nothing aborts and no exception crosses
+ * the ABI.  The Dodis et al. precondition (x neither all-0 nor all-1) is
+ * checked on the device: on violation the output is zero-filled and the
+ * context's device status records CM_EPRECOND, read back by
+ * cm_device_status().
+ */
+#ifndef CM_H
+#define CM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cm_ctx cm_ctx;
+typedef void *cm_stream; /* cudaStream_t */
+
+typedef enum {
+    CM_OK = 0,
+    CM_EINVAL = 1,     /* invalid argument: length, pointer, size beyond limits */
+    CM_EPRECOND = 2,   /* Dodis et al.: x is all-0 or all-1 (device-detected) */
+    CM_ENOMEM = 3,     /* scratch allocation failed or HBM budget exceeded */
+    CM_EAGAIN = 4,     /* not ready / queue full; retry */
+    CM_ETIMEDOUT = 5,  /* a bounded wait ran out */
+    CM_EDEVICE = 6,    /* CUDA runtime error */
+    CM_ENOTFOUND = 7   /* unknown ticket */
+} cm_status;
+
+/* Extractor kinds (used by the batched and serving interfaces). */
+typedef enum { CM_TOEPLITZ = 0, CM_CIRCULANT = 1, CM_DODIS = 2 } cm_kind;
+
+/* Device-status bits accumulated by kernels, read by cm_device_status(). */
+#define CM_FLAG_PRECOND 0x1u  /* a Dodis et al. call saw a constant x */
+#define CM_FLAG_TIMEOUT 0x2u  /* a bounded device wait ran out */
+
+typedef struct {
+    uint64_t hbm_budget_bytes; /* cap on scratch held at once; 0 = 80% of free HBM */
+    uint32_t reserved[8];
+} cm_options;
+
+/* Create a context on CUDA device `device`: root tables resident in HBM, a
+ * scratch memory pool.  opt may be NULL.  Returns CM_EDEVICE if the device is
+ * unusable, CM_EINVAL if out is NULL. */
+cm_status cm_create(cm_ctx **out, int device, const cm_options *opt);
+
+/* Synchronize the device and free everything the context owns. */
+void cm_destroy(cm_ctx *ctx);
+
+/* Static string for a status code. */
+const char *cm_status_str(int status);
+
+/*
+ * Toeplitz extractor, Eq. toep-ext / Eq. toep of the paper:
+ *   z = toep(y) x over GF(2), toep(y)[i][j] = y[(i - j) mod (n + m - 1)],
+ *   i < m, j < n.
+ * x: n bits (ceil(n/64) words).  y: n + m - 1 bits.  z: m bits (ceil(m/64)
+ * words, written).  Requires n >= 1, m >= 1, n + m - 1 <= 2^32 (the
+ * Goldilocks transform length limit).  CM_EINVAL otherwise.
+ */
+cm_status cm_toeplitz(cm_ctx *ctx, const uint64_t *x, uint64_t n, const uint64_t *y, uint64_t m,
+                      uint64_t *z, cm_stream stream);
+
+/*
+ * Circulant extractor, Def. ext-circ with Eq. circ-matrix:
+ *   x' = [x, 0],  z = (circ(x') y)_{0..m-1},  circ(c)[i][j] = c[(j - i) mod P].
+ * n is the INPUT length n_1 = P - 1 (the paper's Def. ext-circ calls the prime
+ * n); P = n + 1 must be prime with 2 as a primitive root.
+ * x: n bits.  y: n + 1 bits.  z: m bits, 1 <= m <= n.  P + m - 1 <= 2^32.
+ * CM_EINVAL otherwise.  x = 0 is allowed (output 0).
+ */
+cm_status cm_circulant(cm_ctx *ctx, const uint64_t *x, uint64_t n, const uint64_t *y, uint64_t m,
+                       uint64_t *z, cm_stream stream);
+
+/*
+ * Dodis et al. two-source extractor, matrix form of the paper's Section
+ * "Dodis (and Circulant) implementation":
+ *   z_i = sum_j x[(j - i) mod n] y_j (mod 2),  i < m
+ * (equivalently the first m entries of R(x) * y, R(x) = x_0, x_{n-1}, ..., x_1).
+ * x, y: n bits each; n prime with 2 as a primitive root; 1 <= m <= n;
+ * n + m - 1 <= 2^32.  CM_EINVAL otherwise.  If x is all-0 or all-1 the call
+ * still returns CM_OK (the check runs on the device), z is zero-filled and
+ * cm_device_status() reports CM_EPRECOND.
+ */
+cm_status cm_dodis(cm_ctx *ctx, const uint64_t *x, const uint64_t *y, uint64_t n, uint64_t m,
+                   uint64_t *z, cm_stream stream);
+
+/* Synchronize `stream`, then read and clear the context's device status bits.
+ * *flags (may be NULL) receives the CM_FLAG_* bits.  Returns CM_EPRECOND if
+ * CM_FLAG_PRECOND was set, CM_ETIMEDOUT if CM_FLAG_TIMEOUT was set, CM_EDEVICE
+ * on a CUDA error, else CM_OK. */
+cm_status cm_device_status(cm_ctx *ctx, cm_stream stream, uint32_t *flags);
+
+/* ----- host helpers (no GPU work) --------------------------------------- */
+
+/* 1 if P is prime and 2 is a primitive root modulo P (the set N_A of the
+ * paper's footnote to Def. ext-circ), else 0.  Deterministic for P < 2^64. */
+int cm_is_na_prime(uint64_t P);
+/* Smallest member of N_A >= n (0 if none below 2^63). */
+uint64_t cm_next_na_prime(uint64_t n);
+/* Largest member of N_A <= n (0 if n < 3). */
+uint64_t cm_prev_na_prime(uint64_t n);
+
+/* Transform length L the library uses for (kind, n, m): the smallest power of
+ * two >= K + m - 1 with K = n (Toeplitz), n + 1 (Circulant), n (Dodis); 0 if
+ * the arguments are invalid for that kind. */
+uint64_t cm_ntt_length(int kind, uint64_t n, uint64_t m);
+
+/* Bytes of scratch one call of (kind, n, m) takes from the pool. */
+uint64_t cm_scratch_bytes(int kind, uint64_t n, uint64_t m);
+
+/* Number of kernel launches one call of (kind, n, m) enqueues. */
+uint32_t cm_launch_count(int kind, uint64_t n, uint64_t m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CM_H */

@@ -1,0 +1,351 @@
+// C ABI entry points: context, plans, single extractions.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "cm.h"
+#include "cm_internal.h"
+#include "cm_ctx.h"
+
+namespace cm {
+
+static int ceil_log2(uint64_t v) {
+    int k = 0;
+    while ((1ull << k) < v) ++k;  // v <= 2^33 here
+    return k;
+}
+
+bool make_plan(int kind, uint64_t n, uint64_t m, Plan *p) {
+    memset(p, 0, sizeof(*p));
+    p->kind = kind;
+    p->n = n;
+    p->m = m;
+    if (m == 0 || n == 0) return false;
+    // every length below is checked against 2^32 before any sum can overflow
+    if (n > (1ull << 32) || m > (1ull << 32)) return false;
+    switch (kind) {
+        case CM_TOEPLITZ: {
+            const uint64_t N = n + m - 1;  // seed length
+            p->K = n;
+            p->amode = kIdentity; p->alen = n; p->asrclen = n; p->aoff = 0;
+            // b_k = y[(k - n + 1) mod N] = y[(k + m) mod N]
+            p->bmode = kModForward; p->blen = N; p->bsrclen = N; p->boff = m % N;
+            break;
+        }
+        case CM_CIRCULANT: {
+            const uint64_t P = n + 1;
+            if (m > n || !is_na_prime(P)) return false;
+            p->K = P;
+            // rev(x')_u = x'_{P-1-u}, x' = [x, 0]: u = 0 reads the pad bit (index n, zero)
+            p->amode = kReverse; p->alen = P; p->asrclen = n; p->aoff = n;
+            p->bmode = kModForward; p->blen = P + m - 1; p->bsrclen = P; p->boff = 0;
+            break;
+        }
+        case CM_DODIS: {
+            if (m > n || !is_na_prime(n)) return false;
+            p->K = n;
+            p->amode = kReverse; p->alen = n; p->asrclen = n; p->aoff = n - 1;
+            p->bmode = kModForward; p->blen = n + m - 1; p->bsrclen = n; p->boff = 0;
+            break;
+        }
+        default:
+            return false;
+    }
+    const uint64_t need = p->K + m - 1;
+    if (need > (1ull << 32)) return false;
+    p->lg = ceil_log2(need);
+    if (p->lg < 1) p->lg = 1;
+    p->L = 1ull << p->lg;
+    p->lo = p->K - 1;
+    const int rest = p->lg - kMidLgMax;
+    if (rest <= 0) {
+        p->npass = 0;
+    } else if (rest <= 12) {
+        p->npass = 1;
+        p->pass_lg[0] = rest;
+    } else {
+        p->npass = 2;
+        p->pass_lg[0] = (rest + 1) / 2;
+        p->pass_lg[1] = rest / 2;
+    }
+    const uint64_t flags = (kind == CM_DODIS) ? 256 : 0;
+    if (p->npass == 0) {
+        p->scratch_bytes = flags;
+        p->launches = 1;
+    } else {
+        p->scratch_bytes = 2 * 8 * p->L + ((m + 255) & ~255ull) + flags;
+        // forward passes of both operands, middle, inverse passes, pack
+        p->launches = 2 * p->npass + 1 + p->npass + 1;
+    }
+    if (kind == CM_DODIS) p->launches += 1;  // precondition check
+    return true;
+}
+
+static BitMap bitmap(const uint64_t *src, int mode, uint64_t len, uint64_t srclen, uint64_t off) {
+    BitMap b;
+    b.src = src;
+    b.mode = mode;
+    b.len = len;
+    b.srclen = srclen;
+    b.off = off;
+    return b;
+}
+
+static cm_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return CM_OK;
+    if (e == cudaErrorMemoryAllocation) return CM_ENOMEM;
+    return CM_EDEVICE;
+}
+
+// Enqueue one extraction described by plan p.  scratch holds p.scratch_bytes.
+cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const uint64_t *y,
+                          uint64_t *z, void *scratch, cudaStream_t st) {
+    const BitMap am = bitmap(x, p.amode, p.alen, p.asrclen, p.aoff);
+    const BitMap bm = bitmap(y, p.bmode, p.blen, p.bsrclen, p.boff);
+    const uint64_t linv = gl_inv_pow2_host(p.L);
+    uint32_t *pre = nullptr;
+    cudaError_t e;
+    uint8_t *sc = static_cast<uint8_t *>(scratch);
+    if (p.kind == CM_DODIS) {
+        pre = reinterpret_cast<uint32_t *>(sc + p.scratch_bytes - 256);
+        if ((e = cudaMemsetAsync(pre, 0, 2 * sizeof(uint32_t), st)) != cudaSuccess) return cuda_status(e);
+        if ((e = launch_allsame(x, p.n, pre, ctx->nsm, st)) != cudaSuccess) return cuda_status(e);
+    }
+    if (p.npass == 0) {
+        Launch q;
+        q.amap = am;
+        q.bmap = bm;
+        q.lo = p.lo;
+        q.m = p.m;
+        q.linv = linv;
+        q.z = z;
+        q.pre = pre;
+        q.status = ctx->d_status;
+        q.rt = ctx->rt;
+        q.stream = st;
+        return cuda_status(launch_small(q, p.lg));
+    }
+    uint64_t *A = reinterpret_cast<uint64_t *>(sc);
+    uint64_t *B = A + p.L;
+    uint8_t *par = reinterpret_cast<uint8_t *>(B + p.L);
+
+    int lgN[2], lgS[2];
+    int cur = p.lg;
+    for (int j = 0; j < p.npass; ++j) {
+        lgN[j] = cur;
+        lgS[j] = cur - p.pass_lg[j];
+        cur = lgS[j];
+    }
+    // forward passes
+    for (int op = 0; op < 2; ++op) {
+        for (int j = 0; j < p.npass; ++j) {
+            PassArgs a;
+            memset(&a, 0, sizeof(a));
+            a.data = op == 0 ? A : B;
+            a.map = op == 0 ? am : bm;
+            a.lgN = lgN[j];
+            a.lgS = lgS[j];
+            a.rt = ctx->rt;
+            a.L = p.L;
+            a.inv = false;
+            a.bits_in = (j == 0);
+            if ((e = launch_pass(a, p.pass_lg[j], st)) != cudaSuccess) return cuda_status(e);
+        }
+    }
+    if ((e = launch_middle(A, B, p.L, linv, ctx->rt, st)) != cudaSuccess) return cuda_status(e);
+    for (int j = p.npass - 1; j >= 0; --j) {
+        PassArgs a;
+        memset(&a, 0, sizeof(a));
+        a.data = A;
+        a.lgN = lgN[j];
+        a.lgS = lgS[j];
+        a.rt = ctx->rt;
+        a.L = p.L;
+        a.inv = true;
+        a.parity_out = (j == 0);
+        a.par = par;
+        a.lo = p.lo;
+        a.m = p.m;
+        if ((e = launch_pass(a, p.pass_lg[j], st)) != cudaSuccess) return cuda_status(e);
+    }
+    return cuda_status(launch_pack(par, p.m, z, pre, ctx->d_status, ctx->nsm, st));
+}
+
+cm_status run_single(cm_ctx *ctx, int kind, const uint64_t *x, uint64_t n, const uint64_t *y,
+                     uint64_t m, uint64_t *z, cudaStream_t st) {
+    if (!ctx || !x || !y || !z) return CM_EINVAL;
+    Plan p;
+    if (!make_plan(kind, n, m, &p)) return CM_EINVAL;
+    if (p.scratch_bytes > ctx->budget) return CM_ENOMEM;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return CM_EDEVICE;
+    void *scratch = nullptr;
+    if (p.scratch_bytes) {
+        e = cudaMallocFromPoolAsync(&scratch, p.scratch_bytes, ctx->pool, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return CM_ENOMEM;
+        }
+    }
+    cm_status s = enqueue_extract(ctx, p, x, y, z, scratch, st);
+    if (scratch) {
+        e = cudaFreeAsync(scratch, st);
+        if (s == CM_OK && e != cudaSuccess) s = CM_EDEVICE;
+    }
+    return s;
+}
+
+static void build_tables(std::vector<uint64_t> &h) {
+    // layout: small_fwd[4096] small_inv[4096] big_lo_fwd[65536] big_hi_fwd[65536]
+    //         big_lo_inv[65536] big_hi_inv[65536]
+    h.assign(2 * 4096 + 4 * 65536, 0);
+    const uint64_t g = gl_root_2_32_host(0), gi = gl_root_2_32_host(1);
+    const uint64_t w = gl_pow_host(g, 1ull << (32 - kSmallLg));   // omega_8192
+    const uint64_t wi = gl_pow_host(gi, 1ull << (32 - kSmallLg));
+    uint64_t a = 1, b = 1;
+    for (int e = 0; e < 4096; ++e) {
+        h[e] = a;
+        h[4096 + e] = b;
+        a = gl_mul_host(a, w);
+        b = gl_mul_host(b, wi);
+    }
+    uint64_t *lf = &h[8192], *hf = lf + 65536, *li = hf + 65536, *hi = li + 65536;
+    const uint64_t g16 = gl_pow_host(g, 65536), gi16 = gl_pow_host(gi, 65536);
+    uint64_t c0 = 1, c1 = 1, c2 = 1, c3 = 1;
+    for (int e = 0; e < 65536; ++e) {
+        lf[e] = c0;
+        hf[e] = c1;
+        li[e] = c2;
+        hi[e] = c3;
+        c0 = gl_mul_host(c0, g);
+        c1 = gl_mul_host(c1, g16);
+        c2 = gl_mul_host(c2, gi);
+        c3 = gl_mul_host(c3, gi16);
+    }
+}
+
+}  // namespace cm
+
+using namespace cm;
+
+extern "C" cm_status cm_create(cm_ctx **out, int device, const cm_options *opt) {
+    if (!out) return CM_EINVAL;
+    *out = nullptr;
+    if (cudaSetDevice(device) != cudaSuccess) return CM_EDEVICE;
+    cm_ctx *c = new cm_ctx();
+    c->device = device;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete c;
+        return CM_EDEVICE;
+    }
+    c->nsm = prop.multiProcessorCount;
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    c->budget = (opt && opt->hbm_budget_bytes) ? opt->hbm_budget_bytes : (uint64_t)(free_b * 0.8);
+
+    cudaMemPoolProps pp;
+    memset(&pp, 0, sizeof(pp));
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = device;
+    if (cudaMemPoolCreate(&c->pool, &pp) != cudaSuccess) {
+        delete c;
+        return CM_EDEVICE;
+    }
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+
+    std::vector<uint64_t> h;
+    build_tables(h);
+    if (cudaMalloc(&c->d_tables, h.size() * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&c->d_status, 64) != cudaSuccess) {
+        cm_destroy(c);
+        return CM_ENOMEM;
+    }
+    cudaMemcpy(c->d_tables, h.data(), h.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    cudaMemset(c->d_status, 0, 64);
+    c->rt.small_fwd = c->d_tables;
+    c->rt.small_inv = c->d_tables + 4096;
+    c->rt.big_lo_fwd = c->d_tables + 8192;
+    c->rt.big_hi_fwd = c->rt.big_lo_fwd + 65536;
+    c->rt.big_lo_inv = c->rt.big_hi_fwd + 65536;
+    c->rt.big_hi_inv = c->rt.big_lo_inv + 65536;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cm_destroy(c);
+        return CM_EDEVICE;
+    }
+    *out = c;
+    return CM_OK;
+}
+
+extern "C" void cm_destroy(cm_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    cm_ctx_release_extras(c);
+    if (c->d_tables) cudaFree(c->d_tables);
+    if (c->d_status) cudaFree(c->d_status);
+    if (c->pool) cudaMemPoolDestroy(c->pool);
+    delete c;
+}
+
+extern "C" const char *cm_status_str(int s) {
+    switch (s) {
+        case CM_OK: return "CM_OK";
+        case CM_EINVAL: return "CM_EINVAL: invalid argument";
+        case CM_EPRECOND: return "CM_EPRECOND: Dodis et al. input is all-0 or all-1";
+        case CM_ENOMEM: return "CM_ENOMEM: out of memory or over the HBM budget";
+        case CM_EAGAIN: return "CM_EAGAIN: not ready";
+        case CM_ETIMEDOUT: return "CM_ETIMEDOUT: bounded wait ran out";
+        case CM_EDEVICE: return "CM_EDEVICE: CUDA error";
+        case CM_ENOTFOUND: return "CM_ENOTFOUND: unknown ticket";
+        default: return "unknown cm_status";
+    }
+}
+
+extern "C" cm_status cm_toeplitz(cm_ctx *ctx, const uint64_t *x, uint64_t n, const uint64_t *y,
+                                 uint64_t m, uint64_t *z, cm_stream stream) {
+    return run_single(ctx, CM_TOEPLITZ, x, n, y, m, z, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" cm_status cm_circulant(cm_ctx *ctx, const uint64_t *x, uint64_t n, const uint64_t *y,
+                                  uint64_t m, uint64_t *z, cm_stream stream) {
+    return run_single(ctx, CM_CIRCULANT, x, n, y, m, z, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" cm_status cm_dodis(cm_ctx *ctx, const uint64_t *x, const uint64_t *y, uint64_t n,
+                              uint64_t m, uint64_t *z, cm_stream stream) {
+    return run_single(ctx, CM_DODIS, x, n, y, m, z, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" cm_status cm_device_status(cm_ctx *ctx, cm_stream stream, uint32_t *flags) {
+    if (!ctx) return CM_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return CM_EDEVICE;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return CM_EDEVICE;
+    uint32_t f = 0;
+    if (cudaMemcpy(&f, ctx->d_status, sizeof(f), cudaMemcpyDeviceToHost) != cudaSuccess) return CM_EDEVICE;
+    if (cudaMemset(ctx->d_status, 0, sizeof(f)) != cudaSuccess) return CM_EDEVICE;
+    if (flags) *flags = f;
+    if (f & CM_FLAG_PRECOND) return CM_EPRECOND;
+    if (f & CM_FLAG_TIMEOUT) return CM_ETIMEDOUT;
+    return CM_OK;
+}
+
+extern "C" uint64_t cm_ntt_length(int kind, uint64_t n, uint64_t m) {
+    Plan p;
+    return make_plan(kind, n, m, &p) ? p.L : 0;
+}
+
+extern "C" uint64_t cm_scratch_bytes(int kind, uint64_t n, uint64_t m) {
+    Plan p;
+    return make_plan(kind, n, m, &p) ? p.scratch_bytes : 0;
+}
+
+extern "C" uint32_t cm_launch_count(int kind, uint64_t n, uint64_t m) {
+    Plan p;
+    return make_plan(kind, n, m, &p) ? p.launches : 0;
+}

@@ -1,0 +1,69 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cm.h"
+#include "ntt_device.cuh"
+
+namespace cm {
+
+constexpr uint32_t kFlagPrecond = CM_FLAG_PRECOND;
+constexpr uint32_t kFlagTimeout = CM_FLAG_TIMEOUT;
+
+// Arguments of the single-CTA extraction (L <= 2^13).
+struct Launch {
+    BitMap amap, bmap;
+    uint64_t lo, m, linv;
+    uint64_t *z;
+    const uint32_t *pre;
+    uint32_t *status;
+    RootTables rt;
+    cudaStream_t stream;
+};
+
+// Arguments of one column pass.
+struct PassArgs {
+    uint64_t *data;
+    BitMap map;
+    int lgN, lgS;
+    uint8_t *par;
+    uint64_t lo, m;
+    RootTables rt;
+    uint64_t L;
+    bool inv, bits_in, parity_out;
+};
+
+cudaError_t launch_small(const Launch &q, int lg);
+cudaError_t launch_pass(const PassArgs &a, int logr, cudaStream_t st);
+cudaError_t launch_middle(uint64_t *A, const uint64_t *B, uint64_t L, uint64_t linv,
+                          const RootTables &rt, cudaStream_t st);
+cudaError_t launch_pack(const uint8_t *par, uint64_t m, uint64_t *z, const uint32_t *pre,
+                        uint32_t *status, int nsm, cudaStream_t st);
+cudaError_t launch_allsame(const uint64_t *x, uint64_t n, uint32_t *flags, int nsm, cudaStream_t st);
+
+// The plan of one extraction: the middle-product form of the extractor and the
+// pass split of its transform.
+struct Plan {
+    int kind;
+    uint64_t n, m;
+    uint64_t K;      // length of a
+    uint64_t L;      // transform length, power of two >= K + m - 1
+    int lg;          // log2 L
+    int amode, bmode;
+    uint64_t alen, asrclen, aoff;
+    uint64_t blen, bsrclen, boff;
+    int npass;       // column passes before the on-chip block (0, 1 or 2)
+    int pass_lg[2];  // log2 R_j, slowest dimension first
+    uint64_t lo;     // window start K - 1
+    uint64_t scratch_bytes;
+    uint32_t launches;
+};
+
+// Validate (kind, n, m) and fill the plan; false if invalid.
+bool make_plan(int kind, uint64_t n, uint64_t m, Plan *out);
+
+// N_A membership and search (host, deterministic).
+bool is_na_prime(uint64_t P);
+
+}  // namespace cm

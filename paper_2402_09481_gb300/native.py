@@ -1,0 +1,199 @@
+"""ctypes binding of libcm.so (the C ABI declared in include/cm.h).
+
+Argument marshalling only: every step of the extraction runs in the library's
+CUDA kernels.  Tensors are used for device memory and streams; the library
+sees raw pointers, sizes and a cudaStream_t.  If the library is missing the
+binding raises: there is no fallback path.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import build as _build
+
+TOEPLITZ, CIRCULANT, DODIS = 0, 1, 2
+
+STATUS = {0: "CM_OK", 1: "CM_EINVAL", 2: "CM_EPRECOND", 3: "CM_ENOMEM", 4: "CM_EAGAIN",
+          5: "CM_ETIMEDOUT", 6: "CM_EDEVICE", 7: "CM_ENOTFOUND"}
+CM_OK, CM_EINVAL, CM_EPRECOND, CM_ENOMEM, CM_EAGAIN, CM_ETIMEDOUT, CM_EDEVICE, CM_ENOTFOUND = range(8)
+FLAG_PRECOND, FLAG_TIMEOUT = 0x1, 0x2
+
+_lib = None
+
+_P = ctypes.c_void_p
+_U64 = ctypes.c_uint64
+_U32 = ctypes.c_uint32
+_I = ctypes.c_int
+
+# name -> (restype, argtypes)
+PROTOTYPES = {
+    "cm_create": (_I, [ctypes.POINTER(_P), _I, _P]),
+    "cm_destroy": (None, [_P]),
+    "cm_status_str": (ctypes.c_char_p, [_I]),
+    "cm_toeplitz": (_I, [_P, _P, _U64, _P, _U64, _P, _P]),
+    "cm_circulant": (_I, [_P, _P, _U64, _P, _U64, _P, _P]),
+    "cm_dodis": (_I, [_P, _P, _P, _U64, _U64, _P, _P]),
+    "cm_device_status": (_I, [_P, _P, ctypes.POINTER(_U32)]),
+    "cm_is_na_prime": (_I, [_U64]),
+    "cm_next_na_prime": (_U64, [_U64]),
+    "cm_prev_na_prime": (_U64, [_U64]),
+    "cm_ntt_length": (_U64, [_I, _U64, _U64]),
+    "cm_scratch_bytes": (_U64, [_I, _U64, _U64]),
+    "cm_launch_count": (_U32, [_I, _U64, _U64]),
+}
+
+
+class CMError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}" if what else STATUS.get(status, str(status)))
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/cm.h declares."""
+    with open(os.path.join(_build.INCLUDE, "cm.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cm_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """Load libcm.so (built by build.build()); raise if it is absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(
+                "libcm.so is not built; run paper_2402_09481_gb300.build.build() "
+                "(there is no CPU fallback)")
+        L = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in PROTOTYPES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != CM_OK:
+        raise CMError(status, what)
+
+
+def words(nbits: int) -> int:
+    return (int(nbits) + 63) // 64
+
+
+def ntt_length(kind: int, n: int, m: int) -> int:
+    return int(lib().cm_ntt_length(kind, n, m))
+
+
+def scratch_bytes(kind: int, n: int, m: int) -> int:
+    return int(lib().cm_scratch_bytes(kind, n, m))
+
+
+def launch_count(kind: int, n: int, m: int) -> int:
+    return int(lib().cm_launch_count(kind, n, m))
+
+
+def is_na_prime(P: int) -> bool:
+    return bool(lib().cm_is_na_prime(P))
+
+
+def next_na_prime(n: int) -> int:
+    return int(lib().cm_next_na_prime(n))
+
+
+def prev_na_prime(n: int) -> int:
+    return int(lib().cm_prev_na_prime(n))
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev_words(t, nbits: int, name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor of 64-bit words")
+    if t.dtype not in (torch.int64, torch.uint64) or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous int64/uint64 tensor")
+    if t.numel() < words(nbits):
+        raise ValueError(f"{name} holds {t.numel()} words, needs {words(nbits)} for {nbits} bits")
+    return t.data_ptr()
+
+
+class Context:
+    """A libcm context on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        import torch
+        self.device = device
+        torch.cuda.set_device(device)
+        self._L = lib()
+        opts = (ctypes.c_uint64 * 5)(hbm_budget_bytes, 0, 0, 0, 0)
+        h = ctypes.c_void_p()
+        _check(self._L.cm_create(ctypes.byref(h), device, ctypes.cast(opts, ctypes.c_void_p)),
+               "cm_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.cm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _out(self, z, m, like):
+        import torch
+        if z is None:
+            z = torch.empty(words(m), dtype=torch.int64, device=like.device)
+        _dev_words(z, m, "z")
+        return z
+
+    def toeplitz(self, x, n: int, y, m: int, z=None, stream=None):
+        """z = toep(y) x over GF(2): x has n bits, y has n + m - 1 bits."""
+        px = _dev_words(x, n, "x")
+        py = _dev_words(y, n + m - 1, "y")
+        z = self._out(z, m, x)
+        _check(self._L.cm_toeplitz(self._h, px, n, py, m, z.data_ptr(), _stream_handle(stream)),
+               "cm_toeplitz")
+        return z
+
+    def circulant(self, x, n: int, y, m: int, z=None, stream=None):
+        """Circulant(x, y): x has n bits, y has n + 1 bits (n + 1 prime in N_A)."""
+        px = _dev_words(x, n, "x")
+        py = _dev_words(y, n + 1, "y")
+        z = self._out(z, m, x)
+        _check(self._L.cm_circulant(self._h, px, n, py, m, z.data_ptr(), _stream_handle(stream)),
+               "cm_circulant")
+        return z
+
+    def dodis(self, x, y, n: int, m: int, z=None, stream=None):
+        """Dodis et al.(x, y): both n bits, n prime in N_A."""
+        px = _dev_words(x, n, "x")
+        py = _dev_words(y, n, "y")
+        z = self._out(z, m, x)
+        _check(self._L.cm_dodis(self._h, px, py, n, m, z.data_ptr(), _stream_handle(stream)),
+               "cm_dodis")
+        return z
+
+    def device_status(self, stream=None) -> tuple[int, int]:
+        f = ctypes.c_uint32(0)
+        s = self._L.cm_device_status(self._h, _stream_handle(stream), ctypes.byref(f))
+        return int(s), int(f.value)

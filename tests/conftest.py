@@ -11,3 +11,27 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+@pytest.fixture(scope="session")
+def cm_ctx():
+    """A libcm context on cuda:0 (GPU tests only)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_09481_gb300 import build, native
+    build.build()
+    ctx = native.Context(0)
+    yield ctx
+    ctx.close()
+
+
+def to_dev(words):
+    import numpy as np
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(words, dtype=np.uint64).view(np.int64)).cuda()
+
+
+def from_dev(t):
+    import numpy as np
+    return t.cpu().numpy().view(np.uint64)
