@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark of the NTT extractor path on GB300.
+
+Default workload (one step = one extraction through the C ABI): the Circulant
+extractor, single instance, n + 1 = 16777259 (the smallest prime >= 2^24 with
+primitive root 2), x of n bits and seed y of n + 1 bits, i.i.d. Bernoulli(1/2)
+from a fixed seed, m = n / 2 output bits.  Transform length L = 2^25.
+
+Printed: ONE JSON line (rank 0) with the output throughput in Gbit/s (inputs
+resident in HBM), the roofline of the dominant kernel (CUDA events on the
+launching stream, via the library's tracing hook), the end-to-end figure
+through cm_extract_host (host buffers, copies inside the timed region), the
+CPU oracle timed on a bounded sample, SM clocks sampled during the timed
+region, and the number of kernel launches.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cm|reference]
+                    [--workload circulant|toeplitz|dodis]
+
+N > 1 runs N independent replicas (one extraction per GPU per step, no
+collective on the data path); value is the sum over ranks divided by the
+slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # kind, n (input length n_1), m, seed-length formula
+    "circulant": dict(kind=1, n=16777258, m=8388629,
+                      name="Circulant single instance: n+1 = 16777259 (smallest N_A prime >= 2^24), "
+                           "m = n/2, Bernoulli(1/2) x and y"),
+    "toeplitz": dict(kind=0, n=1 << 16, m=1 << 15,
+                     name="Toeplitz single instance: n = 2^16, m = 2^15, Bernoulli(1/2) x and y"),
+    "dodis": dict(kind=2, n=1073741789, m=429496715,
+                  name="Dodis et al. single instance: n = 1073741789 (largest N_A prime <= 2^30), "
+                       "m = floor(0.4 n), Bernoulli(1/2) x and y"),
+}
+KIND_NAMES = {0: "toeplitz", 1: "circulant", 2: "dodis"}
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def seed_bits(kind, n, m):
+    return n + m - 1 if kind == 0 else (n + 1 if kind == 1 else n)
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2402_09481_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    with open(path) as f:
+        for line in f:
+            p = line.split()
+            if len(p) >= 4 and not line.startswith("#") and p[0] == kernel and p[1] == workload:
+                return float(p[2]) if p[3] == src else None
+    return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 100 ms, with host timestamps."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [s.strip() for s in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        inside = [s for (t, s) in self.samples if t0 <= t <= t1]
+        if not inside and self.samples:
+            # timed region shorter than the sampling period: nearest samples
+            mid = 0.5 * (t0 + t1)
+            inside = [min(self.samples, key=lambda ts: abs(ts[0] - mid))[1]]
+        if not inside:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for s in inside:
+            try:
+                sm.append(float(s[0]))
+                mx.append(float(s[1]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if len(s) > 3 + k and s[3 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(kernel, L, n, seedlen, m):
+    """Bytes one launch must move: u64 field elements (8 B), bits (1/8 B),
+    parity bytes (1 B)."""
+    if kernel == "k_middle":
+        return 24 * L                       # read both operands' rows, write one
+    if kernel == "k_pass_fwd_bits":
+        return 8 * L + (n + seedlen) / 16   # write one operand; read its bits (avg)
+    if kernel in ("k_pass_fwd", "k_pass_inv"):
+        return 16 * L
+    if kernel == "k_pass_inv_parity":
+        return 8 * L + m                    # read, write parity bytes of the window
+    if kernel == "k_pack":
+        return m + m / 8
+    if kernel == "k_fused_small":
+        return (n + seedlen + m) / 8
+    if kernel == "k_allsame":
+        return n / 8
+    return None
+
+
+def path_bytes(L, n, seedlen, m):
+    """48L + bit I/O: one write and one read of three L-element u64 arrays."""
+    return 48 * L + (n + seedlen + m) / 8
+
+
+def cpu_oracle_rate(kind, n, m, xw, yw, budget_s=12.0):
+    """Oracle output bits per second on a bounded sample of output rows."""
+    import numpy as np
+
+    import oracle
+    rows_fn = {0: lambda r: oracle.toeplitz_rows(xw, n, yw, m, r),
+               1: lambda r: oracle.circulant_rows(xw, n, yw, m, r),
+               2: lambda r: oracle.dodis_rows(xw, yw, n, m, r)}[kind]
+    rng = np.random.default_rng(7)
+    done, t_spent, batch = 0, 0.0, 16
+    while t_spent < budget_s:
+        rows = np.sort(rng.integers(0, m, size=batch))
+        t0 = time.perf_counter()
+        rows_fn(rows)
+        t_spent += time.perf_counter() - t0
+        done += batch
+        batch = min(batch * 2, 4096)
+    return done / t_spent, done, t_spent
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """The oracle as it stands, on the host cores: each step computes a bounded
+    sample of output rows of the same workload."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2402_09481_gb300 import inputs
+    wl = WORKLOADS[args.workload]
+    kind, n, m = wl["kind"], wl["n"], wl["m"]
+    xw = inputs.bernoulli_half(1, n)
+    yw = inputs.bernoulli_half(2, seed_bits(kind, n, m))
+    rows_per_step = int(os.environ.get("CM_REF_ROWS", "128"))
+    rng = np.random.default_rng(11)
+    fn = {0: lambda r: oracle.toeplitz_rows(xw, n, yw, m, r),
+          1: lambda r: oracle.circulant_rows(xw, n, yw, m, r),
+          2: lambda r: oracle.dodis_rows(xw, yw, n, m, r)}[kind]
+    for _ in range(args.warmup):
+        fn(np.sort(rng.integers(0, m, size=rows_per_step)))
+    times = []
+    for _ in range(args.steps):
+        r = np.sort(rng.integers(0, m, size=rows_per_step))
+        t0 = time.perf_counter()
+        fn(r)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = rows_per_step / (ms * 1e-3) / 1e9
+    sample = f"{rows_per_step} random output rows per step of the full-size workload (explicit GF(2) rows, numpy)"
+    line = {
+        "impl": "reference", "metric": "extracted output Gbit/s", "value": value, "unit": "Gbit/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": {"workload": wl["name"], "n": n, "m": m},
+        "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="cm", choices=["cm", "reference"])
+    ap.add_argument("--workload", default="circulant", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2402_09481_gb300 import build, inputs, native
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+
+    wl = WORKLOADS[args.workload]
+    kind, n, m = wl["kind"], wl["n"], wl["m"]
+    sb = seed_bits(kind, n, m)
+    L = native.ntt_length(kind, n, m)
+    launches = native.launch_count(kind, n, m)
+    ctx = native.Context(local)
+    stream = torch.cuda.current_stream()
+
+    xw = inputs.bernoulli_half(1 + 1000 * rank, n)
+    if kind == 2:
+        xw[0] = (xw[0] | np.uint64(1)) & ~np.uint64(2)
+    yw = inputs.bernoulli_half(2 + 1000 * rank, sb)
+    xd = torch.from_numpy(xw.view(np.int64)).cuda()
+    yd = torch.from_numpy(yw.view(np.int64)).cuda()
+    zd = torch.empty(native.words(m), dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    call = {0: lambda: ctx.toeplitz(xd, n, yd, m, zd),
+            1: lambda: ctx.circulant(xd, n, yd, m, zd),
+            2: lambda: ctx.dodis(xd, yd, n, m, zd)}[kind]
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        call()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.25)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    for k in range(args.steps):
+        flush.zero_()                     # L2 flush, outside the events
+        ev[k][0].record(stream)
+        call()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall1 = time.time()
+    time.sleep(0.25)
+    sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * m / (ms_per_step * 1e-3) / 1e9
+    s, flags = ctx.device_status()
+    if s != native.CM_OK:
+        raise RuntimeError(f"device status {native.STATUS.get(s)} flags {flags}")
+
+    # per-kernel device times (tracing hook: events on the launching stream)
+    ctx.profile_enable(True)
+    ctx.profile_read(reset=True)
+    for _ in range(args.steps):
+        flush.zero_()
+        call()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile_enable(False)
+    kernels = {k: {"launches": c, "avg_ms": t / c, "share": 0.0} for k, (c, t) in prof.items()}
+    tot = sum(t for _, t in prof.values()) or 1.0
+    for k, (c, t) in prof.items():
+        kernels[k]["share"] = t / tot
+    dom = max(prof, key=lambda k: prof[k][1])
+    per_launch = prof[dom][1] / prof[dom][0]
+    alg = algorithmic_bytes(dom, L, n, sb, m)
+    peak, peak_src = measured_peaks()
+    achieved = alg / (per_launch * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_src,
+            "traffic": ncu_traffic(dom, args.workload),
+            "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_launch}
+    pb = path_bytes(L, n, sb, m)
+    path_roof = {"bytes_48L": pb, "achieved_gbs": pb / (ms_per_step * 1e-3) / 1e9,
+                 "frac_of_measured_hbm": pb / (ms_per_step * 1e-3) / 1e9 / peak,
+                 "frac_of_8tbs": pb / (ms_per_step * 1e-3) / 1e9 / 8000.0}
+
+    # end to end through the public API with host buffers
+    xh = torch.from_numpy(xw.view(np.int64)).pin_memory()
+    yh = torch.from_numpy(yw.view(np.int64)).pin_memory()
+    zh = torch.empty(native.words(m), dtype=torch.int64).pin_memory()
+    for _ in range(3):
+        ctx.extract_host(kind, xh, n, yh, m, zh)
+    e2e_ms = []
+    for _ in range(max(3, min(args.steps, 50))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.extract_host(kind, xh, n, yh, m, zh)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    assert torch.equal(zh, zd.cpu()), "host-buffer result differs from device-buffer result"
+    e2e_mean = sum(e2e_ms) / len(e2e_ms)
+    e2e = {"value": world * m / (e2e_mean * 1e-3) / 1e9, "unit": "Gbit/s",
+           "h2d_bytes_per_step": 8 * (xw.size + yw.size), "d2h_bytes_per_step": 8 * native.words(m),
+           "ms_per_step": e2e_mean}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, rows, secs = cpu_oracle_rate(kind, n, m, xw, yw)
+        cpu = {"value": rate / 1e9, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
+               "sample": f"{rows} random output rows of the full-size workload in {secs:.1f} s "
+                         f"(explicit GF(2) rows, numpy, one thread)"}
+
+    clocks = sampler.summary(t_wall0, t_wall1)
+    if rank == 0:
+        line = {
+            "metric": "extracted output Gbit/s", "value": value, "unit": "Gbit/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": wl["name"], "n": n, "m": m, "L": L, "seed_bits": sb,
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "latency_ms": {"p50": statistics.median(step_ms),
+                           "p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},
+            "roofline": roof, "path_roofline": path_roof, "kernels": kernels,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": launches * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -117,6 +117,38 @@ cm_status cm_dodis(cm_ctx *ctx, const uint64_t *x, const uint64_t *y, uint64_t n
  * on a CUDA error, else CM_OK. */
 cm_status cm_device_status(cm_ctx *ctx, cm_stream stream, uint32_t *flags);
 
+/*
+ * End-to-end call on HOST buffers: copies x and y host->device, runs the
+ * extraction of `kind` (cm_kind) with the same argument rules as cm_toeplitz /
+ * cm_circulant / cm_dodis, copies z device->host, and synchronizes `stream`
+ * before returning.  x_host, y_host, z_host are host pointers (pinned memory
+ * gives full copy bandwidth; pageable works).  Word counts: x ceil(n/64);
+ * y ceil((n+m-1)/64) for Toeplitz, ceil((n+1)/64) for Circulant, ceil(n/64)
+ * for Dodis et al.; z ceil(m/64).  Device copies come from the context pool.
+ * Returns CM_EPRECOND (z zero-filled) for a constant Dodis et al. x.
+ */
+cm_status cm_extract_host(cm_ctx *ctx, int kind, const uint64_t *x_host, uint64_t n,
+                          const uint64_t *y_host, uint64_t m, uint64_t *z_host, cm_stream stream);
+
+/* ----- tracing ----------------------------------------------------------- */
+
+typedef struct {
+    char name[40];     /* kernel name */
+    uint64_t launches; /* launches since the last reset */
+    double total_ms;   /* summed device time between the events around them */
+} cm_profile_entry;
+
+/* Turn per-kernel tracing on (1) or off (0).  When on, every kernel the
+ * context enqueues is bracketed by two CUDA events recorded on the launching
+ * stream. */
+cm_status cm_profile_enable(cm_ctx *ctx, int on);
+
+/* Wait for the traced launches, then copy up to `cap` per-kernel summaries
+ * into out (sorted by name) and the number of distinct kernels into *count.
+ * reset != 0 clears the summaries afterwards. */
+cm_status cm_profile_read(cm_ctx *ctx, cm_profile_entry *out, uint32_t cap, uint32_t *count,
+                          int reset);
+
 /* ----- host helpers (no GPU work) --------------------------------------- */
 
 /* 1 if P is prime and 2 is a primitive root modulo P (the set N_A of the

@@ -112,6 +112,7 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
     if (p.kind == CM_DODIS) {
         pre = reinterpret_cast<uint32_t *>(sc + p.scratch_bytes - 256);
         if ((e = cudaMemsetAsync(pre, 0, 2 * sizeof(uint32_t), st)) != cudaSuccess) return cuda_status(e);
+        ProfScope ps(ctx, "k_allsame", st);
         if ((e = launch_allsame(x, p.n, pre, ctx->nsm, st)) != cudaSuccess) return cuda_status(e);
     }
     if (p.npass == 0) {
@@ -126,6 +127,7 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
         q.status = ctx->d_status;
         q.rt = ctx->rt;
         q.stream = st;
+        ProfScope ps(ctx, "k_fused_small", st);
         return cuda_status(launch_small(q, p.lg));
     }
     uint64_t *A = reinterpret_cast<uint64_t *>(sc);
@@ -152,10 +154,14 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
             a.L = p.L;
             a.inv = false;
             a.bits_in = (j == 0);
+            ProfScope ps(ctx, j == 0 ? "k_pass_fwd_bits" : "k_pass_fwd", st);
             if ((e = launch_pass(a, p.pass_lg[j], st)) != cudaSuccess) return cuda_status(e);
         }
     }
-    if ((e = launch_middle(A, B, p.L, linv, ctx->rt, st)) != cudaSuccess) return cuda_status(e);
+    {
+        ProfScope ps(ctx, "k_middle", st);
+        if ((e = launch_middle(A, B, p.L, linv, ctx->rt, st)) != cudaSuccess) return cuda_status(e);
+    }
     for (int j = p.npass - 1; j >= 0; --j) {
         PassArgs a;
         memset(&a, 0, sizeof(a));
@@ -169,8 +175,10 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
         a.par = par;
         a.lo = p.lo;
         a.m = p.m;
+        ProfScope ps(ctx, j == 0 ? "k_pass_inv_parity" : "k_pass_inv", st);
         if ((e = launch_pass(a, p.pass_lg[j], st)) != cudaSuccess) return cuda_status(e);
     }
+    ProfScope ps(ctx, "k_pack", st);
     return cuda_status(launch_pack(par, p.m, z, pre, ctx->d_status, ctx->nsm, st));
 }
 
@@ -196,6 +204,33 @@ cm_status run_single(cm_ctx *ctx, int kind, const uint64_t *x, uint64_t n, const
         if (s == CM_OK && e != cudaSuccess) s = CM_EDEVICE;
     }
     return s;
+}
+
+static cudaEvent_t get_event(cm_ctx *c) {
+    cudaEvent_t ev = nullptr;
+    if (!c->ev_pool.empty()) {
+        ev = c->ev_pool.back();
+        c->ev_pool.pop_back();
+    } else if (cudaEventCreate(&ev) != cudaSuccess) {
+        return nullptr;
+    }
+    return ev;
+}
+
+ProfScope::ProfScope(cm_ctx *c_, const char *name_, cudaStream_t st_) : c(c_), name(name_), st(st_) {
+    if (!c->prof_on) return;
+    std::lock_guard<std::mutex> g(c->prof_mu);
+    a = get_event(c);
+    if (a) cudaEventRecord(a, st);
+}
+
+ProfScope::~ProfScope() {
+    if (!a) return;
+    std::lock_guard<std::mutex> g(c->prof_mu);
+    cudaEvent_t b = get_event(c);
+    if (!b) return;
+    cudaEventRecord(b, st);
+    c->prof_pending.push_back({name, a, b});
 }
 
 static void build_tables(std::vector<uint64_t> &h) {
@@ -287,6 +322,11 @@ extern "C" void cm_destroy(cm_ctx *c) {
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     cm_ctx_release_extras(c);
+    for (auto &r : c->prof_pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto ev : c->ev_pool) cudaEventDestroy(ev);
     if (c->d_tables) cudaFree(c->d_tables);
     if (c->d_status) cudaFree(c->d_status);
     if (c->pool) cudaMemPoolDestroy(c->pool);
@@ -348,4 +388,79 @@ extern "C" uint64_t cm_scratch_bytes(int kind, uint64_t n, uint64_t m) {
 extern "C" uint32_t cm_launch_count(int kind, uint64_t n, uint64_t m) {
     Plan p;
     return make_plan(kind, n, m, &p) ? p.launches : 0;
+}
+
+extern "C" cm_status cm_profile_enable(cm_ctx *ctx, int on) {
+    if (!ctx) return CM_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->prof_mu);
+    ctx->prof_on = on != 0;
+    return CM_OK;
+}
+
+extern "C" cm_status cm_profile_read(cm_ctx *ctx, cm_profile_entry *out, uint32_t cap,
+                                     uint32_t *count, int reset) {
+    if (!ctx) return CM_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->prof_mu);
+    cm_status st = CM_OK;
+    for (auto &r : ctx->prof_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+            st = CM_EDEVICE;
+        auto &acc = ctx->prof_acc[r.name];
+        acc.first += 1;
+        acc.second += ms;
+        ctx->ev_pool.push_back(r.a);
+        ctx->ev_pool.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
+    uint32_t k = 0;
+    for (auto &kv : ctx->prof_acc) {
+        if (out && k < cap) {
+            memset(out[k].name, 0, sizeof(out[k].name));
+            strncpy(out[k].name, kv.first.c_str(), sizeof(out[k].name) - 1);
+            out[k].launches = kv.second.first;
+            out[k].total_ms = kv.second.second;
+        }
+        ++k;
+    }
+    if (count) *count = k;
+    if (reset) ctx->prof_acc.clear();
+    return st;
+}
+
+extern "C" cm_status cm_extract_host(cm_ctx *ctx, int kind, const uint64_t *xh, uint64_t n,
+                                     const uint64_t *yh, uint64_t m, uint64_t *zh, cm_stream stream) {
+    if (!ctx || !xh || !yh || !zh) return CM_EINVAL;
+    Plan p;
+    if (!make_plan(kind, n, m, &p)) return CM_EINVAL;
+    const uint64_t ybits = kind == CM_TOEPLITZ ? n + m - 1 : (kind == CM_CIRCULANT ? n + 1 : n);
+    const uint64_t xw = (n + 63) / 64, yw = (ybits + 63) / 64, zw = (m + 63) / 64;
+    const uint64_t io = 8 * (xw + yw + zw) + 3 * 256;
+    if (p.scratch_bytes + io > ctx->budget) return CM_ENOMEM;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return CM_EDEVICE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *buf = nullptr;
+    if (cudaMallocFromPoolAsync(&buf, p.scratch_bytes + io, ctx->pool, st) != cudaSuccess) {
+        cudaGetLastError();
+        return CM_ENOMEM;
+    }
+    uint8_t *b = static_cast<uint8_t *>(buf);
+    uint64_t *xd = reinterpret_cast<uint64_t *>(b + p.scratch_bytes);
+    uint64_t *yd = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(xd) + ((8 * xw + 255) & ~255ull));
+    uint64_t *zd = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(yd) + ((8 * yw + 255) & ~255ull));
+    cm_status s = CM_OK;
+    if (cudaMemcpyAsync(xd, xh, 8 * xw, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(yd, yh, 8 * yw, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        s = CM_EDEVICE;
+    uint32_t pre_h[2] = {1, 1};
+    if (s == CM_OK) s = enqueue_extract(ctx, p, xd, yd, zd, p.scratch_bytes ? b : nullptr, st);
+    if (s == CM_OK && cudaMemcpyAsync(zh, zd, 8 * zw, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        s = CM_EDEVICE;
+    if (s == CM_OK && kind == CM_DODIS &&
+        cudaMemcpyAsync(pre_h, b + p.scratch_bytes - 256, sizeof(pre_h), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        s = CM_EDEVICE;
+    cudaFreeAsync(buf, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CM_EDEVICE;
+    if (s == CM_OK && kind == CM_DODIS && (pre_h[0] == 0 || pre_h[1] == 0)) s = CM_EPRECOND;
+    return s;
 }

@@ -3,6 +3,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
 #include "cm.h"
 #include "ntt_device.cuh"
 
@@ -17,7 +22,30 @@ struct cm_ctx {
     uint32_t *d_status = nullptr;
     cm::RootTables rt{};
     cm_server *server = nullptr;
+
+    // per-kernel tracing (cm_profile_*): events around each launch when on
+    struct ProfRec {
+        const char *name;
+        cudaEvent_t a, b;
+    };
+    bool prof_on = false;
+    std::mutex prof_mu;
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> ev_pool;
+    std::map<std::string, std::pair<uint64_t, double>> prof_acc;
 };
+
+namespace cm {
+// Brackets one kernel launch with profiling events when tracing is on.
+struct ProfScope {
+    cm_ctx *c;
+    const char *name;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    ProfScope(cm_ctx *c_, const char *name_, cudaStream_t st_);
+    ~ProfScope();
+};
+}  // namespace cm
 
 // Frees what optional subsystems attached to the context (server, caches).
 void cm_ctx_release_extras(cm_ctx *c);

@@ -37,6 +37,9 @@ PROTOTYPES = {
     "cm_circulant": (_I, [_P, _P, _U64, _P, _U64, _P, _P]),
     "cm_dodis": (_I, [_P, _P, _P, _U64, _U64, _P, _P]),
     "cm_device_status": (_I, [_P, _P, ctypes.POINTER(_U32)]),
+    "cm_extract_host": (_I, [_P, _I, _P, _U64, _P, _U64, _P, _P]),
+    "cm_profile_enable": (_I, [_P, _I]),
+    "cm_profile_read": (_I, [_P, _P, _U32, ctypes.POINTER(_U32), _I]),
     "cm_is_na_prime": (_I, [_U64]),
     "cm_next_na_prime": (_U64, [_U64]),
     "cm_prev_na_prime": (_U64, [_U64]),
@@ -44,6 +47,11 @@ PROTOTYPES = {
     "cm_scratch_bytes": (_U64, [_I, _U64, _U64]),
     "cm_launch_count": (_U32, [_I, _U64, _U64]),
 }
+
+
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_uint64),
+                ("total_ms", ctypes.c_double)]
 
 
 class CMError(RuntimeError):
@@ -192,6 +200,33 @@ class Context:
         _check(self._L.cm_dodis(self._h, px, py, n, m, z.data_ptr(), _stream_handle(stream)),
                "cm_dodis")
         return z
+
+    def extract_host(self, kind: int, x, n: int, y, m: int, z, stream=None) -> int:
+        """End-to-end call on host buffers (torch CPU tensors, ideally pinned):
+        host->device copies, extraction, device->host copy, stream sync.
+        Returns the cm_status (CM_EPRECOND for a constant Dodis et al. x)."""
+        ybits = n + m - 1 if kind == TOEPLITZ else (n + 1 if kind == CIRCULANT else n)
+        for t, nb, nm in ((x, n, "x"), (y, ybits, "y"), (z, m, "z")):
+            if t.is_cuda or t.numel() < words(nb) or t.element_size() != 8 or not t.is_contiguous():
+                raise ValueError(f"{nm} must be a contiguous host tensor of >= {words(nb)} words")
+        s = self._L.cm_extract_host(self._h, kind, x.data_ptr(), n, y.data_ptr(), m, z.data_ptr(),
+                                    _stream_handle(stream))
+        if s not in (CM_OK, CM_EPRECOND):
+            raise CMError(s, "cm_extract_host")
+        return int(s)
+
+    def profile_enable(self, on: bool = True):
+        _check(self._L.cm_profile_enable(self._h, 1 if on else 0), "cm_profile_enable")
+
+    def profile_read(self, reset: bool = True) -> dict:
+        """{kernel name: (launches, total_ms)} for traced launches."""
+        cap = 64
+        buf = (ProfileEntry * cap)()
+        cnt = ctypes.c_uint32(0)
+        _check(self._L.cm_profile_read(self._h, ctypes.cast(buf, ctypes.c_void_p), cap,
+                                       ctypes.byref(cnt), 1 if reset else 0), "cm_profile_read")
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
+                for i in range(min(cap, cnt.value))}
 
     def device_status(self, stream=None) -> tuple[int, int]:
         f = ctypes.c_uint32(0)
