@@ -130,6 +130,39 @@ cm_status cm_device_status(cm_ctx *ctx, cm_stream stream, uint32_t *flags);
 cm_status cm_extract_host(cm_ctx *ctx, int kind, const uint64_t *x_host, uint64_t n,
                           const uint64_t *y_host, uint64_t m, uint64_t *z_host, cm_stream stream);
 
+/*
+ * Allocation-free Toeplitz extraction (the paper has no counterpart; this is a
+ * deployment interface).  Same arguments, bit layout and result as
+ * cm_toeplitz, but no context and no device allocation of any kind: it calls
+ * neither cudaMalloc nor cudaFree nor any allocating library routine.  It is
+ * for callers that cannot allocate device memory -- for example a host process
+ * whose device memory is fully reserved by another allocator, or a
+ * latency-critical loop that must never enter the driver's allocator -- and
+ * that therefore cannot create a cm_ctx (cm_create allocates its tables and
+ * memory pool).
+ *
+ * Limit: n + m - 1 <= 2^20 (CM_NOALLOC_MAX_LEN); larger sizes return
+ * CM_EINVAL before any work is enqueued.  The scratch (two transform buffers of
+ * 2^20 words and 2^20 parity bytes) and the root tables are fixed-size
+ * __device__ arrays inside libcm.so: every GPU that loads the library holds
+ * them, about 19 MB, until the process exits.
+ *
+ * The first call on a device (the device current on the calling thread) sets
+ * that device up: it looks up the arrays' device addresses and fills the root
+ * tables with a kernel on the legacy default stream, then synchronizes.  Make
+ * that first call before any stream capture.  Later calls only enqueue work
+ * on `stream`.
+ *
+ * All calls on a device share the one scratch array, which keeps the last
+ * call's contents (nothing in it needs to start at zero: every word is written
+ * before it is read).  Calls whose work overlaps on the GPU -- on different
+ * streams, or from different threads without ordering -- race on the scratch
+ * and give wrong results; order them on one stream or with events.
+ */
+#define CM_NOALLOC_MAX_LEN (1ull << 20)
+cm_status cm_toeplitz_noalloc(const uint64_t *x, uint64_t n, const uint64_t *y, uint64_t m,
+                              uint64_t *z, cm_stream stream);
+
 /* ----- tracing ----------------------------------------------------------- */
 
 typedef struct {

@@ -38,6 +38,7 @@ PROTOTYPES = {
     "cm_dodis": (_I, [_P, _P, _P, _U64, _U64, _P, _P]),
     "cm_device_status": (_I, [_P, _P, ctypes.POINTER(_U32)]),
     "cm_extract_host": (_I, [_P, _I, _P, _U64, _P, _U64, _P, _P]),
+    "cm_toeplitz_noalloc": (_I, [_P, _U64, _P, _U64, _P, _P]),
     "cm_profile_enable": (_I, [_P, _I]),
     "cm_profile_read": (_I, [_P, _P, _U32, ctypes.POINTER(_U32), _I]),
     "cm_is_na_prime": (_I, [_U64]),
