@@ -182,6 +182,15 @@ cm_status cm_profile_enable(cm_ctx *ctx, int on);
 cm_status cm_profile_read(cm_ctx *ctx, cm_profile_entry *out, uint32_t cap, uint32_t *count,
                           int reset);
 
+/* ----- diagnostics ------------------------------------------------------ */
+
+/* Field self-test on `device`: for `count` inputs (fixed edge values, then
+ * SplitMix64 samples from `seed`) compares the device's Goldilocks add, sub,
+ * multiply and multiply-by-2^s (s = 0..96), written as 32-bit carry chains,
+ * with the plain 64-bit C forms of the same functions; *mismatches receives the
+ * number of disagreements (0 when correct).  Allocates and frees 8 bytes. */
+cm_status cm_field_selftest(int device, uint64_t count, uint64_t seed, uint64_t *mismatches);
+
 /* ----- host helpers (no GPU work) --------------------------------------- */
 
 /* 1 if P is prime and 2 is a primitive root modulo P (the set N_A of the

@@ -160,7 +160,7 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
     }
     {
         ProfScope ps(ctx, "k_middle", st);
-        if ((e = launch_middle(A, B, p.L, linv, ctx->rt, st)) != cudaSuccess) return cuda_status(e);
+        if ((e = launch_middle(A, B, p.L, linv, ctx->rt, ctx->nsm, st)) != cudaSuccess) return cuda_status(e);
     }
     for (int j = p.npass - 1; j >= 0; --j) {
         PassArgs a;
@@ -234,18 +234,15 @@ ProfScope::~ProfScope() {
 }
 
 static void build_tables(std::vector<uint64_t> &h) {
-    // layout: small_fwd[4096] small_inv[4096] big_lo_fwd[65536] big_hi_fwd[65536]
-    //         big_lo_inv[65536] big_hi_inv[65536]
-    h.assign(2 * 4096 + 4 * 65536, 0);
+    // layout: small[8192] = omega_8192^e; big_lo_fwd[65536] = g^e;
+    //         big_hi_fwd[65536] = g^(65536 e); big_lo_inv, big_hi_inv likewise for g^-1
+    h.assign(kTableWords, 0);
     const uint64_t g = gl_root_2_32_host(0), gi = gl_root_2_32_host(1);
-    const uint64_t w = gl_pow_host(g, 1ull << (32 - kSmallLg));   // omega_8192
-    const uint64_t wi = gl_pow_host(gi, 1ull << (32 - kSmallLg));
-    uint64_t a = 1, b = 1;
-    for (int e = 0; e < 4096; ++e) {
+    const uint64_t w = gl_pow_host(g, 1ull << (32 - kSmallLg));  // omega_8192
+    uint64_t a = 1;
+    for (int e = 0; e < 8192; ++e) {
         h[e] = a;
-        h[4096 + e] = b;
         a = gl_mul_host(a, w);
-        b = gl_mul_host(b, wi);
     }
     uint64_t *lf = &h[8192], *hf = lf + 65536, *li = hf + 65536, *hi = li + 65536;
     const uint64_t g16 = gl_pow_host(g, 65536), gi16 = gl_pow_host(gi, 65536);
@@ -303,8 +300,7 @@ extern "C" cm_status cm_create(cm_ctx **out, int device, const cm_options *opt) 
     }
     cudaMemcpy(c->d_tables, h.data(), h.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
     cudaMemset(c->d_status, 0, 64);
-    c->rt.small_fwd = c->d_tables;
-    c->rt.small_inv = c->d_tables + 4096;
+    c->rt.small = c->d_tables;
     c->rt.big_lo_fwd = c->d_tables + 8192;
     c->rt.big_hi_fwd = c->rt.big_lo_fwd + 65536;
     c->rt.big_lo_inv = c->rt.big_hi_fwd + 65536;

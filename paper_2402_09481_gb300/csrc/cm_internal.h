@@ -10,6 +10,7 @@ namespace cm {
 
 constexpr uint32_t kFlagPrecond = CM_FLAG_PRECOND;
 constexpr uint32_t kFlagTimeout = CM_FLAG_TIMEOUT;
+constexpr size_t kTableWords = 8192 + 4 * 65536;  // resident root tables
 
 // Arguments of the single-CTA extraction (L <= 2^13).
 struct Launch {
@@ -36,8 +37,10 @@ struct PassArgs {
 
 cudaError_t launch_small(const Launch &q, int lg);
 cudaError_t launch_pass(const PassArgs &a, int logr, cudaStream_t st);
+cudaError_t launch_pass_fwd(const PassArgs &a, int logr, cudaStream_t st);
+cudaError_t launch_pass_inv(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_middle(uint64_t *A, const uint64_t *B, uint64_t L, uint64_t linv,
-                          const RootTables &rt, cudaStream_t st);
+                          const RootTables &rt, int nsm, cudaStream_t st);
 cudaError_t launch_pack(const uint8_t *par, uint64_t m, uint64_t *z, const uint32_t *pre,
                         uint32_t *status, int nsm, cudaStream_t st);
 cudaError_t launch_allsame(const uint64_t *x, uint64_t n, uint32_t *flags, int nsm, cudaStream_t st);

@@ -1,0 +1,133 @@
+// NTT kernels of the extractor path (GB300, sm_103a).
+//
+// A length-L transform (L = 2^lg) is a product of in-place passes over HBM:
+//   L = R_1 * ... * R_k * B,  B <= 2^13 contiguous (on chip), R_j <= 2^12.
+// Forward pass j takes every block of N_j = R_j * S_j contiguous elements
+// (S_j = L / (R_1 ... R_j)) as an R_j x S_j matrix, transforms each column
+// (length R_j, stride S_j) and multiplies entry (k, c) by omega_{N_j}^(c k)
+// (the four-step split of Def. ntt).  The B-blocks are then transformed on
+// chip.  The inverse applies the exact inverse of every pass in reverse order,
+// so the frequency order in between never matters: the pointwise product of
+// Thm. convolution is taken in whatever order both operands share.
+//
+// Kernels:
+//   k_fused_small<LG>  whole extraction for L <= 2^13 in one CTA: bit unpack,
+//                      forward NTT of both operands, product * L^-1, inverse NTT,
+//                      parity of the output window, bit pack.
+//   k_pass<...>        one column pass; the first forward pass reads packed bits,
+//                      the last inverse pass writes parity bytes of the window.
+//   k_middle           B = 2^13 rows of both operands: forward row NTTs,
+//                      product * L^-1, inverse row NTT (one read of each operand,
+//                      one write).
+//   k_pack             parity bytes -> packed output words (and the Dodis
+//                      precondition: zero output if x is constant).
+//   k_allsame          Dodis precondition flags (any 1 bit, any 0 bit in x).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cm_internal.h"
+#include "ntt_device.cuh"
+
+namespace cm {
+
+// ---------------------------------------------------------------------------
+// Whole extraction on one CTA (L = 2^LG <= 2^13).
+// ---------------------------------------------------------------------------
+template <int LG>
+__global__ void __launch_bounds__(kThreads, 1)
+k_fused_small(BitMap amap, BitMap bmap, uint64_t lo, uint64_t m, uint64_t linv,
+              uint64_t *__restrict__ z, const uint32_t *__restrict__ pre,
+              uint32_t *__restrict__ status, RootTables rt) {
+    constexpr int L = 1 << LG;
+    extern __shared__ uint64_t smem[];
+    uint64_t *sA = smem;
+    uint64_t *sB = smem + sp_size(L);
+    uint64_t *tw = sB + sp_size(L);
+    load_roots<LG>(tw, rt.small);
+    for (int i = threadIdx.x; i < L; i += kThreads) {
+        sA[sp(i)] = amap.get(i);
+        sB[sp(i)] = bmap.get(i);
+    }
+    __syncthreads();
+    ntt_fwd<LG, 0, 2>(sA, sB, tw);
+    for (int i = threadIdx.x; i < L; i += kThreads)
+        sA[sp(i)] = gl_mul(gl_mul(sA[sp(i)], sB[sp(i)]), linv);
+    __syncthreads();
+    ntt_inv<LG, 0, 1>(sA, sA, tw);
+
+    const bool bad = pre && (pre[0] == 0u || pre[1] == 0u);
+    if (bad && threadIdx.x == 0) atomicOr(status, kFlagPrecond);
+    // window positions lo .. lo + m - 1, parity packed by warp ballots
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t nwords = (m + 63) >> 6;
+    for (uint64_t w = warp; w < nwords; w += kThreads / 32) {
+        const uint64_t p0 = (w << 6) + lane, p1 = p0 + 32;
+        const uint32_t b0 = (p0 < m) ? (uint32_t)(sA[sp((int)(lo + p0))] & 1u) : 0u;
+        const uint32_t b1 = (p1 < m) ? (uint32_t)(sA[sp((int)(lo + p1))] & 1u) : 0u;
+        const uint32_t w0 = __ballot_sync(0xffffffffu, b0);
+        const uint32_t w1 = __ballot_sync(0xffffffffu, b1);
+        if (lane == 0) z[w] = bad ? 0ull : ((uint64_t)w1 << 32 | w0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One column pass over tiles of R = 2^LOGR rows x C = 2^(kTileLg - LOGR) columns.
+// ---------------------------------------------------------------------------
+template <int LOGR, bool INV, bool BITS_IN, bool PARITY_OUT>
+__global__ void __launch_bounds__(kThreads, 1)
+k_pass(uint64_t *__restrict__ data, BitMap map, int lgN, int lgS, uint8_t *__restrict__ par,
+       uint64_t lo, uint64_t m, RootTables rt) {
+    constexpr int R = 1 << LOGR;
+    constexpr int NCOL_LG = kTileLg - LOGR;
+    constexpr int C = 1 << NCOL_LG;
+    extern __shared__ uint64_t smem[];
+    uint64_t *tw = smem + sp_size(R * C);
+    load_roots<LOGR>(tw, rt.small);
+    const uint64_t S = 1ull << lgS;
+    const uint64_t tiles_per_blk = S >> NCOL_LG;
+    const uint64_t tile = blockIdx.x;
+    const uint64_t blk = tile / tiles_per_blk;
+    const uint64_t col0 = (tile - blk * tiles_per_blk) << NCOL_LG;
+    const uint64_t base = (blk << lgN) + col0;
+    const int esh = 32 - lgN;  // omega_N = g^(2^(32 - lgN))
+
+    // rows are stored in the digit-reversed order of the on-chip transform:
+    // row p of the tile holds frequency pos_to_freq(p) (forward) and is read
+    // back as such (inverse), so the pass twiddle uses that frequency.
+    for (int e = threadIdx.x; e < R * C; e += kThreads) {
+        const int i = e >> NCOL_LG, c = e & (C - 1);
+        const uint64_t g = base + ((uint64_t)i << lgS) + c;
+        uint64_t v = BITS_IN ? map.get(g) : data[g];
+        if (INV) {
+            const uint64_t k = pos_to_freq<LOGR>(i);
+            const uint32_t E = (uint32_t)(((col0 + c) * k) << esh);
+            if (E) v = gl_mul(v, big_root(rt.big_lo_inv, rt.big_hi_inv, E));
+        }
+        smem[sp(e)] = v;
+    }
+    __syncthreads();
+    if (INV) {
+        ntt_inv<LOGR, NCOL_LG, 1>(smem, smem, tw);
+    } else {
+        ntt_fwd<LOGR, NCOL_LG, 1>(smem, smem, tw);
+    }
+    for (int e = threadIdx.x; e < R * C; e += kThreads) {
+        const int i = e >> NCOL_LG, c = e & (C - 1);
+        uint64_t v = smem[sp(e)];
+        const uint64_t g = base + ((uint64_t)i << lgS) + c;
+        if (!INV) {
+            const uint64_t k = pos_to_freq<LOGR>(i);
+            const uint32_t E = (uint32_t)(((col0 + c) * k) << esh);
+            if (E) v = gl_mul(v, big_root(rt.big_lo_fwd, rt.big_hi_fwd, E));
+        }
+        if (PARITY_OUT) {
+            const uint64_t p = g - lo;
+            if (g >= lo && p < m) par[p] = (uint8_t)(v & 1u);
+        } else {
+            data[g] = v;
+        }
+    }
+}
+
+}  // namespace cm

@@ -1,0 +1,29 @@
+// Launchers of the single-CTA extraction k_fused_small<LG>, LG = 1 .. 13.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cm_kernels.cuh"
+
+namespace cm {
+
+template <int LG>
+static cudaError_t launch_small_lg(const Launch &q) {
+    const size_t sm = (2 * sp_size(1 << LG) + (1 << LG)) * sizeof(uint64_t);
+    auto kern = k_fused_small<LG>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<1, kThreads, sm, q.stream>>>(q.amap, q.bmap, q.lo, q.m, q.linv, q.z, q.pre, q.status, q.rt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_small(const Launch &q, int lg) {
+    switch (lg) {
+#define CM_CASE(k) case k: return launch_small_lg<k>(q);
+        CM_CASE(1) CM_CASE(2) CM_CASE(3) CM_CASE(4) CM_CASE(5) CM_CASE(6) CM_CASE(7)
+        CM_CASE(8) CM_CASE(9) CM_CASE(10) CM_CASE(11) CM_CASE(12) CM_CASE(13)
+#undef CM_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace cm

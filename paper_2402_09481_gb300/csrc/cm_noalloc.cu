@@ -22,7 +22,6 @@ constexpr int kNoAllocMaxLg = 20;  // n + m - 1 <= 2^20
 constexpr uint64_t kNoAllocMaxL = 1ull << kNoAllocMaxLg;
 // A (8L) + B (8L) + parity bytes of the window (m <= L)
 constexpr size_t kNoAllocScratchBytes = 2 * 8 * kNoAllocMaxL + kNoAllocMaxL;
-constexpr size_t kTableWords = 2 * 4096 + 4 * 65536;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 static __device__ __align__(256) uint64_t g_noalloc_tables[kTableWords];
@@ -50,15 +49,12 @@ __device__ uint64_t pow_dev(uint64_t a, uint32_t e) {
     return r;
 }
 
-// Same table layout as the context's: omega_8192^e and its inverse (e < 4096),
-// then g^e, g^(2^16 e), g^-e, g^-(2^16 e) for e < 2^16.
-__global__ void k_noalloc_tables(uint64_t *t, uint64_t w, uint64_t wi, uint64_t g, uint64_t g16,
+// Same table layout as the context's: omega_8192^e (e < 8192), then g^e,
+// g^(2^16 e), g^-e, g^-(2^16 e) for e < 2^16.
+__global__ void k_noalloc_tables(uint64_t *t, uint64_t w, uint64_t g, uint64_t g16,
                                  uint64_t gi, uint64_t gi16) {
     const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < 4096) {
-        t[e] = pow_dev(w, e);
-        t[4096 + e] = pow_dev(wi, e);
-    }
+    if (e < 8192) t[e] = pow_dev(w, e);
     if (e < 65536) {
         uint64_t *base = t + 8192;
         base[e] = pow_dev(g, e);
@@ -84,9 +80,8 @@ cm_status setup_device(int dev, NoAllocDevice **out) {
             return CM_EDEVICE;
         const uint64_t g = gl_root_2_32_host(0), gi = gl_root_2_32_host(1);
         const uint64_t w = gl_pow_host(g, 1ull << (32 - kSmallLg));
-        const uint64_t wi = gl_pow_host(gi, 1ull << (32 - kSmallLg));
         const uint64_t g16 = gl_pow_host(g, 65536), gi16 = gl_pow_host(gi, 65536);
-        k_noalloc_tables<<<65536 / 256, 256, 0, 0>>>(d.tables, w, wi, g, g16, gi, gi16);
+        k_noalloc_tables<<<65536 / 256, 256, 0, 0>>>(d.tables, w, g, g16, gi, gi16);
         if (cudaGetLastError() != cudaSuccess) return CM_EDEVICE;
         if (cudaMemsetAsync(d.status, 0, sizeof(uint32_t) * 64, 0) != cudaSuccess) return CM_EDEVICE;
         if (cudaStreamSynchronize(0) != cudaSuccess) return CM_EDEVICE;
@@ -117,8 +112,7 @@ extern "C" cm_status cm_toeplitz_noalloc(const uint64_t *x, uint64_t n, const ui
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     RootTables rt;
-    rt.small_fwd = d->tables;
-    rt.small_inv = d->tables + 4096;
+    rt.small = d->tables;
     rt.big_lo_fwd = d->tables + 8192;
     rt.big_hi_fwd = rt.big_lo_fwd + 65536;
     rt.big_lo_inv = rt.big_hi_fwd + 65536;
@@ -162,7 +156,7 @@ extern "C" cm_status cm_toeplitz_noalloc(const uint64_t *x, uint64_t n, const ui
         a.bits_in = true;
         if ((s = status_of(launch_pass(a, p.pass_lg[0], st))) != CM_OK) return s;
     }
-    if ((s = status_of(launch_middle(A, B, p.L, linv, rt, st))) != CM_OK) return s;
+    if ((s = status_of(launch_middle(A, B, p.L, linv, rt, d->nsm, st))) != CM_OK) return s;
     PassArgs a = {};
     a.data = A;
     a.lgN = lgN;

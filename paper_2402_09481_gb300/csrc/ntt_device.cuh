@@ -16,15 +16,14 @@ namespace cm {
 constexpr int kThreads = 512;     // threads per CTA for every NTT kernel
 constexpr int kMidLgMax = 13;     // fused on-chip block: 2 operands x 2^13 x 8 B
 constexpr int kTileLg = 14;       // column-pass tile: 2^14 elements (128 KiB)
-constexpr int kSmallLg = 13;      // root table omega_{2^13}^e, e < 2^12
+constexpr int kSmallLg = 13;      // root table omega_{2^13}^e, e < 2^13
 
 // Shared-memory index with one pad word per 32 (breaks power-of-two strides).
 __device__ __forceinline__ int sp(int i) { return i + (i >> 5); }
 __host__ __device__ constexpr int sp_size(int n) { return n + (n >> 5) + 1; }
 
 struct RootTables {
-    const uint64_t *small_fwd;   // omega_{8192}^e,  e < 4096
-    const uint64_t *small_inv;   // omega_{8192}^-e
+    const uint64_t *small;       // omega_{8192}^e,  e < 8192
     const uint64_t *big_lo_fwd;  // g^e,            e < 2^16, g of order 2^32
     const uint64_t *big_hi_fwd;  // g^(2^16 e),     e < 2^16
     const uint64_t *big_lo_inv;
@@ -70,125 +69,158 @@ struct BitMap {
 };
 
 // ---------------------------------------------------------------------------
-// Radix-2 decimation-in-frequency network on NCOL interleaved columns of length
-// R = 2^LOGR stored in shared memory (element (i, c) at sp(i * NCOL + c)),
-// natural order in, bit-reversed order out.  Stages are grouped: each thread
-// loads 2^Q elements of one column, runs Q stages in registers and writes back.
-// Stage s pairs i and i + h, h = R >> (s + 1), as (a, b) -> (a + b, (a - b) w),
-// w = omega_{2h}^(i mod h) = omega_R^((i mod h) 2^s).
+// On-chip transforms: mixed-radix decimation in frequency over shared memory.
+//
+// A length-R column (R = 2^LOGR) of NCOL interleaved columns lives in shared
+// memory, element (i, c) at sp(i * NCOL + c).  The transform is a sequence of
+// steps of radix RD_j = 2^q_j <= 32 (the four-step split of Def. ntt applied
+// recursively): step j views each sub-block of N_j contiguous rows as an
+// RD_j x M_j matrix (M_j = N_j / RD_j), transforms every column i2 in registers,
+// multiplies output k1 by omega_{N_j}^(i2 k1) and writes it to row k1 M_j + i2,
+// so that each output row k1 becomes a sub-block of the next step.  The
+// in-register sub-transforms have length <= 32, so all their twiddles are
+// powers of two (omega_64 = 8) and cost shifts, not multiplies; one general
+// multiply per element per step remains.  The result sits in digit-reversed
+// order (position -> frequency: pos_to_freq).  The inverse applies the exact
+// inverse of each step in reverse order, mapping that order back to natural.
 // ---------------------------------------------------------------------------
-__host__ __device__ constexpr int ntt_nsteps(int logr) { return (logr + 3) / 4; }
-__host__ __device__ constexpr int ntt_q(int logr, int step) {
-    // split logr into ntt_nsteps(logr) parts, larger parts first
-    return logr / ntt_nsteps(logr) + (step < logr % ntt_nsteps(logr) ? 1 : 0);
+__host__ __device__ constexpr int st_n(int logr) { return (logr + 4) / 5; }
+__host__ __device__ constexpr int st_q(int logr, int j) {
+    return logr / st_n(logr) + (j < logr % st_n(logr) ? 1 : 0);
 }
-__host__ __device__ constexpr int ntt_s0(int logr, int step) {
-    return step == 0 ? 0 : ntt_s0(logr, step - 1) + ntt_q(logr, step - 1);
+__host__ __device__ constexpr int st_off(int logr, int j) {
+    return j == 0 ? 0 : st_off(logr, j - 1) + st_q(logr, j - 1);
 }
 
-template <int LOGR, int S0, int Q, int NCOL_LG, int NBUF>
-__device__ __forceinline__ void dif_step(uint64_t *s0, uint64_t *s1, const uint64_t *__restrict__ tw) {
-    constexpr int R = 1 << LOGR;
-    constexpr int HL = R >> (S0 + Q);
-    constexpr int NG = R >> Q;
-    constexpr int TWS_LG = kSmallLg - LOGR;  // omega_R = omega_8192^(2^TWS_LG)
-    constexpr int ITEMS = NG << NCOL_LG;
+__device__ __forceinline__ int bitrev_c(int k, int lg) {
+    int r = 0;
+#pragma unroll
+    for (int b = 0; b < 6; ++b)
+        if (b < lg) r |= ((k >> b) & 1) << (lg - 1 - b);
+    return r;
+}
+
+// In-register DFT of length 2^LQ <= 32 with omega = 2^(192 / 2^LQ):
+// natural order in, v[bitrev(k)] = X[k] out.
+template <int LQ>
+__device__ __forceinline__ void dft_reg(uint64_t *v) {
+    constexpr int RD = 1 << LQ;
+    // one flat loop with a constant trip count, so that every index and shift
+    // below is a compile-time constant after unrolling
+#pragma unroll
+    for (int j = 0; j < LQ * (RD / 2); ++j) {
+        const int lh = LQ - 1 - j / (RD / 2);  // stage with half-size h = 2^lh
+        const int h = 1 << lh;
+        const int b = j % (RD / 2);
+        const int pos = b % h, blk = (b / h) * 2 * h;
+        const uint64_t a = v[blk + pos], c = v[blk + pos + h];
+        v[blk + pos] = gl_add(a, c);
+        v[blk + pos + h] = gl_shl(gl_sub(a, c), (96 >> lh) * pos);
+    }
+}
+
+// Forward step J over NBUF buffers; tw[e] = omega_R^e, e < R.
+template <int LOGR, int J, int NCOL_LG, int NBUF>
+__device__ __forceinline__ void fwd_step(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
+    constexpr int OFF = st_off(LOGR, J), LQ = st_q(LOGR, J), RD = 1 << LQ;
+    constexpr int LN = LOGR - OFF, LM = LN - LQ;
+    constexpr int ITEMS = (1 << (LOGR - LQ)) << NCOL_LG;
     for (int item = threadIdx.x; item < ITEMS * NBUF; item += kThreads) {
         const int bi = item / ITEMS;
         const int it = item - bi * ITEMS;
         uint64_t *s = (NBUF == 2 && bi) ? s1 : s0;
         const int c = it & ((1 << NCOL_LG) - 1);
-        const int g = it >> NCOL_LG;
-        const int blk = g / HL, off = g - blk * HL;
-        const int base = blk * (R >> S0) + off;
-        uint64_t v[1 << Q];
+        const int rest = it >> NCOL_LG;
+        const int i2 = rest & ((1 << LM) - 1);
+        const int row0 = ((rest >> LM) << LN) + i2;
+        uint64_t v[RD];
 #pragma unroll
-        for (int t = 0; t < (1 << Q); ++t) v[t] = s[sp(((base + t * HL) << NCOL_LG) + c)];
+        for (int i1 = 0; i1 < RD; ++i1) v[i1] = s[sp(((row0 + (i1 << LM)) << NCOL_LG) + c)];
+        dft_reg<LQ>(v);
 #pragma unroll
-        for (int st = 0; st < Q; ++st) {
-            const int span = 1 << (Q - 1 - st);
-            const int h = R >> (S0 + st + 1);
-#pragma unroll
-            for (int t = 0; t < (1 << Q); ++t) {
-                if (t & span) continue;
-                const int pos = (off + t * HL) & (h - 1);
-                const uint64_t w = __ldg(tw + ((pos << (S0 + st)) << TWS_LG));
-                const uint64_t a = v[t], b = v[t + span];
-                v[t] = gl_add(a, b);
-                v[t + span] = gl_mul(gl_sub(a, b), w);
-            }
+        for (int k1 = 0; k1 < RD; ++k1) {
+            uint64_t x = v[bitrev_c(k1, LQ)];
+            if (LM > 0 && k1 > 0 && i2 > 0) x = gl_mul(x, tw[(i2 * k1) << OFF]);
+            s[sp(((row0 + (k1 << LM)) << NCOL_LG) + c)] = x;
         }
-#pragma unroll
-        for (int t = 0; t < (1 << Q); ++t) s[sp(((base + t * HL) << NCOL_LG) + c)] = v[t];
     }
 }
 
-// Inverse of dif_step (up to a factor 2 per stage) with inverse roots:
-// (A, B) -> (A + B w^-1, A - B w^-1), stages in reverse order.
-template <int LOGR, int S0, int Q, int NCOL_LG, int NBUF>
-__device__ __forceinline__ void dit_step(uint64_t *s0, uint64_t *s1, const uint64_t *__restrict__ twi) {
+// Exact inverse of fwd_step J (up to the factor RD), inverse roots.
+template <int LOGR, int J, int NCOL_LG, int NBUF>
+__device__ __forceinline__ void inv_step(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
     constexpr int R = 1 << LOGR;
-    constexpr int HL = R >> (S0 + Q);
-    constexpr int NG = R >> Q;
-    constexpr int TWS_LG = kSmallLg - LOGR;
-    constexpr int ITEMS = NG << NCOL_LG;
+    constexpr int OFF = st_off(LOGR, J), LQ = st_q(LOGR, J), RD = 1 << LQ;
+    constexpr int LN = LOGR - OFF, LM = LN - LQ;
+    constexpr int ITEMS = (1 << (LOGR - LQ)) << NCOL_LG;
     for (int item = threadIdx.x; item < ITEMS * NBUF; item += kThreads) {
         const int bi = item / ITEMS;
         const int it = item - bi * ITEMS;
         uint64_t *s = (NBUF == 2 && bi) ? s1 : s0;
         const int c = it & ((1 << NCOL_LG) - 1);
-        const int g = it >> NCOL_LG;
-        const int blk = g / HL, off = g - blk * HL;
-        const int base = blk * (R >> S0) + off;
-        uint64_t v[1 << Q];
+        const int rest = it >> NCOL_LG;
+        const int i2 = rest & ((1 << LM) - 1);
+        const int row0 = ((rest >> LM) << LN) + i2;
+        uint64_t v[RD];
 #pragma unroll
-        for (int t = 0; t < (1 << Q); ++t) v[t] = s[sp(((base + t * HL) << NCOL_LG) + c)];
-#pragma unroll
-        for (int st = Q - 1; st >= 0; --st) {
-            const int span = 1 << (Q - 1 - st);
-            const int h = R >> (S0 + st + 1);
-#pragma unroll
-            for (int t = 0; t < (1 << Q); ++t) {
-                if (t & span) continue;
-                const int pos = (off + t * HL) & (h - 1);
-                const uint64_t w = __ldg(twi + ((pos << (S0 + st)) << TWS_LG));
-                const uint64_t a = v[t], b = gl_mul(v[t + span], w);
-                v[t] = gl_add(a, b);
-                v[t + span] = gl_sub(a, b);
-            }
+        for (int k1 = 0; k1 < RD; ++k1) {
+            uint64_t x = s[sp(((row0 + (k1 << LM)) << NCOL_LG) + c)];
+            if (LM > 0 && k1 > 0 && i2 > 0) x = gl_mul(x, tw[(R - ((i2 * k1) << OFF)) & (R - 1)]);
+            v[k1] = x;
         }
+        dft_reg<LQ>(v);
+        // inverse DFT output i1 is the forward output at frequency -i1 mod RD
 #pragma unroll
-        for (int t = 0; t < (1 << Q); ++t) s[sp(((base + t * HL) << NCOL_LG) + c)] = v[t];
+        for (int i1 = 0; i1 < RD; ++i1)
+            s[sp(((row0 + (i1 << LM)) << NCOL_LG) + c)] = v[bitrev_c((RD - i1) & (RD - 1), LQ)];
     }
 }
 
-template <int LOGR, int STEP, int NCOL_LG, int NBUF>
-__device__ __forceinline__ void dif_from(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
-    if constexpr (STEP < ntt_nsteps(LOGR)) {
-        dif_step<LOGR, ntt_s0(LOGR, STEP), ntt_q(LOGR, STEP), NCOL_LG, NBUF>(s0, s1, tw);
+template <int LOGR, int J, int NCOL_LG, int NBUF>
+__device__ __forceinline__ void fwd_from(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
+    if constexpr (J < st_n(LOGR)) {
+        fwd_step<LOGR, J, NCOL_LG, NBUF>(s0, s1, tw);
         __syncthreads();
-        dif_from<LOGR, STEP + 1, NCOL_LG, NBUF>(s0, s1, tw);
+        fwd_from<LOGR, J + 1, NCOL_LG, NBUF>(s0, s1, tw);
     }
 }
-
-template <int LOGR, int STEP, int NCOL_LG, int NBUF>
-__device__ __forceinline__ void dit_from(uint64_t *s0, uint64_t *s1, const uint64_t *twi) {
-    if constexpr (STEP >= 0) {
-        dit_step<LOGR, ntt_s0(LOGR, STEP), ntt_q(LOGR, STEP), NCOL_LG, NBUF>(s0, s1, twi);
+template <int LOGR, int J, int NCOL_LG, int NBUF>
+__device__ __forceinline__ void inv_from(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
+    if constexpr (J >= 0) {
+        inv_step<LOGR, J, NCOL_LG, NBUF>(s0, s1, tw);
         __syncthreads();
-        dit_from<LOGR, STEP - 1, NCOL_LG, NBUF>(s0, s1, twi);
+        inv_from<LOGR, J - 1, NCOL_LG, NBUF>(s0, s1, tw);
     }
 }
 
-// Full DIF over LOGR (natural -> bit-reversed); ends with a barrier.
+// Forward transform of every column (natural -> digit-reversed); ends with a barrier.
 template <int LOGR, int NCOL_LG, int NBUF>
-__device__ __forceinline__ void ntt_dif(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
-    if constexpr (LOGR > 0) dif_from<LOGR, 0, NCOL_LG, NBUF>(s0, s1, tw);
+__device__ __forceinline__ void ntt_fwd(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
+    if constexpr (LOGR > 0) fwd_from<LOGR, 0, NCOL_LG, NBUF>(s0, s1, tw);
 }
-// Full DIT over LOGR (bit-reversed -> natural); ends with a barrier.
+// Inverse of ntt_fwd up to the factor R (digit-reversed -> natural); ends with a barrier.
 template <int LOGR, int NCOL_LG, int NBUF>
-__device__ __forceinline__ void ntt_dit(uint64_t *s0, uint64_t *s1, const uint64_t *twi) {
-    if constexpr (LOGR > 0) dit_from<LOGR, ntt_nsteps(LOGR) - 1, NCOL_LG, NBUF>(s0, s1, twi);
+__device__ __forceinline__ void ntt_inv(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
+    if constexpr (LOGR > 0) inv_from<LOGR, st_n(LOGR) - 1, NCOL_LG, NBUF>(s0, s1, tw);
+}
+
+// Frequency held at position p after ntt_fwd<LOGR>: the digits k_j of p (step 0
+// in the top bits) reassembled least-significant first.
+template <int LOGR>
+__device__ __forceinline__ uint32_t pos_to_freq(uint32_t p) {
+    uint32_t f = 0;
+#pragma unroll
+    for (int j = 0; j < st_n(LOGR); ++j) {
+        const int q = st_q(LOGR, j), off = st_off(LOGR, j);
+        f |= ((p >> (LOGR - off - q)) & ((1u << q) - 1)) << off;
+    }
+    return f;
+}
+
+// Fill tw[e] = omega_R^e (e < R) from the global table of omega_8192^e.
+template <int LOGR>
+__device__ __forceinline__ void load_roots(uint64_t *tw, const uint64_t *__restrict__ g8192) {
+    for (int e = threadIdx.x; e < (1 << LOGR); e += kThreads) tw[e] = __ldg(g8192 + (e << (kSmallLg - LOGR)));
 }
 
 __device__ __forceinline__ int bitrev(int k, int lg) {

@@ -39,6 +39,7 @@ PROTOTYPES = {
     "cm_device_status": (_I, [_P, _P, ctypes.POINTER(_U32)]),
     "cm_extract_host": (_I, [_P, _I, _P, _U64, _P, _U64, _P, _P]),
     "cm_toeplitz_noalloc": (_I, [_P, _U64, _P, _U64, _P, _P]),
+    "cm_field_selftest": (_I, [_I, _U64, _U64, ctypes.POINTER(_U64)]),
     "cm_profile_enable": (_I, [_P, _I]),
     "cm_profile_read": (_I, [_P, _P, _U32, ctypes.POINTER(_U32), _I]),
     "cm_is_na_prime": (_I, [_U64]),
@@ -105,6 +106,13 @@ def scratch_bytes(kind: int, n: int, m: int) -> int:
 
 def launch_count(kind: int, n: int, m: int) -> int:
     return int(lib().cm_launch_count(kind, n, m))
+
+
+def field_selftest(device: int = 0, count: int = 1 << 20, seed: int = 1) -> int:
+    """Number of disagreements between the device field arithmetic and its C form."""
+    bad = ctypes.c_uint64(0)
+    _check(lib().cm_field_selftest(device, count, seed, ctypes.byref(bad)), "cm_field_selftest")
+    return int(bad.value)
 
 
 def is_na_prime(P: int) -> bool:

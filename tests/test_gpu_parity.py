@@ -193,3 +193,9 @@ def test_dodis_workload_size(cm_ctx):
     check_tail(z, m)
     rows = sample_rows(m, k=16)
     assert (out_bits(z, m, rows) == oracle.dodis_rows(xw, yw, n, m, rows)).all()
+
+
+def test_field_selftest_device_arithmetic(cm_ctx):
+    # the PTX carry-chain arithmetic against the C forms (which the CPU test
+    # pins to 128-bit integers), on edge values and 4M random pairs
+    assert native.field_selftest(0, 1 << 22, 12345) == 0
