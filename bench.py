@@ -244,19 +244,215 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batched_a(args, world, rank, local):
+    """4096 Toeplitz extractions, n = floor(2^U), U ~ U[10, 22), m = n/2, each with
+    its own Bernoulli(1/2) input and seed; one step = one replay of the planned
+    batch (a single persistent work-list launch, CUDA-graph captured)."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_2402_09481_gb300 import build, inputs, native
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    count = int(os.environ.get("CM_BATCH_COUNT", "4096"))
+    ns = inputs.loguniform_lengths(1, count, 10, 22)
+    ms = ns // 2
+    xw_off = np.concatenate([[0], np.cumsum((ns + 63) // 64)])
+    yw_off = np.concatenate([[0], np.cumsum((ns + ms - 1 + 63) // 64)])
+    zw_off = np.concatenate([[0], np.cumsum((ms + 63) // 64)])
+    xh = np.empty(int(xw_off[-1]), dtype=np.uint64)
+    yh = np.empty(int(yw_off[-1]), dtype=np.uint64)
+    for j in range(count):
+        xh[xw_off[j]:xw_off[j + 1]] = inputs.bernoulli_half(10000 + 2 * j + 100000 * rank, int(ns[j]))
+        yh[yw_off[j]:yw_off[j + 1]] = inputs.bernoulli_half(10001 + 2 * j + 100000 * rank,
+                                                            int(ns[j] + ms[j] - 1))
+    xd = torch.from_numpy(xh.view(np.int64)).cuda()
+    yd = torch.from_numpy(yh.view(np.int64)).cuda()
+    zd = torch.zeros(int(zw_off[-1]), dtype=torch.int64, device="cuda")
+    ctx = native.Context(local)
+    arr = (native.CmDesc * count)()
+    for j in range(count):
+        arr[j] = native.CmDesc(native.TOEPLITZ, 0, int(ns[j]), int(ms[j]),
+                               xd.data_ptr() + 8 * int(xw_off[j]), yd.data_ptr() + 8 * int(yw_off[j]),
+                               zd.data_ptr() + 8 * int(zw_off[j]))
+    h = ctypes.c_void_p()
+    t0 = time.time()
+    st = native.lib().cm_batch_create(ctx.handle, ctypes.cast(arr, ctypes.c_void_p), count,
+                                      native.BATCH_AUTOTUNE, ctypes.byref(h))
+    if st != native.CM_OK:
+        raise native.CMError(st, "cm_batch_create")
+    b = native.Batch(ctx, h, [])
+    plan_s = time.time() - t0
+    info = b.info()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        b.launch()
+    torch.cuda.synchronize()
+    z_ref = zd.clone()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.25)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    tw0 = time.time()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        b.launch()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    tw1 = time.time()
+    time.sleep(0.25)
+    sampler.stop()
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    out_bits = int(ms.sum())
+    value = world * out_bits / (ms_per_step * 1e-3) / 1e9
+    assert torch.equal(zd, z_ref), "replays differ"
+    s_, f_ = ctx.device_status()
+    if s_ != native.CM_OK:
+        raise RuntimeError(f"device status {native.STATUS.get(s_)} flags {f_}")
+
+    # the plain per-call form on the same inputs: one cm_toeplitz per instance
+    zp = torch.zeros_like(zd)
+    L_ = native.lib()
+    sh = stream.cuda_stream
+
+    def plain():
+        for j in range(count):
+            r = L_.cm_toeplitz(ctx.handle, arr[j].x, int(ns[j]), arr[j].y, int(ms[j]),
+                               zp.data_ptr() + 8 * int(zw_off[j]), sh)
+            if r != native.CM_OK:
+                raise native.CMError(r, "cm_toeplitz")
+    plain()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plain_ms = []
+    for _ in range(max(1, min(3, args.steps))):
+        e0.record(stream)
+        plain()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms.append(e0.elapsed_time(e1))
+    assert torch.equal(zp, zd), "batched output differs from the per-call output"
+    plain_value = world * out_bits / (statistics.median(plain_ms) * 1e-3) / 1e9
+
+    # roofline of the work-list kernel (the only kernel of a step)
+    Ls = np.array([native.ntt_length(native.TOEPLITZ, int(n), int(m)) for n, m in zip(ns, ms)])
+    big = Ls > (1 << 13)
+    alg = float(48 * Ls[big].sum() + ((ns + (ns + ms - 1) + ms) / 8).sum())
+    peak, peak_src = measured_peaks()
+    ctx.profile_enable(True)
+    ctx.profile_read(reset=True)
+    for _ in range(args.steps):
+        b.launch()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile_enable(False)
+    kb = prof.get("k_batch", (1, ms_per_step))
+    per_launch = kb[1] / kb[0]
+    achieved = alg / (per_launch * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_batch", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic("k_batch", "batched_a"),
+            "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_launch}
+
+    # end to end: host inputs (pinned) -> device, batch, outputs -> host
+    xp = torch.from_numpy(xh.view(np.int64)).pin_memory()
+    yp = torch.from_numpy(yh.view(np.int64)).pin_memory()
+    zh = torch.empty(zd.numel(), dtype=torch.int64).pin_memory()
+    e2e_ms = []
+    for _ in range(max(1, min(3, args.steps))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xd.copy_(xp, non_blocking=True)
+        yd.copy_(yp, non_blocking=True)
+        b.launch()
+        zh.copy_(zd, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_mean = sum(e2e_ms) / len(e2e_ms)
+    e2e = {"value": world * out_bits / (e2e_mean * 1e-3) / 1e9, "unit": "Gbit/s",
+           "h2d_bytes_per_step": 8 * (xh.size + yh.size), "d2h_bytes_per_step": 8 * int(zw_off[-1]),
+           "ms_per_step": e2e_mean}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        rng = np.random.default_rng(3)
+        done, secs = 0, 0.0
+        while secs < 10.0:
+            j = int(rng.integers(0, count))
+            rows = np.sort(rng.integers(0, int(ms[j]), size=32))
+            t0 = time.perf_counter()
+            oracle.toeplitz_rows(xh[xw_off[j]:xw_off[j + 1]], int(ns[j]), yh[yw_off[j]:yw_off[j + 1]],
+                                 int(ms[j]), rows)
+            secs += time.perf_counter() - t0
+            done += 32
+        cpu = {"value": done / secs / 1e9, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
+               "sample": f"{done} output rows from random instances of the batch in {secs:.1f} s "
+                         "(explicit GF(2) rows, numpy, one thread)"}
+    clocks = sampler.summary(tw0, tw1)
+    if rank == 0:
+        line = {
+            "metric": "extracted output Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": f"Batched Toeplitz: {count} instances, n = floor(2^U), U ~ U[10, 22), "
+                                   "m = floor(n/2), own Bernoulli(1/2) x and seed each",
+                       "sum_n": int(ns.sum()), "sum_m": out_bits, "sum_L": int(Ls.sum()),
+                       "l2": "working set (scratch %.1f GB) far larger than L2" % (info["scratch_bytes"] / 1e9),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "batch": {"work_items": info["work_items"], "tile_lg": info["tile_lg"], "grid": info["grid"],
+                      "graph": info["graph"], "plan_seconds": plan_s},
+            "plain_per_call": {"value": plain_value, "unit": "Gbit/s",
+                               "ms_per_step": statistics.median(plain_ms),
+                               "launches_per_step": sum(native.launch_count(native.TOEPLITZ, int(n), int(m))
+                                                        for n, m in zip(ns, ms))},
+            "latency_ms": {"p50": statistics.median(step_ms), "p99": max(step_ms)},
+            "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": int(info["kernel_launches"]) * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    b.close()
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="cm", choices=["cm", "reference"])
-    ap.add_argument("--workload", default="circulant", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="circulant", choices=sorted(WORKLOADS) + ["batched_a"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "batched_a":
+        run_batched_a(args, world, rank, local)
         return
 
     import numpy as np

@@ -163,6 +163,70 @@ cm_status cm_extract_host(cm_ctx *ctx, int kind, const uint64_t *x_host, uint64_
 cm_status cm_toeplitz_noalloc(const uint64_t *x, uint64_t n, const uint64_t *y, uint64_t m,
                               uint64_t *z, cm_stream stream);
 
+/* ----- batched extraction ------------------------------------------------ */
+
+/* One extraction of a batch.  Same argument rules as the single-call entry
+ * points of that kind; x, y, z are device pointers owned by the caller and must
+ * stay valid (and unchanged in place) for as long as the batch is launched. */
+typedef struct {
+    int32_t kind;       /* cm_kind */
+    uint32_t reserved;  /* 0 */
+    uint64_t n, m;      /* input length n_1 and output length, as for the single calls */
+    const uint64_t *x;
+    const uint64_t *y;
+    uint64_t *z;
+} cm_desc;
+
+#define CM_BATCH_AUTOTUNE 0x1u /* time the candidate pass tiles on this batch, keep the fastest */
+#define CM_BATCH_NO_GRAPH 0x2u /* do not capture a CUDA graph */
+
+typedef struct cm_batch cm_batch;
+
+typedef struct {
+    uint32_t instances, work_items, solo_instances, tile_lg, grid, graph;
+    uint64_t scratch_bytes, kernel_launches, output_bits, transform_elements;
+} cm_batch_stats;
+
+/*
+ * Plan a batch of `count` extractions of any mix of kinds (the paper has no
+ * batched form; each instance computes exactly what its single call computes).
+ * All instances with transform length L <= 2^25 run in ONE persistent kernel
+ * launch that walks a work list: an instance with L <= 2^13 is one item, a
+ * larger one is split into forward column-pass tiles, fused middle rows,
+ * inverse tiles with parity, and pack chunks, each item starting once the
+ * items it depends on are done (bounded waits; CM_FLAG_TIMEOUT if one runs
+ * out).  Instances with L > 2^25 run through the single-call kernels after it.
+ * Scratch for every instance is allocated here (cudaMalloc, held until
+ * cm_batch_destroy); CM_ENOMEM if it exceeds the context budget.  With
+ * CM_BATCH_AUTOTUNE the candidate column-pass tiles (2^14 and 2^13 elements)
+ * are timed on the batch itself and the faster is kept.  Unless
+ * CM_BATCH_NO_GRAPH, the launch sequence is captured once into a CUDA graph.
+ * CM_EINVAL if any descriptor is invalid (nothing is allocated).
+ */
+cm_status cm_batch_create(cm_ctx *ctx, const cm_desc *descs, uint32_t count, uint32_t flags,
+                          cm_batch **out);
+
+/* Enqueue one execution of the batch on `stream` (a graph launch when one was
+ * captured and tracing is off).  Asynchronous; the outputs are complete when
+ * the stream reaches this point.  Executions of one batch must not overlap
+ * (they share its scratch and work list). */
+cm_status cm_batch_launch(cm_batch *b, cm_stream stream);
+
+/* Synchronize the device and free the batch's scratch, work list and graph. */
+void cm_batch_destroy(cm_batch *b);
+
+/* Plan statistics: work items, pass tile chosen, scratch bytes, kernel launches
+ * per execution, total output bits and transform elements. */
+cm_status cm_batch_info(const cm_batch *b, cm_batch_stats *stats);
+
+/* One-shot batch: plan (no autotuning, no graph), run on `stream`, synchronize,
+ * free.  Returns after the outputs are written. */
+cm_status cm_batch_extract(cm_ctx *ctx, const cm_desc *descs, uint32_t count, cm_stream stream);
+
+/* cm_batch_extract for batches whose every descriptor is Toeplitz (CM_EINVAL
+ * otherwise). */
+cm_status cm_batch_toeplitz(cm_ctx *ctx, const cm_desc *descs, uint32_t count, cm_stream stream);
+
 /* ----- tracing ----------------------------------------------------------- */
 
 typedef struct {

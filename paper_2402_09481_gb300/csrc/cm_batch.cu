@@ -1,0 +1,575 @@
+// Batched extraction: one persistent kernel walking a work list.
+//
+// Every instance of a batch is planned like a single call (middle-product form,
+// transform length L = 2^lg).  Instances with L <= 2^13 are one work item (the
+// whole extraction on one CTA).  Instances with 2^13 < L <= 2^25 are split into
+// phases: forward column-pass tiles of both operands (phase 0, bits unpacked on
+// the fly), fused middle rows (phase 1), inverse column-pass tiles with parity
+// (phase 2) and pack chunks (phase 3).  Dodis et al. instances add a
+// precondition item to phase 0.  The list is ordered phase by phase, so an item
+// only ever waits for items that were dequeued before it by CTAs that are
+// running (the grid is sized to be fully resident); each wait is bounded and
+// gives up with CM_FLAG_TIMEOUT.  Instances with L > 2^25 (two column passes)
+// run through the per-call kernels after the work-list kernel.
+//
+// A batch is planned once (cm_batch_create: scratch, work list, optional
+// autotuning of the pass tile, CUDA-graph capture) and replayed with
+// cm_batch_launch.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "cm.h"
+#include "cm_ctx.h"
+#include "cm_internal.h"
+#include "ntt_generic.cuh"
+
+namespace cm {
+
+cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const uint64_t *y,
+                          uint64_t *z, void *scratch, cudaStream_t st);
+
+namespace {
+
+enum ItemType : uint16_t { kItSmall = 0, kItFwdA, kItFwdB, kItMiddle, kItInv, kItPack, kItCheck };
+constexpr int kPackWordsPerItem = 1 << 16;
+constexpr uint64_t kSpinLimit = 1ull << 22;  // polls of 64 ns-ish each before giving up
+
+struct BatchInst {
+    BitMap amap, bmap;
+    uint64_t *A, *B;
+    uint8_t *par;
+    uint64_t *z;
+    uint32_t *pre;  // Dodis et al.: {any 1 bit, any 0 bit} of x, else null
+    uint64_t lo, m, linv, nx;
+    int32_t lg, logr, tile_lg, kind;
+    uint32_t need[4];  // items per phase
+};
+
+struct WorkItem {
+    uint32_t inst;
+    uint16_t type;
+    uint16_t phase;
+    uint32_t idx;
+    uint32_t pad;
+};
+
+// ctrl layout (uint32): [0] next item, [1] abort, [2..] done[inst * 4 + phase]
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ void do_small(const BatchInst &I, const uint64_t *tw, uint64_t *sA, uint64_t *sB,
+                         uint32_t *status) {
+    const int lg = I.lg, L = 1 << lg;
+    int any1 = 0, any0 = 0;
+    for (int i = threadIdx.x; i < L; i += kThreads) {
+        sA[sp(i)] = I.amap.get(i);
+        sB[sp(i)] = I.bmap.get(i);
+    }
+    if (I.kind == CM_DODIS) {
+        for (uint64_t i = threadIdx.x; i < I.nx; i += kThreads) {
+            const uint64_t b = (__ldg(I.amap.src + (i >> 6)) >> (i & 63)) & 1ull;
+            any1 |= (int)b;
+            any0 |= (int)(b ^ 1);
+        }
+    }
+    any1 = __syncthreads_or(any1);
+    any0 = __syncthreads_or(any0);
+    const bool bad = I.kind == CM_DODIS && !(any1 && any0);
+    if (bad && threadIdx.x == 0) atomicOr(status, kFlagPrecond);
+    ntt_fwd_rt(sA, sB, 2, lg, 0, tw);
+    for (int i = threadIdx.x; i < L; i += kThreads) sA[sp(i)] = gl_mul(gl_mul(sA[sp(i)], sB[sp(i)]), I.linv);
+    __syncthreads();
+    ntt_inv_rt(sA, sA, 1, lg, 0, tw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t nwords = (I.m + 63) >> 6;
+    for (uint64_t w = warp; w < nwords; w += kThreads / 32) {
+        const uint64_t p0 = (w << 6) + lane, p1 = p0 + 32;
+        const uint32_t b0 = (p0 < I.m) ? (uint32_t)(sA[sp((int)(I.lo + p0))] & 1u) : 0u;
+        const uint32_t b1 = (p1 < I.m) ? (uint32_t)(sA[sp((int)(I.lo + p1))] & 1u) : 0u;
+        const uint32_t w0 = __ballot_sync(0xffffffffu, b0);
+        const uint32_t w1 = __ballot_sync(0xffffffffu, b1);
+        if (lane == 0) I.z[w] = bad ? 0ull : ((uint64_t)w1 << 32 | w0);
+    }
+}
+
+// Column-pass tile (the single pass of a 2^14 .. 2^25 transform: N = L).
+template <bool INV>
+__device__ void do_pass(const BatchInst &I, int operand, uint32_t tile, const uint64_t *tw, uint64_t *s,
+                        const RootTables &rt) {
+    const int logr = I.logr, lg = I.lg, ncol_lg = I.tile_lg - logr;
+    const int lgS = lg - logr, cmask = (1 << ncol_lg) - 1, n = 1 << I.tile_lg;
+    const uint64_t col0 = (uint64_t)tile << ncol_lg;
+    const int esh = 32 - lg;
+    uint64_t *data = operand ? I.B : I.A;
+    const BitMap &map = operand ? I.bmap : I.amap;
+    for (int e = threadIdx.x; e < n; e += kThreads) {
+        const int i = e >> ncol_lg, c = e & cmask;
+        const uint64_t g = col0 + ((uint64_t)i << lgS) + c;
+        uint64_t v;
+        if (INV) {
+            v = __ldcg(data + g);
+            const uint64_t k = pos_to_freq_rt(i, logr);
+            const uint32_t E = (uint32_t)(((col0 + c) * k) << esh);
+            if (E) v = gl_mul(v, big_root(rt.big_lo_inv, rt.big_hi_inv, E));
+        } else {
+            v = map.get(g);
+        }
+        s[sp(e)] = v;
+    }
+    __syncthreads();
+    if (INV)
+        ntt_inv_rt(s, s, 1, logr, ncol_lg, tw);
+    else
+        ntt_fwd_rt(s, s, 1, logr, ncol_lg, tw);
+    for (int e = threadIdx.x; e < n; e += kThreads) {
+        const int i = e >> ncol_lg, c = e & cmask;
+        uint64_t v = s[sp(e)];
+        const uint64_t g = col0 + ((uint64_t)i << lgS) + c;
+        if (INV) {
+            const uint64_t p = g - I.lo;
+            if (g >= I.lo && p < I.m) I.par[p] = (uint8_t)(v & 1u);
+        } else {
+            const uint64_t k = pos_to_freq_rt(i, logr);
+            const uint32_t E = (uint32_t)(((col0 + c) * k) << esh);
+            if (E) v = gl_mul(v, big_root(rt.big_lo_fwd, rt.big_hi_fwd, E));
+            data[g] = v;
+        }
+    }
+}
+
+__device__ void do_middle(const BatchInst &I, uint32_t r, const uint64_t *tw, uint64_t *sA, uint64_t *sB) {
+    constexpr int LG = kMidLgMax, Bn = 1 << LG;
+    const uint64_t row = (uint64_t)r << LG;
+    const ulonglong2 *a2 = reinterpret_cast<const ulonglong2 *>(I.A + row);
+    const ulonglong2 *b2 = reinterpret_cast<const ulonglong2 *>(I.B + row);
+    for (int i = threadIdx.x; i < Bn / 2; i += kThreads) {
+        const ulonglong2 va = __ldcg(a2 + i), vb = __ldcg(b2 + i);
+        sA[sp(2 * i)] = va.x;
+        sA[sp(2 * i + 1)] = va.y;
+        sB[sp(2 * i)] = vb.x;
+        sB[sp(2 * i + 1)] = vb.y;
+    }
+    __syncthreads();
+    ntt_fwd_rt(sA, sB, 2, LG, 0, tw);
+    for (int i = threadIdx.x; i < Bn; i += kThreads) sA[sp(i)] = gl_mul(gl_mul(sA[sp(i)], sB[sp(i)]), I.linv);
+    __syncthreads();
+    ntt_inv_rt(sA, sA, 1, LG, 0, tw);
+    ulonglong2 *o2 = reinterpret_cast<ulonglong2 *>(I.A + row);
+    for (int i = threadIdx.x; i < Bn / 2; i += kThreads) o2[i] = make_ulonglong2(sA[sp(2 * i)], sA[sp(2 * i + 1)]);
+}
+
+__device__ void do_pack(const BatchInst &I, uint32_t chunk, uint32_t *status) {
+    const bool bad = I.pre && (__ldcg(I.pre) == 0u || __ldcg(I.pre + 1) == 0u);
+    if (bad && chunk == 0 && threadIdx.x == 0) atomicOr(status, kFlagPrecond);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t nwords = (I.m + 63) >> 6;
+    const uint64_t w0 = (uint64_t)chunk * kPackWordsPerItem;
+    const uint64_t w1 = min(nwords, w0 + kPackWordsPerItem);
+    for (uint64_t w = w0 + warp; w < w1; w += kThreads / 32) {
+        const uint64_t p0 = (w << 6) + lane, p1 = p0 + 32;
+        const uint32_t b0 = (p0 < I.m) ? __ldcg(I.par + p0) : 0u;
+        const uint32_t b1 = (p1 < I.m) ? __ldcg(I.par + p1) : 0u;
+        const uint32_t x0 = __ballot_sync(0xffffffffu, b0);
+        const uint32_t x1 = __ballot_sync(0xffffffffu, b1);
+        if (lane == 0) I.z[w] = bad ? 0ull : ((uint64_t)x1 << 32 | x0);
+    }
+}
+
+__device__ void do_check(const BatchInst &I) {
+    int any1 = 0, any0 = 0;
+    const uint64_t nw = (I.nx + 63) >> 6;
+    for (uint64_t w = threadIdx.x; w < nw; w += kThreads) {
+        uint64_t mask = ~0ull;
+        if (w == nw - 1 && (I.nx & 63)) mask = (1ull << (I.nx & 63)) - 1;
+        const uint64_t v = __ldg(I.amap.src + w);
+        any1 |= (v & mask) != 0;
+        any0 |= (~v & mask) != 0;
+    }
+    any1 = __syncthreads_or(any1);
+    any0 = __syncthreads_or(any0);
+    if (threadIdx.x == 0) {
+        I.pre[0] = any1 ? 1u : 0u;
+        I.pre[1] = any0 ? 1u : 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_batch(const BatchInst *__restrict__ insts, const WorkItem *__restrict__ items, uint32_t nitems,
+        uint32_t *ctrl, uint32_t *status, RootTables rt) {
+    extern __shared__ uint64_t smem[];
+    uint64_t *tw = smem;                     // omega_8192^e
+    uint64_t *sA = smem + 8192;              // also the pass tile (2^14 elements)
+    uint64_t *sB = sA + sp_size(1 << kMidLgMax);
+    __shared__ uint32_t s_item, s_skip;
+    for (int e = threadIdx.x; e < 8192; e += kThreads) tw[e] = __ldg(rt.small + e);
+    uint32_t *next = ctrl, *abort_flag = ctrl + 1, *done = ctrl + 2;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = (ld_acquire(abort_flag) != 0u) ? nitems : atomicAdd(next, 1u);
+            s_skip = 0;
+        }
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= nitems) break;
+        const WorkItem w = items[it];
+        const BatchInst &I = insts[w.inst];
+        if (threadIdx.x == 0 && w.phase > 0 && w.type != kItSmall) {
+            const uint32_t need = I.need[w.phase - 1];
+            const uint32_t *cnt = done + 4 * w.inst + (w.phase - 1);
+            uint64_t spins = 0;
+            while (ld_acquire(cnt) < need) {
+                if (++spins > kSpinLimit || ld_acquire(abort_flag)) {
+                    atomicOr(status, kFlagTimeout);
+                    atomicExch(abort_flag, 1u);
+                    s_skip = 1;
+                    break;
+                }
+                __nanosleep(64);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        if (!s_skip) {
+            switch (w.type) {
+                case kItSmall: do_small(I, tw, sA, sB, status); break;
+                case kItFwdA: do_pass<false>(I, 0, w.idx, tw, sA, rt); break;
+                case kItFwdB: do_pass<false>(I, 1, w.idx, tw, sA, rt); break;
+                case kItMiddle: do_middle(I, w.idx, tw, sA, sB); break;
+                case kItInv: do_pass<true>(I, 0, w.idx, tw, sA, rt); break;
+                case kItPack: do_pack(I, w.idx, status); break;
+                case kItCheck: do_check(I); break;
+                default: break;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(done + 4 * w.inst + w.phase, 1u);
+        }
+    }
+}
+
+}  // namespace
+}  // namespace cm
+
+using namespace cm;
+
+struct cm_batch {
+    cm_ctx *ctx = nullptr;
+    std::vector<cm_desc> descs;
+    std::vector<Plan> plans;
+    std::vector<uint32_t> wl;       // instances on the work list
+    std::vector<uint32_t> solo;     // instances with L > 2^25 (per-call kernels)
+    std::vector<size_t> off_scratch;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    BatchInst *d_insts = nullptr;
+    WorkItem *d_items = nullptr;
+    uint32_t nitems = 0;
+    uint32_t *d_ctrl = nullptr;
+    size_t ctrl_words = 0;
+    int tile_lg = kTileLg;
+    int grid = 0;
+    uint64_t kernel_launches = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static size_t round256(size_t v) { return (v + 255) & ~size_t(255); }
+
+static const size_t kBatchSmem = (8192 + 2 * (size_t)sp_size(1 << kMidLgMax)) * sizeof(uint64_t);
+
+// Build instance descriptors and the work list for the current tile size.
+static cm_status batch_build(cm_batch *b) {
+    const uint32_t n = (uint32_t)b->wl.size();
+    std::vector<BatchInst> insts(n);
+    std::vector<WorkItem> phase[4];
+    std::vector<WorkItem> smalls;
+    // larger instances first inside each phase
+    std::vector<uint32_t> order(n);
+    for (uint32_t i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) {
+        return b->plans[b->wl[a]].L > b->plans[b->wl[c]].L;
+    });
+    uint8_t *sc = static_cast<uint8_t *>(b->scratch);
+    for (uint32_t k = 0; k < n; ++k) {
+        const uint32_t di = b->wl[k];
+        const Plan &p = b->plans[di];
+        const cm_desc &d = b->descs[di];
+        BatchInst &I = insts[k];
+        memset(&I, 0, sizeof(I));
+        I.amap.src = d.x; I.amap.mode = p.amode; I.amap.len = p.alen; I.amap.srclen = p.asrclen; I.amap.off = p.aoff;
+        I.bmap.src = d.y; I.bmap.mode = p.bmode; I.bmap.len = p.blen; I.bmap.srclen = p.bsrclen; I.bmap.off = p.boff;
+        I.z = d.z;
+        I.lo = p.lo;
+        I.m = p.m;
+        I.linv = gl_inv_pow2_host(p.L);
+        I.nx = p.n;
+        I.lg = p.lg;
+        I.kind = p.kind;
+        if (p.npass == 0) {
+            smalls.push_back({k, kItSmall, 0, 0, 0});
+            continue;
+        }
+        I.logr = p.pass_lg[0];
+        I.tile_lg = std::max(b->tile_lg, I.logr);  // at least one column per tile
+        uint8_t *base = sc + b->off_scratch[di];
+        I.A = reinterpret_cast<uint64_t *>(base);
+        I.B = I.A + p.L;
+        I.par = reinterpret_cast<uint8_t *>(I.B + p.L);
+        if (p.kind == CM_DODIS) I.pre = reinterpret_cast<uint32_t *>(I.par + round256(p.m));
+        const uint32_t tiles = (uint32_t)(p.L >> I.tile_lg);
+        const uint32_t rows = (uint32_t)(p.L >> kMidLgMax);
+        const uint32_t packs = (uint32_t)((((p.m + 63) >> 6) + kPackWordsPerItem - 1) / kPackWordsPerItem);
+        I.need[0] = 2 * tiles + (I.pre ? 1 : 0);
+        I.need[1] = rows;
+        I.need[2] = tiles;
+        I.need[3] = packs;
+        if (I.pre) phase[0].push_back({k, kItCheck, 0, 0, 0});
+        for (uint32_t t = 0; t < tiles; ++t) {
+            phase[0].push_back({k, kItFwdA, 0, t, 0});
+            phase[0].push_back({k, kItFwdB, 0, t, 0});
+        }
+        for (uint32_t r = 0; r < rows; ++r) phase[1].push_back({k, kItMiddle, 1, r, 0});
+        for (uint32_t t = 0; t < tiles; ++t) phase[2].push_back({k, kItInv, 2, t, 0});
+        for (uint32_t c = 0; c < packs; ++c) phase[3].push_back({k, kItPack, 3, c, 0});
+    }
+    // phase 0 (large forward tiles, then whole small instances), then 1, 2, 3
+    std::vector<WorkItem> items;
+    items.reserve(phase[0].size() + smalls.size() + phase[1].size() + phase[2].size() + phase[3].size());
+    std::vector<WorkItem> smalls_sorted(smalls);
+    std::stable_sort(smalls_sorted.begin(), smalls_sorted.end(), [&](const WorkItem &a, const WorkItem &c) {
+        return insts[a.inst].lg > insts[c.inst].lg;
+    });
+    for (auto &w : phase[0]) items.push_back(w);
+    for (auto &w : smalls_sorted) items.push_back(w);
+    for (int ph = 1; ph < 4; ++ph)
+        for (auto &w : phase[ph]) items.push_back(w);
+
+    if (b->d_insts) cudaFree(b->d_insts);
+    if (b->d_items) cudaFree(b->d_items);
+    b->d_insts = nullptr;
+    b->d_items = nullptr;
+    b->nitems = (uint32_t)items.size();
+    if (n && cudaMalloc(&b->d_insts, n * sizeof(BatchInst)) != cudaSuccess) return CM_ENOMEM;
+    if (!items.empty() && cudaMalloc(&b->d_items, items.size() * sizeof(WorkItem)) != cudaSuccess)
+        return CM_ENOMEM;
+    if (n && cudaMemcpy(b->d_insts, insts.data(), n * sizeof(BatchInst), cudaMemcpyHostToDevice) != cudaSuccess)
+        return CM_EDEVICE;
+    if (!items.empty() &&
+        cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) != cudaSuccess)
+        return CM_EDEVICE;
+    b->ctrl_words = 2 + 4 * (size_t)n;
+    if (!b->d_ctrl && cudaMalloc(&b->d_ctrl, b->ctrl_words * sizeof(uint32_t)) != cudaSuccess) return CM_ENOMEM;
+    return CM_OK;
+}
+
+// Enqueue one execution of the batch on st.
+static cm_status batch_enqueue(cm_batch *b, cudaStream_t st) {
+    cm_ctx *ctx = b->ctx;
+    b->kernel_launches = 0;
+    if (b->nitems) {
+        if (cudaMemsetAsync(b->d_ctrl, 0, b->ctrl_words * sizeof(uint32_t), st) != cudaSuccess) return CM_EDEVICE;
+        ProfScope ps(ctx, "k_batch", st);
+        k_batch<<<b->grid, kThreads, kBatchSmem, st>>>(b->d_insts, b->d_items, b->nitems, b->d_ctrl,
+                                                         ctx->d_status, ctx->rt);
+        if (cudaGetLastError() != cudaSuccess) return CM_EDEVICE;
+        b->kernel_launches += 1;
+    }
+    uint8_t *sc = static_cast<uint8_t *>(b->scratch);
+    for (uint32_t di : b->solo) {
+        const cm_desc &d = b->descs[di];
+        cm_status s = enqueue_extract(ctx, b->plans[di], d.x, d.y, d.z, sc + b->off_scratch[di], st);
+        if (s != CM_OK) return s;
+        b->kernel_launches += b->plans[di].launches;
+    }
+    return CM_OK;
+}
+
+static void batch_free(cm_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->d_insts) cudaFree(b->d_insts);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_ctrl) cudaFree(b->d_ctrl);
+    if (b->scratch) cudaFree(b->scratch);
+    delete b;
+}
+
+static double time_once(cm_batch *b, cudaStream_t st) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    batch_enqueue(b, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+extern "C" cm_status cm_batch_create(cm_ctx *ctx, const cm_desc *descs, uint32_t count, uint32_t flags,
+                                     cm_batch **out) {
+    if (!ctx || !out || (count && !descs)) return CM_EINVAL;
+    *out = nullptr;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return CM_EDEVICE;
+    cm_batch *b = new cm_batch();
+    b->ctx = ctx;
+    b->descs.assign(descs, descs + count);
+    b->plans.resize(count);
+    b->off_scratch.assign(count, 0);
+    size_t total = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+        const cm_desc &d = descs[i];
+        if (!d.x || !d.y || !d.z || !make_plan(d.kind, d.n, d.m, &b->plans[i])) {
+            delete b;
+            return CM_EINVAL;
+        }
+        const Plan &p = b->plans[i];
+        b->off_scratch[i] = total;
+        if (p.npass == 1) {
+            b->wl.push_back(i);
+            total += round256(16 * p.L) + round256(p.m) + (p.kind == CM_DODIS ? 256 : 0);
+        } else if (p.npass == 0) {
+            b->wl.push_back(i);
+        } else {
+            b->solo.push_back(i);
+            total += round256(p.scratch_bytes);
+        }
+    }
+    if (total > ctx->budget) {
+        delete b;
+        return CM_ENOMEM;
+    }
+    b->scratch_bytes = total;
+    if (total && cudaMalloc(&b->scratch, total) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return CM_ENOMEM;
+    }
+    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess) {
+        batch_free(b);
+        return CM_EDEVICE;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kThreads, kBatchSmem) != cudaSuccess ||
+        occ < 1) {
+        batch_free(b);
+        return CM_EDEVICE;
+    }
+    b->grid = ctx->nsm * occ;  // every CTA resident: waits never block a needed item
+    cm_status s = batch_build(b);
+    if (s != CM_OK) {
+        batch_free(b);
+        return s;
+    }
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        batch_free(b);
+        return CM_EDEVICE;
+    }
+    if ((flags & CM_BATCH_AUTOTUNE) && !b->wl.empty()) {
+        // autotuner: pass tile of 2^13 or 2^14 elements (columns per tile vs
+        // tiles in flight), timed on this batch; keep the faster
+        double best = 1e30;
+        int best_tile = kTileLg;
+        for (int tl : {kTileLg, kTileLg - 1}) {
+            b->tile_lg = tl;
+            if ((s = batch_build(b)) != CM_OK) break;
+            time_once(b, st);  // warm-up
+            const double ms = time_once(b, st);
+            if (ms < best) {
+                best = ms;
+                best_tile = tl;
+            }
+        }
+        b->tile_lg = best_tile;
+        if (s == CM_OK) s = batch_build(b);
+    }
+    if (s == CM_OK && !(flags & CM_BATCH_NO_GRAPH)) {
+        cudaStreamSynchronize(st);
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            s = CM_EDEVICE;
+        } else {
+            const bool prof = ctx->prof_on;
+            ctx->prof_on = false;  // no tracing events inside the graph
+            cm_status es = batch_enqueue(b, st);
+            ctx->prof_on = prof;
+            cudaError_t ce = cudaStreamEndCapture(st, &b->graph);
+            if (es != CM_OK || ce != cudaSuccess ||
+                cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
+                s = CM_EDEVICE;
+        }
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (s != CM_OK) {
+        batch_free(b);
+        return s;
+    }
+    *out = b;
+    return CM_OK;
+}
+
+extern "C" cm_status cm_batch_launch(cm_batch *b, cm_stream stream) {
+    if (!b) return CM_EINVAL;
+    if (cudaSetDevice(b->ctx->device) != cudaSuccess) return CM_EDEVICE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (b->exec && !b->ctx->prof_on) {
+        if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return CM_EDEVICE;
+        return CM_OK;
+    }
+    return batch_enqueue(b, st);
+}
+
+extern "C" void cm_batch_destroy(cm_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->ctx->device);
+    cudaDeviceSynchronize();
+    batch_free(b);
+}
+
+extern "C" cm_status cm_batch_info(const cm_batch *b, cm_batch_stats *st) {
+    if (!b || !st) return CM_EINVAL;
+    memset(st, 0, sizeof(*st));
+    st->instances = (uint32_t)b->descs.size();
+    st->work_items = b->nitems;
+    st->solo_instances = (uint32_t)b->solo.size();
+    st->tile_lg = (uint32_t)b->tile_lg;
+    st->grid = (uint32_t)b->grid;
+    st->scratch_bytes = b->scratch_bytes;
+    st->kernel_launches = b->kernel_launches;
+    st->graph = b->exec ? 1u : 0u;
+    for (uint32_t i = 0; i < b->descs.size(); ++i) {
+        st->output_bits += b->plans[i].m;
+        st->transform_elements += b->plans[i].L;
+    }
+    return CM_OK;
+}
+
+extern "C" cm_status cm_batch_extract(cm_ctx *ctx, const cm_desc *descs, uint32_t count, cm_stream stream) {
+    cm_batch *b = nullptr;
+    cm_status s = cm_batch_create(ctx, descs, count, CM_BATCH_NO_GRAPH, &b);
+    if (s != CM_OK) return s;
+    s = batch_enqueue(b, static_cast<cudaStream_t>(stream));
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess && s == CM_OK) s = CM_EDEVICE;
+    cm_batch_destroy(b);
+    return s;
+}
+
+extern "C" cm_status cm_batch_toeplitz(cm_ctx *ctx, const cm_desc *descs, uint32_t count, cm_stream stream) {
+    for (uint32_t i = 0; i < count; ++i)
+        if (!descs || descs[i].kind != CM_TOEPLITZ) return CM_EINVAL;
+    return cm_batch_extract(ctx, descs, count, stream);
+}

@@ -1,0 +1,113 @@
+// Runtime-size on-chip transforms for the batched work-list kernel.
+//
+// Same mixed-radix decimation-in-frequency steps as ntt_device.cuh (the
+// four-step split of Def. ntt applied recursively over shared memory, with
+// power-of-two twiddles inside each register sub-transform), but the column
+// length R = 2^logr and the column count are runtime values, so one kernel can
+// serve every instance of a batch.  Radices are at most 16 (q <= 4); the
+// register sub-transform is the only compile-time part.  All roots come from
+// one shared-memory table of omega_8192^e, e < 8192, read with stride
+// 2^(13 - logr).
+#pragma once
+#include <stdint.h>
+
+#include "ntt_device.cuh"
+
+namespace cm {
+
+__host__ __device__ constexpr int rt_nsteps(int logr) { return (logr + 3) / 4; }
+__host__ __device__ inline int rt_q(int logr, int j) {
+    const int n = rt_nsteps(logr);
+    return logr / n + (j < logr % n ? 1 : 0);
+}
+
+template <int LQ, bool INV>
+__device__ __forceinline__ void step_rt(uint64_t *s0, uint64_t *s1, int nbuf, int logr, int off,
+                                        int ncol_lg, const uint64_t *tw8192) {
+    constexpr int RD = 1 << LQ;
+    const int LN = logr - off, LM = LN - LQ;
+    const int items = (1 << (logr - LQ)) << ncol_lg;
+    const int tws = off + kSmallLg - logr;
+    const int cmask = (1 << ncol_lg) - 1, mmask = (1 << LM) - 1;
+    for (int item = threadIdx.x; item < items * nbuf; item += kThreads) {
+        const int bi = item >= items;
+        const int it = item - (bi ? items : 0);
+        uint64_t *s = bi ? s1 : s0;
+        const int c = it & cmask;
+        const int rest = it >> ncol_lg;
+        const int i2 = rest & mmask;
+        const int row0 = ((rest >> LM) << LN) + i2;
+        uint64_t v[RD];
+        if (!INV) {
+#pragma unroll
+            for (int i1 = 0; i1 < RD; ++i1) v[i1] = s[sp(((row0 + (i1 << LM)) << ncol_lg) + c)];
+            dft_reg<LQ>(v);
+#pragma unroll
+            for (int k1 = 0; k1 < RD; ++k1) {
+                uint64_t x = v[bitrev_c(k1, LQ)];
+                if (k1 > 0 && i2 > 0) x = gl_mul(x, tw8192[(i2 * k1) << tws]);
+                s[sp(((row0 + (k1 << LM)) << ncol_lg) + c)] = x;
+            }
+        } else {
+#pragma unroll
+            for (int k1 = 0; k1 < RD; ++k1) {
+                uint64_t x = s[sp(((row0 + (k1 << LM)) << ncol_lg) + c)];
+                if (k1 > 0 && i2 > 0) x = gl_mul(x, tw8192[(8192 - ((i2 * k1) << tws)) & 8191]);
+                v[k1] = x;
+            }
+            dft_reg<LQ>(v);
+#pragma unroll
+            for (int i1 = 0; i1 < RD; ++i1)
+                s[sp(((row0 + (i1 << LM)) << ncol_lg) + c)] = v[bitrev_c((RD - i1) & (RD - 1), LQ)];
+        }
+    }
+}
+
+template <bool INV>
+__device__ __forceinline__ void step_dispatch(int q, uint64_t *s0, uint64_t *s1, int nbuf, int logr,
+                                              int off, int ncol_lg, const uint64_t *tw) {
+    switch (q) {
+        case 1: step_rt<1, INV>(s0, s1, nbuf, logr, off, ncol_lg, tw); break;
+        case 2: step_rt<2, INV>(s0, s1, nbuf, logr, off, ncol_lg, tw); break;
+        case 3: step_rt<3, INV>(s0, s1, nbuf, logr, off, ncol_lg, tw); break;
+        default: step_rt<4, INV>(s0, s1, nbuf, logr, off, ncol_lg, tw); break;
+    }
+}
+
+// Forward transform of every column (natural -> digit-reversed); ends with a barrier.
+__device__ __forceinline__ void ntt_fwd_rt(uint64_t *s0, uint64_t *s1, int nbuf, int logr, int ncol_lg,
+                                           const uint64_t *tw) {
+    int off = 0;
+    for (int j = 0; j < rt_nsteps(logr); ++j) {
+        const int q = rt_q(logr, j);
+        step_dispatch<false>(q, s0, s1, nbuf, logr, off, ncol_lg, tw);
+        __syncthreads();
+        off += q;
+    }
+}
+
+// Inverse of ntt_fwd_rt up to the factor R; ends with a barrier.
+__device__ __forceinline__ void ntt_inv_rt(uint64_t *s0, uint64_t *s1, int nbuf, int logr, int ncol_lg,
+                                           const uint64_t *tw) {
+    int off = logr;
+    for (int j = rt_nsteps(logr) - 1; j >= 0; --j) {
+        const int q = rt_q(logr, j);
+        off -= q;
+        step_dispatch<true>(q, s0, s1, nbuf, logr, off, ncol_lg, tw);
+        __syncthreads();
+    }
+}
+
+// Frequency held at position p after ntt_fwd_rt(logr).
+__device__ __forceinline__ uint32_t pos_to_freq_rt(uint32_t p, int logr) {
+    uint32_t f = 0;
+    int off = 0;
+    for (int j = 0; j < rt_nsteps(logr); ++j) {
+        const int q = rt_q(logr, j);
+        f |= ((p >> (logr - off - q)) & ((1u << q) - 1)) << off;
+        off += q;
+    }
+    return f;
+}
+
+}  // namespace cm

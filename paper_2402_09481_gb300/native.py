@@ -40,6 +40,12 @@ PROTOTYPES = {
     "cm_extract_host": (_I, [_P, _I, _P, _U64, _P, _U64, _P, _P]),
     "cm_toeplitz_noalloc": (_I, [_P, _U64, _P, _U64, _P, _P]),
     "cm_field_selftest": (_I, [_I, _U64, _U64, ctypes.POINTER(_U64)]),
+    "cm_batch_create": (_I, [_P, _P, _U32, _U32, ctypes.POINTER(_P)]),
+    "cm_batch_launch": (_I, [_P, _P]),
+    "cm_batch_destroy": (None, [_P]),
+    "cm_batch_info": (_I, [_P, _P]),
+    "cm_batch_extract": (_I, [_P, _P, _U32, _P]),
+    "cm_batch_toeplitz": (_I, [_P, _P, _U32, _P]),
     "cm_profile_enable": (_I, [_P, _I]),
     "cm_profile_read": (_I, [_P, _P, _U32, ctypes.POINTER(_U32), _I]),
     "cm_is_na_prime": (_I, [_U64]),
@@ -54,6 +60,23 @@ PROTOTYPES = {
 class ProfileEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_uint64),
                 ("total_ms", ctypes.c_double)]
+
+
+class CmDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_uint32), ("n", ctypes.c_uint64),
+                ("m", ctypes.c_uint64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("z", ctypes.c_void_p)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("instances", ctypes.c_uint32), ("work_items", ctypes.c_uint32),
+                ("solo_instances", ctypes.c_uint32), ("tile_lg", ctypes.c_uint32),
+                ("grid", ctypes.c_uint32), ("graph", ctypes.c_uint32),
+                ("scratch_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("output_bits", ctypes.c_uint64), ("transform_elements", ctypes.c_uint64)]
+
+
+BATCH_AUTOTUNE, BATCH_NO_GRAPH = 0x1, 0x2
 
 
 class CMError(RuntimeError):
@@ -237,7 +260,60 @@ class Context:
         return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
                 for i in range(min(cap, cnt.value))}
 
+    @staticmethod
+    def _descs(items):
+        """items: (kind, n, m, x, y, z) with x, y, z CUDA word tensors."""
+        arr = (CmDesc * max(1, len(items)))()
+        for i, (kind, n, m, x, y, z) in enumerate(items):
+            ybits = n + m - 1 if kind == TOEPLITZ else (n + 1 if kind == CIRCULANT else n)
+            arr[i] = CmDesc(kind, 0, n, m, _dev_words(x, n, "x"), _dev_words(y, ybits, "y"),
+                            _dev_words(z, m, "z"))
+        return arr
+
+    def batch(self, items, autotune: bool = False, graph: bool = True) -> "Batch":
+        """Plan a batch (cm_batch_create); items are (kind, n, m, x, y, z)."""
+        arr = self._descs(items)
+        flags = (BATCH_AUTOTUNE if autotune else 0) | (0 if graph else BATCH_NO_GRAPH)
+        h = ctypes.c_void_p()
+        _check(self._L.cm_batch_create(self._h, ctypes.cast(arr, ctypes.c_void_p), len(items), flags,
+                                       ctypes.byref(h)), "cm_batch_create")
+        return Batch(self, h, items)
+
+    def batch_extract(self, items, stream=None):
+        """One-shot batch (cm_batch_extract): returns after the outputs are written."""
+        arr = self._descs(items)
+        _check(self._L.cm_batch_extract(self._h, ctypes.cast(arr, ctypes.c_void_p), len(items),
+                                        _stream_handle(stream)), "cm_batch_extract")
+
     def device_status(self, stream=None) -> tuple[int, int]:
         f = ctypes.c_uint32(0)
         s = self._L.cm_device_status(self._h, _stream_handle(stream), ctypes.byref(f))
         return int(s), int(f.value)
+
+
+class Batch:
+    """A planned batch (cm_batch); keeps its descriptors' tensors alive."""
+
+    def __init__(self, ctx: Context, handle, items):
+        self._ctx = ctx
+        self._h = handle
+        self._items = items
+
+    def launch(self, stream=None):
+        _check(self._ctx._L.cm_batch_launch(self._h, _stream_handle(stream)), "cm_batch_launch")
+
+    def info(self) -> dict:
+        st = BatchStats()
+        _check(self._ctx._L.cm_batch_info(self._h, ctypes.byref(st)), "cm_batch_info")
+        return {k: getattr(st, k) for k, _ in BatchStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._ctx._L.cm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
