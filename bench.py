@@ -437,13 +437,185 @@ def run_batched_a(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_batched_b(args, world, rank, local):
+    """65,536 inputs of n = 4096 bits under one shared Toeplitz seed, m = 2048:
+    one step = the whole dense product toep(y) X over GF(2) (engine chosen by
+    the library's autotuner), compared in the same run with each engine, the
+    NTT work-list batch and the plain per-call NTT."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_2402_09481_gb300 import build, inputs, native
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    count = int(os.environ.get("CM_SS_COUNT", "65536"))
+    n, m = 4096, 2048
+    wx, wz = n // 64, m // 64
+    yw = inputs.bernoulli_half(20 + 1000 * rank, n + m - 1)
+    X = inputs.bernoulli_half(21 + 1000 * rank, n * count)   # inputs back to back (n = 64 words each)
+    Xd = torch.from_numpy(X.view(np.int64)).cuda()
+    yd = torch.from_numpy(yw.view(np.int64)).cuda()
+    Z = torch.zeros(wz * count, dtype=torch.int64, device="cuda")
+    ctx = native.Context(local)
+    stream = torch.cuda.current_stream()
+    ctx.toeplitz_shared_seed(yd, n, m, Xd, count, Z)   # settles the AUTO engine
+    engine = native.lib().cm_shared_seed_engine(n, m)
+
+    def step(e=native.ENGINE_AUTO):
+        ctx.toeplitz_shared_seed(yd, n, m, Xd, count, Z, engine=e)
+
+    def timed(fn, k):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.25)
+    if dist:
+        dist.barrier()
+    tw0 = time.time()
+    step_ms = timed(step, args.steps)
+    tw1 = time.time()
+    if dist:
+        dist.barrier()
+    time.sleep(0.25)
+    sampler.stop()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    out_bits = count * m
+    value = world * out_bits / (ms_per_step * 1e-3) / 1e9
+    z_ref = Z.clone()
+
+    others = {}
+    for name, e in (("imma", native.ENGINE_IMMA), ("gf2", native.ENGINE_GF2)):
+        Z.zero_()
+        t = statistics.median(timed(lambda e=e: step(e), max(3, min(args.steps, 10))))
+        assert torch.equal(Z, z_ref), name
+        others[name] = {"value": world * out_bits / (t * 1e-3) / 1e9, "unit": "Gbit/s", "ms_per_step": t}
+    # the NTT paths on the same inputs (each input its own Toeplitz extraction)
+    Zn = torch.zeros_like(Z)
+    items = [(native.TOEPLITZ, n, m, Xd[c * wx:(c + 1) * wx], yd, Zn[c * wz:(c + 1) * wz]) for c in range(count)]
+    b = ctx.batch(items, autotune=False)
+    t = statistics.median(timed(b.launch, 3))
+    assert torch.equal(Zn, z_ref), "ntt batch"
+    others["ntt_worklist_batch"] = {"value": world * out_bits / (t * 1e-3) / 1e9, "unit": "Gbit/s",
+                                    "ms_per_step": t}
+    b.close()
+    Zn.zero_()
+    L_ = native.lib()
+    sh = stream.cuda_stream
+
+    def per_call():
+        for c in range(count):
+            L_.cm_toeplitz(ctx.handle, Xd.data_ptr() + 8 * wx * c, n, yd.data_ptr(), m,
+                           Zn.data_ptr() + 8 * wz * c, sh)
+    t = statistics.median(timed(per_call, 1))
+    assert torch.equal(Zn, z_ref), "per call"
+    others["plain_per_call_ntt"] = {"value": world * out_bits / (t * 1e-3) / 1e9, "unit": "Gbit/s",
+                                    "ms_per_step": t}
+
+    # roofline of the dense kernel
+    ctx.profile_enable(True)
+    ctx.profile_read(reset=True)
+    for _ in range(args.steps):
+        step()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile_enable(False)
+    kname = "k_ss_gf2" if engine == native.ENGINE_GF2 else "k_ss_imma"
+    c_, t_ = prof[kname]
+    per_launch = t_ / c_
+    clocks = sampler.summary(tw0, tw1)
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    if engine == native.ENGINE_GF2:
+        ops = count * m * (n // 32)           # LOP3 (32 AND + 32 XOR) per (output bit, 32-bit word)
+        peak = 152 * 64 * sm_mhz * 1e6        # ALU pipe: 64 lanes per SM per clock
+        roof = {"bound": "alu", "kernel": kname, "achieved": ops / (per_launch * 1e-3) / 1e12,
+                "peak": peak / 1e12, "unit": "T LOP3/s", "frac": ops / (per_launch * 1e-3) / peak,
+                "peak_source": "152 SMs x 64 ALU lanes x measured SM clock",
+                "traffic": ncu_traffic(kname, "batched_b"), "avg_launch_ms": per_launch}
+    else:
+        ops = 2 * count * m * n
+        roof = {"bound": "tensor", "kernel": kname, "achieved": ops / (per_launch * 1e-3) / 1e12,
+                "peak": None, "unit": "T int8 op/s", "frac": None, "avg_launch_ms": per_launch,
+                "traffic": ncu_traffic(kname, "batched_b")}
+    # end to end: inputs from pinned host memory, outputs back
+    Xp = torch.from_numpy(X.view(np.int64)).pin_memory()
+    Zh = torch.empty_like(Z, device="cpu").pin_memory()
+    e2e_ms = []
+    for _ in range(max(3, min(args.steps, 10))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Xd.copy_(Xp, non_blocking=True)
+        step()
+        Zh.copy_(Z, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_mean = sum(e2e_ms) / len(e2e_ms)
+    e2e = {"value": world * out_bits / (e2e_mean * 1e-3) / 1e9, "unit": "Gbit/s",
+           "h2d_bytes_per_step": 8 * X.size, "d2h_bytes_per_step": 8 * Z.numel(), "ms_per_step": e2e_mean}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        rng = np.random.default_rng(5)
+        done, secs = 0, 0.0
+        while secs < 10.0:
+            c = int(rng.integers(0, count))
+            t0 = time.perf_counter()
+            oracle.toeplitz_packed(X[c * wx:(c + 1) * wx], n, yw, m)
+            secs += time.perf_counter() - t0
+            done += m
+        cpu = {"value": done / secs / 1e9, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
+               "sample": f"{done // m} whole inputs ({done} output bits) in {secs:.1f} s "
+                         "(explicit GF(2) rows, numpy, one thread)"}
+    if rank == 0:
+        line = {
+            "metric": "extracted output Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 (GF(2) words)"
+            if engine == native.ENGINE_GF2 else "s8", "data": "synthetic",
+            "config": {"workload": f"Shared Toeplitz seed: {count} inputs of n = 4096 bits, m = 2048, "
+                                   "Bernoulli(1/2)", "engine": {1: "imma", 2: "gf2"}.get(engine),
+                       "l2": "inputs (%d MB) larger than L2" % (8 * X.size >> 20),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "compare": others, "latency_ms": {"p50": statistics.median(step_ms), "p99": max(step_ms)},
+            "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": 2 * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="cm", choices=["cm", "reference"])
-    ap.add_argument("--workload", default="circulant", choices=sorted(WORKLOADS) + ["batched_a"])
+    ap.add_argument("--workload", default="circulant", choices=sorted(WORKLOADS) + ["batched_a", "batched_b"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -453,6 +625,9 @@ def main():
         return
     if args.workload == "batched_a":
         run_batched_a(args, world, rank, local)
+        return
+    if args.workload == "batched_b":
+        run_batched_b(args, world, rank, local)
         return
 
     import numpy as np

@@ -227,6 +227,35 @@ cm_status cm_batch_extract(cm_ctx *ctx, const cm_desc *descs, uint32_t count, cm
  * otherwise). */
 cm_status cm_batch_toeplitz(cm_ctx *ctx, const cm_desc *descs, uint32_t count, cm_stream stream);
 
+/* ----- many inputs under one shared Toeplitz seed ------------------------- */
+
+#define CM_ENGINE_AUTO 0 /* faster of the two, timed on the first call of an (n, m) */
+#define CM_ENGINE_IMMA 1 /* INT8 tensor cores (mma.sync s8 x s8 -> s32), mod-2 epilogue */
+#define CM_ENGINE_GF2 2  /* CUDA cores: XOR of AND over packed words, parity epilogue */
+
+/*
+ * Z_c = toep(y) X_c over GF(2) for c < count: the Toeplitz extractor of Eq.
+ * toep-ext / Eq. toep applied to `count` inputs under ONE seed y (n + m - 1
+ * bits), computed as a dense blocked product of the m x n Toeplitz matrix
+ * (expanded once from y, packed bits, zero-padded to whole tiles) with the
+ * inputs.  X holds the inputs back to back, input c at word c*ceil(n/64)
+ * (n bits each); Z receives output c at word c*ceil(m/64) (m bits each, tail
+ * bits 0).  Device pointers, stream-ordered.  Every engine gives the same
+ * bits as cm_toeplitz on each input.  The paper has no batched form; this is
+ * its seeded extractor with the seed reused, which Section "Useful theorems
+ * and results" permits for strong extractors.
+ * Requires 1 <= n, m <= 2^24, n * m <= 2^34, 1 <= count <= 2^31, engine one
+ * of CM_ENGINE_*; CM_EINVAL otherwise.  Scratch: the expanded matrix,
+ * ceil(m/64)*64 * ceil(n/1024)*1024 / 8 bytes from the context pool.
+ */
+cm_status cm_batch_toeplitz_shared_seed(cm_ctx *ctx, const uint64_t *y, uint64_t n, uint64_t m,
+                                        const uint64_t *X, uint64_t count, uint64_t *Z, int engine,
+                                        cm_stream stream);
+
+/* Engine CM_ENGINE_AUTO settled on for (n, m) after its first call, or
+ * CM_ENGINE_AUTO if none yet (process-wide). */
+int cm_shared_seed_engine(uint64_t n, uint64_t m);
+
 /* ----- tracing ----------------------------------------------------------- */
 
 typedef struct {

@@ -1,0 +1,307 @@
+// Many inputs under one Toeplitz seed: Z = toep(y) X over GF(2) as a dense
+// blocked matrix product (Eq. toep-ext / Eq. toep applied to `count` inputs).
+//
+// The seed is expanded once into T, the m x n Toeplitz matrix of Eq. toep as
+// packed bit rows (T[i][j] = y[(i - j) mod (n + m - 1)], zero-padded to whole
+// tiles).  Two exact engines multiply T by the packed inputs:
+//
+//  * kImma: INT8 tensor cores (mma.sync m16n8k32, s8 x s8 -> s32).  Operand
+//    fragments are built in registers from the packed bits (4 bits -> 4 bytes of
+//    0/1 by one multiply and one mask); the int32 accumulators hold exact
+//    counts <= n, and the epilogue keeps bit 0 (mod 2).  sm_103a has no
+//    tcgen05 integer kind, so this is the warp-level MMA.
+//  * kGf2: CUDA cores.  Over GF(2) a dot product of bit vectors is the parity of
+//    popcount(AND); the kernel accumulates XOR(T_word AND X_word) (one LOP3 per
+//    32 bit-products) and takes the parity once per output.
+//
+// Both give identical bits; the default picks the faster on the first call of a
+// shape (timed on that call) and remembers it.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "cm.h"
+#include "cm_ctx.h"
+#include "cm_internal.h"
+
+namespace cm {
+namespace {
+
+constexpr int kSsRows = 64;     // output rows per CTA tile
+constexpr int kSsKw = 32;       // 32-bit words of K per smem chunk (1024 bits)
+constexpr int kGfCols = 256;    // GF(2) engine: instances per CTA tile
+constexpr int kImCols = 128;    // IMMA engine: instances per CTA tile
+
+// T bit rows: word w (32-bit) of row i holds bits j = 32 w .. 32 w + 31.
+__global__ void k_toep_rows(const uint64_t *__restrict__ y, uint64_t n, uint64_t m, uint32_t *T,
+                            uint32_t rows_pad, uint32_t words_pad) {
+    const uint64_t N = n + m - 1;
+    const uint64_t total = (uint64_t)rows_pad * words_pad;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = t / words_pad, w = t - i * words_pad;
+        uint32_t v = 0;
+        if (i < m) {
+            for (int b = 0; b < 32; ++b) {
+                const uint64_t j = 32 * w + b;
+                if (j >= n) break;
+                const uint64_t k = (i + N - (j % N)) % N;  // (i - j) mod N
+                v |= (uint32_t)((__ldg(y + (k >> 6)) >> (k & 63)) & 1ull) << b;
+            }
+        }
+        T[t] = v;
+    }
+}
+
+// 32-bit word w of instance c (zero past the instance's words).
+__device__ __forceinline__ uint32_t x_word(const uint64_t *X, uint64_t wx, uint64_t c, uint64_t w) {
+    if (w >= 2 * wx) return 0u;
+    const uint64_t v = __ldg(X + c * wx + (w >> 1));
+    return (w & 1) ? (uint32_t)(v >> 32) : (uint32_t)v;
+}
+
+// ---------------------------------------------------------------------------
+// GF(2) engine: thread tile 16 rows x 4 instances, XOR-of-AND accumulators.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_ss_gf2(const uint32_t *__restrict__ T, uint32_t words_pad, const uint64_t *__restrict__ X, uint64_t wx,
+         uint64_t count, uint64_t *__restrict__ Z, uint64_t wz) {
+    __shared__ __align__(16) uint32_t sT[kSsKw][kSsRows];    // [w][row]
+    __shared__ __align__(16) uint32_t sX[kSsKw][kGfCols];    // [w][col]
+    __shared__ uint16_t sOut[kGfCols][4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rg = warp & 3, cg = warp >> 2;
+    const uint32_t row0 = blockIdx.x * kSsRows;
+    const uint64_t col0 = (uint64_t)blockIdx.y * kGfCols;
+    uint32_t acc[16][4];
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = 0u;
+    for (uint32_t w0 = 0; w0 < words_pad; w0 += kSsKw) {
+        for (int e = threadIdx.x; e < kSsKw * kSsRows; e += 256) {
+            const int r = e / kSsKw, w = e % kSsKw;
+            sT[w][r] = __ldg(T + (uint64_t)(row0 + r) * words_pad + w0 + w);
+        }
+        {
+            const uint64_t c = col0 + threadIdx.x;
+            for (int w = 0; w < kSsKw; ++w) sX[w][threadIdx.x] = c < count ? x_word(X, wx, c, w0 + w) : 0u;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int w = 0; w < kSsKw; ++w) {
+            const uint4 x4 = *reinterpret_cast<const uint4 *>(&sX[w][cg * 128 + lane * 4]);
+            const uint32_t xv[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 t4 = *reinterpret_cast<const uint4 *>(&sT[w][rg * 16 + q * 4]);
+                const uint32_t tv[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[q * 4 + r][c] ^= tv[r] & xv[c];
+            }
+        }
+        __syncthreads();
+    }
+    // parity of each accumulator: 16 row bits per instance per thread
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uint32_t bits = 0;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) bits |= (uint32_t)(__popc(acc[r][c]) & 1) << r;
+        sOut[cg * 128 + lane * 4 + c][rg] = (uint16_t)bits;
+    }
+    __syncthreads();
+    const uint64_t c = col0 + threadIdx.x;
+    if (c < count) {
+        const uint64_t word = (uint64_t)sOut[threadIdx.x][0] | ((uint64_t)sOut[threadIdx.x][1] << 16) |
+                              ((uint64_t)sOut[threadIdx.x][2] << 32) | ((uint64_t)sOut[threadIdx.x][3] << 48);
+        Z[c * wz + (row0 >> 6)] = word;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// INT8 tensor-core engine: warp tile 32 rows x 32 instances (2 x 4 m16n8k32).
+// ---------------------------------------------------------------------------
+// 4 bits -> 4 bytes of 0/1 (bit k of b lands at bit 8k; the shifted copies do
+// not overlap, so no carries).
+__device__ __forceinline__ uint32_t expand4(uint32_t b) { return (b * 0x00204081u) & 0x01010101u; }
+
+__global__ void __launch_bounds__(256)
+k_ss_imma(const uint32_t *__restrict__ T, uint32_t words_pad, const uint64_t *__restrict__ X, uint64_t wx,
+          uint64_t count, uint64_t *__restrict__ Z, uint64_t wz) {
+    __shared__ __align__(16) uint32_t sT[kSsRows][kSsKw + 1];   // [row][w], padded
+    __shared__ __align__(16) uint32_t sX[kImCols][kSsKw + 1];   // [col][w], padded
+    __shared__ uint8_t sPar[kImCols][kSsRows];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int wr = warp & 1, wc = warp >> 1;  // warp tile: rows wr*32 .., cols wc*32 ..
+    const uint32_t row0 = blockIdx.x * kSsRows;
+    const uint64_t col0 = (uint64_t)blockIdx.y * kImCols;
+    int acc[2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[a][b][k] = 0;
+    for (uint32_t w0 = 0; w0 < words_pad; w0 += kSsKw) {
+        for (int e = threadIdx.x; e < kSsKw * kSsRows; e += 256) {
+            const int r = e / kSsKw, w = e % kSsKw;
+            sT[r][w] = __ldg(T + (uint64_t)(row0 + r) * words_pad + w0 + w);
+        }
+        for (int e = threadIdx.x; e < kSsKw * kImCols; e += 256) {
+            const int cc = e / kSsKw, w = e % kSsKw;
+            const uint64_t c = col0 + cc;
+            sX[cc][w] = c < count ? x_word(X, wx, c, w0 + w) : 0u;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int w = 0; w < kSsKw; ++w) {  // one k32 step per 32-bit word
+            uint32_t afr[2][4], bfr[4][2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const uint32_t lo = sT[wr * 32 + a * 16 + g][w], hi = sT[wr * 32 + a * 16 + g + 8][w];
+                afr[a][0] = expand4((lo >> (4 * t)) & 0xFu);
+                afr[a][1] = expand4((hi >> (4 * t)) & 0xFu);
+                afr[a][2] = expand4((lo >> (16 + 4 * t)) & 0xFu);
+                afr[a][3] = expand4((hi >> (16 + 4 * t)) & 0xFu);
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const uint32_t xv = sX[wc * 32 + b * 8 + g][w];
+                bfr[b][0] = expand4((xv >> (4 * t)) & 0xFu);
+                bfr[b][1] = expand4((xv >> (16 + 4 * t)) & 0xFu);
+            }
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                        "{%8,%9}, {%0,%1,%2,%3};"
+                        : "+r"(acc[a][b][0]), "+r"(acc[a][b][1]), "+r"(acc[a][b][2]), "+r"(acc[a][b][3])
+                        : "r"(afr[a][0]), "r"(afr[a][1]), "r"(afr[a][2]), "r"(afr[a][3]), "r"(bfr[b][0]),
+                          "r"(bfr[b][1]));
+        }
+        __syncthreads();
+    }
+    // mod-2 epilogue: accumulator (row g / g+8, cols 2t, 2t+1) -> parity bytes
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int r = wr * 32 + a * 16 + g, cc = wc * 32 + b * 8 + 2 * t;
+            sPar[cc][r] = (uint8_t)(acc[a][b][0] & 1);
+            sPar[cc + 1][r] = (uint8_t)(acc[a][b][1] & 1);
+            sPar[cc][r + 8] = (uint8_t)(acc[a][b][2] & 1);
+            sPar[cc + 1][r + 8] = (uint8_t)(acc[a][b][3] & 1);
+        }
+    __syncthreads();
+    // pack: one warp per instance column at a time, 64 rows -> one word
+    for (int cc = warp; cc < kImCols; cc += 8) {
+        const uint32_t lo = __ballot_sync(0xffffffffu, sPar[cc][lane]);
+        const uint32_t hi = __ballot_sync(0xffffffffu, sPar[cc][32 + lane]);
+        const uint64_t c = col0 + cc;
+        if (lane == 0 && c < count) Z[c * wz + (row0 >> 6)] = ((uint64_t)hi << 32) | lo;
+    }
+}
+
+std::mutex g_engine_mu;
+std::map<std::pair<uint64_t, uint64_t>, int> g_engine_choice;  // (n, m) -> engine
+
+cm_status launch_engine(int engine, const uint32_t *T, uint32_t rows_pad, uint32_t words_pad,
+                        const uint64_t *X, uint64_t wx, uint64_t count, uint64_t *Z, uint64_t wz,
+                        cm_ctx *ctx, cudaStream_t st) {
+    if (engine == CM_ENGINE_GF2) {
+        dim3 grid(rows_pad / kSsRows, (unsigned)((count + kGfCols - 1) / kGfCols));
+        ProfScope ps(ctx, "k_ss_gf2", st);
+        k_ss_gf2<<<grid, 256, 0, st>>>(T, words_pad, X, wx, count, Z, wz);
+    } else {
+        dim3 grid(rows_pad / kSsRows, (unsigned)((count + kImCols - 1) / kImCols));
+        ProfScope ps(ctx, "k_ss_imma", st);
+        k_ss_imma<<<grid, 256, 0, st>>>(T, words_pad, X, wx, count, Z, wz);
+    }
+    return cudaGetLastError() == cudaSuccess ? CM_OK : CM_EDEVICE;
+}
+
+}  // namespace
+}  // namespace cm
+
+using namespace cm;
+
+extern "C" cm_status cm_batch_toeplitz_shared_seed(cm_ctx *ctx, const uint64_t *y, uint64_t n, uint64_t m,
+                                                   const uint64_t *X, uint64_t count, uint64_t *Z,
+                                                   int engine, cm_stream stream) {
+    if (!ctx || !y || !X || !Z || n == 0 || m == 0 || count == 0) return CM_EINVAL;
+    if (engine != CM_ENGINE_AUTO && engine != CM_ENGINE_IMMA && engine != CM_ENGINE_GF2) return CM_EINVAL;
+    if (n > (1ull << 24) || m > (1ull << 24) || (n * m) > (1ull << 34) || count > (1ull << 31))
+        return CM_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return CM_EDEVICE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const uint32_t rows_pad = (uint32_t)((m + kSsRows - 1) / kSsRows * kSsRows);
+    const uint32_t words_pad = (uint32_t)((n + 32 * kSsKw - 1) / (32 * kSsKw) * kSsKw);
+    const uint64_t wx = (n + 63) / 64, wz = (m + 63) / 64;
+    const size_t tbytes = (size_t)rows_pad * words_pad * sizeof(uint32_t);
+    if (tbytes > ctx->budget) return CM_ENOMEM;
+    void *Tv = nullptr;
+    if (cudaMallocFromPoolAsync(&Tv, tbytes, ctx->pool, st) != cudaSuccess) {
+        cudaGetLastError();
+        return CM_ENOMEM;
+    }
+    uint32_t *T = static_cast<uint32_t *>(Tv);
+    cm_status s = CM_OK;
+    {
+        ProfScope ps(ctx, "k_toep_rows", st);
+        const uint64_t total = (uint64_t)rows_pad * words_pad;
+        uint64_t blocks = (total + 255) / 256;
+        if (blocks > (uint64_t)ctx->nsm * 16) blocks = (uint64_t)ctx->nsm * 16;
+        k_toep_rows<<<(unsigned)blocks, 256, 0, st>>>(y, n, m, T, rows_pad, words_pad);
+        if (cudaGetLastError() != cudaSuccess) s = CM_EDEVICE;
+    }
+    if (s == CM_OK && engine == CM_ENGINE_AUTO) {
+        std::lock_guard<std::mutex> lock(g_engine_mu);
+        auto it = g_engine_choice.find({n, m});
+        if (it != g_engine_choice.end()) {
+            engine = it->second;
+        } else {
+            // time both engines on this call (each writes the same Z) and keep the faster
+            float best = 1e30f;
+            int best_e = CM_ENGINE_GF2;
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            for (int e : {CM_ENGINE_IMMA, CM_ENGINE_GF2}) {
+                launch_engine(e, T, rows_pad, words_pad, X, wx, count, Z, wz, ctx, st);  // warm-up
+                cudaEventRecord(e0, st);
+                s = launch_engine(e, T, rows_pad, words_pad, X, wx, count, Z, wz, ctx, st);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (s == CM_OK && ms < best) {
+                    best = ms;
+                    best_e = e;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            g_engine_choice[{n, m}] = best_e;
+            engine = best_e;
+        }
+    }
+    if (s == CM_OK) s = launch_engine(engine, T, rows_pad, words_pad, X, wx, count, Z, wz, ctx, st);
+    cudaFreeAsync(Tv, st);
+    return s;
+}
+
+extern "C" int cm_shared_seed_engine(uint64_t n, uint64_t m) {
+    std::lock_guard<std::mutex> lock(g_engine_mu);
+    auto it = g_engine_choice.find({n, m});
+    return it == g_engine_choice.end() ? CM_ENGINE_AUTO : it->second;
+}

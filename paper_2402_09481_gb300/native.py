@@ -40,6 +40,8 @@ PROTOTYPES = {
     "cm_extract_host": (_I, [_P, _I, _P, _U64, _P, _U64, _P, _P]),
     "cm_toeplitz_noalloc": (_I, [_P, _U64, _P, _U64, _P, _P]),
     "cm_field_selftest": (_I, [_I, _U64, _U64, ctypes.POINTER(_U64)]),
+    "cm_batch_toeplitz_shared_seed": (_I, [_P, _P, _U64, _U64, _P, _U64, _P, _I, _P]),
+    "cm_shared_seed_engine": (_I, [_U64, _U64]),
     "cm_batch_create": (_I, [_P, _P, _U32, _U32, ctypes.POINTER(_P)]),
     "cm_batch_launch": (_I, [_P, _P]),
     "cm_batch_destroy": (None, [_P]),
@@ -77,6 +79,7 @@ class BatchStats(ctypes.Structure):
 
 
 BATCH_AUTOTUNE, BATCH_NO_GRAPH = 0x1, 0x2
+ENGINE_AUTO, ENGINE_IMMA, ENGINE_GF2 = 0, 1, 2
 
 
 class CMError(RuntimeError):
@@ -284,6 +287,20 @@ class Context:
         arr = self._descs(items)
         _check(self._L.cm_batch_extract(self._h, ctypes.cast(arr, ctypes.c_void_p), len(items),
                                         _stream_handle(stream)), "cm_batch_extract")
+
+    def toeplitz_shared_seed(self, y, n: int, m: int, X, count: int, Z=None, engine: int = ENGINE_AUTO,
+                             stream=None):
+        """count Toeplitz extractions under one seed y: X holds the inputs back to
+        back (ceil(n/64) words each); returns Z (ceil(m/64) words each)."""
+        import torch
+        py = _dev_words(y, n + m - 1, "y")
+        pX = _dev_words(X, words(n) * 64 * count, "X")
+        if Z is None:
+            Z = torch.empty(words(m) * count, dtype=torch.int64, device=X.device)
+        _dev_words(Z, words(m) * 64 * count, "Z")
+        _check(self._L.cm_batch_toeplitz_shared_seed(self._h, py, n, m, pX, count, Z.data_ptr(), engine,
+                                                     _stream_handle(stream)), "cm_batch_toeplitz_shared_seed")
+        return Z
 
     def device_status(self, stream=None) -> tuple[int, int]:
         f = ctypes.c_uint32(0)
