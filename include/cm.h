@@ -256,6 +256,67 @@ cm_status cm_batch_toeplitz_shared_seed(cm_ctx *ctx, const uint64_t *y, uint64_t
  * CM_ENGINE_AUTO if none yet (process-wide). */
 int cm_shared_seed_engine(uint64_t n, uint64_t m);
 
+/* ----- serving: continuous batching ------------------------------------- */
+
+/* One extraction request: same argument rules as the single calls; device
+ * pointers that must stay valid until the request is polled complete. */
+typedef struct {
+    int32_t kind;    /* cm_kind */
+    uint32_t flags;  /* 0 */
+    uint64_t n, m;
+    const uint64_t *x;
+    const uint64_t *y;
+    uint64_t *z;
+    uint64_t user;   /* free for the caller */
+} cm_request;
+
+typedef struct {
+    int32_t status;  /* CM_OK, CM_EPRECOND (Dodis et al. constant x, z zeroed), CM_ETIMEDOUT, ... */
+    uint32_t reserved;
+    uint64_t t_submit_ns, t_admit_ns, t_done_ns;  /* steady clock: submitted, sent to the GPU, seen done */
+    uint64_t wave;   /* the launch wave that carried it */
+} cm_result;
+
+typedef struct {
+    uint64_t hbm_budget_bytes; /* scratch of requests on the device at once; 0 = half the context budget */
+    uint32_t slots;            /* concurrent waves (CUDA streams); 0 = 2 */
+    uint32_t max_queue;        /* pending requests before cm_submit says CM_EAGAIN; 0 = 2^20 */
+    uint32_t max_wave;         /* requests per wave; 0 = 512 */
+    uint32_t reserved[5];
+} cm_server_options;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, waves;
+    uint64_t inflight_bytes, max_inflight_bytes, budget_bytes;
+    uint32_t queued, busy_slots, slots, reserved;
+} cm_server_stats;
+
+/*
+ * Start the request server of a context (one per context): a worker thread
+ * that admits pending requests in arrival order into waves whenever a slot is
+ * free, as long as their scratch fits in what the HBM budget leaves, and
+ * launches each wave as one work-list kernel (the cm_batch_create machinery)
+ * on the slot's stream; waves on different slots overlap on the device.  The
+ * paper has no serving layer; each request computes exactly its single call.
+ */
+cm_status cm_server_start(cm_ctx *ctx, const cm_server_options *opt);
+
+/* Drain the queue, wait for the device, stop the worker (cm_destroy also does). */
+cm_status cm_server_stop(cm_ctx *ctx);
+
+/* Queue one request; *ticket identifies it.  CM_EINVAL for invalid arguments
+ * or no server, CM_ENOMEM if its scratch alone exceeds the budget, CM_EAGAIN
+ * if the queue is full.  Thread-safe. */
+cm_status cm_submit(cm_ctx *ctx, const cm_request *req, uint64_t *ticket);
+
+/* Wait up to timeout_ns for the request; CM_OK with *res filled once it is
+ * done (the ticket is then released), CM_EAGAIN if it is not done yet,
+ * CM_ENOTFOUND for an unknown or already collected ticket.  Thread-safe. */
+cm_status cm_poll(cm_ctx *ctx, uint64_t ticket, cm_result *res, uint64_t timeout_ns);
+
+/* Counters of the server (queue depth, waves, bytes in flight and their peak). */
+cm_status cm_server_get_stats(cm_ctx *ctx, cm_server_stats *stats);
+
 /* ----- tracing ----------------------------------------------------------- */
 
 typedef struct {

@@ -26,6 +26,7 @@
 #include "cm.h"
 #include "cm_ctx.h"
 #include "cm_internal.h"
+#include "cm_batch_internal.h"
 #include "ntt_generic.cuh"
 
 namespace cm {
@@ -35,28 +36,7 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
 
 namespace {
 
-enum ItemType : uint16_t { kItSmall = 0, kItFwdA, kItFwdB, kItMiddle, kItInv, kItPack, kItCheck };
-constexpr int kPackWordsPerItem = 1 << 16;
 constexpr uint64_t kSpinLimit = 1ull << 22;  // polls of 64 ns-ish each before giving up
-
-struct BatchInst {
-    BitMap amap, bmap;
-    uint64_t *A, *B;
-    uint8_t *par;
-    uint64_t *z;
-    uint32_t *pre;  // Dodis et al.: {any 1 bit, any 0 bit} of x, else null
-    uint64_t lo, m, linv, nx;
-    int32_t lg, logr, tile_lg, kind;
-    uint32_t need[4];  // items per phase
-};
-
-struct WorkItem {
-    uint32_t inst;
-    uint16_t type;
-    uint16_t phase;
-    uint32_t idx;
-    uint32_t pad;
-};
 
 // ctrl layout (uint32): [0] next item, [1] abort, [2..] done[inst * 4 + phase]
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
@@ -84,6 +64,10 @@ __device__ void do_small(const BatchInst &I, const uint64_t *tw, uint64_t *sA, u
     any0 = __syncthreads_or(any0);
     const bool bad = I.kind == CM_DODIS && !(any1 && any0);
     if (bad && threadIdx.x == 0) atomicOr(status, kFlagPrecond);
+    if (I.pre && threadIdx.x == 0) {
+        I.pre[0] = any1 ? 1u : 0u;
+        I.pre[1] = any0 ? 1u : 0u;
+    }
     ntt_fwd_rt(sA, sB, 2, lg, 0, tw);
     for (int i = threadIdx.x; i < L; i += kThreads) sA[sp(i)] = gl_mul(gl_mul(sA[sp(i)], sB[sp(i)]), I.linv);
     __syncthreads();
@@ -258,52 +242,46 @@ k_batch(const BatchInst *__restrict__ insts, const WorkItem *__restrict__ items,
 }
 
 }  // namespace
-}  // namespace cm
-
-using namespace cm;
-
-struct cm_batch {
-    cm_ctx *ctx = nullptr;
-    std::vector<cm_desc> descs;
-    std::vector<Plan> plans;
-    std::vector<uint32_t> wl;       // instances on the work list
-    std::vector<uint32_t> solo;     // instances with L > 2^25 (per-call kernels)
-    std::vector<size_t> off_scratch;
-    void *scratch = nullptr;
-    size_t scratch_bytes = 0;
-    BatchInst *d_insts = nullptr;
-    WorkItem *d_items = nullptr;
-    uint32_t nitems = 0;
-    uint32_t *d_ctrl = nullptr;
-    size_t ctrl_words = 0;
-    int tile_lg = kTileLg;
-    int grid = 0;
-    uint64_t kernel_launches = 0;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-};
 
 static size_t round256(size_t v) { return (v + 255) & ~size_t(255); }
-
 static const size_t kBatchSmem = (8192 + 2 * (size_t)sp_size(1 << kMidLgMax)) * sizeof(uint64_t);
 
-// Build instance descriptors and the work list for the current tile size.
-static cm_status batch_build(cm_batch *b) {
-    const uint32_t n = (uint32_t)b->wl.size();
-    std::vector<BatchInst> insts(n);
+size_t worklist_scratch_bytes(const Plan &p) {
+    return p.npass == 1 ? round256(16 * p.L) + round256(p.m) : 0;
+}
+
+size_t batch_smem_bytes() { return kBatchSmem; }
+
+int batch_grid(int nsm) {
+    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess)
+        return 0;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kThreads, kBatchSmem) != cudaSuccess)
+        return 0;
+    return nsm * occ;
+}
+
+cudaError_t launch_k_batch(const BatchInst *insts, const WorkItem *items, uint32_t nitems, uint32_t *ctrl,
+                           uint32_t *status, const RootTables &rt, int grid, cudaStream_t st) {
+    k_batch<<<grid, kThreads, kBatchSmem, st>>>(insts, items, nitems, ctrl, status, rt);
+    return cudaGetLastError();
+}
+
+void build_worklist(const cm_desc *descs, const Plan *plans, const uint32_t *idx, uint32_t n,
+                    uint8_t *scratch, const size_t *off, int tile_lg, uint32_t *pre,
+                    std::vector<BatchInst> &insts, std::vector<WorkItem> &items) {
+    insts.assign(n, BatchInst());
     std::vector<WorkItem> phase[4];
     std::vector<WorkItem> smalls;
-    // larger instances first inside each phase
     std::vector<uint32_t> order(n);
     for (uint32_t i = 0; i < n; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) {
-        return b->plans[b->wl[a]].L > b->plans[b->wl[c]].L;
-    });
-    uint8_t *sc = static_cast<uint8_t *>(b->scratch);
-    for (uint32_t k = 0; k < n; ++k) {
-        const uint32_t di = b->wl[k];
-        const Plan &p = b->plans[di];
-        const cm_desc &d = b->descs[di];
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t a, uint32_t c) { return plans[idx[a]].L > plans[idx[c]].L; });
+    for (uint32_t oi = 0; oi < n; ++oi) {
+        const uint32_t k = order[oi];
+        const uint32_t di = idx[k];
+        const Plan &p = plans[di];
+        const cm_desc &d = descs[di];
         BatchInst &I = insts[k];
         memset(&I, 0, sizeof(I));
         I.amap.src = d.x; I.amap.mode = p.amode; I.amap.len = p.alen; I.amap.srclen = p.asrclen; I.amap.off = p.aoff;
@@ -315,17 +293,17 @@ static cm_status batch_build(cm_batch *b) {
         I.nx = p.n;
         I.lg = p.lg;
         I.kind = p.kind;
+        if (p.kind == CM_DODIS && pre) I.pre = pre + 2 * k;
         if (p.npass == 0) {
             smalls.push_back({k, kItSmall, 0, 0, 0});
             continue;
         }
         I.logr = p.pass_lg[0];
-        I.tile_lg = std::max(b->tile_lg, I.logr);  // at least one column per tile
-        uint8_t *base = sc + b->off_scratch[di];
+        I.tile_lg = std::max(tile_lg, I.logr);  // at least one column per tile
+        uint8_t *base = scratch + off[di];
         I.A = reinterpret_cast<uint64_t *>(base);
         I.B = I.A + p.L;
         I.par = reinterpret_cast<uint8_t *>(I.B + p.L);
-        if (p.kind == CM_DODIS) I.pre = reinterpret_cast<uint32_t *>(I.par + round256(p.m));
         const uint32_t tiles = (uint32_t)(p.L >> I.tile_lg);
         const uint32_t rows = (uint32_t)(p.L >> kMidLgMax);
         const uint32_t packs = (uint32_t)((((p.m + 63) >> 6) + kPackWordsPerItem - 1) / kPackWordsPerItem);
@@ -342,18 +320,49 @@ static cm_status batch_build(cm_batch *b) {
         for (uint32_t t = 0; t < tiles; ++t) phase[2].push_back({k, kItInv, 2, t, 0});
         for (uint32_t c = 0; c < packs; ++c) phase[3].push_back({k, kItPack, 3, c, 0});
     }
-    // phase 0 (large forward tiles, then whole small instances), then 1, 2, 3
-    std::vector<WorkItem> items;
+    items.clear();
     items.reserve(phase[0].size() + smalls.size() + phase[1].size() + phase[2].size() + phase[3].size());
-    std::vector<WorkItem> smalls_sorted(smalls);
-    std::stable_sort(smalls_sorted.begin(), smalls_sorted.end(), [&](const WorkItem &a, const WorkItem &c) {
-        return insts[a.inst].lg > insts[c.inst].lg;
-    });
+    std::stable_sort(smalls.begin(), smalls.end(),
+                     [&](const WorkItem &a, const WorkItem &c) { return insts[a.inst].lg > insts[c.inst].lg; });
     for (auto &w : phase[0]) items.push_back(w);
-    for (auto &w : smalls_sorted) items.push_back(w);
+    for (auto &w : smalls) items.push_back(w);
     for (int ph = 1; ph < 4; ++ph)
         for (auto &w : phase[ph]) items.push_back(w);
+}
 
+}  // namespace cm
+
+using namespace cm;
+
+struct cm_batch {
+    cm_ctx *ctx = nullptr;
+    std::vector<cm_desc> descs;
+    std::vector<Plan> plans;
+    std::vector<uint32_t> wl;       // instances on the work list
+    std::vector<uint32_t> solo;     // instances with L > 2^25 (per-call kernels)
+    std::vector<size_t> off_scratch;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    uint32_t *d_pre = nullptr;      // Dodis et al. precondition flags, 2 per instance
+    BatchInst *d_insts = nullptr;
+    WorkItem *d_items = nullptr;
+    uint32_t nitems = 0;
+    uint32_t *d_ctrl = nullptr;
+    size_t ctrl_words = 0;
+    int tile_lg = kTileLg;
+    int grid = 0;
+    uint64_t kernel_launches = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+// Build instance descriptors and the work list for the current tile size.
+static cm_status batch_build(cm_batch *b) {
+    const uint32_t n = (uint32_t)b->wl.size();
+    std::vector<BatchInst> insts;
+    std::vector<WorkItem> items;
+    build_worklist(b->descs.data(), b->plans.data(), b->wl.data(), n, static_cast<uint8_t *>(b->scratch),
+                   b->off_scratch.data(), b->tile_lg, b->d_pre, insts, items);
     if (b->d_insts) cudaFree(b->d_insts);
     if (b->d_items) cudaFree(b->d_items);
     b->d_insts = nullptr;
@@ -440,7 +449,7 @@ extern "C" cm_status cm_batch_create(cm_ctx *ctx, const cm_desc *descs, uint32_t
         b->off_scratch[i] = total;
         if (p.npass == 1) {
             b->wl.push_back(i);
-            total += round256(16 * p.L) + round256(p.m) + (p.kind == CM_DODIS ? 256 : 0);
+            total += worklist_scratch_bytes(p);
         } else if (p.npass == 0) {
             b->wl.push_back(i);
         } else {
@@ -452,23 +461,20 @@ extern "C" cm_status cm_batch_create(cm_ctx *ctx, const cm_desc *descs, uint32_t
         delete b;
         return CM_ENOMEM;
     }
+    const size_t pre_off = total;  // precondition flags, 2 words per work-list instance
+    total += round256(8 * b->wl.size() + 8);
     b->scratch_bytes = total;
     if (total && cudaMalloc(&b->scratch, total) != cudaSuccess) {
         cudaGetLastError();
         delete b;
         return CM_ENOMEM;
     }
-    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess) {
+    b->d_pre = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(b->scratch) + pre_off);
+    b->grid = batch_grid(ctx->nsm);  // every CTA resident
+    if (b->grid < 1) {
         batch_free(b);
         return CM_EDEVICE;
     }
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kThreads, kBatchSmem) != cudaSuccess ||
-        occ < 1) {
-        batch_free(b);
-        return CM_EDEVICE;
-    }
-    b->grid = ctx->nsm * occ;  // every CTA resident: waits never block a needed item
     cm_status s = batch_build(b);
     if (s != CM_OK) {
         batch_free(b);

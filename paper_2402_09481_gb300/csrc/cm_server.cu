@@ -1,0 +1,442 @@
+// Continuous-batching request server (cm_submit / cm_poll).
+//
+// Clients submit single extractions of any kind and size; a worker thread
+// keeps a FIFO of pending requests and a few "slots" (CUDA streams).  Whenever
+// a slot is free it admits the longest prefix of the queue whose scratch fits
+// in the HBM budget still unclaimed by requests on the device, and launches
+// that wave as one work-list kernel on the slot's stream (instances needing
+// two column passes follow on the same stream through the single-call
+// kernels).  Waves on different slots run concurrently, so requests that
+// arrive while others are on the GPU start as soon as a slot and memory free
+// up.  Scratch comes from the context's stream-ordered pool and returns to it
+// at the end of the wave.  Each request's result (its own status, including
+// the Dodis et al. precondition, and submit / admit / completion times) is
+// collected with cm_poll.  The root tables stay resident in the context.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "cm.h"
+#include "cm_batch_internal.h"
+#include "cm_ctx.h"
+#include "cm_internal.h"
+
+namespace cm {
+cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const uint64_t *y,
+                          uint64_t *z, void *scratch, cudaStream_t st);
+}
+
+using namespace cm;
+
+namespace {
+
+uint64_t now_ns() {
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+size_t r256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Req {
+    cm_desc d;
+    Plan p;
+    size_t foot = 0;  // scratch bytes while on the device
+    uint64_t t_submit = 0, t_admit = 0, t_done = 0, wave = 0;
+    int status = CM_OK;
+    bool done = false;
+};
+
+// Grow-only device / pinned host buffer.
+struct Buf {
+    void *dev = nullptr, *host = nullptr;
+    size_t cap = 0;
+    bool ensure(size_t bytes) {
+        if (bytes <= cap) return true;
+        size_t c = cap ? cap : 4096;
+        while (c < bytes) c *= 2;
+        if (dev) cudaFree(dev);
+        if (host) cudaFreeHost(host);
+        dev = host = nullptr;
+        cap = 0;
+        if (cudaMalloc(&dev, c) != cudaSuccess || cudaMallocHost(&host, c) != cudaSuccess) return false;
+        cap = c;
+        return true;
+    }
+    void release() {
+        if (dev) cudaFree(dev);
+        if (host) cudaFreeHost(host);
+        dev = host = nullptr;
+        cap = 0;
+    }
+};
+
+struct Slot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool busy = false;
+    std::vector<uint64_t> tickets;
+    std::vector<int> pre_index;  // per ticket: flag pair index, or -1
+    size_t foot = 0;
+    uint64_t wave = 0;
+    Buf insts, items, ctrl, flags;  // flags: [0] status word, then 2 words per request
+};
+
+}  // namespace
+
+struct cm_server {
+    cm_ctx *ctx = nullptr;
+    cm_server_options opt{};
+    size_t budget = 0;
+    int grid = 0;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<uint64_t> pending;
+    std::unordered_map<uint64_t, Req> reqs;
+    uint64_t next_ticket = 1, waves = 0;
+    std::vector<Slot> slots;
+    size_t inflight = 0, max_inflight = 0;
+    uint64_t submitted = 0, completed = 0, rejected = 0;
+    bool stop = false;
+};
+
+namespace {
+
+// Finish a completed wave: per-request status from the copied-back flags.
+void finish_slot(cm_server *S, Slot &sl) {
+    const uint32_t *f = static_cast<const uint32_t *>(sl.flags.host);
+    const uint32_t st_word = f[0];
+    const uint64_t t = now_ns();
+    for (size_t i = 0; i < sl.tickets.size(); ++i) {
+        auto it = S->reqs.find(sl.tickets[i]);
+        if (it == S->reqs.end()) continue;
+        Req &r = it->second;
+        int status = CM_OK;
+        if (st_word & CM_FLAG_TIMEOUT) status = CM_ETIMEDOUT;
+        const int pi = sl.pre_index[i];
+        if (pi >= 0 && (f[2 + 2 * pi] == 0u || f[3 + 2 * pi] == 0u)) status = CM_EPRECOND;
+        r.status = status;
+        r.t_done = t;
+        r.done = true;
+        ++S->completed;
+    }
+    S->inflight -= sl.foot;
+    sl.foot = 0;
+    sl.tickets.clear();
+    sl.pre_index.clear();
+    sl.busy = false;
+}
+
+// Launch the requests `tk` (already admitted) as one wave on slot sl.
+cm_status launch_wave(cm_server *S, Slot &sl, const std::vector<uint64_t> &tk) {
+    cm_ctx *ctx = S->ctx;
+    const uint32_t n = (uint32_t)tk.size();
+    std::vector<cm_desc> descs(n);
+    std::vector<Plan> plans(n);
+    std::vector<size_t> off(n, 0);
+    std::vector<uint32_t> wl, solo;
+    size_t total = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const Req &r = S->reqs[tk[i]];
+        descs[i] = r.d;
+        plans[i] = r.p;
+        off[i] = total;
+        if (r.p.npass <= 1) {
+            wl.push_back(i);
+            total += worklist_scratch_bytes(r.p);
+        } else {
+            solo.push_back(i);
+            total += r256(r.p.scratch_bytes);
+        }
+    }
+    void *scratch = nullptr;
+    if (total && cudaMallocFromPoolAsync(&scratch, total, ctx->pool, sl.st) != cudaSuccess) {
+        cudaGetLastError();
+        return CM_ENOMEM;
+    }
+    // flags: status word, pad, then a pair per work-list instance (index k) and
+    // one per single-call request (index wl.size() + i)
+    const size_t flag_words = 2 + 2 * ((size_t)n + n);
+    if (!sl.flags.ensure(flag_words * 4)) return CM_ENOMEM;
+    uint32_t *dflags = static_cast<uint32_t *>(sl.flags.dev);
+    std::vector<BatchInst> insts;
+    std::vector<WorkItem> items;
+    build_worklist(descs.data(), plans.data(), wl.data(), (uint32_t)wl.size(), static_cast<uint8_t *>(scratch),
+                   off.data(), kTileLg, dflags + 2, insts, items);
+    sl.pre_index.assign(n, -1);
+    for (uint32_t k = 0; k < wl.size(); ++k)
+        if (plans[wl[k]].kind == CM_DODIS) sl.pre_index[wl[k]] = (int)k;
+    cudaError_t e = cudaSuccess;
+    if (cudaMemsetAsync(dflags, 0xff, flag_words * 4, sl.st) != cudaSuccess) return CM_EDEVICE;  // pairs "ok"
+    if (cudaMemsetAsync(dflags, 0, 4, sl.st) != cudaSuccess) return CM_EDEVICE;                 // status word
+    if (!wl.empty() && !items.empty()) {
+        const size_t ib = insts.size() * sizeof(BatchInst), wb = items.size() * sizeof(WorkItem);
+        const size_t cb = (2 + 4 * insts.size()) * sizeof(uint32_t);
+        if (!sl.insts.ensure(ib) || !sl.items.ensure(wb) || !sl.ctrl.ensure(cb)) return CM_ENOMEM;
+        memcpy(sl.insts.host, insts.data(), ib);
+        memcpy(sl.items.host, items.data(), wb);
+        if (cudaMemcpyAsync(sl.insts.dev, sl.insts.host, ib, cudaMemcpyHostToDevice, sl.st) != cudaSuccess ||
+            cudaMemcpyAsync(sl.items.dev, sl.items.host, wb, cudaMemcpyHostToDevice, sl.st) != cudaSuccess ||
+            cudaMemsetAsync(sl.ctrl.dev, 0, cb, sl.st) != cudaSuccess)
+            return CM_EDEVICE;
+        ProfScope ps(ctx, "k_batch", sl.st);
+        e = launch_k_batch(static_cast<BatchInst *>(sl.insts.dev), static_cast<WorkItem *>(sl.items.dev),
+                           (uint32_t)items.size(), static_cast<uint32_t *>(sl.ctrl.dev), dflags, ctx->rt, S->grid,
+                           sl.st);
+        if (e != cudaSuccess) return CM_EDEVICE;
+    }
+    for (uint32_t i : solo) {
+        cm_status s = enqueue_extract(ctx, plans[i], descs[i].x, descs[i].y, descs[i].z,
+                                      static_cast<uint8_t *>(scratch) + off[i], sl.st);
+        if (s != CM_OK) return s;
+        if (plans[i].kind == CM_DODIS) {
+            // the single-call path keeps its flag pair in the last 256 bytes of its scratch
+            const uint8_t *pf = static_cast<uint8_t *>(scratch) + off[i] + plans[i].scratch_bytes - 256;
+            sl.pre_index[i] = (int)(wl.size() + i);
+            if (cudaMemcpyAsync(dflags + 2 + 2 * (wl.size() + i), pf, 8, cudaMemcpyDeviceToDevice, sl.st) !=
+                cudaSuccess)
+                return CM_EDEVICE;
+        }
+    }
+    if (cudaMemcpyAsync(sl.flags.host, dflags, flag_words * 4, cudaMemcpyDeviceToHost, sl.st) != cudaSuccess)
+        return CM_EDEVICE;
+    if (scratch) cudaFreeAsync(scratch, sl.st);
+    if (cudaEventRecord(sl.ev, sl.st) != cudaSuccess) return CM_EDEVICE;
+    return CM_OK;
+}
+
+void worker_main(cm_server *S) {
+    cudaSetDevice(S->ctx->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        bool progress = false;
+        bool any_busy = false;
+        for (Slot &sl : S->slots) {
+            if (!sl.busy) continue;
+            const cudaError_t q = cudaEventQuery(sl.ev);
+            if (q == cudaSuccess) {
+                finish_slot(S, sl);
+                progress = true;
+            } else if (q != cudaErrorNotReady) {
+                // device error: fail the wave's requests
+                for (uint64_t t : sl.tickets) {
+                    Req &r = S->reqs[t];
+                    r.status = CM_EDEVICE;
+                    r.done = true;
+                    r.t_done = now_ns();
+                    ++S->completed;
+                }
+                S->inflight -= sl.foot;
+                sl.foot = 0;
+                sl.tickets.clear();
+                sl.busy = false;
+                progress = true;
+            } else {
+                any_busy = true;
+            }
+        }
+        if (progress) S->cv_done.notify_all();
+        if (S->stop && S->pending.empty() && !any_busy) break;
+        for (Slot &sl : S->slots) {
+            if (sl.busy || S->pending.empty()) continue;
+            std::vector<uint64_t> wave;
+            size_t foot = 0;
+            while (!S->pending.empty() && wave.size() < S->opt.max_wave) {
+                Req &r = S->reqs[S->pending.front()];
+                if (S->inflight + foot + r.foot > S->budget) break;  // admitted when memory frees up
+                foot += r.foot;
+                wave.push_back(S->pending.front());
+                S->pending.pop_front();
+            }
+            if (wave.empty()) break;
+            const uint64_t t = now_ns(), w = ++S->waves;
+            for (uint64_t tk : wave) {
+                S->reqs[tk].t_admit = t;
+                S->reqs[tk].wave = w;
+            }
+            sl.tickets = wave;
+            sl.foot = foot;
+            sl.wave = w;
+            sl.busy = true;
+            S->inflight += foot;
+            if (S->inflight > S->max_inflight) S->max_inflight = S->inflight;
+            const cm_status s = launch_wave(S, sl, wave);
+            if (s != CM_OK) {
+                cudaStreamSynchronize(sl.st);
+                for (uint64_t tk : wave) {
+                    Req &r = S->reqs[tk];
+                    r.status = s;
+                    r.done = true;
+                    r.t_done = now_ns();
+                    ++S->completed;
+                }
+                S->inflight -= foot;
+                sl.tickets.clear();
+                sl.foot = 0;
+                sl.busy = false;
+                S->cv_done.notify_all();
+            }
+            progress = true;
+        }
+        if (!progress) S->cv_work.wait_for(lk, std::chrono::microseconds(50));
+    }
+}
+
+void server_release(cm_server *S) {
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    for (Slot &sl : S->slots) {
+        if (sl.st) cudaStreamSynchronize(sl.st);
+        sl.insts.release();
+        sl.items.release();
+        sl.ctrl.release();
+        sl.flags.release();
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.st) cudaStreamDestroy(sl.st);
+    }
+    delete S;
+}
+
+}  // namespace
+
+void cm_ctx_release_extras(cm_ctx *c) {
+    if (c->server) {
+        server_release(c->server);
+        c->server = nullptr;
+    }
+}
+
+extern "C" cm_status cm_server_start(cm_ctx *ctx, const cm_server_options *opt) {
+    if (!ctx) return CM_EINVAL;
+    if (ctx->server) return CM_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return CM_EDEVICE;
+    cm_server *S = new cm_server();
+    S->ctx = ctx;
+    if (opt) S->opt = *opt;
+    if (!S->opt.slots) S->opt.slots = 2;
+    if (!S->opt.max_queue) S->opt.max_queue = 1u << 20;
+    if (!S->opt.max_wave) S->opt.max_wave = 512;
+    S->budget = S->opt.hbm_budget_bytes ? S->opt.hbm_budget_bytes : ctx->budget / 2;
+    if (S->budget > ctx->budget) S->budget = ctx->budget;
+    S->grid = batch_grid(ctx->nsm);
+    if (S->grid < 1) {
+        delete S;
+        return CM_EDEVICE;
+    }
+    S->slots.resize(S->opt.slots);
+    for (Slot &sl : S->slots) {
+        if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
+            server_release(S);
+            return CM_EDEVICE;
+        }
+    }
+    ctx->server = S;
+    S->worker = std::thread(worker_main, S);
+    return CM_OK;
+}
+
+extern "C" cm_status cm_server_stop(cm_ctx *ctx) {
+    if (!ctx || !ctx->server) return CM_EINVAL;
+    server_release(ctx->server);
+    ctx->server = nullptr;
+    return CM_OK;
+}
+
+extern "C" cm_status cm_submit(cm_ctx *ctx, const cm_request *rq, uint64_t *ticket) {
+    if (!ctx || !rq || !ticket) return CM_EINVAL;
+    cm_server *S = ctx->server;
+    if (!S) return CM_EINVAL;
+    Req r;
+    r.d.kind = rq->kind;
+    r.d.reserved = 0;
+    r.d.n = rq->n;
+    r.d.m = rq->m;
+    r.d.x = rq->x;
+    r.d.y = rq->y;
+    r.d.z = rq->z;
+    if (!rq->x || !rq->y || !rq->z || !make_plan(rq->kind, rq->n, rq->m, &r.p)) return CM_EINVAL;
+    r.foot = r.p.npass <= 1 ? worklist_scratch_bytes(r.p) : r256(r.p.scratch_bytes);
+    r.foot += 256;  // work-list and flag share
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        if (r.foot > S->budget) {
+            ++S->rejected;
+            return CM_ENOMEM;
+        }
+        if (S->pending.size() >= S->opt.max_queue || S->stop) {
+            ++S->rejected;
+            return CM_EAGAIN;
+        }
+        const uint64_t t = S->next_ticket++;
+        r.t_submit = now_ns();
+        S->reqs.emplace(t, r);
+        S->pending.push_back(t);
+        ++S->submitted;
+        *ticket = t;
+    }
+    S->cv_work.notify_one();
+    return CM_OK;
+}
+
+extern "C" cm_status cm_poll(cm_ctx *ctx, uint64_t ticket, cm_result *res, uint64_t timeout_ns) {
+    if (!ctx || !ctx->server) return CM_EINVAL;
+    cm_server *S = ctx->server;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return CM_ENOTFOUND;
+    if (!it->second.done) {
+        S->cv_done.wait_for(lk, std::chrono::nanoseconds(timeout_ns), [&] {
+            auto j = S->reqs.find(ticket);
+            return j == S->reqs.end() || j->second.done;
+        });
+        it = S->reqs.find(ticket);
+        if (it == S->reqs.end()) return CM_ENOTFOUND;
+        if (!it->second.done) return CM_EAGAIN;
+    }
+    const Req &r = it->second;
+    if (res) {
+        memset(res, 0, sizeof(*res));
+        res->status = r.status;
+        res->t_submit_ns = r.t_submit;
+        res->t_admit_ns = r.t_admit;
+        res->t_done_ns = r.t_done;
+        res->wave = r.wave;
+    }
+    S->reqs.erase(it);
+    return CM_OK;
+}
+
+extern "C" cm_status cm_server_get_stats(cm_ctx *ctx, cm_server_stats *st) {
+    if (!ctx || !ctx->server || !st) return CM_EINVAL;
+    cm_server *S = ctx->server;
+    std::lock_guard<std::mutex> g(S->mu);
+    memset(st, 0, sizeof(*st));
+    st->submitted = S->submitted;
+    st->completed = S->completed;
+    st->rejected = S->rejected;
+    st->waves = S->waves;
+    st->inflight_bytes = S->inflight;
+    st->max_inflight_bytes = S->max_inflight;
+    st->budget_bytes = S->budget;
+    st->queued = (uint32_t)S->pending.size();
+    uint32_t busy = 0;
+    for (const Slot &sl : S->slots) busy += sl.busy ? 1u : 0u;
+    st->busy_slots = busy;
+    st->slots = (uint32_t)S->slots.size();
+    return CM_OK;
+}

@@ -42,6 +42,11 @@ PROTOTYPES = {
     "cm_field_selftest": (_I, [_I, _U64, _U64, ctypes.POINTER(_U64)]),
     "cm_batch_toeplitz_shared_seed": (_I, [_P, _P, _U64, _U64, _P, _U64, _P, _I, _P]),
     "cm_shared_seed_engine": (_I, [_U64, _U64]),
+    "cm_server_start": (_I, [_P, _P]),
+    "cm_server_stop": (_I, [_P]),
+    "cm_submit": (_I, [_P, _P, ctypes.POINTER(_U64)]),
+    "cm_poll": (_I, [_P, _U64, _P, _U64]),
+    "cm_server_get_stats": (_I, [_P, _P]),
     "cm_batch_create": (_I, [_P, _P, _U32, _U32, ctypes.POINTER(_P)]),
     "cm_batch_launch": (_I, [_P, _P]),
     "cm_batch_destroy": (None, [_P]),
@@ -76,6 +81,31 @@ class BatchStats(ctypes.Structure):
                 ("grid", ctypes.c_uint32), ("graph", ctypes.c_uint32),
                 ("scratch_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
                 ("output_bits", ctypes.c_uint64), ("transform_elements", ctypes.c_uint64)]
+
+
+class CmRequest(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("flags", ctypes.c_uint32), ("n", ctypes.c_uint64),
+                ("m", ctypes.c_uint64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("z", ctypes.c_void_p), ("user", ctypes.c_uint64)]
+
+
+class CmResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_uint32), ("t_submit_ns", ctypes.c_uint64),
+                ("t_admit_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64), ("wave", ctypes.c_uint64)]
+
+
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32),
+                ("max_queue", ctypes.c_uint32), ("max_wave", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 5)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("waves", ctypes.c_uint64), ("inflight_bytes", ctypes.c_uint64),
+                ("max_inflight_bytes", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64),
+                ("queued", ctypes.c_uint32), ("busy_slots", ctypes.c_uint32), ("slots", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 BATCH_AUTOTUNE, BATCH_NO_GRAPH = 0x1, 0x2
@@ -301,6 +331,41 @@ class Context:
         _check(self._L.cm_batch_toeplitz_shared_seed(self._h, py, n, m, pX, count, Z.data_ptr(), engine,
                                                      _stream_handle(stream)), "cm_batch_toeplitz_shared_seed")
         return Z
+
+    # ----- serving -------------------------------------------------------------
+    def server_start(self, hbm_budget_bytes: int = 0, slots: int = 0, max_queue: int = 0, max_wave: int = 0):
+        o = ServerOptions(hbm_budget_bytes, slots, max_queue, max_wave)
+        _check(self._L.cm_server_start(self._h, ctypes.byref(o)), "cm_server_start")
+
+    def server_stop(self):
+        _check(self._L.cm_server_stop(self._h), "cm_server_stop")
+
+    def submit_raw(self, kind: int, n: int, m: int, px: int, py: int, pz: int) -> tuple[int, int]:
+        """(status, ticket) for device pointers; no exception on CM_EAGAIN / CM_ENOMEM."""
+        r = CmRequest(kind, 0, n, m, px, py, pz, 0)
+        t = ctypes.c_uint64(0)
+        s = self._L.cm_submit(self._h, ctypes.byref(r), ctypes.byref(t))
+        return int(s), int(t.value)
+
+    def submit(self, kind: int, n: int, m: int, x, y, z) -> int:
+        ybits = n + m - 1 if kind == TOEPLITZ else (n + 1 if kind == CIRCULANT else n)
+        s, t = self.submit_raw(kind, n, m, _dev_words(x, n, "x"), _dev_words(y, ybits, "y"),
+                               _dev_words(z, m, "z"))
+        _check(s, "cm_submit")
+        return t
+
+    def poll(self, ticket: int, timeout_s: float = 0.0):
+        """(cm_status of the poll, result dict or None)."""
+        r = CmResult()
+        s = self._L.cm_poll(self._h, ticket, ctypes.byref(r), int(timeout_s * 1e9))
+        if s != CM_OK:
+            return int(s), None
+        return CM_OK, {k: getattr(r, k) for k, _ in CmResult._fields_}
+
+    def server_stats(self) -> dict:
+        st = ServerStats()
+        _check(self._L.cm_server_get_stats(self._h, ctypes.byref(st)), "cm_server_get_stats")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_ if k != "reserved"}
 
     def device_status(self, stream=None) -> tuple[int, int]:
         f = ctypes.c_uint32(0)
