@@ -609,13 +609,144 @@ def run_batched_b(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def served_trace(count, rate, seed_stream=3):
+    """Poisson arrivals at `rate`/s; kinds Toeplitz / Circulant / Dodis et al.
+    50/25/25; n = floor(2^U), U ~ U[12, 28), snapped to the next valid N_A
+    length for Circulant (n + 1 prime) and Dodis et al. (n prime), the previous
+    one above 2^28; m = floor(n / 2)."""
+    import numpy as np
+
+    from paper_2402_09481_gb300 import inputs, native
+    arr = inputs.poisson_arrivals(seed_stream, count, rate)
+    u = inputs.uniform01(seed_stream + 1, count)
+    ns = inputs.loguniform_lengths(seed_stream + 2, count, 12, 28)
+    out = []
+    for j in range(count):
+        kind = 0 if u[j] < 0.5 else (1 if u[j] < 0.75 else 2)
+        n = int(ns[j])
+        if kind == 1:
+            P = native.next_na_prime(n + 1)
+            if P > (1 << 28):
+                P = native.prev_na_prime(n + 1)
+            n = P - 1
+        elif kind == 2:
+            P = native.next_na_prime(n)
+            if P > (1 << 28):
+                P = native.prev_na_prime(n)
+            n = P
+        out.append((float(arr[j]), kind, n, max(1, n // 2)))
+    return out
+
+
+def run_served(args, world, rank, local):
+    """Requests of the served workload submitted at their arrival times to the
+    library's continuous-batching server; end-to-end latency (arrival to
+    completion), service time (admission to completion) and output Gbit/s at
+    the 20k req/s rate and at fractions of the measured capacity."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_2402_09481_gb300 import build, native
+
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    build.build()
+    ctx = native.Context(local)
+    ctx.server_start(slots=int(os.environ.get("CM_SERVE_SLOTS", "2")))
+    pool_bits = (1 << 29) + (1 << 24)
+    xpool = torch.randint(-(1 << 62), 1 << 62, ((pool_bits + 63) // 64,), dtype=torch.int64, device="cuda")
+    ypool = torch.randint(-(1 << 62), 1 << 62, ((pool_bits + 63) // 64,), dtype=torch.int64, device="cuda")
+
+    def run(trace):
+        zwords = [native.words(m) for _, _, _, m in trace]
+        zbuf = torch.empty(sum(zwords), dtype=torch.int64, device="cuda")
+        zoff = np.concatenate([[0], np.cumsum(zwords)])
+        rng = np.random.default_rng(len(trace))
+        tickets, arrive = [None] * len(trace), [0] * len(trace)
+        t0 = time.monotonic_ns() + 20_000_000
+
+        def client():
+            for j, (ta, kind, n, m) in enumerate(trace):
+                due = t0 + int(ta * 1e9)
+                while True:
+                    d = due - time.monotonic_ns()
+                    if d <= 0:
+                        break
+                    time.sleep(min(d, 2_000_000) / 1e9)
+                ox, oy = int(rng.integers(0, 1 << 18)), int(rng.integers(0, 1 << 18))
+                arrive[j] = max(due, time.monotonic_ns())
+                s, t = ctx.submit_raw(kind, n, m, xpool.data_ptr() + 8 * ox, ypool.data_ptr() + 8 * oy,
+                                      zbuf.data_ptr() + 8 * int(zoff[j]))
+                if s != native.CM_OK:
+                    raise native.CMError(s, "cm_submit")
+                tickets[j] = t
+
+        th = threading.Thread(target=client)
+        th.start()
+        th.join()
+        res = []
+        for t in tickets:
+            s, r = ctx.poll(t, 600.0)
+            if s != native.CM_OK or r["status"] != native.CM_OK:
+                raise RuntimeError(f"request failed: {native.STATUS.get(s)} {r}")
+            res.append(r)
+        lat = np.array([(r["t_done_ns"] - a) / 1e6 for r, a in zip(res, arrive)])
+        svc = np.array([(r["t_done_ns"] - r["t_admit_ns"]) / 1e6 for r in res])
+        span = (max(r["t_done_ns"] for r in res) - min(arrive)) / 1e9
+        bits = sum(m for _, _, _, m in trace)
+        return {"requests": len(trace), "output_gbits": bits / 1e9, "span_s": span,
+                "gbit_per_s": bits / span / 1e9, "req_per_s": len(trace) / span,
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                "service_ms": {"p50": float(np.percentile(svc, 50)), "p99": float(np.percentile(svc, 99))},
+                "waves": ctx.server_stats()["waves"]}
+
+    rate = float(os.environ.get("CM_SERVE_RATE", "20000"))
+    count = int(os.environ.get("CM_SERVE_COUNT", "600"))
+    run(served_trace(max(8, args.warmup * 4), rate, seed_stream=90))   # warm-up
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.25)
+    tw0 = time.time()
+    main_run = run(served_trace(count, rate))
+    tw1 = time.time()
+    time.sleep(0.25)
+    sampler.stop()
+    cap = main_run["req_per_s"]
+    points = []
+    for frac in (0.25, 0.5, 0.8):
+        k = int(os.environ.get("CM_SERVE_SUB_COUNT", "120"))
+        pt = run(served_trace(k, frac * cap, seed_stream=30 + int(frac * 100)))
+        pt["offered_fraction_of_capacity"] = frac
+        points.append(pt)
+    st = ctx.server_stats()
+    line = {
+        "metric": "extracted output Gbit/s", "value": main_run["gbit_per_s"], "unit": "Gbit/s", "n_gpus": 1,
+        "steps": 1, "warmup": args.warmup, "ms_per_step": main_run["span_s"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": f"Served: {count} requests, Poisson arrivals at {rate:g} req/s, Toeplitz/Circulant/"
+                               "Dodis 50/25/25, n = floor(2^U), U ~ U[12, 28) (N_A-snapped), m = n/2, "
+                               "Bernoulli(1/2) inputs", "slots": st["slots"],
+                   "hbm_budget_bytes": st["budget_bytes"]},
+        "served": main_run, "sub_saturation": points,
+        "latency_ms": main_run["latency_ms"], "max_inflight_bytes": st["max_inflight_bytes"],
+        "clocks": sampler.summary(tw0, tw1),
+    }
+    print(json.dumps(line), flush=True)
+    ctx.server_stop()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="cm", choices=["cm", "reference"])
-    ap.add_argument("--workload", default="circulant", choices=sorted(WORKLOADS) + ["batched_a", "batched_b"])
+    ap.add_argument("--workload", default="circulant", choices=sorted(WORKLOADS) + ["batched_a", "batched_b", "served"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -628,6 +759,9 @@ def main():
         return
     if args.workload == "batched_b":
         run_batched_b(args, world, rank, local)
+        return
+    if args.workload == "served":
+        run_served(args, world, rank, local)
         return
 
     import numpy as np
