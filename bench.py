@@ -767,7 +767,7 @@ def main():
     import numpy as np
     import torch
 
-    from paper_2402_09481_gb300 import build, inputs, native
+    from paper_2402_09481_gb300 import build, inputs, native, replicas
 
     torch.cuda.set_device(local)
     dist = None
@@ -826,13 +826,10 @@ def main():
     time.sleep(0.25)
     sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    # replicas: every rank extracts its own instance; the slowest rank bounds the job
+    units_per_s, total_ms = replicas.job_throughput(m * args.steps, sum(step_ms), device="cuda")
     ms_per_step = total_ms / args.steps
-    value = world * m / (ms_per_step * 1e-3) / 1e9
+    value = units_per_s / 1e9
     s, flags = ctx.device_status()
     if s != native.CM_OK:
         raise RuntimeError(f"device status {native.STATUS.get(s)} flags {flags}")

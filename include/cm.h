@@ -260,14 +260,18 @@ int cm_shared_seed_engine(uint64_t n, uint64_t m);
 
 /* One extraction request: same argument rules as the single calls; device
  * pointers that must stay valid until the request is polled complete. */
+#define CM_REQ_SEED_CACHE 0x1u /* y is immutable under seed_id: keep its transform resident */
+
 typedef struct {
-    int32_t kind;    /* cm_kind */
-    uint32_t flags;  /* 0 */
+    int32_t kind;     /* cm_kind */
+    uint32_t flags;   /* CM_REQ_* */
     uint64_t n, m;
     const uint64_t *x;
     const uint64_t *y;
     uint64_t *z;
-    uint64_t user;   /* free for the caller */
+    uint64_t seed_id; /* with CM_REQ_SEED_CACHE: names the seed y (the caller promises that
+                         every request with this id has the same y contents) */
+    uint64_t user;    /* free for the caller */
 } cm_request;
 
 typedef struct {
@@ -282,12 +286,15 @@ typedef struct {
     uint32_t slots;            /* concurrent waves (CUDA streams); 0 = 2 */
     uint32_t max_queue;        /* pending requests before cm_submit says CM_EAGAIN; 0 = 2^20 */
     uint32_t max_wave;         /* requests per wave; 0 = 512 */
-    uint32_t reserved[5];
+    uint32_t reserved0;
+    uint64_t seed_cache_bytes; /* resident seed transforms (within the budget); 0 = a quarter of it */
+    uint32_t reserved[2];
 } cm_server_options;
 
 typedef struct {
     uint64_t submitted, completed, rejected, waves;
     uint64_t inflight_bytes, max_inflight_bytes, budget_bytes;
+    uint64_t seed_cache_hits, seed_cache_misses, seed_cache_bytes, seed_cache_entries;
     uint32_t queued, busy_slots, slots, reserved;
 } cm_server_stats;
 
@@ -296,8 +303,13 @@ typedef struct {
  * that admits pending requests in arrival order into waves whenever a slot is
  * free, as long as their scratch fits in what the HBM budget leaves, and
  * launches each wave as one work-list kernel (the cm_batch_create machinery)
- * on the slot's stream; waves on different slots overlap on the device.  The
- * paper has no serving layer; each request computes exactly its single call.
+ * on the slot's stream; waves on different slots overlap on the device.
+ * Requests flagged CM_REQ_SEED_CACHE (transform length 2^14 .. 2^25) keep the
+ * forward transform of their seed operand resident, keyed by (seed_id, kind,
+ * n, m); a later request with the same key skips that transform (reuse of the
+ * seed is what the paper's strong extractors allow).  Least recently used
+ * entries are dropped past seed_cache_bytes.  The paper has no serving layer;
+ * each request computes exactly its single call.
  */
 cm_status cm_server_start(cm_ctx *ctx, const cm_server_options *opt);
 

@@ -269,7 +269,8 @@ cudaError_t launch_k_batch(const BatchInst *insts, const WorkItem *items, uint32
 
 void build_worklist(const cm_desc *descs, const Plan *plans, const uint32_t *idx, uint32_t n,
                     uint8_t *scratch, const size_t *off, int tile_lg, uint32_t *pre,
-                    std::vector<BatchInst> &insts, std::vector<WorkItem> &items) {
+                    std::vector<BatchInst> &insts, std::vector<WorkItem> &items, uint64_t *const *bext,
+                    const uint8_t *bready) {
     insts.assign(n, BatchInst());
     std::vector<WorkItem> phase[4];
     std::vector<WorkItem> smalls;
@@ -304,17 +305,19 @@ void build_worklist(const cm_desc *descs, const Plan *plans, const uint32_t *idx
         I.A = reinterpret_cast<uint64_t *>(base);
         I.B = I.A + p.L;
         I.par = reinterpret_cast<uint8_t *>(I.B + p.L);
+        const bool have_b = bext && bext[k] && bready && bready[k];
+        if (bext && bext[k]) I.B = bext[k];
         const uint32_t tiles = (uint32_t)(p.L >> I.tile_lg);
         const uint32_t rows = (uint32_t)(p.L >> kMidLgMax);
         const uint32_t packs = (uint32_t)((((p.m + 63) >> 6) + kPackWordsPerItem - 1) / kPackWordsPerItem);
-        I.need[0] = 2 * tiles + (I.pre ? 1 : 0);
+        I.need[0] = (have_b ? 1 : 2) * tiles + (I.pre ? 1 : 0);
         I.need[1] = rows;
         I.need[2] = tiles;
         I.need[3] = packs;
         if (I.pre) phase[0].push_back({k, kItCheck, 0, 0, 0});
         for (uint32_t t = 0; t < tiles; ++t) {
             phase[0].push_back({k, kItFwdA, 0, t, 0});
-            phase[0].push_back({k, kItFwdB, 0, t, 0});
+            if (!have_b) phase[0].push_back({k, kItFwdB, 0, t, 0});
         }
         for (uint32_t r = 0; r < rows; ++r) phase[1].push_back({k, kItMiddle, 1, r, 0});
         for (uint32_t t = 0; t < tiles; ++t) phase[2].push_back({k, kItInv, 2, t, 0});

@@ -40,9 +40,13 @@ size_t worklist_scratch_bytes(const Plan &p);
 // descs/plans.  Instance k's scratch starts at scratch + off[idx[k]]; Dodis
 // et al. instances get precondition flags at pre + 2 k (pre may be null when
 // none is Dodis et al.).  Within a phase, larger transforms come first.
+// bext (may be null): per instance k, an external buffer for the transformed
+// seed operand B; if bready[k] it already holds that transform (its forward
+// tiles are skipped), otherwise the forward tiles write it there.
 void build_worklist(const cm_desc *descs, const Plan *plans, const uint32_t *idx, uint32_t n,
                     uint8_t *scratch, const size_t *off, int tile_lg, uint32_t *pre,
-                    std::vector<BatchInst> &insts, std::vector<WorkItem> &items);
+                    std::vector<BatchInst> &insts, std::vector<WorkItem> &items,
+                    uint64_t *const *bext = nullptr, const uint8_t *bready = nullptr);
 
 // Dynamic shared memory of the work-list kernel and its resident grid.
 size_t batch_smem_bytes();

@@ -50,6 +50,8 @@ size_t r256(size_t v) { return (v + 255) & ~size_t(255); }
 struct Req {
     cm_desc d;
     Plan p;
+    uint32_t flags = 0;
+    uint64_t seed_id = 0;
     size_t foot = 0;  // scratch bytes while on the device
     uint64_t t_submit = 0, t_admit = 0, t_done = 0, wave = 0;
     int status = CM_OK;
@@ -80,6 +82,25 @@ struct Buf {
     }
 };
 
+// Resident transform of a seed operand, keyed by (seed_id, kind, n, m).
+struct SeedKey {
+    uint64_t id, n, m;
+    int kind;
+    bool operator==(const SeedKey &o) const { return id == o.id && n == o.n && m == o.m && kind == o.kind; }
+};
+struct SeedKeyHash {
+    size_t operator()(const SeedKey &k) const {
+        return std::hash<uint64_t>()(k.id * 0x9E3779B97F4A7C15ull ^ k.n * 31 ^ k.m * 131 ^ (uint64_t)k.kind);
+    }
+};
+struct SeedEntry {
+    uint64_t *buf = nullptr;
+    size_t bytes = 0;
+    bool ready = false;  // holds the transform (its creating wave finished)
+    int refs = 0;        // in-flight waves using it
+    uint64_t last = 0;   // LRU clock
+};
+
 struct Slot {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
@@ -89,6 +110,7 @@ struct Slot {
     size_t foot = 0;
     uint64_t wave = 0;
     Buf insts, items, ctrl, flags;  // flags: [0] status word, then 2 words per request
+    std::vector<std::pair<SeedKey, bool>> seeds;  // cache entries used (true: created by this wave)
 };
 
 }  // namespace
@@ -108,6 +130,9 @@ struct cm_server {
     size_t inflight = 0, max_inflight = 0;
     uint64_t submitted = 0, completed = 0, rejected = 0;
     bool stop = false;
+    std::unordered_map<SeedKey, SeedEntry, SeedKeyHash> seeds;
+    size_t seed_bytes = 0, seed_limit = 0;
+    uint64_t seed_hits = 0, seed_misses = 0, lru = 0;
 };
 
 namespace {
@@ -130,11 +155,43 @@ void finish_slot(cm_server *S, Slot &sl) {
         r.done = true;
         ++S->completed;
     }
+    const bool ok = !(st_word & CM_FLAG_TIMEOUT);
+    for (auto &kc : sl.seeds) {
+        auto it = S->seeds.find(kc.first);
+        if (it == S->seeds.end()) continue;
+        it->second.refs -= 1;
+        if (kc.second) {
+            if (ok) {
+                it->second.ready = true;
+            } else if (it->second.refs == 0) {
+                cudaFreeAsync(it->second.buf, sl.st);
+                S->seed_bytes -= it->second.bytes;
+                S->seeds.erase(it);
+            }
+        }
+    }
+    sl.seeds.clear();
     S->inflight -= sl.foot;
     sl.foot = 0;
     sl.tickets.clear();
     sl.pre_index.clear();
     sl.busy = false;
+}
+
+// Make room for `bytes` of seed transforms by dropping unused entries, least
+// recently used first; false if it cannot.
+bool seed_make_room(cm_server *S, size_t bytes, cudaStream_t st) {
+    while (S->seed_bytes + bytes > S->seed_limit) {
+        auto victim = S->seeds.end();
+        for (auto it = S->seeds.begin(); it != S->seeds.end(); ++it)
+            if (it->second.refs == 0 && it->second.ready && (victim == S->seeds.end() || it->second.last < victim->second.last))
+                victim = it;
+        if (victim == S->seeds.end()) return false;
+        cudaFreeAsync(victim->second.buf, st);
+        S->seed_bytes -= victim->second.bytes;
+        S->seeds.erase(victim);
+    }
+    return true;
 }
 
 // Launch the requests `tk` (already admitted) as one wave on slot sl.
@@ -169,10 +226,47 @@ cm_status launch_wave(cm_server *S, Slot &sl, const std::vector<uint64_t> &tk) {
     const size_t flag_words = 2 + 2 * ((size_t)n + n);
     if (!sl.flags.ensure(flag_words * 4)) return CM_ENOMEM;
     uint32_t *dflags = static_cast<uint32_t *>(sl.flags.dev);
+    // resident seed transforms
+    std::vector<uint64_t *> bext(wl.size(), nullptr);
+    std::vector<uint8_t> bready(wl.size(), 0);
+    sl.seeds.clear();
+    for (uint32_t k = 0; k < wl.size(); ++k) {
+        const Req &r = S->reqs[tk[wl[k]]];
+        if (!(r.flags & CM_REQ_SEED_CACHE) || r.p.npass != 1) continue;
+        const SeedKey key{r.seed_id, r.p.n, r.p.m, r.p.kind};
+        auto it = S->seeds.find(key);
+        if (it != S->seeds.end()) {
+            if (!it->second.ready) continue;  // still being made by a wave in flight
+            it->second.refs += 1;
+            it->second.last = ++S->lru;
+            bext[k] = it->second.buf;
+            bready[k] = 1;
+            sl.seeds.push_back({key, false});
+            ++S->seed_hits;
+            continue;
+        }
+        const size_t bytes = 8 * r.p.L;
+        if (!seed_make_room(S, bytes, sl.st)) continue;
+        void *buf = nullptr;
+        if (cudaMallocFromPoolAsync(&buf, bytes, ctx->pool, sl.st) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        SeedEntry e;
+        e.buf = static_cast<uint64_t *>(buf);
+        e.bytes = bytes;
+        e.refs = 1;
+        e.last = ++S->lru;
+        S->seeds.emplace(key, e);
+        S->seed_bytes += bytes;
+        bext[k] = e.buf;
+        sl.seeds.push_back({key, true});
+        ++S->seed_misses;
+    }
     std::vector<BatchInst> insts;
     std::vector<WorkItem> items;
     build_worklist(descs.data(), plans.data(), wl.data(), (uint32_t)wl.size(), static_cast<uint8_t *>(scratch),
-                   off.data(), kTileLg, dflags + 2, insts, items);
+                   off.data(), kTileLg, dflags + 2, insts, items, bext.data(), bready.data());
     sl.pre_index.assign(n, -1);
     for (uint32_t k = 0; k < wl.size(); ++k)
         if (plans[wl[k]].kind == CM_DODIS) sl.pre_index[wl[k]] = (int)k;
@@ -253,7 +347,7 @@ void worker_main(cm_server *S) {
             size_t foot = 0;
             while (!S->pending.empty() && wave.size() < S->opt.max_wave) {
                 Req &r = S->reqs[S->pending.front()];
-                if (S->inflight + foot + r.foot > S->budget) break;  // admitted when memory frees up
+                if (S->inflight + foot + r.foot + S->seed_bytes > S->budget) break;  // admitted when memory frees up
                 foot += r.foot;
                 wave.push_back(S->pending.front());
                 S->pending.pop_front();
@@ -273,6 +367,17 @@ void worker_main(cm_server *S) {
             const cm_status s = launch_wave(S, sl, wave);
             if (s != CM_OK) {
                 cudaStreamSynchronize(sl.st);
+                for (auto &kc : sl.seeds) {
+                    auto it = S->seeds.find(kc.first);
+                    if (it == S->seeds.end()) continue;
+                    it->second.refs -= 1;
+                    if (kc.second && it->second.refs == 0) {
+                        cudaFreeAsync(it->second.buf, sl.st);
+                        S->seed_bytes -= it->second.bytes;
+                        S->seeds.erase(it);
+                    }
+                }
+                sl.seeds.clear();
                 for (uint64_t tk : wave) {
                     Req &r = S->reqs[tk];
                     r.status = s;
@@ -299,6 +404,8 @@ void server_release(cm_server *S) {
     }
     S->cv_work.notify_all();
     if (S->worker.joinable()) S->worker.join();
+    for (auto &kv : S->seeds) cudaFree(kv.second.buf);  // pool memory; device is idle here
+    S->seeds.clear();
     for (Slot &sl : S->slots) {
         if (sl.st) cudaStreamSynchronize(sl.st);
         sl.insts.release();
@@ -332,6 +439,7 @@ extern "C" cm_status cm_server_start(cm_ctx *ctx, const cm_server_options *opt) 
     if (!S->opt.max_wave) S->opt.max_wave = 512;
     S->budget = S->opt.hbm_budget_bytes ? S->opt.hbm_budget_bytes : ctx->budget / 2;
     if (S->budget > ctx->budget) S->budget = ctx->budget;
+    S->seed_limit = S->opt.seed_cache_bytes ? S->opt.seed_cache_bytes : S->budget / 4;
     S->grid = batch_grid(ctx->nsm);
     if (S->grid < 1) {
         delete S;
@@ -369,6 +477,9 @@ extern "C" cm_status cm_submit(cm_ctx *ctx, const cm_request *rq, uint64_t *tick
     r.d.x = rq->x;
     r.d.y = rq->y;
     r.d.z = rq->z;
+    r.flags = rq->flags;
+    r.seed_id = rq->seed_id;
+    if (rq->flags & ~CM_REQ_SEED_CACHE) return CM_EINVAL;
     if (!rq->x || !rq->y || !rq->z || !make_plan(rq->kind, rq->n, rq->m, &r.p)) return CM_EINVAL;
     r.foot = r.p.npass <= 1 ? worklist_scratch_bytes(r.p) : r256(r.p.scratch_bytes);
     r.foot += 256;  // work-list and flag share
@@ -433,6 +544,10 @@ extern "C" cm_status cm_server_get_stats(cm_ctx *ctx, cm_server_stats *st) {
     st->inflight_bytes = S->inflight;
     st->max_inflight_bytes = S->max_inflight;
     st->budget_bytes = S->budget;
+    st->seed_cache_hits = S->seed_hits;
+    st->seed_cache_misses = S->seed_misses;
+    st->seed_cache_bytes = S->seed_bytes;
+    st->seed_cache_entries = S->seeds.size();
     st->queued = (uint32_t)S->pending.size();
     uint32_t busy = 0;
     for (const Slot &sl : S->slots) busy += sl.busy ? 1u : 0u;

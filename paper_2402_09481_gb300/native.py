@@ -86,7 +86,10 @@ class BatchStats(ctypes.Structure):
 class CmRequest(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("flags", ctypes.c_uint32), ("n", ctypes.c_uint64),
                 ("m", ctypes.c_uint64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
-                ("z", ctypes.c_void_p), ("user", ctypes.c_uint64)]
+                ("z", ctypes.c_void_p), ("seed_id", ctypes.c_uint64), ("user", ctypes.c_uint64)]
+
+
+REQ_SEED_CACHE = 0x1
 
 
 class CmResult(ctypes.Structure):
@@ -96,14 +99,16 @@ class CmResult(ctypes.Structure):
 
 class ServerOptions(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32),
-                ("max_queue", ctypes.c_uint32), ("max_wave", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 5)]
+                ("max_queue", ctypes.c_uint32), ("max_wave", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+                ("seed_cache_bytes", ctypes.c_uint64), ("reserved", ctypes.c_uint32 * 2)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("waves", ctypes.c_uint64), ("inflight_bytes", ctypes.c_uint64),
                 ("max_inflight_bytes", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64),
+                ("seed_cache_hits", ctypes.c_uint64), ("seed_cache_misses", ctypes.c_uint64),
+                ("seed_cache_bytes", ctypes.c_uint64), ("seed_cache_entries", ctypes.c_uint64),
                 ("queued", ctypes.c_uint32), ("busy_slots", ctypes.c_uint32), ("slots", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
 
@@ -333,24 +338,26 @@ class Context:
         return Z
 
     # ----- serving -------------------------------------------------------------
-    def server_start(self, hbm_budget_bytes: int = 0, slots: int = 0, max_queue: int = 0, max_wave: int = 0):
-        o = ServerOptions(hbm_budget_bytes, slots, max_queue, max_wave)
+    def server_start(self, hbm_budget_bytes: int = 0, slots: int = 0, max_queue: int = 0, max_wave: int = 0,
+                     seed_cache_bytes: int = 0):
+        o = ServerOptions(hbm_budget_bytes, slots, max_queue, max_wave, 0, seed_cache_bytes)
         _check(self._L.cm_server_start(self._h, ctypes.byref(o)), "cm_server_start")
 
     def server_stop(self):
         _check(self._L.cm_server_stop(self._h), "cm_server_stop")
 
-    def submit_raw(self, kind: int, n: int, m: int, px: int, py: int, pz: int) -> tuple[int, int]:
-        """(status, ticket) for device pointers; no exception on CM_EAGAIN / CM_ENOMEM."""
-        r = CmRequest(kind, 0, n, m, px, py, pz, 0)
+    def submit_raw(self, kind: int, n: int, m: int, px: int, py: int, pz: int, seed_id: int = 0) -> tuple[int, int]:
+        """(status, ticket) for device pointers; no exception on CM_EAGAIN / CM_ENOMEM.
+        seed_id != 0 asks the server to keep the seed's transform resident."""
+        r = CmRequest(kind, REQ_SEED_CACHE if seed_id else 0, n, m, px, py, pz, seed_id, 0)
         t = ctypes.c_uint64(0)
         s = self._L.cm_submit(self._h, ctypes.byref(r), ctypes.byref(t))
         return int(s), int(t.value)
 
-    def submit(self, kind: int, n: int, m: int, x, y, z) -> int:
+    def submit(self, kind: int, n: int, m: int, x, y, z, seed_id: int = 0) -> int:
         ybits = n + m - 1 if kind == TOEPLITZ else (n + 1 if kind == CIRCULANT else n)
         s, t = self.submit_raw(kind, n, m, _dev_words(x, n, "x"), _dev_words(y, ybits, "y"),
-                               _dev_words(z, m, "z"))
+                               _dev_words(z, m, "z"), seed_id)
         _check(s, "cm_submit")
         return t
 

@@ -163,3 +163,33 @@ def test_server_dodis_precondition_per_request(sctx, cm_ctx):
     for r in reqs[2:]:
         assert torch.equal(r["z"], alone(cm_ctx, r))
     sctx.server_stop()
+
+
+def test_server_seed_transform_resident(sctx, cm_ctx):
+    # several inputs under one seed: the seed's transform is computed once and
+    # reused; every output still equals its single call
+    sctx.server_start(seed_cache_bytes=1 << 30)
+    P = oracle.next_na(200000)
+    groups = [(T, 150000, 60000), (C, P - 1, (P - 1) // 2), (D, P, P // 3)]
+    reqs = []
+    for g, (k, n, m) in enumerate(groups):
+        base = make(k, n, m, 1000 + 100 * g)
+        for j in range(4):
+            r = make(k, n, m, 1000 + 100 * g + 2 * j + 2)
+            r["y"], r["yw"] = base["y"], base["yw"]
+            reqs.append((r, 77 + g))
+    first = [sctx.submit(r["kind"], r["n"], r["m"], r["x"], r["y"], r["z"], seed_id=sid)
+             for r, sid in reqs[::4]]
+    for t in first:
+        assert wait(sctx, t)["status"] == native.CM_OK
+    rest = [sctx.submit(r["kind"], r["n"], r["m"], r["x"], r["y"], r["z"], seed_id=sid)
+            for i, (r, sid) in enumerate(reqs) if i % 4]
+    for t in rest:
+        assert wait(sctx, t)["status"] == native.CM_OK
+    st = sctx.server_stats()
+    assert st["seed_cache_misses"] == 3 and st["seed_cache_hits"] == 9 and st["seed_cache_entries"] == 3
+    for r, _ in reqs:
+        assert torch.equal(r["z"], alone(cm_ctx, r)), (r["kind"], r["n"])
+    r0 = reqs[0][0]
+    assert (from_dev(r0["z"]) == oracle.toeplitz_packed(r0["xw"], r0["n"], r0["yw"], r0["m"])).all()
+    sctx.server_stop()
