@@ -193,7 +193,7 @@ k_batch(const BatchInst *__restrict__ insts, const WorkItem *__restrict__ items,
     uint64_t *sA = smem + 8192;              // also the pass tile (2^14 elements)
     uint64_t *sB = sA + sp_size(1 << kMidLgMax);
     __shared__ uint32_t s_item, s_skip;
-    for (int e = threadIdx.x; e < 8192; e += kThreads) tw[e] = __ldg(rt.small + e);
+    for (int e = threadIdx.x; e < 8192; e += kThreads) tw[tw_swz(e)] = __ldg(rt.small + e);
     uint32_t *next = ctrl, *abort_flag = ctrl + 1, *done = ctrl + 2;
     for (;;) {
         if (threadIdx.x == 0) {

@@ -95,6 +95,7 @@ k_pass(uint64_t *__restrict__ data, BitMap map, int lgN, int lgS, uint8_t *__res
     // rows are stored in the digit-reversed order of the on-chip transform:
     // row p of the tile holds frequency pos_to_freq(p) (forward) and is read
     // back as such (inverse), so the pass twiddle uses that frequency.
+#pragma unroll 4
     for (int e = threadIdx.x; e < R * C; e += kThreads) {
         const int i = e >> NCOL_LG, c = e & (C - 1);
         const uint64_t g = base + ((uint64_t)i << lgS) + c;
@@ -112,6 +113,7 @@ k_pass(uint64_t *__restrict__ data, BitMap map, int lgN, int lgS, uint8_t *__res
     } else {
         ntt_fwd<LOGR, NCOL_LG, 1>(smem, smem, tw);
     }
+#pragma unroll 4
     for (int e = threadIdx.x; e < R * C; e += kThreads) {
         const int i = e >> NCOL_LG, c = e & (C - 1);
         uint64_t v = smem[sp(e)];

@@ -20,6 +20,12 @@ constexpr int kSmallLg = 13;      // root table omega_{2^13}^e, e < 2^13
 
 // Shared-memory index with one pad word per 32 (breaks power-of-two strides).
 __device__ __forceinline__ int sp(int i) { return i + (i >> 5); }
+
+// Position of root e in a shared-memory root table.  Lookups index the table
+// with power-of-two strides (e = i2 k1 2^off for consecutive i2), which would
+// send up to 16 lanes to one bank; XOR-ing the bank-pair bits (e & 15) with
+// higher bits spreads them.  A bijection inside every aligned group of 16.
+__device__ __forceinline__ int tw_swz(int e) { return e ^ (((e >> 5) ^ (e >> 9)) & 15); }
 __host__ __device__ constexpr int sp_size(int n) { return n + (n >> 5) + 1; }
 
 struct RootTables {
@@ -140,7 +146,7 @@ __device__ __forceinline__ void fwd_step(uint64_t *s0, uint64_t *s1, const uint6
 #pragma unroll
         for (int k1 = 0; k1 < RD; ++k1) {
             uint64_t x = v[bitrev_c(k1, LQ)];
-            if (LM > 0 && k1 > 0 && i2 > 0) x = gl_mul(x, tw[(i2 * k1) << OFF]);
+            if (LM > 0 && k1 > 0 && i2 > 0) x = gl_mul(x, tw[tw_swz((i2 * k1) << OFF)]);
             s[sp(((row0 + (k1 << LM)) << NCOL_LG) + c)] = x;
         }
     }
@@ -165,7 +171,7 @@ __device__ __forceinline__ void inv_step(uint64_t *s0, uint64_t *s1, const uint6
 #pragma unroll
         for (int k1 = 0; k1 < RD; ++k1) {
             uint64_t x = s[sp(((row0 + (k1 << LM)) << NCOL_LG) + c)];
-            if (LM > 0 && k1 > 0 && i2 > 0) x = gl_mul(x, tw[(R - ((i2 * k1) << OFF)) & (R - 1)]);
+            if (LM > 0 && k1 > 0 && i2 > 0) x = gl_mul(x, tw[tw_swz((R - ((i2 * k1) << OFF)) & (R - 1))]);
             v[k1] = x;
         }
         dft_reg<LQ>(v);
@@ -220,7 +226,7 @@ __device__ __forceinline__ uint32_t pos_to_freq(uint32_t p) {
 // Fill tw[e] = omega_R^e (e < R) from the global table of omega_8192^e.
 template <int LOGR>
 __device__ __forceinline__ void load_roots(uint64_t *tw, const uint64_t *__restrict__ g8192) {
-    for (int e = threadIdx.x; e < (1 << LOGR); e += kThreads) tw[e] = __ldg(g8192 + (e << (kSmallLg - LOGR)));
+    for (int e = threadIdx.x; e < (1 << LOGR); e += kThreads) tw[tw_swz(e)] = __ldg(g8192 + (e << (kSmallLg - LOGR)));
 }
 
 __device__ __forceinline__ int bitrev(int k, int lg) {

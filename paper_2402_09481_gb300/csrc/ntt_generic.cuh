@@ -45,14 +45,14 @@ __device__ __forceinline__ void step_rt(uint64_t *s0, uint64_t *s1, int nbuf, in
 #pragma unroll
             for (int k1 = 0; k1 < RD; ++k1) {
                 uint64_t x = v[bitrev_c(k1, LQ)];
-                if (k1 > 0 && i2 > 0) x = gl_mul(x, tw8192[(i2 * k1) << tws]);
+                if (k1 > 0 && i2 > 0) x = gl_mul(x, tw8192[tw_swz((i2 * k1) << tws)]);
                 s[sp(((row0 + (k1 << LM)) << ncol_lg) + c)] = x;
             }
         } else {
 #pragma unroll
             for (int k1 = 0; k1 < RD; ++k1) {
                 uint64_t x = s[sp(((row0 + (k1 << LM)) << ncol_lg) + c)];
-                if (k1 > 0 && i2 > 0) x = gl_mul(x, tw8192[(8192 - ((i2 * k1) << tws)) & 8191]);
+                if (k1 > 0 && i2 > 0) x = gl_mul(x, tw8192[tw_swz((8192 - ((i2 * k1) << tws)) & 8191)]);
                 v[k1] = x;
             }
             dft_reg<LQ>(v);
