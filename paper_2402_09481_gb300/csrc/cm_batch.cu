@@ -142,10 +142,7 @@ __device__ void do_middle(const BatchInst &I, uint32_t r, const uint64_t *tw, ui
         sB[sp(2 * i + 1)] = vb.y;
     }
     __syncthreads();
-    ntt_fwd_rt(sA, sB, 2, LG, 0, tw);
-    for (int i = threadIdx.x; i < Bn; i += kThreads) sA[sp(i)] = gl_mul(gl_mul(sA[sp(i)], sB[sp(i)]), I.linv);
-    __syncthreads();
-    ntt_inv_rt(sA, sA, 1, LG, 0, tw);
+    middle_row_13(sA, sB, tw, I.linv);
     ulonglong2 *o2 = reinterpret_cast<ulonglong2 *>(I.A + row);
     for (int i = threadIdx.x; i < Bn / 2; i += kThreads) o2[i] = make_ulonglong2(sA[sp(2 * i)], sA[sp(2 * i + 1)]);
 }

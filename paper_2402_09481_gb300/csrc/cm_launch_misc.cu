@@ -32,11 +32,7 @@ k_middle(uint64_t *__restrict__ A, const uint64_t *__restrict__ Bv, uint64_t nro
             sB[sp(2 * i + 1)] = vb.y;
         }
         __syncthreads();
-        ntt_fwd<LG, 0, 2>(sA, sB, tw);
-        for (int i = threadIdx.x; i < Bn; i += kThreads)
-            sA[sp(i)] = gl_mul(gl_mul(sA[sp(i)], sB[sp(i)]), linv);
-        __syncthreads();
-        ntt_inv<LG, 0, 1>(sA, sA, tw);
+        middle_row_13(sA, sB, tw, linv);
         ulonglong2 *o2 = reinterpret_cast<ulonglong2 *>(A + row);
         for (int i = threadIdx.x; i < Bn / 2; i += kThreads)
             o2[i] = make_ulonglong2(sA[sp(2 * i)], sA[sp(2 * i + 1)]);

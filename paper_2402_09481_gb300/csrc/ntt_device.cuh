@@ -210,6 +210,43 @@ __device__ __forceinline__ void ntt_inv(uint64_t *s0, uint64_t *s1, const uint64
     if constexpr (LOGR > 0) inv_from<LOGR, st_n(LOGR) - 1, NCOL_LG, NBUF>(s0, s1, tw);
 }
 
+// One fused middle row of B = 2^13 elements (steps of radix 32, 16, 16): forward
+// transforms of both operands, the pointwise product scaled by linv, and the
+// inverse transform of the product, left in sA in natural order.  The last
+// forward step, the product and the first inverse step run in registers on
+// 16-row groups (thread t owns rows 16t .. 16t + 15 of both operands), and
+// steps 1 and 2 only touch the 256-row blocks of the calling warp, so they are
+// separated by warp barriers only.  Ends with a block barrier.
+__device__ __forceinline__ void middle_row_13(uint64_t *sA, uint64_t *sB, const uint64_t *tw, uint64_t linv) {
+    static_assert(st_n(13) == 3 && st_q(13, 0) == 5 && st_q(13, 1) == 4 && st_q(13, 2) == 4, "schedule");
+    static_assert(kThreads == 512, "one 16-row group per thread in the fused step");
+    fwd_step<13, 0, 0, 2>(sA, sB, tw);
+    __syncthreads();
+    fwd_step<13, 1, 0, 2>(sA, sB, tw);
+    __syncwarp();
+    {
+        const int row0 = threadIdx.x << 4;
+        uint64_t a[16], b[16], c[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) a[i] = sA[sp(row0 + i)];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) b[i] = sB[sp(row0 + i)];
+        dft_reg<4>(a);
+        dft_reg<4>(b);
+        // frequency k sits in register bitrev(k); the inverse step takes frequency order
+#pragma unroll
+        for (int k = 0; k < 16; ++k) c[k] = gl_mul(gl_mul(a[bitrev_c(k, 4)], b[bitrev_c(k, 4)]), linv);
+        dft_reg<4>(c);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sA[sp(row0 + i)] = c[bitrev_c((16 - i) & 15, 4)];
+    }
+    __syncwarp();
+    inv_step<13, 1, 0, 1>(sA, sA, tw);
+    __syncthreads();
+    inv_step<13, 0, 0, 1>(sA, sA, tw);
+    __syncthreads();
+}
+
 // Frequency held at position p after ntt_fwd<LOGR>: the digits k_j of p (step 0
 // in the top bits) reassembled least-significant first.
 template <int LOGR>
