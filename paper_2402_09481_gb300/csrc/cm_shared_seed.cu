@@ -70,7 +70,7 @@ __device__ __forceinline__ uint32_t x_word(const uint64_t *X, uint64_t wx, uint6
 __global__ void __launch_bounds__(256)
 k_ss_gf2(const uint32_t *__restrict__ T, uint32_t words_pad, const uint64_t *__restrict__ X, uint64_t wx,
          uint64_t count, uint64_t *__restrict__ Z, uint64_t wz) {
-    __shared__ __align__(16) uint32_t sT[kSsKw][kSsRows];    // [w][row]
+    __shared__ __align__(16) uint32_t sT[kSsKw][kSsRows + 4];  // [w][row], rows padded (16-B aligned)
     __shared__ __align__(16) uint32_t sX[kSsKw][kGfCols];    // [w][col]
     __shared__ uint16_t sOut[kGfCols][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -83,6 +83,7 @@ k_ss_gf2(const uint32_t *__restrict__ T, uint32_t words_pad, const uint64_t *__r
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c] = 0u;
     for (uint32_t w0 = 0; w0 < words_pad; w0 += kSsKw) {
+        // coalesced reads of T rows; the row padding spreads the transposed stores
         for (int e = threadIdx.x; e < kSsKw * kSsRows; e += 256) {
             const int r = e / kSsKw, w = e % kSsKw;
             sT[w][r] = __ldg(T + (uint64_t)(row0 + r) * words_pad + w0 + w);

@@ -133,6 +133,22 @@ __device__ __forceinline__ uint64_t gl_reduce_limbs(uint32_t r0, uint32_t r1, ui
     return r;
 }
 
+// Canonical residue of r0 + 2^32 r1 + 2^64 r2 (the shift twiddles with s <= 32,
+// where the 2^96 limb is zero): u = r2 * EPS (< p), v = (r1:r0) + u with the
+// carry folded back as + EPS, then v >= p -> v - p.
+__device__ __forceinline__ uint64_t gl_reduce_limbs3(uint32_t r0, uint32_t r1, uint32_t r2) {
+    uint64_t r;
+    asm("{\n\t.reg .u32 t0, t1, u0, u1, c, e;\n\t.reg .pred q;\n\t"
+        "sub.cc.u32 u0, 0, %3;\n\tsubc.u32 u1, %3, 0;\n\t"
+        "add.cc.u32 t0, %1, u0;\n\taddc.cc.u32 t1, %2, u1;\n\taddc.u32 c, 0, 0;\n\t"
+        "sub.u32 e, 0, c;\n\tadd.cc.u32 t0, t0, e;\n\taddc.u32 t1, t1, 0;\n\t"
+        "setp.eq.u32 q, t1, 0xFFFFFFFF;\n\tsetp.ne.and.u32 q, t0, 0, q;\n\t"
+        "@q sub.u32 t0, t0, 1;\n\t@q mov.u32 t1, 0;\n\t"
+        "mov.b64 %0, {t0, t1};\n\t}"
+        : "=l"(r) : "r"(r0), "r"(r1), "r"(r2));
+    return r;
+}
+
 // a * b mod p for a, b < 2^64; canonical result.
 __device__ __forceinline__ uint64_t gl_mul_ptx(uint64_t a, uint64_t b) {
     uint32_t r0, r1, r2, r3;
@@ -151,8 +167,8 @@ __device__ __forceinline__ uint64_t gl_shl_ptx(uint64_t x, int s) {
     if (s == 0) return x;
     if (s == 96) return gl_sub_ptx(0, x);
     const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32);
-    if (s < 32) return gl_reduce_limbs(x0 << s, __funnelshift_l(x0, x1, s), x1 >> (32 - s), 0);
-    if (s == 32) return gl_reduce_limbs(0, x0, x1, 0);
+    if (s < 32) return gl_reduce_limbs3(x0 << s, __funnelshift_l(x0, x1, s), x1 >> (32 - s));
+    if (s == 32) return gl_reduce_limbs3(0, x0, x1);
     if (s < 64) {
         const int t = s - 32;
         return gl_reduce_limbs(0, x0 << t, __funnelshift_l(x0, x1, t), x1 >> (32 - t));
