@@ -179,6 +179,11 @@ typedef struct {
 
 #define CM_BATCH_AUTOTUNE 0x1u /* time the candidate pass tiles on this batch, keep the fastest */
 #define CM_BATCH_NO_GRAPH 0x2u /* do not capture a CUDA graph */
+/* Failure-path test: the first instance with L > 2^13 waits for one more
+ * forward tile than the work list holds, so its middle rows' bounded waits run
+ * out: the launch ends early with CM_FLAG_TIMEOUT set in the device status
+ * (cm_device_status then returns CM_ETIMEDOUT) and the outputs are undefined. */
+#define CM_BATCH_TEST_STALL 0x4u
 
 typedef struct cm_batch cm_batch;
 

@@ -267,7 +267,8 @@ cudaError_t launch_k_batch(const BatchInst *insts, const WorkItem *items, uint32
 void build_worklist(const cm_desc *descs, const Plan *plans, const uint32_t *idx, uint32_t n,
                     uint8_t *scratch, const size_t *off, int tile_lg, uint32_t *pre,
                     std::vector<BatchInst> &insts, std::vector<WorkItem> &items, uint64_t *const *bext,
-                    const uint8_t *bready) {
+                    const uint8_t *bready, bool test_stall) {
+    bool stalled = false;
     insts.assign(n, BatchInst());
     std::vector<WorkItem> phase[4];
     std::vector<WorkItem> smalls;
@@ -308,6 +309,10 @@ void build_worklist(const cm_desc *descs, const Plan *plans, const uint32_t *idx
         const uint32_t rows = (uint32_t)(p.L >> kMidLgMax);
         const uint32_t packs = (uint32_t)((((p.m + 63) >> 6) + kPackWordsPerItem - 1) / kPackWordsPerItem);
         I.need[0] = (have_b ? 1 : 2) * tiles + (I.pre ? 1 : 0);
+        if (test_stall && !stalled) {
+            I.need[0] += 1;  // a count nothing will ever reach
+            stalled = true;
+        }
         I.need[1] = rows;
         I.need[2] = tiles;
         I.need[3] = packs;
@@ -352,6 +357,7 @@ struct cm_batch {
     int tile_lg = kTileLg;
     int grid = 0;
     uint64_t kernel_launches = 0;
+    bool test_stall = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -362,7 +368,7 @@ static cm_status batch_build(cm_batch *b) {
     std::vector<BatchInst> insts;
     std::vector<WorkItem> items;
     build_worklist(b->descs.data(), b->plans.data(), b->wl.data(), n, static_cast<uint8_t *>(b->scratch),
-                   b->off_scratch.data(), b->tile_lg, b->d_pre, insts, items);
+                   b->off_scratch.data(), b->tile_lg, b->d_pre, insts, items, nullptr, nullptr, b->test_stall);
     if (b->d_insts) cudaFree(b->d_insts);
     if (b->d_items) cudaFree(b->d_items);
     b->d_insts = nullptr;
@@ -435,6 +441,8 @@ extern "C" cm_status cm_batch_create(cm_ctx *ctx, const cm_desc *descs, uint32_t
     if (cudaSetDevice(ctx->device) != cudaSuccess) return CM_EDEVICE;
     cm_batch *b = new cm_batch();
     b->ctx = ctx;
+    b->test_stall = (flags & CM_BATCH_TEST_STALL) != 0;
+    if (b->test_stall) flags = (flags & ~CM_BATCH_AUTOTUNE) | CM_BATCH_NO_GRAPH;
     b->descs.assign(descs, descs + count);
     b->plans.resize(count);
     b->off_scratch.assign(count, 0);

@@ -46,7 +46,7 @@ size_t worklist_scratch_bytes(const Plan &p);
 void build_worklist(const cm_desc *descs, const Plan *plans, const uint32_t *idx, uint32_t n,
                     uint8_t *scratch, const size_t *off, int tile_lg, uint32_t *pre,
                     std::vector<BatchInst> &insts, std::vector<WorkItem> &items,
-                    uint64_t *const *bext = nullptr, const uint8_t *bready = nullptr);
+                    uint64_t *const *bext = nullptr, const uint8_t *bready = nullptr, bool test_stall = false);
 
 // Dynamic shared memory of the work-list kernel and its resident grid.
 size_t batch_smem_bytes();

@@ -113,7 +113,7 @@ class ServerStats(ctypes.Structure):
                 ("reserved", ctypes.c_uint32)]
 
 
-BATCH_AUTOTUNE, BATCH_NO_GRAPH = 0x1, 0x2
+BATCH_AUTOTUNE, BATCH_NO_GRAPH, BATCH_TEST_STALL = 0x1, 0x2, 0x4
 ENGINE_AUTO, ENGINE_IMMA, ENGINE_GF2 = 0, 1, 2
 
 
@@ -308,10 +308,11 @@ class Context:
                             _dev_words(z, m, "z"))
         return arr
 
-    def batch(self, items, autotune: bool = False, graph: bool = True) -> "Batch":
+    def batch(self, items, autotune: bool = False, graph: bool = True, test_stall: bool = False) -> "Batch":
         """Plan a batch (cm_batch_create); items are (kind, n, m, x, y, z)."""
         arr = self._descs(items)
         flags = (BATCH_AUTOTUNE if autotune else 0) | (0 if graph else BATCH_NO_GRAPH)
+        flags |= BATCH_TEST_STALL if test_stall else 0
         h = ctypes.c_void_p()
         _check(self._L.cm_batch_create(self._h, ctypes.cast(arr, ctypes.c_void_p), len(items), flags,
                                        ctypes.byref(h)), "cm_batch_create")

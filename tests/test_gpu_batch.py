@@ -1,6 +1,8 @@
 """Batched extraction (one persistent work-list launch) vs the single calls and
 the CPU oracle, bit for bit."""
 
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -125,3 +127,29 @@ def test_batch_invalid_descriptor(cm_ctx):
     s = native.lib().cm_batch_toeplitz(cm_ctx.handle, native.ctypes.cast(arr, native.ctypes.c_void_p), 1,
                                        torch.cuda.current_stream().cuda_stream)
     assert s == native.CM_EINVAL
+
+
+def test_batch_bounded_wait_times_out_and_context_survives(cm_ctx):
+    # one instance waits for a forward-tile count that nothing will reach: the
+    # bounded spin runs out, the kernel sets CM_FLAG_TIMEOUT and returns (no
+    # trap, no hang), and the context keeps working
+    specs = [(T, 20000, 10000), (T, 3000, 1000), (T, 70000, 30000)]
+    items, _ = make_items(specs, 6100)
+    b = cm_ctx.batch(items, test_stall=True)
+    t0 = time.time()
+    b.launch()
+    torch.cuda.synchronize()
+    elapsed = time.time() - t0
+    s, f = cm_ctx.device_status()
+    assert s == native.CM_ETIMEDOUT and f & native.FLAG_TIMEOUT
+    assert elapsed < 60.0
+    b.close()
+    kind, n, m, x, y, z = items[1]
+    z2 = cm_ctx.toeplitz(x, n, y, m)
+    assert cm_ctx.device_status() == (native.CM_OK, 0)
+    good = cm_ctx.batch(items)
+    good.launch()
+    torch.cuda.synchronize()
+    assert cm_ctx.device_status() == (native.CM_OK, 0)
+    assert torch.equal(items[1][5], z2)
+    good.close()
