@@ -33,7 +33,6 @@ namespace {
 
 constexpr int kSsRows = 64;     // output rows per CTA tile
 constexpr int kSsKw = 32;       // 32-bit words of K per smem chunk (1024 bits)
-constexpr int kGfCols = 256;    // GF(2) engine: instances per CTA tile
 constexpr int kImCols = 128;    // IMMA engine: instances per CTA tile
 
 // T bit rows: word w (32-bit) of row i holds bits j = 32 w .. 32 w + 31.
@@ -65,38 +64,54 @@ __device__ __forceinline__ uint32_t x_word(const uint64_t *X, uint64_t wx, uint6
 }
 
 // ---------------------------------------------------------------------------
-// GF(2) engine: thread tile 16 rows x 4 instances, XOR-of-AND accumulators.
+// GF(2) engine: thread tile 16 rows x CPT instances, XOR-of-AND accumulators.
+// CTA: 8 warps = 4 row groups (16 rows each, 64 rows) x 2 instance groups of
+// 32 CPT instances.  CPT = 4 holds 64 accumulators (2 CTAs per SM by
+// registers); CPT = 2 holds 32 and fits more CTAs; the autotuner picks.
 // ---------------------------------------------------------------------------
+template <int CPT>
 __global__ void __launch_bounds__(256)
 k_ss_gf2(const uint32_t *__restrict__ T, uint32_t words_pad, const uint64_t *__restrict__ X, uint64_t wx,
          uint64_t count, uint64_t *__restrict__ Z, uint64_t wz) {
+    constexpr int COLS = 64 * CPT;  // instances per CTA
     __shared__ __align__(16) uint32_t sT[kSsKw][kSsRows + 4];  // [w][row], rows padded (16-B aligned)
-    __shared__ __align__(16) uint32_t sX[kSsKw][kGfCols];    // [w][col]
-    __shared__ uint16_t sOut[kGfCols][4];
+    __shared__ __align__(16) uint32_t sX[kSsKw][COLS];         // [w][col]
+    __shared__ uint16_t sOut[COLS][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rg = warp & 3, cg = warp >> 2;
     const uint32_t row0 = blockIdx.x * kSsRows;
-    const uint64_t col0 = (uint64_t)blockIdx.y * kGfCols;
-    uint32_t acc[16][4];
+    const uint64_t col0 = (uint64_t)blockIdx.y * COLS;
+    uint32_t acc[16][CPT];
 #pragma unroll
     for (int r = 0; r < 16; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = 0u;
+        for (int c = 0; c < CPT; ++c) acc[r][c] = 0u;
     for (uint32_t w0 = 0; w0 < words_pad; w0 += kSsKw) {
         // coalesced reads of T rows; the row padding spreads the transposed stores
         for (int e = threadIdx.x; e < kSsKw * kSsRows; e += 256) {
             const int r = e / kSsKw, w = e % kSsKw;
             sT[w][r] = __ldg(T + (uint64_t)(row0 + r) * words_pad + w0 + w);
         }
-        {
-            const uint64_t c = col0 + threadIdx.x;
-            for (int w = 0; w < kSsKw; ++w) sX[w][threadIdx.x] = c < count ? x_word(X, wx, c, w0 + w) : 0u;
+        for (int cc = threadIdx.x; cc < COLS; cc += 256) {
+            const uint64_t c = col0 + cc;
+            for (int w = 0; w < kSsKw; w += 2) {
+                uint64_t v = 0;
+                if (c < count && (w0 + w) / 2 < wx) v = __ldg(X + c * wx + (w0 + w) / 2);
+                sX[w][cc] = (uint32_t)v;
+                sX[w + 1][cc] = (uint32_t)(v >> 32);
+            }
         }
         __syncthreads();
 #pragma unroll 4
         for (int w = 0; w < kSsKw; ++w) {
-            const uint4 x4 = *reinterpret_cast<const uint4 *>(&sX[w][cg * 128 + lane * 4]);
-            const uint32_t xv[4] = {x4.x, x4.y, x4.z, x4.w};
+            uint32_t xv[CPT];
+            if constexpr (CPT == 4) {
+                const uint4 x4 = *reinterpret_cast<const uint4 *>(&sX[w][cg * 128 + lane * 4]);
+                xv[0] = x4.x; xv[1] = x4.y; xv[2] = x4.z; xv[3] = x4.w;
+            } else {
+                const uint2 x2 = *reinterpret_cast<const uint2 *>(&sX[w][cg * 64 + lane * 2]);
+                xv[0] = x2.x; xv[1] = x2.y;
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const uint4 t4 = *reinterpret_cast<const uint4 *>(&sT[w][rg * 16 + q * 4]);
@@ -104,25 +119,27 @@ k_ss_gf2(const uint32_t *__restrict__ T, uint32_t words_pad, const uint64_t *__r
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[q * 4 + r][c] ^= tv[r] & xv[c];
+                    for (int c = 0; c < CPT; ++c) acc[q * 4 + r][c] ^= tv[r] & xv[c];
             }
         }
         __syncthreads();
     }
     // parity of each accumulator: 16 row bits per instance per thread
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < CPT; ++c) {
         uint32_t bits = 0;
 #pragma unroll
         for (int r = 0; r < 16; ++r) bits |= (uint32_t)(__popc(acc[r][c]) & 1) << r;
-        sOut[cg * 128 + lane * 4 + c][rg] = (uint16_t)bits;
+        sOut[cg * 32 * CPT + lane * CPT + c][rg] = (uint16_t)bits;
     }
     __syncthreads();
-    const uint64_t c = col0 + threadIdx.x;
-    if (c < count) {
-        const uint64_t word = (uint64_t)sOut[threadIdx.x][0] | ((uint64_t)sOut[threadIdx.x][1] << 16) |
-                              ((uint64_t)sOut[threadIdx.x][2] << 32) | ((uint64_t)sOut[threadIdx.x][3] << 48);
-        Z[c * wz + (row0 >> 6)] = word;
+    for (int cc = threadIdx.x; cc < COLS; cc += 256) {
+        const uint64_t c = col0 + cc;
+        if (c < count) {
+            const uint64_t word = (uint64_t)sOut[cc][0] | ((uint64_t)sOut[cc][1] << 16) |
+                                  ((uint64_t)sOut[cc][2] << 32) | ((uint64_t)sOut[cc][3] << 48);
+            Z[c * wz + (row0 >> 6)] = word;
+        }
     }
 }
 
@@ -214,15 +231,23 @@ k_ss_imma(const uint32_t *__restrict__ T, uint32_t words_pad, const uint64_t *__
 }
 
 std::mutex g_engine_mu;
-std::map<std::pair<uint64_t, uint64_t>, int> g_engine_choice;  // (n, m) -> engine
+std::map<std::pair<uint64_t, uint64_t>, int> g_engine_choice;  // (n, m) -> engine variant
 
-cm_status launch_engine(int engine, const uint32_t *T, uint32_t rows_pad, uint32_t words_pad,
-                        const uint64_t *X, uint64_t wx, uint64_t count, uint64_t *Z, uint64_t wz,
-                        cm_ctx *ctx, cudaStream_t st) {
-    if (engine == CM_ENGINE_GF2) {
-        dim3 grid(rows_pad / kSsRows, (unsigned)((count + kGfCols - 1) / kGfCols));
+// Engine variants the autotuner times: the INT8 engine and the GF(2) engine
+// with 4 or 2 instances per thread.
+constexpr int kVarImma = 0, kVarGf2x4 = 1, kVarGf2x2 = 2;
+
+cm_status launch_variant(int var, const uint32_t *T, uint32_t rows_pad, uint32_t words_pad,
+                         const uint64_t *X, uint64_t wx, uint64_t count, uint64_t *Z, uint64_t wz,
+                         cm_ctx *ctx, cudaStream_t st) {
+    if (var == kVarGf2x4) {
+        dim3 grid(rows_pad / kSsRows, (unsigned)((count + 255) / 256));
         ProfScope ps(ctx, "k_ss_gf2", st);
-        k_ss_gf2<<<grid, 256, 0, st>>>(T, words_pad, X, wx, count, Z, wz);
+        k_ss_gf2<4><<<grid, 256, 0, st>>>(T, words_pad, X, wx, count, Z, wz);
+    } else if (var == kVarGf2x2) {
+        dim3 grid(rows_pad / kSsRows, (unsigned)((count + 127) / 128));
+        ProfScope ps(ctx, "k_ss_gf2", st);
+        k_ss_gf2<2><<<grid, 256, 0, st>>>(T, words_pad, X, wx, count, Z, wz);
     } else {
         dim3 grid(rows_pad / kSsRows, (unsigned)((count + kImCols - 1) / kImCols));
         ProfScope ps(ctx, "k_ss_imma", st);
@@ -265,38 +290,41 @@ extern "C" cm_status cm_batch_toeplitz_shared_seed(cm_ctx *ctx, const uint64_t *
         k_toep_rows<<<(unsigned)blocks, 256, 0, st>>>(y, n, m, T, rows_pad, words_pad);
         if (cudaGetLastError() != cudaSuccess) s = CM_EDEVICE;
     }
-    if (s == CM_OK && engine == CM_ENGINE_AUTO) {
+    int var = engine == CM_ENGINE_IMMA ? kVarImma : kVarGf2x4;
+    if (s == CM_OK && engine != CM_ENGINE_IMMA) {
+        // CM_ENGINE_GF2 and CM_ENGINE_AUTO use the tuned variant for (n, m);
+        // the first call of a shape times the candidates on its own data
         std::lock_guard<std::mutex> lock(g_engine_mu);
         auto it = g_engine_choice.find({n, m});
-        if (it != g_engine_choice.end()) {
-            engine = it->second;
+        if (it != g_engine_choice.end() && (engine == CM_ENGINE_AUTO || it->second != kVarImma)) {
+            var = it->second;
         } else {
-            // time both engines on this call (each writes the same Z) and keep the faster
             float best = 1e30f;
-            int best_e = CM_ENGINE_GF2;
+            int best_v = kVarGf2x4;
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
-            for (int e : {CM_ENGINE_IMMA, CM_ENGINE_GF2}) {
-                launch_engine(e, T, rows_pad, words_pad, X, wx, count, Z, wz, ctx, st);  // warm-up
+            for (int v : {kVarImma, kVarGf2x4, kVarGf2x2}) {
+                if (engine == CM_ENGINE_GF2 && v == kVarImma) continue;
+                launch_variant(v, T, rows_pad, words_pad, X, wx, count, Z, wz, ctx, st);  // warm-up
                 cudaEventRecord(e0, st);
-                s = launch_engine(e, T, rows_pad, words_pad, X, wx, count, Z, wz, ctx, st);
+                s = launch_variant(v, T, rows_pad, words_pad, X, wx, count, Z, wz, ctx, st);
                 cudaEventRecord(e1, st);
                 cudaEventSynchronize(e1);
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
                 if (s == CM_OK && ms < best) {
                     best = ms;
-                    best_e = e;
+                    best_v = v;
                 }
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
-            g_engine_choice[{n, m}] = best_e;
-            engine = best_e;
+            if (engine == CM_ENGINE_AUTO || best_v != kVarImma) g_engine_choice[{n, m}] = best_v;
+            var = best_v;
         }
     }
-    if (s == CM_OK) s = launch_engine(engine, T, rows_pad, words_pad, X, wx, count, Z, wz, ctx, st);
+    if (s == CM_OK) s = launch_variant(var, T, rows_pad, words_pad, X, wx, count, Z, wz, ctx, st);
     cudaFreeAsync(Tv, st);
     return s;
 }
@@ -304,5 +332,6 @@ extern "C" cm_status cm_batch_toeplitz_shared_seed(cm_ctx *ctx, const uint64_t *
 extern "C" int cm_shared_seed_engine(uint64_t n, uint64_t m) {
     std::lock_guard<std::mutex> lock(g_engine_mu);
     auto it = g_engine_choice.find({n, m});
-    return it == g_engine_choice.end() ? CM_ENGINE_AUTO : it->second;
+    if (it == g_engine_choice.end()) return CM_ENGINE_AUTO;
+    return it->second == kVarImma ? CM_ENGINE_IMMA : CM_ENGINE_GF2;
 }
