@@ -13,6 +13,12 @@ the other operand modulo 2.  There is no transform, no field arithmetic and no
 code shared with the CUDA path; the two meet only in the seeded input generator
 ``paper_2402_09481_gb300.inputs``, which holds none of the method's arithmetic.
 
+``oracle.params`` evaluates the output-length theorems of the same Section
+(and the Trevisan seed length, the N_A length planning of the paper's QKD and
+QRNG examples); ``tests/test_params.py`` pins it to the paper's printed
+example arithmetic and re-derives each two-source and Markov-model bound from
+its base theorem.
+
 Parity status: every function here is pinned by ``tests/test_oracle.py``
 (brute force, closed forms, the paper's displayed matrices, the two-universality
 count of Thm. 2-univ, the rank lemmas, cross-definition identities) and

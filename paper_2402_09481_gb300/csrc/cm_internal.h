@@ -68,5 +68,6 @@ bool make_plan(int kind, uint64_t n, uint64_t m, Plan *out);
 
 // N_A membership and search (host, deterministic).
 bool is_na_prime(uint64_t P);
+bool is_prime(uint64_t n);
 
 }  // namespace cm

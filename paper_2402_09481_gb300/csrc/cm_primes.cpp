@@ -71,6 +71,8 @@ static bool na_uncached(uint64_t P) {
     return true;
 }
 
+bool is_prime(uint64_t n) { return is_prime_u64(n); }
+
 bool is_na_prime(uint64_t P) {
     static std::mutex mu;
     static std::unordered_map<uint64_t, bool> cache;

@@ -1,4 +1,4 @@
-"""ctypes binding of libcm.so (the C ABI declared in include/cm.h).
+"""ctypes binding of libcm.so (the C ABI declared in include/*.h).
 
 Argument marshalling only: every step of the extraction runs in the library's
 CUDA kernels.  Tensors are used for device memory and streams; the library
@@ -61,7 +61,24 @@ PROTOTYPES = {
     "cm_ntt_length": (_U64, [_I, _U64, _U64]),
     "cm_scratch_bytes": (_U64, [_I, _U64, _U64]),
     "cm_launch_count": (_U32, [_I, _U64, _U64]),
+    "cm_output_length": (_I, [_I, _I, _I, _U64, _U64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                              ctypes.POINTER(ctypes.c_int64)]),
+    "cm_trevisan_seed_length": (_I, [_U64, _U64, ctypes.c_double, ctypes.POINTER(_U64),
+                                     ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
+    "cm_plan_params": (_I, [_I, _I, _I, _U64, ctypes.c_double, ctypes.c_double, ctypes.c_double, _I, _P]),
+    "cm_closest_na_prime": (_U64, [_U64]),
 }
+
+TREVISAN = 3
+MODEL_SEEDED, MODEL_PRODUCT, MODEL_MARKOV = 0, 1, 2
+ADV_CLASSICAL, ADV_QUANTUM = 0, 1
+ADJUST_UP, ADJUST_DOWN, ADJUST_CLOSEST = 0, 1, 2
+
+
+class ParamPlan(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_uint64), ("n2", ctypes.c_uint64), ("pad_input", ctypes.c_uint64),
+                ("cut_input", ctypes.c_uint64), ("k1", ctypes.c_double), ("k2", ctypes.c_double),
+                ("m", ctypes.c_int64), ("reserved", ctypes.c_uint64 * 3)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -124,11 +141,15 @@ class CMError(RuntimeError):
 
 
 def header_functions() -> list[str]:
-    """Names of the functions include/cm.h declares."""
-    with open(os.path.join(_build.INCLUDE, "cm.h")) as f:
-        text = f.read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(cm_[a-z0-9_]+)\s*\(", text)))
+    """Names of the functions the headers under include/ declare."""
+    names = set()
+    for h in sorted(os.listdir(_build.INCLUDE)):
+        if not h.endswith(".h"):
+            continue
+        with open(os.path.join(_build.INCLUDE, h)) as f:
+            text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+        names |= set(re.findall(r"\b(cm_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def lib():
@@ -186,6 +207,36 @@ def next_na_prime(n: int) -> int:
 
 def prev_na_prime(n: int) -> int:
     return int(lib().cm_prev_na_prime(n))
+
+
+def closest_na_prime(n: int) -> int:
+    return int(lib().cm_closest_na_prime(n))
+
+
+def output_length(kind: int, model: int, adversary: int, n1: int, k1: float, log2_eps: float,
+                  k2: float = 0.0, d: int = 0) -> int:
+    """Largest m the paper's bound allows (cm_output_length)."""
+    m = ctypes.c_int64(0)
+    _check(lib().cm_output_length(kind, model, adversary, n1, d, float(k1), float(k2), float(log2_eps),
+                                  ctypes.byref(m)), "cm_output_length")
+    return int(m.value)
+
+
+def trevisan_seed_length(n1: int, m: int, log2_eps: float) -> tuple[int, int, int]:
+    t, a, d = _U64(0), _U64(0), _U64(0)
+    _check(lib().cm_trevisan_seed_length(n1, m, float(log2_eps), ctypes.byref(t), ctypes.byref(a),
+                                         ctypes.byref(d)), "cm_trevisan_seed_length")
+    return int(t.value), int(a.value), int(d.value)
+
+
+def plan_params(kind: int, model: int, adversary: int, n_raw: int, k1: float, log2_eps: float,
+                seed_rate: float = 1.0, adjust: int = ADJUST_UP) -> dict:
+    """Lengths for one extraction (cm_plan_params) as a dict."""
+    p = ParamPlan()
+    _check(lib().cm_plan_params(kind, model, adversary, n_raw, float(k1), float(seed_rate), float(log2_eps),
+                                adjust, ctypes.byref(p)), "cm_plan_params")
+    return dict(n1=int(p.n1), n2=int(p.n2), pad_input=int(p.pad_input), cut_input=int(p.cut_input),
+                k1=float(p.k1), k2=float(p.k2), m=int(p.m))
 
 
 def _stream_handle(stream) -> int:
