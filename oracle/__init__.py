@@ -19,6 +19,9 @@ QRNG examples); ``tests/test_params.py`` pins it to the paper's printed
 example arithmetic and re-derives each two-source and Markov-model bound from
 its base theorem.
 
+``oracle.von_neumann`` is the Von Neumann extractor of Alg. vn, pinned by
+``tests/test_von_neumann_oracle.py``.
+
 Parity status: every function here is pinned by ``tests/test_oracle.py``
 (brute force, closed forms, the paper's displayed matrices, the two-universality
 count of Thm. 2-univ, the rank lemmas, cross-definition identities) and
