@@ -238,6 +238,12 @@ def run_reference(args, world, rank):
 
     import oracle
     from paper_2402_09481_gb300 import inputs
+    if args.workload == "von_neumann":
+        run_reference_vn(args)
+        return
+    if args.workload not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle arm for the {args.workload} workload"}))
+        return
     wl = WORKLOADS[args.workload]
     kind, n, m = wl["kind"], wl["n"], wl["m"]
     xw = inputs.bernoulli_half(1, n)
@@ -265,6 +271,34 @@ def run_reference(args, world, rank):
         "data": "synthetic", "config": {"workload": wl["name"], "n": n, "m": m},
         "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
+        "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_vn(args):
+    """Von Neumann oracle on the host cores: each step filters a 2^26-bit chunk
+    of the 6.5e9-bit workload input."""
+    from paper_2402_09481_gb300 import inputs
+    n = int(os.environ.get("CM_VN_BITS", str(VN_BITS)))
+    sample_bits = 1 << 26
+    xw = inputs.bernoulli_half(30, sample_bits * 4)
+    for _ in range(args.warmup):
+        vn_reference_rate(xw, sample_bits * 4, 0.0)
+    times, outs = [], 0
+    for k in range(args.steps):
+        rate, done_in, secs = vn_reference_rate(xw, sample_bits * 4, 0.0)
+        times.append(secs)
+        outs += rate * secs
+    ms = 1e3 * sum(times) / len(times)
+    value = outs / sum(times) / 1e9
+    line = {
+        "impl": "reference", "metric": "extracted output Gbit/s", "value": value, "unit": "Gbit/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"Von Neumann: n = {n} i.i.d. Bernoulli(1/2) bits (QRNG example length)", "n": n},
+        "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
+                         "sample": "one 2^26-bit chunk of the same input per step (numpy, one thread)"},
         "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -653,6 +687,157 @@ def run_batched_b(args, world, rank, local):
         dist.destroy_process_group()
 
 
+VN_BITS = 6_500_000_000   # the input length of the paper's QRNG example
+
+
+def vn_reference_rate(xw, n, budget_s, chunk_bits=1 << 26):
+    """The Von Neumann oracle as it stands on consecutive chunks of the input,
+    for about budget_s seconds: (output bits per second, input bits done, s)."""
+    import oracle.von_neumann as ovn
+    from oracle.extractors import unpack_bits
+    done_in, done_out, secs, off = 0, 0, 0.0, 0
+    while done_in == 0 or secs < budget_s:
+        w0 = (off // 64) % max(1, (n - chunk_bits) // 64)
+        t0 = time.perf_counter()
+        out = ovn.von_neumann(unpack_bits(xw[w0:w0 + chunk_bits // 64], chunk_bits))
+        secs += time.perf_counter() - t0
+        done_in += chunk_bits
+        done_out += out.size
+        off += chunk_bits
+    return done_out / secs, done_in, secs
+
+
+def run_von_neumann(args, world, rank, local):
+    """Von Neumann extraction (Alg. vn) of n = 6.5e9 i.i.d. Bernoulli(1/2) bits
+    (the input length of the paper's QRNG example): one step = one
+    cm_von_neumann call (pair filter + order-keeping compaction, one kernel)."""
+    import numpy as np
+    import torch
+
+    from paper_2402_09481_gb300 import build, inputs, native
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    n = int(os.environ.get("CM_VN_BITS", str(VN_BITS)))
+    xw = inputs.bernoulli_half(30 + 1000 * rank, n)
+    xd = torch.from_numpy(xw.view(np.int64)).cuda()
+    zd = torch.empty(native.words(n // 2), dtype=torch.int64, device="cuda")
+    md = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ctx = native.Context(local)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.von_neumann(xd, n, zd, md)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    m = int(md.item())
+    import oracle.von_neumann as ovn
+    m_oracle = int(ovn.pair_counts_per_word(xw, n).sum()) if rank == 0 else m
+    assert m == m_oracle, (m, m_oracle)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.25)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    tw0 = time.time()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev:
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    tw1 = time.time()
+    if dist:
+        dist.barrier()
+    time.sleep(0.25)
+    sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * m / (ms_per_step * 1e-3) / 1e9
+    # kernel time from the library's launch events (same stream)
+    ctx.profile_enable(True)
+    ctx.profile_read(reset=True)
+    for _ in range(args.steps):
+        step()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile_enable(False)
+    words = (2 * (n // 2) + 63) // 64
+    out_bytes = 8 * ((m + 63) // 64)
+    alg = {"k_vn_count": 8 * words, "k_vn_write": 8 * words + out_bytes}
+    kern = {}
+    for name in ("k_vn_count", "k_vn_write"):
+        c_, t_ = prof[name]
+        kern[name] = {"launches": c_, "avg_ms": t_ / c_}
+    tot = sum(k["avg_ms"] for k in kern.values())
+    for k in kern.values():
+        k["share"] = k["avg_ms"] / tot
+    top = max(kern, key=lambda k: kern[k]["avg_ms"])
+    per_launch = kern[top]["avg_ms"]
+    hbm_peak, peak_src = measured_peaks()
+    achieved = alg[top] / (per_launch * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "peak_source": peak_src,
+            "traffic": ncu_traffic(top, "von_neumann"), "algorithmic_bytes_per_launch": alg[top],
+            "avg_launch_ms": per_launch}
+    # the whole path against one read of the input and one write of the output
+    single = 8 * words + out_bytes
+    path = {"algorithmic_bytes": single, "achieved_gbs": single / (ms_per_step * 1e-3) / 1e9,
+            "frac_of_measured_hbm": single / (ms_per_step * 1e-3) / 1e9 / hbm_peak,
+            "note": "two passes over the input: the count pass and the write pass"}
+    # end to end through the host-buffer entry point
+    xh = torch.from_numpy(xw.view(np.int64)).pin_memory()
+    zh = torch.empty(native.words(n // 2), dtype=torch.int64).pin_memory()
+    e2e_ms = []
+    for _ in range(max(3, min(args.steps, 10))):
+        t0 = time.perf_counter()
+        s_, m_e = ctx.von_neumann_host(xh, n, zh)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        assert s_ == native.CM_OK and m_e == m
+    e2e_mean = sum(e2e_ms) / len(e2e_ms)
+    e2e = {"value": world * m / (e2e_mean * 1e-3) / 1e9, "unit": "Gbit/s",
+           "h2d_bytes_per_step": 8 * ((n + 63) // 64), "d2h_bytes_per_step": 8 + 8 * ((m + 63) // 64),
+           "ms_per_step": e2e_mean}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, done_in, secs = vn_reference_rate(xw, n, 10.0)
+        cpu = {"value": rate / 1e9, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
+               "sample": f"{done_in} input bits in 2^26-bit chunks of the same input in {secs:.1f} s "
+                         "(array form of the pair filter, numpy, one thread)"}
+    if rank == 0:
+        line = {
+            "metric": "extracted output Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 (bit words)",
+            "data": "synthetic",
+            "config": {"workload": f"Von Neumann: n = {n} i.i.d. Bernoulli(1/2) bits (QRNG example length)",
+                       "n": n, "m": m, "input_gbit_per_s": world * n / (ms_per_step * 1e-3) / 1e9,
+                       "l2": "input (%d MB) larger than L2" % (8 * words >> 20),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "latency_ms": {"p50": statistics.median(step_ms), "p99": max(step_ms)},
+            "roofline": roof, "path_roofline": path, "kernels": kern, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": sampler.summary(tw0, tw1), "gpu_launches": 2 * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def served_trace(count, rate, seed_stream=3):
     """Poisson arrivals at `rate`/s; kinds Toeplitz / Circulant / Dodis et al.
     50/25/25; n = floor(2^U), U ~ U[12, 28), snapped to the next valid N_A
@@ -790,7 +975,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="cm", choices=["cm", "reference"])
-    ap.add_argument("--workload", default="circulant", choices=sorted(WORKLOADS) + ["batched_a", "batched_b", "served"])
+    ap.add_argument("--workload", default="circulant", choices=sorted(WORKLOADS) + ["batched_a", "batched_b", "served", "von_neumann"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -806,6 +991,9 @@ def main():
         return
     if args.workload == "served":
         run_served(args, world, rank, local)
+        return
+    if args.workload == "von_neumann":
+        run_von_neumann(args, world, rank, local)
         return
 
     import numpy as np

@@ -56,6 +56,52 @@ def von_neumann_packed(words, n: int) -> tuple[np.ndarray, int]:
     return pack_bits(out), int(out.size)
 
 
+def pair_counts_per_word(words, n: int) -> np.ndarray:
+    """Number of unequal pairs (x_{2j}, x_{2j+1}) that fall in each 64-bit word
+    of the packed input (pairs never straddle a word; pairs past floor(n/2)
+    do not count).  Written with word-wide bit operations so that inputs of
+    billions of bits fit in memory: bit 2j of w ^ (w >> 1) is x_{2j} xor
+    x_{2j+1}."""
+    k = n // 2
+    nw = (2 * k + 63) // 64
+    w = np.asarray(words, dtype=np.uint64)[:nw].copy()
+    if nw:
+        vb = 2 * k - 64 * (nw - 1)
+        if vb < 64:
+            w[-1] &= np.uint64((1 << vb) - 1)
+    d = (w ^ (w >> np.uint64(1))) & np.uint64(0x5555555555555555)
+    if hasattr(np, "bitwise_count"):
+        return np.bitwise_count(d).astype(np.int64)
+    return np.array([bin(int(v)).count("1") for v in d], dtype=np.int64)
+
+
+def output_bits_at(words, n: int, positions) -> tuple[np.ndarray, int]:
+    """Output bits at the given output positions, and the output length m,
+    without forming the whole output: the cumulative pair counts locate the
+    word holding each position, and that word's pairs are filtered by the
+    definition.  Positions must be < m."""
+    cnt = pair_counts_per_word(words, n)
+    cum = np.cumsum(cnt)
+    m = int(cum[-1]) if cum.size else 0
+    w = np.asarray(words, dtype=np.uint64)
+    out = np.zeros(len(positions), dtype=np.uint8)
+    for i, pos in enumerate(positions):
+        pos = int(pos)
+        if not 0 <= pos < m:
+            raise IndexError(f"output position {pos} outside [0, {m})")
+        wi = int(np.searchsorted(cum, pos, side="right"))
+        before = int(cum[wi - 1]) if wi else 0
+        npairs = min(32, n // 2 - 32 * wi)
+        word = int(w[wi])
+        local = []
+        for j in range(npairs):
+            a, b = (word >> (2 * j)) & 1, (word >> (2 * j + 1)) & 1
+            if a != b:
+                local.append(a)
+        out[i] = local[pos - before]
+    return out, m
+
+
 def von_neumann_count(words, n: int) -> int:
     """Output length only (number of unequal pairs); 0 is allowed here."""
     b = unpack_bits(words, n)

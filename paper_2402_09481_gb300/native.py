@@ -67,6 +67,9 @@ PROTOTYPES = {
                                      ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
     "cm_plan_params": (_I, [_I, _I, _I, _U64, ctypes.c_double, ctypes.c_double, ctypes.c_double, _I, _P]),
     "cm_closest_na_prime": (_U64, [_U64]),
+    "cm_von_neumann": (_I, [_P, _P, _U64, _P, _P, _P]),
+    "cm_von_neumann_host": (_I, [_P, _P, _U64, _P, ctypes.POINTER(_U64), _P]),
+    "cm_von_neumann_scratch_bytes": (_U64, [_U64]),
 }
 
 TREVISAN = 3
@@ -209,6 +212,10 @@ def prev_na_prime(n: int) -> int:
     return int(lib().cm_prev_na_prime(n))
 
 
+def von_neumann_scratch_bytes(n: int) -> int:
+    return int(lib().cm_von_neumann_scratch_bytes(n))
+
+
 def closest_na_prime(n: int) -> int:
     return int(lib().cm_closest_na_prime(n))
 
@@ -321,6 +328,33 @@ class Context:
         _check(self._L.cm_dodis(self._h, px, py, n, m, z.data_ptr(), _stream_handle(stream)),
                "cm_dodis")
         return z
+
+    def von_neumann(self, x, n: int, z=None, m_out=None, stream=None):
+        """Von Neumann extraction on the device (cm_von_neumann).  Returns
+        (z, m_out): z has room for the longest output, m_out is a one-element
+        device tensor that receives the output length."""
+        import torch
+        px = _dev_words(x, n, "x")
+        if z is None:
+            z = torch.empty(max(1, words(n // 2)), dtype=torch.int64, device=x.device)
+        pz = _dev_words(z, n // 2, "z")
+        if m_out is None:
+            m_out = torch.zeros(1, dtype=torch.int64, device=x.device)
+        pm = _dev_words(m_out, 64, "m_out")
+        _check(self._L.cm_von_neumann(self._h, px, n, pz, pm, _stream_handle(stream)), "cm_von_neumann")
+        return z, m_out
+
+    def von_neumann_host(self, x, n: int, z, stream=None) -> tuple[int, int]:
+        """End-to-end Von Neumann on host tensors; returns (cm_status, m)."""
+        for t, nb, nm in ((x, n, "x"), (z, n // 2, "z")):
+            if t.is_cuda or t.numel() < words(nb) or t.element_size() != 8 or not t.is_contiguous():
+                raise ValueError(f"{nm} must be a contiguous host tensor of >= {words(nb)} words")
+        m = _U64(0)
+        s = self._L.cm_von_neumann_host(self._h, x.data_ptr(), n, z.data_ptr(), ctypes.byref(m),
+                                        _stream_handle(stream))
+        if s not in (CM_OK, CM_EPRECOND):
+            raise CMError(s, "cm_von_neumann_host")
+        return int(s), int(m.value)
 
     def extract_host(self, kind: int, x, n: int, y, m: int, z, stream=None) -> int:
         """End-to-end call on host buffers (torch CPU tensors, ideally pinned):

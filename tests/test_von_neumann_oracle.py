@@ -79,3 +79,21 @@ def test_packed_matches_unpacked():
         assert m == want.size
         assert (words == pack_bits(want)).all()
         assert vn.von_neumann_count(pack_bits(b), n) == m
+
+
+def test_word_counts_and_sampled_bits_match_full_output():
+    rng = np.random.default_rng(9)
+    for n, p in ((1, 0.5), (2, 0.5), (65, 0.5), (1000, 0.1), (4097, 0.93), (20001, 0.5)):
+        b = (rng.random(n) < p).astype(np.uint8)
+        words = pack_bits(b)
+        k = n // 2
+        per_pair = (b[0:2 * k:2] != b[1:2 * k:2]).astype(np.int64)
+        per_word = np.add.reduceat(per_pair, np.arange(0, k, 32)) if k else np.zeros(0, np.int64)
+        assert vn.pair_counts_per_word(words, n).tolist() == per_word.tolist()
+        m = int(per_pair.sum())
+        if m == 0:
+            continue
+        full = vn.von_neumann(b)
+        pos = rng.integers(0, m, 50)
+        got, mm = vn.output_bits_at(words, n, pos)
+        assert mm == m and got.tolist() == full[pos].tolist()
