@@ -778,9 +778,9 @@ def run_von_neumann(args, world, rank, local):
     ctx.profile_enable(False)
     words = (2 * (n // 2) + 63) // 64
     out_bytes = 8 * ((m + 63) // 64)
-    alg = {"k_vn_count": 8 * words, "k_vn_write": 8 * words + out_bytes}
+    alg = {"k_vn_count": 8 * words, "k_vn_zero": None, "k_vn_write": 8 * words + out_bytes}
     kern = {}
-    for name in ("k_vn_count", "k_vn_write"):
+    for name in ("k_vn_count", "k_vn_zero", "k_vn_write"):
         c_, t_ = prof[name]
         kern[name] = {"launches": c_, "avg_ms": t_ / c_}
     tot = sum(k["avg_ms"] for k in kern.values())
@@ -830,7 +830,7 @@ def run_von_neumann(args, world, rank, local):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "latency_ms": {"p50": statistics.median(step_ms), "p99": max(step_ms)},
             "roofline": roof, "path_roofline": path, "kernels": kern, "e2e": e2e, "cpu_baseline": cpu,
-            "clocks": sampler.summary(tw0, tw1), "gpu_launches": 2 * args.steps,
+            "clocks": sampler.summary(tw0, tw1), "gpu_launches": 3 * args.steps,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

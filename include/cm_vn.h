@@ -25,15 +25,16 @@ extern "C" {
 
 /*
  * Von Neumann extraction of the n-bit string x into z on the device: a pair
- * filter and an order-keeping bit compaction, as two kernels (per-tile counts
- * and their scan, then compression and write-out at the scanned offsets).
+ * filter and an order-keeping bit compaction, as three kernels (per-tile counts
+ * and their scan, zeroing of the output words that tiles share, compression
+ * and write-out at the scanned offsets).
  *
  * x: device, ceil(n/64) words, 16-byte aligned.  z: device, 8-byte aligned,
  * room for ceil(floor(n/2)/64) words (the most the output can take).  m_out:
  * device pointer to one uint64_t that receives m.  On return of the stream
  * work z holds the m output bits in words 0 .. ceil(m/64) - 1, the bits past m
  * in the last of them are 0, and later words of z are not written.  The call
- * is asynchronous on `stream`; scratch (256 bytes + 12 bytes per 4096 input
+ * is asynchronous on `stream`; scratch (64.25 KiB + 12 bytes per 4096 input
  * words) comes from the context pool.
  *
  * Errors: CM_EINVAL for a NULL pointer, n < 2 (no pair), a misaligned pointer

@@ -1,16 +1,18 @@
 // Von Neumann extractor (Section "Von Neumann", Alg. vn): pair filter and
 // order-keeping bit compaction on the GPU.
 //
-// The input is cut into tiles of 4096 words (32 KiB).  Two kernels, with no
+// The input is cut into tiles of 4096 words (32 KiB).  Three kernels, with no
 // waiting between CTAs:
 //
 //   k_vn_count  reads each tile once and counts its unequal pairs (a popcount
-//               of the pair-difference mask per word), 4 CTAs per SM striding
-//               over the tiles.  The CTA that finishes last (a done-counter
-//               taken after a memory fence, so every other CTA's counts are
-//               visible to it) scans the counts into each tile's output offset,
-//               writes m, and zeroes the output words that two or more tiles
-//               share (a tile's first and last word when only partly its own).
+//               of the pair-difference mask per word).  Each CTA (4 per SM)
+//               takes a chunk of consecutive tiles and records each tile's
+//               offset inside the chunk; the CTA that finishes last (a
+//               done-counter taken after a memory fence, so every other CTA's
+//               sums are visible to it) turns the chunk sums into chunk
+//               offsets and writes m.
+//   k_vn_zero   zeroes the output words that two or more tiles share (a tile's
+//               first and last word when only partly its own), a thread a tile.
 //   k_vn_write  re-reads each tile, compresses every word with a 64 KiB
 //               shared-memory table (one byte per 16-bit chunk: the outputs of
 //               those 8 pairs, in order), packs the bits into a shared staging
@@ -40,6 +42,7 @@ constexpr int kVnWpt = kVnTileWords / kWriteThreads;
 constexpr int kVnStageWords = kVnTileWords / 2 + 2;     // <= 32 bits a word, + offset word, + guard
 constexpr size_t kWriteSmem = 65536 + 8 * (size_t)kVnStageWords + 2 * 256 + 4 * 64;
 constexpr size_t kVnHeaderBytes = 256;                  // done counter
+constexpr uint32_t kMaxChunks = 4096;                   // count CTAs (4 per SM) at most
 
 // This thread's CNT consecutive words starting at word w0: zeros past the
 // input, the last word masked to whole pairs (pairs past floor(n/2) count as
@@ -71,47 +74,87 @@ __device__ __forceinline__ uint32_t pair_count(uint64_t w) {
     return __popc((uint32_t)d) + __popc((uint32_t)(d >> 32));
 }
 
-__global__ void __launch_bounds__(kCountThreads)
-k_vn_count(const uint64_t *__restrict__ x, uint64_t words, uint64_t lastmask, uint32_t ntiles,
-           uint32_t *__restrict__ cnt, uint64_t *__restrict__ off, uint64_t *__restrict__ z,
-           uint64_t *__restrict__ m_out, uint32_t *__restrict__ done, uint32_t *__restrict__ status) {
+// Output offset of tile t: the exclusive sum over earlier chunks plus the
+// offset inside its chunk of `per` consecutive tiles.
+__device__ __forceinline__ uint64_t tile_offset(const uint64_t *__restrict__ base, const uint64_t *__restrict__ loff,
+                                                uint32_t per, uint32_t t) {
+    return __ldg(base + t / per) + __ldg(loff + t);
+}
+
+__global__ void __launch_bounds__(kCountThreads, 4)
+k_vn_count(const uint64_t *__restrict__ x, uint64_t words, uint64_t lastmask, uint32_t ntiles, uint32_t per,
+           uint32_t *__restrict__ cnt, uint64_t *__restrict__ loff, uint64_t *__restrict__ csum,
+           uint64_t *__restrict__ base, uint64_t *__restrict__ m_out, uint32_t *__restrict__ done,
+           uint32_t *__restrict__ status) {
     __shared__ uint32_t red[2][kCountThreads / 32];
     __shared__ uint64_t wex[kCountThreads / 32];
     __shared__ uint32_t last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // ---- count every tile t = blockIdx.x, + gridDim.x, ... ----
+    // ---- count the chunk of tiles [blockIdx.x * per, + per) in order ----
+    // Word order inside a tile does not matter for a count, so the loads are
+    // fully coalesced: thread i takes 16-byte chunks i, i + 512, ... of the tile.
+    const uint32_t t0 = blockIdx.x * per;
+    const uint32_t t1 = min(ntiles, t0 + per);
+    uint64_t running = 0;  // thread 0: output bits of the chunk so far
     int par = 0;
-    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x, par ^= 1) {
+    for (uint32_t t = t0; t < t1; ++t, par ^= 1) {
+        const uint64_t tb = (uint64_t)t * kVnTileWords;
         uint64_t wv[kCountWpt];
-        vn_load<kCountWpt>(x, words, lastmask, (uint64_t)t * kVnTileWords + (uint64_t)kCountWpt * tid, wv);
+        if (tb + kVnTileWords <= words) {
+            const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(x + tb);
+#pragma unroll
+            for (int i = 0; i < kCountWpt / 2; ++i) {
+                const ulonglong2 v = __ldg(p + i * kCountThreads + tid);
+                wv[2 * i] = v.x;
+                wv[2 * i + 1] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kCountWpt / 2; ++i) {
+                const uint64_t w = tb + 2 * ((uint64_t)i * kCountThreads + tid);
+                wv[2 * i] = w < words ? __ldg(x + w) : 0ull;
+                wv[2 * i + 1] = w + 1 < words ? __ldg(x + w + 1) : 0ull;
+            }
+        }
+        if (tb + kVnTileWords >= words) {  // the tile holding the last word
+#pragma unroll
+            for (int i = 0; i < kCountWpt / 2; ++i) {
+                const uint64_t w = tb + 2 * ((uint64_t)i * kCountThreads + tid);
+                if (w == words - 1) wv[2 * i] &= lastmask;
+                if (w + 1 == words - 1) wv[2 * i + 1] &= lastmask;
+            }
+        }
         uint32_t c = 0;
 #pragma unroll
         for (int i = 0; i < kCountWpt; ++i) c += pair_count(wv[i]);
         c = __reduce_add_sync(0xffffffffu, c);
         if (lane == 0) red[par][warp] = c;  // alternate buffers: one barrier per tile
         __syncthreads();
-        if (warp == 0) {
-            c = __reduce_add_sync(0xffffffffu, lane < kCountThreads / 32 ? red[par][lane] : 0u);
-            if (lane == 0) cnt[t] = c;
+        if (tid == 0) {
+            uint32_t s = 0;
+#pragma unroll
+            for (int w = 0; w < kCountThreads / 32; ++w) s += red[par][w];
+            cnt[t] = s;
+            loff[t] = running;
+            running += s;
         }
     }
     if (tid == 0) {
+        csum[blockIdx.x] = running;
         __threadfence();
         last = atomicAdd(done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
 
-    // ---- the CTA that finished last: offsets, m, zeroed shared words ----
+    // ---- the CTA that finished last: exclusive sums over the chunks, and m ----
     __threadfence();
-    // thread i scans tiles [i*per, (i+1)*per): all loads first, then the sums
-    const uint32_t per = (ntiles + kCountThreads - 1) / kCountThreads;
-    const uint32_t b0 = tid * per;
+    const uint32_t nch = gridDim.x;
+    const uint32_t q = (nch + kCountThreads - 1) / kCountThreads;  // chunks a thread
     uint64_t mine = 0;
-#pragma unroll 8
-    for (uint32_t j = 0; j < per; ++j) {
-        const uint32_t i = b0 + j;
-        if (i < ntiles) mine += __ldcg(cnt + i);
+    for (uint32_t j = 0; j < q; ++j) {
+        const uint32_t i = tid * q + j;
+        if (i < nch) mine += __ldcg(csum + i);
     }
     uint64_t inc = mine;
 #pragma unroll
@@ -138,25 +181,34 @@ k_vn_count(const uint64_t *__restrict__ x, uint64_t words, uint64_t lastmask, ui
     }
     __syncthreads();
     uint64_t O = wex[warp] + (inc - mine);
-#pragma unroll 4
-    for (uint32_t j = 0; j < per; ++j) {
-        const uint32_t i = b0 + j;
-        if (i >= ntiles) break;
-        const uint32_t c = __ldcg(cnt + i);
-        off[i] = O;
-        if (c) {
-            const uint64_t f = O >> 6, l = (O + c - 1) >> 6;
-            const bool head_part = (O & 63) != 0, tail_part = ((O + c) & 63) != 0;
-            if (head_part || (f == l && tail_part)) z[f] = 0;  // first word only partly this tile's
-            if (l != f && tail_part) z[l] = 0;                  // last word only partly this tile's
-        }
-        O += c;
+    for (uint32_t j = 0; j < q; ++j) {
+        const uint32_t i = tid * q + j;
+        if (i >= nch) break;
+        base[i] = O;
+        O += __ldcg(csum + i);
     }
 }
 
+// Zero the output words two or more tiles share (a tile's first and last word
+// when only partly its own); one thread per tile.
+__global__ void k_vn_zero(uint32_t ntiles, uint32_t per, const uint32_t *__restrict__ cnt,
+                          const uint64_t *__restrict__ loff, const uint64_t *__restrict__ base,
+                          uint64_t *__restrict__ z) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const uint32_t c = __ldg(cnt + t);
+    if (!c) return;
+    const uint64_t O = tile_offset(base, loff, per, t);
+    const uint64_t f = O >> 6, l = (O + c - 1) >> 6;
+    const bool head_part = (O & 63) != 0, tail_part = ((O + c) & 63) != 0;
+    if (head_part || (f == l && tail_part)) z[f] = 0;
+    if (l != f && tail_part) z[l] = 0;
+}
+
 __global__ void __launch_bounds__(kWriteThreads, 2)
-k_vn_write(const uint64_t *__restrict__ x, uint64_t words, uint64_t lastmask, uint32_t ntiles,
-           const uint32_t *__restrict__ cnt, const uint64_t *__restrict__ off, uint64_t *__restrict__ z) {
+k_vn_write(const uint64_t *__restrict__ x, uint64_t words, uint64_t lastmask, uint32_t ntiles, uint32_t per,
+           const uint32_t *__restrict__ cnt, const uint64_t *__restrict__ loff, const uint64_t *__restrict__ base,
+           uint64_t *__restrict__ z) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint8_t *lut = smem;                                                     // 65536 entries
     uint64_t *stage = reinterpret_cast<uint64_t *>(smem + 65536);             // kVnStageWords
@@ -193,15 +245,26 @@ k_vn_write(const uint64_t *__restrict__ x, uint64_t words, uint64_t lastmask, ui
     if (t < ntiles)
         vn_load<kVnWpt>(x, words, lastmask, (uint64_t)t * kVnTileWords + (uint64_t)tid * kVnWpt, cur);
     while (t < ntiles) {
-        const uint64_t O = __ldg(off + t);
+        const uint64_t O = tile_offset(base, loff, per, t);
         const uint32_t C = __ldg(cnt + t);
         const uint32_t tn = t + gridDim.x;
         const uint32_t s0 = (uint32_t)(O & 63);
         if (C != 0) {
-            // ---- this thread's offset in the tile's output ----
-            uint32_t total = 0;
+            // ---- compress each word (<= 32 bits, pair order) and count ----
+            uint32_t ov[kVnWpt], oc[kVnWpt], total = 0;
 #pragma unroll
-            for (int i = 0; i < kVnWpt; ++i) total += pair_count(cur[i]);
+            for (int i = 0; i < kVnWpt; ++i) {
+                const uint64_t w = cur[i];
+                const uint64_t d = (w ^ (w >> 1)) & 0x5555555555555555ull;  // bit 2j: pair j differs
+                const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
+                const uint32_t dl = (uint32_t)d, dh = (uint32_t)(d >> 32);
+                const uint32_t c0 = __popc(dl & 0xFFFFu), c01 = __popc(dl), c2 = __popc(dh & 0xFFFFu);
+                oc[i] = c01 + __popc(dh);
+                ov[i] = (uint32_t)lut[lo & 0xFFFFu] | ((uint32_t)lut[lo >> 16] << c0) |
+                        ((uint32_t)lut[hi & 0xFFFFu] << c01) | ((uint32_t)lut[hi >> 16] << (c01 + c2));
+                total += oc[i];
+            }
+            // ---- this thread's offset in the tile's output ----
             uint32_t inc = total;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -222,22 +285,14 @@ k_vn_write(const uint64_t *__restrict__ x, uint64_t words, uint64_t lastmask, ui
             }
             __syncthreads();
 
-            // ---- compress and pack; staging word i is output word (O >> 6) + i ----
+            // ---- pack; staging word i is output word (O >> 6) + i ----
             const uint32_t start = s0 + wsum[32 + warp] + (inc - total);
             uint64_t acc = 0;
             uint32_t pos = start & 63, k = start >> 6;
 #pragma unroll
             for (int i = 0; i < kVnWpt; ++i) {
-                const uint64_t w = cur[i];
-                const uint64_t d = (w ^ (w >> 1)) & 0x5555555555555555ull;
-                const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
-                const uint32_t dl = (uint32_t)d, dh = (uint32_t)(d >> 32);
-                const uint32_t c0 = __popc(dl & 0xFFFFu), c01 = __popc(dl), c2 = __popc(dh & 0xFFFFu);
-                const uint32_t c = c01 + __popc(dh);
+                const uint32_t c = oc[i], v = ov[i];
                 if (c == 0) continue;
-                const uint32_t v = (uint32_t)lut[lo & 0xFFFFu] | ((uint32_t)lut[lo >> 16] << c0) |
-                                   ((uint32_t)lut[hi & 0xFFFFu] << c01) |
-                                   ((uint32_t)lut[hi >> 16] << (c01 + c2));
                 acc |= (uint64_t)v << pos;
                 if (pos + c >= 64) {  // pos >= 32 here
                     atomicOr(reinterpret_cast<unsigned long long *>(stage + k), (unsigned long long)acc);
@@ -297,21 +352,29 @@ static cm_status vn_enqueue(cm_ctx *ctx, const uint64_t *x, uint64_t n, uint64_t
     const uint32_t tiles = vn_tiles(n);
     const uint64_t vb = 2 * (n / 2) - 64 * (words - 1);  // valid bits of the last word, 1..64
     const uint64_t lastmask = vb >= 64 ? ~0ull : ((1ull << vb) - 1);
+    const uint32_t cgrid = tiles < (uint32_t)(4 * ctx->nsm) ? tiles : (uint32_t)(4 * ctx->nsm);
+    const uint32_t per = (tiles + cgrid - 1) / cgrid;
+    const uint32_t nch = (tiles + per - 1) / per;  // chunks with at least one tile
     uint8_t *b = static_cast<uint8_t *>(scratch);
     uint32_t *done = reinterpret_cast<uint32_t *>(b);
-    uint64_t *off = reinterpret_cast<uint64_t *>(b + kVnHeaderBytes);
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(off + tiles);
+    uint64_t *loff = reinterpret_cast<uint64_t *>(b + kVnHeaderBytes);
+    uint64_t *csum = loff + tiles;
+    uint64_t *base = csum + kMaxChunks;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(base + kMaxChunks);
     if (cudaMemsetAsync(done, 0, sizeof(uint32_t), st) != cudaSuccess) return CM_EDEVICE;
     {
         ProfScope ps(ctx, "k_vn_count", st);
-        const uint32_t cgrid = tiles < (uint32_t)(4 * ctx->nsm) ? tiles : (uint32_t)(4 * ctx->nsm);
-        k_vn_count<<<cgrid, kCountThreads, 0, st>>>(x, words, lastmask, tiles, cnt, off, z, m_out, done,
-                                                    ctx->d_status);
+        k_vn_count<<<nch, kCountThreads, 0, st>>>(x, words, lastmask, tiles, per, cnt, loff, csum, base, m_out,
+                                                  done, ctx->d_status);
+    }
+    {
+        ProfScope ps(ctx, "k_vn_zero", st);
+        k_vn_zero<<<(tiles + 255) / 256, 256, 0, st>>>(tiles, per, cnt, loff, base, z);
     }
     const uint32_t grid = tiles < (uint32_t)(2 * ctx->nsm) ? tiles : (uint32_t)(2 * ctx->nsm);
     {
         ProfScope ps(ctx, "k_vn_write", st);
-        k_vn_write<<<grid, kWriteThreads, kWriteSmem, st>>>(x, words, lastmask, tiles, cnt, off, z);
+        k_vn_write<<<grid, kWriteThreads, kWriteSmem, st>>>(x, words, lastmask, tiles, per, cnt, loff, base, z);
     }
     return cudaGetLastError() == cudaSuccess ? CM_OK : CM_EDEVICE;
 }
@@ -320,7 +383,7 @@ static cm_status vn_enqueue(cm_ctx *ctx, const uint64_t *x, uint64_t n, uint64_t
 
 extern "C" uint64_t cm_von_neumann_scratch_bytes(uint64_t n) {
     if (n < 2) return 0;
-    return cm::kVnHeaderBytes + 12ull * cm::vn_tiles(n);
+    return cm::kVnHeaderBytes + 12ull * cm::vn_tiles(n) + 16ull * cm::kMaxChunks;
 }
 
 extern "C" cm_status cm_von_neumann(cm_ctx *ctx, const uint64_t *x, uint64_t n, uint64_t *z, uint64_t *m_out,

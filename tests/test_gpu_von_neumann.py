@@ -123,7 +123,7 @@ def test_argument_checks(cm_ctx):
     assert L.cm_von_neumann(h, x.data_ptr(), 1 << 46, z.data_ptr(), m.data_ptr(), None) == native.CM_EINVAL
     assert L.cm_von_neumann(None, x.data_ptr(), 100, z.data_ptr(), m.data_ptr(), None) == native.CM_EINVAL
     assert native.lib().cm_von_neumann_scratch_bytes(1) == 0
-    assert native.lib().cm_von_neumann_scratch_bytes(TILE_BITS * 3) == 256 + 12 * 3
+    assert native.lib().cm_von_neumann_scratch_bytes(TILE_BITS * 3) == 256 + 12 * 3 + 16 * 4096
 
 
 def test_two_calls_in_a_row_and_streams(cm_ctx):
