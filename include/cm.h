@@ -62,12 +62,17 @@ typedef enum { CM_TOEPLITZ = 0, CM_CIRCULANT = 1, CM_DODIS = 2 } cm_kind;
 
 typedef struct {
     uint64_t hbm_budget_bytes; /* cap on scratch held at once; 0 = 80% of free HBM */
-    uint32_t reserved[8];
+    /* log2 of the longest transform one product may use, 8..32; 0 = 32.  A
+     * single extraction whose K + m - 1 is longer runs as several products
+     * (see cm_toeplitz); lowering it trades transforms for scratch. */
+    uint32_t max_transform_lg;
+    uint32_t reserved[7];
 } cm_options;
 
 /* Create a context on CUDA device `device`: root tables resident in HBM, a
  * scratch memory pool.  opt may be NULL.  Returns CM_EDEVICE if the device is
- * unusable, CM_EINVAL if out is NULL. */
+ * unusable, CM_EINVAL if out is NULL or opt->max_transform_lg is outside
+ * 8..32 (and not 0). */
 cm_status cm_create(cm_ctx **out, int device, const cm_options *opt);
 
 /* Synchronize the device and free everything the context owns. */
@@ -81,8 +86,17 @@ const char *cm_status_str(int status);
  *   z = toep(y) x over GF(2), toep(y)[i][j] = y[(i - j) mod (n + m - 1)],
  *   i < m, j < n.
  * x: n bits (ceil(n/64) words).  y: n + m - 1 bits.  z: m bits (ceil(m/64)
- * words, written).  Requires n >= 1, m >= 1, n + m - 1 <= 2^32 (the
- * Goldilocks transform length limit).  CM_EINVAL otherwise.
+ * words, written).  Requires 1 <= n, m <= 2^40 (the input lengths the paper's
+ * software accepts, Section "Introduction").  CM_EINVAL otherwise.
+ *
+ * Lengths (all three extractors): the product is one transform when
+ * K + m - 1 <= 2^32 (the Goldilocks limit; K = n, n + 1, n for Toeplitz,
+ * Circulant, Dodis et al.) or the context's lower max_transform_lg.  Longer
+ * products are split: over input blocks (GF(2)-linearity: the output is the
+ * XOR of the blocks' outputs) and, when m exceeds half the limit, over output
+ * blocks; each block is an ordinary middle product of transform length at
+ * most the limit, run in turn with the scratch of one block
+ * (cm_block_count).
  */
 cm_status cm_toeplitz(cm_ctx *ctx, const uint64_t *x, uint64_t n, const uint64_t *y, uint64_t m,
                       uint64_t *z, cm_stream stream);
@@ -92,8 +106,9 @@ cm_status cm_toeplitz(cm_ctx *ctx, const uint64_t *x, uint64_t n, const uint64_t
  *   x' = [x, 0],  z = (circ(x') y)_{0..m-1},  circ(c)[i][j] = c[(j - i) mod P].
  * n is the INPUT length n_1 = P - 1 (the paper's Def. ext-circ calls the prime
  * n); P = n + 1 must be prime with 2 as a primitive root.
- * x: n bits.  y: n + 1 bits.  z: m bits, 1 <= m <= n.  P + m - 1 <= 2^32.
- * CM_EINVAL otherwise.  x = 0 is allowed (output 0).
+ * x: n bits.  y: n + 1 bits.  z: m bits, 1 <= m <= n <= 2^40 (blocked
+ * beyond one transform as for cm_toeplitz).  CM_EINVAL otherwise.  x = 0 is
+ * allowed (output 0).
  */
 cm_status cm_circulant(cm_ctx *ctx, const uint64_t *x, uint64_t n, const uint64_t *y, uint64_t m,
                        uint64_t *z, cm_stream stream);
@@ -103,8 +118,8 @@ cm_status cm_circulant(cm_ctx *ctx, const uint64_t *x, uint64_t n, const uint64_
  * "Dodis (and Circulant) implementation":
  *   z_i = sum_j x[(j - i) mod n] y_j (mod 2),  i < m
  * (equivalently the first m entries of R(x) * y, R(x) = x_0, x_{n-1}, ..., x_1).
- * x, y: n bits each; n prime with 2 as a primitive root; 1 <= m <= n;
- * n + m - 1 <= 2^32.  CM_EINVAL otherwise.  If x is all-0 or all-1 the call
+ * x, y: n bits each; n prime with 2 as a primitive root; 1 <= m <= n <= 2^40
+ * (blocked beyond one transform as for cm_toeplitz).  CM_EINVAL otherwise.  If x is all-0 or all-1 the call
  * still returns CM_OK (the check runs on the device), z is zero-filled and
  * cm_device_status() reports CM_EPRECOND.
  */
@@ -372,16 +387,25 @@ uint64_t cm_next_na_prime(uint64_t n);
 /* Largest member of N_A <= n (0 if n < 3). */
 uint64_t cm_prev_na_prime(uint64_t n);
 
-/* Transform length L the library uses for (kind, n, m): the smallest power of
- * two >= K + m - 1 with K = n (Toeplitz), n + 1 (Circulant), n (Dodis); 0 if
- * the arguments are invalid for that kind. */
+/* Transform length L the library uses for (kind, n, m) with the default
+ * limit: the smallest power of two >= K + m - 1 with K = n (Toeplitz), n + 1
+ * (Circulant), n (Dodis); for a blocked product the longest block's; 0 if the
+ * arguments are invalid for that kind. */
 uint64_t cm_ntt_length(int kind, uint64_t n, uint64_t m);
 
-/* Bytes of scratch one call of (kind, n, m) takes from the pool. */
+/* Bytes of scratch one call of (kind, n, m) takes from the pool (default
+ * limit). */
 uint64_t cm_scratch_bytes(int kind, uint64_t n, uint64_t m);
 
-/* Number of kernel launches one call of (kind, n, m) enqueues. */
+/* Number of kernel launches one call of (kind, n, m) enqueues (default
+ * limit). */
 uint32_t cm_launch_count(int kind, uint64_t n, uint64_t m);
+
+/* Number of middle products a call of (kind, n, m) runs when one transform
+ * may be at most 2^max_transform_lg long (0 = 32): 1 when K + m - 1 fits, else
+ * the input blocks times the output blocks; 0 if invalid (including a
+ * max_transform_lg outside 8..32 or more than 65536 products). */
+uint64_t cm_block_count(int kind, uint64_t n, uint64_t m, uint32_t max_transform_lg);
 
 #ifdef __cplusplus
 }

@@ -18,14 +18,15 @@ static int ceil_log2(uint64_t v) {
     return k;
 }
 
-bool make_plan(int kind, uint64_t n, uint64_t m, Plan *p) {
+// Operand maps of (kind, n, m) (lengths up to 2^40); false if invalid.
+static bool base_maps(int kind, uint64_t n, uint64_t m, Plan *p) {
     memset(p, 0, sizeof(*p));
     p->kind = kind;
     p->n = n;
     p->m = m;
     if (m == 0 || n == 0) return false;
-    // every length below is checked against 2^32 before any sum can overflow
-    if (n > (1ull << 32) || m > (1ull << 32)) return false;
+    // every length below is checked against 2^40 before any sum can overflow
+    if (n > kMaxBits || m > kMaxBits) return false;
     switch (kind) {
         case CM_TOEPLITZ: {
             const uint64_t N = n + m - 1;  // seed length
@@ -54,8 +55,12 @@ bool make_plan(int kind, uint64_t n, uint64_t m, Plan *p) {
         default:
             return false;
     }
-    const uint64_t need = p->K + m - 1;
-    if (need > (1ull << 32)) return false;
+    return true;
+}
+
+// Transform length, pass split, scratch and launch count for K + m - 1 <= 2^32.
+static void finish_plan(Plan *p) {
+    const uint64_t need = p->K + p->m - 1;
     p->lg = ceil_log2(need);
     if (p->lg < 1) p->lg = 1;
     p->L = 1ull << p->lg;
@@ -71,16 +76,69 @@ bool make_plan(int kind, uint64_t n, uint64_t m, Plan *p) {
         p->pass_lg[0] = (rest + 1) / 2;
         p->pass_lg[1] = rest / 2;
     }
-    const uint64_t flags = (kind == CM_DODIS) ? 256 : 0;
+    const uint64_t flags = (p->kind == CM_DODIS) ? 256 : 0;
     if (p->npass == 0) {
         p->scratch_bytes = flags;
         p->launches = 1;
     } else {
-        p->scratch_bytes = 2 * 8 * p->L + ((m + 255) & ~255ull) + flags;
+        p->scratch_bytes = 2 * 8 * p->L + ((p->m + 255) & ~255ull) + flags;
         // forward passes of both operands, middle, inverse passes, pack
         p->launches = 2 * p->npass + 1 + p->npass + 1;
     }
-    if (kind == CM_DODIS) p->launches += 1;  // precondition check
+    if (p->kind == CM_DODIS) p->launches += 1;  // precondition check
+}
+
+bool make_plan(int kind, uint64_t n, uint64_t m, Plan *p) {
+    if (!base_maps(kind, n, m, p)) return false;
+    if (p->K + m - 1 > (1ull << 32)) return false;
+    finish_plan(p);
+    return true;
+}
+
+// z_i = sum_{t<K} a_t b_{t+i} splits over input blocks t in [T0, T0 + kb)
+// (each a middle product of a[T0 .. T0 + kb) with b[T0 .. T0 + kb + m - 1),
+// the results XORed: parity of a sum is the XOR of the parities) and over
+// output blocks i in [I0, I0 + mb) (b shifted by I0).  In transform positions
+// u = K - 1 - t, input block [D, D + kb) of A is A shifted by D.
+bool make_blocks(int kind, uint64_t n, uint64_t m, int max_lg, std::vector<Block> *out) {
+    out->clear();
+    Plan b;
+    if (max_lg < 8 || max_lg > 32 || !base_maps(kind, n, m, &b)) return false;
+    const uint64_t Lmax = 1ull << max_lg;
+    if (b.K + m - 1 <= Lmax) {
+        finish_plan(&b);
+        out->push_back({b, 0, false});
+        return true;
+    }
+    const uint64_t Mb = m > Lmax / 2 ? Lmax / 2 : m;  // a multiple of 64 when it splits m
+    const uint64_t nout = (m + Mb - 1) / Mb;
+    const uint64_t kmax = Lmax - Mb + 1;
+    const uint64_t nin = (b.K + kmax - 1) / kmax;
+    if (nin * nout > kMaxBlocks) return false;
+    const uint64_t Kb = (b.K + nin - 1) / nin;
+    for (uint64_t r = 0; r < nout; ++r) {
+        const uint64_t I0 = r * Mb, mr = (m - I0 < Mb) ? m - I0 : Mb;
+        for (uint64_t j = 0; j < nin; ++j) {
+            const uint64_t D = j * Kb;
+            if (D >= b.K) break;
+            const uint64_t kb = (b.K - D < Kb) ? b.K - D : Kb;
+            const uint64_t T0 = b.K - D - kb;
+            Plan q = b;
+            q.m = mr;
+            q.K = kb;
+            if (b.amode == kIdentity) {  // A'_u = x_{D+u}: no wrap, u + D < K = srclen
+                q.amode = kModForward;
+                q.aoff = D;
+            } else {  // A'_u = src[aoff - D - u]
+                q.aoff = b.aoff - D;
+            }
+            q.alen = kb;
+            q.blen = kb + mr - 1;
+            q.boff = (b.boff + T0 + I0) % b.bsrclen;
+            finish_plan(&q);
+            out->push_back({q, I0 / 64, j != 0});
+        }
+    }
     return true;
 }
 
@@ -182,23 +240,56 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
     return cuda_status(launch_pack(par, p.m, z, pre, ctx->d_status, ctx->nsm, st));
 }
 
+static uint64_t words_of(uint64_t bits) { return (bits + 63) / 64; }
+
+// Scratch of a blocked run: the largest block's scratch, then (when blocks
+// accumulate) one output window of XOR temporary at *tmp_off.
+static uint64_t blocks_scratch(const std::vector<Block> &bl, uint64_t *tmp_off) {
+    uint64_t sc = 0, tmpw = 0;
+    for (const Block &b : bl) {
+        if (b.p.scratch_bytes > sc) sc = b.p.scratch_bytes;
+        if (b.accumulate && words_of(b.p.m) > tmpw) tmpw = words_of(b.p.m);
+    }
+    *tmp_off = (sc + 255) & ~255ull;
+    return tmpw ? *tmp_off + 8 * tmpw : sc;
+}
+
+// Enqueue every block of an extraction; scratch holds blocks_scratch() bytes.
+static cm_status enqueue_blocks(cm_ctx *ctx, const std::vector<Block> &bl, const uint64_t *x,
+                                const uint64_t *y, uint64_t *z, uint8_t *scratch, uint64_t tmp_off,
+                                cudaStream_t st) {
+    for (const Block &b : bl) {
+        uint64_t *dst = b.accumulate ? reinterpret_cast<uint64_t *>(scratch + tmp_off) : z + b.zword;
+        cm_status s = enqueue_extract(ctx, b.p, x, y, dst, b.p.scratch_bytes ? scratch : nullptr, st);
+        if (s != CM_OK) return s;
+        if (b.accumulate) {
+            ProfScope ps(ctx, "k_xor_into", st);
+            if (launch_xor_into(z + b.zword, dst, words_of(b.p.m), ctx->nsm, st) != cudaSuccess)
+                return CM_EDEVICE;
+        }
+    }
+    return CM_OK;
+}
+
 cm_status run_single(cm_ctx *ctx, int kind, const uint64_t *x, uint64_t n, const uint64_t *y,
                      uint64_t m, uint64_t *z, cudaStream_t st) {
     if (!ctx || !x || !y || !z) return CM_EINVAL;
-    Plan p;
-    if (!make_plan(kind, n, m, &p)) return CM_EINVAL;
-    if (p.scratch_bytes > ctx->budget) return CM_ENOMEM;
+    std::vector<Block> bl;
+    if (!make_blocks(kind, n, m, ctx->max_lg, &bl)) return CM_EINVAL;
+    uint64_t tmp_off = 0;
+    const uint64_t need = blocks_scratch(bl, &tmp_off);
+    if (need > ctx->budget) return CM_ENOMEM;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return CM_EDEVICE;
     void *scratch = nullptr;
-    if (p.scratch_bytes) {
-        e = cudaMallocFromPoolAsync(&scratch, p.scratch_bytes, ctx->pool, st);
+    if (need) {
+        e = cudaMallocFromPoolAsync(&scratch, need, ctx->pool, st);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return CM_ENOMEM;
         }
     }
-    cm_status s = enqueue_extract(ctx, p, x, y, z, scratch, st);
+    cm_status s = enqueue_blocks(ctx, bl, x, y, z, static_cast<uint8_t *>(scratch), tmp_off, st);
     if (scratch) {
         e = cudaFreeAsync(scratch, st);
         if (s == CM_OK && e != cudaSuccess) s = CM_EDEVICE;
@@ -278,6 +369,13 @@ extern "C" cm_status cm_create(cm_ctx **out, int device, const cm_options *opt) 
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     c->budget = (opt && opt->hbm_budget_bytes) ? opt->hbm_budget_bytes : (uint64_t)(free_b * 0.8);
+    if (opt && opt->max_transform_lg) {
+        if (opt->max_transform_lg < 8 || opt->max_transform_lg > 32) {
+            delete c;
+            return CM_EINVAL;
+        }
+        c->max_lg = (int)opt->max_transform_lg;
+    }
 
     cudaMemPoolProps pp;
     memset(&pp, 0, sizeof(pp));
@@ -372,18 +470,33 @@ extern "C" cm_status cm_device_status(cm_ctx *ctx, cm_stream stream, uint32_t *f
 }
 
 extern "C" uint64_t cm_ntt_length(int kind, uint64_t n, uint64_t m) {
-    Plan p;
-    return make_plan(kind, n, m, &p) ? p.L : 0;
+    std::vector<Block> bl;
+    if (!make_blocks(kind, n, m, 32, &bl)) return 0;
+    uint64_t L = 0;
+    for (const Block &b : bl)
+        if (b.p.L > L) L = b.p.L;
+    return L;
 }
 
 extern "C" uint64_t cm_scratch_bytes(int kind, uint64_t n, uint64_t m) {
-    Plan p;
-    return make_plan(kind, n, m, &p) ? p.scratch_bytes : 0;
+    std::vector<Block> bl;
+    if (!make_blocks(kind, n, m, 32, &bl)) return 0;
+    uint64_t tmp_off = 0;
+    return blocks_scratch(bl, &tmp_off);
 }
 
 extern "C" uint32_t cm_launch_count(int kind, uint64_t n, uint64_t m) {
-    Plan p;
-    return make_plan(kind, n, m, &p) ? p.launches : 0;
+    std::vector<Block> bl;
+    if (!make_blocks(kind, n, m, 32, &bl)) return 0;
+    uint32_t c = 0;
+    for (const Block &b : bl) c += b.p.launches + (b.accumulate ? 1 : 0);
+    return c;
+}
+
+extern "C" uint64_t cm_block_count(int kind, uint64_t n, uint64_t m, uint32_t max_transform_lg) {
+    std::vector<Block> bl;
+    const int lg = max_transform_lg ? (int)max_transform_lg : 32;
+    return make_blocks(kind, n, m, lg, &bl) ? bl.size() : 0;
 }
 
 extern "C" cm_status cm_profile_enable(cm_ctx *ctx, int on) {
@@ -427,21 +540,24 @@ extern "C" cm_status cm_profile_read(cm_ctx *ctx, cm_profile_entry *out, uint32_
 extern "C" cm_status cm_extract_host(cm_ctx *ctx, int kind, const uint64_t *xh, uint64_t n,
                                      const uint64_t *yh, uint64_t m, uint64_t *zh, cm_stream stream) {
     if (!ctx || !xh || !yh || !zh) return CM_EINVAL;
-    Plan p;
-    if (!make_plan(kind, n, m, &p)) return CM_EINVAL;
+    std::vector<Block> bl;
+    if (!make_blocks(kind, n, m, ctx->max_lg, &bl)) return CM_EINVAL;
+    uint64_t tmp_off = 0;
+    const uint64_t sb = blocks_scratch(bl, &tmp_off);
+    const uint64_t sbr = (sb + 255) & ~255ull;
     const uint64_t ybits = kind == CM_TOEPLITZ ? n + m - 1 : (kind == CM_CIRCULANT ? n + 1 : n);
-    const uint64_t xw = (n + 63) / 64, yw = (ybits + 63) / 64, zw = (m + 63) / 64;
+    const uint64_t xw = words_of(n), yw = words_of(ybits), zw = words_of(m);
     const uint64_t io = 8 * (xw + yw + zw) + 3 * 256;
-    if (p.scratch_bytes + io > ctx->budget) return CM_ENOMEM;
+    if (sbr + io > ctx->budget) return CM_ENOMEM;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return CM_EDEVICE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     void *buf = nullptr;
-    if (cudaMallocFromPoolAsync(&buf, p.scratch_bytes + io, ctx->pool, st) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(&buf, sbr + io, ctx->pool, st) != cudaSuccess) {
         cudaGetLastError();
         return CM_ENOMEM;
     }
     uint8_t *b = static_cast<uint8_t *>(buf);
-    uint64_t *xd = reinterpret_cast<uint64_t *>(b + p.scratch_bytes);
+    uint64_t *xd = reinterpret_cast<uint64_t *>(b + sbr);
     uint64_t *yd = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(xd) + ((8 * xw + 255) & ~255ull));
     uint64_t *zd = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(yd) + ((8 * yw + 255) & ~255ull));
     cm_status s = CM_OK;
@@ -449,11 +565,14 @@ extern "C" cm_status cm_extract_host(cm_ctx *ctx, int kind, const uint64_t *xh, 
         cudaMemcpyAsync(yd, yh, 8 * yw, cudaMemcpyHostToDevice, st) != cudaSuccess)
         s = CM_EDEVICE;
     uint32_t pre_h[2] = {1, 1};
-    if (s == CM_OK) s = enqueue_extract(ctx, p, xd, yd, zd, p.scratch_bytes ? b : nullptr, st);
+    if (s == CM_OK) s = enqueue_blocks(ctx, bl, xd, yd, zd, b, tmp_off, st);
     if (s == CM_OK && cudaMemcpyAsync(zh, zd, 8 * zw, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         s = CM_EDEVICE;
+    // the last block's precondition flags (every block checks the whole x)
+    const Plan &last = bl.back().p;
     if (s == CM_OK && kind == CM_DODIS &&
-        cudaMemcpyAsync(pre_h, b + p.scratch_bytes - 256, sizeof(pre_h), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        cudaMemcpyAsync(pre_h, b + last.scratch_bytes - 256, sizeof(pre_h), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess)
         s = CM_EDEVICE;
     cudaFreeAsync(buf, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return CM_EDEVICE;

@@ -17,6 +17,7 @@ struct cm_ctx {
     int device = 0;
     int nsm = 0;
     uint64_t budget = 0;         // scratch bytes one call may take
+    int max_lg = 32;             // longest transform of one product (log2)
     cudaMemPool_t pool = nullptr;
     uint64_t *d_tables = nullptr;
     uint32_t *d_status = nullptr;

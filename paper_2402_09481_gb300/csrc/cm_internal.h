@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "cm.h"
 #include "ntt_device.cuh"
 
@@ -63,8 +65,30 @@ struct Plan {
     uint32_t launches;
 };
 
-// Validate (kind, n, m) and fill the plan; false if invalid.
+// Validate (kind, n, m) and fill the plan; false if invalid or if K + m - 1
+// exceeds 2^32 (one transform).
 bool make_plan(int kind, uint64_t n, uint64_t m, Plan *out);
+
+// Longest bit string a blocked extraction takes (the paper's 2^40).
+constexpr uint64_t kMaxBits = 1ull << 40;
+constexpr uint64_t kMaxBlocks = 1u << 16;
+
+// One product of a blocked extraction: plan p (a middle product over an
+// input block and an output block), written to z + zword words; the first
+// block of each output window writes, later ones XOR into it.
+struct Block {
+    Plan p;
+    uint64_t zword;
+    bool accumulate;
+};
+
+// Split (kind, n, m) into middle products of transform length <= 2^max_lg
+// (GF(2)-linearity: the output is the XOR over input blocks; output blocks are
+// independent).  One block when K + m - 1 <= 2^max_lg.  False if invalid.
+bool make_blocks(int kind, uint64_t n, uint64_t m, int max_lg, std::vector<Block> *out);
+
+// z[i] ^= t[i], i < words (stream-ordered).
+cudaError_t launch_xor_into(uint64_t *z, const uint64_t *t, uint64_t words, int nsm, cudaStream_t st);
 
 // N_A membership and search (host, deterministic).
 bool is_na_prime(uint64_t P);

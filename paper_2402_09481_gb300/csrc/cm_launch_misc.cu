@@ -107,6 +107,22 @@ cudaError_t launch_pack(const uint8_t *par, uint64_t m, uint64_t *z, const uint3
     return cudaGetLastError();
 }
 
+// z[i] ^= t[i]: joins the output windows of a blocked extraction.
+__global__ void k_xor_into(uint64_t *__restrict__ z, const uint64_t *__restrict__ t, uint64_t words) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        z[i] ^= t[i];
+}
+
+cudaError_t launch_xor_into(uint64_t *z, const uint64_t *t, uint64_t words, int nsm, cudaStream_t st) {
+    uint64_t blocks = (words + 255) / 256;
+    const uint64_t cap = (uint64_t)nsm * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) blocks = 1;
+    k_xor_into<<<(unsigned)blocks, 256, 0, st>>>(z, t, words);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_allsame(const uint64_t *x, uint64_t n, uint32_t *flags, int nsm, cudaStream_t st) {
     const uint64_t nw = (n + 63) >> 6;
     uint64_t blocks = (nw + 255) / 256;

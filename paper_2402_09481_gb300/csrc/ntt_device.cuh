@@ -64,8 +64,10 @@ struct BitMap {
         if (mode == kIdentity) {
             idx = k;
         } else if (mode == kModForward) {
-            idx = k + off;
+            idx = k + off;  // k + off < 3 srclen for every plan and block
             if (idx >= srclen) idx -= srclen;
+            if (idx >= srclen) idx -= srclen;
+            if (idx >= srclen) return 0;  // unreachable; keeps every read in bounds
         } else {
             idx = off - k;
             if (idx >= srclen) return 0;

@@ -61,6 +61,7 @@ PROTOTYPES = {
     "cm_ntt_length": (_U64, [_I, _U64, _U64]),
     "cm_scratch_bytes": (_U64, [_I, _U64, _U64]),
     "cm_launch_count": (_U32, [_I, _U64, _U64]),
+    "cm_block_count": (_U64, [_I, _U64, _U64, _U32]),
     "cm_output_length": (_I, [_I, _I, _I, _U64, _U64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                               ctypes.POINTER(ctypes.c_int64)]),
     "cm_trevisan_seed_length": (_I, [_U64, _U64, ctypes.c_double, ctypes.POINTER(_U64),
@@ -189,6 +190,10 @@ def scratch_bytes(kind: int, n: int, m: int) -> int:
     return int(lib().cm_scratch_bytes(kind, n, m))
 
 
+def block_count(kind: int, n: int, m: int, max_transform_lg: int = 0) -> int:
+    return int(lib().cm_block_count(kind, n, m, max_transform_lg))
+
+
 def launch_count(kind: int, n: int, m: int) -> int:
     return int(lib().cm_launch_count(kind, n, m))
 
@@ -269,12 +274,12 @@ def _dev_words(t, nbits: int, name: str):
 class Context:
     """A libcm context on one CUDA device."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_transform_lg: int = 0):
         import torch
         self.device = device
         torch.cuda.set_device(device)
         self._L = lib()
-        opts = (ctypes.c_uint64 * 5)(hbm_budget_bytes, 0, 0, 0, 0)
+        opts = (ctypes.c_uint64 * 5)(hbm_budget_bytes, int(max_transform_lg), 0, 0, 0)
         h = ctypes.c_void_p()
         _check(self._L.cm_create(ctypes.byref(h), device, ctypes.cast(opts, ctypes.c_void_p)),
                "cm_create")

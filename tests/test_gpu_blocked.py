@@ -1,0 +1,155 @@
+"""Blocked extractions (products longer than one transform) against the oracle.
+
+A context whose transform limit is lowered (cm_options.max_transform_lg = 8 ..
+19) splits ordinary sizes into many input and output blocks, so every block
+path (single-CTA blocks, one-pass and two-pass blocks, the Circulant pad bit
+in the block that holds it, the double wrap of the seed index, output windows
+that end mid-word, the Dodis et al. precondition in every block) is compared
+bit for bit with the oracle's whole output.  At the default limit, the QRNG
+example's sizes (n = 6.5e9, m = 581294933, Section "Cryptomite for randomness
+extraction in (Q)RNG") run as two products of length 2^32 and are compared on
+sampled rows, as is the one-transform extreme L = 2^32.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import extractors as ex
+from paper_2402_09481_gb300 import inputs, native
+from conftest import from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+T, C, D = native.TOEPLITZ, native.CIRCULANT, native.DODIS
+
+
+@pytest.fixture(scope="module")
+def ctxs():
+    from paper_2402_09481_gb300 import build
+    build.build()
+    cs = {lg: native.Context(0, max_transform_lg=lg) for lg in (8, 12, 14, 15, 16, 18, 19)}
+    yield cs
+    for c in cs.values():
+        c.close()
+
+
+def run(ctx, kind, n, m, xw, yw):
+    x, y = to_dev(xw), to_dev(yw)
+    z = torch.full((native.words(m),), -1, dtype=torch.int64, device="cuda")
+    if kind == T:
+        ctx.toeplitz(x, n, y, m, z)
+    elif kind == C:
+        ctx.circulant(x, n, y, m, z)
+    else:
+        ctx.dodis(x, y, n, m, z)
+    torch.cuda.synchronize()
+    return from_dev(z)
+
+
+def want(kind, n, m, xw, yw):
+    if kind == T:
+        return oracle.toeplitz_packed(xw, n, yw, m)
+    if kind == C:
+        return oracle.circulant_packed(xw, n, yw, m)
+    return oracle.dodis_packed(xw, yw, n, m)
+
+
+def ybits(kind, n, m):
+    return n + m - 1 if kind == T else (n + 1 if kind == C else n)
+
+
+CASES = [
+    # (kind, n, m, max_transform_lg)
+    (T, 1000, 300, 8), (T, 777, 129, 8), (T, 5000, 2000, 12), (T, 20000, 3000, 12),
+    (T, 100000, 30000, 15), (T, 300000, 1000, 14), (T, 70000, 70000, 16), (T, 4097, 4096, 12),
+    (T, 400_003, 131_077, 19),
+    (C, "P5000", 0.5, 12), (C, "P5000", 0.1, 8), (C, "P200000", 0.5, 16), (C, "P200000", 0.05, 14),
+    (C, "P300000", 0.3, 18),
+    (D, "P50000", 0.4, 14), (D, "P3000", 0.9, 8), (D, "P300000", 0.2, 16),
+]
+
+
+def resolve(kind, n, m):
+    if isinstance(n, str):
+        P = oracle.next_na(int(n[1:]))
+        n = P - 1 if kind == C else P
+        m = max(1, int(m * n))
+    return n, m
+
+
+@pytest.mark.parametrize("kind,n,m,lg", CASES)
+def test_blocked_matches_oracle(ctxs, cm_ctx, kind, n, m, lg):
+    n, m = resolve(kind, n, m)
+    assert native.block_count(kind, n, m, lg) > 1
+    xw = inputs.bernoulli_half(900 + n % 97, n)
+    if kind == D:
+        xw[0] = (xw[0] | np.uint64(1)) & ~np.uint64(2)
+    yw = inputs.bernoulli_half(901 + n % 89, ybits(kind, n, m))
+    got = run(ctxs[lg], kind, n, m, xw, yw)
+    assert (got == want(kind, n, m, xw, yw)).all(), (kind, n, m, lg)
+    # the same bits as the one-transform call
+    assert (got == run(cm_ctx, kind, n, m, xw, yw)).all()
+
+
+def test_blocked_dodis_precondition(ctxs):
+    P = oracle.next_na(20000)
+    for fill in (0, 1):
+        xw = ex.pack_bits(np.full(P, fill, dtype=np.uint8))
+        yw = inputs.bernoulli_half(5, P)
+        got = run(ctxs[12], D, P, P // 2, xw, yw)
+        assert not got.any()
+        assert ctxs[12].device_status()[0] == native.CM_EPRECOND
+
+
+def test_blocked_host_buffers(ctxs):
+    n, m = 50000, 9000
+    xw, yw = inputs.bernoulli_half(11, n), inputs.bernoulli_half(12, n + m - 1)
+    xh = torch.from_numpy(xw.view(np.int64))
+    yh = torch.from_numpy(yw.view(np.int64))
+    zh = torch.zeros(native.words(m), dtype=torch.int64)
+    assert ctxs[12].extract_host(T, xh, n, yh, m, zh) == native.CM_OK
+    assert (zh.numpy().view(np.uint64) == oracle.toeplitz_packed(xw, n, yw, m)).all()
+
+
+def sample_rows(m, k, seed):
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([np.arange(16), np.arange(m - 16, m), rng.integers(0, m, k)]))
+
+
+def out_bits(z, rows):
+    return ((z[rows >> 6] >> (rows & 63).astype(np.uint64)) & np.uint64(1)).astype(np.uint8)
+
+
+@pytest.mark.slow
+def test_qrng_example_toeplitz_sampled(cm_ctx):
+    # n1 = 6.5e9, m = floor(k1 + 2 log2 1e-10) = 581294933, seed n1 + m - 1 bits
+    n, m = 6_500_000_000, 581_294_933
+    assert native.block_count(T, n, m) == 2
+    xw, yw = inputs.bernoulli_half(60, n), inputs.bernoulli_half(61, n + m - 1)
+    z = run(cm_ctx, T, n, m, xw, yw)
+    rows = sample_rows(m, 24, 1)
+    assert (out_bits(z, rows) == oracle.toeplitz_rows(xw, n, yw, m, rows)).all()
+    if m & 63:
+        assert int(z[-1]) >> (m & 63) == 0
+
+
+@pytest.mark.slow
+def test_qrng_example_circulant_sampled(cm_ctx):
+    # the Circulant extension of the same example: P = 6.5e9 + 69, n1' = P - 1
+    n, m = 6_500_000_068, 581_294_933
+    assert oracle.is_prime(n + 1) and native.block_count(C, n, m) == 2
+    xw, yw = inputs.bernoulli_half(62, n), inputs.bernoulli_half(63, n + 1)
+    z = run(cm_ctx, C, n, m, xw, yw)
+    rows = sample_rows(m, 16, 2)
+    assert (out_bits(z, rows) == oracle.circulant_rows(xw, n, yw, m, rows)).all()
+
+
+@pytest.mark.slow
+def test_one_transform_of_length_2_32(cm_ctx):
+    n, m = 2 ** 31, 2 ** 31 + 1
+    assert native.ntt_length(T, n, m) == 2 ** 32 and native.block_count(T, n, m) == 1
+    xw, yw = inputs.bernoulli_half(64, n), inputs.bernoulli_half(65, n + m - 1)
+    z = run(cm_ctx, T, n, m, xw, yw)
+    rows = sample_rows(m, 16, 3)
+    assert (out_bits(z, rows) == oracle.toeplitz_rows(xw, n, yw, m, rows)).all()

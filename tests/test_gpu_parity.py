@@ -158,7 +158,8 @@ def test_invalid_arguments(cm_ctx):
     s = torch.cuda.current_stream().cuda_stream
     h = cm_ctx.handle
     assert L.cm_toeplitz(h, p, 5, p, 0, p, s) == native.CM_EINVAL          # m = 0
-    assert L.cm_toeplitz(h, p, 2 ** 31, p, 2 ** 31 + 2, p, s) == native.CM_EINVAL  # L > 2^32
+    assert L.cm_toeplitz(h, p, 2 ** 40 + 1, p, 5, p, s) == native.CM_EINVAL  # n > 2^40
+    assert L.cm_toeplitz(h, p, 5, p, 2 ** 40 + 1, p, s) == native.CM_EINVAL  # m > 2^40
     assert L.cm_circulant(h, p, 6, p, 3, p, s) == native.CM_EINVAL          # 7 not in N_A
     assert L.cm_circulant(h, p, 10, p, 11, p, s) == native.CM_EINVAL        # m > n
     assert L.cm_dodis(h, p, p, 9, 3, p, s) == native.CM_EINVAL              # 9 not prime
