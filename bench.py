@@ -46,6 +46,13 @@ WORKLOADS = {
     "dodis": dict(kind=2, n=1073741789, m=429496715,
                   name="Dodis et al. single instance: n = 1073741789 (largest N_A prime <= 2^30), "
                        "m = floor(0.4 n), Bernoulli(1/2) x and y"),
+    # the QRNG example of the paper: n1 = 6.5e9, k1 = 581295000, eps = 1e-10
+    "qrng_toeplitz": dict(kind=0, n=6_500_000_000, m=581_294_933,
+                          name="Toeplitz at the QRNG example's sizes: n = 6.5e9, m = 581294933 "
+                               "(two products of length 2^32), Bernoulli(1/2) x and y"),
+    "qrng_circulant": dict(kind=1, n=6_500_000_068, m=581_294_933,
+                           name="Circulant at the QRNG example's sizes: P = 6500000069, m = 581294933 "
+                                "(two products of length 2^32), Bernoulli(1/2) x and y"),
 }
 KIND_NAMES = {0: "toeplitz", 1: "circulant", 2: "dodis"}
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
@@ -185,13 +192,19 @@ def alu_peak_butterflies(sm_mhz):
     return NUM_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / ALU_OPS_PER_BUTTERFLY
 
 
-def kernel_butterflies(kernel, L, lgR=None):
-    """Radix-2 butterflies one launch performs (L/2 per stage per transform)."""
+def kernel_butterflies(kernel, L):
+    """Radix-2 butterflies one launch performs (L/2 per stage per transform).
+    Column passes: one pass for lg - 13 <= 12 (log2 R = lg - 13), else two with
+    log2 R = ceil((lg - 13) / 2) for the outer pass (k_pass_fwd_bits,
+    k_pass_inv_parity) and floor((lg - 13) / 2) for the inner one."""
     lg = int(L).bit_length() - 1
+    rest = lg - 13
     if kernel == "k_middle":
         return 3 * (L // 2) * 13            # two forward row transforms, one inverse
-    if kernel in ("k_pass_fwd_bits", "k_pass_fwd", "k_pass_inv", "k_pass_inv_parity"):
-        return (L // 2) * (lgR if lgR else lg - 13)
+    if kernel in ("k_pass_fwd_bits", "k_pass_inv_parity"):
+        return (L // 2) * (rest if rest <= 12 else (rest + 1) // 2)
+    if kernel in ("k_pass_fwd", "k_pass_inv"):
+        return (L // 2) * (rest // 2)
     if kernel == "k_fused_small":
         return 3 * (L // 2) * lg
     return None
@@ -1084,7 +1097,7 @@ def main():
     peak, peak_src = measured_peaks()
     achieved = alg / (per_launch * 1e-3) / 1e9
     clk = (sampler.summary(t_wall0, t_wall1) or {}).get("sm_mhz") or 2070.0
-    bfly = kernel_butterflies(dom, L, native.ntt_length(kind, n, m).bit_length() - 1 - 13)
+    bfly = kernel_butterflies(dom, L)
     ach_b = bfly / (per_launch * 1e-3) / 1e9
     peak_b = alu_peak_butterflies(clk) / 1e9
     roof = {"bound": "alu", "kernel": dom, "achieved": ach_b, "peak": peak_b, "unit": "G butterflies/s",
@@ -1095,7 +1108,8 @@ def main():
             "avg_launch_ms": per_launch,
             "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src, "algorithmic_bytes_per_launch": alg}}
-    pb = path_bytes(L, n, sb, m)
+    blocks = native.block_count(kind, n, m)
+    pb = blocks * path_bytes(L, n, sb, m)
     path_roof = {"bytes_48L": pb, "achieved_gbs": pb / (ms_per_step * 1e-3) / 1e9,
                  "frac_of_measured_hbm": pb / (ms_per_step * 1e-3) / 1e9 / peak,
                  "frac_of_8tbs": pb / (ms_per_step * 1e-3) / 1e9 / 8000.0}
@@ -1133,7 +1147,7 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": wl["name"], "n": n, "m": m, "L": L, "seed_bits": sb,
+            "config": {"workload": wl["name"], "n": n, "m": m, "L": L, "products": blocks, "seed_bits": sb,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "latency_ms": {"p50": statistics.median(step_ms),
