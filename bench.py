@@ -158,17 +158,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def field_of(kernel):
+    """(kernel name without the field suffix, element bytes): the 32-bit field
+    kernels carry the suffix _f30, the Goldilocks ones none."""
+    return (kernel[:-4], 4) if kernel.endswith("_f30") else (kernel, 8)
+
+
 def algorithmic_bytes(kernel, L, n, seedlen, m):
-    """Bytes one launch must move: u64 field elements (8 B), bits (1/8 B),
-    parity bytes (1 B)."""
+    """Bytes one launch must move: field elements (8 B Goldilocks, 4 B for the
+    32-bit field), bits (1/8 B), parity bytes (1 B)."""
+    kernel, e = field_of(kernel)
     if kernel == "k_middle":
-        return 24 * L                       # read both operands' rows, write one
+        return 3 * e * L                    # read both operands' rows, write one
     if kernel == "k_pass_fwd_bits":
-        return 8 * L + (n + seedlen) / 16   # write one operand; read its bits (avg)
+        return e * L + (n + seedlen) / 16   # write one operand; read its bits (avg)
     if kernel in ("k_pass_fwd", "k_pass_inv"):
-        return 16 * L
+        return 2 * e * L
     if kernel == "k_pass_inv_parity":
-        return 8 * L + m                    # read, write parity bytes of the window
+        return e * L + m                    # read, write parity bytes of the window
     if kernel == "k_pack":
         return m + m / 8
     if kernel == "k_fused_small":
@@ -183,13 +190,16 @@ def algorithmic_bytes(kernel, L, n, seedlen, m):
 # (2 for the carry chain and 4 for the conditional correction, each); the
 # twiddle multiply (FMA pipe) and everything else is not counted, so the model
 # peak is an upper bound on butterflies per second.
+# The 32-bit field's add and subtract are a subtraction, a compare and a
+# conditional add each at least: 6 ALU operations per butterfly.
 ALU_OPS_PER_BUTTERFLY = 12
+ALU_OPS_PER_BUTTERFLY_F30 = 6
 ALU_LANES_PER_SM = 64
 NUM_SMS = 152
 
 
-def alu_peak_butterflies(sm_mhz):
-    return NUM_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / ALU_OPS_PER_BUTTERFLY
+def alu_peak_butterflies(sm_mhz, ops=ALU_OPS_PER_BUTTERFLY):
+    return NUM_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / ops
 
 
 def kernel_butterflies(kernel, L):
@@ -197,6 +207,7 @@ def kernel_butterflies(kernel, L):
     Column passes: one pass for lg - 13 <= 12 (log2 R = lg - 13), else two with
     log2 R = ceil((lg - 13) / 2) for the outer pass (k_pass_fwd_bits,
     k_pass_inv_parity) and floor((lg - 13) / 2) for the inner one."""
+    kernel, _ = field_of(kernel)
     lg = int(L).bit_length() - 1
     rest = lg - 13
     if kernel == "k_middle":
@@ -210,9 +221,10 @@ def kernel_butterflies(kernel, L):
     return None
 
 
-def path_bytes(L, n, seedlen, m):
-    """48L + bit I/O: one write and one read of three L-element u64 arrays."""
-    return 48 * L + (n + seedlen + m) / 8
+def path_bytes(L, n, seedlen, m, esz=8):
+    """6 esz L + bit I/O: one write and one read of three L-element arrays
+    (48L for Goldilocks, 24L for the 32-bit field)."""
+    return 6 * esz * L + (n + seedlen + m) / 8
 
 
 def cpu_oracle_rate(kind, n, m, xw, yw, budget_s=12.0):
@@ -1098,18 +1110,19 @@ def main():
     achieved = alg / (per_launch * 1e-3) / 1e9
     clk = (sampler.summary(t_wall0, t_wall1) or {}).get("sm_mhz") or 2070.0
     bfly = kernel_butterflies(dom, L)
+    ops = ALU_OPS_PER_BUTTERFLY_F30 if dom.endswith("_f30") else ALU_OPS_PER_BUTTERFLY
     ach_b = bfly / (per_launch * 1e-3) / 1e9
-    peak_b = alu_peak_butterflies(clk) / 1e9
+    peak_b = alu_peak_butterflies(clk, ops) / 1e9
     roof = {"bound": "alu", "kernel": dom, "achieved": ach_b, "peak": peak_b, "unit": "G butterflies/s",
             "frac": ach_b / peak_b,
             "peak_source": f"{NUM_SMS} SMs x {ALU_LANES_PER_SM} ALU lanes x {clk:.0f} MHz measured / "
-                           f"{ALU_OPS_PER_BUTTERFLY} ALU ops per radix-2 butterfly",
+                           f"{ops} ALU ops per radix-2 butterfly",
             "traffic": ncu_traffic(dom, args.workload), "butterflies_per_launch": bfly,
             "avg_launch_ms": per_launch,
             "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src, "algorithmic_bytes_per_launch": alg}}
     blocks = native.block_count(kind, n, m)
-    pb = blocks * path_bytes(L, n, sb, m)
+    pb = blocks * path_bytes(L, n, sb, m, field_of(dom)[1])
     path_roof = {"bytes_48L": pb, "achieved_gbs": pb / (ms_per_step * 1e-3) / 1e9,
                  "frac_of_measured_hbm": pb / (ms_per_step * 1e-3) / 1e9 / peak,
                  "frac_of_8tbs": pb / (ms_per_step * 1e-3) / 1e9 / 8000.0}

@@ -66,13 +66,21 @@ typedef struct {
      * single extraction whose K + m - 1 is longer runs as several products
      * (see cm_toeplitz); lowering it trades transforms for scratch. */
     uint32_t max_transform_lg;
-    uint32_t reserved[7];
+    /* Transform field of the single calls: CM_FIELD_AUTO takes the 32-bit field
+     * of the prime 3 * 2^30 + 1 (the paper's small field, Section "Performance")
+     * for every product of length <= 2^30 and Goldilocks above;
+     * CM_FIELD_GOLDILOCKS takes Goldilocks throughout.  Results are identical. */
+    uint32_t field;
+    uint32_t reserved[6];
 } cm_options;
+
+#define CM_FIELD_AUTO 0u
+#define CM_FIELD_GOLDILOCKS 1u
 
 /* Create a context on CUDA device `device`: root tables resident in HBM, a
  * scratch memory pool.  opt may be NULL.  Returns CM_EDEVICE if the device is
- * unusable, CM_EINVAL if out is NULL or opt->max_transform_lg is outside
- * 8..32 (and not 0). */
+ * unusable, CM_EINVAL if out is NULL, opt->max_transform_lg is outside
+ * 8..32 (and not 0) or opt->field is not a CM_FIELD_* value. */
 cm_status cm_create(cm_ctx **out, int device, const cm_options *opt);
 
 /* Synchronize the device and free everything the context owns. */
@@ -373,8 +381,10 @@ cm_status cm_profile_read(cm_ctx *ctx, cm_profile_entry *out, uint32_t cap, uint
 /* Field self-test on `device`: for `count` inputs (fixed edge values, then
  * SplitMix64 samples from `seed`) compares the device's Goldilocks add, sub,
  * multiply and multiply-by-2^s (s = 0..96), written as 32-bit carry chains,
- * with the plain 64-bit C forms of the same functions; *mismatches receives the
- * number of disagreements (0 when correct).  Allocates and frees 8 bytes. */
+ * with the plain 64-bit C forms of the same functions, and the 32-bit field's
+ * add, subtract, Montgomery product and sub-transform twiddles (q = 3 * 2^30
+ * + 1) with plain 64-bit modular arithmetic; *mismatches receives the number
+ * of disagreements (0 when correct).  Allocates and frees 8 bytes. */
 cm_status cm_field_selftest(int device, uint64_t count, uint64_t seed, uint64_t *mismatches);
 
 /* ----- host helpers (no GPU work) --------------------------------------- */

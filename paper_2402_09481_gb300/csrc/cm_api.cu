@@ -100,13 +100,14 @@ bool make_plan(int kind, uint64_t n, uint64_t m, Plan *p) {
 // the results XORed: parity of a sum is the XOR of the parities) and over
 // output blocks i in [I0, I0 + mb) (b shifted by I0).  In transform positions
 // u = K - 1 - t, input block [D, D + kb) of A is A shifted by D.
-bool make_blocks(int kind, uint64_t n, uint64_t m, int max_lg, std::vector<Block> *out) {
+bool make_blocks(int kind, uint64_t n, uint64_t m, int max_lg, bool allow_f30, std::vector<Block> *out) {
     out->clear();
     Plan b;
     if (max_lg < 8 || max_lg > 32 || !base_maps(kind, n, m, &b)) return false;
     const uint64_t Lmax = 1ull << max_lg;
     if (b.K + m - 1 <= Lmax) {
         finish_plan(&b);
+        if (allow_f30 && b.lg <= kF30MaxLg) b.field = kFieldF30;
         out->push_back({b, 0, false});
         return true;
     }
@@ -136,6 +137,7 @@ bool make_blocks(int kind, uint64_t n, uint64_t m, int max_lg, std::vector<Block
             q.blen = kb + mr - 1;
             q.boff = (b.boff + T0 + I0) % b.bsrclen;
             finish_plan(&q);
+            if (allow_f30 && q.lg <= kF30MaxLg) q.field = kFieldF30;
             out->push_back({q, I0 / 64, j != 0});
         }
     }
@@ -163,7 +165,9 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
                           uint64_t *z, void *scratch, cudaStream_t st) {
     const BitMap am = bitmap(x, p.amode, p.alen, p.asrclen, p.aoff);
     const BitMap bm = bitmap(y, p.bmode, p.blen, p.bsrclen, p.boff);
-    const uint64_t linv = gl_inv_pow2_host(p.L);
+    const bool f30 = p.field == kFieldF30;
+    const uint64_t linv = f30 ? f30_linv_mont2(p.L) : gl_inv_pow2_host(p.L);
+    const size_t esz = f30 ? sizeof(uint32_t) : sizeof(uint64_t);
     uint32_t *pre = nullptr;
     cudaError_t e;
     uint8_t *sc = static_cast<uint8_t *>(scratch);
@@ -183,14 +187,16 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
         q.z = z;
         q.pre = pre;
         q.status = ctx->d_status;
+        q.field = p.field;
         q.rt = ctx->rt;
+        q.rt30 = ctx->rt30;
         q.stream = st;
-        ProfScope ps(ctx, "k_fused_small", st);
+        ProfScope ps(ctx, f30 ? "k_fused_small_f30" : "k_fused_small", st);
         return cuda_status(launch_small(q, p.lg));
     }
-    uint64_t *A = reinterpret_cast<uint64_t *>(sc);
-    uint64_t *B = A + p.L;
-    uint8_t *par = reinterpret_cast<uint8_t *>(B + p.L);
+    void *A = sc;
+    void *B = sc + esz * p.L;
+    uint8_t *par = sc + 2 * esz * p.L;
 
     int lgN[2], lgS[2];
     int cur = p.lg;
@@ -208,17 +214,21 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
             a.map = op == 0 ? am : bm;
             a.lgN = lgN[j];
             a.lgS = lgS[j];
+            a.field = p.field;
             a.rt = ctx->rt;
+            a.rt30 = ctx->rt30;
             a.L = p.L;
             a.inv = false;
             a.bits_in = (j == 0);
-            ProfScope ps(ctx, j == 0 ? "k_pass_fwd_bits" : "k_pass_fwd", st);
+            ProfScope ps(ctx, j == 0 ? (f30 ? "k_pass_fwd_bits_f30" : "k_pass_fwd_bits")
+                                     : (f30 ? "k_pass_fwd_f30" : "k_pass_fwd"), st);
             if ((e = launch_pass(a, p.pass_lg[j], st)) != cudaSuccess) return cuda_status(e);
         }
     }
     {
-        ProfScope ps(ctx, "k_middle", st);
-        if ((e = launch_middle(A, B, p.L, linv, ctx->rt, ctx->nsm, st)) != cudaSuccess) return cuda_status(e);
+        ProfScope ps(ctx, f30 ? "k_middle_f30" : "k_middle", st);
+        if ((e = launch_middle(p.field, A, B, p.L, linv, ctx->rt, ctx->rt30, ctx->nsm, st)) != cudaSuccess)
+            return cuda_status(e);
     }
     for (int j = p.npass - 1; j >= 0; --j) {
         PassArgs a;
@@ -226,14 +236,17 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
         a.data = A;
         a.lgN = lgN[j];
         a.lgS = lgS[j];
+        a.field = p.field;
         a.rt = ctx->rt;
+        a.rt30 = ctx->rt30;
         a.L = p.L;
         a.inv = true;
         a.parity_out = (j == 0);
         a.par = par;
         a.lo = p.lo;
         a.m = p.m;
-        ProfScope ps(ctx, j == 0 ? "k_pass_inv_parity" : "k_pass_inv", st);
+        ProfScope ps(ctx, j == 0 ? (f30 ? "k_pass_inv_parity_f30" : "k_pass_inv_parity")
+                                 : (f30 ? "k_pass_inv_f30" : "k_pass_inv"), st);
         if ((e = launch_pass(a, p.pass_lg[j], st)) != cudaSuccess) return cuda_status(e);
     }
     ProfScope ps(ctx, "k_pack", st);
@@ -275,7 +288,7 @@ cm_status run_single(cm_ctx *ctx, int kind, const uint64_t *x, uint64_t n, const
                      uint64_t m, uint64_t *z, cudaStream_t st) {
     if (!ctx || !x || !y || !z) return CM_EINVAL;
     std::vector<Block> bl;
-    if (!make_blocks(kind, n, m, ctx->max_lg, &bl)) return CM_EINVAL;
+    if (!make_blocks(kind, n, m, ctx->max_lg, ctx->allow_f30, &bl)) return CM_EINVAL;
     uint64_t tmp_off = 0;
     const uint64_t need = blocks_scratch(bl, &tmp_off);
     if (need > ctx->budget) return CM_ENOMEM;
@@ -350,6 +363,33 @@ static void build_tables(std::vector<uint64_t> &h) {
     }
 }
 
+// F30 root tables, entries in Montgomery form w R mod q: small[8192] =
+// omega_8192^e; big_lo_fwd[32768] = g30^e; big_hi_fwd[32768] = g30^(32768 e);
+// big_lo_inv, big_hi_inv likewise for g30^-1.
+static void build_tables30(std::vector<uint32_t> &h) {
+    h.assign(kTable30Words, 0);
+    const uint32_t g = f30_root_2_30(false), gi = f30_root_2_30(true);
+    const uint32_t w = f30_pow(g, 1ull << (kF30MaxLg - kSmallLg));  // omega_8192
+    uint32_t a = 1;
+    for (int e = 0; e < 8192; ++e) {
+        h[e] = f30_to_mont(a);
+        a = f30_mulmod(a, w);
+    }
+    uint32_t *lf = &h[8192], *hf = lf + 32768, *li = hf + 32768, *hi = li + 32768;
+    const uint32_t g15 = f30_pow(g, 32768), gi15 = f30_pow(gi, 32768);
+    uint32_t c0 = 1, c1 = 1, c2 = 1, c3 = 1;
+    for (int e = 0; e < 32768; ++e) {
+        lf[e] = f30_to_mont(c0);
+        hf[e] = f30_to_mont(c1);
+        li[e] = f30_to_mont(c2);
+        hi[e] = f30_to_mont(c3);
+        c0 = f30_mulmod(c0, g);
+        c1 = f30_mulmod(c1, g15);
+        c2 = f30_mulmod(c2, gi);
+        c3 = f30_mulmod(c3, gi15);
+    }
+}
+
 }  // namespace cm
 
 using namespace cm;
@@ -376,6 +416,11 @@ extern "C" cm_status cm_create(cm_ctx **out, int device, const cm_options *opt) 
         }
         c->max_lg = (int)opt->max_transform_lg;
     }
+    if (opt && opt->field > CM_FIELD_GOLDILOCKS) {
+        delete c;
+        return CM_EINVAL;
+    }
+    c->allow_f30 = !(opt && opt->field == CM_FIELD_GOLDILOCKS);
 
     cudaMemPoolProps pp;
     memset(&pp, 0, sizeof(pp));
@@ -391,12 +436,21 @@ extern "C" cm_status cm_create(cm_ctx **out, int device, const cm_options *opt) 
 
     std::vector<uint64_t> h;
     build_tables(h);
+    std::vector<uint32_t> h30;
+    build_tables30(h30);
     if (cudaMalloc(&c->d_tables, h.size() * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&c->d_tables30, h30.size() * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&c->d_status, 64) != cudaSuccess) {
         cm_destroy(c);
         return CM_ENOMEM;
     }
     cudaMemcpy(c->d_tables, h.data(), h.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_tables30, h30.data(), h30.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    c->rt30.small = c->d_tables30;
+    c->rt30.big_lo_fwd = c->d_tables30 + 8192;
+    c->rt30.big_hi_fwd = c->rt30.big_lo_fwd + 32768;
+    c->rt30.big_lo_inv = c->rt30.big_hi_fwd + 32768;
+    c->rt30.big_hi_inv = c->rt30.big_lo_inv + 32768;
     cudaMemset(c->d_status, 0, 64);
     c->rt.small = c->d_tables;
     c->rt.big_lo_fwd = c->d_tables + 8192;
@@ -422,6 +476,7 @@ extern "C" void cm_destroy(cm_ctx *c) {
     }
     for (auto ev : c->ev_pool) cudaEventDestroy(ev);
     if (c->d_tables) cudaFree(c->d_tables);
+    if (c->d_tables30) cudaFree(c->d_tables30);
     if (c->d_status) cudaFree(c->d_status);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     delete c;
@@ -471,7 +526,7 @@ extern "C" cm_status cm_device_status(cm_ctx *ctx, cm_stream stream, uint32_t *f
 
 extern "C" uint64_t cm_ntt_length(int kind, uint64_t n, uint64_t m) {
     std::vector<Block> bl;
-    if (!make_blocks(kind, n, m, 32, &bl)) return 0;
+    if (!make_blocks(kind, n, m, 32, true, &bl)) return 0;
     uint64_t L = 0;
     for (const Block &b : bl)
         if (b.p.L > L) L = b.p.L;
@@ -480,14 +535,14 @@ extern "C" uint64_t cm_ntt_length(int kind, uint64_t n, uint64_t m) {
 
 extern "C" uint64_t cm_scratch_bytes(int kind, uint64_t n, uint64_t m) {
     std::vector<Block> bl;
-    if (!make_blocks(kind, n, m, 32, &bl)) return 0;
+    if (!make_blocks(kind, n, m, 32, true, &bl)) return 0;
     uint64_t tmp_off = 0;
     return blocks_scratch(bl, &tmp_off);
 }
 
 extern "C" uint32_t cm_launch_count(int kind, uint64_t n, uint64_t m) {
     std::vector<Block> bl;
-    if (!make_blocks(kind, n, m, 32, &bl)) return 0;
+    if (!make_blocks(kind, n, m, 32, true, &bl)) return 0;
     uint32_t c = 0;
     for (const Block &b : bl) c += b.p.launches + (b.accumulate ? 1 : 0);
     return c;
@@ -496,7 +551,7 @@ extern "C" uint32_t cm_launch_count(int kind, uint64_t n, uint64_t m) {
 extern "C" uint64_t cm_block_count(int kind, uint64_t n, uint64_t m, uint32_t max_transform_lg) {
     std::vector<Block> bl;
     const int lg = max_transform_lg ? (int)max_transform_lg : 32;
-    return make_blocks(kind, n, m, lg, &bl) ? bl.size() : 0;
+    return make_blocks(kind, n, m, lg, true, &bl) ? bl.size() : 0;
 }
 
 extern "C" cm_status cm_profile_enable(cm_ctx *ctx, int on) {
@@ -541,7 +596,7 @@ extern "C" cm_status cm_extract_host(cm_ctx *ctx, int kind, const uint64_t *xh, 
                                      const uint64_t *yh, uint64_t m, uint64_t *zh, cm_stream stream) {
     if (!ctx || !xh || !yh || !zh) return CM_EINVAL;
     std::vector<Block> bl;
-    if (!make_blocks(kind, n, m, ctx->max_lg, &bl)) return CM_EINVAL;
+    if (!make_blocks(kind, n, m, ctx->max_lg, ctx->allow_f30, &bl)) return CM_EINVAL;
     uint64_t tmp_off = 0;
     const uint64_t sb = blocks_scratch(bl, &tmp_off);
     const uint64_t sbr = (sb + 255) & ~255ull;

@@ -18,10 +18,13 @@ struct cm_ctx {
     int nsm = 0;
     uint64_t budget = 0;         // scratch bytes one call may take
     int max_lg = 32;             // longest transform of one product (log2)
+    bool allow_f30 = true;       // single calls may take the 32-bit field
     cudaMemPool_t pool = nullptr;
     uint64_t *d_tables = nullptr;
     uint32_t *d_status = nullptr;
     cm::RootTables rt{};
+    uint32_t *d_tables30 = nullptr;
+    cm::RootTables30 rt30{};
     cm_server *server = nullptr;
 
     // per-kernel tracing (cm_profile_*): events around each launch when on

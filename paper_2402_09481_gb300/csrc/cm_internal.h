@@ -14,25 +14,35 @@ constexpr uint32_t kFlagPrecond = CM_FLAG_PRECOND;
 constexpr uint32_t kFlagTimeout = CM_FLAG_TIMEOUT;
 constexpr size_t kTableWords = 8192 + 4 * 65536;  // resident root tables
 
+// Transform fields (see ntt_device.cuh).
+constexpr int kFieldGL = 0;   // Goldilocks, 64-bit elements, L <= 2^32
+constexpr int kFieldF30 = 1;  // 3 * 2^30 + 1, 32-bit elements, L <= 2^30
+constexpr int kF30MaxLg = 30;
+constexpr size_t kTable30Words = 8192 + 4 * 32768;  // resident F30 root tables
+
 // Arguments of the single-CTA extraction (L <= 2^13).
 struct Launch {
     BitMap amap, bmap;
-    uint64_t lo, m, linv;
+    uint64_t lo, m, linv;  // linv in the field's product form
     uint64_t *z;
     const uint32_t *pre;
     uint32_t *status;
+    int field;
     RootTables rt;
+    RootTables30 rt30;
     cudaStream_t stream;
 };
 
-// Arguments of one column pass.
+// Arguments of one column pass.  data: L elements of the field's word size.
 struct PassArgs {
-    uint64_t *data;
+    void *data;
     BitMap map;
     int lgN, lgS;
     uint8_t *par;
     uint64_t lo, m;
+    int field;
     RootTables rt;
+    RootTables30 rt30;
     uint64_t L;
     bool inv, bits_in, parity_out;
 };
@@ -41,8 +51,11 @@ cudaError_t launch_small(const Launch &q, int lg);
 cudaError_t launch_pass(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_fwd(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_inv(const PassArgs &a, int logr, cudaStream_t st);
-cudaError_t launch_middle(uint64_t *A, const uint64_t *B, uint64_t L, uint64_t linv,
-                          const RootTables &rt, int nsm, cudaStream_t st);
+cudaError_t launch_pass_fwd30(const PassArgs &a, int logr, cudaStream_t st);
+cudaError_t launch_pass_inv30(const PassArgs &a, int logr, cudaStream_t st);
+// A, B: L elements of the field's word size.
+cudaError_t launch_middle(int field, void *A, const void *B, uint64_t L, uint64_t linv, const RootTables &rt,
+                          const RootTables30 &rt30, int nsm, cudaStream_t st);
 cudaError_t launch_pack(const uint8_t *par, uint64_t m, uint64_t *z, const uint32_t *pre,
                         uint32_t *status, int nsm, cudaStream_t st);
 cudaError_t launch_allsame(const uint64_t *x, uint64_t n, uint32_t *flags, int nsm, cudaStream_t st);
@@ -63,6 +76,7 @@ struct Plan {
     uint64_t lo;     // window start K - 1
     uint64_t scratch_bytes;
     uint32_t launches;
+    int field;       // kFieldGL or kFieldF30
 };
 
 // Validate (kind, n, m) and fill the plan; false if invalid or if K + m - 1
@@ -85,7 +99,8 @@ struct Block {
 // Split (kind, n, m) into middle products of transform length <= 2^max_lg
 // (GF(2)-linearity: the output is the XOR over input blocks; output blocks are
 // independent).  One block when K + m - 1 <= 2^max_lg.  False if invalid.
-bool make_blocks(int kind, uint64_t n, uint64_t m, int max_lg, std::vector<Block> *out);
+// allow_f30: blocks whose transform fits 2^30 run over the 32-bit field.
+bool make_blocks(int kind, uint64_t n, uint64_t m, int max_lg, bool allow_f30, std::vector<Block> *out);
 
 // z[i] ^= t[i], i < words (stream-ordered).
 cudaError_t launch_xor_into(uint64_t *z, const uint64_t *t, uint64_t words, int nsm, cudaStream_t st);

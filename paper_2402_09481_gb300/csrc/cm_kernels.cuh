@@ -11,6 +11,8 @@
 // Thm. convolution is taken in whatever order both operands share.
 //
 // Kernels:
+// Each kernel is a template over the field policy F (FieldGL, FieldF30).
+//
 //   k_fused_small<LG>  whole extraction for L <= 2^13 in one CTA: bit unpack,
 //                      forward NTT of both operands, product * L^-1, inverse NTT,
 //                      parity of the output window, bit pack.
@@ -34,27 +36,28 @@ namespace cm {
 // ---------------------------------------------------------------------------
 // Whole extraction on one CTA (L = 2^LG <= 2^13).
 // ---------------------------------------------------------------------------
-template <int LG>
+template <class F, int LG>
 __global__ void __launch_bounds__(kThreads, 1)
-k_fused_small(BitMap amap, BitMap bmap, uint64_t lo, uint64_t m, uint64_t linv,
+k_fused_small(BitMap amap, BitMap bmap, uint64_t lo, uint64_t m, uint64_t linv_,
               uint64_t *__restrict__ z, const uint32_t *__restrict__ pre,
-              uint32_t *__restrict__ status, RootTables rt) {
+              uint32_t *__restrict__ status, RootTablesT<typename F::T> rt) {
+    using T = typename F::T;
     constexpr int L = 1 << LG;
-    extern __shared__ uint64_t smem[];
-    uint64_t *sA = smem;
-    uint64_t *sB = smem + sp_size(L);
-    uint64_t *tw = sB + sp_size(L);
+    const T linv = (T)linv_;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    T *sA = reinterpret_cast<T *>(smem_raw);
+    T *sB = sA + sp_size(L);
+    T *tw = sB + sp_size(L);
     load_roots<LG>(tw, rt.small);
     for (int i = threadIdx.x; i < L; i += kThreads) {
-        sA[sp(i)] = amap.get(i);
-        sB[sp(i)] = bmap.get(i);
+        sA[sp(i)] = (T)amap.get(i);
+        sB[sp(i)] = (T)bmap.get(i);
     }
     __syncthreads();
-    ntt_fwd<LG, 0, 2>(sA, sB, tw);
-    for (int i = threadIdx.x; i < L; i += kThreads)
-        sA[sp(i)] = gl_mul(gl_mul(sA[sp(i)], sB[sp(i)]), linv);
+    ntt_fwd_f<F, LG, 0, 2>(sA, sB, tw);
+    for (int i = threadIdx.x; i < L; i += kThreads) sA[sp(i)] = F::prod(sA[sp(i)], sB[sp(i)], linv);
     __syncthreads();
-    ntt_inv<LG, 0, 1>(sA, sA, tw);
+    ntt_inv_f<F, LG, 0, 1>(sA, sA, tw);
 
     const bool bad = pre && (pre[0] == 0u || pre[1] == 0u);
     if (bad && threadIdx.x == 0) atomicOr(status, kFlagPrecond);
@@ -72,17 +75,19 @@ k_fused_small(BitMap amap, BitMap bmap, uint64_t lo, uint64_t m, uint64_t linv,
 }
 
 // ---------------------------------------------------------------------------
-// One column pass over tiles of R = 2^LOGR rows x C = 2^(kTileLg - LOGR) columns.
+// One column pass over tiles of R = 2^LOGR rows x C = 2^F::ncol_lg(LOGR) columns.
 // ---------------------------------------------------------------------------
-template <int LOGR, bool INV, bool BITS_IN, bool PARITY_OUT>
+template <class F, int LOGR, bool INV, bool BITS_IN, bool PARITY_OUT>
 __global__ void __launch_bounds__(kThreads, 1)
-k_pass(uint64_t *__restrict__ data, BitMap map, int lgN, int lgS, uint8_t *__restrict__ par,
-       uint64_t lo, uint64_t m, RootTables rt) {
+k_pass(typename F::T *__restrict__ data, BitMap map, int lgN, int lgS, uint8_t *__restrict__ par,
+       uint64_t lo, uint64_t m, RootTablesT<typename F::T> rt) {
+    using T = typename F::T;
     constexpr int R = 1 << LOGR;
-    constexpr int NCOL_LG = kTileLg - LOGR;
+    constexpr int NCOL_LG = F::ncol_lg(LOGR);
     constexpr int C = 1 << NCOL_LG;
-    extern __shared__ uint64_t smem[];
-    uint64_t *tw = smem + sp_size(R * C);
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    T *smem = reinterpret_cast<T *>(smem_raw);
+    T *tw = smem + sp_size(R * C);
     load_roots<LOGR>(tw, rt.small);
     const uint64_t S = 1ull << lgS;
     const uint64_t tiles_per_blk = S >> NCOL_LG;
@@ -90,7 +95,7 @@ k_pass(uint64_t *__restrict__ data, BitMap map, int lgN, int lgS, uint8_t *__res
     const uint64_t blk = tile / tiles_per_blk;
     const uint64_t col0 = (tile - blk * tiles_per_blk) << NCOL_LG;
     const uint64_t base = (blk << lgN) + col0;
-    const int esh = 32 - lgN;  // omega_N = g^(2^(32 - lgN))
+    const int esh = F::kAdicity - lgN;  // omega_N = g^(2^(adicity - lgN))
 
     // rows are stored in the digit-reversed order of the on-chip transform:
     // row p of the tile holds frequency pos_to_freq(p) (forward) and is read
@@ -99,29 +104,29 @@ k_pass(uint64_t *__restrict__ data, BitMap map, int lgN, int lgS, uint8_t *__res
     for (int e = threadIdx.x; e < R * C; e += kThreads) {
         const int i = e >> NCOL_LG, c = e & (C - 1);
         const uint64_t g = base + ((uint64_t)i << lgS) + c;
-        uint64_t v = BITS_IN ? map.get(g) : data[g];
+        T v = BITS_IN ? (T)map.get(g) : data[g];
         if (INV) {
             const uint64_t k = pos_to_freq<LOGR>(i);
             const uint32_t E = (uint32_t)(((col0 + c) * k) << esh);
-            if (E) v = gl_mul(v, big_root(rt.big_lo_inv, rt.big_hi_inv, E));
+            if (E) v = F::twmul(v, big_root_f<F>(rt.big_lo_inv, rt.big_hi_inv, E));
         }
         smem[sp(e)] = v;
     }
     __syncthreads();
     if (INV) {
-        ntt_inv<LOGR, NCOL_LG, 1>(smem, smem, tw);
+        ntt_inv_f<F, LOGR, NCOL_LG, 1>(smem, smem, tw);
     } else {
-        ntt_fwd<LOGR, NCOL_LG, 1>(smem, smem, tw);
+        ntt_fwd_f<F, LOGR, NCOL_LG, 1>(smem, smem, tw);
     }
 #pragma unroll 4
     for (int e = threadIdx.x; e < R * C; e += kThreads) {
         const int i = e >> NCOL_LG, c = e & (C - 1);
-        uint64_t v = smem[sp(e)];
+        T v = smem[sp(e)];
         const uint64_t g = base + ((uint64_t)i << lgS) + c;
         if (!INV) {
             const uint64_t k = pos_to_freq<LOGR>(i);
             const uint32_t E = (uint32_t)(((col0 + c) * k) << esh);
-            if (E) v = gl_mul(v, big_root(rt.big_lo_fwd, rt.big_hi_fwd, E));
+            if (E) v = F::twmul(v, big_root_f<F>(rt.big_lo_fwd, rt.big_hi_fwd, E));
         }
         if (PARITY_OUT) {
             const uint64_t p = g - lo;

@@ -9,33 +9,60 @@ namespace cm {
 // ---------------------------------------------------------------------------
 // Fused middle: rows of B = 2^13 contiguous elements of both operands.
 // ---------------------------------------------------------------------------
+// 16 bytes as 2 x 64-bit or 4 x 32-bit elements, and back.
+__device__ __forceinline__ void unpack16(uint4 v, uint64_t (&o)[2]) {
+    o[0] = ((uint64_t)v.y << 32) | v.x;
+    o[1] = ((uint64_t)v.w << 32) | v.z;
+}
+__device__ __forceinline__ void unpack16(uint4 v, uint32_t (&o)[4]) {
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+}
+__device__ __forceinline__ uint4 pack16(const uint64_t (&o)[2]) {
+    return make_uint4((uint32_t)o[0], (uint32_t)(o[0] >> 32), (uint32_t)o[1], (uint32_t)(o[1] >> 32));
+}
+__device__ __forceinline__ uint4 pack16(const uint32_t (&o)[4]) { return make_uint4(o[0], o[1], o[2], o[3]); }
+
+template <class F>
 __global__ void __launch_bounds__(kThreads, 1)
-k_middle(uint64_t *__restrict__ A, const uint64_t *__restrict__ Bv, uint64_t nrows, uint64_t linv,
-         RootTables rt) {
+k_middle(typename F::T *__restrict__ A, const typename F::T *__restrict__ Bv, uint64_t nrows, uint64_t linv_,
+         RootTablesT<typename F::T> rt) {
+    using T = typename F::T;
     constexpr int LG = kMidLgMax;
     constexpr int Bn = 1 << LG;
-    extern __shared__ uint64_t smem[];
-    uint64_t *sA = smem;
-    uint64_t *sB = smem + sp_size(Bn);
-    uint64_t *tw = sB + sp_size(Bn);
+    constexpr int PER = 16 / sizeof(T);  // elements per 16-byte access
+    const T linv = (T)linv_;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    T *sA = reinterpret_cast<T *>(smem_raw);
+    T *sB = sA + sp_size(Bn);
+    T *tw = sB + sp_size(Bn);
     load_roots<LG>(tw, rt.small);
     // persistent: each CTA walks rows blockIdx.x, blockIdx.x + gridDim.x, ...
     for (uint64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
         const uint64_t row = r << LG;
-        const ulonglong2 *a2 = reinterpret_cast<const ulonglong2 *>(A + row);
-        const ulonglong2 *b2 = reinterpret_cast<const ulonglong2 *>(Bv + row);
-        for (int i = threadIdx.x; i < Bn / 2; i += kThreads) {
-            const ulonglong2 va = a2[i], vb = __ldg(b2 + i);
-            sA[sp(2 * i)] = va.x;
-            sA[sp(2 * i + 1)] = va.y;
-            sB[sp(2 * i)] = vb.x;
-            sB[sp(2 * i + 1)] = vb.y;
+        const uint4 *a4 = reinterpret_cast<const uint4 *>(A + row);
+        const uint4 *b4 = reinterpret_cast<const uint4 *>(Bv + row);
+        for (int i = threadIdx.x; i < Bn / PER; i += kThreads) {
+            T pa[PER], pb[PER];
+            unpack16(a4[i], pa);
+            unpack16(__ldg(b4 + i), pb);
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                sA[sp(PER * i + j)] = pa[j];
+                sB[sp(PER * i + j)] = pb[j];
+            }
         }
         __syncthreads();
-        middle_row_13(sA, sB, tw, linv);
-        ulonglong2 *o2 = reinterpret_cast<ulonglong2 *>(A + row);
-        for (int i = threadIdx.x; i < Bn / 2; i += kThreads)
-            o2[i] = make_ulonglong2(sA[sp(2 * i)], sA[sp(2 * i + 1)]);
+        middle_row_13_f<F>(sA, sB, tw, linv);
+        uint4 *o4 = reinterpret_cast<uint4 *>(A + row);
+        for (int i = threadIdx.x; i < Bn / PER; i += kThreads) {
+            T pv[PER];
+#pragma unroll
+            for (int j = 0; j < PER; ++j) pv[j] = sA[sp(PER * i + j)];
+            o4[i] = pack16(pv);
+        }
         __syncthreads();
     }
 }
@@ -82,18 +109,28 @@ __global__ void k_allsame(const uint64_t *__restrict__ x, uint64_t n, uint32_t *
 }
 
 cudaError_t launch_pass(const PassArgs &a, int logr, cudaStream_t st) {
+    if (a.field == kFieldF30) return a.inv ? launch_pass_inv30(a, logr, st) : launch_pass_fwd30(a, logr, st);
     return a.inv ? launch_pass_inv(a, logr, st) : launch_pass_fwd(a, logr, st);
 }
 
-cudaError_t launch_middle(uint64_t *A, const uint64_t *B, uint64_t L, uint64_t linv,
-                          const RootTables &rt, int nsm, cudaStream_t st) {
-    const size_t sm = (2 * sp_size(1 << kMidLgMax) + (1 << kMidLgMax)) * sizeof(uint64_t);
-    cudaError_t e = cudaFuncSetAttribute(k_middle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+template <class F>
+static cudaError_t launch_middle_f(void *A, const void *B, uint64_t L, uint64_t linv,
+                                   const RootTablesT<typename F::T> &rt, int nsm, cudaStream_t st) {
+    using T = typename F::T;
+    const size_t sm = (2 * sp_size(1 << kMidLgMax) + (1 << kMidLgMax)) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(k_middle<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const uint64_t rows = L >> kMidLgMax;
     const uint64_t grid = rows < (uint64_t)nsm ? rows : (uint64_t)nsm;
-    k_middle<<<(unsigned)grid, kThreads, sm, st>>>(A, B, rows, linv, rt);
+    k_middle<F><<<(unsigned)grid, kThreads, sm, st>>>(static_cast<T *>(A), static_cast<const T *>(B), rows, linv,
+                                                      rt);
     return cudaGetLastError();
+}
+
+cudaError_t launch_middle(int field, void *A, const void *B, uint64_t L, uint64_t linv, const RootTables &rt,
+                          const RootTables30 &rt30, int nsm, cudaStream_t st) {
+    return field == kFieldF30 ? launch_middle_f<FieldF30>(A, B, L, linv, rt30, nsm, st)
+                              : launch_middle_f<FieldGL>(A, B, L, linv, rt, nsm, st);
 }
 
 cudaError_t launch_pack(const uint8_t *par, uint64_t m, uint64_t *z, const uint32_t *pre,
@@ -163,6 +200,23 @@ __global__ void k_field_selftest(uint64_t count, uint64_t seed, unsigned long lo
     n += gl_mul_ptx(a, b) != gl_mul_c(a, b);
 #pragma unroll
     for (int s = 0; s <= 96; ++s) n += gl_shl_ptx(a, s) != gl_shl_c(a, s);
+    // the 32-bit field against plain 64-bit modular arithmetic
+    const uint32_t e30[8] = {0u, 1u, 2u, F30_Q - 1, F30_Q - 2, 0x80000000u, 0x7FFFFFFFu, F30_R};
+    uint32_t a3 = (uint32_t)(a % F30_Q), b3 = (uint32_t)(b % F30_Q);
+    if (i < 64) {
+        a3 = e30[i % 8];
+        b3 = e30[i / 8];
+    }
+    constexpr uint32_t rinv = f30_pow(F30_R, F30_Q - 2);
+    n += f30_add(a3, b3) != (uint32_t)(((uint64_t)a3 + b3) % F30_Q);
+    n += f30_sub(a3, b3) != (uint32_t)(((uint64_t)a3 + F30_Q - b3) % F30_Q);
+    n += f30_mont(a3, b3) != f30_mulmod(f30_mulmod(a3, b3), rinv);
+    const uint32_t w32 = f30_pow(F30_G30, 1ull << 25);
+    uint32_t wj = 1;
+    for (int j = 0; j < 32; ++j) {
+        n += f30_mont(a3, kF30Tw32[j]) != f30_mulmod(a3, wj);
+        wj = f30_mulmod(wj, w32);
+    }
     if (n) atomicAdd(bad, n);
 }
 

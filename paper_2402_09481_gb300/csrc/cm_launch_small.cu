@@ -6,14 +6,19 @@
 
 namespace cm {
 
-template <int LG>
-static cudaError_t launch_small_lg(const Launch &q) {
-    const size_t sm = (2 * sp_size(1 << LG) + (1 << LG)) * sizeof(uint64_t);
-    auto kern = k_fused_small<LG>;
+template <class F, int LG>
+static cudaError_t launch_small_f(const Launch &q, const RootTablesT<typename F::T> &rt) {
+    const size_t sm = (2 * sp_size(1 << LG) + (1 << LG)) * sizeof(typename F::T);
+    auto kern = k_fused_small<F, LG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    kern<<<1, kThreads, sm, q.stream>>>(q.amap, q.bmap, q.lo, q.m, q.linv, q.z, q.pre, q.status, q.rt);
+    kern<<<1, kThreads, sm, q.stream>>>(q.amap, q.bmap, q.lo, q.m, q.linv, q.z, q.pre, q.status, rt);
     return cudaGetLastError();
+}
+
+template <int LG>
+static cudaError_t launch_small_lg(const Launch &q) {
+    return q.field == kFieldF30 ? launch_small_f<FieldF30, LG>(q, q.rt30) : launch_small_f<FieldGL, LG>(q, q.rt);
 }
 
 cudaError_t launch_small(const Launch &q, int lg) {

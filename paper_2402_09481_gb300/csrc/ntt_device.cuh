@@ -9,6 +9,7 @@
 // are read out of the packed input bits (see BitMap).
 #pragma once
 #include <stdint.h>
+#include "f30.cuh"
 #include "gl.cuh"
 
 namespace cm {
@@ -28,17 +29,66 @@ __device__ __forceinline__ int sp(int i) { return i + (i >> 5); }
 __device__ __forceinline__ int tw_swz(int e) { return e ^ (((e >> 5) ^ (e >> 9)) & 15); }
 __host__ __device__ constexpr int sp_size(int n) { return n + (n >> 5) + 1; }
 
-struct RootTables {
-    const uint64_t *small;       // omega_{8192}^e,  e < 8192
-    const uint64_t *big_lo_fwd;  // g^e,            e < 2^16, g of order 2^32
-    const uint64_t *big_hi_fwd;  // g^(2^16 e),     e < 2^16
-    const uint64_t *big_lo_inv;
-    const uint64_t *big_hi_inv;
+// Resident root tables of one field (element type T).  Goldilocks: g of order
+// 2^32, 2^16-entry halves; F30: g of order 2^30, 2^15-entry halves, entries in
+// Montgomery form.
+template <class T>
+struct RootTablesT {
+    const T *small;       // omega_{8192}^e,  e < 8192
+    const T *big_lo_fwd;  // g^e,             e < 2^kBigLg
+    const T *big_hi_fwd;  // g^(2^kBigLg e),  e < 2^kBigLg
+    const T *big_lo_inv;
+    const T *big_hi_inv;
+};
+using RootTables = RootTablesT<uint64_t>;
+using RootTables30 = RootTablesT<uint32_t>;
+
+// ---------------------------------------------------------------------------
+// Field policies.  Every transform below is written once over a policy F:
+//   FieldGL  -- Goldilocks p = 2^64 - 2^32 + 1, 64-bit words, every L <= 2^32;
+//              the root of order 64 is 8 = 2^3, so register sub-transforms
+//              twiddle by shifts;
+//   FieldF30 -- q = 3 * 2^30 + 1 (the paper's small field), 32-bit words,
+//              L <= 2^30; Montgomery products with constant twiddles.
+// ---------------------------------------------------------------------------
+struct FieldGL {
+    using T = uint64_t;
+    static constexpr int kAdicity = 32;
+    static constexpr int kBigLg = 16;
+    // columns of a column-pass tile of 2^LOGR rows: 2^14 elements (32-byte rows
+    // for LOGR = 12)
+    static constexpr int ncol_lg(int logr) { return kTileLg - logr; }
+    __device__ static __forceinline__ T add(T a, T b) { return gl_add(a, b); }
+    __device__ static __forceinline__ T sub(T a, T b) { return gl_sub(a, b); }
+    __device__ static __forceinline__ T twmul(T x, T w) { return gl_mul(x, w); }
+    // x omega_{2h}^pos, h = 2^lh <= 16: omega_{2h} = 2^(96 / h)
+    __device__ static __forceinline__ T rot(T x, int lh, int pos) { return gl_shl(x, (96 >> lh) * pos); }
+    __device__ static __forceinline__ T prod(T a, T b, T linv) { return gl_mul(gl_mul(a, b), linv); }
 };
 
-// g^(E) for E < 2^32, g the fixed root of order 2^32.
+struct FieldF30 {
+    using T = uint32_t;
+    static constexpr int kAdicity = 30;
+    static constexpr int kBigLg = 15;
+    // 2^15-element tiles, so that a row of the tile still spans a whole 32-byte
+    // sector; 2^14 when R = 2 (the single pass of L = 2^14 has columns 2^13 apart)
+    static constexpr int ncol_lg(int logr) { return logr == 1 ? 13 : 15 - logr; }
+    __device__ static __forceinline__ T add(T a, T b) { return f30_add(a, b); }
+    __device__ static __forceinline__ T sub(T a, T b) { return f30_sub(a, b); }
+    __device__ static __forceinline__ T twmul(T x, T w) { return f30_mont(x, w); }
+    __device__ static __forceinline__ T rot(T x, int lh, int pos) {
+        return pos == 0 ? x : f30_mont(x, kF30Tw32[(16 >> lh) * pos]);
+    }
+    __device__ static __forceinline__ T prod(T a, T b, T linv) { return f30_mont(f30_mont(a, b), linv); }
+};
+
+// g^E for E < 2^kAdicity, g the field's fixed root of maximal 2-power order.
+template <class F>
+__device__ __forceinline__ typename F::T big_root_f(const typename F::T *lo, const typename F::T *hi, uint32_t E) {
+    return F::twmul(__ldg(hi + (E >> F::kBigLg)), __ldg(lo + (E & ((1u << F::kBigLg) - 1))));
+}
 __device__ __forceinline__ uint64_t big_root(const uint64_t *lo, const uint64_t *hi, uint32_t E) {
-    return gl_mul(__ldg(hi + (E >> 16)), __ldg(lo + (E & 0xFFFFu)));
+    return big_root_f<FieldGL>(lo, hi, E);
 }
 
 // ---------------------------------------------------------------------------
@@ -108,10 +158,10 @@ __device__ __forceinline__ int bitrev_c(int k, int lg) {
     return r;
 }
 
-// In-register DFT of length 2^LQ <= 32 with omega = 2^(192 / 2^LQ):
+// In-register DFT of length 2^LQ <= 32 (Goldilocks: omega = 2^(192 / 2^LQ)):
 // natural order in, v[bitrev(k)] = X[k] out.
-template <int LQ>
-__device__ __forceinline__ void dft_reg(uint64_t *v) {
+template <class F, int LQ>
+__device__ __forceinline__ void dft_reg_f(typename F::T *v) {
     constexpr int RD = 1 << LQ;
     // one flat loop with a constant trip count, so that every index and shift
     // below is a compile-time constant after unrolling
@@ -121,42 +171,50 @@ __device__ __forceinline__ void dft_reg(uint64_t *v) {
         const int h = 1 << lh;
         const int b = j % (RD / 2);
         const int pos = b % h, blk = (b / h) * 2 * h;
-        const uint64_t a = v[blk + pos], c = v[blk + pos + h];
-        v[blk + pos] = gl_add(a, c);
-        v[blk + pos + h] = gl_shl(gl_sub(a, c), (96 >> lh) * pos);
+        const typename F::T a = v[blk + pos], c = v[blk + pos + h];
+        v[blk + pos] = F::add(a, c);
+        v[blk + pos + h] = F::rot(F::sub(a, c), lh, pos);
     }
 }
+template <int LQ>
+__device__ __forceinline__ void dft_reg(uint64_t *v) { dft_reg_f<FieldGL, LQ>(v); }
 
 // Forward step J over NBUF buffers; tw[e] = omega_R^e, e < R.
-template <int LOGR, int J, int NCOL_LG, int NBUF>
-__device__ __forceinline__ void fwd_step(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
+template <class F, int LOGR, int J, int NCOL_LG, int NBUF>
+__device__ __forceinline__ void fwd_step_f(typename F::T *s0, typename F::T *s1, const typename F::T *tw) {
+    using T = typename F::T;
     constexpr int OFF = st_off(LOGR, J), LQ = st_q(LOGR, J), RD = 1 << LQ;
     constexpr int LN = LOGR - OFF, LM = LN - LQ;
     constexpr int ITEMS = (1 << (LOGR - LQ)) << NCOL_LG;
     for (int item = threadIdx.x; item < ITEMS * NBUF; item += kThreads) {
         const int bi = item / ITEMS;
         const int it = item - bi * ITEMS;
-        uint64_t *s = (NBUF == 2 && bi) ? s1 : s0;
+        T *s = (NBUF == 2 && bi) ? s1 : s0;
         const int c = it & ((1 << NCOL_LG) - 1);
         const int rest = it >> NCOL_LG;
         const int i2 = rest & ((1 << LM) - 1);
         const int row0 = ((rest >> LM) << LN) + i2;
-        uint64_t v[RD];
+        T v[RD];
 #pragma unroll
         for (int i1 = 0; i1 < RD; ++i1) v[i1] = s[sp(((row0 + (i1 << LM)) << NCOL_LG) + c)];
-        dft_reg<LQ>(v);
+        dft_reg_f<F, LQ>(v);
 #pragma unroll
         for (int k1 = 0; k1 < RD; ++k1) {
-            uint64_t x = v[bitrev_c(k1, LQ)];
-            if (LM > 0 && k1 > 0 && i2 > 0) x = gl_mul(x, tw[tw_swz((i2 * k1) << OFF)]);
+            T x = v[bitrev_c(k1, LQ)];
+            if (LM > 0 && k1 > 0 && i2 > 0) x = F::twmul(x, tw[tw_swz((i2 * k1) << OFF)]);
             s[sp(((row0 + (k1 << LM)) << NCOL_LG) + c)] = x;
         }
     }
 }
+template <int LOGR, int J, int NCOL_LG, int NBUF>
+__device__ __forceinline__ void fwd_step(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
+    fwd_step_f<FieldGL, LOGR, J, NCOL_LG, NBUF>(s0, s1, tw);
+}
 
 // Exact inverse of fwd_step J (up to the factor RD), inverse roots.
-template <int LOGR, int J, int NCOL_LG, int NBUF>
-__device__ __forceinline__ void inv_step(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
+template <class F, int LOGR, int J, int NCOL_LG, int NBUF>
+__device__ __forceinline__ void inv_step_f(typename F::T *s0, typename F::T *s1, const typename F::T *tw) {
+    using T = typename F::T;
     constexpr int R = 1 << LOGR;
     constexpr int OFF = st_off(LOGR, J), LQ = st_q(LOGR, J), RD = 1 << LQ;
     constexpr int LN = LOGR - OFF, LM = LN - LQ;
@@ -164,52 +222,64 @@ __device__ __forceinline__ void inv_step(uint64_t *s0, uint64_t *s1, const uint6
     for (int item = threadIdx.x; item < ITEMS * NBUF; item += kThreads) {
         const int bi = item / ITEMS;
         const int it = item - bi * ITEMS;
-        uint64_t *s = (NBUF == 2 && bi) ? s1 : s0;
+        T *s = (NBUF == 2 && bi) ? s1 : s0;
         const int c = it & ((1 << NCOL_LG) - 1);
         const int rest = it >> NCOL_LG;
         const int i2 = rest & ((1 << LM) - 1);
         const int row0 = ((rest >> LM) << LN) + i2;
-        uint64_t v[RD];
+        T v[RD];
 #pragma unroll
         for (int k1 = 0; k1 < RD; ++k1) {
-            uint64_t x = s[sp(((row0 + (k1 << LM)) << NCOL_LG) + c)];
-            if (LM > 0 && k1 > 0 && i2 > 0) x = gl_mul(x, tw[tw_swz((R - ((i2 * k1) << OFF)) & (R - 1))]);
+            T x = s[sp(((row0 + (k1 << LM)) << NCOL_LG) + c)];
+            if (LM > 0 && k1 > 0 && i2 > 0) x = F::twmul(x, tw[tw_swz((R - ((i2 * k1) << OFF)) & (R - 1))]);
             v[k1] = x;
         }
-        dft_reg<LQ>(v);
+        dft_reg_f<F, LQ>(v);
         // inverse DFT output i1 is the forward output at frequency -i1 mod RD
 #pragma unroll
         for (int i1 = 0; i1 < RD; ++i1)
             s[sp(((row0 + (i1 << LM)) << NCOL_LG) + c)] = v[bitrev_c((RD - i1) & (RD - 1), LQ)];
     }
 }
-
 template <int LOGR, int J, int NCOL_LG, int NBUF>
-__device__ __forceinline__ void fwd_from(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
+__device__ __forceinline__ void inv_step(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
+    inv_step_f<FieldGL, LOGR, J, NCOL_LG, NBUF>(s0, s1, tw);
+}
+
+template <class F, int LOGR, int J, int NCOL_LG, int NBUF>
+__device__ __forceinline__ void fwd_from(typename F::T *s0, typename F::T *s1, const typename F::T *tw) {
     if constexpr (J < st_n(LOGR)) {
-        fwd_step<LOGR, J, NCOL_LG, NBUF>(s0, s1, tw);
+        fwd_step_f<F, LOGR, J, NCOL_LG, NBUF>(s0, s1, tw);
         __syncthreads();
-        fwd_from<LOGR, J + 1, NCOL_LG, NBUF>(s0, s1, tw);
+        fwd_from<F, LOGR, J + 1, NCOL_LG, NBUF>(s0, s1, tw);
     }
 }
-template <int LOGR, int J, int NCOL_LG, int NBUF>
-__device__ __forceinline__ void inv_from(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
+template <class F, int LOGR, int J, int NCOL_LG, int NBUF>
+__device__ __forceinline__ void inv_from(typename F::T *s0, typename F::T *s1, const typename F::T *tw) {
     if constexpr (J >= 0) {
-        inv_step<LOGR, J, NCOL_LG, NBUF>(s0, s1, tw);
+        inv_step_f<F, LOGR, J, NCOL_LG, NBUF>(s0, s1, tw);
         __syncthreads();
-        inv_from<LOGR, J - 1, NCOL_LG, NBUF>(s0, s1, tw);
+        inv_from<F, LOGR, J - 1, NCOL_LG, NBUF>(s0, s1, tw);
     }
 }
 
 // Forward transform of every column (natural -> digit-reversed); ends with a barrier.
-template <int LOGR, int NCOL_LG, int NBUF>
-__device__ __forceinline__ void ntt_fwd(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
-    if constexpr (LOGR > 0) fwd_from<LOGR, 0, NCOL_LG, NBUF>(s0, s1, tw);
+template <class F, int LOGR, int NCOL_LG, int NBUF>
+__device__ __forceinline__ void ntt_fwd_f(typename F::T *s0, typename F::T *s1, const typename F::T *tw) {
+    if constexpr (LOGR > 0) fwd_from<F, LOGR, 0, NCOL_LG, NBUF>(s0, s1, tw);
 }
 // Inverse of ntt_fwd up to the factor R (digit-reversed -> natural); ends with a barrier.
+template <class F, int LOGR, int NCOL_LG, int NBUF>
+__device__ __forceinline__ void ntt_inv_f(typename F::T *s0, typename F::T *s1, const typename F::T *tw) {
+    if constexpr (LOGR > 0) inv_from<F, LOGR, st_n(LOGR) - 1, NCOL_LG, NBUF>(s0, s1, tw);
+}
+template <int LOGR, int NCOL_LG, int NBUF>
+__device__ __forceinline__ void ntt_fwd(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
+    ntt_fwd_f<FieldGL, LOGR, NCOL_LG, NBUF>(s0, s1, tw);
+}
 template <int LOGR, int NCOL_LG, int NBUF>
 __device__ __forceinline__ void ntt_inv(uint64_t *s0, uint64_t *s1, const uint64_t *tw) {
-    if constexpr (LOGR > 0) inv_from<LOGR, st_n(LOGR) - 1, NCOL_LG, NBUF>(s0, s1, tw);
+    ntt_inv_f<FieldGL, LOGR, NCOL_LG, NBUF>(s0, s1, tw);
 }
 
 // One fused middle row of B = 2^13 elements (steps of radix 32, 16, 16): forward
@@ -219,34 +289,40 @@ __device__ __forceinline__ void ntt_inv(uint64_t *s0, uint64_t *s1, const uint64
 // 16-row groups (thread t owns rows 16t .. 16t + 15 of both operands), and
 // steps 1 and 2 only touch the 256-row blocks of the calling warp, so they are
 // separated by warp barriers only.  Ends with a block barrier.
-__device__ __forceinline__ void middle_row_13(uint64_t *sA, uint64_t *sB, const uint64_t *tw, uint64_t linv) {
+template <class F>
+__device__ __forceinline__ void middle_row_13_f(typename F::T *sA, typename F::T *sB, const typename F::T *tw,
+                                                typename F::T linv) {
+    using T = typename F::T;
     static_assert(st_n(13) == 3 && st_q(13, 0) == 5 && st_q(13, 1) == 4 && st_q(13, 2) == 4, "schedule");
     static_assert(kThreads == 512, "one 16-row group per thread in the fused step");
-    fwd_step<13, 0, 0, 2>(sA, sB, tw);
+    fwd_step_f<F, 13, 0, 0, 2>(sA, sB, tw);
     __syncthreads();
-    fwd_step<13, 1, 0, 2>(sA, sB, tw);
+    fwd_step_f<F, 13, 1, 0, 2>(sA, sB, tw);
     __syncwarp();
     {
         const int row0 = threadIdx.x << 4;
-        uint64_t a[16], b[16], c[16];
+        T a[16], b[16], c[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) a[i] = sA[sp(row0 + i)];
 #pragma unroll
         for (int i = 0; i < 16; ++i) b[i] = sB[sp(row0 + i)];
-        dft_reg<4>(a);
-        dft_reg<4>(b);
+        dft_reg_f<F, 4>(a);
+        dft_reg_f<F, 4>(b);
         // frequency k sits in register bitrev(k); the inverse step takes frequency order
 #pragma unroll
-        for (int k = 0; k < 16; ++k) c[k] = gl_mul(gl_mul(a[bitrev_c(k, 4)], b[bitrev_c(k, 4)]), linv);
-        dft_reg<4>(c);
+        for (int k = 0; k < 16; ++k) c[k] = F::prod(a[bitrev_c(k, 4)], b[bitrev_c(k, 4)], linv);
+        dft_reg_f<F, 4>(c);
 #pragma unroll
         for (int i = 0; i < 16; ++i) sA[sp(row0 + i)] = c[bitrev_c((16 - i) & 15, 4)];
     }
     __syncwarp();
-    inv_step<13, 1, 0, 1>(sA, sA, tw);
+    inv_step_f<F, 13, 1, 0, 1>(sA, sA, tw);
     __syncthreads();
-    inv_step<13, 0, 0, 1>(sA, sA, tw);
+    inv_step_f<F, 13, 0, 0, 1>(sA, sA, tw);
     __syncthreads();
+}
+__device__ __forceinline__ void middle_row_13(uint64_t *sA, uint64_t *sB, const uint64_t *tw, uint64_t linv) {
+    middle_row_13_f<FieldGL>(sA, sB, tw, linv);
 }
 
 // Frequency held at position p after ntt_fwd<LOGR>: the digits k_j of p (step 0
@@ -263,8 +339,8 @@ __device__ __forceinline__ uint32_t pos_to_freq(uint32_t p) {
 }
 
 // Fill tw[e] = omega_R^e (e < R) from the global table of omega_8192^e.
-template <int LOGR>
-__device__ __forceinline__ void load_roots(uint64_t *tw, const uint64_t *__restrict__ g8192) {
+template <int LOGR, class T>
+__device__ __forceinline__ void load_roots(T *tw, const T *__restrict__ g8192) {
     for (int e = threadIdx.x; e < (1 << LOGR); e += kThreads) tw[tw_swz(e)] = __ldg(g8192 + (e << (kSmallLg - LOGR)));
 }
 

@@ -77,6 +77,7 @@ TREVISAN = 3
 MODEL_SEEDED, MODEL_PRODUCT, MODEL_MARKOV = 0, 1, 2
 ADV_CLASSICAL, ADV_QUANTUM = 0, 1
 ADJUST_UP, ADJUST_DOWN, ADJUST_CLOSEST = 0, 1, 2
+FIELD_AUTO, FIELD_GOLDILOCKS = 0, 1
 
 
 class ParamPlan(ctypes.Structure):
@@ -274,12 +275,13 @@ def _dev_words(t, nbits: int, name: str):
 class Context:
     """A libcm context on one CUDA device."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_transform_lg: int = 0):
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_transform_lg: int = 0, field: int = 0):
         import torch
         self.device = device
         torch.cuda.set_device(device)
         self._L = lib()
-        opts = (ctypes.c_uint64 * 5)(hbm_budget_bytes, int(max_transform_lg), 0, 0, 0)
+        # cm_options: budget, then max_transform_lg and field as two 32-bit words
+        opts = (ctypes.c_uint64 * 5)(hbm_budget_bytes, int(max_transform_lg) | (int(field) << 32), 0, 0, 0)
         h = ctypes.c_void_p()
         _check(self._L.cm_create(ctypes.byref(h), device, ctypes.cast(opts, ctypes.c_void_p)),
                "cm_create")

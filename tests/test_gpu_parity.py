@@ -200,3 +200,52 @@ def test_field_selftest_device_arithmetic(cm_ctx):
     # the PTX carry-chain arithmetic against the C forms (which the CPU test
     # pins to 128-bit integers), on edge values and 4M random pairs
     assert native.field_selftest(0, 1 << 22, 12345) == 0
+
+
+# --------------------------------------------------------------------------- #
+# The single calls take the 32-bit field of 3 * 2^30 + 1 for transforms up to
+# 2^30 and Goldilocks above; a context with CM_FIELD_GOLDILOCKS keeps the
+# 64-bit field at every length.  Both must give the oracle's bits.
+@pytest.fixture(scope="module")
+def gl_ctx():
+    from paper_2402_09481_gb300 import build
+    build.build()
+    c = native.Context(0, field=native.FIELD_GOLDILOCKS)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("kind,n,m", [
+    (native.TOEPLITZ, 5, 3), (native.TOEPLITZ, 5000, 4000), (native.TOEPLITZ, 100000, 31073),
+    (native.TOEPLITZ, 2 ** 20, 2 ** 19 + 3),
+    (native.CIRCULANT, "P131101", 0.5), (native.DODIS, "P40000", 0.4), (native.DODIS, "P3000", 0.9),
+])
+def test_both_fields_match_oracle(gl_ctx, cm_ctx, kind, n, m):
+    if isinstance(n, str):
+        P = oracle.next_na(int(n[1:]))
+        n = P - 1 if kind == native.CIRCULANT else P
+        m = max(1, int(m * n))
+    xw = inputs.bernoulli_half(700 + n % 89, n)
+    if kind == native.DODIS:
+        xw[0] = (xw[0] | np.uint64(1)) & ~np.uint64(2)
+    yb = n + m - 1 if kind == native.TOEPLITZ else (n + 1 if kind == native.CIRCULANT else n)
+    yw = inputs.bernoulli_half(701 + n % 83, yb)
+    outs = []
+    for ctx in (gl_ctx, cm_ctx):
+        x, y = to_dev(xw), to_dev(yw)
+        if kind == native.TOEPLITZ:
+            z = ctx.toeplitz(x, n, y, m)
+        elif kind == native.CIRCULANT:
+            z = ctx.circulant(x, n, y, m)
+        else:
+            z = ctx.dodis(x, y, n, m)
+        outs.append(from_dev(z))
+    if m <= 131100:
+        want = {native.TOEPLITZ: lambda: oracle.toeplitz_packed(xw, n, yw, m),
+                native.CIRCULANT: lambda: oracle.circulant_packed(xw, n, yw, m),
+                native.DODIS: lambda: oracle.dodis_packed(xw, yw, n, m)}[kind]()
+        assert (outs[0] == want).all()
+    else:
+        rows = sample_rows(m)
+        assert (out_bits(outs[0], m, rows) == oracle.toeplitz_rows(xw, n, yw, m, rows)).all()
+    assert (outs[0] == outs[1]).all()
