@@ -78,7 +78,7 @@ k_fused_small(BitMap amap, BitMap bmap, uint64_t lo, uint64_t m, uint64_t linv_,
 // One column pass over tiles of R = 2^LOGR rows x C = 2^F::ncol_lg(LOGR) columns.
 // ---------------------------------------------------------------------------
 template <class F, int LOGR, bool INV, bool BITS_IN, bool PARITY_OUT>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, sizeof(typename F::T) == 4 ? 2 : 1)
 k_pass(typename F::T *__restrict__ data, BitMap map, int lgN, int lgS, uint8_t *__restrict__ par,
        uint64_t lo, uint64_t m, RootTablesT<typename F::T> rt) {
     using T = typename F::T;
@@ -99,18 +99,32 @@ k_pass(typename F::T *__restrict__ data, BitMap map, int lgN, int lgS, uint8_t *
 
     // rows are stored in the digit-reversed order of the on-chip transform:
     // row p of the tile holds frequency pos_to_freq(p) (forward) and is read
-    // back as such (inverse), so the pass twiddle uses that frequency.
+    // back as such (inverse), so the pass twiddle uses that frequency.  Each
+    // access moves 16 consecutive bytes of a tile row (VW elements).
+    constexpr int VW = 16 / (int)sizeof(T);
+    static_assert(C % VW == 0, "tile rows hold whole 16-byte vectors");
 #pragma unroll 4
-    for (int e = threadIdx.x; e < R * C; e += kThreads) {
-        const int i = e >> NCOL_LG, c = e & (C - 1);
+    for (int q = threadIdx.x; q < R * C / VW; q += kThreads) {
+        const int e0 = q * VW;
+        const int i = e0 >> NCOL_LG, c = e0 & (C - 1);
         const uint64_t g = base + ((uint64_t)i << lgS) + c;
-        T v = BITS_IN ? (T)map.get(g) : data[g];
+        T v[VW];
+        if (BITS_IN) {
+#pragma unroll
+            for (int j = 0; j < VW; ++j) v[j] = (T)map.get(g + j);
+        } else {
+            unpack16(*reinterpret_cast<const uint4 *>(data + g), v);
+        }
         if (INV) {
             const uint64_t k = pos_to_freq<LOGR>(i);
-            const uint32_t E = (uint32_t)(((col0 + c) * k) << esh);
-            if (E) v = F::twmul(v, big_root_f<F>(rt.big_lo_inv, rt.big_hi_inv, E));
+#pragma unroll
+            for (int j = 0; j < VW; ++j) {
+                const uint32_t E = (uint32_t)(((col0 + c + j) * k) << esh);
+                if (E) v[j] = F::twmul(v[j], big_root_f<F>(rt.big_lo_inv, rt.big_hi_inv, E));
+            }
         }
-        smem[sp(e)] = v;
+#pragma unroll
+        for (int j = 0; j < VW; ++j) smem[sp(e0 + j)] = v[j];
     }
     __syncthreads();
     if (INV) {
@@ -119,20 +133,29 @@ k_pass(typename F::T *__restrict__ data, BitMap map, int lgN, int lgS, uint8_t *
         ntt_fwd_f<F, LOGR, NCOL_LG, 1>(smem, smem, tw);
     }
 #pragma unroll 4
-    for (int e = threadIdx.x; e < R * C; e += kThreads) {
-        const int i = e >> NCOL_LG, c = e & (C - 1);
-        T v = smem[sp(e)];
+    for (int q = threadIdx.x; q < R * C / VW; q += kThreads) {
+        const int e0 = q * VW;
+        const int i = e0 >> NCOL_LG, c = e0 & (C - 1);
         const uint64_t g = base + ((uint64_t)i << lgS) + c;
+        T v[VW];
+#pragma unroll
+        for (int j = 0; j < VW; ++j) v[j] = smem[sp(e0 + j)];
         if (!INV) {
             const uint64_t k = pos_to_freq<LOGR>(i);
-            const uint32_t E = (uint32_t)(((col0 + c) * k) << esh);
-            if (E) v = F::twmul(v, big_root_f<F>(rt.big_lo_fwd, rt.big_hi_fwd, E));
+#pragma unroll
+            for (int j = 0; j < VW; ++j) {
+                const uint32_t E = (uint32_t)(((col0 + c + j) * k) << esh);
+                if (E) v[j] = F::twmul(v[j], big_root_f<F>(rt.big_lo_fwd, rt.big_hi_fwd, E));
+            }
         }
         if (PARITY_OUT) {
-            const uint64_t p = g - lo;
-            if (g >= lo && p < m) par[p] = (uint8_t)(v & 1u);
+#pragma unroll
+            for (int j = 0; j < VW; ++j) {
+                const uint64_t p = g + j - lo;
+                if (g + j >= lo && p < m) par[p] = (uint8_t)(v[j] & 1u);
+            }
         } else {
-            data[g] = v;
+            *reinterpret_cast<uint4 *>(data + g) = pack16(v);
         }
     }
 }

@@ -9,24 +9,8 @@ namespace cm {
 // ---------------------------------------------------------------------------
 // Fused middle: rows of B = 2^13 contiguous elements of both operands.
 // ---------------------------------------------------------------------------
-// 16 bytes as 2 x 64-bit or 4 x 32-bit elements, and back.
-__device__ __forceinline__ void unpack16(uint4 v, uint64_t (&o)[2]) {
-    o[0] = ((uint64_t)v.y << 32) | v.x;
-    o[1] = ((uint64_t)v.w << 32) | v.z;
-}
-__device__ __forceinline__ void unpack16(uint4 v, uint32_t (&o)[4]) {
-    o[0] = v.x;
-    o[1] = v.y;
-    o[2] = v.z;
-    o[3] = v.w;
-}
-__device__ __forceinline__ uint4 pack16(const uint64_t (&o)[2]) {
-    return make_uint4((uint32_t)o[0], (uint32_t)(o[0] >> 32), (uint32_t)o[1], (uint32_t)(o[1] >> 32));
-}
-__device__ __forceinline__ uint4 pack16(const uint32_t (&o)[4]) { return make_uint4(o[0], o[1], o[2], o[3]); }
-
 template <class F>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, sizeof(typename F::T) == 4 ? 2 : 1)
 k_middle(typename F::T *__restrict__ A, const typename F::T *__restrict__ Bv, uint64_t nrows, uint64_t linv_,
          RootTablesT<typename F::T> rt) {
     using T = typename F::T;
@@ -121,7 +105,8 @@ static cudaError_t launch_middle_f(void *A, const void *B, uint64_t L, uint64_t 
     cudaError_t e = cudaFuncSetAttribute(k_middle<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const uint64_t rows = L >> kMidLgMax;
-    const uint64_t grid = rows < (uint64_t)nsm ? rows : (uint64_t)nsm;
+    const uint64_t per_sm = sizeof(T) == 4 ? 2 : 1;  // resident CTAs per SM (shared memory, registers)
+    const uint64_t grid = rows < per_sm * nsm ? rows : per_sm * nsm;
     k_middle<F><<<(unsigned)grid, kThreads, sm, st>>>(static_cast<T *>(A), static_cast<const T *>(B), rows, linv,
                                                       rt);
     return cudaGetLastError();

@@ -70,9 +70,8 @@ struct FieldF30 {
     using T = uint32_t;
     static constexpr int kAdicity = 30;
     static constexpr int kBigLg = 15;
-    // 2^15-element tiles, so that a row of the tile still spans a whole 32-byte
-    // sector; 2^14 when R = 2 (the single pass of L = 2^14 has columns 2^13 apart)
-    static constexpr int ncol_lg(int logr) { return logr == 1 ? 13 : 15 - logr; }
+    // 2^14-element tiles (64 KiB), so that two CTAs fit on an SM
+    static constexpr int ncol_lg(int logr) { return kTileLg - logr; }
     __device__ static __forceinline__ T add(T a, T b) { return f30_add(a, b); }
     __device__ static __forceinline__ T sub(T a, T b) { return f30_sub(a, b); }
     __device__ static __forceinline__ T twmul(T x, T w) { return f30_mont(x, w); }
@@ -81,6 +80,22 @@ struct FieldF30 {
     }
     __device__ static __forceinline__ T prod(T a, T b, T linv) { return f30_mont(f30_mont(a, b), linv); }
 };
+
+// 16 bytes as 2 x 64-bit or 4 x 32-bit elements, and back.
+__device__ __forceinline__ void unpack16(uint4 v, uint64_t (&o)[2]) {
+    o[0] = ((uint64_t)v.y << 32) | v.x;
+    o[1] = ((uint64_t)v.w << 32) | v.z;
+}
+__device__ __forceinline__ void unpack16(uint4 v, uint32_t (&o)[4]) {
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+}
+__device__ __forceinline__ uint4 pack16(const uint64_t (&o)[2]) {
+    return make_uint4((uint32_t)o[0], (uint32_t)(o[0] >> 32), (uint32_t)o[1], (uint32_t)(o[1] >> 32));
+}
+__device__ __forceinline__ uint4 pack16(const uint32_t (&o)[4]) { return make_uint4(o[0], o[1], o[2], o[3]); }
 
 // g^E for E < 2^kAdicity, g the field's fixed root of maximal 2-power order.
 template <class F>
