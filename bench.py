@@ -448,7 +448,7 @@ def run_batched_a(args, world, rank, local):
     # roofline of the work-list kernel (the only kernel of a step)
     Ls = np.array([native.ntt_length(native.TOEPLITZ, int(n), int(m)) for n, m in zip(ns, ms)])
     big = Ls > (1 << 13)
-    alg = float(48 * Ls[big].sum() + ((ns + (ns + ms - 1) + ms) / 8).sum())
+    alg = float(24 * Ls[big].sum() + ((ns + (ns + ms - 1) + ms) / 8).sum())  # 32-bit field elements
     peak, peak_src = measured_peaks()
     ctx.profile_enable(True)
     ctx.profile_read(reset=True)
@@ -463,11 +463,11 @@ def run_batched_a(args, world, rank, local):
     bfly = float((3 * (Ls // 2) * lgs).sum())
     clk = (sampler.summary(tw0, tw1) or {}).get("sm_mhz") or 2070.0
     ach_b = bfly / (per_launch * 1e-3) / 1e9
-    peak_b = alu_peak_butterflies(clk) / 1e9
+    peak_b = alu_peak_butterflies(clk, ALU_OPS_PER_BUTTERFLY_F30) / 1e9  # the work list runs the 32-bit field
     roof = {"bound": "alu", "kernel": "k_batch", "achieved": ach_b, "peak": peak_b, "unit": "G butterflies/s",
             "frac": ach_b / peak_b,
             "peak_source": f"{NUM_SMS} SMs x {ALU_LANES_PER_SM} ALU lanes x {clk:.0f} MHz measured / "
-                           f"{ALU_OPS_PER_BUTTERFLY} ALU ops per radix-2 butterfly",
+                           f"{ALU_OPS_PER_BUTTERFLY_F30} ALU ops per radix-2 butterfly",
             "traffic": ncu_traffic("k_batch", "batched_a"), "butterflies_per_launch": bfly,
             "avg_launch_ms": per_launch,
             "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -88,10 +88,11 @@ static void finish_plan(Plan *p) {
     if (p->kind == CM_DODIS) p->launches += 1;  // precondition check
 }
 
-bool make_plan(int kind, uint64_t n, uint64_t m, Plan *p) {
+bool make_plan(int kind, uint64_t n, uint64_t m, Plan *p, bool allow_f30) {
     if (!base_maps(kind, n, m, p)) return false;
     if (p->K + m - 1 > (1ull << 32)) return false;
     finish_plan(p);
+    if (allow_f30 && p->lg <= kF30MaxLg) p->field = kFieldF30;
     return true;
 }
 

@@ -45,13 +45,15 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     return v;
 }
 
-__device__ void do_small(const BatchInst &I, const uint64_t *tw, uint64_t *sA, uint64_t *sB,
+template <class F>
+__device__ void do_small(const BatchInst &I, const typename F::T *tw, typename F::T *sA, typename F::T *sB,
                          uint32_t *status) {
+    using T = typename F::T;
     const int lg = I.lg, L = 1 << lg;
     int any1 = 0, any0 = 0;
     for (int i = threadIdx.x; i < L; i += kThreads) {
-        sA[sp(i)] = I.amap.get(i);
-        sB[sp(i)] = I.bmap.get(i);
+        sA[sp(i)] = (T)I.amap.get(i);
+        sB[sp(i)] = (T)I.bmap.get(i);
     }
     if (I.kind == CM_DODIS) {
         for (uint64_t i = threadIdx.x; i < I.nx; i += kThreads) {
@@ -68,10 +70,11 @@ __device__ void do_small(const BatchInst &I, const uint64_t *tw, uint64_t *sA, u
         I.pre[0] = any1 ? 1u : 0u;
         I.pre[1] = any0 ? 1u : 0u;
     }
-    ntt_fwd_rt(sA, sB, 2, lg, 0, tw);
-    for (int i = threadIdx.x; i < L; i += kThreads) sA[sp(i)] = gl_mul(gl_mul(sA[sp(i)], sB[sp(i)]), I.linv);
+    ntt_fwd_rt<F>(sA, sB, 2, lg, 0, tw);
+    const T linv = (T)I.linv;
+    for (int i = threadIdx.x; i < L; i += kThreads) sA[sp(i)] = F::prod(sA[sp(i)], sB[sp(i)], linv);
     __syncthreads();
-    ntt_inv_rt(sA, sA, 1, lg, 0, tw);
+    ntt_inv_rt<F>(sA, sA, 1, lg, 0, tw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t nwords = (I.m + 63) >> 6;
     for (uint64_t w = warp; w < nwords; w += kThreads / 32) {
@@ -85,37 +88,38 @@ __device__ void do_small(const BatchInst &I, const uint64_t *tw, uint64_t *sA, u
 }
 
 // Column-pass tile (the single pass of a 2^14 .. 2^25 transform: N = L).
-template <bool INV>
-__device__ void do_pass(const BatchInst &I, int operand, uint32_t tile, const uint64_t *tw, uint64_t *s,
-                        const RootTables &rt) {
+template <class F, bool INV>
+__device__ void do_pass(const BatchInst &I, int operand, uint32_t tile, const typename F::T *tw,
+                        typename F::T *s, const RootTablesT<typename F::T> &rt) {
+    using T = typename F::T;
     const int logr = I.logr, lg = I.lg, ncol_lg = I.tile_lg - logr;
     const int lgS = lg - logr, cmask = (1 << ncol_lg) - 1, n = 1 << I.tile_lg;
     const uint64_t col0 = (uint64_t)tile << ncol_lg;
-    const int esh = 32 - lg;
-    uint64_t *data = operand ? I.B : I.A;
+    const int esh = F::kAdicity - lg;
+    T *data = static_cast<T *>(operand ? I.B : I.A);
     const BitMap &map = operand ? I.bmap : I.amap;
     for (int e = threadIdx.x; e < n; e += kThreads) {
         const int i = e >> ncol_lg, c = e & cmask;
         const uint64_t g = col0 + ((uint64_t)i << lgS) + c;
-        uint64_t v;
+        T v;
         if (INV) {
             v = __ldcg(data + g);
             const uint64_t k = pos_to_freq_rt(i, logr);
             const uint32_t E = (uint32_t)(((col0 + c) * k) << esh);
-            if (E) v = gl_mul(v, big_root(rt.big_lo_inv, rt.big_hi_inv, E));
+            if (E) v = F::twmul(v, big_root_f<F>(rt.big_lo_inv, rt.big_hi_inv, E));
         } else {
-            v = map.get(g);
+            v = (T)map.get(g);
         }
         s[sp(e)] = v;
     }
     __syncthreads();
     if (INV)
-        ntt_inv_rt(s, s, 1, logr, ncol_lg, tw);
+        ntt_inv_rt<F>(s, s, 1, logr, ncol_lg, tw);
     else
-        ntt_fwd_rt(s, s, 1, logr, ncol_lg, tw);
+        ntt_fwd_rt<F>(s, s, 1, logr, ncol_lg, tw);
     for (int e = threadIdx.x; e < n; e += kThreads) {
         const int i = e >> ncol_lg, c = e & cmask;
-        uint64_t v = s[sp(e)];
+        T v = s[sp(e)];
         const uint64_t g = col0 + ((uint64_t)i << lgS) + c;
         if (INV) {
             const uint64_t p = g - I.lo;
@@ -123,28 +127,40 @@ __device__ void do_pass(const BatchInst &I, int operand, uint32_t tile, const ui
         } else {
             const uint64_t k = pos_to_freq_rt(i, logr);
             const uint32_t E = (uint32_t)(((col0 + c) * k) << esh);
-            if (E) v = gl_mul(v, big_root(rt.big_lo_fwd, rt.big_hi_fwd, E));
+            if (E) v = F::twmul(v, big_root_f<F>(rt.big_lo_fwd, rt.big_hi_fwd, E));
             data[g] = v;
         }
     }
 }
 
-__device__ void do_middle(const BatchInst &I, uint32_t r, const uint64_t *tw, uint64_t *sA, uint64_t *sB) {
+template <class F>
+__device__ void do_middle(const BatchInst &I, uint32_t r, const typename F::T *tw, typename F::T *sA,
+                          typename F::T *sB) {
+    using T = typename F::T;
     constexpr int LG = kMidLgMax, Bn = 1 << LG;
+    constexpr int PER = 16 / sizeof(T);
     const uint64_t row = (uint64_t)r << LG;
-    const ulonglong2 *a2 = reinterpret_cast<const ulonglong2 *>(I.A + row);
-    const ulonglong2 *b2 = reinterpret_cast<const ulonglong2 *>(I.B + row);
-    for (int i = threadIdx.x; i < Bn / 2; i += kThreads) {
-        const ulonglong2 va = __ldcg(a2 + i), vb = __ldcg(b2 + i);
-        sA[sp(2 * i)] = va.x;
-        sA[sp(2 * i + 1)] = va.y;
-        sB[sp(2 * i)] = vb.x;
-        sB[sp(2 * i + 1)] = vb.y;
+    const uint4 *a4 = reinterpret_cast<const uint4 *>(static_cast<const T *>(I.A) + row);
+    const uint4 *b4 = reinterpret_cast<const uint4 *>(static_cast<const T *>(I.B) + row);
+    for (int i = threadIdx.x; i < Bn / PER; i += kThreads) {
+        T pa[PER], pb[PER];
+        unpack16(__ldcg(a4 + i), pa);
+        unpack16(__ldcg(b4 + i), pb);
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            sA[sp(PER * i + j)] = pa[j];
+            sB[sp(PER * i + j)] = pb[j];
+        }
     }
     __syncthreads();
-    middle_row_13(sA, sB, tw, I.linv);
-    ulonglong2 *o2 = reinterpret_cast<ulonglong2 *>(I.A + row);
-    for (int i = threadIdx.x; i < Bn / 2; i += kThreads) o2[i] = make_ulonglong2(sA[sp(2 * i)], sA[sp(2 * i + 1)]);
+    middle_row_13_f<F>(sA, sB, tw, (T)I.linv);
+    uint4 *o4 = reinterpret_cast<uint4 *>(static_cast<T *>(I.A) + row);
+    for (int i = threadIdx.x; i < Bn / PER; i += kThreads) {
+        T pv[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) pv[j] = sA[sp(PER * i + j)];
+        o4[i] = pack16(pv);
+    }
 }
 
 __device__ void do_pack(const BatchInst &I, uint32_t chunk, uint32_t *status) {
@@ -182,13 +198,15 @@ __device__ void do_check(const BatchInst &I) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+template <class F>
+__global__ void __launch_bounds__(kThreads, sizeof(typename F::T) == 4 ? 2 : 1)
 k_batch(const BatchInst *__restrict__ insts, const WorkItem *__restrict__ items, uint32_t nitems,
-        uint32_t *ctrl, uint32_t *status, RootTables rt) {
-    extern __shared__ uint64_t smem[];
-    uint64_t *tw = smem;                     // omega_8192^e
-    uint64_t *sA = smem + 8192;              // also the pass tile (2^14 elements)
-    uint64_t *sB = sA + sp_size(1 << kMidLgMax);
+        uint32_t *ctrl, uint32_t *status, RootTablesT<typename F::T> rt) {
+    using T = typename F::T;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    T *tw = reinterpret_cast<T *>(smem_raw);  // omega_8192^e
+    T *sA = tw + 8192;                        // also the pass tile (2^14 elements)
+    T *sB = sA + sp_size(1 << kMidLgMax);
     __shared__ uint32_t s_item, s_skip;
     for (int e = threadIdx.x; e < 8192; e += kThreads) tw[tw_swz(e)] = __ldg(rt.small + e);
     uint32_t *next = ctrl, *abort_flag = ctrl + 1, *done = ctrl + 2;
@@ -220,11 +238,11 @@ k_batch(const BatchInst *__restrict__ insts, const WorkItem *__restrict__ items,
         __syncthreads();
         if (!s_skip) {
             switch (w.type) {
-                case kItSmall: do_small(I, tw, sA, sB, status); break;
-                case kItFwdA: do_pass<false>(I, 0, w.idx, tw, sA, rt); break;
-                case kItFwdB: do_pass<false>(I, 1, w.idx, tw, sA, rt); break;
-                case kItMiddle: do_middle(I, w.idx, tw, sA, sB); break;
-                case kItInv: do_pass<true>(I, 0, w.idx, tw, sA, rt); break;
+                case kItSmall: do_small<F>(I, tw, sA, sB, status); break;
+                case kItFwdA: do_pass<F, false>(I, 0, w.idx, tw, sA, rt); break;
+                case kItFwdB: do_pass<F, false>(I, 1, w.idx, tw, sA, rt); break;
+                case kItMiddle: do_middle<F>(I, w.idx, tw, sA, sB); break;
+                case kItInv: do_pass<F, true>(I, 0, w.idx, tw, sA, rt); break;
                 case kItPack: do_pack(I, w.idx, status); break;
                 case kItCheck: do_check(I); break;
                 default: break;
@@ -241,32 +259,38 @@ k_batch(const BatchInst *__restrict__ insts, const WorkItem *__restrict__ items,
 }  // namespace
 
 static size_t round256(size_t v) { return (v + 255) & ~size_t(255); }
-static const size_t kBatchSmem = (8192 + 2 * (size_t)sp_size(1 << kMidLgMax)) * sizeof(uint64_t);
+// The work list runs every instance (L <= 2^25) over the 32-bit field.
+using BatchField = FieldF30;
+using BatchT = BatchField::T;
+static const size_t kBatchSmem = (8192 + 2 * (size_t)sp_size(1 << kMidLgMax)) * sizeof(BatchT);
 
 size_t worklist_scratch_bytes(const Plan &p) {
-    return p.npass == 1 ? round256(16 * p.L) + round256(p.m) : 0;
+    return p.npass == 1 ? round256(2 * sizeof(BatchT) * p.L) + round256(p.m) : 0;
 }
+
+size_t worklist_seed_bytes(const Plan &p) { return sizeof(BatchT) * p.L; }
 
 size_t batch_smem_bytes() { return kBatchSmem; }
 
 int batch_grid(int nsm) {
-    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess)
+    auto kern = k_batch<BatchField>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess)
         return 0;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kThreads, kBatchSmem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, kBatchSmem) != cudaSuccess)
         return 0;
     return nsm * occ;
 }
 
 cudaError_t launch_k_batch(const BatchInst *insts, const WorkItem *items, uint32_t nitems, uint32_t *ctrl,
-                           uint32_t *status, const RootTables &rt, int grid, cudaStream_t st) {
-    k_batch<<<grid, kThreads, kBatchSmem, st>>>(insts, items, nitems, ctrl, status, rt);
+                           uint32_t *status, const RootTables30 &rt, int grid, cudaStream_t st) {
+    k_batch<BatchField><<<grid, kThreads, kBatchSmem, st>>>(insts, items, nitems, ctrl, status, rt);
     return cudaGetLastError();
 }
 
 void build_worklist(const cm_desc *descs, const Plan *plans, const uint32_t *idx, uint32_t n,
                     uint8_t *scratch, const size_t *off, int tile_lg, uint32_t *pre,
-                    std::vector<BatchInst> &insts, std::vector<WorkItem> &items, uint64_t *const *bext,
+                    std::vector<BatchInst> &insts, std::vector<WorkItem> &items, void *const *bext,
                     const uint8_t *bready, bool test_stall) {
     bool stalled = false;
     insts.assign(n, BatchInst());
@@ -288,7 +312,7 @@ void build_worklist(const cm_desc *descs, const Plan *plans, const uint32_t *idx
         I.z = d.z;
         I.lo = p.lo;
         I.m = p.m;
-        I.linv = gl_inv_pow2_host(p.L);
+        I.linv = f30_linv_mont2(p.L);
         I.nx = p.n;
         I.lg = p.lg;
         I.kind = p.kind;
@@ -300,9 +324,9 @@ void build_worklist(const cm_desc *descs, const Plan *plans, const uint32_t *idx
         I.logr = p.pass_lg[0];
         I.tile_lg = std::max(tile_lg, I.logr);  // at least one column per tile
         uint8_t *base = scratch + off[di];
-        I.A = reinterpret_cast<uint64_t *>(base);
-        I.B = I.A + p.L;
-        I.par = reinterpret_cast<uint8_t *>(I.B + p.L);
+        I.A = base;
+        I.B = base + sizeof(BatchT) * p.L;
+        I.par = base + 2 * sizeof(BatchT) * p.L;
         const bool have_b = bext && bext[k] && bready && bready[k];
         if (bext && bext[k]) I.B = bext[k];
         const uint32_t tiles = (uint32_t)(p.L >> I.tile_lg);
@@ -394,8 +418,8 @@ static cm_status batch_enqueue(cm_batch *b, cudaStream_t st) {
     if (b->nitems) {
         if (cudaMemsetAsync(b->d_ctrl, 0, b->ctrl_words * sizeof(uint32_t), st) != cudaSuccess) return CM_EDEVICE;
         ProfScope ps(ctx, "k_batch", st);
-        k_batch<<<b->grid, kThreads, kBatchSmem, st>>>(b->d_insts, b->d_items, b->nitems, b->d_ctrl,
-                                                         ctx->d_status, ctx->rt);
+        k_batch<BatchField><<<b->grid, kThreads, kBatchSmem, st>>>(b->d_insts, b->d_items, b->nitems, b->d_ctrl,
+                                                         ctx->d_status, ctx->rt30);
         if (cudaGetLastError() != cudaSuccess) return CM_EDEVICE;
         b->kernel_launches += 1;
     }
@@ -449,7 +473,7 @@ extern "C" cm_status cm_batch_create(cm_ctx *ctx, const cm_desc *descs, uint32_t
     size_t total = 0;
     for (uint32_t i = 0; i < count; ++i) {
         const cm_desc &d = descs[i];
-        if (!d.x || !d.y || !d.z || !make_plan(d.kind, d.n, d.m, &b->plans[i])) {
+        if (!d.x || !d.y || !d.z || !make_plan(d.kind, d.n, d.m, &b->plans[i], ctx->allow_f30)) {
             delete b;
             return CM_EINVAL;
         }

@@ -15,11 +15,11 @@ constexpr int kPackWordsPerItem = 1 << 16;
 
 struct BatchInst {
     BitMap amap, bmap;
-    uint64_t *A, *B;
+    void *A, *B;  // L elements each of the work list's field (32-bit words)
     uint8_t *par;
     uint64_t *z;
     uint32_t *pre;  // Dodis et al.: {any 1 bit, any 0 bit} of x, else null
-    uint64_t lo, m, linv, nx;
+    uint64_t lo, m, linv, nx;  // linv in the field's product form
     int32_t lg, logr, tile_lg, kind;
     uint32_t need[4];  // items per phase
 };
@@ -33,8 +33,12 @@ struct WorkItem {
 };
 
 // Scratch one work-list instance needs (0 for L <= 2^13): operands A and B
-// (8L bytes each) and the parity bytes of its window.
+// (L elements each of the work list's field, 4 bytes) and the parity bytes of
+// its window.
 size_t worklist_scratch_bytes(const Plan &p);
+
+// Bytes of one resident seed transform (operand B) of a work-list instance.
+size_t worklist_seed_bytes(const Plan &p);
 
 // Instance table and phase-ordered work list for the instances idx[0..n) of
 // descs/plans.  Instance k's scratch starts at scratch + off[idx[k]]; Dodis
@@ -46,7 +50,7 @@ size_t worklist_scratch_bytes(const Plan &p);
 void build_worklist(const cm_desc *descs, const Plan *plans, const uint32_t *idx, uint32_t n,
                     uint8_t *scratch, const size_t *off, int tile_lg, uint32_t *pre,
                     std::vector<BatchInst> &insts, std::vector<WorkItem> &items,
-                    uint64_t *const *bext = nullptr, const uint8_t *bready = nullptr, bool test_stall = false);
+                    void *const *bext = nullptr, const uint8_t *bready = nullptr, bool test_stall = false);
 
 // Dynamic shared memory of the work-list kernel and its resident grid.
 size_t batch_smem_bytes();
@@ -54,6 +58,6 @@ int batch_grid(int nsm);
 
 // One launch of the work-list kernel; ctrl holds 2 + 4 n zeroed words.
 cudaError_t launch_k_batch(const BatchInst *insts, const WorkItem *items, uint32_t nitems, uint32_t *ctrl,
-                           uint32_t *status, const RootTables &rt, int grid, cudaStream_t st);
+                           uint32_t *status, const RootTables30 &rt, int grid, cudaStream_t st);
 
 }  // namespace cm

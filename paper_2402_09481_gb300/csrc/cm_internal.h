@@ -81,7 +81,8 @@ struct Plan {
 
 // Validate (kind, n, m) and fill the plan; false if invalid or if K + m - 1
 // exceeds 2^32 (one transform).
-bool make_plan(int kind, uint64_t n, uint64_t m, Plan *out);
+// allow_f30: a transform of length <= 2^30 runs over the 32-bit field.
+bool make_plan(int kind, uint64_t n, uint64_t m, Plan *out, bool allow_f30 = false);
 
 // Longest bit string a blocked extraction takes (the paper's 2^40).
 constexpr uint64_t kMaxBits = 1ull << 40;

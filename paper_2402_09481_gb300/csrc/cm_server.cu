@@ -94,7 +94,7 @@ struct SeedKeyHash {
     }
 };
 struct SeedEntry {
-    uint64_t *buf = nullptr;
+    void *buf = nullptr;
     size_t bytes = 0;
     bool ready = false;  // holds the transform (its creating wave finished)
     int refs = 0;        // in-flight waves using it
@@ -227,7 +227,7 @@ cm_status launch_wave(cm_server *S, Slot &sl, const std::vector<uint64_t> &tk) {
     if (!sl.flags.ensure(flag_words * 4)) return CM_ENOMEM;
     uint32_t *dflags = static_cast<uint32_t *>(sl.flags.dev);
     // resident seed transforms
-    std::vector<uint64_t *> bext(wl.size(), nullptr);
+    std::vector<void *> bext(wl.size(), nullptr);
     std::vector<uint8_t> bready(wl.size(), 0);
     sl.seeds.clear();
     for (uint32_t k = 0; k < wl.size(); ++k) {
@@ -245,7 +245,7 @@ cm_status launch_wave(cm_server *S, Slot &sl, const std::vector<uint64_t> &tk) {
             ++S->seed_hits;
             continue;
         }
-        const size_t bytes = 8 * r.p.L;
+        const size_t bytes = worklist_seed_bytes(r.p);
         if (!seed_make_room(S, bytes, sl.st)) continue;
         void *buf = nullptr;
         if (cudaMallocFromPoolAsync(&buf, bytes, ctx->pool, sl.st) != cudaSuccess) {
@@ -253,7 +253,7 @@ cm_status launch_wave(cm_server *S, Slot &sl, const std::vector<uint64_t> &tk) {
             continue;
         }
         SeedEntry e;
-        e.buf = static_cast<uint64_t *>(buf);
+        e.buf = buf;
         e.bytes = bytes;
         e.refs = 1;
         e.last = ++S->lru;
@@ -285,7 +285,7 @@ cm_status launch_wave(cm_server *S, Slot &sl, const std::vector<uint64_t> &tk) {
             return CM_EDEVICE;
         ProfScope ps(ctx, "k_batch", sl.st);
         e = launch_k_batch(static_cast<BatchInst *>(sl.insts.dev), static_cast<WorkItem *>(sl.items.dev),
-                           (uint32_t)items.size(), static_cast<uint32_t *>(sl.ctrl.dev), dflags, ctx->rt, S->grid,
+                           (uint32_t)items.size(), static_cast<uint32_t *>(sl.ctrl.dev), dflags, ctx->rt30, S->grid,
                            sl.st);
         if (e != cudaSuccess) return CM_EDEVICE;
     }
@@ -480,7 +480,7 @@ extern "C" cm_status cm_submit(cm_ctx *ctx, const cm_request *rq, uint64_t *tick
     r.flags = rq->flags;
     r.seed_id = rq->seed_id;
     if (rq->flags & ~CM_REQ_SEED_CACHE) return CM_EINVAL;
-    if (!rq->x || !rq->y || !rq->z || !make_plan(rq->kind, rq->n, rq->m, &r.p)) return CM_EINVAL;
+    if (!rq->x || !rq->y || !rq->z || !make_plan(rq->kind, rq->n, rq->m, &r.p, ctx->allow_f30)) return CM_EINVAL;
     r.foot = r.p.npass <= 1 ? worklist_scratch_bytes(r.p) : r256(r.p.scratch_bytes);
     r.foot += 256;  // work-list and flag share
     {

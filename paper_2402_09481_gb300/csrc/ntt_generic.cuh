@@ -1,4 +1,5 @@
-// Runtime-size on-chip transforms for the batched work-list kernel.
+// Runtime-size on-chip transforms for the batched work-list kernel, over a
+// field policy F of ntt_device.cuh.
 //
 // Same mixed-radix decimation-in-frequency steps as ntt_device.cuh (the
 // four-step split of Def. ntt applied recursively over shared memory, with
@@ -21,9 +22,10 @@ __host__ __device__ inline int rt_q(int logr, int j) {
     return logr / n + (j < logr % n ? 1 : 0);
 }
 
-template <int LQ, bool INV>
-__device__ __forceinline__ void step_rt(uint64_t *s0, uint64_t *s1, int nbuf, int logr, int off,
-                                        int ncol_lg, const uint64_t *tw8192) {
+template <class F, int LQ, bool INV>
+__device__ __forceinline__ void step_rt(typename F::T *s0, typename F::T *s1, int nbuf, int logr, int off,
+                                        int ncol_lg, const typename F::T *tw8192) {
+    using T = typename F::T;
     constexpr int RD = 1 << LQ;
     const int LN = logr - off, LM = LN - LQ;
     const int items = (1 << (logr - LQ)) << ncol_lg;
@@ -32,30 +34,30 @@ __device__ __forceinline__ void step_rt(uint64_t *s0, uint64_t *s1, int nbuf, in
     for (int item = threadIdx.x; item < items * nbuf; item += kThreads) {
         const int bi = item >= items;
         const int it = item - (bi ? items : 0);
-        uint64_t *s = bi ? s1 : s0;
+        T *s = bi ? s1 : s0;
         const int c = it & cmask;
         const int rest = it >> ncol_lg;
         const int i2 = rest & mmask;
         const int row0 = ((rest >> LM) << LN) + i2;
-        uint64_t v[RD];
+        T v[RD];
         if (!INV) {
 #pragma unroll
             for (int i1 = 0; i1 < RD; ++i1) v[i1] = s[sp(((row0 + (i1 << LM)) << ncol_lg) + c)];
-            dft_reg<LQ>(v);
+            dft_reg_f<F, LQ>(v);
 #pragma unroll
             for (int k1 = 0; k1 < RD; ++k1) {
-                uint64_t x = v[bitrev_c(k1, LQ)];
-                if (k1 > 0 && i2 > 0) x = gl_mul(x, tw8192[tw_swz((i2 * k1) << tws)]);
+                T x = v[bitrev_c(k1, LQ)];
+                if (k1 > 0 && i2 > 0) x = F::twmul(x, tw8192[tw_swz((i2 * k1) << tws)]);
                 s[sp(((row0 + (k1 << LM)) << ncol_lg) + c)] = x;
             }
         } else {
 #pragma unroll
             for (int k1 = 0; k1 < RD; ++k1) {
-                uint64_t x = s[sp(((row0 + (k1 << LM)) << ncol_lg) + c)];
-                if (k1 > 0 && i2 > 0) x = gl_mul(x, tw8192[tw_swz((8192 - ((i2 * k1) << tws)) & 8191)]);
+                T x = s[sp(((row0 + (k1 << LM)) << ncol_lg) + c)];
+                if (k1 > 0 && i2 > 0) x = F::twmul(x, tw8192[tw_swz((8192 - ((i2 * k1) << tws)) & 8191)]);
                 v[k1] = x;
             }
-            dft_reg<LQ>(v);
+            dft_reg_f<F, LQ>(v);
 #pragma unroll
             for (int i1 = 0; i1 < RD; ++i1)
                 s[sp(((row0 + (i1 << LM)) << ncol_lg) + c)] = v[bitrev_c((RD - i1) & (RD - 1), LQ)];
@@ -63,37 +65,39 @@ __device__ __forceinline__ void step_rt(uint64_t *s0, uint64_t *s1, int nbuf, in
     }
 }
 
-template <bool INV>
-__device__ __forceinline__ void step_dispatch(int q, uint64_t *s0, uint64_t *s1, int nbuf, int logr,
-                                              int off, int ncol_lg, const uint64_t *tw) {
+template <class F, bool INV>
+__device__ __forceinline__ void step_dispatch(int q, typename F::T *s0, typename F::T *s1, int nbuf, int logr,
+                                              int off, int ncol_lg, const typename F::T *tw) {
     switch (q) {
-        case 1: step_rt<1, INV>(s0, s1, nbuf, logr, off, ncol_lg, tw); break;
-        case 2: step_rt<2, INV>(s0, s1, nbuf, logr, off, ncol_lg, tw); break;
-        case 3: step_rt<3, INV>(s0, s1, nbuf, logr, off, ncol_lg, tw); break;
-        default: step_rt<4, INV>(s0, s1, nbuf, logr, off, ncol_lg, tw); break;
+        case 1: step_rt<F, 1, INV>(s0, s1, nbuf, logr, off, ncol_lg, tw); break;
+        case 2: step_rt<F, 2, INV>(s0, s1, nbuf, logr, off, ncol_lg, tw); break;
+        case 3: step_rt<F, 3, INV>(s0, s1, nbuf, logr, off, ncol_lg, tw); break;
+        default: step_rt<F, 4, INV>(s0, s1, nbuf, logr, off, ncol_lg, tw); break;
     }
 }
 
 // Forward transform of every column (natural -> digit-reversed); ends with a barrier.
-__device__ __forceinline__ void ntt_fwd_rt(uint64_t *s0, uint64_t *s1, int nbuf, int logr, int ncol_lg,
-                                           const uint64_t *tw) {
+template <class F>
+__device__ __forceinline__ void ntt_fwd_rt(typename F::T *s0, typename F::T *s1, int nbuf, int logr, int ncol_lg,
+                                           const typename F::T *tw) {
     int off = 0;
     for (int j = 0; j < rt_nsteps(logr); ++j) {
         const int q = rt_q(logr, j);
-        step_dispatch<false>(q, s0, s1, nbuf, logr, off, ncol_lg, tw);
+        step_dispatch<F, false>(q, s0, s1, nbuf, logr, off, ncol_lg, tw);
         __syncthreads();
         off += q;
     }
 }
 
 // Inverse of ntt_fwd_rt up to the factor R; ends with a barrier.
-__device__ __forceinline__ void ntt_inv_rt(uint64_t *s0, uint64_t *s1, int nbuf, int logr, int ncol_lg,
-                                           const uint64_t *tw) {
+template <class F>
+__device__ __forceinline__ void ntt_inv_rt(typename F::T *s0, typename F::T *s1, int nbuf, int logr, int ncol_lg,
+                                           const typename F::T *tw) {
     int off = logr;
     for (int j = rt_nsteps(logr) - 1; j >= 0; --j) {
         const int q = rt_q(logr, j);
         off -= q;
-        step_dispatch<true>(q, s0, s1, nbuf, logr, off, ncol_lg, tw);
+        step_dispatch<F, true>(q, s0, s1, nbuf, logr, off, ncol_lg, tw);
         __syncthreads();
     }
 }

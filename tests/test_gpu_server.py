@@ -111,8 +111,8 @@ def test_server_mix_same_alone_and_in_mix(sctx, cm_ctx):
 
 
 def test_server_admission_by_footprint(sctx, cm_ctx):
-    # L = 2^20 needs 16 MiB of transform scratch + window bytes; a 40 MiB budget
-    # fits two at a time
+    # L = 2^20 needs 8 MiB of transform scratch (two operands of 32-bit field
+    # elements) + window bytes; a 40 MiB budget fits four at a time
     budget = 40 << 20
     sctx.server_start(hbm_budget_bytes=budget, slots=3)
     reqs = [make(T, 600000, 300000, 700 + 3 * j) for j in range(8)]
@@ -123,17 +123,17 @@ def test_server_admission_by_footprint(sctx, cm_ctx):
     assert 0 < st["max_inflight_bytes"] <= budget
     for r in reqs:
         assert torch.equal(r["z"], alone(cm_ctx, r))
-    big = make(T, 2 ** 21, 2 ** 21, 999)   # L = 2^22: 64 MiB alone
+    big = make(T, 2 ** 22, 2 ** 22, 999)   # L = 2^23: 64 MiB alone
     s, _ = sctx.submit_raw(T, big["n"], big["m"], big["x"].data_ptr(), big["y"].data_ptr(), big["z"].data_ptr())
     assert s == native.CM_ENOMEM
     sctx.server_stop()
 
 
 def test_server_queue_full_poll_timeout_unknown(sctx):
-    a = make(T, 2 ** 24, 2 ** 24, 41)     # L = 2^25: about 0.5 GiB of scratch
+    a = make(T, 2 ** 24, 2 ** 24, 41)     # L = 2^25: about 0.25 GiB of scratch
     b = make(T, 2 ** 24, 2 ** 24, 43)
     c = make(T, 1000, 500, 45)
-    foot = 16 * 2 ** 25 + 2 ** 24 + 4096
+    foot = 8 * 2 ** 25 + 2 ** 24 + 4096   # room for one of them
     sctx.server_start(hbm_budget_bytes=foot, slots=2, max_queue=1)
     ta = submit(sctx, a)                  # admitted at once
     time.sleep(0.001)
