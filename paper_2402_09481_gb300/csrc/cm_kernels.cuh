@@ -110,8 +110,9 @@ k_pass(typename F::T *__restrict__ data, BitMap map, int lgN, int lgS, uint8_t *
         const uint64_t g = base + ((uint64_t)i << lgS) + c;
         T v[VW];
         if (BITS_IN) {
+            const uint32_t bits = map.get_run<VW>(g);
 #pragma unroll
-            for (int j = 0; j < VW; ++j) v[j] = (T)map.get(g + j);
+            for (int j = 0; j < VW; ++j) v[j] = (T)((bits >> j) & 1u);
         } else {
             unpack16(*reinterpret_cast<const uint4 *>(data + g), v);
         }

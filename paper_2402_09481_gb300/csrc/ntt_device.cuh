@@ -139,6 +139,44 @@ struct BitMap {
         }
         return (__ldg(src + (idx >> 6)) >> (idx & 63)) & 1ull;
     }
+
+    // Values of the CNT <= 32 consecutive positions k .. k + CNT - 1 as bits
+    // 0 .. CNT - 1, from one or two word loads when the run maps to a run of
+    // source bits (no cut at len, no wrap, no pad bit); else position by position.
+    template <int CNT>
+    __device__ __forceinline__ uint32_t get_run(uint64_t k) const {
+        constexpr uint64_t mask = (1ull << CNT) - 1;
+        if (k + CNT <= len) {
+            uint64_t lo;   // lowest source index of the run
+            bool fast;
+            if (mode == kIdentity) {
+                lo = k;
+                fast = true;
+            } else if (mode == kModForward) {
+                lo = k + off;
+                if (lo >= srclen) lo -= srclen;
+                if (lo >= srclen) lo -= srclen;
+                fast = lo + CNT <= srclen;
+            } else {
+                const uint64_t hi = off - k;  // decreasing: hi, hi - 1, ..., hi - CNT + 1
+                fast = hi < srclen && hi >= CNT - 1;
+                lo = hi - (CNT - 1);
+            }
+            if (fast) {
+                const uint64_t w = lo >> 6;
+                const int sh = (int)(lo & 63);
+                uint64_t r = __ldg(src + w) >> sh;
+                if (sh + CNT > 64) r |= __ldg(src + w + 1) << (64 - sh);
+                r &= mask;
+                if (mode == kReverse) r = __brev((uint32_t)r) >> (32 - CNT);
+                return (uint32_t)r;
+            }
+        }
+        uint32_t r = 0;
+#pragma unroll
+        for (int j = 0; j < CNT; ++j) r |= (uint32_t)get(k + j) << j;
+        return r;
+    }
 };
 
 // ---------------------------------------------------------------------------
