@@ -74,6 +74,32 @@ k_fused_small(BitMap amap, BitMap bmap, uint64_t lo, uint64_t m, uint64_t linv_,
     }
 }
 
+// v[j] *= omega^((c0 + j) k 2^esh), j < VW: the pass twiddles of VW consecutive
+// columns of one row.  For VW >= 4 the roots are a geometric run: two table
+// lookups (the first root and the step) and a running product replace one
+// lookup per element.
+template <class F, int VW>
+__device__ __forceinline__ void row_twiddle(typename F::T (&v)[VW], uint64_t k, uint64_t c0, int esh,
+                                            const typename F::T *lo, const typename F::T *hi) {
+    using T = typename F::T;
+    if (k == 0) return;
+    if constexpr (VW >= 4) {
+        T w = big_root_f<F>(lo, hi, (uint32_t)((c0 * k) << esh));
+        const T d = big_root_f<F>(lo, hi, (uint32_t)(k << esh));
+#pragma unroll
+        for (int j = 0; j < VW; ++j) {
+            v[j] = F::twmul(v[j], w);
+            if (j + 1 < VW) w = F::twmul(w, d);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < VW; ++j) {
+            const uint32_t E = (uint32_t)(((c0 + j) * k) << esh);
+            if (E) v[j] = F::twmul(v[j], big_root_f<F>(lo, hi, E));
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // One column pass over tiles of R = 2^LOGR rows x C = 2^F::ncol_lg(LOGR) columns.
 // ---------------------------------------------------------------------------
@@ -116,14 +142,7 @@ k_pass(typename F::T *__restrict__ data, BitMap map, int lgN, int lgS, uint8_t *
         } else {
             unpack16(*reinterpret_cast<const uint4 *>(data + g), v);
         }
-        if (INV) {
-            const uint64_t k = pos_to_freq<LOGR>(i);
-#pragma unroll
-            for (int j = 0; j < VW; ++j) {
-                const uint32_t E = (uint32_t)(((col0 + c + j) * k) << esh);
-                if (E) v[j] = F::twmul(v[j], big_root_f<F>(rt.big_lo_inv, rt.big_hi_inv, E));
-            }
-        }
+        if (INV) row_twiddle<F, VW>(v, pos_to_freq<LOGR>(i), col0 + c, esh, rt.big_lo_inv, rt.big_hi_inv);
 #pragma unroll
         for (int j = 0; j < VW; ++j) smem[sp(e0 + j)] = v[j];
     }
@@ -141,14 +160,7 @@ k_pass(typename F::T *__restrict__ data, BitMap map, int lgN, int lgS, uint8_t *
         T v[VW];
 #pragma unroll
         for (int j = 0; j < VW; ++j) v[j] = smem[sp(e0 + j)];
-        if (!INV) {
-            const uint64_t k = pos_to_freq<LOGR>(i);
-#pragma unroll
-            for (int j = 0; j < VW; ++j) {
-                const uint32_t E = (uint32_t)(((col0 + c + j) * k) << esh);
-                if (E) v[j] = F::twmul(v[j], big_root_f<F>(rt.big_lo_fwd, rt.big_hi_fwd, E));
-            }
-        }
+        if (!INV) row_twiddle<F, VW>(v, pos_to_freq<LOGR>(i), col0 + c, esh, rt.big_lo_fwd, rt.big_hi_fwd);
         if (PARITY_OUT) {
 #pragma unroll
             for (int j = 0; j < VW; ++j) {
