@@ -48,11 +48,11 @@ WORKLOADS = {
                        "m = floor(0.4 n), Bernoulli(1/2) x and y"),
     # the QRNG example of the paper: n1 = 6.5e9, k1 = 581295000, eps = 1e-10
     "qrng_toeplitz": dict(kind=0, n=6_500_000_000, m=581_294_933,
-                          name="Toeplitz at the QRNG example's sizes: n = 6.5e9, m = 581294933 "
-                               "(two products of length 2^32), Bernoulli(1/2) x and y"),
+                          name="Toeplitz at the QRNG example's sizes: n = 6.5e9, m = 581294933, "
+                               "Bernoulli(1/2) x and y"),
     "qrng_circulant": dict(kind=1, n=6_500_000_068, m=581_294_933,
-                           name="Circulant at the QRNG example's sizes: P = 6500000069, m = 581294933 "
-                                "(two products of length 2^32), Bernoulli(1/2) x and y"),
+                           name="Circulant at the QRNG example's sizes: P = 6500000069, m = 581294933, "
+                                "Bernoulli(1/2) x and y"),
 }
 KIND_NAMES = {0: "toeplitz", 1: "circulant", 2: "dodis"}
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
@@ -221,10 +221,14 @@ def kernel_butterflies(kernel, L):
     return None
 
 
-def path_bytes(L, n, seedlen, m, esz=8):
-    """6 esz L + bit I/O: one write and one read of three L-element arrays
-    (48L for Goldilocks, 24L for the 32-bit field)."""
-    return 6 * esz * L + (n + seedlen + m) / 8
+def path_bytes(products, n, seedlen, m):
+    """Bytes the path moves at least: per product of transform length L over
+    e-byte elements, one write and one read of three L-element arrays (6 e L:
+    48L for Goldilocks, 24L for the 32-bit field), plus the bit I/O once."""
+    tot = (n + seedlen + m) / 8
+    for p in products:
+        tot += 6 * (4 if p["field"] == 2 else 8) * p["L"]
+    return tot
 
 
 def cpu_oracle_rate(kind, n, m, xw, yw, budget_s=12.0):
@@ -446,7 +450,9 @@ def run_batched_a(args, world, rank, local):
     plain_value = world * out_bits / (statistics.median(plain_ms) * 1e-3) / 1e9
 
     # roofline of the work-list kernel (the only kernel of a step)
-    Ls = np.array([native.ntt_length(native.TOEPLITZ, int(n), int(m)) for n, m in zip(ns, ms)])
+    # (the work list plans every instance as one transform)
+    Ls = np.array([native.plan_query(native.TOEPLITZ, int(n), int(m), plan_mode=native.PLAN_SINGLE)
+                   ["transform_length"] for n, m in zip(ns, ms)])
     big = Ls > (1 << 13)
     alg = float(24 * Ls[big].sum() + ((ns + (ns + ms - 1) + ms) / 8).sum())  # 32-bit field elements
     peak, peak_src = measured_peaks()
@@ -1039,8 +1045,10 @@ def main():
     wl = WORKLOADS[args.workload]
     kind, n, m = wl["kind"], wl["n"], wl["m"]
     sb = seed_bits(kind, n, m)
-    L = native.ntt_length(kind, n, m)
-    launches = native.launch_count(kind, n, m)
+    plan = native.plan_query(kind, n, m)
+    products = native.plan_products(kind, n, m)
+    L = plan["transform_length"]
+    launches = plan["launches"]
     ctx = native.Context(local)
     stream = torch.cuda.current_stream()
 
@@ -1121,11 +1129,39 @@ def main():
             "avg_launch_ms": per_launch,
             "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src, "algorithmic_bytes_per_launch": alg}}
-    blocks = native.block_count(kind, n, m)
-    pb = blocks * path_bytes(L, n, sb, m, field_of(dom)[1])
-    path_roof = {"bytes_48L": pb, "achieved_gbs": pb / (ms_per_step * 1e-3) / 1e9,
+    pb = path_bytes(products, n, sb, m)
+    path_roof = {"model": "6 e L per product (e = element bytes) + bit I/O", "bytes": pb,
+                 "achieved_gbs": pb / (ms_per_step * 1e-3) / 1e9,
                  "frac_of_measured_hbm": pb / (ms_per_step * 1e-3) / 1e9 / peak,
                  "frac_of_8tbs": pb / (ms_per_step * 1e-3) / 1e9 / 8000.0}
+
+    # the Dodis et al. workload as its configuration states it: one Goldilocks
+    # transform of length 2^31 (single-transform plan); same bits
+    as_configured = None
+    if args.workload == "dodis":
+        gctx = native.Context(local, field=native.FIELD_GOLDILOCKS, plan_mode=native.PLAN_SINGLE)
+        zg = torch.empty_like(zd)
+        gcall = lambda: gctx.dodis(xd, yd, n, m, zg)  # noqa: E731
+        for _ in range(2):
+            gcall()
+        g_ms = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            gcall()
+            b.record(stream)
+            torch.cuda.synchronize()
+            g_ms.append(a.elapsed_time(b))
+        assert torch.equal(zg, zd), "single-transform result differs"
+        gq = native.plan_query(kind, n, m, field=native.FIELD_GOLDILOCKS, plan_mode=native.PLAN_SINGLE)
+        as_configured = {"plan": "one Goldilocks transform of length 2^31 (CM_FIELD_GOLDILOCKS, CM_PLAN_SINGLE)",
+                         "transform_length": gq["transform_length"], "ms_per_step": statistics.median(g_ms),
+                         "value": world * m / (statistics.median(g_ms) * 1e-3) / 1e9, "unit": "Gbit/s",
+                         "bit_identical": True}
+        gctx.close()
+        del zg
+        torch.cuda.empty_cache()
 
     # end to end through the public API with host buffers
     xh = torch.from_numpy(xw.view(np.int64)).pin_memory()
@@ -1160,13 +1196,18 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": wl["name"], "n": n, "m": m, "L": L, "products": blocks, "seed_bits": sb,
+            "config": {"workload": wl["name"], "n": n, "m": m, "seed_bits": sb,
+                       "plan": {"products": plan["products"], "windows": plan["windows"],
+                                "transform_length": L,
+                                "field": "q = 3 * 2^30 + 1" if plan["field"] == 2 else "Goldilocks",
+                                "planner_estimate_ms": plan["est_ms"]},
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "latency_ms": {"p50": statistics.median(step_ms),
                            "p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},
             "roofline": roof, "path_roofline": path_roof, "kernels": kernels,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            **({"as_configured": as_configured} if as_configured else {}),
             "gpu_launches": launches * args.steps,
         }
         print(json.dumps(line), flush=True)

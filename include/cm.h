@@ -68,14 +68,28 @@ typedef struct {
     uint32_t max_transform_lg;
     /* Transform field of the single calls: CM_FIELD_AUTO takes the 32-bit field
      * of the prime 3 * 2^30 + 1 (the paper's small field, Section "Performance")
-     * for every product of length <= 2^30 and Goldilocks above;
+     * for every product of length <= 2^30 and Goldilocks above (and the
+     * planner may prefer 32-bit-field blocks to one Goldilocks transform);
      * CM_FIELD_GOLDILOCKS takes Goldilocks throughout.  Results are identical. */
     uint32_t field;
-    uint32_t reserved[6];
+    /* Most input blocks whose transform-domain products are summed before one
+     * inverse transform; 0 = as many as keep every count below the field's
+     * characteristic.  Later groups XOR their parities in.  Results are
+     * identical for every value. */
+    uint32_t max_sum_blocks;
+    /* CM_PLAN_COST: the planner splits a product whenever that is estimated
+     * faster; CM_PLAN_SINGLE: one transform whenever K + m - 1 fits the limit
+     * (splits only longer products).  Results are identical. */
+    uint32_t plan_mode;
+    uint32_t reserved[4];
 } cm_options;
+
+#define CM_PLAN_COST 0u
+#define CM_PLAN_SINGLE 1u
 
 #define CM_FIELD_AUTO 0u
 #define CM_FIELD_GOLDILOCKS 1u
+#define CM_FIELD_Q30 2u /* reported by cm_plan_query only: q = 3 * 2^30 + 1 */
 
 /* Create a context on CUDA device `device`: root tables resident in HBM, a
  * scratch memory pool.  opt may be NULL.  Returns CM_EDEVICE if the device is
@@ -97,14 +111,18 @@ const char *cm_status_str(int status);
  * words, written).  Requires 1 <= n, m <= 2^40 (the input lengths the paper's
  * software accepts, Section "Introduction").  CM_EINVAL otherwise.
  *
- * Lengths (all three extractors): the product is one transform when
- * K + m - 1 <= 2^32 (the Goldilocks limit; K = n, n + 1, n for Toeplitz,
- * Circulant, Dodis et al.) or the context's lower max_transform_lg.  Longer
- * products are split: over input blocks (GF(2)-linearity: the output is the
- * XOR of the blocks' outputs) and, when m exceeds half the limit, over output
- * blocks; each block is an ordinary middle product of transform length at
- * most the limit, run in turn with the scratch of one block
- * (cm_block_count).
+ * Lengths (all three extractors): the middle product has K + m - 1 terms
+ * (K = n, n + 1, n for Toeplitz, Circulant, Dodis et al.).  It runs as one
+ * transform of the smallest power of two >= K + m - 1, or split: over input
+ * blocks (GF(2)-linearity: the output is the parity of the sum over blocks;
+ * the blocks of one output window share one transform length, their
+ * transform-domain products are added and one inverse transform serves the
+ * window) and over output windows.  A planner picks the form with the lowest
+ * estimated GPU time among those whose transforms fit 2^32 (or the context's
+ * max_transform_lg) and whose scratch fits the HBM budget: a split is taken
+ * when it is faster, e.g. 32-bit-field blocks of 2^30 instead of one
+ * Goldilocks transform of 2^31, and whenever one transform cannot hold the
+ * product.  Products run in turn with the scratch of one (cm_plan_query).
  */
 cm_status cm_toeplitz(cm_ctx *ctx, const uint64_t *x, uint64_t n, const uint64_t *y, uint64_t m,
                       uint64_t *z, cm_stream stream);
@@ -397,24 +415,67 @@ uint64_t cm_next_na_prime(uint64_t n);
 /* Largest member of N_A <= n (0 if n < 3). */
 uint64_t cm_prev_na_prime(uint64_t n);
 
-/* Transform length L the library uses for (kind, n, m) with the default
- * limit: the smallest power of two >= K + m - 1 with K = n (Toeplitz), n + 1
- * (Circulant), n (Dodis); for a blocked product the longest block's; 0 if the
- * arguments are invalid for that kind. */
+/* How a single call of (kind, n, m) runs under the given options (the
+ * planner of cm_toeplitz). */
+typedef struct {
+    uint64_t transform_length; /* the longest product's transform length L */
+    uint64_t products;         /* middle products: input blocks x output windows */
+    uint64_t windows;          /* output windows (one inverse transform each) */
+    uint64_t scratch_bytes;    /* pool bytes the call holds */
+    uint32_t launches;         /* kernel launches the call enqueues */
+    uint32_t field;            /* CM_FIELD_GOLDILOCKS if any product runs over
+                                  Goldilocks, else CM_FIELD_Q30 */
+    double est_ms;             /* the planner's GPU-time estimate (GB300) */
+    uint64_t reserved[4];
+} cm_plan_info;
+
+/* Fill *out with the plan of (kind, n, m) under opt (NULL: defaults, no
+ * budget).  CM_EINVAL if the arguments or options are invalid, or the product
+ * needs more than 65536 middle products. */
+cm_status cm_plan_query(int kind, uint64_t n, uint64_t m, const cm_options *opt, cm_plan_info *out);
+
+/* One middle product of a call's plan (cm_plan_products).  Its operands are
+ * bit maps over x (a) and y (b): the value at transform position k in [0, L)
+ * is 0 for k >= len, else the source bit at
+ *   mode 0: k;   mode 1: (k + off) mod srclen;
+ *   mode 2: off - k, or 0 when off - k is outside [0, srclen).
+ * With c the cyclic convolution of length L of the two maps, output
+ * zword * 64 + i (i < m) of the call is the parity of the sum of c[K - 1 + i]
+ * over the product's sum group (sum 1 .. 3 in order, or the product alone,
+ * sum 0), XORed over the window's groups. */
+typedef struct {
+    uint64_t K, m, L, zword;
+    uint64_t a_len, a_srclen, a_off;
+    uint64_t b_len, b_srclen, b_off;
+    uint32_t a_mode, b_mode;
+    uint32_t field;    /* CM_FIELD_GOLDILOCKS or CM_FIELD_Q30 */
+    int32_t sum;       /* 0 alone, 1 first of a sum group, 2 inner, 3 last */
+    uint32_t xor_into; /* this product's parities are XORed into z */
+    uint32_t reserved;
+} cm_product_desc;
+
+/* Write up to cap product descriptors of the plan of (kind, n, m) under opt
+ * to out (may be NULL when cap is 0) and their number to *count.  CM_EINVAL
+ * as cm_plan_query. */
+cm_status cm_plan_products(int kind, uint64_t n, uint64_t m, const cm_options *opt, cm_product_desc *out,
+                           uint64_t cap, uint64_t *count);
+
+/* Transform length of the longest product of (kind, n, m) with default
+ * options (cm_plan_query); 0 if the arguments are invalid for that kind. */
 uint64_t cm_ntt_length(int kind, uint64_t n, uint64_t m);
 
 /* Bytes of scratch one call of (kind, n, m) takes from the pool (default
- * limit). */
+ * options). */
 uint64_t cm_scratch_bytes(int kind, uint64_t n, uint64_t m);
 
 /* Number of kernel launches one call of (kind, n, m) enqueues (default
- * limit). */
+ * options). */
 uint32_t cm_launch_count(int kind, uint64_t n, uint64_t m);
 
 /* Number of middle products a call of (kind, n, m) runs when one transform
- * may be at most 2^max_transform_lg long (0 = 32): 1 when K + m - 1 fits, else
- * the input blocks times the output blocks; 0 if invalid (including a
- * max_transform_lg outside 8..32 or more than 65536 products). */
+ * may be at most 2^max_transform_lg long (0 = 32), other options default; 0 if
+ * invalid (including a max_transform_lg outside 8..32 or more than 65536
+ * products). */
 uint64_t cm_block_count(int kind, uint64_t n, uint64_t m, uint32_t max_transform_lg);
 
 #ifdef __cplusplus

@@ -58,13 +58,29 @@ static bool base_maps(int kind, uint64_t n, uint64_t m, Plan *p) {
     return true;
 }
 
-// Transform length, pass split, scratch and launch count for K + m - 1 <= 2^32.
-static void finish_plan(Plan *p) {
+// Scratch of one product: the operands A and B (and the transform-domain sum C
+// of a summed window) and the parity bytes; one-CTA plans (lg <= 13) keep
+// everything on chip.  A single call's plan adds 256 bytes of Dodis et al.
+// precondition flags (kFlagBytes).
+constexpr uint64_t kFlagBytes = 256;
+static uint64_t flag_bytes(int kind) { return kind == CM_DODIS ? kFlagBytes : 0; }
+static uint64_t plan_scratch(int lg, uint64_t m, int field, bool summed) {
+    if (lg <= kMidLgMax) return 0;
+    const uint64_t esz = field == kFieldF30 ? 4 : 8;
+    return (summed ? 3 : 2) * esz * (1ull << lg) + ((m + 255) & ~255ull);
+}
+
+// Transform length (at least 2^min_lg), field, pass split, scratch and launch
+// count for K + m - 1 <= 2^32.
+static void finish_plan(Plan *p, bool allow_f30, int min_lg, bool summed) {
     const uint64_t need = p->K + p->m - 1;
     p->lg = ceil_log2(need);
+    if (p->lg < min_lg) p->lg = min_lg;
     if (p->lg < 1) p->lg = 1;
     p->L = 1ull << p->lg;
     p->lo = p->K - 1;
+    p->field = (allow_f30 && p->lg <= kF30MaxLg) ? kFieldF30 : kFieldGL;
+    p->summed = summed;
     const int rest = p->lg - kMidLgMax;
     if (rest <= 0) {
         p->npass = 0;
@@ -76,73 +92,244 @@ static void finish_plan(Plan *p) {
         p->pass_lg[0] = (rest + 1) / 2;
         p->pass_lg[1] = rest / 2;
     }
-    const uint64_t flags = (p->kind == CM_DODIS) ? 256 : 0;
-    if (p->npass == 0) {
-        p->scratch_bytes = flags;
-        p->launches = 1;
-    } else {
-        p->scratch_bytes = 2 * 8 * p->L + ((p->m + 255) & ~255ull) + flags;
-        // forward passes of both operands, middle, inverse passes, pack
-        p->launches = 2 * p->npass + 1 + p->npass + 1;
-    }
+    p->scratch_bytes = plan_scratch(p->lg, p->m, p->field, summed) + flag_bytes(p->kind);
+    // forward passes of both operands, middle, inverse passes, pack
+    p->launches = p->npass == 0 ? 1 : 2 * p->npass + 1 + p->npass + 1;
     if (p->kind == CM_DODIS) p->launches += 1;  // precondition check
 }
 
 bool make_plan(int kind, uint64_t n, uint64_t m, Plan *p, bool allow_f30) {
     if (!base_maps(kind, n, m, p)) return false;
     if (p->K + m - 1 > (1ull << 32)) return false;
-    finish_plan(p);
-    if (allow_f30 && p->lg <= kF30MaxLg) p->field = kFieldF30;
+    finish_plan(p, allow_f30, 1, false);
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// Block planner.
+//
 // z_i = sum_{t<K} a_t b_{t+i} splits over input blocks t in [T0, T0 + kb)
-// (each a middle product of a[T0 .. T0 + kb) with b[T0 .. T0 + kb + m - 1),
-// the results XORed: parity of a sum is the XOR of the parities) and over
-// output blocks i in [I0, I0 + mb) (b shifted by I0).  In transform positions
-// u = K - 1 - t, input block [D, D + kb) of A is A shifted by D.
-bool make_blocks(int kind, uint64_t n, uint64_t m, int max_lg, bool allow_f30, std::vector<Block> *out) {
+// (each a middle product of a[T0 .. T0 + kb) with b[T0 .. T0 + kb + m - 1))
+// and over output windows i in [I0, I0 + mb) (b shifted by I0).  In transform
+// positions u = K - 1 - t, input block [D, D + kb) of A is A shifted by D.
+// Every input block of a window is planned with the same K = Kb (a shorter
+// last block is zero beyond its kb positions and its b map moves back by
+// Kb - kb), so all of them share the transform length and the output window
+// position: their transform-domain products are added (exact integer counts,
+// at most K < q in total) and one inverse transform with parity serves the
+// window.
+//
+// Shapes (block transform length 2^lg, output windows, input blocks) are
+// compared by an estimate of GPU time built from measured whole-extraction
+// times per transform length and field: a summed window costs nin times the
+// forward share (both forward transforms and the middle) plus one inverse
+// share.
+// ---------------------------------------------------------------------------
+
+// Measured on one GB300 (SM clock 2070 MHz): ms per extraction of transform
+// length 2^lg (Toeplitz, K = L/2 + 1, m = L/4); below 2^16 launch latency
+// dominates and the figures are floors.
+static const double kCostF30[kF30MaxLg + 1] = {
+    0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,   0.02,   0.02,
+    0.02,  0.02,  0.02,  0.080, 0.081, 0.0822, 0.0829, 0.0857, 0.0950, 0.0991, 0.1162,
+    0.1907, 0.3389, 0.6710, 1.3995, 2.6839, 5.4039, 10.960, 22.246, 45.643};
+static const double kCostGL[33] = {
+    0.03,  0.03,  0.03,  0.03,  0.03,  0.03,  0.03,  0.03,  0.03,   0.03,   0.03,
+    0.03,  0.03,  0.03,  0.130, 0.133, 0.1356, 0.1419, 0.1459, 0.1604, 0.1678, 0.2221,
+    0.4375, 0.8792, 1.6702, 3.3082, 7.4412, 15.095, 30.538, 62.422, 127.87, 261.78, 534.40};
+constexpr double kFwdShare = 0.77;     // forward passes of both operands + middle
+constexpr double kXorMs = 0.005;       // one k_xor_into launch
+constexpr double kSingleMargin = 0.97;  // a blocked shape must beat one transform by 3%
+constexpr int kSumMinLg = kMidLgMax + 1;  // summed windows need a column pass
+
+static uint64_t words_of(uint64_t bits) { return (bits + 63) / 64; }
+static uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+static double plan_cost(int field, int lg) { return field == kFieldF30 ? kCostF30[lg] : kCostGL[lg]; }
+
+// Input blocks whose products one sum may hold: the counts of G blocks add up
+// to at most G Kb, which must stay below the field's characteristic (the
+// Goldilocks prime exceeds every count up to 2^40).  Windows with more blocks
+// sum in groups, each with its own inverse transform; the groups' parities XOR.
+static uint64_t group_size(int field, uint64_t Kb, uint64_t nin, uint32_t cap) {
+    uint64_t g = field == kFieldF30 ? (F30_Q - 1) / Kb : nin;  // >= 3: Kb <= 2^30
+    if (cap && g > cap) g = cap;
+    return g < nin ? g : nin;
+}
+
+// One window of nin input blocks summed in groups of G (G = 1: every block
+// inverse-transformed on its own and XORed).
+static double window_cost(int field, int lg, uint64_t nin, uint64_t G) {
+    const double t = plan_cost(field, lg);
+    const uint64_t ng = ceil_div(nin, G);
+    if (G == 1) return (double)nin * t + (double)(nin - 1) * kXorMs;
+    return ((double)nin * kFwdShare + (double)ng * (1.0 - kFwdShare)) * t + (double)(ng - 1) * kXorMs;
+}
+
+
+struct Shape {
+    int lg;          // limit of the block transforms
+    uint64_t Mb;     // outputs per window (a multiple of 64 when m splits)
+    uint64_t nout;   // windows
+    uint64_t nin;    // input blocks per window
+    uint64_t Kb;     // terms per input block
+    bool summed;
+    double cost;
+    uint64_t scratch;
+};
+
+// Window transform length, field and scratch of a shape.
+static int window_lg(const Shape &s, uint64_t mr) {
+    int lg = ceil_log2(s.Kb + mr - 1);
+    if (s.summed && lg < kSumMinLg) lg = kSumMinLg;
+    return lg < 1 ? 1 : lg;
+}
+
+static int field_of(bool allow_f30, int lg) { return (allow_f30 && lg <= kF30MaxLg) ? kFieldF30 : kFieldGL; }
+
+static void evaluate(int kind, uint64_t m, bool allow_f30, uint32_t max_sum, Shape *s) {
+    const uint64_t mlast = m - (s->nout - 1) * s->Mb;
+    s->cost = 0;
+    s->scratch = 0;
+    bool xors = false;
+    for (int w = 0; w < 2; ++w) {  // the nout - 1 full windows, then the last
+        const uint64_t cnt = w == 0 ? s->nout - 1 : 1, mr = w == 0 ? s->Mb : mlast;
+        if (!cnt) continue;
+        const int lg = window_lg(*s, mr);
+        const int field = field_of(allow_f30, lg);
+        const uint64_t G = s->summed ? group_size(field, s->Kb, s->nin, max_sum) : 1;
+        s->cost += (double)cnt * window_cost(field, lg, s->nin, G);
+        const uint64_t sc = plan_scratch(lg, mr, field, s->summed);
+        if (sc > s->scratch) s->scratch = sc;
+        xors = xors || G < s->nin;
+    }
+    // blocks_scratch's layout: XOR temporary, then the precondition flags
+    const uint64_t tmp_off = (s->scratch + 255) & ~255ull, tmpw = xors ? words_of(s->Mb) : 0;
+    if (kind == CM_DODIS) s->scratch = ((tmp_off + 8 * tmpw + 255) & ~255ull) + kFlagBytes;
+    else if (tmpw) s->scratch = tmp_off + 8 * tmpw;
+}
+
+bool plan_options(const cm_options *opt, PlanOptions *o) {
+    *o = PlanOptions();
+    if (!opt) return true;
+    if (opt->max_transform_lg) {
+        if (opt->max_transform_lg < 8 || opt->max_transform_lg > 32) return false;
+        o->max_lg = (int)opt->max_transform_lg;
+    }
+    if (opt->field > CM_FIELD_GOLDILOCKS) return false;
+    o->allow_f30 = opt->field != CM_FIELD_GOLDILOCKS;
+    o->budget = opt->hbm_budget_bytes;
+    o->max_sum = opt->max_sum_blocks;
+    if (opt->plan_mode > CM_PLAN_SINGLE) return false;
+    o->single = opt->plan_mode == CM_PLAN_SINGLE;
+    return true;
+}
+
+bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::vector<Block> *out) {
+    const int max_lg = o.max_lg;
+    const bool allow_f30 = o.allow_f30;
+    const uint64_t budget = o.budget;
     out->clear();
     Plan b;
     if (max_lg < 8 || max_lg > 32 || !base_maps(kind, n, m, &b)) return false;
-    const uint64_t Lmax = 1ull << max_lg;
-    if (b.K + m - 1 <= Lmax) {
-        finish_plan(&b);
-        if (allow_f30 && b.lg <= kF30MaxLg) b.field = kFieldF30;
-        out->push_back({b, 0, false});
+    const uint64_t K = b.K;
+    // candidate block limits: the single transform (when it fits) and, when the
+    // limit allows column-pass plans, every limit from 2^14 up
+    const int lg_single = ceil_log2(K + m - 1);
+    std::vector<int> lgs;
+    if (lg_single <= max_lg) lgs.push_back(lg_single);
+    if (lg_single <= max_lg && o.single) {
+        // one transform, as asked
+    } else if (max_lg <= kMidLgMax) {
+        if (lg_single > max_lg) lgs.push_back(max_lg);
+    } else {
+        for (int lg = kSumMinLg; lg <= max_lg; ++lg)
+            if (lg != lg_single) lgs.push_back(lg);
+    }
+    Shape best{};
+    bool have = false, best_fits = false;
+    for (int lg : lgs) {
+        const uint64_t Lmax = 1ull << lg;
+        const uint64_t nout_min = ceil_div(m, Lmax);
+        uint64_t nout_max = nout_min * 4 + 16;
+        if (nout_max > kMaxBlocks) nout_max = kMaxBlocks;
+        for (uint64_t nout = nout_min; nout <= nout_max; ++nout) {
+            Shape s{};
+            s.lg = lg;
+            s.Mb = nout == 1 ? m : ceil_div(ceil_div(m, nout), 64) * 64;
+            if (ceil_div(m, s.Mb) != nout || s.Mb > Lmax) continue;
+            s.nout = nout;
+            const uint64_t kmax = Lmax - s.Mb + 1;
+            s.nin = ceil_div(K, kmax);
+            if (s.nin > kMaxBlocks / s.nout) continue;  // (no overflow: both <= 2^40)
+            s.Kb = ceil_div(K, s.nin);
+            s.summed = s.nin > 1 && max_lg > kMidLgMax;
+            evaluate(kind, m, allow_f30, o.max_sum, &s);
+            const bool single = s.nin == 1 && s.nout == 1;
+            const bool fits = budget == 0 || s.scratch <= budget;
+            double c = s.cost, bc = best.cost;
+            if (!single) c /= kSingleMargin;
+            if (have && best.nin * best.nout != 1) bc /= kSingleMargin;
+            const bool better = !have || (fits && !best_fits) ||
+                                (fits == best_fits &&
+                                 (c < bc || (c == bc && s.nin * s.nout < best.nin * best.nout)));
+            if (better) {
+                best = s;
+                have = true;
+                best_fits = fits;
+            }
+        }
+    }
+    if (!have) return false;
+    const Shape &s = best;
+    if (s.nin == 1 && s.nout == 1) {
+        finish_plan(&b, allow_f30, 1, false);
+        out->push_back({b, 0, kSumNone, false});
         return true;
     }
-    const uint64_t Mb = m > Lmax / 2 ? Lmax / 2 : m;  // a multiple of 64 when it splits m
-    const uint64_t nout = (m + Mb - 1) / Mb;
-    const uint64_t kmax = Lmax - Mb + 1;
-    const uint64_t nin = (b.K + kmax - 1) / kmax;
-    if (nin * nout > kMaxBlocks) return false;
-    const uint64_t Kb = (b.K + nin - 1) / nin;
-    for (uint64_t r = 0; r < nout; ++r) {
-        const uint64_t I0 = r * Mb, mr = (m - I0 < Mb) ? m - I0 : Mb;
-        for (uint64_t j = 0; j < nin; ++j) {
-            const uint64_t D = j * Kb;
-            if (D >= b.K) break;
-            const uint64_t kb = (b.K - D < Kb) ? b.K - D : Kb;
-            const uint64_t T0 = b.K - D - kb;
+    for (uint64_t r = 0; r < s.nout; ++r) {
+        const uint64_t I0 = r * s.Mb, mr = (m - I0 < s.Mb) ? m - I0 : s.Mb;
+        const int lg_r = window_lg(s, mr);
+        const uint64_t G = s.summed ? group_size(field_of(allow_f30, lg_r), s.Kb, s.nin, o.max_sum) : 1;
+        for (uint64_t j = 0; j < s.nin; ++j) {
+            const uint64_t D = j * s.Kb;  // < K: (nin - 1) Kb < K
+            const uint64_t kb = (K - D < s.Kb) ? K - D : s.Kb;
+            const uint64_t T0 = K - D - kb;
             Plan q = b;
             q.m = mr;
-            q.K = kb;
+            q.K = s.Kb;
             if (b.amode == kIdentity) {  // A'_u = x_{D+u}: no wrap, u + D < K = srclen
                 q.amode = kModForward;
                 q.aoff = D;
             } else {  // A'_u = src[aoff - D - u]
                 q.aoff = b.aoff - D;
             }
-            q.alen = kb;
-            q.blen = kb + mr - 1;
-            q.boff = (b.boff + T0 + I0) % b.bsrclen;
-            finish_plan(&q);
-            if (allow_f30 && q.lg <= kF30MaxLg) q.field = kFieldF30;
-            out->push_back({q, I0 / 64, j != 0});
+            q.alen = kb;  // zero beyond: the padded positions of a short block
+            q.blen = s.Kb + mr - 1;
+            // B'_v = B_{v + T0 + I0 - (Kb - kb)}, kept in [0, bsrclen)
+            const uint64_t src = b.bsrclen;
+            q.boff = ((b.boff + T0 + I0) % src + src - (s.Kb - kb) % src) % src;
+            finish_plan(&q, allow_f30, lg_r, s.summed);
+            // sum group [g0, g1) of this window; a group of one stands alone
+            const uint64_t g0 = j / G * G, g1 = (g0 + G < s.nin) ? g0 + G : s.nin;
+            int sum = kSumNone;
+            if (g1 - g0 > 1) sum = j == g0 ? kSumFirst : (j + 1 == g1 ? kSumLast : kSumInner);
+            const bool packs = sum == kSumNone || sum == kSumLast;
+            out->push_back({q, I0 / 64, sum, packs && g0 != 0});
         }
     }
     return true;
+}
+
+double blocks_cost_ms(const std::vector<Block> &bl) {
+    double c = 0;
+    for (const Block &b : bl) {
+        const double t = plan_cost(b.p.field, b.p.lg);
+        if (b.sum == kSumNone) c += t;
+        else c += kFwdShare * t + (b.sum == kSumLast ? (1.0 - kFwdShare) * t : 0.0);
+        if (b.xor_into) c += kXorMs;
+    }
+    return c;
 }
 
 static BitMap bitmap(const uint64_t *src, int mode, uint64_t len, uint64_t srclen, uint64_t off) {
@@ -161,23 +348,18 @@ static cm_status cuda_status(cudaError_t e) {
     return CM_EDEVICE;
 }
 
-// Enqueue one extraction described by plan p.  scratch holds p.scratch_bytes.
-cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const uint64_t *y,
-                          uint64_t *z, void *scratch, cudaStream_t st) {
+// Enqueue the product of plan p (no precondition check; pre: the Dodis et al.
+// flags the pack kernel reads, or null).  scratch holds p.scratch_bytes; sum
+// (SumMode) says whether the product stands alone or joins its window's sum.
+static cm_status enqueue_product(cm_ctx *ctx, const Plan &p, const uint64_t *x, const uint64_t *y,
+                                 uint64_t *z, void *scratch, const uint32_t *pre, int sum, cudaStream_t st) {
     const BitMap am = bitmap(x, p.amode, p.alen, p.asrclen, p.aoff);
     const BitMap bm = bitmap(y, p.bmode, p.blen, p.bsrclen, p.boff);
     const bool f30 = p.field == kFieldF30;
     const uint64_t linv = f30 ? f30_linv_mont2(p.L) : gl_inv_pow2_host(p.L);
     const size_t esz = f30 ? sizeof(uint32_t) : sizeof(uint64_t);
-    uint32_t *pre = nullptr;
     cudaError_t e;
     uint8_t *sc = static_cast<uint8_t *>(scratch);
-    if (p.kind == CM_DODIS) {
-        pre = reinterpret_cast<uint32_t *>(sc + p.scratch_bytes - 256);
-        if ((e = cudaMemsetAsync(pre, 0, 2 * sizeof(uint32_t), st)) != cudaSuccess) return cuda_status(e);
-        ProfScope ps(ctx, "k_allsame", st);
-        if ((e = launch_allsame(x, p.n, pre, ctx->nsm, st)) != cudaSuccess) return cuda_status(e);
-    }
     if (p.npass == 0) {
         Launch q;
         q.amap = am;
@@ -197,7 +379,8 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
     }
     void *A = sc;
     void *B = sc + esz * p.L;
-    uint8_t *par = sc + 2 * esz * p.L;
+    void *C = sum == kSumNone ? nullptr : sc + 2 * esz * p.L;
+    uint8_t *par = sc + (sum == kSumNone ? 2 : 3) * esz * p.L;
 
     int lgN[2], lgS[2];
     int cur = p.lg;
@@ -228,13 +411,16 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
     }
     {
         ProfScope ps(ctx, f30 ? "k_middle_f30" : "k_middle", st);
-        if ((e = launch_middle(p.field, A, B, p.L, linv, ctx->rt, ctx->rt30, ctx->nsm, st)) != cudaSuccess)
-            return cuda_status(e);
+        e = launch_middle(p.field, A, B, C, sum == kSumInner || sum == kSumLast, p.L, linv, ctx->rt, ctx->rt30,
+                          ctx->nsm, st);
+        if (e != cudaSuccess) return cuda_status(e);
     }
+    if (sum == kSumFirst || sum == kSumInner) return CM_OK;  // the window's last block finishes
+    void *R = C ? C : A;
     for (int j = p.npass - 1; j >= 0; --j) {
         PassArgs a;
         memset(&a, 0, sizeof(a));
-        a.data = A;
+        a.data = R;
         a.lgN = lgN[j];
         a.lgS = lgS[j];
         a.field = p.field;
@@ -254,29 +440,59 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
     return cuda_status(launch_pack(par, p.m, z, pre, ctx->d_status, ctx->nsm, st));
 }
 
-static uint64_t words_of(uint64_t bits) { return (bits + 63) / 64; }
+// Dodis et al. precondition flags at pre (two words, reset first).
+static cm_status enqueue_precondition(cm_ctx *ctx, const uint64_t *x, uint64_t n, uint32_t *pre, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(pre, 0, 2 * sizeof(uint32_t), st)) != cudaSuccess) return cuda_status(e);
+    ProfScope ps(ctx, "k_allsame", st);
+    return cuda_status(launch_allsame(x, n, pre, ctx->nsm, st));
+}
 
-// Scratch of a blocked run: the largest block's scratch, then (when blocks
-// accumulate) one output window of XOR temporary at *tmp_off.
-static uint64_t blocks_scratch(const std::vector<Block> &bl, uint64_t *tmp_off) {
+// Enqueue one single-transform extraction described by plan p.  scratch holds
+// p.scratch_bytes (the Dodis et al. flags in its last 256 bytes).
+cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const uint64_t *y,
+                          uint64_t *z, void *scratch, cudaStream_t st) {
+    uint32_t *pre = nullptr;
+    if (p.kind == CM_DODIS) {
+        pre = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(scratch) + p.scratch_bytes - 256);
+        cm_status s = enqueue_precondition(ctx, x, p.n, pre, st);
+        if (s != CM_OK) return s;
+    }
+    return enqueue_product(ctx, p, x, y, z, scratch, pre, kSumNone, st);
+}
+
+// Scratch of a blocked run: the largest block's scratch; then (one-CTA windows
+// whose blocks XOR) one output window of temporary at *tmp_off; then 256 bytes
+// of precondition flags at *pre_off.
+static uint64_t blocks_scratch(const std::vector<Block> &bl, uint64_t *tmp_off, uint64_t *pre_off) {
     uint64_t sc = 0, tmpw = 0;
     for (const Block &b : bl) {
-        if (b.p.scratch_bytes > sc) sc = b.p.scratch_bytes;
-        if (b.accumulate && words_of(b.p.m) > tmpw) tmpw = words_of(b.p.m);
+        const uint64_t own = b.p.scratch_bytes - flag_bytes(b.p.kind);  // flags are shared
+        if (own > sc) sc = own;
+        if (b.xor_into && words_of(b.p.m) > tmpw) tmpw = words_of(b.p.m);
     }
     *tmp_off = (sc + 255) & ~255ull;
-    return tmpw ? *tmp_off + 8 * tmpw : sc;
+    *pre_off = (*tmp_off + 8 * tmpw + 255) & ~255ull;
+    const bool dodis = !bl.empty() && bl[0].p.kind == CM_DODIS;
+    if (!dodis && !tmpw) return sc;
+    return dodis ? *pre_off + kFlagBytes : *tmp_off + 8 * tmpw;
 }
 
 // Enqueue every block of an extraction; scratch holds blocks_scratch() bytes.
 static cm_status enqueue_blocks(cm_ctx *ctx, const std::vector<Block> &bl, const uint64_t *x,
                                 const uint64_t *y, uint64_t *z, uint8_t *scratch, uint64_t tmp_off,
-                                cudaStream_t st) {
-    for (const Block &b : bl) {
-        uint64_t *dst = b.accumulate ? reinterpret_cast<uint64_t *>(scratch + tmp_off) : z + b.zword;
-        cm_status s = enqueue_extract(ctx, b.p, x, y, dst, b.p.scratch_bytes ? scratch : nullptr, st);
+                                uint64_t pre_off, cudaStream_t st) {
+    uint32_t *pre = nullptr;
+    if (!bl.empty() && bl[0].p.kind == CM_DODIS) {
+        pre = reinterpret_cast<uint32_t *>(scratch + pre_off);
+        cm_status s = enqueue_precondition(ctx, x, bl[0].p.n, pre, st);
         if (s != CM_OK) return s;
-        if (b.accumulate) {
+    }
+    for (const Block &b : bl) {
+        uint64_t *dst = b.xor_into ? reinterpret_cast<uint64_t *>(scratch + tmp_off) : z + b.zword;
+        cm_status s = enqueue_product(ctx, b.p, x, y, dst, b.p.scratch_bytes ? scratch : nullptr, pre, b.sum, st);
+        if (s != CM_OK) return s;
+        if (b.xor_into) {
             ProfScope ps(ctx, "k_xor_into", st);
             if (launch_xor_into(z + b.zword, dst, words_of(b.p.m), ctx->nsm, st) != cudaSuccess)
                 return CM_EDEVICE;
@@ -289,9 +505,9 @@ cm_status run_single(cm_ctx *ctx, int kind, const uint64_t *x, uint64_t n, const
                      uint64_t m, uint64_t *z, cudaStream_t st) {
     if (!ctx || !x || !y || !z) return CM_EINVAL;
     std::vector<Block> bl;
-    if (!make_blocks(kind, n, m, ctx->max_lg, ctx->allow_f30, &bl)) return CM_EINVAL;
-    uint64_t tmp_off = 0;
-    const uint64_t need = blocks_scratch(bl, &tmp_off);
+    if (!make_blocks(kind, n, m, ctx->popt, &bl)) return CM_EINVAL;
+    uint64_t tmp_off = 0, pre_off = 0;
+    const uint64_t need = blocks_scratch(bl, &tmp_off, &pre_off);
     if (need > ctx->budget) return CM_ENOMEM;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return CM_EDEVICE;
@@ -303,7 +519,7 @@ cm_status run_single(cm_ctx *ctx, int kind, const uint64_t *x, uint64_t n, const
             return CM_ENOMEM;
         }
     }
-    cm_status s = enqueue_blocks(ctx, bl, x, y, z, static_cast<uint8_t *>(scratch), tmp_off, st);
+    cm_status s = enqueue_blocks(ctx, bl, x, y, z, static_cast<uint8_t *>(scratch), tmp_off, pre_off, st);
     if (scratch) {
         e = cudaFreeAsync(scratch, st);
         if (s == CM_OK && e != cudaSuccess) s = CM_EDEVICE;
@@ -398,6 +614,8 @@ using namespace cm;
 extern "C" cm_status cm_create(cm_ctx **out, int device, const cm_options *opt) {
     if (!out) return CM_EINVAL;
     *out = nullptr;
+    PlanOptions po;
+    if (!plan_options(opt, &po)) return CM_EINVAL;
     if (cudaSetDevice(device) != cudaSuccess) return CM_EDEVICE;
     cm_ctx *c = new cm_ctx();
     c->device = device;
@@ -410,18 +628,8 @@ extern "C" cm_status cm_create(cm_ctx **out, int device, const cm_options *opt) 
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     c->budget = (opt && opt->hbm_budget_bytes) ? opt->hbm_budget_bytes : (uint64_t)(free_b * 0.8);
-    if (opt && opt->max_transform_lg) {
-        if (opt->max_transform_lg < 8 || opt->max_transform_lg > 32) {
-            delete c;
-            return CM_EINVAL;
-        }
-        c->max_lg = (int)opt->max_transform_lg;
-    }
-    if (opt && opt->field > CM_FIELD_GOLDILOCKS) {
-        delete c;
-        return CM_EINVAL;
-    }
-    c->allow_f30 = !(opt && opt->field == CM_FIELD_GOLDILOCKS);
+    c->popt = po;
+    c->popt.budget = c->budget;
 
     cudaMemPoolProps pp;
     memset(&pp, 0, sizeof(pp));
@@ -525,34 +733,94 @@ extern "C" cm_status cm_device_status(cm_ctx *ctx, cm_stream stream, uint32_t *f
     return CM_OK;
 }
 
-extern "C" uint64_t cm_ntt_length(int kind, uint64_t n, uint64_t m) {
-    std::vector<Block> bl;
-    if (!make_blocks(kind, n, m, 32, true, &bl)) return 0;
-    uint64_t L = 0;
-    for (const Block &b : bl)
-        if (b.p.L > L) L = b.p.L;
-    return L;
-}
-
-extern "C" uint64_t cm_scratch_bytes(int kind, uint64_t n, uint64_t m) {
-    std::vector<Block> bl;
-    if (!make_blocks(kind, n, m, 32, true, &bl)) return 0;
-    uint64_t tmp_off = 0;
-    return blocks_scratch(bl, &tmp_off);
-}
-
-extern "C" uint32_t cm_launch_count(int kind, uint64_t n, uint64_t m) {
-    std::vector<Block> bl;
-    if (!make_blocks(kind, n, m, 32, true, &bl)) return 0;
-    uint32_t c = 0;
-    for (const Block &b : bl) c += b.p.launches + (b.accumulate ? 1 : 0);
+static uint32_t blocks_launches(const std::vector<Block> &bl) {
+    uint32_t c = (!bl.empty() && bl[0].p.kind == CM_DODIS) ? 1 : 0;  // precondition, once
+    for (const Block &b : bl) {
+        const Plan &p = b.p;
+        if (p.npass == 0) c += 1;
+        else if (b.sum == kSumFirst || b.sum == kSumInner) c += 2 * p.npass + 1;  // forward + middle
+        else c += 2 * p.npass + 1 + p.npass + 1;                                   // + inverse + pack
+        if (b.xor_into) c += 1;
+    }
     return c;
 }
 
-extern "C" uint64_t cm_block_count(int kind, uint64_t n, uint64_t m, uint32_t max_transform_lg) {
+// The plan of (kind, n, m) under opt (NULL: defaults); false if invalid.
+static bool query(int kind, uint64_t n, uint64_t m, const cm_options *opt, cm_plan_info *info) {
+    memset(info, 0, sizeof(*info));
+    PlanOptions o;
     std::vector<Block> bl;
-    const int lg = max_transform_lg ? (int)max_transform_lg : 32;
-    return make_blocks(kind, n, m, lg, true, &bl) ? bl.size() : 0;
+    if (!plan_options(opt, &o) || !make_blocks(kind, n, m, o, &bl)) return false;
+    uint64_t tmp_off = 0, pre_off = 0;
+    info->scratch_bytes = blocks_scratch(bl, &tmp_off, &pre_off);
+    info->products = bl.size();
+    info->launches = blocks_launches(bl);
+    info->field = CM_FIELD_Q30;
+    for (size_t i = 0; i < bl.size(); ++i) {
+        const Block &b = bl[i];
+        if (b.p.L > info->transform_length) info->transform_length = b.p.L;
+        if (b.p.field == kFieldGL) info->field = CM_FIELD_GOLDILOCKS;
+        if (i == 0 || b.zword != bl[i - 1].zword) ++info->windows;  // blocks come window by window
+    }
+    info->est_ms = blocks_cost_ms(bl);
+    return true;
+}
+
+extern "C" cm_status cm_plan_query(int kind, uint64_t n, uint64_t m, const cm_options *opt, cm_plan_info *out) {
+    if (!out) return CM_EINVAL;
+    return query(kind, n, m, opt, out) ? CM_OK : CM_EINVAL;
+}
+
+extern "C" cm_status cm_plan_products(int kind, uint64_t n, uint64_t m, const cm_options *opt,
+                                      cm_product_desc *out, uint64_t cap, uint64_t *count) {
+    PlanOptions o;
+    std::vector<Block> bl;
+    if (!count || (cap && !out) || !plan_options(opt, &o) || !make_blocks(kind, n, m, o, &bl)) return CM_EINVAL;
+    *count = bl.size();
+    for (uint64_t i = 0; i < bl.size() && i < cap; ++i) {
+        const Block &b = bl[i];
+        cm_product_desc &d = out[i];
+        memset(&d, 0, sizeof(d));
+        d.K = b.p.K;
+        d.m = b.p.m;
+        d.L = b.p.L;
+        d.zword = b.zword;
+        d.a_len = b.p.alen;
+        d.a_srclen = b.p.asrclen;
+        d.a_off = b.p.aoff;
+        d.b_len = b.p.blen;
+        d.b_srclen = b.p.bsrclen;
+        d.b_off = b.p.boff;
+        d.a_mode = (uint32_t)b.p.amode;
+        d.b_mode = (uint32_t)b.p.bmode;
+        d.field = b.p.field == kFieldF30 ? CM_FIELD_Q30 : CM_FIELD_GOLDILOCKS;
+        d.sum = b.sum;
+        d.xor_into = b.xor_into ? 1u : 0u;
+    }
+    return CM_OK;
+}
+
+extern "C" uint64_t cm_ntt_length(int kind, uint64_t n, uint64_t m) {
+    cm_plan_info i;
+    return query(kind, n, m, nullptr, &i) ? i.transform_length : 0;
+}
+
+extern "C" uint64_t cm_scratch_bytes(int kind, uint64_t n, uint64_t m) {
+    cm_plan_info i;
+    return query(kind, n, m, nullptr, &i) ? i.scratch_bytes : 0;
+}
+
+extern "C" uint32_t cm_launch_count(int kind, uint64_t n, uint64_t m) {
+    cm_plan_info i;
+    return query(kind, n, m, nullptr, &i) ? i.launches : 0;
+}
+
+extern "C" uint64_t cm_block_count(int kind, uint64_t n, uint64_t m, uint32_t max_transform_lg) {
+    cm_options o;
+    memset(&o, 0, sizeof(o));
+    o.max_transform_lg = max_transform_lg;
+    cm_plan_info i;
+    return query(kind, n, m, &o, &i) ? i.products : 0;
 }
 
 extern "C" cm_status cm_profile_enable(cm_ctx *ctx, int on) {
@@ -597,9 +865,9 @@ extern "C" cm_status cm_extract_host(cm_ctx *ctx, int kind, const uint64_t *xh, 
                                      const uint64_t *yh, uint64_t m, uint64_t *zh, cm_stream stream) {
     if (!ctx || !xh || !yh || !zh) return CM_EINVAL;
     std::vector<Block> bl;
-    if (!make_blocks(kind, n, m, ctx->max_lg, ctx->allow_f30, &bl)) return CM_EINVAL;
-    uint64_t tmp_off = 0;
-    const uint64_t sb = blocks_scratch(bl, &tmp_off);
+    if (!make_blocks(kind, n, m, ctx->popt, &bl)) return CM_EINVAL;
+    uint64_t tmp_off = 0, pre_off = 0;
+    const uint64_t sb = blocks_scratch(bl, &tmp_off, &pre_off);
     const uint64_t sbr = (sb + 255) & ~255ull;
     const uint64_t ybits = kind == CM_TOEPLITZ ? n + m - 1 : (kind == CM_CIRCULANT ? n + 1 : n);
     const uint64_t xw = words_of(n), yw = words_of(ybits), zw = words_of(m);
@@ -621,14 +889,11 @@ extern "C" cm_status cm_extract_host(cm_ctx *ctx, int kind, const uint64_t *xh, 
         cudaMemcpyAsync(yd, yh, 8 * yw, cudaMemcpyHostToDevice, st) != cudaSuccess)
         s = CM_EDEVICE;
     uint32_t pre_h[2] = {1, 1};
-    if (s == CM_OK) s = enqueue_blocks(ctx, bl, xd, yd, zd, b, tmp_off, st);
+    if (s == CM_OK) s = enqueue_blocks(ctx, bl, xd, yd, zd, b, tmp_off, pre_off, st);
     if (s == CM_OK && cudaMemcpyAsync(zh, zd, 8 * zw, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         s = CM_EDEVICE;
-    // the last block's precondition flags (every block checks the whole x)
-    const Plan &last = bl.back().p;
     if (s == CM_OK && kind == CM_DODIS &&
-        cudaMemcpyAsync(pre_h, b + last.scratch_bytes - 256, sizeof(pre_h), cudaMemcpyDeviceToHost, st) !=
-            cudaSuccess)
+        cudaMemcpyAsync(pre_h, b + pre_off, sizeof(pre_h), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         s = CM_EDEVICE;
     cudaFreeAsync(buf, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return CM_EDEVICE;

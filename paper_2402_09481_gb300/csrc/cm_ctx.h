@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "cm.h"
+#include "cm_internal.h"
 #include "ntt_device.cuh"
 
 struct cm_server;  // continuous-batching request loop (cm_server.cu)
@@ -17,8 +18,7 @@ struct cm_ctx {
     int device = 0;
     int nsm = 0;
     uint64_t budget = 0;         // scratch bytes one call may take
-    int max_lg = 32;             // longest transform of one product (log2)
-    bool allow_f30 = true;       // single calls may take the 32-bit field
+    cm::PlanOptions popt;        // planner options of the single calls
     cudaMemPool_t pool = nullptr;
     uint64_t *d_tables = nullptr;
     uint32_t *d_status = nullptr;

@@ -53,9 +53,10 @@ cudaError_t launch_pass_fwd(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_inv(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_fwd30(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_inv30(const PassArgs &a, int logr, cudaStream_t st);
-// A, B: L elements of the field's word size.
-cudaError_t launch_middle(int field, void *A, const void *B, uint64_t L, uint64_t linv, const RootTables &rt,
-                          const RootTables30 &rt30, int nsm, cudaStream_t st);
+// A, B: L elements of the field's word size.  The product's row-transformed
+// result goes to A (C null), to C (acc false) or is added into C (acc true).
+cudaError_t launch_middle(int field, void *A, const void *B, void *C, bool acc, uint64_t L, uint64_t linv,
+                          const RootTables &rt, const RootTables30 &rt30, int nsm, cudaStream_t st);
 cudaError_t launch_pack(const uint8_t *par, uint64_t m, uint64_t *z, const uint32_t *pre,
                         uint32_t *status, int nsm, cudaStream_t st);
 cudaError_t launch_allsame(const uint64_t *x, uint64_t n, uint32_t *flags, int nsm, cudaStream_t st);
@@ -77,6 +78,7 @@ struct Plan {
     uint64_t scratch_bytes;
     uint32_t launches;
     int field;       // kFieldGL or kFieldF30
+    bool summed;     // one of several products summed before one inverse transform
 };
 
 // Validate (kind, n, m) and fill the plan; false if invalid or if K + m - 1
@@ -88,20 +90,47 @@ bool make_plan(int kind, uint64_t n, uint64_t m, Plan *out, bool allow_f30 = fal
 constexpr uint64_t kMaxBits = 1ull << 40;
 constexpr uint64_t kMaxBlocks = 1u << 16;
 
-// One product of a blocked extraction: plan p (a middle product over an
-// input block and an output block), written to z + zword words; the first
-// block of each output window writes, later ones XOR into it.
+// How a block's product joins the others of its output window.
+enum SumMode : int {
+    kSumNone = 0,   // a product on its own: inverse transform, parity, pack
+    kSumFirst = 1,  // writes the sum group's transform-domain sum C
+    kSumInner = 2,  // adds into C
+    kSumLast = 3,   // adds into C, then the inverse passes, parity and pack of C
+};
+
+// One product of a blocked extraction: plan p (a middle product over an input
+// block and an output window) for the output words from zword on.  Input
+// blocks of one window share the transform length and the window position, so
+// their products are summed before one inverse transform (the counts add; a
+// sum group holds as many blocks as keep the total below the field's
+// characteristic).  Packing blocks of later groups, and of windows of one-CTA
+// plans (transform length <= 2^13, never summed), XOR their parities into z.
 struct Block {
     Plan p;
     uint64_t zword;
-    bool accumulate;
+    int sum;        // SumMode
+    bool xor_into;  // this block packs to a temporary and XORs it into z
 };
 
 // Split (kind, n, m) into middle products of transform length <= 2^max_lg
-// (GF(2)-linearity: the output is the XOR over input blocks; output blocks are
-// independent).  One block when K + m - 1 <= 2^max_lg.  False if invalid.
-// allow_f30: blocks whose transform fits 2^30 run over the 32-bit field.
-bool make_blocks(int kind, uint64_t n, uint64_t m, int max_lg, bool allow_f30, std::vector<Block> *out);
+// (GF(2)-linearity: a window's output is the parity of the sum over its input
+// blocks; output windows are independent), choosing among single transforms
+// and block shapes by an estimate of GPU time; shapes whose scratch exceeds
+// budget (0 = no limit) are taken only if none fits.  False if invalid.
+// allow_f30: products whose transform fits 2^30 run over the 32-bit field.
+struct PlanOptions {
+    int max_lg = 32;          // longest transform of one product (log2), 8..32
+    bool allow_f30 = true;    // products of length <= 2^30 take the 32-bit field
+    uint64_t budget = 0;      // scratch cap for choosing a shape (0 = none)
+    uint32_t max_sum = 0;     // cap on blocks per sum group (0 = the field's bound)
+    bool single = false;      // one transform whenever it fits (no cost-based split)
+};
+// PlanOptions from cm_options (NULL: defaults); false if a value is invalid.
+bool plan_options(const cm_options *opt, PlanOptions *o);
+bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::vector<Block> *out);
+
+// Estimated GPU time (ms) of a block list, from measured per-length times.
+double blocks_cost_ms(const std::vector<Block> &bl);
 
 // z[i] ^= t[i], i < words (stream-ordered).
 cudaError_t launch_xor_into(uint64_t *z, const uint64_t *t, uint64_t words, int nsm, cudaStream_t st);

@@ -480,7 +480,7 @@ extern "C" cm_status cm_submit(cm_ctx *ctx, const cm_request *rq, uint64_t *tick
     r.flags = rq->flags;
     r.seed_id = rq->seed_id;
     if (rq->flags & ~CM_REQ_SEED_CACHE) return CM_EINVAL;
-    if (!rq->x || !rq->y || !rq->z || !make_plan(rq->kind, rq->n, rq->m, &r.p, ctx->allow_f30)) return CM_EINVAL;
+    if (!rq->x || !rq->y || !rq->z || !make_plan(rq->kind, rq->n, rq->m, &r.p, ctx->popt.allow_f30)) return CM_EINVAL;
     r.foot = r.p.npass <= 1 ? worklist_scratch_bytes(r.p) : r256(r.p.scratch_bytes);
     r.foot += 256;  // work-list and flag share
     {

@@ -62,6 +62,8 @@ PROTOTYPES = {
     "cm_scratch_bytes": (_U64, [_I, _U64, _U64]),
     "cm_launch_count": (_U32, [_I, _U64, _U64]),
     "cm_block_count": (_U64, [_I, _U64, _U64, _U32]),
+    "cm_plan_query": (_I, [_I, _U64, _U64, ctypes.c_void_p, ctypes.c_void_p]),
+    "cm_plan_products": (_I, [_I, _U64, _U64, ctypes.c_void_p, ctypes.c_void_p, _U64, ctypes.POINTER(_U64)]),
     "cm_output_length": (_I, [_I, _I, _I, _U64, _U64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                               ctypes.POINTER(ctypes.c_int64)]),
     "cm_trevisan_seed_length": (_I, [_U64, _U64, ctypes.c_double, ctypes.POINTER(_U64),
@@ -77,7 +79,28 @@ TREVISAN = 3
 MODEL_SEEDED, MODEL_PRODUCT, MODEL_MARKOV = 0, 1, 2
 ADV_CLASSICAL, ADV_QUANTUM = 0, 1
 ADJUST_UP, ADJUST_DOWN, ADJUST_CLOSEST = 0, 1, 2
-FIELD_AUTO, FIELD_GOLDILOCKS = 0, 1
+FIELD_AUTO, FIELD_GOLDILOCKS, FIELD_Q30 = 0, 1, 2
+PLAN_COST, PLAN_SINGLE = 0, 1
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_transform_lg", ctypes.c_uint32),
+                ("field", ctypes.c_uint32), ("max_sum_blocks", ctypes.c_uint32),
+                ("plan_mode", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 4)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("transform_length", ctypes.c_uint64), ("products", ctypes.c_uint64),
+                ("windows", ctypes.c_uint64), ("scratch_bytes", ctypes.c_uint64),
+                ("launches", ctypes.c_uint32), ("field", ctypes.c_uint32), ("est_ms", ctypes.c_double),
+                ("reserved", ctypes.c_uint64 * 4)]
+
+
+class ProductDesc(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("K", "m", "L", "zword", "a_len", "a_srclen", "a_off",
+                                               "b_len", "b_srclen", "b_off")] + \
+               [("a_mode", ctypes.c_uint32), ("b_mode", ctypes.c_uint32), ("field", ctypes.c_uint32),
+                ("sum", ctypes.c_int32), ("xor_into", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class ParamPlan(ctypes.Structure):
@@ -195,6 +218,29 @@ def block_count(kind: int, n: int, m: int, max_transform_lg: int = 0) -> int:
     return int(lib().cm_block_count(kind, n, m, max_transform_lg))
 
 
+def plan_query(kind: int, n: int, m: int, max_transform_lg: int = 0, field: int = FIELD_AUTO,
+               hbm_budget_bytes: int = 0, max_sum_blocks: int = 0, plan_mode: int = PLAN_COST) -> dict:
+    """How one call of (kind, n, m) runs under these options (cm_plan_query)."""
+    o = Options(hbm_budget_bytes, max_transform_lg, field, max_sum_blocks, plan_mode)
+    info = PlanInfo()
+    _check(lib().cm_plan_query(kind, n, m, ctypes.byref(o), ctypes.byref(info)), "cm_plan_query")
+    return {k: getattr(info, k) for k in ("transform_length", "products", "windows", "scratch_bytes",
+                                          "launches", "field", "est_ms")}
+
+
+def plan_products(kind: int, n: int, m: int, max_transform_lg: int = 0, field: int = FIELD_AUTO,
+                  hbm_budget_bytes: int = 0, max_sum_blocks: int = 0, plan_mode: int = PLAN_COST) -> list[dict]:
+    """The middle products of one call's plan (cm_plan_products), in run order."""
+    o = Options(hbm_budget_bytes, max_transform_lg, field, max_sum_blocks, plan_mode)
+    cnt = ctypes.c_uint64()
+    _check(lib().cm_plan_products(kind, n, m, ctypes.byref(o), None, 0, ctypes.byref(cnt)), "cm_plan_products")
+    arr = (ProductDesc * max(cnt.value, 1))()
+    _check(lib().cm_plan_products(kind, n, m, ctypes.byref(o), arr, cnt.value, ctypes.byref(cnt)),
+           "cm_plan_products")
+    return [{k: getattr(arr[i], k) for k, _ in ProductDesc._fields_ if k != "reserved"}
+            for i in range(cnt.value)]
+
+
 def launch_count(kind: int, n: int, m: int) -> int:
     return int(lib().cm_launch_count(kind, n, m))
 
@@ -275,16 +321,15 @@ def _dev_words(t, nbits: int, name: str):
 class Context:
     """A libcm context on one CUDA device."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_transform_lg: int = 0, field: int = 0):
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_transform_lg: int = 0, field: int = 0,
+                 max_sum_blocks: int = 0, plan_mode: int = 0):
         import torch
         self.device = device
         torch.cuda.set_device(device)
         self._L = lib()
-        # cm_options: budget, then max_transform_lg and field as two 32-bit words
-        opts = (ctypes.c_uint64 * 5)(hbm_budget_bytes, int(max_transform_lg) | (int(field) << 32), 0, 0, 0)
+        opts = Options(hbm_budget_bytes, max_transform_lg, field, max_sum_blocks, plan_mode)
         h = ctypes.c_void_p()
-        _check(self._L.cm_create(ctypes.byref(h), device, ctypes.cast(opts, ctypes.c_void_p)),
-               "cm_create")
+        _check(self._L.cm_create(ctypes.byref(h), device, ctypes.byref(opts)), "cm_create")
         self._h = h
 
     @property

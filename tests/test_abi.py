@@ -40,14 +40,19 @@ def test_na_primes_match_oracle(lib):
 
 def test_plan_lengths(lib):
     T, C, D = native.TOEPLITZ, native.CIRCULANT, native.DODIS
-    # smallest power of two >= K + m - 1
+    # one transform: the smallest power of two >= K + m - 1
     assert native.ntt_length(T, 2 ** 16, 2 ** 15) == 2 ** 17
     assert native.ntt_length(C, 16777258, 8388629) == 2 ** 25
-    assert native.ntt_length(D, 1073741789, 429496715) == 2 ** 31
     assert native.ntt_length(T, 1, 1) == 2
     assert native.ntt_length(T, 2 ** 31, 2 ** 31 + 1) == 2 ** 32
-    # beyond one transform: blocked (here two output blocks of one transform each)
-    assert native.ntt_length(T, 2 ** 31, 2 ** 31 + 2) == 2 ** 32
+    # Dodis et al. at n = 2^30 runs as two 2^30 products over the 32-bit field
+    # (estimated faster than one Goldilocks transform of 2^31, which single
+    # mode keeps)
+    assert native.ntt_length(D, 1073741789, 429496715) == 2 ** 30
+    assert native.plan_query(D, 1073741789, 429496715, plan_mode=native.PLAN_SINGLE)["transform_length"] == 2 ** 31
+    # beyond one transform: split into products of at most 2^32
+    assert native.ntt_length(T, 2 ** 31, 2 ** 31 + 2) in (2 ** 30, 2 ** 31, 2 ** 32)
+    assert native.block_count(T, 2 ** 31, 2 ** 31 + 2) > 1
     # invalid: m = 0, n = 0, beyond 2^40, non-N_A lengths, m > n
     assert native.ntt_length(T, 2 ** 40 + 1, 5) == 0
     assert native.ntt_length(T, 5, 2 ** 40 + 1) == 0
@@ -64,28 +69,37 @@ def test_scratch_and_launches(lib):
     assert native.scratch_bytes(T, 100, 50) == 0          # one CTA, no scratch
     assert native.launch_count(T, 100, 50) == 1
     L = 2 ** 17
-    assert native.scratch_bytes(T, 2 ** 16, 2 ** 15) == 16 * L + 2 ** 15
+    # two operands of L 32-bit elements, then the parity bytes
+    assert native.scratch_bytes(T, 2 ** 16, 2 ** 15) == 8 * L + 2 ** 15
     assert native.launch_count(T, 2 ** 16, 2 ** 15) == 5   # 2 fwd, middle, inv, pack
-    assert native.launch_count(D, 1073741789, 429496715) == 9
+    # Dodis et al. at 2^30: precondition, then two summed products of two
+    # column passes each: 2 x (2 x 2 fwd + middle) + 2 inv + pack
+    assert native.launch_count(D, 1073741789, 429496715) == 1 + 2 * 5 + 3
+    # Goldilocks, one transform of 2^31: precondition + 2 x 2 fwd + middle + 2 inv + pack
+    single_gl = native.plan_query(D, 1073741789, 429496715, field=native.FIELD_GOLDILOCKS,
+                                  plan_mode=native.PLAN_SINGLE)
+    assert single_gl["launches"] == 9 and single_gl["scratch_bytes"] == 2 * 8 * 2 ** 31 + 429496832 + 256
 
 
 def test_block_counts(lib):
     T, C, D = native.TOEPLITZ, native.CIRCULANT, native.DODIS
     assert native.block_count(T, 2 ** 16, 2 ** 15) == 1
     assert native.block_count(T, 2 ** 31, 2 ** 31 + 1) == 1
-    # the QRNG example (n = 6.5e9, m = 581294933): K + m - 1 = 7.08e9 > 2^32,
-    # input blocks of at most 2^32 - m + 1 = 3.71e9: two products
-    assert native.block_count(T, 6_500_000_000, 581_294_933) == 2
-    assert native.block_count(C, 6_500_000_068, 581_294_933) == 2
-    # m above half the limit splits the output too: 2^12 limit, m = 3000 ->
-    # output blocks of 2048, input blocks of at most 2049: 2 x 5
-    assert native.block_count(T, 10_000, 3_000, 12) == 10
+    # the QRNG example (n = 6.5e9, m = 581294933): K + m - 1 = 7.08e9 > 2^32;
+    # 2^30 products over the 32-bit field, input blocks of at most
+    # 2^30 - m + 1 = 492446892 terms: 14 products in one output window
+    assert native.block_count(T, 6_500_000_000, 581_294_933) == 14
+    assert native.block_count(C, 6_500_000_068, 581_294_933) == 14
+    # 2^12 limit, m = 3000: two output windows of 1536 and 1464 rows and input
+    # blocks of 2500 terms (2500 + 1536 - 1 <= 4096): 2 x 4, cheaper than one
+    # window of 10 input blocks
+    assert native.block_count(T, 10_000, 3_000, 12) == 8
     assert native.block_count(T, 2000, 2000, 12) == 1
     assert native.block_count(T, 2000, 2098, 12) == 2
     assert native.block_count(T, 100, 50, 7) == 0
     assert native.block_count(T, 100, 50, 33) == 0
     assert native.block_count(T, 2 ** 40, 2 ** 40, 8) == 0     # over 65536 products
     assert native.block_count(C, 6, 3, 12) == 0                # 7 not in N_A
-    # launches: both products plus one XOR pass
-    one = native.launch_count(T, 2 ** 31, 2 ** 31 + 1)
-    assert native.launch_count(T, 6_500_000_000, 581_294_933) == 2 * one + 1
+    # launches: 14 forward halves (2 x 2 column passes + middle), three sum
+    # groups (6, 6, 2) each with 2 inverse passes and a pack, two XOR passes
+    assert native.launch_count(T, 6_500_000_000, 581_294_933) == 14 * 5 + 3 * 3 + 2

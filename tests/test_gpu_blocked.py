@@ -1,14 +1,20 @@
-"""Blocked extractions (products longer than one transform) against the oracle.
+"""Blocked extractions (products split over input blocks and output windows)
+against the oracle.
 
 A context whose transform limit is lowered (cm_options.max_transform_lg = 8 ..
-19) splits ordinary sizes into many input and output blocks, so every block
-path (single-CTA blocks, one-pass and two-pass blocks, the Circulant pad bit
-in the block that holds it, the double wrap of the seed index, output windows
-that end mid-word, the Dodis et al. precondition in every block) is compared
-bit for bit with the oracle's whole output.  At the default limit, the QRNG
-example's sizes (n = 6.5e9, m = 581294933, Section "Cryptomite for randomness
-extraction in (Q)RNG") run as two products of length 2^32 and are compared on
-sampled rows, as is the one-transform extreme L = 2^32.
+19) splits ordinary sizes into many input blocks and output windows, so every
+block path (single-CTA blocks XORed, one-pass and two-pass blocks summed in
+the transform domain, sum groups capped by max_sum_blocks and XORed, the
+Circulant pad bit in the block that holds it, a short last input block padded
+to the window's common length, the double wrap of the seed index, output
+windows that end mid-word, the Dodis et al. precondition) is compared bit for
+bit with the oracle's whole output, over both fields.  At the default limit
+the planner splits by cost alone (three 2^21 products instead of one 2^23;
+Dodis et al. at n = 2^30 as two 2^30 products over the 32-bit field), and the
+QRNG example's sizes (n = 6.5e9, m = 581294933, Section "Cryptomite for
+randomness extraction in (Q)RNG") run as 14 summed products of 2^30 in three
+sum groups; those and the one-transform extreme L = 2^32 are compared on
+sampled rows.
 """
 
 import numpy as np
@@ -29,6 +35,10 @@ def ctxs():
     from paper_2402_09481_gb300 import build
     build.build()
     cs = {lg: native.Context(0, max_transform_lg=lg) for lg in (8, 12, 14, 15, 16, 18, 19)}
+    cs["14s2"] = native.Context(0, max_transform_lg=14, max_sum_blocks=2)
+    cs["16s3"] = native.Context(0, max_transform_lg=16, max_sum_blocks=3)
+    cs["15gl"] = native.Context(0, max_transform_lg=15, field=native.FIELD_GOLDILOCKS)
+    cs["17gls2"] = native.Context(0, max_transform_lg=17, field=native.FIELD_GOLDILOCKS, max_sum_blocks=2)
     yield cs
     for c in cs.values():
         c.close()
@@ -67,7 +77,15 @@ CASES = [
     (C, "P5000", 0.5, 12), (C, "P5000", 0.1, 8), (C, "P200000", 0.5, 16), (C, "P200000", 0.05, 14),
     (C, "P300000", 0.3, 18),
     (D, "P50000", 0.4, 14), (D, "P3000", 0.9, 8), (D, "P300000", 0.2, 16),
+    # sum groups of at most 2 or 3 products, XORed; Goldilocks sums
+    (T, 100000, 3000, "14s2"), (T, 300000, 20000, "16s3"), (C, "P200000", 0.1, "14s2"),
+    (D, "P300000", 0.3, "16s3"), (T, 100000, 30000, "15gl"), (C, "P300000", 0.2, "17gls2"),
+    (D, "P100000", 0.5, "15gl"),
 ]
+
+
+def limit(lg):
+    return lg if isinstance(lg, int) else int(lg[:2])
 
 
 def resolve(kind, n, m):
@@ -81,7 +99,7 @@ def resolve(kind, n, m):
 @pytest.mark.parametrize("kind,n,m,lg", CASES)
 def test_blocked_matches_oracle(ctxs, cm_ctx, kind, n, m, lg):
     n, m = resolve(kind, n, m)
-    assert native.block_count(kind, n, m, lg) > 1
+    assert native.block_count(kind, n, m, limit(lg)) > 1
     xw = inputs.bernoulli_half(900 + n % 97, n)
     if kind == D:
         xw[0] = (xw[0] | np.uint64(1)) & ~np.uint64(2)
@@ -121,11 +139,38 @@ def out_bits(z, rows):
     return ((z[rows >> 6] >> (rows & 63).astype(np.uint64)) & np.uint64(1)).astype(np.uint8)
 
 
+def test_split_by_cost(cm_ctx):
+    # K + m - 1 just above 2^22 with few outputs: three summed 2^21 products
+    n, m = 2 ** 22 + 50, 100
+    info = native.plan_query(T, n, m)
+    assert (info["products"], info["transform_length"]) == (3, 2 ** 21)
+    xw, yw = inputs.bernoulli_half(66, n), inputs.bernoulli_half(67, n + m - 1)
+    assert (run(cm_ctx, T, n, m, xw, yw) == oracle.toeplitz_packed(xw, n, yw, m)).all()
+
+
+@pytest.mark.slow
+def test_dodis_workload_both_plans(cm_ctx):
+    # n = 2^30 - 35, m = 0.4 n: two 2^30 products over the 32-bit field, and
+    # one Goldilocks transform of 2^31 (single mode): same bits
+    n = 1073741789
+    m = int(0.4 * n)
+    assert native.plan_query(D, n, m)["products"] == 2
+    xw, yw = inputs.bernoulli_half(68, n), inputs.bernoulli_half(69, n)
+    z = run(cm_ctx, D, n, m, xw, yw)
+    rows = sample_rows(m, 16, 4)
+    assert (out_bits(z, rows) == oracle.dodis_rows(xw, yw, n, m, rows)).all()
+    single = native.Context(0, field=native.FIELD_GOLDILOCKS, plan_mode=native.PLAN_SINGLE)
+    try:
+        assert (run(single, D, n, m, xw, yw) == z).all()
+    finally:
+        single.close()
+
+
 @pytest.mark.slow
 def test_qrng_example_toeplitz_sampled(cm_ctx):
     # n1 = 6.5e9, m = floor(k1 + 2 log2 1e-10) = 581294933, seed n1 + m - 1 bits
     n, m = 6_500_000_000, 581_294_933
-    assert native.block_count(T, n, m) == 2
+    assert native.block_count(T, n, m) == 14
     xw, yw = inputs.bernoulli_half(60, n), inputs.bernoulli_half(61, n + m - 1)
     z = run(cm_ctx, T, n, m, xw, yw)
     rows = sample_rows(m, 24, 1)
@@ -138,7 +183,7 @@ def test_qrng_example_toeplitz_sampled(cm_ctx):
 def test_qrng_example_circulant_sampled(cm_ctx):
     # the Circulant extension of the same example: P = 6.5e9 + 69, n1' = P - 1
     n, m = 6_500_000_068, 581_294_933
-    assert oracle.is_prime(n + 1) and native.block_count(C, n, m) == 2
+    assert oracle.is_prime(n + 1) and native.block_count(C, n, m) == 14
     xw, yw = inputs.bernoulli_half(62, n), inputs.bernoulli_half(63, n + 1)
     z = run(cm_ctx, C, n, m, xw, yw)
     rows = sample_rows(m, 16, 2)
