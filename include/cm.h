@@ -117,7 +117,9 @@ const char *cm_status_str(int status);
  * blocks (GF(2)-linearity: the output is the parity of the sum over blocks;
  * the blocks of one output window share one transform length, their
  * transform-domain products are added and one inverse transform serves the
- * window) and over output windows.  A planner picks the form with the lowest
+ * window) and over output windows; up to 256 leading terms (t < T) may be
+ * left out of the transforms and XORed in by a dense GF(2) kernel, so that
+ * the rest fits a transform half as long.  A planner picks the form with the lowest
  * estimated GPU time among those whose transforms fit 2^32 (or the context's
  * max_transform_lg) and whose scratch fits the HBM budget: a split is taken
  * when it is faster, e.g. 32-bit-field blocks of 2^30 instead of one
@@ -426,7 +428,9 @@ typedef struct {
     uint32_t field;            /* CM_FIELD_GOLDILOCKS if any product runs over
                                   Goldilocks, else CM_FIELD_Q30 */
     double est_ms;             /* the planner's GPU-time estimate (GB300) */
-    uint64_t reserved[4];
+    uint64_t tail_terms;       /* terms t < tail_terms left out of the transforms
+                                  and XORed in densely (0: none) */
+    uint64_t reserved[3];
 } cm_plan_info;
 
 /* Fill *out with the plan of (kind, n, m) under opt (NULL: defaults, no
@@ -442,16 +446,19 @@ cm_status cm_plan_query(int kind, uint64_t n, uint64_t m, const cm_options *opt,
  * With c the cyclic convolution of length L of the two maps, output
  * zword * 64 + i (i < m) of the call is the parity of the sum of c[K - 1 + i]
  * over the product's sum group (sum 1 .. 3 in order, or the product alone,
- * sum 0), XORed over the window's groups. */
+ * sum 0), XORed over the window's groups.  A last entry with sum 4 (L = 0)
+ * is the dense tail: every output i < m is XORed with the parity of
+ * sum_{t < tail_terms} a(K - 1 - t) b(t + i) over its maps (the whole
+ * product's). */
 typedef struct {
     uint64_t K, m, L, zword;
     uint64_t a_len, a_srclen, a_off;
     uint64_t b_len, b_srclen, b_off;
     uint32_t a_mode, b_mode;
-    uint32_t field;    /* CM_FIELD_GOLDILOCKS or CM_FIELD_Q30 */
-    int32_t sum;       /* 0 alone, 1 first of a sum group, 2 inner, 3 last */
-    uint32_t xor_into; /* this product's parities are XORed into z */
-    uint32_t reserved;
+    uint32_t field;      /* CM_FIELD_GOLDILOCKS or CM_FIELD_Q30 */
+    int32_t sum;         /* 0 alone, 1 first of a sum group, 2 inner, 3 last, 4 tail */
+    uint32_t xor_into;   /* this product's parities are XORed into z */
+    uint32_t tail_terms; /* sum 4: the number of tail terms */
 } cm_product_desc;
 
 /* Write up to cap product descriptors of the plan of (kind, n, m) under opt

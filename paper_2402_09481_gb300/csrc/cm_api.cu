@@ -139,6 +139,9 @@ static const double kCostGL[33] = {
     0.4375, 0.8792, 1.6702, 3.3082, 7.4412, 15.095, 30.538, 62.422, 127.87, 261.78, 534.40};
 constexpr double kFwdShare = 0.77;     // forward passes of both operands + middle
 constexpr double kXorMs = 0.005;       // one k_xor_into launch
+// the dense tail: a launch plus about 1.5 ns per 1000 outputs (a fixed
+// kTailMax-term loop per output word)
+static double tail_cost(uint64_t m) { return 0.005 + 1.5e-9 * (double)m; }
 constexpr double kSingleMargin = 0.97;  // a blocked shape must beat one transform by 3%
 constexpr int kSumMinLg = kMidLgMax + 1;  // summed windows need a column pass
 
@@ -173,6 +176,7 @@ struct Shape {
     uint64_t nout;   // windows
     uint64_t nin;    // input blocks per window
     uint64_t Kb;     // terms per input block
+    uint64_t tail;   // terms left to the dense tail (t < tail)
     bool summed;
     double cost;
     uint64_t scratch;
@@ -203,6 +207,7 @@ static void evaluate(int kind, uint64_t m, bool allow_f30, uint32_t max_sum, Sha
         if (sc > s->scratch) s->scratch = sc;
         xors = xors || G < s->nin;
     }
+    if (s->tail) s->cost += tail_cost(m);
     // blocks_scratch's layout: XOR temporary, then the precondition flags
     const uint64_t tmp_off = (s->scratch + 255) & ~255ull, tmpw = xors ? words_of(s->Mb) : 0;
     if (kind == CM_DODIS) s->scratch = ((tmp_off + 8 * tmpw + 255) & ~255ull) + kFlagBytes;
@@ -260,40 +265,55 @@ bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::ve
             if (ceil_div(m, s.Mb) != nout || s.Mb > Lmax) continue;
             s.nout = nout;
             const uint64_t kmax = Lmax - s.Mb + 1;
-            s.nin = ceil_div(K, kmax);
-            if (s.nin > kMaxBlocks / s.nout) continue;  // (no overflow: both <= 2^40)
-            s.Kb = ceil_div(K, s.nin);
-            s.summed = s.nin > 1 && max_lg > kMidLgMax;
-            evaluate(kind, m, allow_f30, o.max_sum, &s);
-            const bool single = s.nin == 1 && s.nout == 1;
-            const bool fits = budget == 0 || s.scratch <= budget;
-            double c = s.cost, bc = best.cost;
-            if (!single) c /= kSingleMargin;
-            if (have && best.nin * best.nout != 1) bc /= kSingleMargin;
-            const bool better = !have || (fits && !best_fits) ||
-                                (fits == best_fits &&
-                                 (c < bc || (c == bc && s.nin * s.nout < best.nin * best.nout)));
-            if (better) {
-                best = s;
-                have = true;
-                best_fits = fits;
+            const uint64_t nin0 = ceil_div(K, kmax);
+            // the fewest input blocks, and (column-pass limits, cost mode) one
+            // block fewer when the terms left over fit the dense tail
+            for (int with_tail = 0; with_tail < 2; ++with_tail) {
+                Shape c = s;
+                if (with_tail) {
+                    if (max_lg <= kMidLgMax || o.single || lg < kSumMinLg || nin0 < 2) break;
+                    const uint64_t left = K - (nin0 - 1) * kmax;
+                    if (left > (uint64_t)kTailMax) break;
+                    c.nin = nin0 - 1;
+                    c.tail = left;
+                } else {
+                    c.nin = nin0;
+                }
+                if (c.nin > kMaxBlocks / c.nout) continue;  // (no overflow: both <= 2^40)
+                c.Kb = ceil_div(K - c.tail, c.nin);
+                c.summed = c.nin > 1 && max_lg > kMidLgMax;
+                evaluate(kind, m, allow_f30, o.max_sum, &c);
+                const bool single = c.nin == 1 && c.nout == 1 && c.tail == 0;
+                const bool fits = budget == 0 || c.scratch <= budget;
+                double cc = c.cost, bc = best.cost;
+                if (!single) cc /= kSingleMargin;
+                if (have && (best.nin * best.nout != 1 || best.tail)) bc /= kSingleMargin;
+                const bool better = !have || (fits && !best_fits) ||
+                                    (fits == best_fits &&
+                                     (cc < bc || (cc == bc && c.nin * c.nout < best.nin * best.nout)));
+                if (better) {
+                    best = c;
+                    have = true;
+                    best_fits = fits;
+                }
             }
         }
     }
     if (!have) return false;
     const Shape &s = best;
-    if (s.nin == 1 && s.nout == 1) {
+    if (s.nin == 1 && s.nout == 1 && s.tail == 0) {
         finish_plan(&b, allow_f30, 1, false);
-        out->push_back({b, 0, kSumNone, false});
+        out->push_back({b, 0, kSumNone, false, 0});
         return true;
     }
+    const uint64_t Kc = K - s.tail;  // terms t in [tail, K): transform positions u < Kc
     for (uint64_t r = 0; r < s.nout; ++r) {
         const uint64_t I0 = r * s.Mb, mr = (m - I0 < s.Mb) ? m - I0 : s.Mb;
         const int lg_r = window_lg(s, mr);
         const uint64_t G = s.summed ? group_size(field_of(allow_f30, lg_r), s.Kb, s.nin, o.max_sum) : 1;
         for (uint64_t j = 0; j < s.nin; ++j) {
-            const uint64_t D = j * s.Kb;  // < K: (nin - 1) Kb < K
-            const uint64_t kb = (K - D < s.Kb) ? K - D : s.Kb;
+            const uint64_t D = j * s.Kb;  // < Kc: (nin - 1) Kb < Kc
+            const uint64_t kb = (Kc - D < s.Kb) ? Kc - D : s.Kb;
             const uint64_t T0 = K - D - kb;
             Plan q = b;
             q.m = mr;
@@ -315,8 +335,12 @@ bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::ve
             int sum = kSumNone;
             if (g1 - g0 > 1) sum = j == g0 ? kSumFirst : (j + 1 == g1 ? kSumLast : kSumInner);
             const bool packs = sum == kSumNone || sum == kSumLast;
-            out->push_back({q, I0 / 64, sum, packs && g0 != 0});
+            out->push_back({q, I0 / 64, sum, packs && g0 != 0, 0});
         }
+    }
+    if (s.tail) {
+        finish_plan(&b, allow_f30, 1, false);  // maps only: the tail runs no transform
+        out->push_back({b, 0, kSumTail, true, (uint32_t)s.tail});
     }
     return true;
 }
@@ -324,6 +348,10 @@ bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::ve
 double blocks_cost_ms(const std::vector<Block> &bl) {
     double c = 0;
     for (const Block &b : bl) {
+        if (b.sum == kSumTail) {
+            c += tail_cost(b.p.m);
+            continue;
+        }
         const double t = plan_cost(b.p.field, b.p.lg);
         if (b.sum == kSumNone) c += t;
         else c += kFwdShare * t + (b.sum == kSumLast ? (1.0 - kFwdShare) * t : 0.0);
@@ -467,6 +495,7 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
 static uint64_t blocks_scratch(const std::vector<Block> &bl, uint64_t *tmp_off, uint64_t *pre_off) {
     uint64_t sc = 0, tmpw = 0;
     for (const Block &b : bl) {
+        if (b.sum == kSumTail) continue;  // no scratch; XORs straight into z
         const uint64_t own = b.p.scratch_bytes - flag_bytes(b.p.kind);  // flags are shared
         if (own > sc) sc = own;
         if (b.xor_into && words_of(b.p.m) > tmpw) tmpw = words_of(b.p.m);
@@ -489,6 +518,14 @@ static cm_status enqueue_blocks(cm_ctx *ctx, const std::vector<Block> &bl, const
         if (s != CM_OK) return s;
     }
     for (const Block &b : bl) {
+        if (b.sum == kSumTail) {
+            const Plan &p = b.p;
+            ProfScope ps(ctx, "k_tail", st);
+            if (launch_tail(bitmap(x, p.amode, p.alen, p.asrclen, p.aoff), bitmap(y, p.bmode, p.blen, p.bsrclen, p.boff),
+                            p.K, b.tail, p.m, z, pre, ctx->nsm, st) != cudaSuccess)
+                return CM_EDEVICE;
+            continue;
+        }
         uint64_t *dst = b.xor_into ? reinterpret_cast<uint64_t *>(scratch + tmp_off) : z + b.zword;
         cm_status s = enqueue_product(ctx, b.p, x, y, dst, b.p.scratch_bytes ? scratch : nullptr, pre, b.sum, st);
         if (s != CM_OK) return s;
@@ -737,10 +774,11 @@ static uint32_t blocks_launches(const std::vector<Block> &bl) {
     uint32_t c = (!bl.empty() && bl[0].p.kind == CM_DODIS) ? 1 : 0;  // precondition, once
     for (const Block &b : bl) {
         const Plan &p = b.p;
-        if (p.npass == 0) c += 1;
+        if (b.sum == kSumTail) c += 1;
+        else if (p.npass == 0) c += 1;
         else if (b.sum == kSumFirst || b.sum == kSumInner) c += 2 * p.npass + 1;  // forward + middle
         else c += 2 * p.npass + 1 + p.npass + 1;                                   // + inverse + pack
-        if (b.xor_into) c += 1;
+        if (b.xor_into && b.sum != kSumTail) c += 1;
     }
     return c;
 }
@@ -753,11 +791,15 @@ static bool query(int kind, uint64_t n, uint64_t m, const cm_options *opt, cm_pl
     if (!plan_options(opt, &o) || !make_blocks(kind, n, m, o, &bl)) return false;
     uint64_t tmp_off = 0, pre_off = 0;
     info->scratch_bytes = blocks_scratch(bl, &tmp_off, &pre_off);
-    info->products = bl.size();
+    info->products = bl.size() - (bl.back().sum == kSumTail ? 1 : 0);
     info->launches = blocks_launches(bl);
     info->field = CM_FIELD_Q30;
     for (size_t i = 0; i < bl.size(); ++i) {
         const Block &b = bl[i];
+        if (b.sum == kSumTail) {
+            info->tail_terms = b.tail;
+            continue;
+        }
         if (b.p.L > info->transform_length) info->transform_length = b.p.L;
         if (b.p.field == kFieldGL) info->field = CM_FIELD_GOLDILOCKS;
         if (i == 0 || b.zword != bl[i - 1].zword) ++info->windows;  // blocks come window by window
@@ -796,6 +838,8 @@ extern "C" cm_status cm_plan_products(int kind, uint64_t n, uint64_t m, const cm
         d.field = b.p.field == kFieldF30 ? CM_FIELD_Q30 : CM_FIELD_GOLDILOCKS;
         d.sum = b.sum;
         d.xor_into = b.xor_into ? 1u : 0u;
+        d.tail_terms = b.tail;
+        if (b.sum == kSumTail) d.L = 0;
     }
     return CM_OK;
 }

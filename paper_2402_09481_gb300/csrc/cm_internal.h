@@ -60,6 +60,11 @@ cudaError_t launch_middle(int field, void *A, const void *B, void *C, bool acc, 
 cudaError_t launch_pack(const uint8_t *par, uint64_t m, uint64_t *z, const uint32_t *pre,
                         uint32_t *status, int nsm, cudaStream_t st);
 cudaError_t launch_allsame(const uint64_t *x, uint64_t n, uint32_t *flags, int nsm, cudaStream_t st);
+// z_i ^= sum_{t<T} amap(K-1-t) bmap(t+i) (mod 2), i < m, 1 <= T <= min(kTailMax, K);
+// nothing when the Dodis et al. flags at pre (if any) report a constant x.
+constexpr int kTailMax = 256;
+cudaError_t launch_tail(const BitMap &amap, const BitMap &bmap, uint64_t K, uint32_t T, uint64_t m, uint64_t *z,
+                        const uint32_t *pre, int nsm, cudaStream_t st);
 
 // The plan of one extraction: the middle-product form of the extractor and the
 // pass split of its transform.
@@ -96,6 +101,7 @@ enum SumMode : int {
     kSumFirst = 1,  // writes the sum group's transform-domain sum C
     kSumInner = 2,  // adds into C
     kSumLast = 3,   // adds into C, then the inverse passes, parity and pack of C
+    kSumTail = 4,   // not a transform: the dense tail (p: the whole product's maps)
 };
 
 // One product of a blocked extraction: plan p (a middle product over an input
@@ -105,11 +111,15 @@ enum SumMode : int {
 // sum group holds as many blocks as keep the total below the field's
 // characteristic).  Packing blocks of later groups, and of windows of one-CTA
 // plans (transform length <= 2^13, never summed), XOR their parities into z.
+// A plan may also leave its first `tail` terms (t < tail <= kTailMax) out of
+// the transforms: a last pseudo-block (kSumTail) XORs their dense GF(2)
+// product into every output, so that the rest fits a shorter transform.
 struct Block {
     Plan p;
     uint64_t zword;
     int sum;        // SumMode
     bool xor_into;  // this block packs to a temporary and XORs it into z
+    uint32_t tail;  // kSumTail: the number of tail terms
 };
 
 // Split (kind, n, m) into middle products of transform length <= 2^max_lg

@@ -152,6 +152,66 @@ cudaError_t launch_xor_into(uint64_t *z, const uint64_t *t, uint64_t words, int 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Dense tail of a middle product: z_i ^= sum_{t<T} a_t b_{t+i} (mod 2), i < m,
+// with a_t = A_{K-1-t} and b_v = B_v read through the product's operand maps,
+// T <= kTailMax.  The CTA gathers the T tail bits of a once (warp ballots into
+// shared memory); then one thread builds one 64-bit output word: the 64 + T - 1
+// seed bits it needs sit in registers, and every tail term with a_t = 1 XORs
+// in the 64-bit run of them that starts at offset t.
+// ---------------------------------------------------------------------------
+constexpr int kTailThreads = 256;
+static_assert(kTailMax == kTailThreads && kTailMax % 64 == 0, "one tail bit per thread");
+
+__global__ void __launch_bounds__(kTailThreads)
+k_tail(BitMap amap, BitMap bmap, uint64_t K, uint32_t T, uint64_t m, uint64_t *__restrict__ z,
+       const uint32_t *__restrict__ pre) {
+    if (pre && (pre[0] == 0u || pre[1] == 0u)) return;  // the pack kernel left z zero
+    constexpr int NW = kTailMax / 64;
+    __shared__ uint32_t sal[kTailMax / 32];
+    {
+        const int t = threadIdx.x;  // one tail position per thread
+        const uint32_t bit = (uint32_t)t < T ? (uint32_t)amap.get(K - 1 - (uint64_t)t) : 0u;
+        const uint32_t w = __ballot_sync(0xffffffffu, bit);
+        if ((t & 31) == 0) sal[t >> 5] = w;
+    }
+    __syncthreads();
+    uint64_t al[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) al[q] = (uint64_t)sal[2 * q] | ((uint64_t)sal[2 * q + 1] << 32);
+    const uint64_t nwords = (m + 63) >> 6;
+    for (uint64_t w = (uint64_t)blockIdx.x * kTailThreads + threadIdx.x; w < nwords;
+         w += (uint64_t)gridDim.x * kTailThreads) {
+        uint64_t W[NW + 1];  // seed bits 64 w .. 64 w + 64 (NW + 1) - 1
+#pragma unroll
+        for (int q = 0; q <= NW; ++q) {
+            const uint64_t v = (w << 6) + 64 * q;
+            W[q] = (uint64_t)bmap.get_run<32>(v) | ((uint64_t)bmap.get_run<32>(v + 32) << 32);
+        }
+        uint64_t acc = 0;
+#pragma unroll
+        for (int t = 0; t < kTailMax; ++t) {
+            const int q = t >> 6, s = t & 63;
+            const uint64_t run = s ? (W[q] >> s) | (W[q + 1] << (64 - s)) : W[q];
+            if ((al[q] >> s) & 1ull) acc ^= run;
+        }
+        if (w == nwords - 1 && (m & 63)) acc &= (1ull << (m & 63)) - 1;
+        z[w] ^= acc;
+    }
+}
+
+cudaError_t launch_tail(const BitMap &amap, const BitMap &bmap, uint64_t K, uint32_t T, uint64_t m, uint64_t *z,
+                        const uint32_t *pre, int nsm, cudaStream_t st) {
+    if (T == 0 || T > (uint32_t)kTailMax || T > K) return cudaErrorInvalidValue;
+    const uint64_t nwords = (m + 63) >> 6;
+    uint64_t blocks = (nwords + kTailThreads - 1) / kTailThreads;
+    const uint64_t cap = (uint64_t)nsm * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) blocks = 1;
+    k_tail<<<(unsigned)blocks, kTailThreads, 0, st>>>(amap, bmap, K, T, m, z, pre);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_allsame(const uint64_t *x, uint64_t n, uint32_t *flags, int nsm, cudaStream_t st) {
     const uint64_t nw = (n + 63) >> 6;
     uint64_t blocks = (nw + 255) / 256;

@@ -93,14 +93,14 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("transform_length", ctypes.c_uint64), ("products", ctypes.c_uint64),
                 ("windows", ctypes.c_uint64), ("scratch_bytes", ctypes.c_uint64),
                 ("launches", ctypes.c_uint32), ("field", ctypes.c_uint32), ("est_ms", ctypes.c_double),
-                ("reserved", ctypes.c_uint64 * 4)]
+                ("tail_terms", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 3)]
 
 
 class ProductDesc(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in ("K", "m", "L", "zword", "a_len", "a_srclen", "a_off",
                                                "b_len", "b_srclen", "b_off")] + \
                [("a_mode", ctypes.c_uint32), ("b_mode", ctypes.c_uint32), ("field", ctypes.c_uint32),
-                ("sum", ctypes.c_int32), ("xor_into", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("sum", ctypes.c_int32), ("xor_into", ctypes.c_uint32), ("tail_terms", ctypes.c_uint32)]
 
 
 class ParamPlan(ctypes.Structure):
@@ -225,7 +225,7 @@ def plan_query(kind: int, n: int, m: int, max_transform_lg: int = 0, field: int 
     info = PlanInfo()
     _check(lib().cm_plan_query(kind, n, m, ctypes.byref(o), ctypes.byref(info)), "cm_plan_query")
     return {k: getattr(info, k) for k in ("transform_length", "products", "windows", "scratch_bytes",
-                                          "launches", "field", "est_ms")}
+                                          "launches", "field", "est_ms", "tail_terms")}
 
 
 def plan_products(kind: int, n: int, m: int, max_transform_lg: int = 0, field: int = FIELD_AUTO,
@@ -237,8 +237,7 @@ def plan_products(kind: int, n: int, m: int, max_transform_lg: int = 0, field: i
     arr = (ProductDesc * max(cnt.value, 1))()
     _check(lib().cm_plan_products(kind, n, m, ctypes.byref(o), arr, cnt.value, ctypes.byref(cnt)),
            "cm_plan_products")
-    return [{k: getattr(arr[i], k) for k, _ in ProductDesc._fields_ if k != "reserved"}
-            for i in range(cnt.value)]
+    return [{k: getattr(arr[i], k) for k, _ in ProductDesc._fields_} for i in range(cnt.value)]
 
 
 def launch_count(kind: int, n: int, m: int) -> int:

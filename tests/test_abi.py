@@ -42,7 +42,9 @@ def test_plan_lengths(lib):
     T, C, D = native.TOEPLITZ, native.CIRCULANT, native.DODIS
     # one transform: the smallest power of two >= K + m - 1
     assert native.ntt_length(T, 2 ** 16, 2 ** 15) == 2 ** 17
-    assert native.ntt_length(C, 16777258, 8388629) == 2 ** 25
+    assert native.plan_query(C, 16777258, 8388629, plan_mode=native.PLAN_SINGLE)["transform_length"] == 2 ** 25
+    # the planner's form: two summed 2^24 products and an 83-term dense tail
+    assert native.ntt_length(C, 16777258, 8388629) == 2 ** 24
     assert native.ntt_length(T, 1, 1) == 2
     assert native.ntt_length(T, 2 ** 31, 2 ** 31 + 1) == 2 ** 32
     # Dodis et al. at n = 2^30 runs as two 2^30 products over the 32-bit field
@@ -50,9 +52,9 @@ def test_plan_lengths(lib):
     # mode keeps)
     assert native.ntt_length(D, 1073741789, 429496715) == 2 ** 30
     assert native.plan_query(D, 1073741789, 429496715, plan_mode=native.PLAN_SINGLE)["transform_length"] == 2 ** 31
-    # beyond one transform: split into products of at most 2^32
-    assert native.ntt_length(T, 2 ** 31, 2 ** 31 + 2) in (2 ** 30, 2 ** 31, 2 ** 32)
-    assert native.block_count(T, 2 ** 31, 2 ** 31 + 2) > 1
+    # one term beyond one transform: a 2^32 product and a one-term dense tail
+    q = native.plan_query(T, 2 ** 31, 2 ** 31 + 2)
+    assert (q["products"], q["transform_length"], q["tail_terms"]) == (1, 2 ** 32, 1)
     # invalid: m = 0, n = 0, beyond 2^40, non-N_A lengths, m > n
     assert native.ntt_length(T, 2 ** 40 + 1, 5) == 0
     assert native.ntt_length(T, 5, 2 ** 40 + 1) == 0

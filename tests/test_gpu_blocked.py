@@ -9,7 +9,10 @@ Circulant pad bit in the block that holds it, a short last input block padded
 to the window's common length, the double wrap of the seed index, output
 windows that end mid-word, the Dodis et al. precondition) is compared bit for
 bit with the oracle's whole output, over both fields.  At the default limit
-the planner splits by cost alone (three 2^21 products instead of one 2^23;
+the planner splits by cost alone (one 2^22 product and a dense tail of the
+149 terms that do not fit, instead of one 2^23 transform; the Circulant
+workload as two summed 2^24 products and an 83-term tail, checked against the
+single 2^25 transform bit for bit;
 Dodis et al. at n = 2^30 as two 2^30 products over the 32-bit field), and the
 QRNG example's sizes (n = 6.5e9, m = 581294933, Section "Cryptomite for
 randomness extraction in (Q)RNG") run as 14 summed products of 2^30 in three
@@ -39,6 +42,7 @@ def ctxs():
     cs["16s3"] = native.Context(0, max_transform_lg=16, max_sum_blocks=3)
     cs["15gl"] = native.Context(0, max_transform_lg=15, field=native.FIELD_GOLDILOCKS)
     cs["17gls2"] = native.Context(0, max_transform_lg=17, field=native.FIELD_GOLDILOCKS, max_sum_blocks=2)
+    cs["16gl"] = native.Context(0, max_transform_lg=16, field=native.FIELD_GOLDILOCKS)
     yield cs
     for c in cs.values():
         c.close()
@@ -139,13 +143,60 @@ def out_bits(z, rows):
     return ((z[rows >> 6] >> (rows & 63).astype(np.uint64)) & np.uint64(1)).astype(np.uint8)
 
 
+TAIL_CASES = [
+    # (kind, n, m, context): products of 2^14 .. 2^16 plus a dense tail of
+    # 136, 71, 202, 200 terms (one product; two summed; one; two windows)
+    (C, 16_420, 100, 14), (C, 16_420, 8_210, 14), (D, 32_771, 200, 15), (T, 35_721, 60_000, 16),
+    (T, 35_721, 60_000, "16gl"),
+]
+
+
+@pytest.mark.parametrize("kind,n,m,lg", TAIL_CASES)
+def test_dense_tail_matches_oracle(ctxs, kind, n, m, lg):
+    info = native.plan_query(kind, n, m, max_transform_lg=limit(lg),
+                             field=native.FIELD_GOLDILOCKS if str(lg).endswith("gl") else native.FIELD_AUTO)
+    assert info["tail_terms"] > 0
+    xw = inputs.bernoulli_half(70 + n % 13, n)
+    if kind == D:
+        xw[0] = (xw[0] | np.uint64(1)) & ~np.uint64(2)
+    yw = inputs.bernoulli_half(71 + n % 11, ybits(kind, n, m))
+    assert (run(ctxs[lg], kind, n, m, xw, yw) == want(kind, n, m, xw, yw)).all()
+
+
+def test_dense_tail_dodis_precondition(ctxs):
+    # a constant source zeroes the output of a plan with a tail as well
+    P = 32_771
+    for fill in (0, 1):
+        xw = ex.pack_bits(np.full(P, fill, dtype=np.uint8))
+        got = run(ctxs[15], D, P, 200, xw, inputs.bernoulli_half(74, P))
+        assert not got.any()
+        assert ctxs[15].device_status()[0] == native.CM_EPRECOND
+
+
 def test_split_by_cost(cm_ctx):
-    # K + m - 1 just above 2^22 with few outputs: three summed 2^21 products
+    # K + m - 1 = 2^22 + 149: one 2^22 product and a 149-term dense tail
     n, m = 2 ** 22 + 50, 100
     info = native.plan_query(T, n, m)
-    assert (info["products"], info["transform_length"]) == (3, 2 ** 21)
+    assert (info["products"], info["transform_length"], info["tail_terms"]) == (1, 2 ** 22, 149)
     xw, yw = inputs.bernoulli_half(66, n), inputs.bernoulli_half(67, n + m - 1)
     assert (run(cm_ctx, T, n, m, xw, yw) == oracle.toeplitz_packed(xw, n, yw, m)).all()
+
+
+def test_circulant_workload_plans_agree(cm_ctx):
+    # n + 1 = 16777259, m = n / 2: two summed 2^24 products and an 83-term
+    # tail; every output bit equals the single 2^25 transform's
+    n = 16777258
+    m = n // 2
+    assert native.plan_query(C, n, m)["tail_terms"] == 83
+    xw, yw = inputs.bernoulli_half(72, n), inputs.bernoulli_half(73, n + 1)
+    z = run(cm_ctx, C, n, m, xw, yw)
+    single = native.Context(0, plan_mode=native.PLAN_SINGLE)
+    try:
+        assert (run(single, C, n, m, xw, yw) == z).all()
+    finally:
+        single.close()
+    rows = sample_rows(m, 64, 5)
+    assert (out_bits(z, rows) == oracle.circulant_rows(xw, n, yw, m, rows)).all()
 
 
 @pytest.mark.slow

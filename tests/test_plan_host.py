@@ -70,6 +70,16 @@ def emulate(kind, n, m, xw, yw, prods):
     z = np.zeros(m, dtype=np.uint8)
     acc = None
     for p in prods:
+        if p["sum"] == 4:  # dense tail over the whole product's maps
+            T, K = p["tail_terms"], p["K"]
+            a = map_bits(xb, p["a_mode"], p["a_len"], p["a_srclen"], p["a_off"], K)
+            b = map_bits(yb, p["b_mode"], p["b_len"], p["b_srclen"], p["b_off"], m + T)
+            tail = np.zeros(m, dtype=np.int64)
+            for t in range(T):
+                if a[K - 1 - t]:
+                    tail += b[t:t + m]
+            z ^= (tail & 1).astype(np.uint8)
+            continue
         L, K, mr = p["L"], p["K"], p["m"]
         a = map_bits(xb, p["a_mode"], p["a_len"], p["a_srclen"], p["a_off"], L)
         b = map_bits(yb, p["b_mode"], p["b_len"], p["b_srclen"], p["b_off"], L)
@@ -97,6 +107,12 @@ def want(kind, n, m, xw, yw):
 
 def check_structure(kind, n, m, prods):
     K = k_terms(kind, n)
+    if prods and prods[-1]["sum"] == 4:
+        tail = prods[-1]
+        assert 0 < tail["tail_terms"] <= 256 and tail["L"] == 0 and tail["K"] == K and tail["m"] == m
+        K -= tail["tail_terms"]
+        prods = prods[:-1]
+    assert all(p["sum"] != 4 for p in prods)
     i = 0
     next_word = 0
     while i < len(prods):
@@ -146,7 +162,16 @@ CASES = [
     (T, 20_000, 3_000, dict(max_transform_lg=12)),
     (T, 1_000, 300, dict(max_transform_lg=8)),
     (T, 50_000, 9_000, dict(max_transform_lg=14, field=native.FIELD_GOLDILOCKS)),
-    (T, 2 ** 22 + 50, 100, {}),  # split by cost alone: three 2^21 products beat one 2^23
+    (T, 2 ** 22 + 50, 100, {}),  # one 2^22 product and a 149-term dense tail, not one 2^23
+    (T, 2 ** 22 + 50, 100, dict(max_transform_lg=21)),  # three 2^21 products
+    # dense tails: one product and 136 / 202 tail terms, two summed products
+    # and 71, two output windows sharing a 200-term tail, over both fields
+    (C, 16_420, 100, dict(max_transform_lg=14)),
+    (C, 16_420, 8_210, dict(max_transform_lg=14)),
+    (D, 32_771, 200, dict(max_transform_lg=15)),
+    (T, 35_721, 60_000, dict(max_transform_lg=16)),
+    (T, 35_721, 60_000, dict(max_transform_lg=16, field=native.FIELD_GOLDILOCKS)),
+    (D, 32_771, 13_108, dict(max_transform_lg=15, field=native.FIELD_GOLDILOCKS)),
     (C, "P60000", 0.5, dict(max_transform_lg=14)),
     (C, "P60000", 0.05, dict(max_transform_lg=14, max_sum_blocks=2)),
     (C, "P5000", 0.5, dict(max_transform_lg=12)),
@@ -185,15 +210,22 @@ def test_structure_at_large_sizes(kind, n, m):
     prods = native.plan_products(kind, n, m)
     check_structure(kind, n, m, prods)
     info = native.plan_query(kind, n, m)
+    tail = [p for p in prods if p["sum"] == 4]
+    prods = [p for p in prods if p["sum"] != 4]
     assert info["products"] == len(prods)
+    assert info["tail_terms"] == (tail[0]["tail_terms"] if tail else 0)
     assert info["transform_length"] == max(p["L"] for p in prods)
     assert info["windows"] == len({p["zword"] for p in prods})
 
 
 def test_planner_choices():
     # one transform where it is cheapest: the Circulant and Toeplitz workloads
-    assert native.plan_query(C, 16_777_258, 8_388_629)["products"] == 1
     assert native.plan_query(T, 2 ** 16, 2 ** 15)["products"] == 1
+    # the Circulant workload (n + 1 = 2^24 + 43, m = n / 2): two summed 2^24
+    # products and an 83-term dense tail instead of one 2^25 transform
+    c = native.plan_query(C, 16_777_258, 8_388_629)
+    assert (c["products"], c["transform_length"], c["tail_terms"]) == (2, 2 ** 24, 83)
+    assert native.plan_query(C, 16_777_258, 8_388_629, plan_mode=native.PLAN_SINGLE)["transform_length"] == 2 ** 25
     # Dodis et al. at n = 2^30: two summed 2^30 products over the 32-bit field
     # instead of one Goldilocks transform of 2^31; forced Goldilocks keeps 2^31
     d = native.plan_query(D, 1_073_741_789, 429_496_715)
