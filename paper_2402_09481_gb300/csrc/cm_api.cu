@@ -93,8 +93,8 @@ static void finish_plan(Plan *p, bool allow_f30, int min_lg, bool summed) {
         p->pass_lg[1] = rest / 2;
     }
     p->scratch_bytes = plan_scratch(p->lg, p->m, p->field, summed) + flag_bytes(p->kind);
-    // forward passes of both operands, middle, inverse passes, pack
-    p->launches = p->npass == 0 ? 1 : 2 * p->npass + 1 + p->npass + 1;
+    // forward passes (both operands per launch), middle, inverse passes, pack
+    p->launches = p->npass == 0 ? 1 : p->npass + 1 + p->npass + 1;
     if (p->kind == CM_DODIS) p->launches += 1;  // precondition check
 }
 
@@ -417,13 +417,15 @@ static cm_status enqueue_product(cm_ctx *ctx, const Plan &p, const uint64_t *x, 
         lgS[j] = cur - p.pass_lg[j];
         cur = lgS[j];
     }
-    // forward passes
-    for (int op = 0; op < 2; ++op) {
-        for (int j = 0; j < p.npass; ++j) {
+    // forward passes, both operands in each launch
+    for (int j = 0; j < p.npass; ++j) {
+        {
             PassArgs a;
             memset(&a, 0, sizeof(a));
-            a.data = op == 0 ? A : B;
-            a.map = op == 0 ? am : bm;
+            a.data = A;
+            a.map = am;
+            a.data2 = B;
+            a.map2 = bm;
             a.lgN = lgN[j];
             a.lgS = lgS[j];
             a.field = p.field;
@@ -776,8 +778,8 @@ static uint32_t blocks_launches(const std::vector<Block> &bl) {
         const Plan &p = b.p;
         if (b.sum == kSumTail) c += 1;
         else if (p.npass == 0) c += 1;
-        else if (b.sum == kSumFirst || b.sum == kSumInner) c += 2 * p.npass + 1;  // forward + middle
-        else c += 2 * p.npass + 1 + p.npass + 1;                                   // + inverse + pack
+        else if (b.sum == kSumFirst || b.sum == kSumInner) c += p.npass + 1;  // forward + middle
+        else c += p.npass + 1 + p.npass + 1;                                   // + inverse + pack
         if (b.xor_into && b.sum != kSumTail) c += 1;
     }
     return c;

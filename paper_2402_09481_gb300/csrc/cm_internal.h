@@ -33,10 +33,14 @@ struct Launch {
     cudaStream_t stream;
 };
 
-// Arguments of one column pass.  data: L elements of the field's word size.
+// Arguments of one column pass.  data: L elements of the field's word size;
+// a forward pass may also take the second operand (data2, map2) in the same
+// launch (data2 null: one operand).
 struct PassArgs {
     void *data;
     BitMap map;
+    void *data2;
+    BitMap map2;
     int lgN, lgS;
     uint8_t *par;
     uint64_t lo, m;

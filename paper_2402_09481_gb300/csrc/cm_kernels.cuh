@@ -103,10 +103,13 @@ __device__ __forceinline__ void row_twiddle(typename F::T (&v)[VW], uint64_t k, 
 // ---------------------------------------------------------------------------
 // One column pass over tiles of R = 2^LOGR rows x C = 2^F::ncol_lg(LOGR) columns.
 // ---------------------------------------------------------------------------
+// Tiles 0 .. ntiles - 1 of the grid work on (data, map); a forward pass may
+// take both operands in one launch, tiles ntiles .. 2 ntiles - 1 on (data2, map2).
 template <class F, int LOGR, bool INV, bool BITS_IN, bool PARITY_OUT>
 __global__ void __launch_bounds__(kThreads, sizeof(typename F::T) == 4 ? 2 : 1)
-k_pass(typename F::T *__restrict__ data, BitMap map, int lgN, int lgS, uint8_t *__restrict__ par,
-       uint64_t lo, uint64_t m, RootTablesT<typename F::T> rt) {
+k_pass(typename F::T *__restrict__ data1, BitMap map1, typename F::T *__restrict__ data2, BitMap map2,
+       uint64_t ntiles, int lgN, int lgS, uint8_t *__restrict__ par, uint64_t lo, uint64_t m,
+       RootTablesT<typename F::T> rt) {
     using T = typename F::T;
     constexpr int R = 1 << LOGR;
     constexpr int NCOL_LG = F::ncol_lg(LOGR);
@@ -117,7 +120,10 @@ k_pass(typename F::T *__restrict__ data, BitMap map, int lgN, int lgS, uint8_t *
     load_roots<LOGR>(tw, rt.small);
     const uint64_t S = 1ull << lgS;
     const uint64_t tiles_per_blk = S >> NCOL_LG;
-    const uint64_t tile = blockIdx.x;
+    const bool second = blockIdx.x >= ntiles;
+    const uint64_t tile = second ? blockIdx.x - ntiles : blockIdx.x;
+    T *__restrict__ data = second ? data2 : data1;
+    const BitMap map = second ? map2 : map1;
     const uint64_t blk = tile / tiles_per_blk;
     const uint64_t col0 = (tile - blk * tiles_per_blk) << NCOL_LG;
     const uint64_t base = (blk << lgN) + col0;

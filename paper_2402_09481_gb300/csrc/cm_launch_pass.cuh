@@ -25,8 +25,9 @@ static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const uint64_t tiles = a.L >> TILE_LG;
-    kern<<<(unsigned)tiles, kThreads, sm, st>>>(static_cast<T *>(a.data), a.map, a.lgN, a.lgS, a.par, a.lo, a.m,
-                                                 pass_tables<F>(a));
+    const uint64_t grid = a.data2 ? 2 * tiles : tiles;
+    kern<<<(unsigned)grid, kThreads, sm, st>>>(static_cast<T *>(a.data), a.map, static_cast<T *>(a.data2), a.map2,
+                                                tiles, a.lgN, a.lgS, a.par, a.lo, a.m, pass_tables<F>(a));
     return cudaGetLastError();
 }
 

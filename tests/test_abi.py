@@ -73,14 +73,15 @@ def test_scratch_and_launches(lib):
     L = 2 ** 17
     # two operands of L 32-bit elements, then the parity bytes
     assert native.scratch_bytes(T, 2 ** 16, 2 ** 15) == 8 * L + 2 ** 15
-    assert native.launch_count(T, 2 ** 16, 2 ** 15) == 5   # 2 fwd, middle, inv, pack
+    # one forward pass (both operands), middle, inverse pass, pack
+    assert native.launch_count(T, 2 ** 16, 2 ** 15) == 4
     # Dodis et al. at 2^30: precondition, then two summed products of two
-    # column passes each: 2 x (2 x 2 fwd + middle) + 2 inv + pack
-    assert native.launch_count(D, 1073741789, 429496715) == 1 + 2 * 5 + 3
-    # Goldilocks, one transform of 2^31: precondition + 2 x 2 fwd + middle + 2 inv + pack
+    # column passes each: 2 x (2 fwd + middle) + 2 inv + pack
+    assert native.launch_count(D, 1073741789, 429496715) == 1 + 2 * 3 + 3
+    # Goldilocks, one transform of 2^31: precondition + 2 fwd + middle + 2 inv + pack
     single_gl = native.plan_query(D, 1073741789, 429496715, field=native.FIELD_GOLDILOCKS,
                                   plan_mode=native.PLAN_SINGLE)
-    assert single_gl["launches"] == 9 and single_gl["scratch_bytes"] == 2 * 8 * 2 ** 31 + 429496832 + 256
+    assert single_gl["launches"] == 7 and single_gl["scratch_bytes"] == 2 * 8 * 2 ** 31 + 429496832 + 256
 
 
 def test_block_counts(lib):
@@ -102,6 +103,6 @@ def test_block_counts(lib):
     assert native.block_count(T, 100, 50, 33) == 0
     assert native.block_count(T, 2 ** 40, 2 ** 40, 8) == 0     # over 65536 products
     assert native.block_count(C, 6, 3, 12) == 0                # 7 not in N_A
-    # launches: 14 forward halves (2 x 2 column passes + middle), three sum
+    # launches: 14 forward halves (2 column passes + middle), three sum
     # groups (6, 6, 2) each with 2 inverse passes and a pack, two XOR passes
-    assert native.launch_count(T, 6_500_000_000, 581_294_933) == 14 * 5 + 3 * 3 + 2
+    assert native.launch_count(T, 6_500_000_000, 581_294_933) == 14 * 3 + 3 * 3 + 2
