@@ -138,6 +138,8 @@ static const double kCostGL[33] = {
     0.03,  0.03,  0.03,  0.130, 0.133, 0.1356, 0.1419, 0.1459, 0.1604, 0.1678, 0.2221,
     0.4375, 0.8792, 1.6702, 3.3082, 7.4412, 15.095, 30.538, 62.422, 127.87, 261.78, 534.40};
 constexpr double kFwdShare = 0.77;     // forward passes of both operands + middle
+constexpr double kInvRowShare = 0.15;  // the middle's inverse row transform (a third of it)
+constexpr double kSumShare = kFwdShare - kInvRowShare;  // a product summed into C
 constexpr double kXorMs = 0.005;       // one k_xor_into launch
 // the dense tail: a launch plus about 1.5 ns per 1000 outputs (a fixed
 // kTailMax-term loop per output word)
@@ -161,12 +163,14 @@ static uint64_t group_size(int field, uint64_t Kb, uint64_t nin, uint32_t cap) {
 }
 
 // One window of nin input blocks summed in groups of G (G = 1: every block
-// inverse-transformed on its own and XORed).
+// inverse-transformed on its own and XORed): a group's last block costs a
+// whole extraction, the others their forward passes and the middle without
+// its inverse row transform.
 static double window_cost(int field, int lg, uint64_t nin, uint64_t G) {
     const double t = plan_cost(field, lg);
     const uint64_t ng = ceil_div(nin, G);
     if (G == 1) return (double)nin * t + (double)(nin - 1) * kXorMs;
-    return ((double)nin * kFwdShare + (double)ng * (1.0 - kFwdShare)) * t + (double)(ng - 1) * kXorMs;
+    return ((double)(nin - ng) * kSumShare + (double)ng) * t + (double)(ng - 1) * kXorMs;
 }
 
 
@@ -353,8 +357,7 @@ double blocks_cost_ms(const std::vector<Block> &bl) {
             continue;
         }
         const double t = plan_cost(b.p.field, b.p.lg);
-        if (b.sum == kSumNone) c += t;
-        else c += kFwdShare * t + (b.sum == kSumLast ? (1.0 - kFwdShare) * t : 0.0);
+        c += (b.sum == kSumFirst || b.sum == kSumInner) ? kSumShare * t : t;
         if (b.xor_into) c += kXorMs;
     }
     return c;
@@ -441,12 +444,13 @@ static cm_status enqueue_product(cm_ctx *ctx, const Plan &p, const uint64_t *x, 
     }
     {
         ProfScope ps(ctx, f30 ? "k_middle_f30" : "k_middle", st);
-        e = launch_middle(p.field, A, B, C, sum == kSumInner || sum == kSumLast, p.L, linv, ctx->rt, ctx->rt30,
-                          ctx->nsm, st);
+        const int mode = sum == kSumFirst ? kMidFirst : sum == kSumInner ? kMidInner
+                         : sum == kSumLast ? kMidLast : kMidAlone;
+        e = launch_middle(p.field, A, B, C, mode, p.L, linv, ctx->rt, ctx->rt30, ctx->nsm, st);
         if (e != cudaSuccess) return cuda_status(e);
     }
-    if (sum == kSumFirst || sum == kSumInner) return CM_OK;  // the window's last block finishes
-    void *R = C ? C : A;
+    if (sum == kSumFirst || sum == kSumInner) return CM_OK;  // the group's last block finishes
+    void *R = A;
     for (int j = p.npass - 1; j >= 0; --j) {
         PassArgs a;
         memset(&a, 0, sizeof(a));

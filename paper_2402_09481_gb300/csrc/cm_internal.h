@@ -57,9 +57,12 @@ cudaError_t launch_pass_fwd(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_inv(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_fwd30(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_inv30(const PassArgs &a, int logr, cudaStream_t st);
-// A, B: L elements of the field's word size.  The product's row-transformed
-// result goes to A (C null), to C (acc false) or is added into C (acc true).
-cudaError_t launch_middle(int field, void *A, const void *B, void *C, bool acc, uint64_t L, uint64_t linv,
+// A, B: L elements of the field's word size.  C null: the product's
+// row-transformed result goes to A.  Otherwise mode (MidSum) sums the scaled
+// transform-domain products of a sum group in C (L elements): kMidFirst
+// stores, kMidInner adds, kMidLast adds and writes the inverse row transform
+// of the sum to A.
+cudaError_t launch_middle(int field, void *A, const void *B, void *C, int mode, uint64_t L, uint64_t linv,
                           const RootTables &rt, const RootTables30 &rt30, int nsm, cudaStream_t st);
 cudaError_t launch_pack(const uint8_t *par, uint64_t m, uint64_t *z, const uint32_t *pre,
                         uint32_t *status, int nsm, cudaStream_t st);
@@ -102,18 +105,19 @@ constexpr uint64_t kMaxBlocks = 1u << 16;
 // How a block's product joins the others of its output window.
 enum SumMode : int {
     kSumNone = 0,   // a product on its own: inverse transform, parity, pack
-    kSumFirst = 1,  // writes the sum group's transform-domain sum C
-    kSumInner = 2,  // adds into C
-    kSumLast = 3,   // adds into C, then the inverse passes, parity and pack of C
+    kSumFirst = 1,  // forward passes, middle: stores the scaled product to C
+    kSumInner = 2,  // forward passes, middle: adds it into C
+    kSumLast = 3,   // adds it into C, inverse row and column passes of the sum, parity, pack
     kSumTail = 4,   // not a transform: the dense tail (p: the whole product's maps)
 };
 
 // One product of a blocked extraction: plan p (a middle product over an input
 // block and an output window) for the output words from zword on.  Input
 // blocks of one window share the transform length and the window position, so
-// their products are summed before one inverse transform (the counts add; a
-// sum group holds as many blocks as keep the total below the field's
-// characteristic).  Packing blocks of later groups, and of windows of one-CTA
+// their pointwise products are summed in the transform domain (in the middle
+// kernel, before the inverse row transform) and one inverse transform serves
+// the sum (the counts add; a sum group holds as many blocks as keep the total
+// below the field's characteristic).  Packing blocks of later groups, and of windows of one-CTA
 // plans (transform length <= 2^13, never summed), XOR their parities into z.
 // A plan may also leave its first `tail` terms (t < tail <= kTailMax) out of
 // the transforms: a last pseudo-block (kSumTail) XORs their dense GF(2)

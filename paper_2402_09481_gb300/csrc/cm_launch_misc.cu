@@ -12,7 +12,7 @@ namespace cm {
 template <class F>
 __global__ void __launch_bounds__(kThreads, sizeof(typename F::T) == 4 ? 2 : 1)
 k_middle(typename F::T *__restrict__ A, const typename F::T *__restrict__ Bv, typename F::T *__restrict__ C,
-         int acc, uint64_t nrows, uint64_t linv_, RootTablesT<typename F::T> rt) {
+         int mode, uint64_t nrows, uint64_t linv_, RootTablesT<typename F::T> rt) {
     using T = typename F::T;
     constexpr int LG = kMidLgMax;
     constexpr int Bn = 1 << LG;
@@ -39,19 +39,14 @@ k_middle(typename F::T *__restrict__ A, const typename F::T *__restrict__ Bv, ty
             }
         }
         __syncthreads();
-        middle_row_13_f<F>(sA, sB, tw, linv);
-        // result row -> A (in place), or C = row, or C += row (a sum of products)
-        uint4 *o4 = reinterpret_cast<uint4 *>((C ? C : A) + row);
+        middle_row_13_f<F>(sA, sB, tw, linv, C ? C + row : nullptr, mode);
+        if (mode == kMidFirst || mode == kMidInner) continue;  // the product went to C
+        // result row -> A (in place)
+        uint4 *o4 = reinterpret_cast<uint4 *>(A + row);
         for (int i = threadIdx.x; i < Bn / PER; i += kThreads) {
             T pv[PER];
 #pragma unroll
             for (int j = 0; j < PER; ++j) pv[j] = sA[sp(PER * i + j)];
-            if (acc) {
-                T pc[PER];
-                unpack16(o4[i], pc);
-#pragma unroll
-                for (int j = 0; j < PER; ++j) pv[j] = F::add(pv[j], pc[j]);
-            }
             o4[i] = pack16(pv);
         }
         __syncthreads();
@@ -105,7 +100,7 @@ cudaError_t launch_pass(const PassArgs &a, int logr, cudaStream_t st) {
 }
 
 template <class F>
-static cudaError_t launch_middle_f(void *A, const void *B, void *C, bool acc, uint64_t L, uint64_t linv,
+static cudaError_t launch_middle_f(void *A, const void *B, void *C, int mode, uint64_t L, uint64_t linv,
                                    const RootTablesT<typename F::T> &rt, int nsm, cudaStream_t st) {
     using T = typename F::T;
     const size_t sm = (2 * sp_size(1 << kMidLgMax) + (1 << kMidLgMax)) * sizeof(T);
@@ -115,14 +110,15 @@ static cudaError_t launch_middle_f(void *A, const void *B, void *C, bool acc, ui
     const uint64_t per_sm = sizeof(T) == 4 ? 2 : 1;  // resident CTAs per SM (shared memory, registers)
     const uint64_t grid = rows < per_sm * nsm ? rows : per_sm * nsm;
     k_middle<F><<<(unsigned)grid, kThreads, sm, st>>>(static_cast<T *>(A), static_cast<const T *>(B),
-                                                      static_cast<T *>(C), (C && acc) ? 1 : 0, rows, linv, rt);
+                                                      static_cast<T *>(C), C ? mode : (int)kMidAlone, rows, linv,
+                                                      rt);
     return cudaGetLastError();
 }
 
-cudaError_t launch_middle(int field, void *A, const void *B, void *C, bool acc, uint64_t L, uint64_t linv,
+cudaError_t launch_middle(int field, void *A, const void *B, void *C, int mode, uint64_t L, uint64_t linv,
                           const RootTables &rt, const RootTables30 &rt30, int nsm, cudaStream_t st) {
-    return field == kFieldF30 ? launch_middle_f<FieldF30>(A, B, C, acc, L, linv, rt30, nsm, st)
-                              : launch_middle_f<FieldGL>(A, B, C, acc, L, linv, rt, nsm, st);
+    return field == kFieldF30 ? launch_middle_f<FieldF30>(A, B, C, mode, L, linv, rt30, nsm, st)
+                              : launch_middle_f<FieldGL>(A, B, C, mode, L, linv, rt, nsm, st);
 }
 
 cudaError_t launch_pack(const uint8_t *par, uint64_t m, uint64_t *z, const uint32_t *pre,

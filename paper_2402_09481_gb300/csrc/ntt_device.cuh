@@ -335,16 +335,31 @@ __device__ __forceinline__ void ntt_inv(uint64_t *s0, uint64_t *s1, const uint64
     ntt_inv_f<FieldGL, LOGR, NCOL_LG, NBUF>(s0, s1, tw);
 }
 
+// How a fused middle row treats a product that is one of several summed in
+// the transform domain (a sum group of input blocks): the scaled pointwise
+// products are added up before the inverse row transform (which is linear), so
+// only the group's last product pays for it.
+enum MidSum : int {
+    kMidAlone = 0,  // inverse row transform of this product
+    kMidFirst = 1,  // store the product to the row's accumulator, no inverse
+    kMidInner = 2,  // add the product into the accumulator, no inverse
+    kMidLast = 3,   // inverse row transform of accumulator + product
+};
+
 // One fused middle row of B = 2^13 elements (steps of radix 32, 16, 16): forward
 // transforms of both operands, the pointwise product scaled by linv, and the
 // inverse transform of the product, left in sA in natural order.  The last
 // forward step, the product and the first inverse step run in registers on
 // 16-row groups (thread t owns rows 16t .. 16t + 15 of both operands), and
 // steps 1 and 2 only touch the 256-row blocks of the calling warp, so they are
-// separated by warp barriers only.  Ends with a block barrier.
+// separated by warp barriers only.  With a sum mode other than kMidAlone, gC
+// is the row's accumulator in global memory: thread t keeps its 16 products
+// (frequency order) at gC[16t .. 16t + 15]; kMidFirst and kMidInner return
+// after writing it (sA then holds nothing of use).  Ends with a block barrier.
 template <class F>
 __device__ __forceinline__ void middle_row_13_f(typename F::T *sA, typename F::T *sB, const typename F::T *tw,
-                                                typename F::T linv) {
+                                                typename F::T linv, typename F::T *gC = nullptr,
+                                                int mode = kMidAlone) {
     using T = typename F::T;
     static_assert(st_n(13) == 3 && st_q(13, 0) == 5 && st_q(13, 1) == 4 && st_q(13, 2) == 4, "schedule");
     static_assert(kThreads == 512, "one 16-row group per thread in the fused step");
@@ -364,9 +379,37 @@ __device__ __forceinline__ void middle_row_13_f(typename F::T *sA, typename F::T
         // frequency k sits in register bitrev(k); the inverse step takes frequency order
 #pragma unroll
         for (int k = 0; k < 16; ++k) c[k] = F::prod(a[bitrev_c(k, 4)], b[bitrev_c(k, 4)], linv);
-        dft_reg_f<F, 4>(c);
+        if (mode != kMidAlone) {
+            constexpr int PER = 16 / (int)sizeof(T);
+            uint4 *g4 = reinterpret_cast<uint4 *>(gC + row0);
+            if (mode != kMidFirst) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) sA[sp(row0 + i)] = c[bitrev_c((16 - i) & 15, 4)];
+                for (int q = 0; q < 16 / PER; ++q) {
+                    T pc[PER];
+                    unpack16(__ldcg(g4 + q), pc);
+#pragma unroll
+                    for (int j = 0; j < PER; ++j) c[PER * q + j] = F::add(c[PER * q + j], pc[j]);
+                }
+            }
+            if (mode != kMidLast) {
+#pragma unroll
+                for (int q = 0; q < 16 / PER; ++q) {
+                    T pc[PER];
+#pragma unroll
+                    for (int j = 0; j < PER; ++j) pc[j] = c[PER * q + j];
+                    g4[q] = pack16(pc);
+                }
+            }
+        }
+        if (mode == kMidAlone || mode == kMidLast) {
+            dft_reg_f<F, 4>(c);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) sA[sp(row0 + i)] = c[bitrev_c((16 - i) & 15, 4)];
+        }
+    }
+    if (mode == kMidFirst || mode == kMidInner) {
+        __syncthreads();  // sA / sB free for the next row
+        return;
     }
     __syncwarp();
     inv_step_f<F, 13, 1, 0, 1>(sA, sA, tw);

@@ -162,7 +162,7 @@ CASES = [
     (T, 20_000, 3_000, dict(max_transform_lg=12)),
     (T, 1_000, 300, dict(max_transform_lg=8)),
     (T, 50_000, 9_000, dict(max_transform_lg=14, field=native.FIELD_GOLDILOCKS)),
-    (T, 2 ** 22 + 50, 100, {}),  # one 2^22 product and a 149-term dense tail, not one 2^23
+    (T, 2 ** 22 + 50, 100, {}),  # products of 2^21 or 2^22 and a dense tail, not one 2^23
     (T, 2 ** 22 + 50, 100, dict(max_transform_lg=21)),  # three 2^21 products
     # dense tails: one product and 136 / 202 tail terms, two summed products
     # and 71, two output windows sharing a 200-term tail, over both fields
