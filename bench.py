@@ -164,25 +164,56 @@ def field_of(kernel):
     return (kernel[:-4], 4) if kernel.endswith("_f30") else (kernel, 8)
 
 
-def algorithmic_bytes(kernel, L, n, seedlen, m):
-    """Bytes one launch must move: field elements (8 B Goldilocks, 4 B for the
-    32-bit field), bits (1/8 B), parity bytes (1 B)."""
-    kernel, e = field_of(kernel)
-    if kernel == "k_middle":
-        return 3 * e * L                    # read both operands' rows, write one
-    if kernel == "k_pass_fwd_bits":
-        return e * L + (n + seedlen) / 16   # write one operand; read its bits (avg)
-    if kernel in ("k_pass_fwd", "k_pass_inv"):
-        return 2 * e * L
-    if kernel == "k_pass_inv_parity":
-        return e * L + m                    # read, write parity bytes of the window
-    if kernel == "k_pack":
-        return m + m / 8
-    if kernel == "k_fused_small":
-        return (n + seedlen + m) / 8
-    if kernel == "k_allsame":
-        return n / 8
-    return None
+def pass_split(L):
+    """Column passes of a transform of length L (log2 R of each, outer first):
+    none up to 2^13, one for lg - 13 <= 12, else ceil / floor halves."""
+    rest = int(L).bit_length() - 1 - 13
+    if rest <= 0:
+        return []
+    if rest <= 12:
+        return [rest]
+    return [(rest + 1) // 2, rest // 2]
+
+
+def kernel_model(products, m):
+    """Per-step totals of algorithmic bytes, radix-2 butterflies and launches
+    for each kernel (name without the field suffix), from the plan's product
+    list (cm_plan_products).  A forward-pass launch takes both operands; a
+    summed product's middle (sum 1, 2) skips the inverse row transform and
+    stores or adds its product to the group's accumulator (sum 2, 3 read it);
+    only alone (0) and last (3) products run the inverse passes and pack."""
+    tot = {}
+
+    def add(k, b, f):
+        t = tot.setdefault(k, {"bytes": 0.0, "butterflies": 0.0, "launches": 0})
+        t["bytes"] += b
+        t["butterflies"] += f
+        t["launches"] += 1
+
+    for p in products:
+        if p["sum"] == 4:  # dense tail: seed bits and z read, z written
+            add("k_tail", (p["m"] + p["tail_terms"]) / 8 + 2 * p["m"] / 8, 0.0)
+            continue
+        L, e, s, mr = p["L"], (4 if p["field"] == 2 else 8), p["sum"], p["m"]
+        lg = int(L).bit_length() - 1
+        split = pass_split(L)
+        if not split:
+            add("k_fused_small", (p["a_len"] + p["b_len"] + mr) / 8, 3 * (L // 2) * lg)
+            continue
+        for j, r in enumerate(split):
+            if j == 0:
+                add("k_pass_fwd_bits", 2 * e * L + (p["a_len"] + p["b_len"]) / 8, 2 * (L // 2) * r)
+            else:
+                add("k_pass_fwd", 4 * e * L, 2 * (L // 2) * r)
+        add("k_middle", e * L * (3 if s in (0, 1) else 4), (3 if s in (0, 3) else 2) * (L // 2) * 13)
+        if s in (0, 3):
+            for j in reversed(range(len(split))):
+                if j == 0:
+                    add("k_pass_inv_parity", e * L + mr, (L // 2) * split[j])
+                else:
+                    add("k_pass_inv", 2 * e * L, (L // 2) * split[j])
+            add("k_pack", mr + mr / 8, 0.0)
+    return tot
 
 
 # ALU roofline model for the transforms: a radix-2 butterfly needs at least a
@@ -200,25 +231,6 @@ NUM_SMS = 152
 
 def alu_peak_butterflies(sm_mhz, ops=ALU_OPS_PER_BUTTERFLY):
     return NUM_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / ops
-
-
-def kernel_butterflies(kernel, L):
-    """Radix-2 butterflies one launch performs (L/2 per stage per transform).
-    Column passes: one pass for lg - 13 <= 12 (log2 R = lg - 13), else two with
-    log2 R = ceil((lg - 13) / 2) for the outer pass (k_pass_fwd_bits,
-    k_pass_inv_parity) and floor((lg - 13) / 2) for the inner one."""
-    kernel, _ = field_of(kernel)
-    lg = int(L).bit_length() - 1
-    rest = lg - 13
-    if kernel == "k_middle":
-        return 3 * (L // 2) * 13            # two forward row transforms, one inverse
-    if kernel in ("k_pass_fwd_bits", "k_pass_inv_parity"):
-        return (L // 2) * (rest if rest <= 12 else (rest + 1) // 2)
-    if kernel in ("k_pass_fwd", "k_pass_inv"):
-        return (L // 2) * (rest // 2)
-    if kernel == "k_fused_small":
-        return 3 * (L // 2) * lg
-    return None
 
 
 def path_bytes(products, n, seedlen, m):
@@ -1113,11 +1125,13 @@ def main():
         kernels[k]["share"] = t / tot
     dom = max(prof, key=lambda k: prof[k][1])
     per_launch = prof[dom][1] / prof[dom][0]
-    alg = algorithmic_bytes(dom, L, n, sb, m)
+    model = kernel_model(products, m)[field_of(dom)[0]]
+    # per launch: the step's totals over the kernel's launches in a step
+    alg = model["bytes"] / model["launches"]
+    bfly = model["butterflies"] / model["launches"]
     peak, peak_src = measured_peaks()
     achieved = alg / (per_launch * 1e-3) / 1e9
     clk = (sampler.summary(t_wall0, t_wall1) or {}).get("sm_mhz") or 2070.0
-    bfly = kernel_butterflies(dom, L)
     ops = ALU_OPS_PER_BUTTERFLY_F30 if dom.endswith("_f30") else ALU_OPS_PER_BUTTERFLY
     ach_b = bfly / (per_launch * 1e-3) / 1e9
     peak_b = alu_peak_butterflies(clk, ops) / 1e9
@@ -1126,7 +1140,7 @@ def main():
             "peak_source": f"{NUM_SMS} SMs x {ALU_LANES_PER_SM} ALU lanes x {clk:.0f} MHz measured / "
                            f"{ops} ALU ops per radix-2 butterfly",
             "traffic": ncu_traffic(dom, args.workload), "butterflies_per_launch": bfly,
-            "avg_launch_ms": per_launch,
+            "launches_per_step": model["launches"], "avg_launch_ms": per_launch,
             "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src, "algorithmic_bytes_per_launch": alg}}
     pb = path_bytes(products, n, sb, m)

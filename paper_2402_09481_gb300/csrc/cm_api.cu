@@ -498,7 +498,7 @@ cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const u
 // Scratch of a blocked run: the largest block's scratch; then (one-CTA windows
 // whose blocks XOR) one output window of temporary at *tmp_off; then 256 bytes
 // of precondition flags at *pre_off.
-static uint64_t blocks_scratch(const std::vector<Block> &bl, uint64_t *tmp_off, uint64_t *pre_off) {
+uint64_t blocks_scratch(const std::vector<Block> &bl, uint64_t *tmp_off, uint64_t *pre_off) {
     uint64_t sc = 0, tmpw = 0;
     for (const Block &b : bl) {
         if (b.sum == kSumTail) continue;  // no scratch; XORs straight into z
@@ -514,9 +514,8 @@ static uint64_t blocks_scratch(const std::vector<Block> &bl, uint64_t *tmp_off, 
 }
 
 // Enqueue every block of an extraction; scratch holds blocks_scratch() bytes.
-static cm_status enqueue_blocks(cm_ctx *ctx, const std::vector<Block> &bl, const uint64_t *x,
-                                const uint64_t *y, uint64_t *z, uint8_t *scratch, uint64_t tmp_off,
-                                uint64_t pre_off, cudaStream_t st) {
+cm_status enqueue_blocks(cm_ctx *ctx, const std::vector<Block> &bl, const uint64_t *x, const uint64_t *y,
+                         uint64_t *z, uint8_t *scratch, uint64_t tmp_off, uint64_t pre_off, cudaStream_t st) {
     uint32_t *pre = nullptr;
     if (!bl.empty() && bl[0].p.kind == CM_DODIS) {
         pre = reinterpret_cast<uint32_t *>(scratch + pre_off);

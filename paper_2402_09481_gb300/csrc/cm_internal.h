@@ -150,6 +150,11 @@ bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::ve
 // Estimated GPU time (ms) of a block list, from measured per-length times.
 double blocks_cost_ms(const std::vector<Block> &bl);
 
+// Scratch bytes of a block list: the largest block's scratch, then an XOR
+// temporary at *tmp_off (when blocks XOR), then 256 bytes of Dodis et al.
+// precondition flags at *pre_off.
+uint64_t blocks_scratch(const std::vector<Block> &bl, uint64_t *tmp_off, uint64_t *pre_off);
+
 // z[i] ^= t[i], i < words (stream-ordered).
 cudaError_t launch_xor_into(uint64_t *z, const uint64_t *t, uint64_t words, int nsm, cudaStream_t st);
 

@@ -159,11 +159,12 @@ cudaError_t launch_xor_into(uint64_t *z, const uint64_t *t, uint64_t words, int 
 constexpr int kTailThreads = 256;
 static_assert(kTailMax == kTailThreads && kTailMax % 64 == 0, "one tail bit per thread");
 
+// NW = ceil(T / 64) words of tail bits (the loop runs over 64 NW terms).
+template <int NW>
 __global__ void __launch_bounds__(kTailThreads)
 k_tail(BitMap amap, BitMap bmap, uint64_t K, uint32_t T, uint64_t m, uint64_t *__restrict__ z,
        const uint32_t *__restrict__ pre) {
     if (pre && (pre[0] == 0u || pre[1] == 0u)) return;  // the pack kernel left z zero
-    constexpr int NW = kTailMax / 64;
     __shared__ uint32_t sal[kTailMax / 32];
     {
         const int t = threadIdx.x;  // one tail position per thread
@@ -186,7 +187,7 @@ k_tail(BitMap amap, BitMap bmap, uint64_t K, uint32_t T, uint64_t m, uint64_t *_
         }
         uint64_t acc = 0;
 #pragma unroll
-        for (int t = 0; t < kTailMax; ++t) {
+        for (int t = 0; t < 64 * NW; ++t) {
             const int q = t >> 6, s = t & 63;
             const uint64_t run = s ? (W[q] >> s) | (W[q + 1] << (64 - s)) : W[q];
             if ((al[q] >> s) & 1ull) acc ^= run;
@@ -204,7 +205,12 @@ cudaError_t launch_tail(const BitMap &amap, const BitMap &bmap, uint64_t K, uint
     const uint64_t cap = (uint64_t)nsm * 8;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) blocks = 1;
-    k_tail<<<(unsigned)blocks, kTailThreads, 0, st>>>(amap, bmap, K, T, m, z, pre);
+    switch ((T + 63) / 64) {
+        case 1: k_tail<1><<<(unsigned)blocks, kTailThreads, 0, st>>>(amap, bmap, K, T, m, z, pre); break;
+        case 2: k_tail<2><<<(unsigned)blocks, kTailThreads, 0, st>>>(amap, bmap, K, T, m, z, pre); break;
+        case 3: k_tail<3><<<(unsigned)blocks, kTailThreads, 0, st>>>(amap, bmap, K, T, m, z, pre); break;
+        default: k_tail<4><<<(unsigned)blocks, kTailThreads, 0, st>>>(amap, bmap, K, T, m, z, pre); break;
+    }
     return cudaGetLastError();
 }
 

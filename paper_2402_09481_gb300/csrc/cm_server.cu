@@ -31,8 +31,8 @@
 #include "cm_internal.h"
 
 namespace cm {
-cm_status enqueue_extract(cm_ctx *ctx, const Plan &p, const uint64_t *x, const uint64_t *y,
-                          uint64_t *z, void *scratch, cudaStream_t st);
+cm_status enqueue_blocks(cm_ctx *ctx, const std::vector<Block> &bl, const uint64_t *x, const uint64_t *y,
+                         uint64_t *z, uint8_t *scratch, uint64_t tmp_off, uint64_t pre_off, cudaStream_t st);
 }
 
 using namespace cm;
@@ -49,7 +49,9 @@ size_t r256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Req {
     cm_desc d;
-    Plan p;
+    Plan p;                     // one-transform plan (work-list requests: L <= 2^25)
+    std::vector<Block> blocks;  // longer requests: the single-call planner's products
+    uint64_t tmp_off = 0, pre_off = 0;
     uint32_t flags = 0;
     uint64_t seed_id = 0;
     size_t foot = 0;  // scratch bytes while on the device
@@ -213,7 +215,8 @@ cm_status launch_wave(cm_server *S, Slot &sl, const std::vector<uint64_t> &tk) {
             total += worklist_scratch_bytes(r.p);
         } else {
             solo.push_back(i);
-            total += r256(r.p.scratch_bytes);
+            uint64_t t0, t1;
+            total += r256(blocks_scratch(r.blocks, &t0, &t1));
         }
     }
     void *scratch = nullptr;
@@ -290,12 +293,14 @@ cm_status launch_wave(cm_server *S, Slot &sl, const std::vector<uint64_t> &tk) {
         if (e != cudaSuccess) return CM_EDEVICE;
     }
     for (uint32_t i : solo) {
-        cm_status s = enqueue_extract(ctx, plans[i], descs[i].x, descs[i].y, descs[i].z,
-                                      static_cast<uint8_t *>(scratch) + off[i], sl.st);
+        const Req &r = S->reqs[tk[i]];
+        uint8_t *sc = static_cast<uint8_t *>(scratch) + off[i];
+        cm_status s = enqueue_blocks(ctx, r.blocks, descs[i].x, descs[i].y, descs[i].z, sc, r.tmp_off, r.pre_off,
+                                     sl.st);
         if (s != CM_OK) return s;
         if (plans[i].kind == CM_DODIS) {
-            // the single-call path keeps its flag pair in the last 256 bytes of its scratch
-            const uint8_t *pf = static_cast<uint8_t *>(scratch) + off[i] + plans[i].scratch_bytes - 256;
+            // the single-call path keeps its flag pair at pre_off of its scratch
+            const uint8_t *pf = sc + r.pre_off;
             sl.pre_index[i] = (int)(wl.size() + i);
             if (cudaMemcpyAsync(dflags + 2 + 2 * (wl.size() + i), pf, 8, cudaMemcpyDeviceToDevice, sl.st) !=
                 cudaSuccess)
@@ -481,7 +486,16 @@ extern "C" cm_status cm_submit(cm_ctx *ctx, const cm_request *rq, uint64_t *tick
     r.seed_id = rq->seed_id;
     if (rq->flags & ~CM_REQ_SEED_CACHE) return CM_EINVAL;
     if (!rq->x || !rq->y || !rq->z || !make_plan(rq->kind, rq->n, rq->m, &r.p, ctx->popt.allow_f30)) return CM_EINVAL;
-    r.foot = r.p.npass <= 1 ? worklist_scratch_bytes(r.p) : r256(r.p.scratch_bytes);
+    if (r.p.npass > 1) {
+        // too long for the work list: the single-call planner (sums of shorter
+        // products, a dense tail) within the server's budget
+        PlanOptions po = ctx->popt;
+        po.budget = S->budget;
+        if (!make_blocks(rq->kind, rq->n, rq->m, po, &r.blocks)) return CM_EINVAL;
+        r.foot = r256(blocks_scratch(r.blocks, &r.tmp_off, &r.pre_off));
+    } else {
+        r.foot = worklist_scratch_bytes(r.p);
+    }
     r.foot += 256;  // work-list and flag share
     {
         std::lock_guard<std::mutex> g(S->mu);
