@@ -233,6 +233,56 @@ def alu_peak_butterflies(sm_mhz, ops=ALU_OPS_PER_BUTTERFLY):
     return NUM_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / ops
 
 
+def _steps(logr):
+    """Radix steps (log2 radix each) of an on-chip transform of 2^logr."""
+    ns = (logr + 4) // 5
+    return [logr // ns + (1 if j < logr % ns else 0) for j in range(ns)]
+
+
+def _transform_modmuls(logr, f30):
+    """General modular multiplies per element of one on-chip transform of
+    2^logr: the sub-transform twiddles (non-trivial radix-2 rotations; shifts
+    over Goldilocks, products over the 32-bit field) and the twiddles between
+    steps (all but the last step)."""
+    st = _steps(logr)
+    tot = 0.0
+    for j, q in enumerate(st):
+        rd = 1 << q
+        if f30:
+            tot += ((rd // 2) * q - (rd - 1)) / rd
+        if j + 1 < len(st):
+            tot += (rd - 1) / rd
+    return tot
+
+
+def path_modmuls(products):
+    """(N_path, N_official): general modular multiplies of the path as the
+    kernels run it (on-chip sub-transform and step twiddles, the column passes'
+    row twiddles, the pointwise product and its scaling), and the count of
+    the reference model, 3 L (ceil(lg / 6) - 1) + L per product (a radix-64
+    plan whose inner twiddles are shifts)."""
+    n_path = n_off = 0.0
+    for p in products:
+        if p["sum"] == 4:
+            continue
+        L, f30, s = p["L"], p["field"] == 2, p["sum"]
+        lg = int(L).bit_length() - 1
+        n_off += 3 * L * (-(-lg // 6) - 1) + L
+        split = pass_split(L)
+        row_tw = 9 / 4 if f30 else 2.0
+        per = 0.0
+        for r in split:  # forward column passes of both operands
+            per += 2 * (_transform_modmuls(r, f30) + row_tw)
+        mid = _transform_modmuls(min(lg, 13), f30)
+        inverse = s in (0, 3)
+        per += 2 * mid + 2 + (mid if inverse else 0.0)
+        if inverse:
+            for r in split:
+                per += _transform_modmuls(r, f30) + row_tw
+        n_path += per * L
+    return n_path, n_off
+
+
 def path_bytes(products, n, seedlen, m):
     """Bytes the path moves at least: per product of transform length L over
     e-byte elements, one write and one read of three L-element arrays (6 e L:
@@ -1143,11 +1193,28 @@ def main():
             "launches_per_step": model["launches"], "avg_launch_ms": per_launch,
             "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src, "algorithmic_bytes_per_launch": alg}}
+    # path roofline: max(HBM time of the path bytes, integer-pipe time of its
+    # modular multiplies at the measured rate) against the measured step time
     pb = path_bytes(products, n, sb, m)
-    path_roof = {"model": "6 e L per product (e = element bytes) + bit I/O", "bytes": pb,
+    n_path, n_off = path_modmuls(products)
+    r_gl = native.modmul_rate(local, native.FIELD_GOLDILOCKS)
+    r_q30 = native.modmul_rate(local, native.FIELD_Q30)
+    r_path = r_q30 if plan["field"] == native.FIELD_Q30 else r_gl
+    t_hbm = pb / (peak * 1e9) * 1e3
+    t_int_off = n_off / r_gl * 1e3
+    t_int_path = n_path / r_path * 1e3
+    path_roof = {"model": "6 e L per product (e = element bytes) + bit I/O; modular multiplies at the "
+                          "measured rate (cm_modmul_rate)", "bytes": pb,
                  "achieved_gbs": pb / (ms_per_step * 1e-3) / 1e9,
                  "frac_of_measured_hbm": pb / (ms_per_step * 1e-3) / 1e9 / peak,
-                 "frac_of_8tbs": pb / (ms_per_step * 1e-3) / 1e9 / 8000.0}
+                 "frac_of_8tbs": pb / (ms_per_step * 1e-3) / 1e9 / 8000.0,
+                 "t_hbm_ms": t_hbm, "t_hbm_8tbs_ms": pb / 8e12 * 1e3,
+                 "modmuls_reference_model": n_off, "modmul_rate_goldilocks_per_s": r_gl,
+                 "t_int_reference_model_ms": t_int_off,
+                 "roofline_ms": max(t_hbm, t_int_off), "frac": max(t_hbm, t_int_off) / ms_per_step,
+                 "modmuls_path": n_path, "modmul_rate_path_per_s": r_path, "t_int_path_ms": t_int_path,
+                 "roofline_path_ms": max(t_hbm, t_int_path),
+                 "frac_path": max(t_hbm, t_int_path) / ms_per_step}
 
     # the Dodis et al. workload as its configuration states it: one Goldilocks
     # transform of length 2^31 (single-transform plan); same bits

@@ -407,6 +407,15 @@ cm_status cm_profile_read(cm_ctx *ctx, cm_profile_entry *out, uint32_t cap, uint
  * of disagreements (0 when correct).  Allocates and frees 8 bytes. */
 cm_status cm_field_selftest(int device, uint64_t count, uint64_t seed, uint64_t *mismatches);
 
+/* Modular-multiply rate of `device` for `field` (CM_FIELD_GOLDILOCKS: the
+ * 64-bit product and reduction of the transforms; CM_FIELD_Q30: the 32-bit
+ * Montgomery product), measured by a kernel of independent register chains of
+ * products on every SM (8 chains a thread, 4 CTAs of 256 threads per SM) and
+ * timed with CUDA events: *per_second receives products per second.  The
+ * integer-pipe bound of a path is its number of general multiplies divided by
+ * this rate.  Allocates and frees 8 bytes; CM_EINVAL for another field. */
+cm_status cm_modmul_rate(int device, uint32_t field, double *per_second);
+
 /* ----- host helpers (no GPU work) --------------------------------------- */
 
 /* 1 if P is prime and 2 is a primitive root modulo P (the set N_A of the

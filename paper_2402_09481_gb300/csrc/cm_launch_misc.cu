@@ -276,6 +276,65 @@ __global__ void k_field_selftest(uint64_t count, uint64_t seed, unsigned long lo
 
 }  // namespace cm
 
+namespace cm {
+
+// Independent chains x <- x w of the field's product, kChains per thread;
+// the chains' sum goes to *sink so that nothing is dead code.
+constexpr int kChains = 8;
+template <class F>
+__global__ void __launch_bounds__(256) k_modmul_rate(uint32_t iters, typename F::T w, typename F::T *sink) {
+    using T = typename F::T;
+    T x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = (T)(threadIdx.x + 977u * (c + 1) + blockIdx.x);
+    for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = F::twmul(x[c], w);
+    }
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s ^= x[c];
+    if (s == (T)0x5bd1e995u) *sink = s;  // practically never; keeps the chains live
+}
+
+template <class F>
+static cm_status modmul_rate(int nsm, typename F::T w, double *rate) {
+    using T = typename F::T;
+    T *sink = nullptr;
+    if (cudaMalloc(&sink, sizeof(T)) != cudaSuccess) return CM_ENOMEM;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cm_status st = CM_OK;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) st = CM_EDEVICE;
+    const unsigned grid = 4u * (unsigned)nsm;
+    const uint32_t iters = 4096;
+    float ms = 0.f;
+    if (st == CM_OK) {
+        k_modmul_rate<F><<<grid, 256>>>(iters, w, sink);  // warm-up
+        cudaEventRecord(a);
+        k_modmul_rate<F><<<grid, 256>>>(iters, w, sink);
+        cudaEventRecord(b);
+        if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, a, b) != cudaSuccess || ms <= 0.f)
+            st = CM_EDEVICE;
+    }
+    if (st == CM_OK) *rate = (double)grid * 256.0 * kChains * iters / (ms * 1e-3);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(sink);
+    return st;
+}
+
+}  // namespace cm
+
+extern "C" cm_status cm_modmul_rate(int device, uint32_t field, double *per_second) {
+    if (!per_second || (field != CM_FIELD_GOLDILOCKS && field != CM_FIELD_Q30)) return CM_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return CM_EDEVICE;
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return CM_EDEVICE;
+    if (field == CM_FIELD_Q30) return cm::modmul_rate<cm::FieldF30>(nsm, f30_to_mont(12345u), per_second);
+    return cm::modmul_rate<cm::FieldGL>(nsm, 0x123456789ABCDEFull, per_second);
+}
+
 extern "C" cm_status cm_field_selftest(int device, uint64_t count, uint64_t seed, uint64_t *mismatches) {
     if (!mismatches) return CM_EINVAL;
     if (cudaSetDevice(device) != cudaSuccess) return CM_EDEVICE;

@@ -63,6 +63,7 @@ PROTOTYPES = {
     "cm_launch_count": (_U32, [_I, _U64, _U64]),
     "cm_block_count": (_U64, [_I, _U64, _U64, _U32]),
     "cm_plan_query": (_I, [_I, _U64, _U64, ctypes.c_void_p, ctypes.c_void_p]),
+    "cm_modmul_rate": (_I, [_I, _U32, ctypes.POINTER(ctypes.c_double)]),
     "cm_plan_products": (_I, [_I, _U64, _U64, ctypes.c_void_p, ctypes.c_void_p, _U64, ctypes.POINTER(_U64)]),
     "cm_output_length": (_I, [_I, _I, _I, _U64, _U64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                               ctypes.POINTER(ctypes.c_int64)]),
@@ -242,6 +243,13 @@ def plan_products(kind: int, n: int, m: int, max_transform_lg: int = 0, field: i
 
 def launch_count(kind: int, n: int, m: int) -> int:
     return int(lib().cm_launch_count(kind, n, m))
+
+
+def modmul_rate(device: int = 0, field: int = FIELD_Q30) -> float:
+    """Measured modular products per second of the field's multiply (cm_modmul_rate)."""
+    r = ctypes.c_double()
+    _check(lib().cm_modmul_rate(device, field, ctypes.byref(r)), "cm_modmul_rate")
+    return r.value
 
 
 def field_selftest(device: int = 0, count: int = 1 << 20, seed: int = 1) -> int:

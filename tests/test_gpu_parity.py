@@ -196,6 +196,17 @@ def test_dodis_workload_size(cm_ctx):
     assert (out_bits(z, m, rows) == oracle.dodis_rows(xw, yw, n, m, rows)).all()
 
 
+def test_modmul_rate(cm_ctx):
+    # the integer-pipe denominators of the path roofline: positive, and the
+    # 32-bit Montgomery product (3 multiply-adds) faster than the Goldilocks
+    # product (a 64 x 64-bit multiply in 32-bit pieces and its reduction)
+    q30 = native.modmul_rate(0, native.FIELD_Q30)
+    gl = native.modmul_rate(0, native.FIELD_GOLDILOCKS)
+    assert 1e11 < gl < q30 < 1e14
+    with pytest.raises(native.CMError):
+        native.modmul_rate(0, 7)
+
+
 def test_field_selftest_device_arithmetic(cm_ctx):
     # the PTX carry-chain arithmetic against the C forms (which the CPU test
     # pins to 128-bit integers), on edge values and 4M random pairs
