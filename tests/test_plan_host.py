@@ -261,3 +261,39 @@ def test_plan_query_rejects():
         native.plan_query(T, 2 ** 40, 2 ** 40)  # more than 65536 products
     with pytest.raises(native.CMError):
         native.plan_query(C, 6, 3)  # 7 is not in N_A
+
+
+def random_cases(count, seed=2402):
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < count:
+        kind = int(rng.integers(0, 3))
+        n = int(rng.integers(200, 60_000))
+        if kind == C:
+            n = oracle.next_na(n + 1) - 1
+        elif kind == D:
+            n = oracle.next_na(n)
+        m = int(rng.integers(1, (20_000 if kind == T else n) + 1))
+        opts = dict(max_transform_lg=int(rng.choice([8, 10, 12, 14, 15, 16])),
+                    max_sum_blocks=int(rng.choice([0, 2, 3])),
+                    field=int(rng.choice([native.FIELD_AUTO, native.FIELD_GOLDILOCKS])))
+        try:
+            prods = native.plan_products(kind, n, m, **opts)
+        except native.CMError:  # more than 65536 products at the smallest limits
+            continue
+        if len(prods) > 1:
+            out.append((kind, n, m, opts))
+    return out
+
+
+@pytest.mark.parametrize("kind,n,m,opts", random_cases(24))
+def test_random_plans_reproduce_oracle(kind, n, m, opts):
+    # seeded random lengths, limits, sum caps and fields: every listed product
+    # list reproduces the oracle's output bit for bit
+    prods = native.plan_products(kind, n, m, **opts)
+    check_structure(kind, n, m, prods)
+    xw = inputs.bernoulli_half(800 + n % 71, n)
+    if kind == D:
+        xw[0] = (xw[0] | np.uint64(1)) & ~np.uint64(2)
+    yw = inputs.bernoulli_half(801 + m % 67, ybits(kind, n, m))
+    assert (emulate(kind, n, m, xw, yw, prods) == want(kind, n, m, xw, yw)).all()
