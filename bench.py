@@ -50,6 +50,10 @@ WORKLOADS = {
     "qrng_toeplitz": dict(kind=0, n=6_500_000_000, m=581_294_933,
                           name="Toeplitz at the QRNG example's sizes: n = 6.5e9, m = 581294933, "
                                "Bernoulli(1/2) x and y"),
+    # the QKD privacy-amplification example: n1 = 1.738e9 raw key bits, m = 41378264
+    "qkd_toeplitz": dict(kind=0, n=1_738_000_000, m=41_378_264,
+                         name="Toeplitz at the QKD example's sizes: n = 1.738e9, m = 41378264, "
+                              "Bernoulli(1/2) x and y"),
     "qrng_circulant": dict(kind=1, n=6_500_000_068, m=581_294_933,
                            name="Circulant at the QRNG example's sizes: P = 6500000069, m = 581294933, "
                                 "Bernoulli(1/2) x and y"),

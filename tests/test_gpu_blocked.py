@@ -232,6 +232,19 @@ def test_qrng_example_toeplitz_sampled(cm_ctx):
 
 
 @pytest.mark.slow
+def test_qkd_example_toeplitz_sampled(cm_ctx):
+    # Section "Cryptomite for privacy amplification in QKD": n = 1.738e9 raw
+    # key bits, m = 41378264, seed n + m - 1 bits
+    n, m = 1_738_000_000, 41_378_264
+    xw, yw = inputs.bernoulli_half(64, n), inputs.bernoulli_half(65, n + m - 1)
+    z = run(cm_ctx, T, n, m, xw, yw)
+    rows = sample_rows(m, 24, 6)
+    assert (out_bits(z, rows) == oracle.toeplitz_rows(xw, n, yw, m, rows)).all()
+    if m & 63:
+        assert int(z[-1]) >> (m & 63) == 0
+
+
+@pytest.mark.slow
 def test_qrng_example_circulant_sampled(cm_ctx):
     # the Circulant extension of the same example: P = 6.5e9 + 69, n1' = P - 1
     n, m = 6_500_000_068, 581_294_933

@@ -152,15 +152,22 @@ def test_server_queue_full_poll_timeout_unknown(sctx):
 
 
 def test_server_dodis_precondition_per_request(sctx, cm_ctx):
-    P, Q = oracle.next_na(70000), oracle.next_na(700)
+    # work-list requests and, past the work list's 2^25 (P about 2^25 + 2^24:
+    # the single-call planner inside the wave), requests of both paths
+    P, Q, B = oracle.next_na(70000), oracle.next_na(700), oracle.next_na(3 << 24)
     reqs = [make(D, P, P // 2, 51, const_x=1), make(D, Q, Q // 2, 53, const_x=0),
-            make(D, P, P // 3, 55), make(T, 5000, 2500, 57)]
+            make(D, P, P // 3, 55), make(T, 5000, 2500, 57),
+            make(D, B, B // 2, 59, const_x=0), make(D, B, B // 3, 61)]
+    assert native.plan_query(D, B, B // 2)["transform_length"] > 2 ** 25 or \
+        native.plan_query(D, B, B // 2)["products"] > 1
     sctx.server_start()
     tickets = [submit(sctx, r) for r in reqs]
     res = [wait(sctx, t) for t in tickets]
-    assert [r["status"] for r in res] == [native.CM_EPRECOND, native.CM_EPRECOND, native.CM_OK, native.CM_OK]
+    assert [r["status"] for r in res] == [native.CM_EPRECOND, native.CM_EPRECOND, native.CM_OK, native.CM_OK,
+                                           native.CM_EPRECOND, native.CM_OK]
     assert not from_dev(reqs[0]["z"]).any() and not from_dev(reqs[1]["z"]).any()
-    for r in reqs[2:]:
+    assert not from_dev(reqs[4]["z"]).any()
+    for r in reqs[2:4] + reqs[5:]:
         assert torch.equal(r["z"], alone(cm_ctx, r))
     sctx.server_stop()
 
