@@ -22,6 +22,11 @@ its base theorem.
 ``oracle.von_neumann`` is the Von Neumann extractor of Alg. vn, pinned by
 ``tests/test_von_neumann_oracle.py``.
 
+``oracle.trevisan`` is the one-bit step of Trevisan's extractor (the
+Reed-Solomon-Hadamard one-bit extractor of Section "Trevisan implementation",
+with the weak design's sets as an input), pinned by
+``tests/test_trevisan_oracle.py``.
+
 Parity status: every function here is pinned by ``tests/test_oracle.py``
 (brute force, closed forms, the paper's displayed matrices, the two-universality
 count of Thm. 2-univ, the rank lemmas, cross-definition identities) and
