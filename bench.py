@@ -336,6 +336,24 @@ def run_reference(args, world, rank):
     if args.workload == "von_neumann":
         run_reference_vn(args)
         return
+    if args.workload == "trevisan":
+        n, m, l = trevisan_shape()
+        xw, sw = inputs.bernoulli_half(40, n), inputs.bernoulli_half(41, 2 * l * m)
+        t0 = time.perf_counter()
+        rates = [trevisan_reference_rate(xw, n, sw, l, 5.0)[0] for _ in range(args.steps)]
+        secs = time.perf_counter() - t0
+        value = statistics.median(rates) / 1e9
+        print(json.dumps({"impl": "reference", "metric": "extracted output Gbit/s", "value": value,
+                          "unit": "Gbit/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": 0,
+                          "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "python int", "data": "synthetic",
+                          "config": {"workload": f"Trevisan one-bit step: n = {n}, m = {m} RSH one-bit "
+                                                 f"extractions, l = {l}", "n": n, "m": m, "l": l},
+                          "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
+                                           "sample": "one-bit extractions for 5 s per step"},
+                          "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return
     if args.workload not in WORKLOADS:
         print(json.dumps({"impl": "reference", "unavailable": f"no oracle arm for the {args.workload} workload"}))
         return
@@ -935,6 +953,165 @@ def run_von_neumann(args, world, rank, local):
         dist.destroy_process_group()
 
 
+TREV_N, TREV_M, TREV_EPS = 1 << 20, 1 << 16, 1e-10
+
+
+def trevisan_shape():
+    """n, m, l of the Trevisan one-bit-step workload: l from the per-bit error
+    eps / m (the total error eps = m eps1)."""
+    import math
+    l = math.ceil(math.log2(TREV_N) + 2 * math.log2(2.0 / (TREV_EPS / TREV_M)))
+    return TREV_N, TREV_M, l
+
+
+def trevisan_reference_rate(xw, n, sw, l, budget_s):
+    """Oracle one-bit extractions per second on the first outputs."""
+    import oracle.trevisan as otv
+    from oracle import extractors as ex
+    xb = ex.unpack_bits(xw, n)
+    f = otv.rsh_modulus(l)
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        sb = ex.unpack_bits(sw, 2 * l * (done + 1))[2 * l * done:]
+        otv.rsh_onebit(xb, n, sb, l, f)
+        done += 1
+    secs = time.perf_counter() - t0
+    return done / secs, done, secs
+
+
+def run_trevisan(args, world, rank, local):
+    """Trevisan's one-bit step (Section "Trevisan implementation"): m = 2^16
+    Reed-Solomon-Hadamard one-bit extractions of one input of n = 2^20
+    Bernoulli(1/2) bits, each under its own 2l-bit seed (standing for the
+    weak design's sub-seeds), l = ceil(log2 n + 2 log2(2 m / eps)), eps = 1e-10.
+    One step = one cm_trevisan_rsh call."""
+    import numpy as np
+    import torch
+
+    from paper_2402_09481_gb300 import build, inputs, native
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    n, m, l = trevisan_shape()
+    xw = inputs.bernoulli_half(40 + 1000 * rank, n)
+    sw = inputs.bernoulli_half(41 + 1000 * rank, 2 * l * m)
+    xd = torch.from_numpy(xw.view(np.int64)).cuda()
+    sd = torch.from_numpy(sw.view(np.int64)).cuda()
+    zd = torch.empty(native.words(m), dtype=torch.int64, device="cuda")
+    ctx = native.Context(local)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.trevisan_rsh(xd, n, l, sd, m, zd)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if rank == 0:  # spot check against the oracle
+        import oracle.trevisan as otv
+        from oracle import extractors as ex
+        xb, sb = ex.unpack_bits(xw, n), ex.unpack_bits(sw, 2 * l * 3)
+        zb = ex.unpack_bits(zd.cpu().numpy().view(np.uint64), m)
+        for i in range(3):
+            assert zb[i] == otv.rsh_onebit(xb, n, sb[2 * l * i: 2 * l * (i + 1)], l), i
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.25)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    tw0 = time.time()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev:
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    tw1 = time.time()
+    if dist:
+        dist.barrier()
+    time.sleep(0.25)
+    sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * m / (ms_per_step * 1e-3) / 1e9
+    ctx.profile_enable(True)
+    ctx.profile_read(reset=True)
+    for _ in range(args.steps):
+        step()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile_enable(False)
+    c_, t_ = prof["k_rsh"]
+    per_launch = t_ / c_
+    s = -(-n // l)
+    # schoolbook GF(2) work: (s - 1) products of l-bit polynomials (l^2 bit
+    # AND-XORs each) per output; one LOP3 does 32 of them on one lane
+    macs = float(m) * (s - 1) * l * l
+    clk = (sampler.summary(tw0, tw1) or {}).get("sm_mhz") or 2070.0
+    peak = NUM_SMS * ALU_LANES_PER_SM * clk * 1e6 * 32 / 1e9
+    ach = macs / (per_launch * 1e-3) / 1e9
+    roof = {"bound": "alu", "kernel": "k_rsh", "achieved": ach, "peak": peak, "unit": "G GF(2) bit-MACs/s",
+            "frac": ach / peak,
+            "peak_source": f"{NUM_SMS} SMs x {ALU_LANES_PER_SM} ALU lanes x {clk:.0f} MHz measured x 32 "
+                           "(one LOP3 = 32 AND + 32 XOR)",
+            "traffic": ncu_traffic("k_rsh", "trevisan"), "avg_launch_ms": per_launch,
+            "gf2_bit_macs_per_launch": macs}
+    # end to end: input and seeds from pinned host memory, output back
+    xh = torch.from_numpy(xw.view(np.int64)).pin_memory()
+    sh = torch.from_numpy(sw.view(np.int64)).pin_memory()
+    zh = torch.empty(native.words(m), dtype=torch.int64).pin_memory()
+    e2e_ms = []
+    for _ in range(max(3, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xd.copy_(xh, non_blocking=True)
+        sd.copy_(sh, non_blocking=True)
+        step()
+        zh.copy_(zd, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_mean = sum(e2e_ms) / len(e2e_ms)
+    e2e = {"value": world * m / (e2e_mean * 1e-3) / 1e9, "unit": "Gbit/s",
+           "h2d_bytes_per_step": 8 * (xw.size + sw.size), "d2h_bytes_per_step": 8 * native.words(m),
+           "ms_per_step": e2e_mean}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, done, secs = trevisan_reference_rate(xw, n, sw, l, 10.0)
+        cpu = {"value": rate / 1e9, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
+               "sample": f"{done} output bits (one-bit extractions) in {secs:.1f} s (Python integers, one thread)"}
+    if rank == 0:
+        line = {
+            "metric": "extracted output Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 (GF(2^l) words)",
+            "data": "synthetic",
+            "config": {"workload": f"Trevisan one-bit step: n = {n} Bernoulli(1/2) input bits, m = {m} RSH "
+                                   f"one-bit extractions, l = {l} (eps = {TREV_EPS}), random 2l-bit seeds",
+                       "n": n, "m": m, "l": l, "chunks": s, "modulus_taps": native.rsh_modulus(l),
+                       "l2": "input and chunks L2-resident (read by every thread)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "latency_ms": {"p50": statistics.median(step_ms), "p99": max(step_ms)},
+            "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": sampler.summary(tw0, tw1), "gpu_launches": 2 * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def served_trace(count, rate, seed_stream=3):
     """Poisson arrivals at `rate`/s; kinds Toeplitz / Circulant / Dodis et al.
     50/25/25; n = floor(2^U), U ~ U[12, 28), snapped to the next valid N_A
@@ -1072,7 +1249,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="cm", choices=["cm", "reference"])
-    ap.add_argument("--workload", default="circulant", choices=sorted(WORKLOADS) + ["batched_a", "batched_b", "served", "von_neumann"])
+    ap.add_argument("--workload", default="circulant",
+                    choices=sorted(WORKLOADS) + ["batched_a", "batched_b", "served", "von_neumann", "trevisan"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -1091,6 +1269,9 @@ def main():
         return
     if args.workload == "von_neumann":
         run_von_neumann(args, world, rank, local)
+        return
+    if args.workload == "trevisan":
+        run_trevisan(args, world, rank, local)
         return
 
     import numpy as np

@@ -1,0 +1,485 @@
+// Trevisan's extractor, one-bit step (Section "Trevisan implementation"): m
+// Reed-Solomon-Hadamard one-bit extractions of one input, one output bit per
+// GPU thread.
+//
+// GF(2^l) elements are polynomials over GF(2) modulo f (cm_rsh_modulus), held
+// "left-aligned" in W = ceil(l / 64) words: the element e is stored as
+// e x^delta, delta = 64 W - l, so that the high half of a double-length
+// product starts on a word boundary whatever l is.  With p' = p x^delta and
+// alpha1 plain, p' alpha1 = (p alpha1) x^delta: its low W words are the low
+// part of p alpha1 (aligned) and its high W words are p alpha1's coefficients
+// from x^l up.  Horner's rule p <- p alpha1 + x_i then takes per step
+//   - a carry-less product by 4-bit windows of p': each thread keeps the 16
+//     multiples v alpha1 (v < 16) in shared memory;
+//   - a reduction by 4-bit windows of the high half: a table shared by the
+//     CTA holds ((v x^(l + 4k)) mod f) x^delta for every window k and v < 16;
+//   - an XOR of the next chunk (pre-aligned by k_rsh_chunks).
+// The output bit is the parity of alpha2' AND p' (both aligned alike).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "cm_ctx.h"
+#include "cm_internal.h"
+#include "cm_trevisan.h"
+
+namespace cm {
+namespace {
+
+constexpr uint32_t kMaxL = 256;
+constexpr int kRshThreads = 128;
+
+// ---------------------------------------------------------------------------
+// Host: GF(2)[x] polynomials of degree < 64 kPolyWords, the modulus search
+// (Rabin's irreducibility test) and the reduction table.
+// ---------------------------------------------------------------------------
+constexpr int kPolyWords = 9;  // degree < 576 >= 2 * 256 + 4
+struct Poly {
+    uint64_t w[kPolyWords];
+};
+
+static Poly pzero() {
+    Poly p;
+    memset(&p, 0, sizeof(p));
+    return p;
+}
+static int pdeg(const Poly &p) {
+    for (int i = kPolyWords - 1; i >= 0; --i)
+        if (p.w[i]) return 64 * i + 63 - __builtin_clzll(p.w[i]);
+    return -1;
+}
+static bool pbit(const Poly &p, int k) { return (p.w[k >> 6] >> (k & 63)) & 1; }
+static void pset(Poly &p, int k) { p.w[k >> 6] ^= 1ull << (k & 63); }
+static Poly pshl(const Poly &p, int s) {
+    Poly r = pzero();
+    const int ws = s >> 6, bs = s & 63;
+    for (int i = kPolyWords - 1; i >= ws; --i) {
+        uint64_t v = p.w[i - ws] << bs;
+        if (bs && i - ws - 1 >= 0) v |= p.w[i - ws - 1] >> (64 - bs);
+        r.w[i] = v;
+    }
+    return r;
+}
+static void pxor(Poly &a, const Poly &b) {
+    for (int i = 0; i < kPolyWords; ++i) a.w[i] ^= b.w[i];
+}
+static Poly pmod(Poly a, const Poly &f) {
+    const int df = pdeg(f);
+    for (int d = pdeg(a); d >= df; d = pdeg(a)) pxor(a, pshl(f, d - df));
+    return a;
+}
+static Poly pmulmod(const Poly &a, const Poly &b, const Poly &f) {
+    Poly r = pzero();
+    const int db = pdeg(b);
+    for (int k = 0; k <= db; ++k)
+        if (pbit(b, k)) pxor(r, pshl(a, k));
+    return pmod(r, f);
+}
+static Poly pgcd(Poly a, Poly b) {
+    while (pdeg(b) >= 0) {
+        Poly t = pmod(a, b);
+        a = b;
+        b = t;
+    }
+    return a;
+}
+static bool pequal(const Poly &a, const Poly &b) { return memcmp(&a, &b, sizeof(Poly)) == 0; }
+
+// x^(2^k) mod f by k squarings.
+static Poly x_pow_2k(int k, const Poly &f) {
+    Poly r = pzero();
+    pset(r, 1);
+    r = pmod(r, f);
+    for (int i = 0; i < k; ++i) r = pmulmod(r, r, f);
+    return r;
+}
+
+static bool irreducible(const Poly &f) {
+    const int l = pdeg(f);
+    Poly x = pzero();
+    pset(x, 1);
+    if (!pequal(x_pow_2k(l, f), pmod(x, f))) return false;
+    int n = l;
+    for (int p = 2; p <= n; ++p) {
+        if (n % p) continue;
+        while (n % p == 0) n /= p;
+        Poly g = x_pow_2k(l / p, f);
+        pxor(g, x);
+        const Poly d = pgcd(f, pmod(g, f));
+        if (pdeg(d) != 0) return false;
+    }
+    return true;
+}
+
+struct Modulus {
+    uint32_t taps[3];
+    uint32_t count;
+};
+
+static bool find_modulus(uint32_t l, Modulus *out) {
+    static std::mutex mu;
+    static std::map<uint32_t, Modulus> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(l);
+    if (it != cache.end()) {
+        *out = it->second;
+        return true;
+    }
+    auto make = [&](std::initializer_list<uint32_t> taps) {
+        Poly f = pzero();
+        pset(f, (int)l);
+        pset(f, 0);
+        for (uint32_t t : taps) pset(f, (int)t);
+        return f;
+    };
+    Modulus m;
+    memset(&m, 0, sizeof(m));
+    bool found = false;
+    for (uint32_t k = 1; k < l && !found; ++k) {
+        if (irreducible(make({k}))) {
+            m.taps[0] = k;
+            m.count = 1;
+            found = true;
+        }
+    }
+    for (uint32_t a = 3; a < l && !found; ++a)
+        for (uint32_t b = 2; b < a && !found; ++b)
+            for (uint32_t c = 1; c < b && !found; ++c)
+                if (irreducible(make({a, b, c}))) {
+                    m.taps[0] = a;
+                    m.taps[1] = b;
+                    m.taps[2] = c;
+                    m.count = 3;
+                    found = true;
+                }
+    if (!found) return false;
+    cache[l] = m;
+    *out = m;
+    return true;
+}
+
+static Poly modulus_poly(uint32_t l, const Modulus &m) {
+    Poly f = pzero();
+    pset(f, (int)l);
+    pset(f, 0);
+    for (uint32_t i = 0; i < m.count; ++i) pset(f, (int)m.taps[i]);
+    return f;
+}
+
+// Rt[(k * 16 + v) * W + q]: word q of ((v x^(l + 4k)) mod f) x^delta, for the
+// 16 W windows k of the high half and v < 16.
+static void reduction_table(uint32_t l, const Poly &f, int W, std::vector<uint64_t> *rt) {
+    const int delta = 64 * W - (int)l;
+    rt->assign((size_t)16 * W * 16 * W, 0);
+    Poly xk = pzero();
+    pset(xk, (int)l);
+    xk = pmod(xk, f);  // x^l mod f
+    for (int k = 0; k < 16 * W; ++k) {
+        Poly m[4];
+        m[0] = xk;
+        for (int b = 1; b < 4; ++b) m[b] = pmod(pshl(m[b - 1], 1), f);
+        for (int v = 0; v < 16; ++v) {
+            Poly r = pzero();
+            for (int b = 0; b < 4; ++b)
+                if ((v >> b) & 1) pxor(r, m[b]);
+            r = pshl(r, delta);
+            for (int q = 0; q < W; ++q) (*rt)[((size_t)k * 16 + v) * W + q] = r.w[q];
+        }
+        xk = pmod(pshl(xk, 4), f);  // x^(l + 4(k + 1)) mod f
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Device
+// ---------------------------------------------------------------------------
+
+// 64 bits of a packed bit string from bit `pos` (bits at or past nbits read 0).
+__device__ __forceinline__ uint64_t bits64(const uint64_t *__restrict__ src, uint64_t nbits, uint64_t pos) {
+    if (pos >= nbits) return 0;
+    const uint64_t nw = (nbits + 63) >> 6;
+    const uint64_t w = pos >> 6;
+    const int sh = (int)(pos & 63);
+    uint64_t r = __ldg(src + w) >> sh;
+    if (sh && w + 1 < nw) r |= __ldg(src + w + 1) << (64 - sh);
+    if (nbits - pos < 64) r &= (1ull << (nbits - pos)) - 1;
+    return r;
+}
+
+// The l bits at `pos` as an aligned element: bit j of the run (the j-th listed
+// bit) is the coefficient of x^(l-1-j), times x^delta: the bit reversal of
+// the run zero-extended to 64 W bits.
+template <int W>
+__device__ __forceinline__ void aligned_element(const uint64_t *__restrict__ src, uint64_t nbits, uint64_t pos,
+                                                uint32_t l, uint64_t (&e)[W]) {
+    uint64_t raw[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        const uint32_t lo = 64u * q;
+        raw[q] = lo < l ? bits64(src, nbits, pos + lo) : 0ull;
+        if (lo < l && l - lo < 64) raw[q] &= (1ull << (l - lo)) - 1;
+    }
+#pragma unroll
+    for (int q = 0; q < W; ++q) e[q] = __brevll(raw[W - 1 - q]);
+}
+
+// Chunks x_1 .. x_s of the input, aligned: X[i * W + q].
+template <int W>
+__global__ void k_rsh_chunks(const uint64_t *__restrict__ x, uint64_t n, uint32_t l, uint64_t s,
+                             uint64_t *__restrict__ X) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t e[W];
+        aligned_element<W>(x, n, i * l, l, e);
+#pragma unroll
+        for (int q = 0; q < W; ++q) X[i * W + q] = e[q];
+    }
+}
+
+// One output bit per thread; see the file comment.
+template <int W>
+__global__ void __launch_bounds__(kRshThreads)
+k_rsh(const uint64_t *__restrict__ X, uint64_t s, const uint64_t *__restrict__ seeds, uint32_t l, uint64_t m,
+      const uint64_t *__restrict__ Rt_g, uint32_t *__restrict__ z32) {
+    constexpr int WT = W + 1;   // a multiple v alpha1 (v < 16) may reach x^(l + 3)
+    constexpr int NWIN = 16 * W;
+    extern __shared__ __align__(16) uint64_t sm[];
+    uint64_t *Rt = sm;                                // NWIN * 16 * W
+    uint64_t *T = sm + (size_t)NWIN * 16 * W;         // [v][word][thread]
+    const int tid = threadIdx.x;
+    for (int i = tid; i < NWIN * 16 * W; i += kRshThreads) Rt[i] = __ldg(Rt_g + i);
+
+    const uint64_t out = (uint64_t)blockIdx.x * kRshThreads + tid;
+    const bool active = out < m;
+    const int delta = 64 * W - (int)l;
+    uint64_t a2[W], pa[W];
+    if (active) {
+        const uint64_t nb = 2ull * l * m;
+        uint64_t a1[W];
+        aligned_element<W>(seeds, nb, 2ull * l * out, l, a1);
+        aligned_element<W>(seeds, nb, 2ull * l * out + l, l, a2);
+        // alpha1 itself (not aligned): shift right by delta
+        uint64_t al[WT];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            uint64_t v = delta ? (a1[q] >> delta) : a1[q];
+            if (delta && q + 1 < W) v |= a1[q + 1] << (64 - delta);
+            al[q] = v;
+        }
+        al[W] = 0;
+        // T[v] = v alpha1, v < 16
+        uint64_t t2[WT], t4[WT], t8[WT];
+#pragma unroll
+        for (int q = 0; q < WT; ++q) {
+            t2[q] = (al[q] << 1) | (q ? al[q - 1] >> 63 : 0);
+            t4[q] = (al[q] << 2) | (q ? al[q - 1] >> 62 : 0);
+            t8[q] = (al[q] << 3) | (q ? al[q - 1] >> 61 : 0);
+        }
+#pragma unroll
+        for (int v = 0; v < 16; ++v) {
+#pragma unroll
+            for (int q = 0; q < WT; ++q) {
+                uint64_t e = 0;
+                if (v & 1) e ^= al[q];
+                if (v & 2) e ^= t2[q];
+                if (v & 4) e ^= t4[q];
+                if (v & 8) e ^= t8[q];
+                T[((size_t)v * WT + q) * kRshThreads + tid] = e;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < W; ++q) pa[q] = __ldg(X + q);
+    }
+    __syncthreads();
+    uint32_t zbit = 0;
+    if (active) {
+        for (uint64_t i = 1; i < s; ++i) {
+            uint64_t prod[2 * W + 1];
+#pragma unroll
+            for (int q = 0; q < 2 * W + 1; ++q) prod[q] = 0;
+            // carry-less product p' alpha1 by 4-bit windows of p'
+#pragma unroll
+            for (int k = 0; k < NWIN; ++k) {
+                const int o = k >> 4, sh = (k & 15) * 4;
+                const uint32_t nib = (uint32_t)(pa[o] >> sh) & 15u;
+#pragma unroll
+                for (int q = 0; q < WT; ++q) {
+                    const uint64_t t = T[((size_t)nib * WT + q) * kRshThreads + tid];
+                    prod[o + q] ^= t << sh;
+                    if (sh) prod[o + q + 1] ^= t >> (64 - sh);
+                }
+            }
+            // reduce the high half (coefficients from x^l up) by 4-bit windows
+            uint64_t r[W];
+#pragma unroll
+            for (int q = 0; q < W; ++q) r[q] = prod[q];
+#pragma unroll
+            for (int k = 0; k < NWIN; ++k) {
+                const uint32_t nib = (uint32_t)(prod[W + (k >> 4)] >> ((k & 15) * 4)) & 15u;
+#pragma unroll
+                for (int q = 0; q < W; ++q) r[q] ^= Rt[((size_t)k * 16 + nib) * W + q];
+            }
+#pragma unroll
+            for (int q = 0; q < W; ++q) pa[q] = r[q] ^ __ldg(X + i * W + q);
+        }
+        uint32_t par = 0;
+#pragma unroll
+        for (int q = 0; q < W; ++q) par ^= __popcll(a2[q] & pa[q]) & 1u;
+        zbit = par;
+    }
+    const uint32_t word = __ballot_sync(0xffffffffu, zbit);
+    if ((tid & 31) == 0) z32[out >> 5] = word;
+}
+
+// One-bit seeds from the weak design's sets: bit j < 2l of seed i is
+// y[sets[i * t + j]] (an index at or past d reads 0); seeds (zeroed first)
+// receive 2 l m bits.
+__global__ void k_gather_seeds(const uint64_t *__restrict__ y, uint64_t d, const uint32_t *__restrict__ sets,
+                               uint32_t t, uint32_t l, uint64_t m, uint64_t *__restrict__ seeds) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint64_t base = 2ull * l * i;
+    uint64_t acc = 0;
+    int have = 0;
+    uint64_t wpos = base >> 6;
+    int off = (int)(base & 63);
+    for (uint32_t j = 0; j < 2 * l; ++j) {
+        const uint32_t idx = __ldg(sets + i * t + j);
+        const uint64_t b = idx < d ? (__ldg(y + (idx >> 6)) >> (idx & 63)) & 1ull : 0ull;
+        acc |= b << (off + have);
+        if (++have + off == 64) {
+            atomicOr(reinterpret_cast<unsigned long long *>(seeds + wpos), (unsigned long long)acc);
+            acc = 0;
+            have = 0;
+            off = 0;
+            ++wpos;
+        }
+    }
+    if (have) atomicOr(reinterpret_cast<unsigned long long *>(seeds + wpos), (unsigned long long)acc);
+}
+
+template <int W>
+static cudaError_t launch_rsh_w(const uint64_t *x, uint64_t n, uint32_t l, const uint64_t *seeds, uint64_t m,
+                                uint64_t *z, uint64_t *X, const uint64_t *Rt, int nsm, cudaStream_t st) {
+    const uint64_t s = (n + l - 1) / l;
+    uint64_t cb = (s + 255) / 256;
+    if (cb > (uint64_t)nsm * 8) cb = (uint64_t)nsm * 8;
+    k_rsh_chunks<W><<<(unsigned)cb, 256, 0, st>>>(x, n, l, s, X);
+    const size_t smem = ((size_t)16 * W * 16 * W + (size_t)16 * (W + 1) * kRshThreads) * sizeof(uint64_t);
+    cudaError_t e = cudaFuncSetAttribute(k_rsh<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t m64 = (m + 63) / 64 * 64;  // every output word written, tail bits 0
+    const uint64_t grid = (m64 + kRshThreads - 1) / kRshThreads;
+    k_rsh<W><<<(unsigned)grid, kRshThreads, smem, st>>>(X, s, seeds, l, m, Rt, reinterpret_cast<uint32_t *>(z));
+    return cudaGetLastError();
+}
+
+static uint64_t rsh_scratch(uint64_t n, uint32_t l) {
+    const int W = (int)((l + 63) / 64);
+    const uint64_t s = (n + l - 1) / l;
+    const uint64_t xb = (8ull * W * s + 255) & ~255ull;
+    return xb + 8ull * 16 * W * 16 * W;
+}
+
+static cm_status cuda_st(cudaError_t e) {
+    if (e == cudaSuccess) return CM_OK;
+    if (e == cudaErrorMemoryAllocation) return CM_ENOMEM;
+    return CM_EDEVICE;
+}
+
+// Enqueue the RSH extractions; scratch holds rsh_scratch(n, l) bytes.
+static cm_status enqueue_rsh(cm_ctx *ctx, const uint64_t *x, uint64_t n, uint32_t l, const uint64_t *seeds,
+                             uint64_t m, uint64_t *z, uint8_t *scratch, cudaStream_t st) {
+    Modulus md;
+    if (!find_modulus(l, &md)) return CM_EINVAL;
+    const int W = (int)((l + 63) / 64);
+    std::vector<uint64_t> rt;
+    reduction_table(l, modulus_poly(l, md), W, &rt);
+    const uint64_t s = (n + l - 1) / l;
+    uint64_t *X = reinterpret_cast<uint64_t *>(scratch);
+    uint64_t *Rt = reinterpret_cast<uint64_t *>(scratch + ((8ull * W * s + 255) & ~255ull));
+    cudaError_t e = cudaMemcpyAsync(Rt, rt.data(), rt.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_st(e);
+    e = cudaStreamSynchronize(st);  // the host table goes out of scope
+    if (e != cudaSuccess) return cuda_st(e);
+    ProfScope ps(ctx, "k_rsh", st);
+    switch (W) {
+        case 1: e = launch_rsh_w<1>(x, n, l, seeds, m, z, X, Rt, ctx->nsm, st); break;
+        case 2: e = launch_rsh_w<2>(x, n, l, seeds, m, z, X, Rt, ctx->nsm, st); break;
+        case 3: e = launch_rsh_w<3>(x, n, l, seeds, m, z, X, Rt, ctx->nsm, st); break;
+        default: e = launch_rsh_w<4>(x, n, l, seeds, m, z, X, Rt, ctx->nsm, st); break;
+    }
+    return cuda_st(e);
+}
+
+static bool rsh_args_ok(const void *x, uint64_t n, uint32_t l, const void *seeds, uint64_t m, const void *z) {
+    return x && seeds && z && n >= 1 && n <= (1ull << 40) && l >= 2 && l <= kMaxL && m >= 1 &&
+           m <= (1ull << 32);
+}
+
+}  // namespace
+}  // namespace cm
+
+using namespace cm;
+
+extern "C" uint32_t cm_rsh_field_bits(uint64_t n, double eps1) {
+    if (n == 0 || !(eps1 > 0.0) || !(eps1 < 1.0)) return 0;
+    return (uint32_t)ceil(log2((double)n) + 2.0 * log2(2.0 / eps1));
+}
+
+extern "C" cm_status cm_rsh_modulus(uint32_t l, uint32_t taps[3], uint32_t *count) {
+    if (!taps || !count || l < 2 || l > kMaxL) return CM_EINVAL;
+    Modulus m;
+    if (!find_modulus(l, &m)) return CM_EINVAL;
+    memcpy(taps, m.taps, sizeof(m.taps));
+    *count = m.count;
+    return CM_OK;
+}
+
+extern "C" cm_status cm_trevisan_rsh(cm_ctx *ctx, const uint64_t *x, uint64_t n, uint32_t l, const uint64_t *seeds,
+                                     uint64_t m, uint64_t *z, cm_stream stream) {
+    if (!ctx || !rsh_args_ok(x, n, l, seeds, m, z)) return CM_EINVAL;
+    const uint64_t need = rsh_scratch(n, l);
+    if (need > ctx->budget) return CM_ENOMEM;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return CM_EDEVICE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *sc = nullptr;
+    if (cudaMallocFromPoolAsync(&sc, need, ctx->pool, st) != cudaSuccess) {
+        cudaGetLastError();
+        return CM_ENOMEM;
+    }
+    cm_status s = enqueue_rsh(ctx, x, n, l, seeds, m, z, static_cast<uint8_t *>(sc), st);
+    if (cudaFreeAsync(sc, st) != cudaSuccess && s == CM_OK) s = CM_EDEVICE;
+    return s;
+}
+
+extern "C" cm_status cm_trevisan(cm_ctx *ctx, const uint64_t *x, uint64_t n, const uint64_t *y, uint64_t d,
+                                 const uint32_t *sets, uint32_t t, uint64_t m, uint32_t l, uint64_t *z,
+                                 cm_stream stream) {
+    if (!ctx || !y || !sets || d == 0 || !rsh_args_ok(x, n, l, sets, m, z) || t < 2 * l) return CM_EINVAL;
+    const uint64_t sb = (2ull * l * m + 63) / 64 * 8;
+    const uint64_t soff = (rsh_scratch(n, l) + 255) & ~255ull;
+    const uint64_t need = soff + sb;
+    if (need > ctx->budget) return CM_ENOMEM;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return CM_EDEVICE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *sc = nullptr;
+    if (cudaMallocFromPoolAsync(&sc, need, ctx->pool, st) != cudaSuccess) {
+        cudaGetLastError();
+        return CM_ENOMEM;
+    }
+    uint8_t *b = static_cast<uint8_t *>(sc);
+    uint64_t *seeds = reinterpret_cast<uint64_t *>(b + soff);
+    cm_status s = cuda_st(cudaMemsetAsync(seeds, 0, sb, st));
+    if (s == CM_OK) {
+        ProfScope ps(ctx, "k_gather_seeds", st);
+        k_gather_seeds<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(y, d, sets, t, l, m, seeds);
+        s = cuda_st(cudaGetLastError());
+    }
+    if (s == CM_OK) s = enqueue_rsh(ctx, x, n, l, seeds, m, z, b, st);
+    if (cudaFreeAsync(sc, st) != cudaSuccess && s == CM_OK) s = CM_EDEVICE;
+    return s;
+}

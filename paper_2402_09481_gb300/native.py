@@ -64,6 +64,12 @@ PROTOTYPES = {
     "cm_block_count": (_U64, [_I, _U64, _U64, _U32]),
     "cm_plan_query": (_I, [_I, _U64, _U64, ctypes.c_void_p, ctypes.c_void_p]),
     "cm_modmul_rate": (_I, [_I, _U32, ctypes.POINTER(ctypes.c_double)]),
+    "cm_rsh_field_bits": (_U32, [_U64, ctypes.c_double]),
+    "cm_rsh_modulus": (_I, [_U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
+    "cm_trevisan_rsh": (_I, [ctypes.c_void_p, ctypes.c_void_p, _U64, _U32, ctypes.c_void_p, _U64, ctypes.c_void_p,
+                             ctypes.c_void_p]),
+    "cm_trevisan": (_I, [ctypes.c_void_p, ctypes.c_void_p, _U64, ctypes.c_void_p, _U64, ctypes.c_void_p, _U32,
+                         _U64, _U32, ctypes.c_void_p, ctypes.c_void_p]),
     "cm_plan_products": (_I, [_I, _U64, _U64, ctypes.c_void_p, ctypes.c_void_p, _U64, ctypes.POINTER(_U64)]),
     "cm_output_length": (_I, [_I, _I, _I, _U64, _U64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                               ctypes.POINTER(ctypes.c_int64)]),
@@ -245,6 +251,19 @@ def launch_count(kind: int, n: int, m: int) -> int:
     return int(lib().cm_launch_count(kind, n, m))
 
 
+def rsh_field_bits(n: int, eps1: float) -> int:
+    """l = ceil(log2 n + 2 log2(2 / eps1)) of the RSH one-bit extractor."""
+    return int(lib().cm_rsh_field_bits(n, eps1))
+
+
+def rsh_modulus(l: int) -> list[int]:
+    """Middle exponents of the GF(2^l) modulus: [k] (trinomial) or [a, b, c]."""
+    taps = (_U32 * 3)()
+    cnt = _U32()
+    _check(lib().cm_rsh_modulus(l, taps, ctypes.byref(cnt)), "cm_rsh_modulus")
+    return [int(taps[i]) for i in range(cnt.value)]
+
+
 def modmul_rate(device: int = 0, field: int = FIELD_Q30) -> float:
     """Measured modular products per second of the field's multiply (cm_modmul_rate)."""
     r = ctypes.c_double()
@@ -402,6 +421,26 @@ class Context:
         pm = _dev_words(m_out, 64, "m_out")
         _check(self._L.cm_von_neumann(self._h, px, n, pz, pm, _stream_handle(stream)), "cm_von_neumann")
         return z, m_out
+
+    def trevisan_rsh(self, x, n: int, l: int, seeds, m: int, z=None, stream=None):
+        """m RSH one-bit extractions of x; one-bit seed i = bits 2 l i .. 2 l i + 2l - 1 of seeds."""
+        _dev_words(x, n, "x")
+        _dev_words(seeds, 2 * l * m, "seeds")
+        z = self._out(z, m, x)
+        _check(self._L.cm_trevisan_rsh(self._h, x.data_ptr(), n, l, seeds.data_ptr(), m, z.data_ptr(),
+                                       _stream_handle(stream)), "cm_trevisan_rsh")
+        return z
+
+    def trevisan(self, x, n: int, y, d: int, sets, t: int, m: int, l: int, z=None, stream=None):
+        """Trevisan(x, y) over the weak design's sets (m x t uint32 / int32 device array)."""
+        _dev_words(x, n, "x")
+        _dev_words(y, d, "y")
+        if sets.device.type != "cuda" or sets.numel() < m * t or sets.element_size() != 4:
+            raise ValueError("sets: a CUDA tensor of m * t 32-bit indices")
+        z = self._out(z, m, x)
+        _check(self._L.cm_trevisan(self._h, x.data_ptr(), n, y.data_ptr(), d, sets.data_ptr(), t, m, l,
+                                   z.data_ptr(), _stream_handle(stream)), "cm_trevisan")
+        return z
 
     def von_neumann_host(self, x, n: int, z, stream=None) -> tuple[int, int]:
         """End-to-end Von Neumann on host tensors; returns (cm_status, m)."""
