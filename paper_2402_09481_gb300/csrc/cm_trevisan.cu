@@ -239,18 +239,66 @@ __global__ void k_rsh_chunks(const uint64_t *__restrict__ x, uint64_t n, uint32_
     }
 }
 
-// One output bit per thread; see the file comment.
+// out = in << s (s < 64 NO), words past NO dropped.  s is the same in every
+// thread: a bit shift, then word shifts by the binary digits of s / 64 under
+// uniform branches, so that every register index is a constant.
+template <int NI, int NO>
+__device__ __forceinline__ void shl_words(const uint64_t (&in)[NI], uint32_t s, uint64_t (&out)[NO]) {
+    const int bs = (int)(s & 63);
+    const uint32_t ws = s >> 6;
+#pragma unroll
+    for (int q = 0; q < NO; ++q) {
+        const uint64_t cur = q < NI ? in[q] : 0ull;
+        const uint64_t prev = (q >= 1 && q - 1 < NI) ? in[q - 1] : 0ull;
+        out[q] = (cur << bs) | (bs ? prev >> (64 - bs) : 0ull);
+    }
+#pragma unroll
+    for (int b = 1; b < NO; b <<= 1) {
+        if (ws & (uint32_t)b) {
+#pragma unroll
+            for (int q = NO - 1; q >= 0; --q) out[q] = q >= b ? out[q - b] : 0ull;
+        }
+    }
+}
+
+// h (a polynomial of W words) times g = x^l mod f = 1 + x^t1 [+ x^t2 + x^t3],
+// into 2W words.
 template <int W>
+__device__ __forceinline__ void times_g(const uint64_t (&h)[W], const uint32_t (&taps)[3], int ntaps,
+                                        uint64_t (&q)[2 * W]) {
+#pragma unroll
+    for (int i = 0; i < 2 * W; ++i) q[i] = i < W ? h[i] : 0ull;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (k < ntaps) {
+            uint64_t sh[2 * W];
+            shl_words<W, 2 * W>(h, taps[k], sh);
+#pragma unroll
+            for (int i = 0; i < 2 * W; ++i) q[i] ^= sh[i];
+        }
+    }
+}
+
+// One output bit per thread; see the file comment.  WIDE: l + 3 > 64 W, so
+// that a multiple v alpha1 (v < 16, degree < l + 3) needs one more word.
+// SPARSE: the reduction multiplies the high half by x^l mod f = 1 + (one or
+// three taps) with shifts, twice (every tap at most (l + 1) / 2, so the second
+// round's high part vanishes); otherwise it reads the CTA-shared window table.
+template <int W, bool WIDE, bool SPARSE>
 __global__ void __launch_bounds__(kRshThreads)
 k_rsh(const uint64_t *__restrict__ X, uint64_t s, const uint64_t *__restrict__ seeds, uint32_t l, uint64_t m,
-      const uint64_t *__restrict__ Rt_g, uint32_t *__restrict__ z32) {
-    constexpr int WT = W + 1;   // a multiple v alpha1 (v < 16) may reach x^(l + 3)
+      const uint64_t *__restrict__ Rt_g, uint32_t t1, uint32_t t2, uint32_t t3, int ntaps,
+      uint32_t *__restrict__ z32) {
+    constexpr int WT = WIDE ? W + 1 : W;
     constexpr int NWIN = 16 * W;
+    constexpr int NRT = SPARSE ? 0 : NWIN * 16 * W;
     extern __shared__ __align__(16) uint64_t sm[];
-    uint64_t *Rt = sm;                                // NWIN * 16 * W
-    uint64_t *T = sm + (size_t)NWIN * 16 * W;         // [v][word][thread]
+    uint64_t *Rt = sm;                                // NRT
+    uint64_t *T = sm + NRT;                           // [v][word][thread]
     const int tid = threadIdx.x;
-    for (int i = tid; i < NWIN * 16 * W; i += kRshThreads) Rt[i] = __ldg(Rt_g + i);
+    for (int i = tid; i < NRT; i += kRshThreads) Rt[i] = __ldg(Rt_g + i);
+    const uint32_t taps[3] = {t1, t2, t3};
+    const uint32_t wl = l >> 6, bl = l & 63;  // x^l at word wl, bit bl
 
     const uint64_t out = (uint64_t)blockIdx.x * kRshThreads + tid;
     const bool active = out < m;
@@ -269,7 +317,7 @@ k_rsh(const uint64_t *__restrict__ X, uint64_t s, const uint64_t *__restrict__ s
             if (delta && q + 1 < W) v |= a1[q + 1] << (64 - delta);
             al[q] = v;
         }
-        al[W] = 0;
+        if (WIDE) al[WT - 1] = 0;
         // T[v] = v alpha1, v < 16
         uint64_t t2[WT], t4[WT], t8[WT];
 #pragma unroll
@@ -309,18 +357,42 @@ k_rsh(const uint64_t *__restrict__ X, uint64_t s, const uint64_t *__restrict__ s
                 for (int q = 0; q < WT; ++q) {
                     const uint64_t t = T[((size_t)nib * WT + q) * kRshThreads + tid];
                     prod[o + q] ^= t << sh;
-                    if (sh) prod[o + q + 1] ^= t >> (64 - sh);
+                    if (sh && o + q + 1 < 2 * W + 1) prod[o + q + 1] ^= t >> (64 - sh);
                 }
             }
-            // reduce the high half (coefficients from x^l up) by 4-bit windows
             uint64_t r[W];
 #pragma unroll
             for (int q = 0; q < W; ++q) r[q] = prod[q];
+            if (SPARSE) {
+                // h = coefficients from x^l up (unaligned); h g = lo + x^l h2;
+                // h2 g has degree < l; add (lo + h2 g) x^delta to the low half
+                uint64_t h[W], qg[2 * W], h2[W], r2[2 * W], u[W];
 #pragma unroll
-            for (int k = 0; k < NWIN; ++k) {
-                const uint32_t nib = (uint32_t)(prod[W + (k >> 4)] >> ((k & 15) * 4)) & 15u;
+                for (int q = 0; q < W; ++q) h[q] = prod[W + q];
+                times_g<W>(h, taps, ntaps, qg);
 #pragma unroll
-                for (int q = 0; q < W; ++q) r[q] ^= Rt[((size_t)k * 16 + nib) * W + q];
+                for (int q = 0; q < W; ++q) {  // h2 = qg >> l, lo = qg mod x^l
+                    const uint64_t a0 = (wl == (uint32_t)(W - 1)) ? qg[q + W - 1] : qg[q + W];
+                    const uint64_t a1 = (wl == (uint32_t)(W - 1)) ? qg[q + W] : (q + W + 1 < 2 * W ? qg[q + W + 1] : 0ull);
+                    h2[q] = bl ? (a0 >> bl) | (a1 << (64 - bl)) : a0;
+                    const uint64_t lo = q < (int)wl ? qg[q] : (q == (int)wl && bl ? qg[q] & ((1ull << bl) - 1) : 0ull);
+                    u[q] = lo;
+                }
+                times_g<W>(h2, taps, ntaps, r2);
+#pragma unroll
+                for (int q = 0; q < W; ++q) u[q] ^= r2[q];
+                // align: u x^delta (delta < 64)
+#pragma unroll
+                for (int q = 0; q < W; ++q)
+                    r[q] ^= delta ? (u[q] << delta) | (q ? u[q - 1] >> (64 - delta) : 0ull) : u[q];
+            } else {
+                // reduce the high half (coefficients from x^l up) by 4-bit windows
+#pragma unroll
+                for (int k = 0; k < NWIN; ++k) {
+                    const uint32_t nib = (uint32_t)(prod[W + (k >> 4)] >> ((k & 15) * 4)) & 15u;
+#pragma unroll
+                    for (int q = 0; q < W; ++q) r[q] ^= Rt[((size_t)k * 16 + nib) * W + q];
+                }
             }
 #pragma unroll
             for (int q = 0; q < W; ++q) pa[q] = r[q] ^ __ldg(X + i * W + q);
@@ -361,20 +433,43 @@ __global__ void k_gather_seeds(const uint64_t *__restrict__ y, uint64_t d, const
     if (have) atomicOr(reinterpret_cast<unsigned long long *>(seeds + wpos), (unsigned long long)acc);
 }
 
+template <int W, bool WIDE, bool SPARSE>
+static cudaError_t launch_rsh_kernel(const uint64_t *X, uint64_t s, const uint64_t *seeds, uint32_t l, uint64_t m,
+                                     uint64_t *z, const uint64_t *Rt, const Modulus &md, cudaStream_t st) {
+    constexpr int WT = WIDE ? W + 1 : W;
+    const size_t nrt = SPARSE ? 0 : (size_t)16 * W * 16 * W;
+    const size_t smem = (nrt + (size_t)16 * WT * kRshThreads) * sizeof(uint64_t);
+    auto kern = k_rsh<W, WIDE, SPARSE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t m64 = (m + 63) / 64 * 64;  // every output word written, tail bits 0
+    const uint64_t grid = (m64 + kRshThreads - 1) / kRshThreads;
+    kern<<<(unsigned)grid, kRshThreads, smem, st>>>(X, s, seeds, l, m, Rt, md.taps[0], md.taps[1], md.taps[2],
+                                                    (int)md.count, reinterpret_cast<uint32_t *>(z));
+    return cudaGetLastError();
+}
+
+// The shift reduction needs 2 t_max - 2 < l (true of every modulus up to 256).
+static bool sparse_ok(uint32_t l, const Modulus &md) {
+    uint32_t t = 0;
+    for (uint32_t i = 0; i < md.count; ++i) t = md.taps[i] > t ? md.taps[i] : t;
+    return 2 * t < l + 2;
+}
+
 template <int W>
 static cudaError_t launch_rsh_w(const uint64_t *x, uint64_t n, uint32_t l, const uint64_t *seeds, uint64_t m,
-                                uint64_t *z, uint64_t *X, const uint64_t *Rt, int nsm, cudaStream_t st) {
+                                uint64_t *z, uint64_t *X, const uint64_t *Rt, const Modulus &md, int nsm,
+                                cudaStream_t st) {
     const uint64_t s = (n + l - 1) / l;
     uint64_t cb = (s + 255) / 256;
     if (cb > (uint64_t)nsm * 8) cb = (uint64_t)nsm * 8;
     k_rsh_chunks<W><<<(unsigned)cb, 256, 0, st>>>(x, n, l, s, X);
-    const size_t smem = ((size_t)16 * W * 16 * W + (size_t)16 * (W + 1) * kRshThreads) * sizeof(uint64_t);
-    cudaError_t e = cudaFuncSetAttribute(k_rsh<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const uint64_t m64 = (m + 63) / 64 * 64;  // every output word written, tail bits 0
-    const uint64_t grid = (m64 + kRshThreads - 1) / kRshThreads;
-    k_rsh<W><<<(unsigned)grid, kRshThreads, smem, st>>>(X, s, seeds, l, m, Rt, reinterpret_cast<uint32_t *>(z));
-    return cudaGetLastError();
+    const bool wide = l + 3 > 64u * W;
+    if (sparse_ok(l, md))
+        return wide ? launch_rsh_kernel<W, true, true>(X, s, seeds, l, m, z, Rt, md, st)
+                    : launch_rsh_kernel<W, false, true>(X, s, seeds, l, m, z, Rt, md, st);
+    return wide ? launch_rsh_kernel<W, true, false>(X, s, seeds, l, m, z, Rt, md, st)
+                : launch_rsh_kernel<W, false, false>(X, s, seeds, l, m, z, Rt, md, st);
 }
 
 static uint64_t rsh_scratch(uint64_t n, uint32_t l) {
@@ -407,10 +502,10 @@ static cm_status enqueue_rsh(cm_ctx *ctx, const uint64_t *x, uint64_t n, uint32_
     if (e != cudaSuccess) return cuda_st(e);
     ProfScope ps(ctx, "k_rsh", st);
     switch (W) {
-        case 1: e = launch_rsh_w<1>(x, n, l, seeds, m, z, X, Rt, ctx->nsm, st); break;
-        case 2: e = launch_rsh_w<2>(x, n, l, seeds, m, z, X, Rt, ctx->nsm, st); break;
-        case 3: e = launch_rsh_w<3>(x, n, l, seeds, m, z, X, Rt, ctx->nsm, st); break;
-        default: e = launch_rsh_w<4>(x, n, l, seeds, m, z, X, Rt, ctx->nsm, st); break;
+        case 1: e = launch_rsh_w<1>(x, n, l, seeds, m, z, X, Rt, md, ctx->nsm, st); break;
+        case 2: e = launch_rsh_w<2>(x, n, l, seeds, m, z, X, Rt, md, ctx->nsm, st); break;
+        case 3: e = launch_rsh_w<3>(x, n, l, seeds, m, z, X, Rt, md, ctx->nsm, st); break;
+        default: e = launch_rsh_w<4>(x, n, l, seeds, m, z, X, Rt, md, ctx->nsm, st); break;
     }
     return cuda_st(e);
 }
