@@ -81,3 +81,17 @@ def test_argument_errors(cm_ctx):
     sets = torch.zeros(64, dtype=torch.int32, device="cuda")
     assert L.cm_trevisan(h, x.data_ptr(), 100, s.data_ptr(), 64, sets.data_ptr(), 15, 1, 8, x.data_ptr(),
                          None) == native.CM_EINVAL   # t < 2l
+
+
+@pytest.mark.slow
+def test_rsh_workload_size_sampled(cm_ctx):
+    # the bench workload's input (n = 2^20, l = 121) on 1024 outputs; the
+    # oracle checks outputs 0, 1, 511, 1022, 1023 (about 0.4 s each)
+    n, m, l = 1 << 20, 1024, 121
+    xw = inputs.bernoulli_half(1400, n)
+    sw = inputs.bernoulli_half(1401, 2 * l * m)
+    got = bits_of(run_rsh(cm_ctx, xw, n, l, sw, m), m)
+    xb, sb = bits_of(xw, n), bits_of(sw, 2 * l * m)
+    f = tv.rsh_modulus(l)
+    for i in (0, 1, 511, 1022, 1023):
+        assert got[i] == tv.rsh_onebit(xb, n, sb[2 * l * i: 2 * l * (i + 1)], l, f), i
