@@ -49,9 +49,9 @@ cm_status cm_rsh_modulus(uint32_t l, uint32_t taps[3], uint32_t *count);
 /* m RSH one-bit extractions of x (n bits, 1 <= n <= 2^40): output bit i
  * (z: ceil(m/64) words, written) uses the 2l-bit one-bit seed at bits
  * 2 l i .. 2 l i + 2l - 1 of `seeds` (ceil(2 l m / 64) words).  2 <= l <= 256,
- * 1 <= m <= 2^32.  Scratch: ceil(n / l) chunks of ceil(l / 64) words plus a
- * table of at most 33 KiB, from the context's pool.  CM_EINVAL for bad
- * arguments, CM_ENOMEM over the HBM budget. */
+ * 1 <= m <= 2^32.  Scratch: ceil(n / l) chunks of ceil(l / 64) words, from
+ * the context's pool.  CM_EINVAL for bad arguments, CM_ENOMEM over the HBM
+ * budget. */
 cm_status cm_trevisan_rsh(cm_ctx *ctx, const uint64_t *x, uint64_t n, uint32_t l, const uint64_t *seeds,
                           uint64_t m, uint64_t *z, cm_stream stream);
 

@@ -11,8 +11,9 @@
 // from x^l up.  Horner's rule p <- p alpha1 + x_i then takes per step
 //   - a carry-less product by 4-bit windows of p': each thread keeps the 16
 //     multiples v alpha1 (v < 16) in shared memory;
-//   - a reduction by 4-bit windows of the high half: a table shared by the
-//     CTA holds ((v x^(l + 4k)) mod f) x^delta for every window k and v < 16;
+//   - a reduction of the high half h by x^l mod f = 1 + x^t (one or three
+//     taps t) with shifts: h g = lo + x^l h2, and h2 g has degree below l,
+//     since every tap of the moduli up to l = 256 is at most (l + 1) / 2;
 //   - an XOR of the next chunk (pre-aligned by k_rsh_chunks).
 // The output bit is the parity of alpha2' AND p' (both aligned alike).
 #include <cuda_runtime.h>
@@ -22,7 +23,6 @@
 
 #include <map>
 #include <mutex>
-#include <vector>
 
 #include "cm_ctx.h"
 #include "cm_internal.h"
@@ -35,8 +35,8 @@ constexpr uint32_t kMaxL = 256;
 constexpr int kRshThreads = 128;
 
 // ---------------------------------------------------------------------------
-// Host: GF(2)[x] polynomials of degree < 64 kPolyWords, the modulus search
-// (Rabin's irreducibility test) and the reduction table.
+// Host: GF(2)[x] polynomials of degree < 64 kPolyWords and the modulus search
+// (Rabin's irreducibility test).
 // ---------------------------------------------------------------------------
 constexpr int kPolyWords = 9;  // degree < 576 >= 2 * 256 + 4
 struct Poly {
@@ -163,37 +163,6 @@ static bool find_modulus(uint32_t l, Modulus *out) {
     return true;
 }
 
-static Poly modulus_poly(uint32_t l, const Modulus &m) {
-    Poly f = pzero();
-    pset(f, (int)l);
-    pset(f, 0);
-    for (uint32_t i = 0; i < m.count; ++i) pset(f, (int)m.taps[i]);
-    return f;
-}
-
-// Rt[(k * 16 + v) * W + q]: word q of ((v x^(l + 4k)) mod f) x^delta, for the
-// 16 W windows k of the high half and v < 16.
-static void reduction_table(uint32_t l, const Poly &f, int W, std::vector<uint64_t> *rt) {
-    const int delta = 64 * W - (int)l;
-    rt->assign((size_t)16 * W * 16 * W, 0);
-    Poly xk = pzero();
-    pset(xk, (int)l);
-    xk = pmod(xk, f);  // x^l mod f
-    for (int k = 0; k < 16 * W; ++k) {
-        Poly m[4];
-        m[0] = xk;
-        for (int b = 1; b < 4; ++b) m[b] = pmod(pshl(m[b - 1], 1), f);
-        for (int v = 0; v < 16; ++v) {
-            Poly r = pzero();
-            for (int b = 0; b < 4; ++b)
-                if ((v >> b) & 1) pxor(r, m[b]);
-            r = pshl(r, delta);
-            for (int q = 0; q < W; ++q) (*rt)[((size_t)k * 16 + v) * W + q] = r.w[q];
-        }
-        xk = pmod(pshl(xk, 4), f);  // x^(l + 4(k + 1)) mod f
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Device
 // ---------------------------------------------------------------------------
@@ -281,22 +250,17 @@ __device__ __forceinline__ void times_g(const uint64_t (&h)[W], const uint32_t (
 
 // One output bit per thread; see the file comment.  WIDE: l + 3 > 64 W, so
 // that a multiple v alpha1 (v < 16, degree < l + 3) needs one more word.
-// SPARSE: the reduction multiplies the high half by x^l mod f = 1 + (one or
-// three taps) with shifts, twice (every tap at most (l + 1) / 2, so the second
-// round's high part vanishes); otherwise it reads the CTA-shared window table.
-template <int W, bool WIDE, bool SPARSE>
+// The reduction multiplies the high half by x^l mod f = 1 + (one or three
+// taps) with shifts, twice: every tap is at most (l + 1) / 2 (checked on the
+// host), so the second round's high part vanishes.
+template <int W, bool WIDE>
 __global__ void __launch_bounds__(kRshThreads)
 k_rsh(const uint64_t *__restrict__ X, uint64_t s, const uint64_t *__restrict__ seeds, uint32_t l, uint64_t m,
-      const uint64_t *__restrict__ Rt_g, uint32_t t1, uint32_t t2, uint32_t t3, int ntaps,
-      uint32_t *__restrict__ z32) {
+      uint32_t t1, uint32_t t2, uint32_t t3, int ntaps, uint32_t *__restrict__ z32) {
     constexpr int WT = WIDE ? W + 1 : W;
     constexpr int NWIN = 16 * W;
-    constexpr int NRT = SPARSE ? 0 : NWIN * 16 * W;
-    extern __shared__ __align__(16) uint64_t sm[];
-    uint64_t *Rt = sm;                                // NRT
-    uint64_t *T = sm + NRT;                           // [v][word][thread]
+    extern __shared__ __align__(16) uint64_t T[];   // [v][word][thread]
     const int tid = threadIdx.x;
-    for (int i = tid; i < NRT; i += kRshThreads) Rt[i] = __ldg(Rt_g + i);
     const uint32_t taps[3] = {t1, t2, t3};
     const uint32_t wl = l >> 6, bl = l & 63;  // x^l at word wl, bit bl
 
@@ -363,7 +327,7 @@ k_rsh(const uint64_t *__restrict__ X, uint64_t s, const uint64_t *__restrict__ s
             uint64_t r[W];
 #pragma unroll
             for (int q = 0; q < W; ++q) r[q] = prod[q];
-            if (SPARSE) {
+            {
                 // h = coefficients from x^l up (unaligned); h g = lo + x^l h2;
                 // h2 g has degree < l; add (lo + h2 g) x^delta to the low half
                 uint64_t h[W], qg[2 * W], h2[W], r2[2 * W], u[W];
@@ -385,14 +349,6 @@ k_rsh(const uint64_t *__restrict__ X, uint64_t s, const uint64_t *__restrict__ s
 #pragma unroll
                 for (int q = 0; q < W; ++q)
                     r[q] ^= delta ? (u[q] << delta) | (q ? u[q - 1] >> (64 - delta) : 0ull) : u[q];
-            } else {
-                // reduce the high half (coefficients from x^l up) by 4-bit windows
-#pragma unroll
-                for (int k = 0; k < NWIN; ++k) {
-                    const uint32_t nib = (uint32_t)(prod[W + (k >> 4)] >> ((k & 15) * 4)) & 15u;
-#pragma unroll
-                    for (int q = 0; q < W; ++q) r[q] ^= Rt[((size_t)k * 16 + nib) * W + q];
-                }
             }
 #pragma unroll
             for (int q = 0; q < W; ++q) pa[q] = r[q] ^ __ldg(X + i * W + q);
@@ -433,24 +389,25 @@ __global__ void k_gather_seeds(const uint64_t *__restrict__ y, uint64_t d, const
     if (have) atomicOr(reinterpret_cast<unsigned long long *>(seeds + wpos), (unsigned long long)acc);
 }
 
-template <int W, bool WIDE, bool SPARSE>
+template <int W, bool WIDE>
 static cudaError_t launch_rsh_kernel(const uint64_t *X, uint64_t s, const uint64_t *seeds, uint32_t l, uint64_t m,
-                                     uint64_t *z, const uint64_t *Rt, const Modulus &md, cudaStream_t st) {
+                                     uint64_t *z, const Modulus &md, cudaStream_t st) {
     constexpr int WT = WIDE ? W + 1 : W;
-    const size_t nrt = SPARSE ? 0 : (size_t)16 * W * 16 * W;
-    const size_t smem = (nrt + (size_t)16 * WT * kRshThreads) * sizeof(uint64_t);
-    auto kern = k_rsh<W, WIDE, SPARSE>;
+    const size_t smem = (size_t)16 * WT * kRshThreads * sizeof(uint64_t);
+    auto kern = k_rsh<W, WIDE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const uint64_t m64 = (m + 63) / 64 * 64;  // every output word written, tail bits 0
     const uint64_t grid = (m64 + kRshThreads - 1) / kRshThreads;
-    kern<<<(unsigned)grid, kRshThreads, smem, st>>>(X, s, seeds, l, m, Rt, md.taps[0], md.taps[1], md.taps[2],
+    kern<<<(unsigned)grid, kRshThreads, smem, st>>>(X, s, seeds, l, m, md.taps[0], md.taps[1], md.taps[2],
                                                     (int)md.count, reinterpret_cast<uint32_t *>(z));
     return cudaGetLastError();
 }
 
-// The shift reduction needs 2 t_max - 2 < l (true of every modulus up to 256).
-static bool sparse_ok(uint32_t l, const Modulus &md) {
+// The shift reduction needs 2 t_max - 2 < l: true of every modulus up to 256
+// (a trinomial's smallest k is at most l / 2: its reciprocal, with l - k, is
+// irreducible too; the pentanomials' taps are small).
+static bool taps_ok(uint32_t l, const Modulus &md) {
     uint32_t t = 0;
     for (uint32_t i = 0; i < md.count; ++i) t = md.taps[i] > t ? md.taps[i] : t;
     return 2 * t < l + 2;
@@ -458,25 +415,19 @@ static bool sparse_ok(uint32_t l, const Modulus &md) {
 
 template <int W>
 static cudaError_t launch_rsh_w(const uint64_t *x, uint64_t n, uint32_t l, const uint64_t *seeds, uint64_t m,
-                                uint64_t *z, uint64_t *X, const uint64_t *Rt, const Modulus &md, int nsm,
-                                cudaStream_t st) {
+                                uint64_t *z, uint64_t *X, const Modulus &md, int nsm, cudaStream_t st) {
     const uint64_t s = (n + l - 1) / l;
     uint64_t cb = (s + 255) / 256;
     if (cb > (uint64_t)nsm * 8) cb = (uint64_t)nsm * 8;
     k_rsh_chunks<W><<<(unsigned)cb, 256, 0, st>>>(x, n, l, s, X);
-    const bool wide = l + 3 > 64u * W;
-    if (sparse_ok(l, md))
-        return wide ? launch_rsh_kernel<W, true, true>(X, s, seeds, l, m, z, Rt, md, st)
-                    : launch_rsh_kernel<W, false, true>(X, s, seeds, l, m, z, Rt, md, st);
-    return wide ? launch_rsh_kernel<W, true, false>(X, s, seeds, l, m, z, Rt, md, st)
-                : launch_rsh_kernel<W, false, false>(X, s, seeds, l, m, z, Rt, md, st);
+    return l + 3 > 64u * W ? launch_rsh_kernel<W, true>(X, s, seeds, l, m, z, md, st)
+                           : launch_rsh_kernel<W, false>(X, s, seeds, l, m, z, md, st);
 }
 
 static uint64_t rsh_scratch(uint64_t n, uint32_t l) {
     const int W = (int)((l + 63) / 64);
     const uint64_t s = (n + l - 1) / l;
-    const uint64_t xb = (8ull * W * s + 255) & ~255ull;
-    return xb + 8ull * 16 * W * 16 * W;
+    return (8ull * W * s + 255) & ~255ull;
 }
 
 static cm_status cuda_st(cudaError_t e) {
@@ -489,23 +440,16 @@ static cm_status cuda_st(cudaError_t e) {
 static cm_status enqueue_rsh(cm_ctx *ctx, const uint64_t *x, uint64_t n, uint32_t l, const uint64_t *seeds,
                              uint64_t m, uint64_t *z, uint8_t *scratch, cudaStream_t st) {
     Modulus md;
-    if (!find_modulus(l, &md)) return CM_EINVAL;
+    if (!find_modulus(l, &md) || !taps_ok(l, md)) return CM_EINVAL;
     const int W = (int)((l + 63) / 64);
-    std::vector<uint64_t> rt;
-    reduction_table(l, modulus_poly(l, md), W, &rt);
-    const uint64_t s = (n + l - 1) / l;
     uint64_t *X = reinterpret_cast<uint64_t *>(scratch);
-    uint64_t *Rt = reinterpret_cast<uint64_t *>(scratch + ((8ull * W * s + 255) & ~255ull));
-    cudaError_t e = cudaMemcpyAsync(Rt, rt.data(), rt.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_st(e);
-    e = cudaStreamSynchronize(st);  // the host table goes out of scope
-    if (e != cudaSuccess) return cuda_st(e);
+    cudaError_t e;
     ProfScope ps(ctx, "k_rsh", st);
     switch (W) {
-        case 1: e = launch_rsh_w<1>(x, n, l, seeds, m, z, X, Rt, md, ctx->nsm, st); break;
-        case 2: e = launch_rsh_w<2>(x, n, l, seeds, m, z, X, Rt, md, ctx->nsm, st); break;
-        case 3: e = launch_rsh_w<3>(x, n, l, seeds, m, z, X, Rt, md, ctx->nsm, st); break;
-        default: e = launch_rsh_w<4>(x, n, l, seeds, m, z, X, Rt, md, ctx->nsm, st); break;
+        case 1: e = launch_rsh_w<1>(x, n, l, seeds, m, z, X, md, ctx->nsm, st); break;
+        case 2: e = launch_rsh_w<2>(x, n, l, seeds, m, z, X, md, ctx->nsm, st); break;
+        case 3: e = launch_rsh_w<3>(x, n, l, seeds, m, z, X, md, ctx->nsm, st); break;
+        default: e = launch_rsh_w<4>(x, n, l, seeds, m, z, X, md, ctx->nsm, st); break;
     }
     return cuda_st(e);
 }

@@ -36,3 +36,10 @@ def test_field_bits():
         assert native.rsh_field_bits(n, e) == tv.rsh_field_bits(n, e) == math.ceil(math.log2(n) + 2 * math.log2(2 / e))
     assert native.rsh_field_bits(0, 0.1) == 0 and native.rsh_field_bits(10, 0.0) == 0
     assert native.rsh_field_bits(10, 1.0) == 0
+
+
+def test_every_modulus_has_small_taps():
+    # the GPU reduction multiplies by x^l mod f with shifts in two rounds,
+    # which needs 2 t_max - 2 < l for the largest middle exponent t_max
+    for l in range(2, 257):
+        assert 2 * max(native.rsh_modulus(l)) < l + 2, l
