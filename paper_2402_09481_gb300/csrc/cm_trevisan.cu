@@ -248,118 +248,213 @@ __device__ __forceinline__ void times_g(const uint64_t (&h)[W], const uint32_t (
     }
 }
 
-// One output bit per thread; see the file comment.  WIDE: l + 3 > 64 W, so
-// that a multiple v alpha1 (v < 16, degree < l + 3) needs one more word.
-// The reduction multiplies the high half by x^l mod f = 1 + (one or three
-// taps) with shifts, twice: every tap is at most (l + 1) / 2 (checked on the
-// host), so the second round's high part vanishes.
-template <int W, bool WIDE>
+// T (this thread's column of shared memory) <- v b for v < 16, b plain.
+template <int WT>
+__device__ __forceinline__ void build_table(uint64_t *T, int tid, const uint64_t (&b)[WT]) {
+    uint64_t t2[WT], t4[WT], t8[WT];
+#pragma unroll
+    for (int q = 0; q < WT; ++q) {
+        t2[q] = (b[q] << 1) | (q ? b[q - 1] >> 63 : 0);
+        t4[q] = (b[q] << 2) | (q ? b[q - 1] >> 62 : 0);
+        t8[q] = (b[q] << 3) | (q ? b[q - 1] >> 61 : 0);
+    }
+#pragma unroll
+    for (int v = 0; v < 16; ++v) {
+#pragma unroll
+        for (int q = 0; q < WT; ++q) {
+            uint64_t e = 0;
+            if (v & 1) e ^= b[q];
+            if (v & 2) e ^= t2[q];
+            if (v & 4) e ^= t4[q];
+            if (v & 8) e ^= t8[q];
+            T[((size_t)v * WT + q) * kRshThreads + tid] = e;
+        }
+    }
+}
+
+// The plain element of an aligned one (a' >> delta), in WT words.
+template <int W, int WT>
+__device__ __forceinline__ void to_plain(const uint64_t (&a)[W], int delta, uint64_t (&p)[WT]) {
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        uint64_t v = delta ? (a[q] >> delta) : a[q];
+        if (delta && q + 1 < W) v |= a[q + 1] << (64 - delta);
+        p[q] = v;
+    }
+    if (WT > W) p[WT - 1] = 0;
+}
+
+struct RshField {
+    uint32_t tap0, tap1, tap2;  // scalars: a member array here ends up in local memory
+    int ntaps;
+    uint32_t wl, bl;  // x^l at word wl, bit bl
+    int delta;        // 64 W - l
+};
+
+// r' = a' b mod f, a' and r' aligned, b plain with its 16 multiples in T.
+template <int W, int WT>
+__device__ __forceinline__ void mul_table(const uint64_t *T, int tid, const RshField &F, const uint64_t (&a)[W],
+                                          uint64_t (&r)[W]) {
+    constexpr int NWIN = 16 * W;
+    uint64_t prod[2 * W + 1];
+#pragma unroll
+    for (int q = 0; q < 2 * W + 1; ++q) prod[q] = 0;
+    // carry-less product by 4-bit windows of a'
+#pragma unroll
+    for (int k = 0; k < NWIN; ++k) {
+        const int o = k >> 4, sh = (k & 15) * 4;
+        const uint32_t nib = (uint32_t)(a[o] >> sh) & 15u;
+#pragma unroll
+        for (int q = 0; q < WT; ++q) {
+            const uint64_t t = T[((size_t)nib * WT + q) * kRshThreads + tid];
+            prod[o + q] ^= t << sh;
+            if (sh && o + q + 1 < 2 * W + 1) prod[o + q + 1] ^= t >> (64 - sh);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < W; ++q) r[q] = prod[q];
+    // h = coefficients from x^l up (unaligned); h g = lo + x^l h2; h2 g has
+    // degree < l; add (lo + h2 g) x^delta to the low half
+    uint64_t h[W], qg[2 * W], h2[W], r2[2 * W], u[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) h[q] = prod[W + q];
+    const uint32_t taps[3] = {F.tap0, F.tap1, F.tap2};
+    times_g<W>(h, taps, F.ntaps, qg);
+#pragma unroll
+    for (int q = 0; q < W; ++q) {  // h2 = qg >> l, lo = qg mod x^l
+        const uint64_t a0 = (F.wl == (uint32_t)(W - 1)) ? qg[q + W - 1] : qg[q + W];
+        const uint64_t a1 = (F.wl == (uint32_t)(W - 1)) ? qg[q + W] : (q + W + 1 < 2 * W ? qg[q + W + 1] : 0ull);
+        h2[q] = F.bl ? (a0 >> F.bl) | (a1 << (64 - F.bl)) : a0;
+        u[q] = q < (int)F.wl ? qg[q] : (q == (int)F.wl && F.bl ? qg[q] & ((1ull << F.bl) - 1) : 0ull);
+    }
+    times_g<W>(h2, taps, F.ntaps, r2);
+#pragma unroll
+    for (int q = 0; q < W; ++q) u[q] ^= r2[q];
+#pragma unroll
+    for (int q = 0; q < W; ++q)
+        r[q] ^= F.delta ? (u[q] << F.delta) | (q ? u[q - 1] >> (64 - F.delta) : 0ull) : u[q];
+}
+
+// r' = (alpha1')^e aligned, by square-and-multiply; al = plain alpha1.  T is
+// rebuilt for every multiplicand.
+template <int W, int WT>
+__device__ __forceinline__ void pow_aligned(uint64_t *T, int tid, const RshField &F, const uint64_t (&al)[WT],
+                                            uint64_t e, uint64_t (&r)[W]) {
+#pragma unroll
+    for (int q = 0; q < W; ++q) r[q] = 0;
+    r[0] = 1ull << F.delta;  // the aligned 1 (delta < 64)
+    for (int b = 63 - __clzll(e | 1); b >= 0; --b) {
+        uint64_t p[WT], t[W];
+        to_plain<W, WT>(r, F.delta, p);
+        build_table<WT>(T, tid, p);
+        mul_table<W, WT>(T, tid, F, r, t);  // r^2
+        if ((e >> b) & 1) {
+            build_table<WT>(T, tid, al);
+            mul_table<W, WT>(T, tid, F, t, r);
+        } else {
+#pragma unroll
+            for (int q = 0; q < W; ++q) r[q] = t[q];
+        }
+    }
+    if (e == 0) {
+#pragma unroll
+        for (int q = 0; q < W; ++q) r[q] = q ? 0ull : 1ull << F.delta;
+    }
+}
+
+// G threads per output bit (G a power of two <= 32).  The s chunks, after
+// G len - s leading zero chunks (which leave p unchanged), split into G blocks
+// of len; thread g runs Horner's rule over its block (P_g) and multiplies it
+// by beta^(G-1-g), beta = alpha1^len, so that p = sum_g of those terms; the
+// output is the XOR over the group of parity(alpha2 AND term).  G = 1 is the
+// plain one-thread Horner.  WIDE: l + 3 > 64 W, so that a multiple v b
+// (v < 16, degree < l + 3) needs one more word.
+template <int W, bool WIDE, int G>
 __global__ void __launch_bounds__(kRshThreads)
 k_rsh(const uint64_t *__restrict__ X, uint64_t s, const uint64_t *__restrict__ seeds, uint32_t l, uint64_t m,
       uint32_t t1, uint32_t t2, uint32_t t3, int ntaps, uint32_t *__restrict__ z32) {
     constexpr int WT = WIDE ? W + 1 : W;
-    constexpr int NWIN = 16 * W;
     extern __shared__ __align__(16) uint64_t T[];   // [v][word][thread]
     const int tid = threadIdx.x;
-    const uint32_t taps[3] = {t1, t2, t3};
-    const uint32_t wl = l >> 6, bl = l & 63;  // x^l at word wl, bit bl
+    RshField F;
+    F.tap0 = t1;
+    F.tap1 = t2;
+    F.tap2 = t3;
+    F.ntaps = ntaps;
+    F.wl = l >> 6;
+    F.bl = l & 63;
+    F.delta = 64 * W - (int)l;
 
-    const uint64_t out = (uint64_t)blockIdx.x * kRshThreads + tid;
+    const uint64_t gt = (uint64_t)blockIdx.x * kRshThreads + tid;
+    const uint64_t out = gt / G;
+    const int g = (int)(gt % G);
     const bool active = out < m;
-    const int delta = 64 * W - (int)l;
-    uint64_t a2[W], pa[W];
-    if (active) {
-        const uint64_t nb = 2ull * l * m;
-        uint64_t a1[W];
-        aligned_element<W>(seeds, nb, 2ull * l * out, l, a1);
-        aligned_element<W>(seeds, nb, 2ull * l * out + l, l, a2);
-        // alpha1 itself (not aligned): shift right by delta
-        uint64_t al[WT];
-#pragma unroll
-        for (int q = 0; q < W; ++q) {
-            uint64_t v = delta ? (a1[q] >> delta) : a1[q];
-            if (delta && q + 1 < W) v |= a1[q + 1] << (64 - delta);
-            al[q] = v;
-        }
-        if (WIDE) al[WT - 1] = 0;
-        // T[v] = v alpha1, v < 16
-        uint64_t t2[WT], t4[WT], t8[WT];
-#pragma unroll
-        for (int q = 0; q < WT; ++q) {
-            t2[q] = (al[q] << 1) | (q ? al[q - 1] >> 63 : 0);
-            t4[q] = (al[q] << 2) | (q ? al[q - 1] >> 62 : 0);
-            t8[q] = (al[q] << 3) | (q ? al[q - 1] >> 61 : 0);
-        }
-#pragma unroll
-        for (int v = 0; v < 16; ++v) {
-#pragma unroll
-            for (int q = 0; q < WT; ++q) {
-                uint64_t e = 0;
-                if (v & 1) e ^= al[q];
-                if (v & 2) e ^= t2[q];
-                if (v & 4) e ^= t4[q];
-                if (v & 8) e ^= t8[q];
-                T[((size_t)v * WT + q) * kRshThreads + tid] = e;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < W; ++q) pa[q] = __ldg(X + q);
-    }
-    __syncthreads();
     uint32_t zbit = 0;
     if (active) {
-        for (uint64_t i = 1; i < s; ++i) {
-            uint64_t prod[2 * W + 1];
+        const uint64_t nb = 2ull * l * m;
+        uint64_t a1[W], a2[W], al[WT];
+        aligned_element<W>(seeds, nb, 2ull * l * out, l, a1);
+        aligned_element<W>(seeds, nb, 2ull * l * out + l, l, a2);
+        to_plain<W, WT>(a1, F.delta, al);
+        build_table<WT>(T, tid, al);
+        const uint64_t len = (s + G - 1) / G, pad = G * len - s;
+        const uint64_t k0 = (uint64_t)g * len, k1 = k0 + len;
+        uint64_t pa[W];
 #pragma unroll
-            for (int q = 0; q < 2 * W + 1; ++q) prod[q] = 0;
-            // carry-less product p' alpha1 by 4-bit windows of p'
-#pragma unroll
-            for (int k = 0; k < NWIN; ++k) {
-                const int o = k >> 4, sh = (k & 15) * 4;
-                const uint32_t nib = (uint32_t)(pa[o] >> sh) & 15u;
-#pragma unroll
-                for (int q = 0; q < WT; ++q) {
-                    const uint64_t t = T[((size_t)nib * WT + q) * kRshThreads + tid];
-                    prod[o + q] ^= t << sh;
-                    if (sh && o + q + 1 < 2 * W + 1) prod[o + q + 1] ^= t >> (64 - sh);
-                }
-            }
+        for (int q = 0; q < W; ++q) pa[q] = k0 >= pad ? __ldg(X + (k0 - pad) * W + q) : 0ull;
+        for (uint64_t k = k0 + 1; k < k1; ++k) {
             uint64_t r[W];
+            mul_table<W, WT>(T, tid, F, pa, r);
 #pragma unroll
-            for (int q = 0; q < W; ++q) r[q] = prod[q];
-            {
-                // h = coefficients from x^l up (unaligned); h g = lo + x^l h2;
-                // h2 g has degree < l; add (lo + h2 g) x^delta to the low half
-                uint64_t h[W], qg[2 * W], h2[W], r2[2 * W], u[W];
+            for (int q = 0; q < W; ++q) pa[q] = k >= pad ? r[q] ^ __ldg(X + (k - pad) * W + q) : r[q];
+        }
+        if (G > 1) {
+            uint64_t beta[W], gam[W], pb[WT], term[W];
+            pow_aligned<W, WT>(T, tid, F, al, len, beta);
+            to_plain<W, WT>(beta, F.delta, pb);
+            pow_aligned<W, WT>(T, tid, F, pb, (uint64_t)(G - 1 - g), gam);
+            to_plain<W, WT>(gam, F.delta, pb);
+            build_table<WT>(T, tid, pb);
+            mul_table<W, WT>(T, tid, F, pa, term);
 #pragma unroll
-                for (int q = 0; q < W; ++q) h[q] = prod[W + q];
-                times_g<W>(h, taps, ntaps, qg);
-#pragma unroll
-                for (int q = 0; q < W; ++q) {  // h2 = qg >> l, lo = qg mod x^l
-                    const uint64_t a0 = (wl == (uint32_t)(W - 1)) ? qg[q + W - 1] : qg[q + W];
-                    const uint64_t a1 = (wl == (uint32_t)(W - 1)) ? qg[q + W] : (q + W + 1 < 2 * W ? qg[q + W + 1] : 0ull);
-                    h2[q] = bl ? (a0 >> bl) | (a1 << (64 - bl)) : a0;
-                    const uint64_t lo = q < (int)wl ? qg[q] : (q == (int)wl && bl ? qg[q] & ((1ull << bl) - 1) : 0ull);
-                    u[q] = lo;
-                }
-                times_g<W>(h2, taps, ntaps, r2);
-#pragma unroll
-                for (int q = 0; q < W; ++q) u[q] ^= r2[q];
-                // align: u x^delta (delta < 64)
-#pragma unroll
-                for (int q = 0; q < W; ++q)
-                    r[q] ^= delta ? (u[q] << delta) | (q ? u[q - 1] >> (64 - delta) : 0ull) : u[q];
-            }
-#pragma unroll
-            for (int q = 0; q < W; ++q) pa[q] = r[q] ^ __ldg(X + i * W + q);
+            for (int q = 0; q < W; ++q) pa[q] = term[q];
         }
         uint32_t par = 0;
 #pragma unroll
         for (int q = 0; q < W; ++q) par ^= __popcll(a2[q] & pa[q]) & 1u;
         zbit = par;
     }
-    const uint32_t word = __ballot_sync(0xffffffffu, zbit);
-    if ((tid & 31) == 0) z32[out >> 5] = word;
+    if (G == 1) {
+        const uint32_t word = __ballot_sync(0xffffffffu, zbit);
+        if ((tid & 31) == 0) z32[out >> 5] = word;
+    } else {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) zbit ^= __shfl_xor_sync(0xffffffffu, zbit, o);
+        if (active && g == 0 && zbit) atomicOr(z32 + (out >> 5), 1u << (out & 31));
+    }
+}
+
+template <int W, bool WIDE, int G>
+static cudaError_t launch_rsh_kernel(const uint64_t *X, uint64_t s, const uint64_t *seeds, uint32_t l, uint64_t m,
+                                     uint64_t *z, const Modulus &md, cudaStream_t st) {
+    constexpr int WT = WIDE ? W + 1 : W;
+    const size_t smem = (size_t)16 * WT * kRshThreads * sizeof(uint64_t);
+    auto kern = k_rsh<W, WIDE, G>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    uint64_t threads;
+    if (G == 1) {
+        threads = (m + 63) / 64 * 64;  // every output word written by ballots, tail bits 0
+    } else {
+        // bits are ORed in: clear the output first
+        e = cudaMemsetAsync(z, 0, (m + 63) / 64 * 8, st);
+        if (e != cudaSuccess) return e;
+        threads = m * G;
+    }
+    const uint64_t grid = (threads + kRshThreads - 1) / kRshThreads;
+    kern<<<(unsigned)grid, kRshThreads, smem, st>>>(X, s, seeds, l, m, md.taps[0], md.taps[1], md.taps[2],
+                                                    (int)md.count, reinterpret_cast<uint32_t *>(z));
+    return cudaGetLastError();
 }
 
 // One-bit seeds from the weak design's sets: bit j < 2l of seed i is
@@ -389,21 +484,6 @@ __global__ void k_gather_seeds(const uint64_t *__restrict__ y, uint64_t d, const
     if (have) atomicOr(reinterpret_cast<unsigned long long *>(seeds + wpos), (unsigned long long)acc);
 }
 
-template <int W, bool WIDE>
-static cudaError_t launch_rsh_kernel(const uint64_t *X, uint64_t s, const uint64_t *seeds, uint32_t l, uint64_t m,
-                                     uint64_t *z, const Modulus &md, cudaStream_t st) {
-    constexpr int WT = WIDE ? W + 1 : W;
-    const size_t smem = (size_t)16 * WT * kRshThreads * sizeof(uint64_t);
-    auto kern = k_rsh<W, WIDE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const uint64_t m64 = (m + 63) / 64 * 64;  // every output word written, tail bits 0
-    const uint64_t grid = (m64 + kRshThreads - 1) / kRshThreads;
-    kern<<<(unsigned)grid, kRshThreads, smem, st>>>(X, s, seeds, l, m, md.taps[0], md.taps[1], md.taps[2],
-                                                    (int)md.count, reinterpret_cast<uint32_t *>(z));
-    return cudaGetLastError();
-}
-
 // The shift reduction needs 2 t_max - 2 < l: true of every modulus up to 256
 // (a trinomial's smallest k is at most l / 2: its reciprocal, with l - k, is
 // irreducible too; the pentanomials' taps are small).
@@ -413,6 +493,23 @@ static bool taps_ok(uint32_t l, const Modulus &md) {
     return 2 * t < l + 2;
 }
 
+template <int W, int G>
+static cudaError_t launch_rsh_g(const uint64_t *X, uint64_t s, const uint64_t *seeds, uint32_t l, uint64_t m,
+                                uint64_t *z, const Modulus &md, cudaStream_t st) {
+    return l + 3 > 64u * W ? launch_rsh_kernel<W, true, G>(X, s, seeds, l, m, z, md, st)
+                           : launch_rsh_kernel<W, false, G>(X, s, seeds, l, m, z, md, st);
+}
+
+// Threads per output: enough outputs-in-flight to fill the GPU (about 2048
+// threads per SM) with one thread each; fewer outputs share their chunks
+// among 8 or 32 threads (when each thread still has at least 64 chunks).
+static int rsh_group(uint64_t m, uint64_t s, int nsm) {
+    const uint64_t fill = (uint64_t)nsm * 2048;
+    if (m * 8 <= fill && s >= 64 * 32) return m * 32 <= fill ? 32 : 8;
+    if (m * 8 <= fill && s >= 64 * 8) return 8;
+    return 1;
+}
+
 template <int W>
 static cudaError_t launch_rsh_w(const uint64_t *x, uint64_t n, uint32_t l, const uint64_t *seeds, uint64_t m,
                                 uint64_t *z, uint64_t *X, const Modulus &md, int nsm, cudaStream_t st) {
@@ -420,8 +517,11 @@ static cudaError_t launch_rsh_w(const uint64_t *x, uint64_t n, uint32_t l, const
     uint64_t cb = (s + 255) / 256;
     if (cb > (uint64_t)nsm * 8) cb = (uint64_t)nsm * 8;
     k_rsh_chunks<W><<<(unsigned)cb, 256, 0, st>>>(x, n, l, s, X);
-    return l + 3 > 64u * W ? launch_rsh_kernel<W, true>(X, s, seeds, l, m, z, md, st)
-                           : launch_rsh_kernel<W, false>(X, s, seeds, l, m, z, md, st);
+    switch (rsh_group(m, s, nsm)) {
+        case 32: return launch_rsh_g<W, 32>(X, s, seeds, l, m, z, md, st);
+        case 8: return launch_rsh_g<W, 8>(X, s, seeds, l, m, z, md, st);
+        default: return launch_rsh_g<W, 1>(X, s, seeds, l, m, z, md, st);
+    }
 }
 
 static uint64_t rsh_scratch(uint64_t n, uint32_t l) {

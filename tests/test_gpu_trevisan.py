@@ -37,6 +37,9 @@ CASES = [
     (1, 3, 5), (5, 3, 64), (200, 7, 65), (1000, 17, 130), (4097, 63, 64), (3000, 64, 100),
     (3001, 65, 33), (20000, 100, 96), (9000, 128, 70), (9001, 129, 40), (6000, 200, 37), (5000, 256, 31),
     (100, 121, 10),   # n < l: one chunk
+    # few outputs: chunks shared by 8 or 32 threads per output, with leading
+    # zero chunks padding s to a multiple of the group
+    (60000, 64, 100), (200000, 30, 77), (150000, 129, 50), (300000, 256, 40),
 ]
 
 
@@ -95,3 +98,15 @@ def test_rsh_workload_size_sampled(cm_ctx):
     f = tv.rsh_modulus(l)
     for i in (0, 1, 511, 1022, 1023):
         assert got[i] == tv.rsh_onebit(xb, n, sb[2 * l * i: 2 * l * (i + 1)], l, f), i
+
+
+def test_thread_groups_agree(cm_ctx):
+    # the same seeds' outputs with one thread per output (many outputs) and
+    # with 8 or 32 threads per output (few outputs)
+    n, l = 1 << 18, 77
+    big, small = 40000, 300
+    xw = inputs.bernoulli_half(1500, n)
+    sw = inputs.bernoulli_half(1501, 2 * l * big)
+    zb = bits_of(run_rsh(cm_ctx, xw, n, l, sw, big), big)
+    zs = bits_of(run_rsh(cm_ctx, xw, n, l, sw, small), small)
+    assert (zb[:small] == zs).all()
