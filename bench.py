@@ -66,13 +66,28 @@ def seed_bits(kind, n, m):
     return n + m - 1 if kind == 0 else (n + 1 if kind == 1 else n)
 
 
-def kernel_source_hash() -> str:
+# Kernels compiled from a translation unit of their own: a capture of one of
+# them stays valid while only other units change.  Every other kernel (the
+# transforms, the tail, the batch kernels) is keyed on all remaining units.
+# Headers count for every kernel.
+OWN_UNITS = {"k_vn": "cm_vn.cu", "k_rsh": "cm_trevisan.cu", "k_ss": "cm_shared_seed.cu"}
+
+
+def kernel_source_hash(kernel: str | None = None) -> str:
+    """Hash of the sources `kernel` is built from (all of csrc when None)."""
+    own = next((u for pre, u in OWN_UNITS.items() if kernel and kernel.startswith(pre)), None)
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2402_09481_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+        if not f.endswith((".cu", ".cuh", ".h")):
+            continue
+        if kernel is not None and f.endswith(".cu"):
+            if own is not None and f != own:
+                continue
+            if own is None and f in OWN_UNITS.values():
+                continue
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -82,7 +97,7 @@ def ncu_traffic(kernel: str, workload: str):
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    src = kernel_source_hash()
+    src = kernel_source_hash(kernel)
     with open(path) as f:
         for line in f:
             p = line.split()
