@@ -1,0 +1,61 @@
+"""bench.py host logic: the per-kernel source hash that keys the committed ncu
+traffic figures, checked on a scratch copy of the kernel sources."""
+
+import os
+import shutil
+
+import bench
+
+
+def _copy_tree(tmp_path):
+    src = os.path.join(bench.ROOT, "paper_2402_09481_gb300", "csrc")
+    dst = tmp_path / "paper_2402_09481_gb300" / "csrc"
+    shutil.copytree(src, dst)
+    (tmp_path / "profiles").mkdir()
+    return dst
+
+
+def _hashes():
+    return {k: bench.kernel_source_hash(k) for k in ("k_pass", "k_middle_f30", "k_vn_write", "k_rsh", "k_ss_gf2")}
+
+
+def test_hash_follows_own_unit(tmp_path, monkeypatch):
+    csrc = _copy_tree(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    before = _hashes()
+    assert before["k_pass"] == before["k_middle_f30"]          # one family
+    assert len({before[k] for k in ("k_pass", "k_vn_write", "k_rsh", "k_ss_gf2")}) == 4
+
+    with open(csrc / "cm_trevisan.cu", "a") as f:
+        f.write("\n// edit\n")
+    after = _hashes()
+    assert after["k_rsh"] != before["k_rsh"]
+    assert all(after[k] == before[k] for k in ("k_pass", "k_vn_write", "k_ss_gf2"))
+
+    with open(csrc / "cm_api.cu", "a") as f:                  # a transform unit
+        f.write("\n// edit\n")
+    after2 = _hashes()
+    assert after2["k_pass"] != after["k_pass"]
+    assert all(after2[k] == after[k] for k in ("k_rsh", "k_vn_write", "k_ss_gf2"))
+
+    with open(csrc / "cm_internal.h", "a") as f:              # a header: every kernel
+        f.write("\n// edit\n")
+    after3 = _hashes()
+    assert all(after3[k] != after2[k] for k in after3)
+
+
+def test_traffic_only_for_matching_sources(tmp_path, monkeypatch):
+    csrc = _copy_tree(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h_rsh, h_vn = bench.kernel_source_hash("k_rsh"), bench.kernel_source_hash("k_vn_write")
+    (tmp_path / "profiles" / "ncu_traffic.txt").write_text(
+        "# kernel workload bytes hash\n"
+        f"k_rsh trevisan 1234 {h_rsh}\n"
+        f"k_vn_write von_neumann 5678 {h_vn}\n")
+    assert bench.ncu_traffic("k_rsh", "trevisan") == 1234.0
+    assert bench.ncu_traffic("k_vn_write", "von_neumann") == 5678.0
+    assert bench.ncu_traffic("k_rsh", "von_neumann") is None
+    with open(csrc / "cm_vn.cu", "a") as f:
+        f.write("\n// edit\n")
+    assert bench.ncu_traffic("k_vn_write", "von_neumann") is None
+    assert bench.ncu_traffic("k_rsh", "trevisan") == 1234.0
