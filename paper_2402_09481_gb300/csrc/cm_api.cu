@@ -647,6 +647,17 @@ static void build_tables30(std::vector<uint32_t> &h) {
         c2 = f30_mulmod(c2, gi);
         c3 = f30_mulmod(c3, gi15);
     }
+    // bits16[k * 256 + p] = sum over the set bits j of p of w^(j k), w = omega_16
+    // (the root the on-chip radix-16 DFT uses: g30^(2^26))
+    uint32_t *b16 = hi + 32768;
+    const uint32_t w16 = f30_pow(F30_G30, 1ull << 26);
+    for (int k = 0; k < 16; ++k)
+        for (int p = 0; p < 256; ++p) {
+            uint64_t acc = 0;
+            for (int j = 0; j < 8; ++j)
+                if ((p >> j) & 1) acc += f30_pow(w16, (uint64_t)((j * k) & 15));
+            b16[k * 256 + p] = (uint32_t)(acc % F30_Q);
+        }
 }
 
 }  // namespace cm
@@ -702,6 +713,7 @@ extern "C" cm_status cm_create(cm_ctx **out, int device, const cm_options *opt) 
     c->rt30.big_hi_fwd = c->rt30.big_lo_fwd + 32768;
     c->rt30.big_lo_inv = c->rt30.big_hi_fwd + 32768;
     c->rt30.big_hi_inv = c->rt30.big_lo_inv + 32768;
+    c->rt30.bits16 = c->rt30.big_hi_inv + 32768;
     cudaMemset(c->d_status, 0, 64);
     c->rt.small = c->d_tables;
     c->rt.big_lo_fwd = c->d_tables + 8192;

@@ -18,7 +18,7 @@ constexpr size_t kTableWords = 8192 + 4 * 65536;  // resident root tables
 constexpr int kFieldGL = 0;   // Goldilocks, 64-bit elements, L <= 2^32
 constexpr int kFieldF30 = 1;  // 3 * 2^30 + 1, 32-bit elements, L <= 2^30
 constexpr int kF30MaxLg = 30;
-constexpr size_t kTable30Words = 8192 + 4 * 32768;  // resident F30 root tables
+constexpr size_t kTable30Words = 8192 + 4 * 32768 + 4096;  // resident F30 root tables + bit DFT table
 
 // Arguments of the single-CTA extraction (L <= 2^13).
 struct Launch {

@@ -100,6 +100,19 @@ __device__ __forceinline__ void row_twiddle(typename F::T (&v)[VW], uint64_t k, 
     }
 }
 
+// A forward pass over input bits in the 32-bit field whose first on-chip step
+// has radix 16 takes that step's DFTs from the bit table (fwd_step_f, BITS0).
+// The table (4096 elements) follows the roots in shared memory, 16-byte aligned.
+template <class F, int LOGR, bool INV, bool BITS_IN>
+__host__ __device__ constexpr bool pass_bits_table() {
+    return !INV && BITS_IN && sizeof(typename F::T) == 4 && st_q(LOGR, 0) == 4;
+}
+template <class F, int LOGR>
+__host__ __device__ constexpr int pass_table_off() {
+    return (sp_size(1 << (LOGR + F::ncol_lg(LOGR))) + (1 << LOGR) + 3) & ~3;
+}
+constexpr int kBitsTable = 16 * 256;
+
 // ---------------------------------------------------------------------------
 // One column pass over tiles of R = 2^LOGR rows x C = 2^F::ncol_lg(LOGR) columns.
 // ---------------------------------------------------------------------------
@@ -118,6 +131,12 @@ k_pass(typename F::T *__restrict__ data1, BitMap map1, typename F::T *__restrict
     T *smem = reinterpret_cast<T *>(smem_raw);
     T *tw = smem + sp_size(R * C);
     load_roots<LOGR>(tw, rt.small);
+    constexpr bool BTAB = pass_bits_table<F, LOGR, INV, BITS_IN>();
+    T *tab = smem + pass_table_off<F, LOGR>();
+    if constexpr (BTAB) {
+        for (int i = threadIdx.x; i < kBitsTable / 4; i += kThreads)
+            reinterpret_cast<uint4 *>(tab)[i] = __ldg(reinterpret_cast<const uint4 *>(rt.bits16) + i);
+    }
     const uint64_t S = 1ull << lgS;
     const uint64_t tiles_per_blk = S >> NCOL_LG;
     const bool second = blockIdx.x >= ntiles;
@@ -156,7 +175,7 @@ k_pass(typename F::T *__restrict__ data1, BitMap map1, typename F::T *__restrict
     if (INV) {
         ntt_inv_f<F, LOGR, NCOL_LG, 1>(smem, smem, tw);
     } else {
-        ntt_fwd_f<F, LOGR, NCOL_LG, 1>(smem, smem, tw);
+        ntt_fwd_f<F, LOGR, NCOL_LG, 1, BTAB>(smem, smem, tw, tab);
     }
 #pragma unroll 4
     for (int q = threadIdx.x; q < R * C / VW; q += kThreads) {

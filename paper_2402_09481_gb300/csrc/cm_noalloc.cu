@@ -111,7 +111,7 @@ extern "C" cm_status cm_toeplitz_noalloc(const uint64_t *x, uint64_t n, const ui
     if (s != CM_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
-    RootTables rt;
+    RootTables rt{};
     rt.small = d->tables;
     rt.big_lo_fwd = d->tables + 8192;
     rt.big_hi_fwd = rt.big_lo_fwd + 65536;

@@ -39,6 +39,10 @@ struct RootTablesT {
     const T *big_hi_fwd;  // g^(2^kBigLg e),  e < 2^kBigLg
     const T *big_lo_inv;
     const T *big_hi_inv;
+    // F30 only (null for Goldilocks): the length-16 DFT of 8 input bits,
+    // bits16[k * 256 + p] = sum over the set bits j of p of omega_16^(j k),
+    // canonical, for the first forward step on 0/1 inputs (fwd_step_f).
+    const T *bits16;
 };
 using RootTables = RootTablesT<uint64_t>;
 using RootTables30 = RootTablesT<uint32_t>;
@@ -233,8 +237,16 @@ template <int LQ>
 __device__ __forceinline__ void dft_reg(uint64_t *v) { dft_reg_f<FieldGL, LQ>(v); }
 
 // Forward step J over NBUF buffers; tw[e] = omega_R^e, e < R.
-template <class F, int LOGR, int J, int NCOL_LG, int NBUF>
-__device__ __forceinline__ void fwd_step_f(typename F::T *s0, typename F::T *s1, const typename F::T *tw) {
+//
+// BITS0: every input of step 0 is 0 or 1 and step 0 has radix 16 (32-bit
+// field).  Its DFTs then come from a table instead of 32 butterflies each: for
+// input bits b_0 .. b_15, since omega_16^8 = -1,
+//   X_k = sum_i b_i omega_16^(i k) = T_k(b_0 .. b_7) + (-1)^k T_k(b_8 .. b_15),
+//   T_k(p) = tab[k * 256 + p] (RootTablesT::bits16, copied to shared memory),
+// the same canonical values the butterflies give.
+template <class F, int LOGR, int J, int NCOL_LG, int NBUF, bool BITS0 = false>
+__device__ __forceinline__ void fwd_step_f(typename F::T *s0, typename F::T *s1, const typename F::T *tw,
+                                           const typename F::T *tab = nullptr) {
     using T = typename F::T;
     constexpr int OFF = st_off(LOGR, J), LQ = st_q(LOGR, J), RD = 1 << LQ;
     constexpr int LN = LOGR - OFF, LM = LN - LQ;
@@ -248,9 +260,22 @@ __device__ __forceinline__ void fwd_step_f(typename F::T *s0, typename F::T *s1,
         const int i2 = rest & ((1 << LM) - 1);
         const int row0 = ((rest >> LM) << LN) + i2;
         T v[RD];
+        if constexpr (BITS0 && J == 0) {
+            static_assert(RD == 16 && sizeof(T) == 4, "the bit table holds radix-16 DFTs of the 32-bit field");
+            uint32_t p = 0;
 #pragma unroll
-        for (int i1 = 0; i1 < RD; ++i1) v[i1] = s[sp(((row0 + (i1 << LM)) << NCOL_LG) + c)];
-        dft_reg_f<F, LQ>(v);
+            for (int i1 = 0; i1 < RD; ++i1) p |= (uint32_t)s[sp(((row0 + (i1 << LM)) << NCOL_LG) + c)] << i1;
+            const T *tlo = tab + (p & 255u), *thi = tab + (p >> 8);
+#pragma unroll
+            for (int k = 0; k < RD; ++k) {
+                const T a = tlo[k << 8], b = thi[k << 8];
+                v[bitrev_c(k, LQ)] = (k & 1) ? F::sub(a, b) : F::add(a, b);
+            }
+        } else {
+#pragma unroll
+            for (int i1 = 0; i1 < RD; ++i1) v[i1] = s[sp(((row0 + (i1 << LM)) << NCOL_LG) + c)];
+            dft_reg_f<F, LQ>(v);
+        }
 #pragma unroll
         for (int k1 = 0; k1 < RD; ++k1) {
             T x = v[bitrev_c(k1, LQ)];
@@ -299,12 +324,13 @@ __device__ __forceinline__ void inv_step(uint64_t *s0, uint64_t *s1, const uint6
     inv_step_f<FieldGL, LOGR, J, NCOL_LG, NBUF>(s0, s1, tw);
 }
 
-template <class F, int LOGR, int J, int NCOL_LG, int NBUF>
-__device__ __forceinline__ void fwd_from(typename F::T *s0, typename F::T *s1, const typename F::T *tw) {
+template <class F, int LOGR, int J, int NCOL_LG, int NBUF, bool BITS0 = false>
+__device__ __forceinline__ void fwd_from(typename F::T *s0, typename F::T *s1, const typename F::T *tw,
+                                         const typename F::T *tab = nullptr) {
     if constexpr (J < st_n(LOGR)) {
-        fwd_step_f<F, LOGR, J, NCOL_LG, NBUF>(s0, s1, tw);
+        fwd_step_f<F, LOGR, J, NCOL_LG, NBUF, BITS0>(s0, s1, tw, tab);
         __syncthreads();
-        fwd_from<F, LOGR, J + 1, NCOL_LG, NBUF>(s0, s1, tw);
+        fwd_from<F, LOGR, J + 1, NCOL_LG, NBUF, BITS0>(s0, s1, tw, tab);
     }
 }
 template <class F, int LOGR, int J, int NCOL_LG, int NBUF>
@@ -317,9 +343,10 @@ __device__ __forceinline__ void inv_from(typename F::T *s0, typename F::T *s1, c
 }
 
 // Forward transform of every column (natural -> digit-reversed); ends with a barrier.
-template <class F, int LOGR, int NCOL_LG, int NBUF>
-__device__ __forceinline__ void ntt_fwd_f(typename F::T *s0, typename F::T *s1, const typename F::T *tw) {
-    if constexpr (LOGR > 0) fwd_from<F, LOGR, 0, NCOL_LG, NBUF>(s0, s1, tw);
+template <class F, int LOGR, int NCOL_LG, int NBUF, bool BITS0 = false>
+__device__ __forceinline__ void ntt_fwd_f(typename F::T *s0, typename F::T *s1, const typename F::T *tw,
+                                          const typename F::T *tab = nullptr) {
+    if constexpr (LOGR > 0) fwd_from<F, LOGR, 0, NCOL_LG, NBUF, BITS0>(s0, s1, tw, tab);
 }
 // Inverse of ntt_fwd up to the factor R (digit-reversed -> natural); ends with a barrier.
 template <class F, int LOGR, int NCOL_LG, int NBUF>
