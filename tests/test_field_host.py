@@ -36,3 +36,22 @@ def test_field30_routines(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "field30_check: ok" in r.stdout
+
+
+def test_radix16_bit_table_identity():
+    # The first forward step on 0/1 inputs (32-bit field) reads its length-16
+    # DFTs from a table: w = omega_16 = g30^(2^26) (the square of the
+    # sub-transform root omega_32 = g30^(2^25)), w^8 = -1, so
+    # X_k = T_k(b_0..b_7) + (-1)^k T_k(b_8..b_15), T_k(p) = sum_{j in p} w^(jk).
+    import random
+    q = 3 * 2 ** 30 + 1
+    w = pow(125, 2 ** 26, q)
+    assert pow(w, 8, q) == q - 1 and pow(w, 16, q) == 1
+    T = [[sum(pow(w, j * k % 16, q) for j in range(8) if p >> j & 1) % q for p in range(256)] for k in range(16)]
+    rng = random.Random(16)
+    for p in [0, 1, 0xFFFF, 0x8000, 0x00FF, 0xFF00] + [rng.getrandbits(16) for _ in range(300)]:
+        b = [(p >> i) & 1 for i in range(16)]
+        for k in range(16):
+            want = sum(b[i] * pow(w, i * k, q) for i in range(16)) % q
+            got = (T[k][p & 255] + (q - T[k][p >> 8] if k & 1 else T[k][p >> 8])) % q
+            assert got == want, (p, k)
