@@ -258,16 +258,18 @@ def _steps(logr):
     return [logr // ns + (1 if j < logr % ns else 0) for j in range(ns)]
 
 
-def _transform_modmuls(logr, f30):
+def _transform_modmuls(logr, f30, bits_in=False):
     """General modular multiplies per element of one on-chip transform of
     2^logr: the sub-transform twiddles (non-trivial radix-2 rotations; shifts
     over Goldilocks, products over the 32-bit field) and the twiddles between
-    steps (all but the last step)."""
+    steps (all but the last step).  bits_in: the first forward pass of the
+    32-bit field, whose radix-16 first step on 0/1 inputs is a table lookup
+    (no multiplies)."""
     st = _steps(logr)
     tot = 0.0
     for j, q in enumerate(st):
         rd = 1 << q
-        if f30:
+        if f30 and not (bits_in and j == 0 and q == 4):
             tot += ((rd // 2) * q - (rd - 1)) / rd
         if j + 1 < len(st):
             tot += (rd - 1) / rd
@@ -290,8 +292,8 @@ def path_modmuls(products):
         split = pass_split(L)
         row_tw = 9 / 4 if f30 else 2.0
         per = 0.0
-        for r in split:  # forward column passes of both operands
-            per += 2 * (_transform_modmuls(r, f30) + row_tw)
+        for j, r in enumerate(split):  # forward column passes of both operands
+            per += 2 * (_transform_modmuls(r, f30, bits_in=(j == 0)) + row_tw)
         mid = _transform_modmuls(min(lg, 13), f30)
         inverse = s in (0, 3)
         per += 2 * mid + 2 + (mid if inverse else 0.0)
