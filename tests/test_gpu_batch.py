@@ -153,3 +153,41 @@ def test_batch_bounded_wait_times_out_and_context_survives(cm_ctx):
     assert cm_ctx.device_status() == (native.CM_OK, 0)
     assert torch.equal(items[1][5], z2)
     good.close()
+
+
+def test_batch_workload_size_sampled(cm_ctx):
+    # the batched (a) workload at full size, in the launch configuration the
+    # bench times (autotuned plan, CUDA-graph replay): 4096 Toeplitz instances,
+    # n = floor(2^U), U ~ U[10, 22), m = n / 2, the bench's seeds; every
+    # instance's first and last 4 rows and 8 random ones (64 random ones for
+    # the 24 longest instances) against the oracle; tails zero
+    count = 4096
+    ns = inputs.loguniform_lengths(1, count, 10, 22)
+    ms = ns // 2
+    items, host = [], []
+    for j in range(count):
+        n, m = int(ns[j]), int(ms[j])
+        xw = inputs.bernoulli_half(10000 + 2 * j, n)
+        yw = inputs.bernoulli_half(10001 + 2 * j, n + m - 1)
+        z = torch.full((native.words(m),), -1, dtype=torch.int64, device="cuda")
+        items.append((T, n, m, to_dev(xw), to_dev(yw), z))
+        host.append((xw, yw))
+    b = cm_ctx.batch(items, autotune=True, graph=True)
+    b.launch()
+    b.launch()  # a replay writes the same bits
+    torch.cuda.synchronize()
+    assert cm_ctx.device_status() == (native.CM_OK, 0)
+    rng = np.random.default_rng(4096)
+    longest = set(np.argsort(ns)[-24:].tolist())
+    for j in range(count):
+        n, m = int(ns[j]), int(ms[j])
+        xw, yw = host[j]
+        zw = from_dev(items[j][5])
+        k = 64 if j in longest else 8
+        rows = np.unique(np.concatenate([np.arange(min(4, m)), np.arange(max(0, m - 4), m),
+                                         rng.integers(0, m, k)]))
+        got = ((zw[rows >> 6] >> (rows & 63).astype(np.uint64)) & np.uint64(1)).astype(np.uint8)
+        assert (got == oracle.toeplitz_rows(xw, n, yw, m, rows)).all(), (j, n, m)
+        if m & 63:
+            assert int(zw[-1]) >> (m & 63) == 0, (j, n, m)
+    b.close()
