@@ -60,3 +60,21 @@ def test_shared_seed_invalid(cm_ctx):
     assert L.cm_batch_toeplitz_shared_seed(h, p, 5, 5, p, 0, p, 0, s) == native.CM_EINVAL
     assert L.cm_batch_toeplitz_shared_seed(h, p, 5, 5, p, 1, p, 7, s) == native.CM_EINVAL
     assert L.cm_batch_toeplitz_shared_seed(h, p, 1 << 20, 1 << 20, p, 1, p, 0, s) == native.CM_EINVAL
+
+
+def test_engines_full_count_sampled(cm_ctx):
+    # the shared-seed workload at full size: 65536 inputs of 4096 bits under one
+    # 2048 x 4096 Toeplitz seed.  The two engines and the auto choice agree on
+    # every output bit; 50 inputs against the oracle.
+    n, m, count = 4096, 2048, 65536
+    wx, wz = native.words(n), native.words(m)
+    yw = inputs.bernoulli_half(4096, n + m - 1)
+    X = inputs.bernoulli_half(4097, n * count)
+    Xd, yd = to_dev(X), to_dev(yw)
+    Zg = from_dev(cm_ctx.toeplitz_shared_seed(yd, n, m, Xd, count, engine=native.ENGINE_GF2)).reshape(count, wz)
+    Zi = from_dev(cm_ctx.toeplitz_shared_seed(yd, n, m, Xd, count, engine=native.ENGINE_IMMA)).reshape(count, wz)
+    Za = from_dev(cm_ctx.toeplitz_shared_seed(yd, n, m, Xd, count)).reshape(count, wz)
+    assert (Zg == Zi).all() and (Zg == Za).all()
+    picks = [0, count - 1] + np.random.default_rng(4098).choice(count, 48, replace=False).tolist()
+    for c in picks:
+        assert (Zg[c] == oracle.toeplitz_packed(X[c * wx:(c + 1) * wx], n, yw, m)).all(), c
