@@ -54,7 +54,8 @@ k_middle(typename F::T *__restrict__ A, const typename F::T *__restrict__ Bv, ty
 }
 
 // ---------------------------------------------------------------------------
-// Parity bytes -> packed words.  One warp builds one 64-bit word per iteration.
+// Parity bytes -> packed words.  Over the floor(m / 512) whole groups of 512
+// positions a warp builds eight 64-bit words per iteration; past them, one.
 // ---------------------------------------------------------------------------
 __global__ void k_pack(const uint8_t *__restrict__ par, uint64_t m, uint64_t *__restrict__ z,
                        const uint32_t *__restrict__ pre, uint32_t *__restrict__ status) {
@@ -63,8 +64,21 @@ __global__ void k_pack(const uint8_t *__restrict__ par, uint64_t m, uint64_t *__
     const int lane = threadIdx.x & 31;
     const uint64_t nwords = (m + 63) >> 6;
     const uint64_t wstride = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nwords;
-         w += wstride) {
+    const uint64_t warp0 = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    // Groups of 8 words whose 512 parity bytes all lie below m: one 16-byte
+    // load per lane (16 positions), packed by a multiply per 4 bytes (bytes are
+    // 0 or 1: byte 3 of x * 0x01020408 is b0 + 2 b1 + 4 b2 + 8 b3, no carries),
+    // and four lanes' 16 bits joined by shuffles into one word.
+    const uint64_t ngroups = (reinterpret_cast<uintptr_t>(par) & 15) ? 0 : (m >> 9);
+    for (uint64_t g = warp0; g < ngroups; g += wstride) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(par + (g << 9)) + lane);
+        const uint32_t u = ((v.x * 0x01020408u) >> 24) | (((v.y * 0x01020408u) >> 24) << 4) |
+                           (((v.z * 0x01020408u) >> 24) << 8) | (((v.w * 0x01020408u) >> 24) << 12);
+        const uint32_t t = u | (__shfl_down_sync(0xffffffffu, u, 1) << 16);
+        const uint32_t t2 = __shfl_down_sync(0xffffffffu, t, 2);
+        if ((lane & 3) == 0) z[(g << 3) + (lane >> 2)] = bad ? 0ull : ((uint64_t)t2 << 32 | t);
+    }
+    for (uint64_t w = (ngroups << 3) + warp0; w < nwords; w += wstride) {
         const uint64_t p0 = (w << 6) + lane, p1 = p0 + 32;
         const uint32_t b0 = (p0 < m) ? par[p0] : 0u;
         const uint32_t b1 = (p1 < m) ? par[p1] : 0u;
