@@ -55,3 +55,12 @@ def test_radix16_bit_table_identity():
             want = sum(b[i] * pow(w, i * k, q) for i in range(16)) % q
             got = (T[k][p & 255] + (q - T[k][p >> 8] if k & 1 else T[k][p >> 8])) % q
             assert got == want, (p, k)
+
+
+def test_pack_multiply_gathers_four_parity_bytes():
+    # k_pack: for 4 bytes b0..b3 in {0, 1} (little-endian word x), byte 3 of
+    # x * 0x01020408 (mod 2^32) is b0 + 2 b1 + 4 b2 + 8 b3: no carry reaches it
+    for p in range(16):
+        b = [(p >> i) & 1 for i in range(4)]
+        x = b[0] | b[1] << 8 | b[2] << 16 | b[3] << 24
+        assert ((x * 0x01020408) & 0xFFFFFFFF) >> 24 == p
