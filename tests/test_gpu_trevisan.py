@@ -40,6 +40,7 @@ CASES = [
     # few outputs: chunks shared by 8 or 32 threads per output, with leading
     # zero chunks padding s to a multiple of the group
     (60000, 64, 100), (200000, 30, 77), (150000, 129, 50), (300000, 256, 40),
+    (100000, 100, 30), (400000, 150, 10), (600000, 256, 8),
 ]
 
 
