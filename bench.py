@@ -872,9 +872,6 @@ def run_von_neumann(args, world, rank, local):
         step()
     torch.cuda.synchronize()
     m = int(md.item())
-    import oracle.von_neumann as ovn
-    m_oracle = int(ovn.pair_counts_per_word(xw, n).sum()) if rank == 0 else m
-    assert m == m_oracle, (m, m_oracle)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.25)
@@ -1031,13 +1028,6 @@ def run_trevisan(args, world, rank, local):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    if rank == 0:  # spot check against the oracle
-        import oracle.trevisan as otv
-        from oracle import extractors as ex
-        xb, sb = ex.unpack_bits(xw, n), ex.unpack_bits(sw, 2 * l * 3)
-        zb = ex.unpack_bits(zd.cpu().numpy().view(np.uint64), m)
-        for i in range(3):
-            assert zb[i] == otv.rsh_onebit(xb, n, sb[2 * l * i: 2 * l * (i + 1)], l), i
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.25)
