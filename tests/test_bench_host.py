@@ -1,5 +1,6 @@
 """bench.py host logic: the per-kernel source hash that keys the committed ncu
-traffic figures, checked on a scratch copy of the kernel sources."""
+traffic figures (checked on a scratch copy of the kernel sources), and the
+reference arm's JSON line (the oracle on the host cores, no GPU)."""
 
 import os
 import shutil
@@ -59,3 +60,21 @@ def test_traffic_only_for_matching_sources(tmp_path, monkeypatch):
         f.write("\n// edit\n")
     assert bench.ncu_traffic("k_vn_write", "von_neumann") is None
     assert bench.ncu_traffic("k_rsh", "trevisan") == 1234.0
+
+
+def test_reference_arm_json_line():
+    # the reference arm times the oracle on the host cores (no GPU): one JSON
+    # line with the contract's keys, the ratio's inputs and no host copies
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1"],
+                       cwd=bench.ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 1
+    for k in ("metric", "value", "unit", "ms_per_step", "higher_is_better", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
