@@ -27,6 +27,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -69,24 +70,43 @@ def seed_bits(kind, n, m):
 # Kernels compiled from a translation unit of their own: a capture of one of
 # them stays valid while only other units change.  Every other kernel (the
 # transforms, the tail, the batch kernels) is keyed on all remaining units.
-# Headers count for every kernel.
+# Each unit counts with the headers it includes (transitively).
 OWN_UNITS = {"k_vn": "cm_vn.cu", "k_rsh": "cm_trevisan.cu", "k_ss": "cm_shared_seed.cu"}
+_INCLUDE = re.compile(r'^\s*#\s*include\s+"([^"]+)"', re.M)
+
+
+def _source_closure(units):
+    """The units and every header they include with quotes, resolved in the
+    kernel source directory, then the public include directory."""
+    dirs = [os.path.join(ROOT, "paper_2402_09481_gb300", "csrc"), os.path.join(ROOT, "include")]
+    seen, todo = set(), list(units)
+    while todo:
+        path = todo.pop()
+        if path in seen:
+            continue
+        seen.add(path)
+        with open(path, errors="replace") as fh:
+            text = fh.read()
+        for name in _INCLUDE.findall(text):
+            for d in [os.path.dirname(path)] + dirs:
+                cand = os.path.join(d, name)
+                if os.path.exists(cand):
+                    todo.append(os.path.normpath(cand))
+                    break
+    return sorted(seen)
 
 
 def kernel_source_hash(kernel: str | None = None) -> str:
-    """Hash of the sources `kernel` is built from (all of csrc when None)."""
+    """Hash of the sources `kernel` is built from (every unit when None)."""
     own = next((u for pre, u in OWN_UNITS.items() if kernel and kernel.startswith(pre)), None)
-    h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2402_09481_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if not f.endswith((".cu", ".cuh", ".h")):
-            continue
-        if kernel is not None and f.endswith(".cu"):
-            if own is not None and f != own:
-                continue
-            if own is None and f in OWN_UNITS.values():
-                continue
-        with open(os.path.join(csrc, f), "rb") as fh:
+    units = [f for f in sorted(os.listdir(csrc)) if f.endswith(".cu")]
+    if kernel is not None:
+        units = [f for f in units if f == own] if own else [f for f in units if f not in OWN_UNITS.values()]
+    h = hashlib.sha256()
+    for path in _source_closure([os.path.join(csrc, f) for f in units]):
+        h.update(os.path.relpath(path, ROOT).encode())
+        with open(path, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

@@ -39,10 +39,13 @@ def test_hash_follows_own_unit(tmp_path, monkeypatch):
     assert after2["k_pass"] != after["k_pass"]
     assert all(after2[k] == after[k] for k in ("k_rsh", "k_vn_write", "k_ss_gf2"))
 
-    with open(csrc / "cm_internal.h", "a") as f:              # a header: every kernel
+    with open(csrc / "cm_internal.h", "a") as f:              # a header every unit includes
         f.write("\n// edit\n")
     after3 = _hashes()
     assert all(after3[k] != after2[k] for k in after3)
+
+    (csrc / "unused_new.cuh").write_text("// included by nothing\n")   # no kernel's source
+    assert _hashes() == after3
 
 
 def test_traffic_only_for_matching_sources(tmp_path, monkeypatch):
