@@ -199,8 +199,8 @@ class ClockSampler:
 
 def field_of(kernel):
     """(kernel name without the field suffix, element bytes): the 32-bit field
-    kernels carry the suffix _f30, the Goldilocks ones none."""
-    return (kernel[:-4], 4) if kernel.endswith("_f30") else (kernel, 8)
+    kernels carry the suffix _f30 or _f25, the Goldilocks ones none."""
+    return (kernel[:-4], 4) if kernel.endswith(("_f30", "_f25")) else (kernel, 8)
 
 
 def pass_split(L):
@@ -233,7 +233,7 @@ def kernel_model(products, m):
         if p["sum"] == 4:  # dense tail: seed bits and z read, z written
             add("k_tail", (p["m"] + p["tail_terms"]) / 8 + 2 * p["m"] / 8, 0.0)
             continue
-        L, e, s, mr = p["L"], (4 if p["field"] == 2 else 8), p["sum"], p["m"]
+        L, e, s, mr = p["L"], (8 if p["field"] == 1 else 4), p["sum"], p["m"]
         lg = int(L).bit_length() - 1
         split = pass_split(L)
         if not split:
@@ -306,7 +306,7 @@ def path_modmuls(products):
     for p in products:
         if p["sum"] == 4:
             continue
-        L, f30, s = p["L"], p["field"] == 2, p["sum"]
+        L, f30, s = p["L"], p["field"] != 1, p["sum"]
         lg = int(L).bit_length() - 1
         n_off += 3 * L * (-(-lg // 6) - 1) + L
         split = pass_split(L)
@@ -330,7 +330,7 @@ def path_bytes(products, n, seedlen, m):
     48L for Goldilocks, 24L for the 32-bit field), plus the bit I/O once."""
     tot = (n + seedlen + m) / 8
     for p in products:
-        tot += 6 * (4 if p["field"] == 2 else 8) * p["L"]
+        tot += 6 * (8 if p["field"] == 1 else 4) * p["L"]
     return tot
 
 
@@ -1279,6 +1279,8 @@ def main():
     ap.add_argument("--workload", default="circulant",
                     choices=sorted(WORKLOADS) + ["batched_a", "batched_b", "served", "von_neumann", "trevisan"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--field", default="auto", choices=["auto", "q30", "goldilocks"],
+                    help="transform fields of the single calls (cm_options.field)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args)
@@ -1319,11 +1321,12 @@ def main():
     wl = WORKLOADS[args.workload]
     kind, n, m = wl["kind"], wl["n"], wl["m"]
     sb = seed_bits(kind, n, m)
-    plan = native.plan_query(kind, n, m)
-    products = native.plan_products(kind, n, m)
+    fopt = {"auto": native.FIELD_AUTO, "q30": native.FIELD_Q30, "goldilocks": native.FIELD_GOLDILOCKS}[args.field]
+    plan = native.plan_query(kind, n, m, field=fopt)
+    products = native.plan_products(kind, n, m, field=fopt)
     L = plan["transform_length"]
     launches = plan["launches"]
-    ctx = native.Context(local)
+    ctx = native.Context(local, field=fopt)
     stream = torch.cuda.current_stream()
 
     xw = inputs.bernoulli_half(1 + 1000 * rank, n)
@@ -1394,7 +1397,7 @@ def main():
     peak, peak_src = measured_peaks()
     achieved = alg / (per_launch * 1e-3) / 1e9
     clk = (sampler.summary(t_wall0, t_wall1) or {}).get("sm_mhz") or 2070.0
-    ops = ALU_OPS_PER_BUTTERFLY_F30 if dom.endswith("_f30") else ALU_OPS_PER_BUTTERFLY
+    ops = ALU_OPS_PER_BUTTERFLY_F30 if dom.endswith(("_f30", "_f25")) else ALU_OPS_PER_BUTTERFLY
     ach_b = bfly / (per_launch * 1e-3) / 1e9
     peak_b = alu_peak_butterflies(clk, ops) / 1e9
     roof = {"bound": "alu", "kernel": dom, "achieved": ach_b, "peak": peak_b, "unit": "G butterflies/s",
@@ -1411,7 +1414,8 @@ def main():
     n_path, n_off = path_modmuls(products)
     r_gl = native.modmul_rate(local, native.FIELD_GOLDILOCKS)
     r_q30 = native.modmul_rate(local, native.FIELD_Q30)
-    r_path = r_q30 if plan["field"] == native.FIELD_Q30 else r_gl
+    r_q25 = native.modmul_rate(local, native.FIELD_Q25)
+    r_path = {native.FIELD_Q30: r_q30, native.FIELD_Q25: r_q25}.get(plan["field"], r_gl)
     t_hbm = pb / (peak * 1e9) * 1e3
     t_int_off = n_off / r_gl * 1e3
     t_int_path = n_path / r_path * 1e3
@@ -1492,7 +1496,7 @@ def main():
             "config": {"workload": wl["name"], "n": n, "m": m, "seed_bits": sb,
                        "plan": {"products": plan["products"], "windows": plan["windows"],
                                 "transform_length": L,
-                                "field": "q = 3 * 2^30 + 1" if plan["field"] == 2 else "Goldilocks",
+                                "field": {2: "q = 3 * 2^30 + 1", 3: "q = 5 * 2^25 + 1"}.get(plan["field"], "Goldilocks"),
                                 "planner_estimate_ms": plan["est_ms"]},
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

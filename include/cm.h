@@ -4,8 +4,13 @@
  * The library computes the Toeplitz, Circulant and Dodis et al. extractors of
  * Cryptomite (arXiv 2402.09481) on one NVIDIA GB300 GPU.  Each output is a
  * GF(2) matrix-vector product, computed exactly as an integer convolution by a
- * number-theoretic transform over the Goldilocks prime p = 2^64 - 2^32 + 1
- * (Def. ntt and Thm. convolution of the paper), then reduced mod 2.
+ * number-theoretic transform (Def. ntt and Thm. convolution of the paper),
+ * then reduced mod 2.  The transform runs over one of three prime fields, each
+ * large enough that every convolution coefficient (a count of at most the
+ * product's length) is exact: q = 5 * 2^25 + 1 with lazy reduction for
+ * transforms up to 2^25, the paper's own q = 3 * 2^30 + 1 (Section
+ * "Performance") up to 2^30, and Goldilocks p = 2^64 - 2^32 + 1 up to 2^32.
+ * The choice changes speed, never a result bit.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -66,11 +71,14 @@ typedef struct {
      * single extraction whose K + m - 1 is longer runs as several products
      * (see cm_toeplitz); lowering it trades transforms for scratch. */
     uint32_t max_transform_lg;
-    /* Transform field of the single calls: CM_FIELD_AUTO takes the 32-bit field
-     * of the prime 3 * 2^30 + 1 (the paper's small field, Section "Performance")
-     * for every product of length <= 2^30 and Goldilocks above (and the
-     * planner may prefer 32-bit-field blocks to one Goldilocks transform);
-     * CM_FIELD_GOLDILOCKS takes Goldilocks throughout.  Results are identical. */
+    /* Transform field of the single calls: CM_FIELD_AUTO takes the field of
+     * 5 * 2^25 + 1 (lazy reduction) for every product of length <= 2^25, the
+     * field of 3 * 2^30 + 1 (the paper's small field, Section "Performance")
+     * up to 2^30 and Goldilocks above (the planner may prefer blocks over the
+     * smaller fields to one longer transform); CM_FIELD_Q30 skips the field of
+     * 5 * 2^25 + 1; CM_FIELD_GOLDILOCKS takes Goldilocks throughout.  Results
+     * are identical.  Batches and the server run their work-list instances
+     * over 3 * 2^30 + 1 (Goldilocks in a CM_FIELD_GOLDILOCKS context). */
     uint32_t field;
     /* Most input blocks whose transform-domain products are summed before one
      * inverse transform; 0 = as many as keep every count below the field's
@@ -89,7 +97,8 @@ typedef struct {
 
 #define CM_FIELD_AUTO 0u
 #define CM_FIELD_GOLDILOCKS 1u
-#define CM_FIELD_Q30 2u /* reported by cm_plan_query only: q = 3 * 2^30 + 1 */
+#define CM_FIELD_Q30 2u /* q = 3 * 2^30 + 1 (and Goldilocks above 2^30) */
+#define CM_FIELD_Q25 3u /* reported by cm_plan_query only: q = 5 * 2^25 + 1 */
 
 /* Create a context on CUDA device `device`: root tables resident in HBM, a
  * scratch memory pool.  opt may be NULL.  Returns CM_EDEVICE if the device is
@@ -403,13 +412,16 @@ cm_status cm_profile_read(cm_ctx *ctx, cm_profile_entry *out, uint32_t cap, uint
  * multiply and multiply-by-2^s (s = 0..96), written as 32-bit carry chains,
  * with the plain 64-bit C forms of the same functions, and the 32-bit field's
  * add, subtract, Montgomery product and sub-transform twiddles (q = 3 * 2^30
- * + 1) with plain 64-bit modular arithmetic; *mismatches receives the number
- * of disagreements (0 when correct).  Allocates and frees 8 bytes. */
+ * + 1) and the lazily reduced field's (q = 5 * 2^25 + 1) reduction, canonical
+ * form, add, subtract, Montgomery and Shoup products, values and output ranges
+ * included, with plain 64-bit modular arithmetic; *mismatches receives the
+ * number of disagreements (0 when correct).  Allocates and frees 8 bytes. */
 cm_status cm_field_selftest(int device, uint64_t count, uint64_t seed, uint64_t *mismatches);
 
 /* Modular-multiply rate of `device` for `field` (CM_FIELD_GOLDILOCKS: the
  * 64-bit product and reduction of the transforms; CM_FIELD_Q30: the 32-bit
- * Montgomery product), measured by a kernel of independent register chains of
+ * Montgomery product; CM_FIELD_Q25: the lazy Montgomery product of the field
+ * of 5 * 2^25 + 1), measured by a kernel of independent register chains of
  * products on every SM (8 chains a thread, 4 CTAs of 256 threads per SM) and
  * timed with CUDA events: *per_second receives products per second.  The
  * integer-pipe bound of a path is its number of general multiplies divided by
@@ -434,8 +446,8 @@ typedef struct {
     uint64_t windows;          /* output windows (one inverse transform each) */
     uint64_t scratch_bytes;    /* pool bytes the call holds */
     uint32_t launches;         /* kernel launches the call enqueues */
-    uint32_t field;            /* CM_FIELD_GOLDILOCKS if any product runs over
-                                  Goldilocks, else CM_FIELD_Q30 */
+    uint32_t field;            /* the widest field of any product: CM_FIELD_GOLDILOCKS,
+                                  else CM_FIELD_Q30, else CM_FIELD_Q25 */
     double est_ms;             /* the planner's GPU-time estimate (GB300) */
     uint64_t tail_terms;       /* terms t < tail_terms left out of the transforms
                                   and XORed in densely (0: none) */
@@ -464,7 +476,7 @@ typedef struct {
     uint64_t a_len, a_srclen, a_off;
     uint64_t b_len, b_srclen, b_off;
     uint32_t a_mode, b_mode;
-    uint32_t field;      /* CM_FIELD_GOLDILOCKS or CM_FIELD_Q30 */
+    uint32_t field;      /* CM_FIELD_GOLDILOCKS, CM_FIELD_Q30 or CM_FIELD_Q25 */
     int32_t sum;         /* 0 alone, 1 first of a sum group, 2 inner, 3 last, 4 tail */
     uint32_t xor_into;   /* this product's parities are XORed into z */
     uint32_t tail_terms; /* sum 4: the number of tail terms */

@@ -66,20 +66,20 @@ constexpr uint64_t kFlagBytes = 256;
 static uint64_t flag_bytes(int kind) { return kind == CM_DODIS ? kFlagBytes : 0; }
 static uint64_t plan_scratch(int lg, uint64_t m, int field, bool summed) {
     if (lg <= kMidLgMax) return 0;
-    const uint64_t esz = field == kFieldF30 ? 4 : 8;
+    const uint64_t esz = field == kFieldGL ? 8 : 4;
     return (summed ? 3 : 2) * esz * (1ull << lg) + ((m + 255) & ~255ull);
 }
 
 // Transform length (at least 2^min_lg), field, pass split, scratch and launch
 // count for K + m - 1 <= 2^32.
-static void finish_plan(Plan *p, bool allow_f30, int min_lg, bool summed) {
+static void finish_plan(Plan *p, int fields, int min_lg, bool summed) {
     const uint64_t need = p->K + p->m - 1;
     p->lg = ceil_log2(need);
     if (p->lg < min_lg) p->lg = min_lg;
     if (p->lg < 1) p->lg = 1;
     p->L = 1ull << p->lg;
     p->lo = p->K - 1;
-    p->field = (allow_f30 && p->lg <= kF30MaxLg) ? kFieldF30 : kFieldGL;
+    p->field = field_for(fields, p->lg);
     p->summed = summed;
     const int rest = p->lg - kMidLgMax;
     if (rest <= 0) {
@@ -98,10 +98,10 @@ static void finish_plan(Plan *p, bool allow_f30, int min_lg, bool summed) {
     if (p->kind == CM_DODIS) p->launches += 1;  // precondition check
 }
 
-bool make_plan(int kind, uint64_t n, uint64_t m, Plan *p, bool allow_f30) {
+bool make_plan(int kind, uint64_t n, uint64_t m, Plan *p, int fields) {
     if (!base_maps(kind, n, m, p)) return false;
     if (p->K + m - 1 > (1ull << 32)) return false;
-    finish_plan(p, allow_f30, 1, false);
+    finish_plan(p, fields, 1, false);
     return true;
 }
 
@@ -133,6 +133,11 @@ static const double kCostF30[kF30MaxLg + 1] = {
     0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,   0.02,   0.02,
     0.02,  0.02,  0.02,  0.080, 0.081, 0.0822, 0.0829, 0.0857, 0.0950, 0.0991, 0.1162,
     0.1907, 0.3389, 0.6710, 1.3995, 2.6839, 5.4039, 10.960, 22.246, 45.643};
+// F25: estimated from the F30 figures until measured (lazy butterflies).
+static const double kCostF25[kF25MaxLg + 1] = {
+    0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,   0.02,   0.02,
+    0.02,  0.02,  0.02,  0.060, 0.061, 0.0620, 0.0625, 0.0640, 0.0700, 0.0720, 0.0800,
+    0.1200, 0.2000, 0.3900, 0.8000};
 static const double kCostGL[33] = {
     0.03,  0.03,  0.03,  0.03,  0.03,  0.03,  0.03,  0.03,  0.03,   0.03,   0.03,
     0.03,  0.03,  0.03,  0.130, 0.133, 0.1356, 0.1419, 0.1459, 0.1604, 0.1678, 0.2221,
@@ -150,14 +155,17 @@ constexpr int kSumMinLg = kMidLgMax + 1;  // summed windows need a column pass
 static uint64_t words_of(uint64_t bits) { return (bits + 63) / 64; }
 static uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 
-static double plan_cost(int field, int lg) { return field == kFieldF30 ? kCostF30[lg] : kCostGL[lg]; }
+static double plan_cost(int field, int lg) {
+    return field == kFieldF25 ? kCostF25[lg] : field == kFieldF30 ? kCostF30[lg] : kCostGL[lg];
+}
 
 // Input blocks whose products one sum may hold: the counts of G blocks add up
 // to at most G Kb, which must stay below the field's characteristic (the
 // Goldilocks prime exceeds every count up to 2^40).  Windows with more blocks
 // sum in groups, each with its own inverse transform; the groups' parities XOR.
 static uint64_t group_size(int field, uint64_t Kb, uint64_t nin, uint32_t cap) {
-    uint64_t g = field == kFieldF30 ? (F30_Q - 1) / Kb : nin;  // >= 3: Kb <= 2^30
+    // >= 3: Kb <= 2^30 (F30), Kb <= 2^25 (F25)
+    uint64_t g = field == kFieldF30 ? (F30_Q - 1) / Kb : field == kFieldF25 ? (F25_Q - 1) / Kb : nin;
     if (cap && g > cap) g = cap;
     return g < nin ? g : nin;
 }
@@ -193,9 +201,7 @@ static int window_lg(const Shape &s, uint64_t mr) {
     return lg < 1 ? 1 : lg;
 }
 
-static int field_of(bool allow_f30, int lg) { return (allow_f30 && lg <= kF30MaxLg) ? kFieldF30 : kFieldGL; }
-
-static void evaluate(int kind, uint64_t m, bool allow_f30, uint32_t max_sum, Shape *s) {
+static void evaluate(int kind, uint64_t m, int fields, uint32_t max_sum, Shape *s) {
     const uint64_t mlast = m - (s->nout - 1) * s->Mb;
     s->cost = 0;
     s->scratch = 0;
@@ -204,7 +210,7 @@ static void evaluate(int kind, uint64_t m, bool allow_f30, uint32_t max_sum, Sha
         const uint64_t cnt = w == 0 ? s->nout - 1 : 1, mr = w == 0 ? s->Mb : mlast;
         if (!cnt) continue;
         const int lg = window_lg(*s, mr);
-        const int field = field_of(allow_f30, lg);
+        const int field = field_for(fields, lg);
         const uint64_t G = s->summed ? group_size(field, s->Kb, s->nin, max_sum) : 1;
         s->cost += (double)cnt * window_cost(field, lg, s->nin, G);
         const uint64_t sc = plan_scratch(lg, mr, field, s->summed);
@@ -225,8 +231,12 @@ bool plan_options(const cm_options *opt, PlanOptions *o) {
         if (opt->max_transform_lg < 8 || opt->max_transform_lg > 32) return false;
         o->max_lg = (int)opt->max_transform_lg;
     }
-    if (opt->field > CM_FIELD_GOLDILOCKS) return false;
-    o->allow_f30 = opt->field != CM_FIELD_GOLDILOCKS;
+    switch (opt->field) {
+        case CM_FIELD_AUTO: o->fields = kFieldsAll; break;
+        case CM_FIELD_Q30: o->fields = kFieldsQ30; break;
+        case CM_FIELD_GOLDILOCKS: o->fields = kFieldsGL; break;
+        default: return false;
+    }
     o->budget = opt->hbm_budget_bytes;
     o->max_sum = opt->max_sum_blocks;
     if (opt->plan_mode > CM_PLAN_SINGLE) return false;
@@ -236,7 +246,7 @@ bool plan_options(const cm_options *opt, PlanOptions *o) {
 
 bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::vector<Block> *out) {
     const int max_lg = o.max_lg;
-    const bool allow_f30 = o.allow_f30;
+    const int fields = o.fields;
     const uint64_t budget = o.budget;
     out->clear();
     Plan b;
@@ -286,7 +296,7 @@ bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::ve
                 if (c.nin > kMaxBlocks / c.nout) continue;  // (no overflow: both <= 2^40)
                 c.Kb = ceil_div(K - c.tail, c.nin);
                 c.summed = c.nin > 1 && max_lg > kMidLgMax;
-                evaluate(kind, m, allow_f30, o.max_sum, &c);
+                evaluate(kind, m, fields, o.max_sum, &c);
                 const bool single = c.nin == 1 && c.nout == 1 && c.tail == 0;
                 const bool fits = budget == 0 || c.scratch <= budget;
                 double cc = c.cost, bc = best.cost;
@@ -306,7 +316,7 @@ bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::ve
     if (!have) return false;
     const Shape &s = best;
     if (s.nin == 1 && s.nout == 1 && s.tail == 0) {
-        finish_plan(&b, allow_f30, 1, false);
+        finish_plan(&b, fields, 1, false);
         out->push_back({b, 0, kSumNone, false, 0});
         return true;
     }
@@ -314,7 +324,7 @@ bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::ve
     for (uint64_t r = 0; r < s.nout; ++r) {
         const uint64_t I0 = r * s.Mb, mr = (m - I0 < s.Mb) ? m - I0 : s.Mb;
         const int lg_r = window_lg(s, mr);
-        const uint64_t G = s.summed ? group_size(field_of(allow_f30, lg_r), s.Kb, s.nin, o.max_sum) : 1;
+        const uint64_t G = s.summed ? group_size(field_for(fields, lg_r), s.Kb, s.nin, o.max_sum) : 1;
         for (uint64_t j = 0; j < s.nin; ++j) {
             const uint64_t D = j * s.Kb;  // < Kc: (nin - 1) Kb < Kc
             const uint64_t kb = (Kc - D < s.Kb) ? Kc - D : s.Kb;
@@ -333,7 +343,7 @@ bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::ve
             // B'_v = B_{v + T0 + I0 - (Kb - kb)}, kept in [0, bsrclen)
             const uint64_t src = b.bsrclen;
             q.boff = ((b.boff + T0 + I0) % src + src - (s.Kb - kb) % src) % src;
-            finish_plan(&q, allow_f30, lg_r, s.summed);
+            finish_plan(&q, fields, lg_r, s.summed);
             // sum group [g0, g1) of this window; a group of one stands alone
             const uint64_t g0 = j / G * G, g1 = (g0 + G < s.nin) ? g0 + G : s.nin;
             int sum = kSumNone;
@@ -343,7 +353,7 @@ bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::ve
         }
     }
     if (s.tail) {
-        finish_plan(&b, allow_f30, 1, false);  // maps only: the tail runs no transform
+        finish_plan(&b, fields, 1, false);  // maps only: the tail runs no transform
         out->push_back({b, 0, kSumTail, true, (uint32_t)s.tail});
     }
     return true;
@@ -386,9 +396,11 @@ static cm_status enqueue_product(cm_ctx *ctx, const Plan &p, const uint64_t *x, 
                                  uint64_t *z, void *scratch, const uint32_t *pre, int sum, cudaStream_t st) {
     const BitMap am = bitmap(x, p.amode, p.alen, p.asrclen, p.aoff);
     const BitMap bm = bitmap(y, p.bmode, p.blen, p.bsrclen, p.boff);
-    const bool f30 = p.field == kFieldF30;
-    const uint64_t linv = f30 ? f30_linv_mont2(p.L) : gl_inv_pow2_host(p.L);
-    const size_t esz = f30 ? sizeof(uint32_t) : sizeof(uint64_t);
+    const bool f30 = p.field == kFieldF30, f25 = p.field == kFieldF25;
+    const uint64_t linv = f25 ? f25_linv_mont2(p.L) : f30 ? f30_linv_mont2(p.L) : gl_inv_pow2_host(p.L);
+    const size_t esz = p.field == kFieldGL ? sizeof(uint64_t) : sizeof(uint32_t);
+    // kernel names for the trace: Goldilocks, F30 or F25 forms
+    auto kname = [&](const char *gl, const char *k30, const char *k25) { return f25 ? k25 : f30 ? k30 : gl; };
     cudaError_t e;
     uint8_t *sc = static_cast<uint8_t *>(scratch);
     if (p.npass == 0) {
@@ -404,8 +416,9 @@ static cm_status enqueue_product(cm_ctx *ctx, const Plan &p, const uint64_t *x, 
         q.field = p.field;
         q.rt = ctx->rt;
         q.rt30 = ctx->rt30;
+        q.rt25 = ctx->rt25;
         q.stream = st;
-        ProfScope ps(ctx, f30 ? "k_fused_small_f30" : "k_fused_small", st);
+        ProfScope ps(ctx, kname("k_fused_small", "k_fused_small_f30", "k_fused_small_f25"), st);
         return cuda_status(launch_small(q, p.lg));
     }
     void *A = sc;
@@ -434,19 +447,20 @@ static cm_status enqueue_product(cm_ctx *ctx, const Plan &p, const uint64_t *x, 
             a.field = p.field;
             a.rt = ctx->rt;
             a.rt30 = ctx->rt30;
+            a.rt25 = ctx->rt25;
             a.L = p.L;
             a.inv = false;
             a.bits_in = (j == 0);
-            ProfScope ps(ctx, j == 0 ? (f30 ? "k_pass_fwd_bits_f30" : "k_pass_fwd_bits")
-                                     : (f30 ? "k_pass_fwd_f30" : "k_pass_fwd"), st);
+            ProfScope ps(ctx, j == 0 ? kname("k_pass_fwd_bits", "k_pass_fwd_bits_f30", "k_pass_fwd_bits_f25")
+                                     : kname("k_pass_fwd", "k_pass_fwd_f30", "k_pass_fwd_f25"), st);
             if ((e = launch_pass(a, p.pass_lg[j], st)) != cudaSuccess) return cuda_status(e);
         }
     }
     {
-        ProfScope ps(ctx, f30 ? "k_middle_f30" : "k_middle", st);
+        ProfScope ps(ctx, kname("k_middle", "k_middle_f30", "k_middle_f25"), st);
         const int mode = sum == kSumFirst ? kMidFirst : sum == kSumInner ? kMidInner
                          : sum == kSumLast ? kMidLast : kMidAlone;
-        e = launch_middle(p.field, A, B, C, mode, p.L, linv, ctx->rt, ctx->rt30, ctx->nsm, st);
+        e = launch_middle(p.field, A, B, C, mode, p.L, linv, ctx->rt, ctx->rt30, ctx->rt25, ctx->nsm, st);
         if (e != cudaSuccess) return cuda_status(e);
     }
     if (sum == kSumFirst || sum == kSumInner) return CM_OK;  // the group's last block finishes
@@ -460,14 +474,15 @@ static cm_status enqueue_product(cm_ctx *ctx, const Plan &p, const uint64_t *x, 
         a.field = p.field;
         a.rt = ctx->rt;
         a.rt30 = ctx->rt30;
+        a.rt25 = ctx->rt25;
         a.L = p.L;
         a.inv = true;
         a.parity_out = (j == 0);
         a.par = par;
         a.lo = p.lo;
         a.m = p.m;
-        ProfScope ps(ctx, j == 0 ? (f30 ? "k_pass_inv_parity_f30" : "k_pass_inv_parity")
-                                 : (f30 ? "k_pass_inv_f30" : "k_pass_inv"), st);
+        ProfScope ps(ctx, j == 0 ? kname("k_pass_inv_parity", "k_pass_inv_parity_f30", "k_pass_inv_parity_f25")
+                                 : kname("k_pass_inv", "k_pass_inv_f30", "k_pass_inv_f25"), st);
         if ((e = launch_pass(a, p.pass_lg[j], st)) != cudaSuccess) return cuda_status(e);
     }
     ProfScope ps(ctx, "k_pack", st);
@@ -660,6 +675,45 @@ static void build_tables30(std::vector<uint32_t> &h) {
         }
 }
 
+// F25 root tables, entries in Montgomery form w 2^32 mod q: small[8192] =
+// omega_8192^e; big_lo_fwd[8192] = g25^e; big_hi_fwd[4096] = g25^(8192 e);
+// big_lo_inv, big_hi_inv likewise for g25^-1; then the bit DFT table (plain,
+// canonical) of the radix-16 root omega_16 = g25^(2^21).
+static void build_tables25(std::vector<uint32_t> &h) {
+    h.assign(kTable25Words, 0);
+    const uint32_t g = f25_root_2_25(false), gi = f25_root_2_25(true);
+    const uint32_t w = f25_pow(g, 1ull << (kF25MaxLg - kSmallLg));  // omega_8192
+    uint32_t a = 1;
+    for (int e = 0; e < 8192; ++e) {
+        h[e] = f25_to_mont(a);
+        a = f25_mulmod(a, w);
+    }
+    uint32_t *lf = &h[8192], *hf = lf + 8192, *li = hf + 4096, *hi = li + 8192;
+    const uint32_t g13 = f25_pow(g, 8192), gi13 = f25_pow(gi, 8192);
+    uint32_t c0 = 1, c1 = 1, c2 = 1, c3 = 1;
+    for (int e = 0; e < 8192; ++e) {
+        lf[e] = f25_to_mont(c0);
+        li[e] = f25_to_mont(c2);
+        c0 = f25_mulmod(c0, g);
+        c2 = f25_mulmod(c2, gi);
+        if (e < 4096) {
+            hf[e] = f25_to_mont(c1);
+            hi[e] = f25_to_mont(c3);
+            c1 = f25_mulmod(c1, g13);
+            c3 = f25_mulmod(c3, gi13);
+        }
+    }
+    uint32_t *b16 = hi + 4096;
+    const uint32_t w16 = f25_pow(F25_G25, 1ull << 21);
+    for (int k = 0; k < 16; ++k)
+        for (int p = 0; p < 256; ++p) {
+            uint64_t acc = 0;
+            for (int j = 0; j < 8; ++j)
+                if ((p >> j) & 1) acc += f25_pow(w16, (uint64_t)((j * k) & 15));
+            b16[k * 256 + p] = (uint32_t)(acc % F25_Q);
+        }
+}
+
 }  // namespace cm
 
 using namespace cm;
@@ -698,16 +752,25 @@ extern "C" cm_status cm_create(cm_ctx **out, int device, const cm_options *opt) 
 
     std::vector<uint64_t> h;
     build_tables(h);
-    std::vector<uint32_t> h30;
+    std::vector<uint32_t> h30, h25;
     build_tables30(h30);
+    build_tables25(h25);
     if (cudaMalloc(&c->d_tables, h.size() * sizeof(uint64_t)) != cudaSuccess ||
         cudaMalloc(&c->d_tables30, h30.size() * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&c->d_tables25, h25.size() * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&c->d_status, 64) != cudaSuccess) {
         cm_destroy(c);
         return CM_ENOMEM;
     }
     cudaMemcpy(c->d_tables, h.data(), h.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
     cudaMemcpy(c->d_tables30, h30.data(), h30.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_tables25, h25.data(), h25.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    c->rt25.small = c->d_tables25;
+    c->rt25.big_lo_fwd = c->d_tables25 + 8192;
+    c->rt25.big_hi_fwd = c->rt25.big_lo_fwd + 8192;
+    c->rt25.big_lo_inv = c->rt25.big_hi_fwd + 4096;
+    c->rt25.big_hi_inv = c->rt25.big_lo_inv + 8192;
+    c->rt25.bits16 = c->rt25.big_hi_inv + 4096;
     c->rt30.small = c->d_tables30;
     c->rt30.big_lo_fwd = c->d_tables30 + 8192;
     c->rt30.big_hi_fwd = c->rt30.big_lo_fwd + 32768;
@@ -740,6 +803,7 @@ extern "C" void cm_destroy(cm_ctx *c) {
     for (auto ev : c->ev_pool) cudaEventDestroy(ev);
     if (c->d_tables) cudaFree(c->d_tables);
     if (c->d_tables30) cudaFree(c->d_tables30);
+    if (c->d_tables25) cudaFree(c->d_tables25);
     if (c->d_status) cudaFree(c->d_status);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     delete c;
@@ -810,7 +874,7 @@ static bool query(int kind, uint64_t n, uint64_t m, const cm_options *opt, cm_pl
     info->scratch_bytes = blocks_scratch(bl, &tmp_off, &pre_off);
     info->products = bl.size() - (bl.back().sum == kSumTail ? 1 : 0);
     info->launches = blocks_launches(bl);
-    info->field = CM_FIELD_Q30;
+    info->field = CM_FIELD_Q25;  // the widest field of any product
     for (size_t i = 0; i < bl.size(); ++i) {
         const Block &b = bl[i];
         if (b.sum == kSumTail) {
@@ -819,6 +883,7 @@ static bool query(int kind, uint64_t n, uint64_t m, const cm_options *opt, cm_pl
         }
         if (b.p.L > info->transform_length) info->transform_length = b.p.L;
         if (b.p.field == kFieldGL) info->field = CM_FIELD_GOLDILOCKS;
+        else if (b.p.field == kFieldF30 && info->field == CM_FIELD_Q25) info->field = CM_FIELD_Q30;
         if (i == 0 || b.zword != bl[i - 1].zword) ++info->windows;  // blocks come window by window
     }
     info->est_ms = blocks_cost_ms(bl);
@@ -852,7 +917,7 @@ extern "C" cm_status cm_plan_products(int kind, uint64_t n, uint64_t m, const cm
         d.b_off = b.p.boff;
         d.a_mode = (uint32_t)b.p.amode;
         d.b_mode = (uint32_t)b.p.bmode;
-        d.field = b.p.field == kFieldF30 ? CM_FIELD_Q30 : CM_FIELD_GOLDILOCKS;
+        d.field = b.p.field == kFieldF25 ? CM_FIELD_Q25 : b.p.field == kFieldF30 ? CM_FIELD_Q30 : CM_FIELD_GOLDILOCKS;
         d.sum = b.sum;
         d.xor_into = b.xor_into ? 1u : 0u;
         d.tail_terms = b.tail;

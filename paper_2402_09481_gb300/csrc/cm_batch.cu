@@ -473,7 +473,7 @@ extern "C" cm_status cm_batch_create(cm_ctx *ctx, const cm_desc *descs, uint32_t
     size_t total = 0;
     for (uint32_t i = 0; i < count; ++i) {
         const cm_desc &d = descs[i];
-        if (!d.x || !d.y || !d.z || !make_plan(d.kind, d.n, d.m, &b->plans[i], ctx->popt.allow_f30)) {
+        if (!d.x || !d.y || !d.z || !make_plan(d.kind, d.n, d.m, &b->plans[i], worklist_fields(ctx->popt))) {
             delete b;
             return CM_EINVAL;
         }

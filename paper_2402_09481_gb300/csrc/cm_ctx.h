@@ -25,6 +25,8 @@ struct cm_ctx {
     cm::RootTables rt{};
     uint32_t *d_tables30 = nullptr;
     cm::RootTables30 rt30{};
+    uint32_t *d_tables25 = nullptr;
+    cm::RootTables25 rt25{};
     cm_server *server = nullptr;
 
     // per-kernel tracing (cm_profile_*): events around each launch when on

@@ -17,8 +17,11 @@ constexpr size_t kTableWords = 8192 + 4 * 65536;  // resident root tables
 // Transform fields (see ntt_device.cuh).
 constexpr int kFieldGL = 0;   // Goldilocks, 64-bit elements, L <= 2^32
 constexpr int kFieldF30 = 1;  // 3 * 2^30 + 1, 32-bit elements, L <= 2^30
+constexpr int kFieldF25 = 2;  // 5 * 2^25 + 1, 32-bit elements, L <= 2^25, lazy reduction
 constexpr int kF30MaxLg = 30;
+constexpr int kF25MaxLg = 25;
 constexpr size_t kTable30Words = 8192 + 4 * 32768 + 4096;  // resident F30 root tables + bit DFT table
+constexpr size_t kTable25Words = 8192 + 2 * 8192 + 2 * 4096 + 4096;  // F25 root tables + bit DFT table
 
 // Arguments of the single-CTA extraction (L <= 2^13).
 struct Launch {
@@ -30,6 +33,7 @@ struct Launch {
     int field;
     RootTables rt;
     RootTables30 rt30;
+    RootTables25 rt25;
     cudaStream_t stream;
 };
 
@@ -47,6 +51,7 @@ struct PassArgs {
     int field;
     RootTables rt;
     RootTables30 rt30;
+    RootTables25 rt25;
     uint64_t L;
     bool inv, bits_in, parity_out;
 };
@@ -57,13 +62,16 @@ cudaError_t launch_pass_fwd(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_inv(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_fwd30(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_inv30(const PassArgs &a, int logr, cudaStream_t st);
+cudaError_t launch_pass_fwd25(const PassArgs &a, int logr, cudaStream_t st);
+cudaError_t launch_pass_inv25(const PassArgs &a, int logr, cudaStream_t st);
 // A, B: L elements of the field's word size.  C null: the product's
 // row-transformed result goes to A.  Otherwise mode (MidSum) sums the scaled
 // transform-domain products of a sum group in C (L elements): kMidFirst
 // stores, kMidInner adds, kMidLast adds and writes the inverse row transform
 // of the sum to A.
 cudaError_t launch_middle(int field, void *A, const void *B, void *C, int mode, uint64_t L, uint64_t linv,
-                          const RootTables &rt, const RootTables30 &rt30, int nsm, cudaStream_t st);
+                          const RootTables &rt, const RootTables30 &rt30, const RootTables25 &rt25, int nsm,
+                          cudaStream_t st);
 cudaError_t launch_pack(const uint8_t *par, uint64_t m, uint64_t *z, const uint32_t *pre,
                         uint32_t *status, int nsm, cudaStream_t st);
 cudaError_t launch_allsame(const uint64_t *x, uint64_t n, uint32_t *flags, int nsm, cudaStream_t st);
@@ -89,14 +97,28 @@ struct Plan {
     uint64_t lo;     // window start K - 1
     uint64_t scratch_bytes;
     uint32_t launches;
-    int field;       // kFieldGL or kFieldF30
+    int field;       // kFieldGL, kFieldF30 or kFieldF25
     bool summed;     // one of several products summed before one inverse transform
 };
 
+// Which fields a plan may take (cm_options.field):
+//   kFieldsAll -- F25 for transforms of length <= 2^25, F30 up to 2^30,
+//                 Goldilocks above;
+//   kFieldsQ30 -- F30 up to 2^30, Goldilocks above;
+//   kFieldsGL  -- Goldilocks throughout.
+constexpr int kFieldsAll = 0;
+constexpr int kFieldsQ30 = 1;
+constexpr int kFieldsGL = 2;
+// The field of a transform of length 2^lg under a field set.
+inline int field_for(int fields, int lg) {
+    if (fields == kFieldsAll && lg <= kF25MaxLg) return kFieldF25;
+    if (fields != kFieldsGL && lg <= kF30MaxLg) return kFieldF30;
+    return kFieldGL;
+}
+
 // Validate (kind, n, m) and fill the plan; false if invalid or if K + m - 1
-// exceeds 2^32 (one transform).
-// allow_f30: a transform of length <= 2^30 runs over the 32-bit field.
-bool make_plan(int kind, uint64_t n, uint64_t m, Plan *out, bool allow_f30 = false);
+// exceeds 2^32 (one transform).  fields: a field set (kFields*).
+bool make_plan(int kind, uint64_t n, uint64_t m, Plan *out, int fields = kFieldsGL);
 
 // Longest bit string a blocked extraction takes (the paper's 2^40).
 constexpr uint64_t kMaxBits = 1ull << 40;
@@ -135,16 +157,19 @@ struct Block {
 // blocks; output windows are independent), choosing among single transforms
 // and block shapes by an estimate of GPU time; shapes whose scratch exceeds
 // budget (0 = no limit) are taken only if none fits.  False if invalid.
-// allow_f30: products whose transform fits 2^30 run over the 32-bit field.
+// fields: the field set of the products (kFields*).
 struct PlanOptions {
     int max_lg = 32;          // longest transform of one product (log2), 8..32
-    bool allow_f30 = true;    // products of length <= 2^30 take the 32-bit field
+    int fields = kFieldsAll;  // F25 up to 2^25, F30 up to 2^30, Goldilocks above
     uint64_t budget = 0;      // scratch cap for choosing a shape (0 = none)
     uint32_t max_sum = 0;     // cap on blocks per sum group (0 = the field's bound)
     bool single = false;      // one transform whenever it fits (no cost-based split)
 };
 // PlanOptions from cm_options (NULL: defaults); false if a value is invalid.
 bool plan_options(const cm_options *opt, PlanOptions *o);
+// The work-list kernel of batches and the server runs over F30: its instances
+// are planned over F30 (Goldilocks in a Goldilocks-only context).
+inline int worklist_fields(const PlanOptions &o) { return o.fields == kFieldsGL ? kFieldsGL : kFieldsQ30; }
 bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::vector<Block> *out);
 
 // Estimated GPU time (ms) of a block list, from measured per-length times.

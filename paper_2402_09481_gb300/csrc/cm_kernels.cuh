@@ -11,7 +11,10 @@
 // Thm. convolution is taken in whatever order both operands share.
 //
 // Kernels:
-// Each kernel is a template over the field policy F (FieldGL, FieldF30).
+// Each kernel is a template over the field policy F (FieldGL, FieldF30,
+// FieldF25).  Over the lazily reduced F25, forward passes leave values in
+// [0, 2q), inverse passes and the middle any representative below 12 q; a
+// parity is read from the canonical value (F::canon).
 //
 //   k_fused_small<LG>  whole extraction for L <= 2^13 in one CTA: bit unpack,
 //                      forward NTT of both operands, product * L^-1, inverse NTT,
@@ -66,8 +69,8 @@ k_fused_small(BitMap amap, BitMap bmap, uint64_t lo, uint64_t m, uint64_t linv_,
     const uint64_t nwords = (m + 63) >> 6;
     for (uint64_t w = warp; w < nwords; w += kThreads / 32) {
         const uint64_t p0 = (w << 6) + lane, p1 = p0 + 32;
-        const uint32_t b0 = (p0 < m) ? (uint32_t)(sA[sp((int)(lo + p0))] & 1u) : 0u;
-        const uint32_t b1 = (p1 < m) ? (uint32_t)(sA[sp((int)(lo + p1))] & 1u) : 0u;
+        const uint32_t b0 = (p0 < m) ? (uint32_t)(F::canon(sA[sp((int)(lo + p0))]) & 1u) : 0u;
+        const uint32_t b1 = (p1 < m) ? (uint32_t)(F::canon(sA[sp((int)(lo + p1))]) & 1u) : 0u;
         const uint32_t w0 = __ballot_sync(0xffffffffu, b0);
         const uint32_t w1 = __ballot_sync(0xffffffffu, b1);
         if (lane == 0) z[w] = bad ? 0ull : ((uint64_t)w1 << 32 | w0);
@@ -190,7 +193,7 @@ k_pass(typename F::T *__restrict__ data1, BitMap map1, typename F::T *__restrict
 #pragma unroll
             for (int j = 0; j < VW; ++j) {
                 const uint64_t p = g + j - lo;
-                if (g + j >= lo && p < m) par[p] = (uint8_t)(v[j] & 1u);
+                if (g + j >= lo && p < m) par[p] = (uint8_t)(F::canon(v[j]) & 1u);
             }
         } else {
             *reinterpret_cast<uint4 *>(data + g) = pack16(v);

@@ -109,6 +109,7 @@ __global__ void k_allsame(const uint64_t *__restrict__ x, uint64_t n, uint32_t *
 }
 
 cudaError_t launch_pass(const PassArgs &a, int logr, cudaStream_t st) {
+    if (a.field == kFieldF25) return a.inv ? launch_pass_inv25(a, logr, st) : launch_pass_fwd25(a, logr, st);
     if (a.field == kFieldF30) return a.inv ? launch_pass_inv30(a, logr, st) : launch_pass_fwd30(a, logr, st);
     return a.inv ? launch_pass_inv(a, logr, st) : launch_pass_fwd(a, logr, st);
 }
@@ -130,7 +131,9 @@ static cudaError_t launch_middle_f(void *A, const void *B, void *C, int mode, ui
 }
 
 cudaError_t launch_middle(int field, void *A, const void *B, void *C, int mode, uint64_t L, uint64_t linv,
-                          const RootTables &rt, const RootTables30 &rt30, int nsm, cudaStream_t st) {
+                          const RootTables &rt, const RootTables30 &rt30, const RootTables25 &rt25, int nsm,
+                          cudaStream_t st) {
+    if (field == kFieldF25) return launch_middle_f<FieldF25>(A, B, C, mode, L, linv, rt25, nsm, st);
     return field == kFieldF30 ? launch_middle_f<FieldF30>(A, B, C, mode, L, linv, rt30, nsm, st)
                               : launch_middle_f<FieldGL>(A, B, C, mode, L, linv, rt, nsm, st);
 }
@@ -285,6 +288,38 @@ __global__ void k_field_selftest(uint64_t count, uint64_t seed, unsigned long lo
         n += f30_mont(a3, kF30Tw32[j]) != f30_mulmod(a3, wj);
         wj = f30_mulmod(wj, w32);
     }
+    // the lazily reduced field: values and ranges.  x is any 32-bit word (the
+    // representatives the kernels hold), c, d canonical, e, f in [0, 2q).
+    {
+        constexpr uint64_t Q = F25_Q;
+        constexpr uint32_t rinv25 = f25_pow(F25_R, F25_Q - 2);
+        const uint32_t ex[8] = {0u, 1u, F25_Q - 1, F25_Q, 2 * F25_Q - 1, 12 * F25_Q, 0x7FFFFFFFu, 0xFFFFFFFFu};
+        const uint32_t x = i < 64 ? ex[i % 8] : (uint32_t)(a >> 32);
+        const uint32_t c = i < 64 ? (uint32_t)(ex[i / 8] % Q) : (uint32_t)(b % Q);
+        const uint32_t d = (uint32_t)((a ^ b) % Q);
+        const uint32_t e = (uint32_t)(a % (2 * Q)), f = i < 64 ? (uint32_t)(ex[i / 8] % (2 * Q)) : (uint32_t)(b % (2 * Q));
+        const uint32_t r = f25_red(x), k = f25_canon(x);
+        n += r >= 2 * Q || r % Q != x % Q;
+        n += k != x % Q;
+        const uint32_t ad = f25_add(e, f), sb = f25_sub(e, f);
+        n += ad >= 2 * Q || ad % Q != (e + (uint64_t)f) % Q;
+        n += sb >= 2 * Q || sb % Q != (e % Q + Q - f % Q) % Q;
+        const uint32_t mo = f25_mont(x, c);  // any x, canonical root
+        n += mo == 0 || mo >= 2 * Q || mo % Q != f25_mulmod(f25_mulmod((uint32_t)(x % Q), c), rinv25);
+        if (x < 0x80000000u) {  // x < 2^31, root in [0, 2q)
+            const uint32_t m2 = f25_mont(x, f);
+            n += m2 >= 2 * Q || m2 % Q != f25_mulmod(f25_mulmod((uint32_t)(x % Q), (uint32_t)(f % Q)), rinv25);
+        }
+        const uint32_t sh = f25_shoup(x, d, f25_shoup_q(d));
+        n += sh >= 2 * Q || sh % Q != f25_mulmod((uint32_t)(x % Q), d);
+        const uint32_t w25 = f25_pow(F25_G25, 1ull << 20);
+        uint32_t wk = 1;
+        for (int j = 0; j < 32; ++j) {
+            const uint32_t t = f25_shoup(x, kF25W32[j], kF25W32Q[j]);
+            n += t >= 2 * Q || t % Q != f25_mulmod((uint32_t)(x % Q), wk);
+            wk = f25_mulmod(wk, w25);
+        }
+    }
     if (n) atomicAdd(bad, n);
 }
 
@@ -341,11 +376,13 @@ static cm_status modmul_rate(int nsm, typename F::T w, double *rate) {
 }  // namespace cm
 
 extern "C" cm_status cm_modmul_rate(int device, uint32_t field, double *per_second) {
-    if (!per_second || (field != CM_FIELD_GOLDILOCKS && field != CM_FIELD_Q30)) return CM_EINVAL;
+    if (!per_second || (field != CM_FIELD_GOLDILOCKS && field != CM_FIELD_Q30 && field != CM_FIELD_Q25))
+        return CM_EINVAL;
     if (cudaSetDevice(device) != cudaSuccess) return CM_EDEVICE;
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return CM_EDEVICE;
     if (field == CM_FIELD_Q30) return cm::modmul_rate<cm::FieldF30>(nsm, f30_to_mont(12345u), per_second);
+    if (field == CM_FIELD_Q25) return cm::modmul_rate<cm::FieldF25>(nsm, f25_to_mont(12345u), per_second);
     return cm::modmul_rate<cm::FieldGL>(nsm, 0x123456789ABCDEFull, per_second);
 }
 

@@ -15,6 +15,8 @@ template <>
 inline const RootTables &pass_tables<FieldGL>(const PassArgs &a) { return a.rt; }
 template <>
 inline const RootTables30 &pass_tables<FieldF30>(const PassArgs &a) { return a.rt30; }
+template <>
+inline const RootTables25 &pass_tables<FieldF25>(const PassArgs &a) { return a.rt25; }
 
 template <class F, int LOGR, bool INV, bool BITS_IN, bool PARITY_OUT>
 static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st) {

@@ -18,6 +18,7 @@ static cudaError_t launch_small_f(const Launch &q, const RootTablesT<typename F:
 
 template <int LG>
 static cudaError_t launch_small_lg(const Launch &q) {
+    if (q.field == kFieldF25) return launch_small_f<FieldF25, LG>(q, q.rt25);
     return q.field == kFieldF30 ? launch_small_f<FieldF30, LG>(q, q.rt30) : launch_small_f<FieldGL, LG>(q, q.rt);
 }
 

@@ -136,6 +136,7 @@ extern "C" cm_status cm_toeplitz_noalloc(const uint64_t *x, uint64_t n, const ui
         q.field = kFieldGL;
         q.rt = rt;
         q.rt30 = RootTables30{};
+        q.rt25 = RootTables25{};
         q.stream = st;
         return status_of(launch_small(q, p.lg));
     }
@@ -158,7 +159,8 @@ extern "C" cm_status cm_toeplitz_noalloc(const uint64_t *x, uint64_t n, const ui
         a.bits_in = true;
         if ((s = status_of(launch_pass(a, p.pass_lg[0], st))) != CM_OK) return s;
     }
-    if ((s = status_of(launch_middle(kFieldGL, A, B, nullptr, kMidAlone, p.L, linv, rt, RootTables30{}, d->nsm, st))) != CM_OK)
+    if ((s = status_of(launch_middle(kFieldGL, A, B, nullptr, kMidAlone, p.L, linv, rt, RootTables30{}, RootTables25{},
+                                         d->nsm, st))) != CM_OK)
         return s;
     PassArgs a = {};
     a.data = A;

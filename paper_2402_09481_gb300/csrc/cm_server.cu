@@ -485,7 +485,7 @@ extern "C" cm_status cm_submit(cm_ctx *ctx, const cm_request *rq, uint64_t *tick
     r.flags = rq->flags;
     r.seed_id = rq->seed_id;
     if (rq->flags & ~CM_REQ_SEED_CACHE) return CM_EINVAL;
-    if (!rq->x || !rq->y || !rq->z || !make_plan(rq->kind, rq->n, rq->m, &r.p, ctx->popt.allow_f30)) return CM_EINVAL;
+    if (!rq->x || !rq->y || !rq->z || !make_plan(rq->kind, rq->n, rq->m, &r.p, worklist_fields(ctx->popt))) return CM_EINVAL;
     if (r.p.npass > 1) {
         // too long for the work list: the single-call planner (sums of shorter
         // products, a dense tail) within the server's budget

@@ -9,6 +9,7 @@
 // are read out of the packed input bits (see BitMap).
 #pragma once
 #include <stdint.h>
+#include "f25.cuh"
 #include "f30.cuh"
 #include "gl.cuh"
 
@@ -31,7 +32,8 @@ __host__ __device__ constexpr int sp_size(int n) { return n + (n >> 5) + 1; }
 
 // Resident root tables of one field (element type T).  Goldilocks: g of order
 // 2^32, 2^16-entry halves; F30: g of order 2^30, 2^15-entry halves, entries in
-// Montgomery form.
+// Montgomery form; F25: g of order 2^25, halves of 2^13 (low) and 2^12 (high)
+// entries, Montgomery form.
 template <class T>
 struct RootTablesT {
     const T *small;       // omega_{8192}^e,  e < 8192
@@ -46,6 +48,7 @@ struct RootTablesT {
 };
 using RootTables = RootTablesT<uint64_t>;
 using RootTables30 = RootTablesT<uint32_t>;
+using RootTables25 = RootTablesT<uint32_t>;
 
 // ---------------------------------------------------------------------------
 // Field policies.  Every transform below is written once over a policy F:
@@ -53,10 +56,19 @@ using RootTables30 = RootTablesT<uint32_t>;
 //              the root of order 64 is 8 = 2^3, so register sub-transforms
 //              twiddle by shifts;
 //   FieldF30 -- q = 3 * 2^30 + 1 (the paper's small field), 32-bit words,
-//              L <= 2^30; Montgomery products with constant twiddles.
+//              L <= 2^30; Montgomery products with constant twiddles;
+//   FieldF25 -- q = 5 * 2^25 + 1, 32-bit words, L <= 2^25, lazy reduction
+//              (f25.cuh): values between steps are any representative below
+//              12 q (< 2^31), every on-chip step brings its inputs to [0, 2q)
+//              (by its twiddle product or red) and its butterflies skip the
+//              compare-and-select of a canonical field.
+// Every policy has red (to the representative the next DFT accepts) and canon
+// (to [0, q), before a parity is read); both are the identity for the
+// canonical fields.
 // ---------------------------------------------------------------------------
 struct FieldGL {
     using T = uint64_t;
+    static constexpr bool kLazy = false;
     static constexpr int kAdicity = 32;
     static constexpr int kBigLg = 16;
     // columns of a column-pass tile of 2^LOGR rows: 2^14 elements (32-byte rows
@@ -68,10 +80,13 @@ struct FieldGL {
     // x omega_{2h}^pos, h = 2^lh <= 16: omega_{2h} = 2^(96 / h)
     __device__ static __forceinline__ T rot(T x, int lh, int pos) { return gl_shl(x, (96 >> lh) * pos); }
     __device__ static __forceinline__ T prod(T a, T b, T linv) { return gl_mul(gl_mul(a, b), linv); }
+    __device__ static __forceinline__ T red(T x) { return x; }
+    __device__ static __forceinline__ T canon(T x) { return x; }
 };
 
 struct FieldF30 {
     using T = uint32_t;
+    static constexpr bool kLazy = false;
     static constexpr int kAdicity = 30;
     static constexpr int kBigLg = 15;
     // 2^14-element tiles (64 KiB), so that two CTAs fit on an SM
@@ -83,6 +98,29 @@ struct FieldF30 {
         return pos == 0 ? x : f30_mont(x, kF30Tw32[(16 >> lh) * pos]);
     }
     __device__ static __forceinline__ T prod(T a, T b, T linv) { return f30_mont(f30_mont(a, b), linv); }
+    __device__ static __forceinline__ T red(T x) { return x; }
+    __device__ static __forceinline__ T canon(T x) { return x; }
+};
+
+struct FieldF25 {
+    using T = uint32_t;
+    static constexpr bool kLazy = true;
+    static constexpr int kAdicity = 25;
+    static constexpr int kBigLg = 13;
+    static constexpr int ncol_lg(int logr) { return kTileLg - logr; }
+    // a, b in [0, 2q) -> [0, 2q)
+    __device__ static __forceinline__ T add(T a, T b) { return f25_add(a, b); }
+    __device__ static __forceinline__ T sub(T a, T b) { return f25_sub(a, b); }
+    // x w for any x < 2^31 and a table root w < 2q (canonical roots: any x) -> (0, 2q)
+    __device__ static __forceinline__ T twmul(T x, T w) { return f25_mont(x, w); }
+    // x omega_{2h}^pos, h = 2^lh <= 16 (Shoup product with a constant root) -> [0, 2q)
+    __device__ static __forceinline__ T rot(T x, int lh, int pos) {
+        return pos == 0 ? f25_red(x) : f25_shoup(x, kF25W32[(16 >> lh) * pos], kF25W32Q[(16 >> lh) * pos]);
+    }
+    // a b L^-1 for any a and b < 12 q (a DFT output) -> (0, 2q)
+    __device__ static __forceinline__ T prod(T a, T b, T linv) { return f25_mont(f25_mont(f25_red(a), b), linv); }
+    __device__ static __forceinline__ T red(T x) { return f25_red(x); }
+    __device__ static __forceinline__ T canon(T x) { return f25_canon(x); }
 };
 
 // 16 bytes as 2 x 64-bit or 4 x 32-bit elements, and back.
@@ -215,10 +253,53 @@ __device__ __forceinline__ int bitrev_c(int k, int lg) {
     return r;
 }
 
+// In-register DFT of length 2^LQ <= 32 over F25 with lazy reduction: natural
+// order in, v[bitrev(k)] = X[k] out, like dft_reg_f.  Cooley-Tukey butterflies
+// on natural-order input: stage s (half-length len = RD / 2^(s+1)) splits each
+// residue of the input polynomial modulo X^(2 len) - zeta^2 into the residues
+// modulo X^len - zeta and X^len + zeta, (lo, hi) -> (lo + zeta hi, lo - zeta hi),
+// where block b of the stage has zeta = omega_(2^(s+1))^bitrev_s(b); after the
+// last stage position b holds the residue modulo X - omega^bitrev(b), i.e.
+// X[bitrev(b)].  Inputs in [0, 2q); the first stage (zeta = 1) doubles the
+// bound to 4q, every later one adds 2q (t = zeta hi is brought to [0, 2q) by the
+// Shoup product, or by red when zeta = 1): outputs below (2 + 2 LQ) q <= 12 q.
+template <int LQ>
+__device__ __forceinline__ void dft_reg_f25(uint32_t *v) {
+    constexpr int RD = 1 << LQ;
+    static_assert(LQ >= 1 && LQ <= 5, "register sub-transforms of length 2 .. 32");
+#pragma unroll
+    for (int s = 0; s < LQ; ++s) {
+        const int len = RD >> (s + 1);
+#pragma unroll
+        for (int b = 0; b < (1 << s); ++b) {
+            const int e = (32 >> (s + 1)) * bitrev_c(b, s);  // zeta = omega_32^e
+#pragma unroll
+            for (int j = 0; j < len; ++j) {
+                const int i0 = b * 2 * len + j, i1 = i0 + len;
+                const uint32_t x = v[i0], y = v[i1];
+                uint32_t t;
+                if (s == 0) {
+                    t = y;
+                } else if (b == 0) {
+                    t = f25_red(y);
+                } else {
+                    t = f25_shoup(y, kF25W32[e], kF25W32Q[e]);
+                }
+                v[i0] = x + t;
+                v[i1] = x - t + 2 * F25_Q;
+            }
+        }
+    }
+}
+
 // In-register DFT of length 2^LQ <= 32 (Goldilocks: omega = 2^(192 / 2^LQ)):
 // natural order in, v[bitrev(k)] = X[k] out.
 template <class F, int LQ>
 __device__ __forceinline__ void dft_reg_f(typename F::T *v) {
+    if constexpr (F::kLazy) {
+        dft_reg_f25<LQ>(v);
+        return;
+    }
     constexpr int RD = 1 << LQ;
     // one flat loop with a constant trip count, so that every index and shift
     // below is a compile-time constant after unrolling
@@ -279,7 +360,11 @@ __device__ __forceinline__ void fwd_step_f(typename F::T *s0, typename F::T *s1,
 #pragma unroll
         for (int k1 = 0; k1 < RD; ++k1) {
             T x = v[bitrev_c(k1, LQ)];
-            if (LM > 0 && k1 > 0 && i2 > 0) x = F::twmul(x, tw[tw_swz((i2 * k1) << OFF)]);
+            if (LM > 0 && k1 > 0 && i2 > 0) {
+                x = F::twmul(x, tw[tw_swz((i2 * k1) << OFF)]);
+            } else {
+                x = F::red(x);
+            }
             s[sp(((row0 + (k1 << LM)) << NCOL_LG) + c)] = x;
         }
     }
@@ -309,7 +394,11 @@ __device__ __forceinline__ void inv_step_f(typename F::T *s0, typename F::T *s1,
 #pragma unroll
         for (int k1 = 0; k1 < RD; ++k1) {
             T x = s[sp(((row0 + (k1 << LM)) << NCOL_LG) + c)];
-            if (LM > 0 && k1 > 0 && i2 > 0) x = F::twmul(x, tw[tw_swz((R - ((i2 * k1) << OFF)) & (R - 1))]);
+            if (LM > 0 && k1 > 0 && i2 > 0) {
+                x = F::twmul(x, tw[tw_swz((R - ((i2 * k1) << OFF)) & (R - 1))]);
+            } else {
+                x = F::red(x);
+            }
             v[k1] = x;
         }
         dft_reg_f<F, LQ>(v);

@@ -86,7 +86,7 @@ TREVISAN = 3
 MODEL_SEEDED, MODEL_PRODUCT, MODEL_MARKOV = 0, 1, 2
 ADV_CLASSICAL, ADV_QUANTUM = 0, 1
 ADJUST_UP, ADJUST_DOWN, ADJUST_CLOSEST = 0, 1, 2
-FIELD_AUTO, FIELD_GOLDILOCKS, FIELD_Q30 = 0, 1, 2
+FIELD_AUTO, FIELD_GOLDILOCKS, FIELD_Q30, FIELD_Q25 = 0, 1, 2, 3
 PLAN_COST, PLAN_SINGLE = 0, 1
 
 

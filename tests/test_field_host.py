@@ -5,7 +5,9 @@ Goldilocks (csrc/gl.cuh) against 128-bit integer arithmetic: add, sub, the
 and the root structure (g of order 2^32 with g^(2^26) = 8, L^-1).  The 32-bit
 field of q = 3 * 2^30 + 1 (csrc/f30.cuh) against plain 64-bit modular
 arithmetic: primality, the generator and the root of order 2^30, add, sub, the
-Montgomery product, the sub-transform twiddles and the L^-1 constant."""
+Montgomery product, the sub-transform twiddles and the L^-1 constant.  The
+lazily reduced field of q = 5 * 2^25 + 1 (csrc/f25.cuh) likewise, with the
+value ranges its kernels rely on, and its register DFT modelled step for step."""
 
 import os
 import subprocess
@@ -36,6 +38,59 @@ def test_field30_routines(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "field30_check: ok" in r.stdout
+
+
+def test_field25_routines(tmp_path):
+    exe = tmp_path / "field25_check"
+    r = subprocess.run(["g++", "-O2", "-std=c++17", f"-I{CSRC}", os.path.join(HERE, "field25_check.cpp"),
+                        "-o", str(exe)], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.fail(r.stderr)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "field25_check: ok" in r.stdout
+
+
+def test_lazy_radix_dft_model():
+    # The register sub-transform of the lazily reduced field (dft_reg_f25):
+    # Cooley-Tukey butterflies on natural-order input, stage s splitting block
+    # b with zeta = omega_(2^(s+1))^bitrev_s(b), give X[k] at position
+    # bitrev(k), and from inputs in [0, 2q) every intermediate stays below
+    # (2 + 2 LQ) q < 2^32.  Modelled step for step with exact integers.
+    import random
+    q = 5 * 2 ** 25 + 1
+    w32 = pow(243, 2 ** 20, q)
+    mu = 2 ** 32 // q
+
+    def red(x):
+        return x - ((x * mu) >> 32) * q
+
+    def shoup(x, w):
+        return (x * w - ((x * ((w << 32) // q)) >> 32) * q) % 2 ** 32
+
+    def brv(k, lg):
+        return int(format(k, f"0{lg}b")[::-1], 2) if lg else 0
+
+    rng = random.Random(25)
+    for lq in range(1, 6):
+        rd = 1 << lq
+        wr = pow(w32, 32 // rd, q)
+        for _ in range(300):
+            v = [rng.choice([0, 1, q, 2 * q - 1, rng.randrange(2 * q)]) for _ in range(rd)]
+            x = list(v)
+            for s in range(lq):
+                ln = rd >> (s + 1)
+                for b in range(1 << s):
+                    zeta = pow(w32, (32 >> (s + 1)) * brv(b, s), q)
+                    for j in range(ln):
+                        i0 = b * 2 * ln + j
+                        i1 = i0 + ln
+                        t = v[i1] if s == 0 else (red(v[i1]) if b == 0 else shoup(v[i1], zeta))
+                        assert t < 2 * q or s == 0
+                        v[i0], v[i1] = v[i0] + t, v[i0] - t + 2 * q
+                        assert 0 <= v[i1] and max(v[i0], v[i1]) < (2 + 2 * (s + 1)) * q < 2 ** 32
+            for k in range(rd):
+                assert v[brv(k, lq)] % q == sum(x[j] * pow(wr, j * k, q) for j in range(rd)) % q
 
 
 def test_radix16_bit_table_identity():

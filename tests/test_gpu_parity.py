@@ -201,8 +201,9 @@ def test_modmul_rate(cm_ctx):
     # 32-bit Montgomery product (3 multiply-adds) faster than the Goldilocks
     # product (a 64 x 64-bit multiply in 32-bit pieces and its reduction)
     q30 = native.modmul_rate(0, native.FIELD_Q30)
+    q25 = native.modmul_rate(0, native.FIELD_Q25)
     gl = native.modmul_rate(0, native.FIELD_GOLDILOCKS)
-    assert 1e11 < gl < q30 < 1e14
+    assert 1e11 < gl < q30 < 1e14 and 1e11 < q25 < 1e14
     with pytest.raises(native.CMError):
         native.modmul_rate(0, 7)
 
@@ -214,9 +215,10 @@ def test_field_selftest_device_arithmetic(cm_ctx):
 
 
 # --------------------------------------------------------------------------- #
-# The single calls take the 32-bit field of 3 * 2^30 + 1 for transforms up to
-# 2^30 and Goldilocks above; a context with CM_FIELD_GOLDILOCKS keeps the
-# 64-bit field at every length.  Both must give the oracle's bits.
+# The single calls take the lazily reduced field of 5 * 2^25 + 1 for transforms
+# up to 2^25, the field of 3 * 2^30 + 1 up to 2^30 and Goldilocks above; a
+# context with CM_FIELD_Q30 skips the first, one with CM_FIELD_GOLDILOCKS keeps
+# the 64-bit field at every length.  All must give the oracle's bits.
 @pytest.fixture(scope="module")
 def gl_ctx():
     from paper_2402_09481_gb300 import build
@@ -226,12 +228,23 @@ def gl_ctx():
     c.close()
 
 
+@pytest.fixture(scope="module")
+def q30_ctx():
+    from paper_2402_09481_gb300 import build
+    build.build()
+    c = native.Context(0, field=native.FIELD_Q30)
+    yield c
+    c.close()
+
+
 @pytest.mark.parametrize("kind,n,m", [
     (native.TOEPLITZ, 5, 3), (native.TOEPLITZ, 5000, 4000), (native.TOEPLITZ, 100000, 31073),
-    (native.TOEPLITZ, 2 ** 20, 2 ** 19 + 3),
+    (native.TOEPLITZ, 2 ** 20, 2 ** 19 + 3), (native.TOEPLITZ, 8193, 8192), (native.TOEPLITZ, 2 ** 24, 2 ** 24),
+    (native.TOEPLITZ, 9_000_001, 777_777),
     (native.CIRCULANT, "P131101", 0.5), (native.DODIS, "P40000", 0.4), (native.DODIS, "P3000", 0.9),
+    (native.CIRCULANT, "P16777259", 0.5),
 ])
-def test_both_fields_match_oracle(gl_ctx, cm_ctx, kind, n, m):
+def test_all_fields_match_oracle(gl_ctx, q30_ctx, cm_ctx, kind, n, m):
     if isinstance(n, str):
         P = oracle.next_na(int(n[1:]))
         n = P - 1 if kind == native.CIRCULANT else P
@@ -242,7 +255,7 @@ def test_both_fields_match_oracle(gl_ctx, cm_ctx, kind, n, m):
     yb = n + m - 1 if kind == native.TOEPLITZ else (n + 1 if kind == native.CIRCULANT else n)
     yw = inputs.bernoulli_half(701 + n % 83, yb)
     outs = []
-    for ctx in (gl_ctx, cm_ctx):
+    for ctx in (gl_ctx, q30_ctx, cm_ctx):
         x, y = to_dev(xw), to_dev(yw)
         if kind == native.TOEPLITZ:
             z = ctx.toeplitz(x, n, y, m)
@@ -258,5 +271,11 @@ def test_both_fields_match_oracle(gl_ctx, cm_ctx, kind, n, m):
         assert (outs[0] == want).all()
     else:
         rows = sample_rows(m)
-        assert (out_bits(outs[0], m, rows) == oracle.toeplitz_rows(xw, n, yw, m, rows)).all()
-    assert (outs[0] == outs[1]).all()
+        got = out_bits(outs[0], m, rows)
+        if kind == native.TOEPLITZ:
+            assert (got == oracle.toeplitz_rows(xw, n, yw, m, rows)).all()
+        elif kind == native.CIRCULANT:
+            assert (got == oracle.circulant_rows(xw, n, yw, m, rows)).all()
+        else:
+            assert (got == oracle.dodis_rows(xw, yw, n, m, rows)).all()
+    assert (outs[0] == outs[1]).all() and (outs[0] == outs[2]).all()

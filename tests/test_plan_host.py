@@ -6,7 +6,8 @@ products are summed (sum groups) or XORed.  These tests need no GPU:
 
 - structure: windows tile [0, m) in order, input blocks tile the K terms, the
   products of a sum group share K, m and L, the window fits its transform, and
-  no group can hold a count at or above the 32-bit field's prime;
+  no group can hold a count at or above its 32-bit field's prime (3 * 2^30 + 1
+  or 5 * 2^25 + 1);
 - value: the listed products, evaluated exactly in numpy (maps as the header
   defines them, cyclic convolution of length L, window K - 1 .. K + m - 2,
   sums taken modulo the product's field, parity, XOR) give the oracle's
@@ -23,6 +24,8 @@ from paper_2402_09481_gb300 import inputs, native
 
 T, C, D = native.TOEPLITZ, native.CIRCULANT, native.DODIS
 Q30 = 3 * 2 ** 30 + 1
+Q25 = 5 * 2 ** 25 + 1
+PRIME = {native.FIELD_Q30: Q30, native.FIELD_Q25: Q25}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -87,7 +90,7 @@ def emulate(kind, n, m, xw, yw, prods):
         acc = win.copy() if p["sum"] in (0, 1) else acc + win
         if p["sum"] in (0, 3):
             # Goldilocks: every count (< 2^40) is below the prime, nothing wraps
-            s = acc % Q30 if p["field"] == native.FIELD_Q30 else acc
+            s = acc % PRIME[p["field"]] if p["field"] in PRIME else acc
             par = (s & 1).astype(np.uint8)
             lo = p["zword"] * 64
             if p["xor_into"]:
@@ -143,6 +146,8 @@ def check_structure(kind, n, m, prods):
             assert g0["K"] - 1 + mr <= g0["L"]
             if g0["field"] == native.FIELD_Q30:
                 assert g0["L"] <= 2 ** 30 and len(grp) * g0["K"] < Q30
+            if g0["field"] == native.FIELD_Q25:
+                assert g0["L"] <= 2 ** 25 and len(grp) * g0["K"] < Q25
             assert grp[-1]["xor_into"] == (0 if first_group else 1)
             assert all(g["xor_into"] == 0 for g in grp[:-1])
             first_group = False
@@ -276,7 +281,7 @@ def random_cases(count, seed=2402):
         m = int(rng.integers(1, (20_000 if kind == T else n) + 1))
         opts = dict(max_transform_lg=int(rng.choice([8, 10, 12, 14, 15, 16])),
                     max_sum_blocks=int(rng.choice([0, 2, 3])),
-                    field=int(rng.choice([native.FIELD_AUTO, native.FIELD_GOLDILOCKS])))
+                    field=int(rng.choice([native.FIELD_AUTO, native.FIELD_GOLDILOCKS, native.FIELD_Q30])))
         try:
             prods = native.plan_products(kind, n, m, **opts)
         except native.CMError:  # more than 65536 products at the smallest limits
