@@ -9,6 +9,7 @@
 #include "cm.h"
 #include "cm_internal.h"
 #include "cm_ctx.h"
+#include "ntt25.cuh"
 
 namespace cm {
 
@@ -712,6 +713,17 @@ static void build_tables25(std::vector<uint32_t> &h) {
                 if ((p >> j) & 1) acc += f25_pow(w16, (uint64_t)((j * k) & 15));
             b16[k * 256 + p] = (uint32_t)(acc % F25_Q);
         }
+    // per-step tables (ntt25.cuh): length 2^l at word 2^l, step J's roots
+    // omega_(N_J)^(i2 k1) at [(k1 - 1) M_J + i2]
+    uint32_t *steps = b16 + 4096;
+    for (int l = 1; l <= kSmallLg; ++l)
+        for (int j = 0; j + 1 < st_n(l); ++j) {
+            const int lq = st_q(l, j), rd = 1 << lq, lnj = l - st_off(l, j), mj = 1 << (lnj - lq);
+            const uint32_t wn = f25_pow(F25_G25, 1ull << (kF25MaxLg - lnj));  // omega_(N_J)
+            uint32_t *t = steps + (1 << l) + st25_tab_off(l, j);
+            for (int k1 = 1; k1 < rd; ++k1)
+                for (int i2 = 0; i2 < mj; ++i2) t[(k1 - 1) * mj + i2] = f25_to_mont(f25_pow(wn, (uint64_t)i2 * k1));
+        }
 }
 
 }  // namespace cm
@@ -771,6 +783,7 @@ extern "C" cm_status cm_create(cm_ctx **out, int device, const cm_options *opt) 
     c->rt25.big_lo_inv = c->rt25.big_hi_fwd + 4096;
     c->rt25.big_hi_inv = c->rt25.big_lo_inv + 8192;
     c->rt25.bits16 = c->rt25.big_hi_inv + 4096;
+    c->rt25.steps = c->rt25.bits16 + 4096;
     c->rt30.small = c->d_tables30;
     c->rt30.big_lo_fwd = c->d_tables30 + 8192;
     c->rt30.big_hi_fwd = c->rt30.big_lo_fwd + 32768;

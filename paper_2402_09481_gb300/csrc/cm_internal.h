@@ -21,7 +21,8 @@ constexpr int kFieldF25 = 2;  // 5 * 2^25 + 1, 32-bit elements, L <= 2^25, lazy 
 constexpr int kF30MaxLg = 30;
 constexpr int kF25MaxLg = 25;
 constexpr size_t kTable30Words = 8192 + 4 * 32768 + 4096;  // resident F30 root tables + bit DFT table
-constexpr size_t kTable25Words = 8192 + 2 * 8192 + 2 * 4096 + 4096;  // F25 root tables + bit DFT table
+// F25 root tables + bit DFT table + per-step tables of every on-chip length
+constexpr size_t kTable25Words = 8192 + 2 * 8192 + 2 * 4096 + 4096 + 16384;
 
 // Arguments of the single-CTA extraction (L <= 2^13).
 struct Launch {
@@ -64,6 +65,11 @@ cudaError_t launch_pass_fwd30(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_inv30(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_fwd25(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_inv25(const PassArgs &a, int logr, cudaStream_t st);
+// F25 passes: the fused column-pass kernels (cm_pass25.cu) for the single pass
+// of a transform of 2^22 .. 2^25, else the generic k_pass.
+cudaError_t launch_pass25(const PassArgs &a, int logr, cudaStream_t st);
+cudaError_t launch_middle25(void *A, const void *B, void *C, int mode, uint64_t L, uint64_t linv,
+                            const RootTables25 &rt, int nsm, cudaStream_t st);
 // A, B: L elements of the field's word size.  C null: the product's
 // row-transformed result goes to A.  Otherwise mode (MidSum) sums the scaled
 // transform-domain products of a sum group in C (L elements): kMidFirst

@@ -32,6 +32,7 @@
 #include <stdint.h>
 
 #include "cm_internal.h"
+#include "ntt25.cuh"
 #include "ntt_device.cuh"
 
 namespace cm {
@@ -51,16 +52,28 @@ k_fused_small(BitMap amap, BitMap bmap, uint64_t lo, uint64_t m, uint64_t linv_,
     T *sA = reinterpret_cast<T *>(smem_raw);
     T *sB = sA + sp_size(L);
     T *tw = sB + sp_size(L);
-    load_roots<LG>(tw, rt.small);
+    if constexpr (F::kLazy)
+        load_steps25<LG>(tw, rt.steps);
+    else
+        load_roots<LG>(tw, rt.small);
     for (int i = threadIdx.x; i < L; i += kThreads) {
         sA[sp(i)] = (T)amap.get(i);
         sB[sp(i)] = (T)bmap.get(i);
     }
     __syncthreads();
-    ntt_fwd_f<F, LG, 0, 2>(sA, sB, tw);
-    for (int i = threadIdx.x; i < L; i += kThreads) sA[sp(i)] = F::prod(sA[sp(i)], sB[sp(i)], linv);
-    __syncthreads();
-    ntt_inv_f<F, LG, 0, 1>(sA, sA, tw);
+    if constexpr (F::kLazy) {
+        ntt_fwd25<LG, 0, 2>(sA, sB, tw);
+        for (int i = threadIdx.x; i < L; i += kThreads) sA[sp(i)] = prod25(sA[sp(i)], sB[sp(i)], linv);
+        __syncthreads();
+        ntt_inv25<LG, 0, 1>(sA, sA, tw);
+    } else {
+        ntt_fwd_f<F, LG, 0, 2>(sA, sB, tw);
+        for (int i = threadIdx.x; i < L; i += kThreads) sA[sp(i)] = F::prod(sA[sp(i)], sB[sp(i)], linv);
+        __syncthreads();
+        ntt_inv_f<F, LG, 0, 1>(sA, sA, tw);
+    }
+    // F25's inverse leaves coefficient n at position (L - n) mod L
+    auto at = [](uint64_t n) { return F::kLazy ? (int)((L - n) & (L - 1)) : (int)n; };
 
     const bool bad = pre && (pre[0] == 0u || pre[1] == 0u);
     if (bad && threadIdx.x == 0) atomicOr(status, kFlagPrecond);
@@ -69,8 +82,8 @@ k_fused_small(BitMap amap, BitMap bmap, uint64_t lo, uint64_t m, uint64_t linv_,
     const uint64_t nwords = (m + 63) >> 6;
     for (uint64_t w = warp; w < nwords; w += kThreads / 32) {
         const uint64_t p0 = (w << 6) + lane, p1 = p0 + 32;
-        const uint32_t b0 = (p0 < m) ? (uint32_t)(F::canon(sA[sp((int)(lo + p0))]) & 1u) : 0u;
-        const uint32_t b1 = (p1 < m) ? (uint32_t)(F::canon(sA[sp((int)(lo + p1))]) & 1u) : 0u;
+        const uint32_t b0 = (p0 < m) ? (uint32_t)(F::canon(sA[sp(at(lo + p0))]) & 1u) : 0u;
+        const uint32_t b1 = (p1 < m) ? (uint32_t)(F::canon(sA[sp(at(lo + p1))]) & 1u) : 0u;
         const uint32_t w0 = __ballot_sync(0xffffffffu, b0);
         const uint32_t w1 = __ballot_sync(0xffffffffu, b1);
         if (lane == 0) z[w] = bad ? 0ull : ((uint64_t)w1 << 32 | w0);
@@ -133,7 +146,10 @@ k_pass(typename F::T *__restrict__ data1, BitMap map1, typename F::T *__restrict
     extern __shared__ __align__(16) uint8_t smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);
     T *tw = smem + sp_size(R * C);
-    load_roots<LOGR>(tw, rt.small);
+    if constexpr (F::kLazy)
+        load_steps25<LOGR>(tw, rt.steps);
+    else
+        load_roots<LOGR>(tw, rt.small);
     constexpr bool BTAB = pass_bits_table<F, LOGR, INV, BITS_IN>();
     T *tab = smem + pass_table_off<F, LOGR>();
     if constexpr (BTAB) {
@@ -170,12 +186,23 @@ k_pass(typename F::T *__restrict__ data1, BitMap map1, typename F::T *__restrict
         } else {
             unpack16(*reinterpret_cast<const uint4 *>(data + g), v);
         }
-        if (INV) row_twiddle<F, VW>(v, pos_to_freq<LOGR>(i), col0 + c, esh, rt.big_lo_inv, rt.big_hi_inv);
+        // F25's inverse takes every root inverted: the forward row roots
+        if (INV) {
+            if constexpr (F::kLazy)
+                row_twiddle<F, VW>(v, pos_to_freq<LOGR>(i), col0 + c, esh, rt.big_lo_fwd, rt.big_hi_fwd);
+            else
+                row_twiddle<F, VW>(v, pos_to_freq<LOGR>(i), col0 + c, esh, rt.big_lo_inv, rt.big_hi_inv);
+        }
 #pragma unroll
         for (int j = 0; j < VW; ++j) smem[sp(e0 + j)] = v[j];
     }
     __syncthreads();
-    if (INV) {
+    if constexpr (F::kLazy) {
+        if constexpr (INV)
+            ntt_inv25<LOGR, NCOL_LG, 1>(smem, smem, tw);
+        else
+            ntt_fwd25<LOGR, NCOL_LG, 1, BTAB>(smem, smem, tw, tab);
+    } else if (INV) {
         ntt_inv_f<F, LOGR, NCOL_LG, 1>(smem, smem, tw);
     } else {
         ntt_fwd_f<F, LOGR, NCOL_LG, 1, BTAB>(smem, smem, tw, tab);
@@ -190,10 +217,14 @@ k_pass(typename F::T *__restrict__ data1, BitMap map1, typename F::T *__restrict
         for (int j = 0; j < VW; ++j) v[j] = smem[sp(e0 + j)];
         if (!INV) row_twiddle<F, VW>(v, pos_to_freq<LOGR>(i), col0 + c, esh, rt.big_lo_fwd, rt.big_hi_fwd);
         if (PARITY_OUT) {
+            // F25: position g holds coefficient (L - g) mod L, L = 2^lgN (this
+            // pass is the transform's first)
+            const uint64_t lmask = (1ull << lgN) - 1;
 #pragma unroll
             for (int j = 0; j < VW; ++j) {
-                const uint64_t p = g + j - lo;
-                if (g + j >= lo && p < m) par[p] = (uint8_t)(F::canon(v[j]) & 1u);
+                const uint64_t n = F::kLazy ? ((lmask + 1 - (g + j)) & lmask) : g + j;
+                const uint64_t p = n - lo;
+                if (n >= lo && p < m) par[p] = (uint8_t)(F::canon(v[j]) & 1u);
             }
         } else {
             *reinterpret_cast<uint4 *>(data + g) = pack16(v);

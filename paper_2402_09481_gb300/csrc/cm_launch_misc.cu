@@ -22,7 +22,10 @@ k_middle(typename F::T *__restrict__ A, const typename F::T *__restrict__ Bv, ty
     T *sA = reinterpret_cast<T *>(smem_raw);
     T *sB = sA + sp_size(Bn);
     T *tw = sB + sp_size(Bn);
-    load_roots<LG>(tw, rt.small);
+    if constexpr (F::kLazy)
+        load_steps25<LG>(tw, rt.steps);
+    else
+        load_roots<LG>(tw, rt.small);
     // persistent: each CTA walks rows blockIdx.x, blockIdx.x + gridDim.x, ...
     for (uint64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
         const uint64_t row = r << LG;
@@ -39,7 +42,10 @@ k_middle(typename F::T *__restrict__ A, const typename F::T *__restrict__ Bv, ty
             }
         }
         __syncthreads();
-        middle_row_13_f<F>(sA, sB, tw, linv, C ? C + row : nullptr, mode);
+        if constexpr (F::kLazy)
+            middle_row25(sA, sB, tw, linv, C ? C + row : nullptr, mode);
+        else
+            middle_row_13_f<F>(sA, sB, tw, linv, C ? C + row : nullptr, mode);
         if (mode == kMidFirst || mode == kMidInner) continue;  // the product went to C
         // result row -> A (in place)
         uint4 *o4 = reinterpret_cast<uint4 *>(A + row);
@@ -109,7 +115,7 @@ __global__ void k_allsame(const uint64_t *__restrict__ x, uint64_t n, uint32_t *
 }
 
 cudaError_t launch_pass(const PassArgs &a, int logr, cudaStream_t st) {
-    if (a.field == kFieldF25) return a.inv ? launch_pass_inv25(a, logr, st) : launch_pass_fwd25(a, logr, st);
+    if (a.field == kFieldF25) return launch_pass25(a, logr, st);
     if (a.field == kFieldF30) return a.inv ? launch_pass_inv30(a, logr, st) : launch_pass_fwd30(a, logr, st);
     return a.inv ? launch_pass_inv(a, logr, st) : launch_pass_fwd(a, logr, st);
 }
@@ -133,7 +139,7 @@ static cudaError_t launch_middle_f(void *A, const void *B, void *C, int mode, ui
 cudaError_t launch_middle(int field, void *A, const void *B, void *C, int mode, uint64_t L, uint64_t linv,
                           const RootTables &rt, const RootTables30 &rt30, const RootTables25 &rt25, int nsm,
                           cudaStream_t st) {
-    if (field == kFieldF25) return launch_middle_f<FieldF25>(A, B, C, mode, L, linv, rt25, nsm, st);
+    if (field == kFieldF25) return launch_middle25(A, B, C, mode, L, linv, rt25, nsm, st);
     return field == kFieldF30 ? launch_middle_f<FieldF30>(A, B, C, mode, L, linv, rt30, nsm, st)
                               : launch_middle_f<FieldGL>(A, B, C, mode, L, linv, rt, nsm, st);
 }

@@ -1,0 +1,396 @@
+// Column passes and the fused middle for transforms over F25 (q = 5 * 2^25 + 1)
+// of length L = R * 2^13 with R = 2^9 .. 2^12 (L = 2^22 .. 2^25).
+//
+// Same decomposition as k_pass / k_middle (four-step split of Def. ntt: a
+// column pass over tiles of R rows x C = 2^(14 - LOGR) columns, the rows of
+// 2^13 on chip), arranged so that every element crosses shared memory as few
+// times as the steps need:
+//   k25_fwd  the tile's input bits are loaded once per row into shared memory
+//            (C <= 32 bits a row); step 0 reads its 0/1 inputs from there (a
+//            radix-16 step takes its DFTs from the bit table); the last step
+//            multiplies by the pass twiddle omega_N^(col freq) and stores
+//            straight from registers to HBM.
+//   k25_inv  the first step loads straight from HBM and multiplies by the pass
+//            twiddle (every root inverted, as in ntt25.cuh); the last step
+//            writes the parity bytes of the output window straight from
+//            registers (position g holds coefficient (L - g) mod L).
+//   k25_middle  step 0 of both operands loads straight from HBM; the last
+//            inverse step stores straight to HBM.
+// The pass twiddle of output k1 of last-step item (c, blk) is
+// omega_N^(col (f_b + k1 2^OFFL)) = beta * P[c][k1]: beta = omega_N^(col f_b) per
+// item (f_b = the frequency of the item's first row), P[c][k1] =
+// omega_N^(col k1 2^OFFL) per tile (C x RD_last entries in shared memory).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "cm_kernels.cuh"
+
+namespace cm {
+
+template <int LOGR>
+struct Pass25 {
+    static_assert(LOGR >= 9 && LOGR <= 12, "tiles of at most 32 columns");
+    static constexpr int R = 1 << LOGR;
+    static constexpr int NCOL_LG = kTileLg - LOGR;
+    static constexpr int C = 1 << NCOL_LG;
+    static constexpr int NST = st_n(LOGR);
+    static constexpr int LAST = NST - 1;
+    static constexpr int QL = st_q(LOGR, LAST), RDL = 1 << QL, OFFL = st_off(LOGR, LAST);
+    static constexpr int Q0 = st_q(LOGR, 0), RD0 = 1 << Q0, M0 = R / RD0;
+    static constexpr bool BTAB = Q0 == 4;
+    using BitsT = std::conditional_t<(C <= 8), uint8_t, std::conditional_t<(C <= 16), uint16_t, uint32_t>>;
+    // shared memory layout (32-bit words)
+    static constexpr int O_STEPS = sp_size(1 << kTileLg);
+    static constexpr int O_P = O_STEPS + st25_tab_words(LOGR);
+    static constexpr int O_BITS = O_P + C * RDL;
+    static constexpr int O_TAB = (O_BITS + (int)(R * sizeof(BitsT) + 3) / 4 + 3) & ~3;
+    static constexpr int W_FWD = O_TAB + (BTAB ? kBitsTable : 0);
+    static constexpr int W_INV = O_BITS;
+    static_assert(NST >= 2 && C * RDL <= kThreads, "two or more steps; one P entry per thread");
+};
+
+// P[c * RDL + k1] = omega_N^(col k1 2^OFFL), col = col0 + c; omega_N = g25^(2^esh).
+template <int LOGR>
+__device__ __forceinline__ void load_pass_p25(uint32_t *P, uint32_t col0, int esh, const RootTables25 &rt) {
+    using PS = Pass25<LOGR>;
+    const int t = threadIdx.x;
+    if (t < PS::C * PS::RDL) {
+        const uint64_t col = col0 + (uint32_t)(t / PS::RDL), k1 = (uint32_t)(t % PS::RDL);
+        const uint32_t E = (uint32_t)(((col * k1) << (PS::OFFL + esh)) & ((1ull << 25) - 1));
+        P[t] = big_root_f<FieldF25>(rt.big_lo_fwd, rt.big_hi_fwd, E);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward column pass from bits (both operands: tiles ntiles .. 2 ntiles - 1
+// take the second).
+// ---------------------------------------------------------------------------
+template <int LOGR>
+__global__ void __launch_bounds__(kThreads, 2)
+k25_fwd(uint32_t *__restrict__ data1, BitMap map1, uint32_t *__restrict__ data2, BitMap map2, uint32_t ntiles,
+        int lgN, int lgS, RootTables25 rt) {
+    using PS = Pass25<LOGR>;
+    using BitsT = typename PS::BitsT;
+    constexpr int C = PS::C, NCOL_LG = PS::NCOL_LG, M0 = PS::M0, RD0 = PS::RD0, RDL = PS::RDL;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw);
+    uint32_t *steps = tile + PS::O_STEPS;
+    uint32_t *P = tile + PS::O_P;
+    BitsT *sbits = reinterpret_cast<BitsT *>(tile + PS::O_BITS);
+    uint32_t *tab = tile + PS::O_TAB;
+
+    const bool second = blockIdx.x >= ntiles;
+    const uint32_t t_ = second ? blockIdx.x - ntiles : blockIdx.x;
+    uint32_t *__restrict__ data = second ? data2 : data1;
+    const BitMap map = second ? map2 : map1;
+    const uint32_t S = 1u << lgS;
+    const uint32_t tiles_per_blk = S >> NCOL_LG;
+    const uint32_t blkN = t_ / tiles_per_blk;
+    const uint32_t col0 = (t_ - blkN * tiles_per_blk) << NCOL_LG;
+    const uint32_t base = (blkN << lgN) + col0;  // < L <= 2^25
+    const int esh = FieldF25::kAdicity - lgN;
+
+    load_steps25<LOGR>(steps, rt.steps);
+    if constexpr (PS::BTAB) {
+        for (int i = threadIdx.x; i < kBitsTable / 4; i += kThreads)
+            reinterpret_cast<uint4 *>(tab)[i] = __ldg(reinterpret_cast<const uint4 *>(rt.bits16) + i);
+    }
+    load_pass_p25<LOGR>(P, col0, esh, rt);
+    for (int i = threadIdx.x; i < PS::R; i += kThreads) sbits[i] = (BitsT)map.get_run<C>(base + (uint64_t)i * S);
+    __syncthreads();
+
+    // step 0: 0/1 inputs from the row bits
+    {
+        const uint32_t *tw0 = steps + st25_tab_off(LOGR, 0);
+        for (int item = threadIdx.x; item < M0 * C; item += kThreads) {
+            const int c = item & (C - 1), i2 = item >> NCOL_LG;
+            uint32_t v[RD0];
+            if constexpr (PS::BTAB) {
+                uint32_t p = 0;
+#pragma unroll
+                for (int i1 = 0; i1 < RD0; ++i1) p |= (((uint32_t)sbits[i2 + M0 * i1] >> c) & 1u) << i1;
+                const uint32_t *tlo = tab + (p & 255u), *thi = tab + (p >> 8);
+#pragma unroll
+                for (int k = 0; k < RD0; ++k) {
+                    const uint32_t a = tlo[k << 8], b = thi[k << 8];
+                    v[bitrev_c(k, PS::Q0)] = (k & 1) ? f25_sub(a, b) : f25_add(a, b);
+                }
+            } else {
+#pragma unroll
+                for (int i1 = 0; i1 < RD0; ++i1) v[i1] = ((uint32_t)sbits[i2 + M0 * i1] >> c) & 1u;
+                dft_reg_f25<PS::Q0>(v);
+            }
+            const uint32_t *tw = tw0 + i2;
+            const int p0 = sp((i2 << NCOL_LG) + c);
+            constexpr int STRIDE = (M0 << NCOL_LG) + (M0 << NCOL_LG) / 32;  // M0 C >= 32
+#pragma unroll
+            for (int k1 = 0; k1 < RD0; ++k1) {
+                uint32_t x = v[bitrev_c(k1, PS::Q0)];
+                x = k1 ? f25_mont(x, tw[(k1 - 1) * M0]) : f25_red(x);
+                tile[p0 + k1 * STRIDE] = x;
+            }
+        }
+    }
+    __syncthreads();
+    if constexpr (PS::NST == 3) {
+        fwd_step25<LOGR, 1, NCOL_LG, 1>(tile, tile, steps);
+        __syncthreads();
+    }
+    // last step (no step roots): pass twiddle, store to HBM
+    for (int item = threadIdx.x; item < (PS::R / RDL) * C; item += kThreads) {
+        const int c = item & (C - 1), blk = item >> NCOL_LG;
+        const int e0 = ((blk * RDL) << NCOL_LG) + c;
+        uint32_t v[RDL];
+#pragma unroll
+        for (int i1 = 0; i1 < RDL; ++i1) v[i1] = tile[sp(e0 + i1 * C)];
+        dft_reg_f25<PS::QL>(v);
+        const uint32_t col = col0 + c;
+        const uint32_t fb = pos_to_freq<LOGR>((uint32_t)(blk * RDL));
+        const uint32_t beta = big_root_f<FieldF25>(rt.big_lo_fwd, rt.big_hi_fwd, (col * fb) << esh);
+        uint32_t *g = data + base + (uint32_t)(blk * RDL) * S + c;
+#pragma unroll
+        for (int k1 = 0; k1 < RDL; ++k1) {
+            const uint32_t w = k1 ? f25_mont(beta, P[c * RDL + k1]) : beta;
+            g[(uint32_t)k1 * S] = f25_mont(v[bitrev_c(k1, PS::QL)], w);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse column pass (every root inverted) with the parity of the window:
+// par[n - lo] = bit 0 of coefficient n for n in [lo, lo + m).
+// ---------------------------------------------------------------------------
+template <int LOGR>
+__global__ void __launch_bounds__(kThreads, 2)
+k25_inv(const uint32_t *__restrict__ data, int lgN, int lgS, uint8_t *__restrict__ par, uint64_t lo, uint64_t m,
+        RootTables25 rt) {
+    using PS = Pass25<LOGR>;
+    constexpr int C = PS::C, NCOL_LG = PS::NCOL_LG, M0 = PS::M0, RD0 = PS::RD0, RDL = PS::RDL;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw);
+    uint32_t *steps = tile + PS::O_STEPS;
+    uint32_t *P = tile + PS::O_P;
+
+    const uint32_t S = 1u << lgS;
+    const uint32_t tiles_per_blk = S >> NCOL_LG;
+    const uint32_t blkN = blockIdx.x / tiles_per_blk;
+    const uint32_t col0 = (blockIdx.x - blkN * tiles_per_blk) << NCOL_LG;
+    const uint32_t base = (blkN << lgN) + col0;
+    const int esh = FieldF25::kAdicity - lgN;
+
+    load_steps25<LOGR>(steps, rt.steps);
+    load_pass_p25<LOGR>(P, col0, esh, rt);
+    __syncthreads();
+
+    // first step (the forward's last): load from HBM, pass twiddle, DFT
+    for (int item = threadIdx.x; item < (PS::R / RDL) * C; item += kThreads) {
+        const int c = item & (C - 1), blk = item >> NCOL_LG;
+        const int e0 = ((blk * RDL) << NCOL_LG) + c;
+        const uint32_t col = col0 + c;
+        const uint32_t fb = pos_to_freq<LOGR>((uint32_t)(blk * RDL));
+        const uint32_t beta = big_root_f<FieldF25>(rt.big_lo_fwd, rt.big_hi_fwd, (col * fb) << esh);
+        const uint32_t *g = data + base + (uint32_t)(blk * RDL) * S + c;
+        uint32_t v[RDL];
+#pragma unroll
+        for (int k1 = 0; k1 < RDL; ++k1) {
+            const uint32_t w = k1 ? f25_mont(beta, P[c * RDL + k1]) : beta;
+            v[k1] = f25_mont(g[(uint32_t)k1 * S], w);
+        }
+        dft_reg_f25<PS::QL>(v);
+#pragma unroll
+        for (int i1 = 0; i1 < RDL; ++i1) tile[sp(e0 + i1 * C)] = v[bitrev_c(i1, PS::QL)];
+    }
+    __syncthreads();
+    if constexpr (PS::NST == 3) {
+        inv_step25<LOGR, 1, NCOL_LG, 1>(tile, tile, steps);
+        __syncthreads();
+    }
+    // last step (the forward's step 0): parity of the window positions
+    {
+        const uint32_t lmask = (1u << lgN) - 1;
+        const uint32_t *tw0 = steps + st25_tab_off(LOGR, 0);
+        for (int item = threadIdx.x; item < M0 * C; item += kThreads) {
+            const int c = item & (C - 1), i2 = item >> NCOL_LG;
+            const uint32_t *tw = tw0 + i2;
+            const int p0 = sp((i2 << NCOL_LG) + c);
+            constexpr int STRIDE = (M0 << NCOL_LG) + (M0 << NCOL_LG) / 32;
+            uint32_t v[RD0];
+#pragma unroll
+            for (int k1 = 0; k1 < RD0; ++k1) {
+                const uint32_t x = tile[p0 + k1 * STRIDE];
+                v[k1] = k1 ? f25_mont(x, tw[(k1 - 1) * M0]) : f25_red(x);
+            }
+            dft_reg_f25<PS::Q0>(v);
+            const uint32_t g0 = base + (uint32_t)i2 * S + c;
+#pragma unroll
+            for (int i1 = 0; i1 < RD0; ++i1) {
+                const uint32_t n = (lmask + 1 - (g0 + (uint32_t)(M0 * i1) * S)) & lmask;
+                const uint64_t p = (uint64_t)n - lo;
+                if (n >= lo && p < m) par[p] = (uint8_t)(f25_canon(v[bitrev_c(i1, PS::Q0)]) & 1u);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused middle (rows of 2^13): as k_middle with middle_row25, but step 0 of
+// both operands loads from HBM and the last inverse step stores to HBM.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 2)
+k25_middle(uint32_t *__restrict__ A, const uint32_t *__restrict__ Bv, uint32_t *__restrict__ Cacc, int mode,
+           uint32_t nrows, uint32_t linv, RootTables25 rt) {
+    constexpr int Bn = 1 << kMidLgMax;
+    static_assert(st_q(13, 0) == 5 && kThreads == 512, "step 0: one radix-32 column of one operand per thread");
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    uint32_t *sA = reinterpret_cast<uint32_t *>(smem_raw);
+    uint32_t *sB = sA + sp_size(Bn);
+    uint32_t *steps = sB + sp_size(Bn);
+    load_steps25<kMidLgMax>(steps, rt.steps);
+    __syncthreads();
+    const int t = threadIdx.x;
+    const int i2 = t & 255;
+    const uint32_t *tw0 = steps + i2;  // step 0: [(k1 - 1) 256 + i2]
+    const int p0 = sp(i2);
+    constexpr int STRIDE0 = 256 + 8;  // sp(i2 + 256 k) - sp(i2)
+    for (uint32_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const uint32_t row = r << kMidLgMax;
+        {
+            // step 0: threads 0 .. 255 take A, 256 .. 511 take B
+            uint32_t v[32];
+            if (t < 256) {
+#pragma unroll
+                for (int i1 = 0; i1 < 32; ++i1) v[i1] = A[row + i2 + 256 * i1];
+            } else {
+#pragma unroll
+                for (int i1 = 0; i1 < 32; ++i1) v[i1] = __ldg(Bv + row + i2 + 256 * i1);
+            }
+            dft_reg_f25<5>(v);
+            uint32_t *s = t < 256 ? sA : sB;
+#pragma unroll
+            for (int k1 = 0; k1 < 32; ++k1) {
+                uint32_t x = v[bitrev_c(k1, 5)];
+                x = k1 ? f25_mont(x, tw0[(k1 - 1) * 256]) : f25_red(x);
+                s[p0 + k1 * STRIDE0] = x;
+            }
+        }
+        __syncthreads();
+        fwd_step25<13, 1, 0, 2>(sA, sB, steps);
+        __syncwarp();
+        {
+            const int row0 = t << 4;
+            const int q0 = sp(row0);
+            uint32_t a[16], b[16], c[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) a[i] = sA[q0 + i];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) b[i] = sB[q0 + i];
+            dft_reg_f25<4>(a);
+            dft_reg_f25<4>(b);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) c[k] = prod25(a[bitrev_c(k, 4)], b[bitrev_c(k, 4)], linv);
+            if (mode != kMidAlone) {
+                uint4 *g4 = reinterpret_cast<uint4 *>(Cacc + row + row0);
+                if (mode != kMidFirst) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint4 pc = __ldcg(g4 + q);
+                        c[4 * q + 0] = f25_add(c[4 * q + 0], pc.x);
+                        c[4 * q + 1] = f25_add(c[4 * q + 1], pc.y);
+                        c[4 * q + 2] = f25_add(c[4 * q + 2], pc.z);
+                        c[4 * q + 3] = f25_add(c[4 * q + 3], pc.w);
+                    }
+                }
+                if (mode != kMidLast) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        g4[q] = make_uint4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
+                }
+            }
+            if (mode == kMidAlone || mode == kMidLast) {
+                dft_reg_f25<4>(c);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) sA[q0 + i] = c[bitrev_c(i, 4)];
+            }
+        }
+        if (mode == kMidFirst || mode == kMidInner) {
+            __syncthreads();  // sA / sB free for the next row
+            continue;
+        }
+        __syncwarp();
+        inv_step25<13, 1, 0, 1>(sA, sA, steps);
+        __syncthreads();
+        if (t < 256) {
+            // inverse step 0 (roots inverted) straight to HBM
+            uint32_t v[32];
+#pragma unroll
+            for (int k1 = 0; k1 < 32; ++k1) {
+                const uint32_t x = sA[p0 + k1 * STRIDE0];
+                v[k1] = k1 ? f25_mont(x, tw0[(k1 - 1) * 256]) : f25_red(x);
+            }
+            dft_reg_f25<5>(v);
+#pragma unroll
+            for (int i1 = 0; i1 < 32; ++i1) A[row + i2 + 256 * i1] = v[bitrev_c(i1, 5)];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <int LOGR>
+static cudaError_t launch_fwd25_t(const PassArgs &a, cudaStream_t st) {
+    using PS = Pass25<LOGR>;
+    const size_t sm = PS::W_FWD * sizeof(uint32_t);
+    auto kern = k25_fwd<LOGR>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const uint32_t tiles = (uint32_t)(a.L >> kTileLg);
+    const uint32_t grid = a.data2 ? 2 * tiles : tiles;
+    kern<<<grid, kThreads, sm, st>>>(static_cast<uint32_t *>(a.data), a.map, static_cast<uint32_t *>(a.data2), a.map2,
+                                     tiles, a.lgN, a.lgS, a.rt25);
+    return cudaGetLastError();
+}
+
+template <int LOGR>
+static cudaError_t launch_inv25_t(const PassArgs &a, cudaStream_t st) {
+    using PS = Pass25<LOGR>;
+    const size_t sm = PS::W_INV * sizeof(uint32_t);
+    auto kern = k25_inv<LOGR>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const uint32_t tiles = (uint32_t)(a.L >> kTileLg);
+    kern<<<tiles, kThreads, sm, st>>>(static_cast<const uint32_t *>(a.data), a.lgN, a.lgS, a.par, a.lo, a.m, a.rt25);
+    return cudaGetLastError();
+}
+
+bool pass25_fused(const PassArgs &a, int logr) {
+    // the single column pass of a transform of 2^22 .. 2^25: forward from bits,
+    // inverse with parity out
+    return logr >= 9 && logr <= 12 && a.lgN == logr + kMidLgMax && (a.inv ? a.parity_out : a.bits_in);
+}
+
+cudaError_t launch_pass25(const PassArgs &a, int logr, cudaStream_t st) {
+    if (!pass25_fused(a, logr)) return a.inv ? launch_pass_inv25(a, logr, st) : launch_pass_fwd25(a, logr, st);
+    switch (logr) {
+        case 9: return a.inv ? launch_inv25_t<9>(a, st) : launch_fwd25_t<9>(a, st);
+        case 10: return a.inv ? launch_inv25_t<10>(a, st) : launch_fwd25_t<10>(a, st);
+        case 11: return a.inv ? launch_inv25_t<11>(a, st) : launch_fwd25_t<11>(a, st);
+        default: return a.inv ? launch_inv25_t<12>(a, st) : launch_fwd25_t<12>(a, st);
+    }
+}
+
+cudaError_t launch_middle25(void *A, const void *B, void *C, int mode, uint64_t L, uint64_t linv,
+                            const RootTables25 &rt, int nsm, cudaStream_t st) {
+    const size_t sm = (2 * sp_size(1 << kMidLgMax) + st25_tab_words(kMidLgMax)) * sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(k25_middle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const uint64_t rows = L >> kMidLgMax;
+    const uint64_t grid = rows < 2ull * nsm ? rows : 2ull * nsm;
+    k25_middle<<<(unsigned)grid, kThreads, sm, st>>>(static_cast<uint32_t *>(A), static_cast<const uint32_t *>(B),
+                                                     static_cast<uint32_t *>(C), C ? mode : (int)kMidAlone,
+                                                     (uint32_t)rows, (uint32_t)linv, rt);
+    return cudaGetLastError();
+}
+
+}  // namespace cm

@@ -41,10 +41,14 @@ struct RootTablesT {
     const T *big_hi_fwd;  // g^(2^kBigLg e),  e < 2^kBigLg
     const T *big_lo_inv;
     const T *big_hi_inv;
-    // F30 only (null for Goldilocks): the length-16 DFT of 8 input bits,
-    // bits16[k * 256 + p] = sum over the set bits j of p of omega_16^(j k),
-    // canonical, for the first forward step on 0/1 inputs (fwd_step_f).
+    // 32-bit fields only (null for Goldilocks): the length-16 DFT of 8 input
+    // bits, bits16[k * 256 + p] = sum over the set bits j of p of
+    // omega_16^(j k), canonical, for the first forward step on 0/1 inputs
+    // (fwd_step_f, fwd_step25).
     const T *bits16;
+    // F25 only: the per-step root tables of every on-chip length 2^l
+    // (l = 1 .. 13) at word 2^l (ntt25.cuh).
+    const T *steps;
 };
 using RootTables = RootTablesT<uint64_t>;
 using RootTables30 = RootTablesT<uint32_t>;
