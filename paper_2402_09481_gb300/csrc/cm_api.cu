@@ -398,7 +398,7 @@ static cm_status enqueue_product(cm_ctx *ctx, const Plan &p, const uint64_t *x, 
     const BitMap am = bitmap(x, p.amode, p.alen, p.asrclen, p.aoff);
     const BitMap bm = bitmap(y, p.bmode, p.blen, p.bsrclen, p.boff);
     const bool f30 = p.field == kFieldF30, f25 = p.field == kFieldF25;
-    const uint64_t linv = f25 ? f25_linv_mont2(p.L) : f30 ? f30_linv_mont2(p.L) : gl_inv_pow2_host(p.L);
+    const uint64_t linv = f25 ? f25_linv_shoup(p.L) : f30 ? f30_linv_mont2(p.L) : gl_inv_pow2_host(p.L);
     const size_t esz = p.field == kFieldGL ? sizeof(uint64_t) : sizeof(uint32_t);
     // kernel names for the trace: Goldilocks, F30 or F25 forms
     auto kname = [&](const char *gl, const char *k30, const char *k25) { return f25 ? k25 : f30 ? k30 : gl; };
@@ -713,16 +713,20 @@ static void build_tables25(std::vector<uint32_t> &h) {
                 if ((p >> j) & 1) acc += f25_pow(w16, (uint64_t)((j * k) & 15));
             b16[k * 256 + p] = (uint32_t)(acc % F25_Q);
         }
-    // per-step tables (ntt25.cuh): length 2^l at word 2^l, step J's roots
-    // omega_(N_J)^(i2 k1) at [(k1 - 1) M_J + i2]
+    // per-step tables (ntt25.cuh): length 2^l at pair 2^l, step J's roots
+    // omega_(N_J)^(i2 k1) at pair [(k1 - 1) M_J + i2] as (root, Shoup quotient)
     uint32_t *steps = b16 + 4096;
     for (int l = 1; l <= kSmallLg; ++l)
         for (int j = 0; j + 1 < st_n(l); ++j) {
             const int lq = st_q(l, j), rd = 1 << lq, lnj = l - st_off(l, j), mj = 1 << (lnj - lq);
             const uint32_t wn = f25_pow(F25_G25, 1ull << (kF25MaxLg - lnj));  // omega_(N_J)
-            uint32_t *t = steps + (1 << l) + st25_tab_off(l, j);
+            uint32_t *t = steps + 2 * ((1 << l) + st25_tab_off(l, j));
             for (int k1 = 1; k1 < rd; ++k1)
-                for (int i2 = 0; i2 < mj; ++i2) t[(k1 - 1) * mj + i2] = f25_to_mont(f25_pow(wn, (uint64_t)i2 * k1));
+                for (int i2 = 0; i2 < mj; ++i2) {
+                    const uint32_t w = f25_pow(wn, (uint64_t)i2 * k1);
+                    t[2 * ((k1 - 1) * mj + i2)] = w;
+                    t[2 * ((k1 - 1) * mj + i2) + 1] = f25_shoup_q(w);
+                }
         }
 }
 

@@ -22,7 +22,7 @@ constexpr int kF30MaxLg = 30;
 constexpr int kF25MaxLg = 25;
 constexpr size_t kTable30Words = 8192 + 4 * 32768 + 4096;  // resident F30 root tables + bit DFT table
 // F25 root tables + bit DFT table + per-step tables of every on-chip length
-constexpr size_t kTable25Words = 8192 + 2 * 8192 + 2 * 4096 + 4096 + 16384;
+constexpr size_t kTable25Words = 8192 + 2 * 8192 + 2 * 4096 + 4096 + 2 * 16384;
 
 // Arguments of the single-CTA extraction (L <= 2^13).
 struct Launch {

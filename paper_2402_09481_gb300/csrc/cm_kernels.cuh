@@ -63,7 +63,7 @@ k_fused_small(BitMap amap, BitMap bmap, uint64_t lo, uint64_t m, uint64_t linv_,
     __syncthreads();
     if constexpr (F::kLazy) {
         ntt_fwd25<LG, 0, 2>(sA, sB, tw);
-        for (int i = threadIdx.x; i < L; i += kThreads) sA[sp(i)] = prod25(sA[sp(i)], sB[sp(i)], linv);
+        for (int i = threadIdx.x; i < L; i += kThreads) sA[sp(i)] = prod25(sA[sp(i)], sB[sp(i)], linv_);
         __syncthreads();
         ntt_inv25<LG, 0, 1>(sA, sA, tw);
     } else {
@@ -123,9 +123,19 @@ template <class F, int LOGR, bool INV, bool BITS_IN>
 __host__ __device__ constexpr bool pass_bits_table() {
     return !INV && BITS_IN && sizeof(typename F::T) == 4 && st_q(LOGR, 0) == 4;
 }
+// Shared memory of a column pass: the tile, then the step roots (F25: root
+// pairs, 8-byte aligned), then the bit table (16-byte aligned).
+template <class F, int LOGR>
+__host__ __device__ constexpr int pass_tw_off() {
+    return F::kLazy ? (sp_size(1 << (LOGR + F::ncol_lg(LOGR))) + 1) & ~1 : sp_size(1 << (LOGR + F::ncol_lg(LOGR)));
+}
+template <class F, int LOGR>
+__host__ __device__ constexpr int pass_tw_words() {
+    return F::kLazy ? st25_smem_words(LOGR) : (1 << LOGR);
+}
 template <class F, int LOGR>
 __host__ __device__ constexpr int pass_table_off() {
-    return (sp_size(1 << (LOGR + F::ncol_lg(LOGR))) + (1 << LOGR) + 3) & ~3;
+    return (pass_tw_off<F, LOGR>() + pass_tw_words<F, LOGR>() + 3) & ~3;
 }
 constexpr int kBitsTable = 16 * 256;
 
@@ -145,7 +155,7 @@ k_pass(typename F::T *__restrict__ data1, BitMap map1, typename F::T *__restrict
     constexpr int C = 1 << NCOL_LG;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);
-    T *tw = smem + sp_size(R * C);
+    T *tw = smem + pass_tw_off<F, LOGR>();
     if constexpr (F::kLazy)
         load_steps25<LOGR>(tw, rt.steps);
     else
@@ -186,11 +196,14 @@ k_pass(typename F::T *__restrict__ data1, BitMap map1, typename F::T *__restrict
         } else {
             unpack16(*reinterpret_cast<const uint4 *>(data + g), v);
         }
-        // F25's inverse takes every root inverted: the forward row roots
+        // F25's inverse takes every root inverted: the forward row roots, on
+        // values brought below 2q first (the root is below 2q, not below q)
         if (INV) {
-            if constexpr (F::kLazy)
+            if constexpr (F::kLazy) {
+#pragma unroll
+                for (int j = 0; j < VW; ++j) v[j] = F::red(v[j]);
                 row_twiddle<F, VW>(v, pos_to_freq<LOGR>(i), col0 + c, esh, rt.big_lo_fwd, rt.big_hi_fwd);
-            else
+            } else
                 row_twiddle<F, VW>(v, pos_to_freq<LOGR>(i), col0 + c, esh, rt.big_lo_inv, rt.big_hi_inv);
         }
 #pragma unroll

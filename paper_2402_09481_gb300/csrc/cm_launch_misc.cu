@@ -22,10 +22,7 @@ k_middle(typename F::T *__restrict__ A, const typename F::T *__restrict__ Bv, ty
     T *sA = reinterpret_cast<T *>(smem_raw);
     T *sB = sA + sp_size(Bn);
     T *tw = sB + sp_size(Bn);
-    if constexpr (F::kLazy)
-        load_steps25<LG>(tw, rt.steps);
-    else
-        load_roots<LG>(tw, rt.small);
+    load_roots<LG>(tw, rt.small);
     // persistent: each CTA walks rows blockIdx.x, blockIdx.x + gridDim.x, ...
     for (uint64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
         const uint64_t row = r << LG;
@@ -42,10 +39,7 @@ k_middle(typename F::T *__restrict__ A, const typename F::T *__restrict__ Bv, ty
             }
         }
         __syncthreads();
-        if constexpr (F::kLazy)
-            middle_row25(sA, sB, tw, linv, C ? C + row : nullptr, mode);
-        else
-            middle_row_13_f<F>(sA, sB, tw, linv, C ? C + row : nullptr, mode);
+        middle_row_13_f<F>(sA, sB, tw, linv, C ? C + row : nullptr, mode);
         if (mode == kMidFirst || mode == kMidInner) continue;  // the product went to C
         // result row -> A (in place)
         uint4 *o4 = reinterpret_cast<uint4 *>(A + row);

@@ -24,7 +24,8 @@ static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st) {
     constexpr int TILE_LG = LOGR + F::ncol_lg(LOGR);
     constexpr bool BTAB = pass_bits_table<F, LOGR, INV, BITS_IN>();
     const size_t sm =
-        (BTAB ? pass_table_off<F, LOGR>() + kBitsTable : sp_size(1 << TILE_LG) + (1 << LOGR)) * sizeof(T);
+        (BTAB ? pass_table_off<F, LOGR>() + kBitsTable : pass_tw_off<F, LOGR>() + pass_tw_words<F, LOGR>()) *
+        sizeof(T);
     auto kern = k_pass<F, LOGR, INV, BITS_IN, PARITY_OUT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

@@ -18,8 +18,10 @@
 //            inverse step stores straight to HBM.
 // The pass twiddle of output k1 of last-step item (c, blk) is
 // omega_N^(col (f_b + k1 2^OFFL)) = beta * P[c][k1]: beta = omega_N^(col f_b) per
-// item (f_b = the frequency of the item's first row), P[c][k1] =
-// omega_N^(col k1 2^OFFL) per tile (C x RD_last entries in shared memory).
+// item (f_b = the frequency of the item's first row; Montgomery form, a lazy
+// Montgomery product), P[c][k1] = omega_N^(col k1 2^OFFL) per tile (C x
+// RD_last root pairs in shared memory, a Shoup product that also brings the
+// raw DFT output to [0, 2q) first).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -39,27 +41,33 @@ struct Pass25 {
     static constexpr int LAST = NST - 1;
     static constexpr int QL = st_q(LOGR, LAST), RDL = 1 << QL, OFFL = st_off(LOGR, LAST);
     static constexpr int Q0 = st_q(LOGR, 0), RD0 = 1 << Q0, M0 = R / RD0;
-    static constexpr bool BTAB = Q0 == 4;
+    // the bit table where two CTAs still fit an SM (not at 2^12 rows, whose
+    // root pairs take 32 KiB)
+    static constexpr bool BTAB = Q0 == 4 && LOGR <= 11;
     using BitsT = std::conditional_t<(C <= 8), uint8_t, std::conditional_t<(C <= 16), uint16_t, uint32_t>>;
-    // shared memory layout (32-bit words)
-    static constexpr int O_STEPS = sp_size(1 << kTileLg);
-    static constexpr int O_P = O_STEPS + st25_tab_words(LOGR);
-    static constexpr int O_BITS = O_P + C * RDL;
+    // shared memory layout (32-bit words): tile, step root pairs, P pairs,
+    // row bits, bit table
+    static constexpr int O_STEPS = (sp_size(1 << kTileLg) + 1) & ~1;
+    static constexpr int O_P = O_STEPS + st25_smem_words(LOGR);
+    static constexpr int O_BITS = O_P + 2 * C * RDL;
     static constexpr int O_TAB = (O_BITS + (int)(R * sizeof(BitsT) + 3) / 4 + 3) & ~3;
     static constexpr int W_FWD = O_TAB + (BTAB ? kBitsTable : 0);
     static constexpr int W_INV = O_BITS;
     static_assert(NST >= 2 && C * RDL <= kThreads, "two or more steps; one P entry per thread");
+    static_assert(W_FWD * 4 <= 113 * 1024, "two CTAs per SM");
 };
 
-// P[c * RDL + k1] = omega_N^(col k1 2^OFFL), col = col0 + c; omega_N = g25^(2^esh).
+// P[c * RDL + k1] = omega_N^(col k1 2^OFFL) as a Shoup pair (plain root,
+// quotient), col = col0 + c; omega_N = g25^(2^esh).
 template <int LOGR>
-__device__ __forceinline__ void load_pass_p25(uint32_t *P, uint32_t col0, int esh, const RootTables25 &rt) {
+__device__ __forceinline__ void load_pass_p25(uint2 *P, uint32_t col0, int esh, const RootTables25 &rt) {
     using PS = Pass25<LOGR>;
     const int t = threadIdx.x;
     if (t < PS::C * PS::RDL) {
         const uint64_t col = col0 + (uint32_t)(t / PS::RDL), k1 = (uint32_t)(t % PS::RDL);
         const uint32_t E = (uint32_t)(((col * k1) << (PS::OFFL + esh)) & ((1ull << 25) - 1));
-        P[t] = big_root_f<FieldF25>(rt.big_lo_fwd, rt.big_hi_fwd, E);
+        const uint32_t w = f25_canon(f25_mont(big_root_f<FieldF25>(rt.big_lo_fwd, rt.big_hi_fwd, E), 1u));
+        P[t] = make_uint2(w, f25_shoup_q(w));
     }
 }
 
@@ -77,7 +85,7 @@ k25_fwd(uint32_t *__restrict__ data1, BitMap map1, uint32_t *__restrict__ data2,
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw);
     uint32_t *steps = tile + PS::O_STEPS;
-    uint32_t *P = tile + PS::O_P;
+    uint2 *P = reinterpret_cast<uint2 *>(tile + PS::O_P);
     BitsT *sbits = reinterpret_cast<BitsT *>(tile + PS::O_BITS);
     uint32_t *tab = tile + PS::O_TAB;
 
@@ -103,7 +111,7 @@ k25_fwd(uint32_t *__restrict__ data1, BitMap map1, uint32_t *__restrict__ data2,
 
     // step 0: 0/1 inputs from the row bits
     {
-        const uint32_t *tw0 = steps + st25_tab_off(LOGR, 0);
+        const uint2 *tw0 = reinterpret_cast<const uint2 *>(steps) + st25_tab_off(LOGR, 0);
         for (int item = threadIdx.x; item < M0 * C; item += kThreads) {
             const int c = item & (C - 1), i2 = item >> NCOL_LG;
             uint32_t v[RD0];
@@ -122,13 +130,13 @@ k25_fwd(uint32_t *__restrict__ data1, BitMap map1, uint32_t *__restrict__ data2,
                 for (int i1 = 0; i1 < RD0; ++i1) v[i1] = ((uint32_t)sbits[i2 + M0 * i1] >> c) & 1u;
                 dft_reg_f25<PS::Q0>(v);
             }
-            const uint32_t *tw = tw0 + i2;
+            const uint2 *tw = tw0 + i2;
             const int p0 = sp((i2 << NCOL_LG) + c);
             constexpr int STRIDE = (M0 << NCOL_LG) + (M0 << NCOL_LG) / 32;  // M0 C >= 32
 #pragma unroll
             for (int k1 = 0; k1 < RD0; ++k1) {
                 uint32_t x = v[bitrev_c(k1, PS::Q0)];
-                x = k1 ? f25_mont(x, tw[(k1 - 1) * M0]) : f25_red(x);
+                x = k1 ? shoup_pair(x, tw[(k1 - 1) * M0]) : f25_red(x);
                 tile[p0 + k1 * STRIDE] = x;
             }
         }
@@ -150,11 +158,9 @@ k25_fwd(uint32_t *__restrict__ data1, BitMap map1, uint32_t *__restrict__ data2,
         const uint32_t fb = pos_to_freq<LOGR>((uint32_t)(blk * RDL));
         const uint32_t beta = big_root_f<FieldF25>(rt.big_lo_fwd, rt.big_hi_fwd, (col * fb) << esh);
         uint32_t *g = data + base + (uint32_t)(blk * RDL) * S + c;
+        const uint2 *pc = P + c * RDL;
 #pragma unroll
-        for (int k1 = 0; k1 < RDL; ++k1) {
-            const uint32_t w = k1 ? f25_mont(beta, P[c * RDL + k1]) : beta;
-            g[(uint32_t)k1 * S] = f25_mont(v[bitrev_c(k1, PS::QL)], w);
-        }
+        for (int k1 = 0; k1 < RDL; ++k1) g[(uint32_t)k1 * S] = f25_mont(shoup_pair(v[bitrev_c(k1, PS::QL)], pc[k1]), beta);
     }
 }
 
@@ -171,7 +177,7 @@ k25_inv(const uint32_t *__restrict__ data, int lgN, int lgS, uint8_t *__restrict
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw);
     uint32_t *steps = tile + PS::O_STEPS;
-    uint32_t *P = tile + PS::O_P;
+    uint2 *P = reinterpret_cast<uint2 *>(tile + PS::O_P);
 
     const uint32_t S = 1u << lgS;
     const uint32_t tiles_per_blk = S >> NCOL_LG;
@@ -192,12 +198,10 @@ k25_inv(const uint32_t *__restrict__ data, int lgN, int lgS, uint8_t *__restrict
         const uint32_t fb = pos_to_freq<LOGR>((uint32_t)(blk * RDL));
         const uint32_t beta = big_root_f<FieldF25>(rt.big_lo_fwd, rt.big_hi_fwd, (col * fb) << esh);
         const uint32_t *g = data + base + (uint32_t)(blk * RDL) * S + c;
+        const uint2 *pc = P + c * RDL;
         uint32_t v[RDL];
 #pragma unroll
-        for (int k1 = 0; k1 < RDL; ++k1) {
-            const uint32_t w = k1 ? f25_mont(beta, P[c * RDL + k1]) : beta;
-            v[k1] = f25_mont(g[(uint32_t)k1 * S], w);
-        }
+        for (int k1 = 0; k1 < RDL; ++k1) v[k1] = f25_mont(shoup_pair(g[(uint32_t)k1 * S], pc[k1]), beta);
         dft_reg_f25<PS::QL>(v);
 #pragma unroll
         for (int i1 = 0; i1 < RDL; ++i1) tile[sp(e0 + i1 * C)] = v[bitrev_c(i1, PS::QL)];
@@ -210,17 +214,17 @@ k25_inv(const uint32_t *__restrict__ data, int lgN, int lgS, uint8_t *__restrict
     // last step (the forward's step 0): parity of the window positions
     {
         const uint32_t lmask = (1u << lgN) - 1;
-        const uint32_t *tw0 = steps + st25_tab_off(LOGR, 0);
+        const uint2 *tw0 = reinterpret_cast<const uint2 *>(steps) + st25_tab_off(LOGR, 0);
         for (int item = threadIdx.x; item < M0 * C; item += kThreads) {
             const int c = item & (C - 1), i2 = item >> NCOL_LG;
-            const uint32_t *tw = tw0 + i2;
+            const uint2 *tw = tw0 + i2;
             const int p0 = sp((i2 << NCOL_LG) + c);
             constexpr int STRIDE = (M0 << NCOL_LG) + (M0 << NCOL_LG) / 32;
             uint32_t v[RD0];
 #pragma unroll
             for (int k1 = 0; k1 < RD0; ++k1) {
                 const uint32_t x = tile[p0 + k1 * STRIDE];
-                v[k1] = k1 ? f25_mont(x, tw[(k1 - 1) * M0]) : f25_red(x);
+                v[k1] = k1 ? shoup_pair(x, tw[(k1 - 1) * M0]) : f25_red(x);
             }
             dft_reg_f25<PS::Q0>(v);
             const uint32_t g0 = base + (uint32_t)i2 * S + c;
@@ -235,23 +239,44 @@ k25_inv(const uint32_t *__restrict__ data, int lgN, int lgS, uint8_t *__restrict
 }
 
 // ---------------------------------------------------------------------------
-// Fused middle (rows of 2^13): as k_middle with middle_row25, but step 0 of
-// both operands loads from HBM and the last inverse step stores to HBM.
+// Fused middle (rows of 2^13), two CTAs of 512 threads per SM.  Per row as
+// middle_row_13_f: forward steps 0 and 1 of both operands, per thread 16 rows
+// in registers (step 2 of both, the product scaled by L^-1, step 2 of the
+// inverse), inverse steps 1 and 0 (every root inverted); step 0 of both
+// operands loads from HBM and the last inverse step stores to HBM.  Step 1
+// takes Shoup root pairs; step 0's roots (31 x 256 of them) stay single
+// words in Montgomery form, so that two CTAs still fit an SM.
 // ---------------------------------------------------------------------------
+constexpr int kMid0Words = 31 * 256;                         // step 0: omega_8192^(i2 k1) 2^32 mod q
+constexpr int kMid1Pairs = st25_tab_words(13) - kMid0Words;  // step 1: root pairs
+static_assert(st25_tab_off(13, 1) == kMid0Words, "step 0 of 2^13 has 31 x 256 roots");
+
 __global__ void __launch_bounds__(kThreads, 2)
 k25_middle(uint32_t *__restrict__ A, const uint32_t *__restrict__ Bv, uint32_t *__restrict__ Cacc, int mode,
-           uint32_t nrows, uint32_t linv, RootTables25 rt) {
+           uint32_t nrows, uint64_t linv, RootTables25 rt) {
     constexpr int Bn = 1 << kMidLgMax;
-    static_assert(st_q(13, 0) == 5 && kThreads == 512, "step 0: one radix-32 column of one operand per thread");
+    static_assert(st_q(13, 0) == 5 && st_q(13, 1) == 4 && st_q(13, 2) == 4 && kThreads == 512,
+                  "step 0: one radix-32 column of one operand per thread");
     extern __shared__ __align__(16) uint8_t smem_raw[];
-    uint32_t *sA = reinterpret_cast<uint32_t *>(smem_raw);
+    uint2 *pairs1 = reinterpret_cast<uint2 *>(smem_raw);                  // kMid1Pairs
+    uint32_t *mont0 = reinterpret_cast<uint32_t *>(pairs1 + kMid1Pairs);  // kMid0Words
+    uint32_t *sA = mont0 + kMid0Words;
     uint32_t *sB = sA + sp_size(Bn);
-    uint32_t *steps = sB + sp_size(Bn);
-    load_steps25<kMidLgMax>(steps, rt.steps);
+    {
+        const uint2 *src = reinterpret_cast<const uint2 *>(rt.steps) + (1 << 13) + kMid0Words;
+        for (int i = threadIdx.x; i < kMid1Pairs; i += kThreads) pairs1[i] = __ldg(src + i);
+        for (int i = threadIdx.x; i < kMid0Words; i += kThreads) {
+            const int k1 = 1 + (i >> 8), i2 = i & 255;
+            mont0[i] = __ldg(rt.small + i2 * k1);  // omega_8192^(i2 k1), i2 k1 < 8192
+        }
+    }
     __syncthreads();
+    // fwd_step25 / inv_step25 find step J's pairs at pair st25_tab_off(13, J) of
+    // their table argument: step 1's pairs sit at that offset from tab1
+    const uint32_t *tab1 = reinterpret_cast<const uint32_t *>(pairs1 - kMid0Words);
     const int t = threadIdx.x;
     const int i2 = t & 255;
-    const uint32_t *tw0 = steps + i2;  // step 0: [(k1 - 1) 256 + i2]
+    const uint32_t *tw0 = mont0 + i2;  // step 0: [(k1 - 1) 256 + i2]
     const int p0 = sp(i2);
     constexpr int STRIDE0 = 256 + 8;  // sp(i2 + 256 k) - sp(i2)
     for (uint32_t r = blockIdx.x; r < nrows; r += gridDim.x) {
@@ -276,20 +301,27 @@ k25_middle(uint32_t *__restrict__ A, const uint32_t *__restrict__ Bv, uint32_t *
             }
         }
         __syncthreads();
-        fwd_step25<13, 1, 0, 2>(sA, sB, steps);
-        __syncwarp();
+        fwd_step25<13, 1, 0, 2>(sA, sB, tab1);
+        __syncwarp();  // step 1 and the fused step touch the 256-row blocks of the calling warp only
         {
             const int row0 = t << 4;
-            const int q0 = sp(row0);
-            uint32_t a[16], b[16], c[16];
+            const int q0 = sp(row0);  // the 16 rows of a group do not cross a pad word
+            uint32_t a[16];
+            {
+                uint32_t b[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) a[i] = sA[q0 + i];
+                for (int i = 0; i < 16; ++i) a[i] = sA[q0 + i];
+                dft_reg_f25<4>(a);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) b[i] = sB[q0 + i];
-            dft_reg_f25<4>(a);
-            dft_reg_f25<4>(b);
+                for (int i = 0; i < 16; ++i) b[i] = sB[q0 + i];
+                dft_reg_f25<4>(b);
+                // frequency k sits in register bitrev(k) of both
 #pragma unroll
-            for (int k = 0; k < 16; ++k) c[k] = prod25(a[bitrev_c(k, 4)], b[bitrev_c(k, 4)], linv);
+                for (int j = 0; j < 16; ++j) a[j] = prod25(a[j], b[j], linv);
+            }
+            uint32_t c[16];  // the products in frequency order (a renaming of a)
+#pragma unroll
+            for (int k = 0; k < 16; ++k) c[k] = a[bitrev_c(k, 4)];
             if (mode != kMidAlone) {
                 uint4 *g4 = reinterpret_cast<uint4 *>(Cacc + row + row0);
                 if (mode != kMidFirst) {
@@ -319,7 +351,7 @@ k25_middle(uint32_t *__restrict__ A, const uint32_t *__restrict__ Bv, uint32_t *
             continue;
         }
         __syncwarp();
-        inv_step25<13, 1, 0, 1>(sA, sA, steps);
+        inv_step25<13, 1, 0, 1>(sA, sA, tab1);
         __syncthreads();
         if (t < 256) {
             // inverse step 0 (roots inverted) straight to HBM
@@ -382,14 +414,14 @@ cudaError_t launch_pass25(const PassArgs &a, int logr, cudaStream_t st) {
 
 cudaError_t launch_middle25(void *A, const void *B, void *C, int mode, uint64_t L, uint64_t linv,
                             const RootTables25 &rt, int nsm, cudaStream_t st) {
-    const size_t sm = (2 * sp_size(1 << kMidLgMax) + st25_tab_words(kMidLgMax)) * sizeof(uint32_t);
+    const size_t sm = 2 * kMid1Pairs * sizeof(uint32_t) + (kMid0Words + 2 * sp_size(1 << kMidLgMax)) * sizeof(uint32_t);
     cudaError_t e = cudaFuncSetAttribute(k25_middle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const uint64_t rows = L >> kMidLgMax;
     const uint64_t grid = rows < 2ull * nsm ? rows : 2ull * nsm;
     k25_middle<<<(unsigned)grid, kThreads, sm, st>>>(static_cast<uint32_t *>(A), static_cast<const uint32_t *>(B),
                                                      static_cast<uint32_t *>(C), C ? mode : (int)kMidAlone,
-                                                     (uint32_t)rows, (uint32_t)linv, rt);
+                                                     (uint32_t)rows, linv, rt);
     return cudaGetLastError();
 }
 

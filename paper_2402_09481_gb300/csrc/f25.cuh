@@ -110,6 +110,12 @@ F25_CX uint32_t f25_root_2_25(bool inverse) {
 F25_CX uint32_t f25_linv_mont2(uint64_t L) {
     return f25_to_mont(f25_to_mont(f25_pow((uint32_t)(L % F25_Q), F25_Q - 2)));
 }
+// The Shoup pair of L^-1 2^32 mod q (low word: the root, high word: its
+// quotient): shoup(mont(a, b), pair) = a b L^-1.
+F25_CX uint64_t f25_linv_shoup(uint64_t L) {
+    return (uint64_t)f25_to_mont(f25_pow((uint32_t)(L % F25_Q), F25_Q - 2)) |
+           ((uint64_t)f25_shoup_q(f25_to_mont(f25_pow((uint32_t)(L % F25_Q), F25_Q - 2))) << 32);
+}
 
 #ifdef __CUDACC__
 // Constant-bank copies of omega_32^j and their Shoup quotients.

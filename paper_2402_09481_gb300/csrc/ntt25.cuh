@@ -7,9 +7,11 @@
 // - Step roots come from per-step tables laid out for the thread that uses
 //   them.  Step J multiplies output k1 of column i2 by omega_(N_J)^(i2 k1)
 //   (N_J = 2^(LOGR - OFF_J), M_J = N_J / RD_J columns); its table holds that
-//   root at [(k1 - 1) M_J + i2].  A thread reads its RD_J - 1 roots at fixed
-//   offsets from its own base i2 (no index arithmetic), and the lanes of a
-//   warp, which take consecutive columns, read consecutive words.
+//   root at [(k1 - 1) M_J + i2] as a pair (w, floor(w 2^32 / q)) for the
+//   Shoup product (three multiplies, no compare).  A thread reads its
+//   RD_J - 1 roots at fixed offsets from its own base i2 (no index
+//   arithmetic), and the lanes of a warp, which take consecutive columns,
+//   read consecutive pairs.
 // - The inverse transform takes every root inverted, i.e. it runs the exact
 //   inverse steps with omega in place of omega^-1.  That computes
 //   F_omega Pi^-1 (Pi: the forward transform's digit-reversed order) instead
@@ -19,9 +21,9 @@
 //   folded into the pointwise product position g holds the convolution
 //   coefficient at (L - g) mod L; the parity readers index accordingly.
 // - Values: forward steps take inputs in [0, 2q) and leave [0, 2q) (the root
-//   product or red); inverse steps take any value below 2^31, bring each
-//   input to [0, 2q) by the root product or red, and leave the raw DFT
-//   output (below 12 q).
+//   product or red); inverse steps take any 32-bit value, bring each input to
+//   [0, 2q) by the root product or red, and leave the raw DFT output (below
+//   20 q, dft_reg_f25).
 #pragma once
 #include <stdint.h>
 
@@ -29,23 +31,36 @@
 
 namespace cm {
 
-// Offset of step J's table within the tables of a transform of length 2^logr,
-// and the words of all of them (steps 0 .. st_n - 2; the last step has no
-// roots).  The set for length 2^logr starts at word 2^logr of
-// RootTables25::steps, and has fewer than 2^logr words.
-__host__ __device__ constexpr int st25_tab_off(int logr, int j) {
-    return j == 0 ? 0
-                  : st25_tab_off(logr, j - 1) +
-                        ((1 << st_q(logr, j - 1)) - 1) * (1 << (logr - st_off(logr, j - 1) - st_q(logr, j - 1)));
+// Offset (in root pairs) of step J's table within the tables of a transform
+// of length 2^logr, and the pairs of all of them (steps 0 .. st_n - 2; the
+// last step has no roots).  The set for length 2^logr starts at pair 2^logr
+// of RootTables25::steps, and has fewer than 2^logr pairs.
+__host__ __device__ __forceinline__ constexpr int st25_tab_off(int logr, int j) {
+    int o = 0, off = 0;
+    for (int i = 0; i < j; ++i) {
+        const int q = st_q(logr, i);
+        o += ((1 << q) - 1) * (1 << (logr - off - q));
+        off += q;
+    }
+    return o;
 }
-__host__ __device__ constexpr int st25_tab_words(int logr) { return st25_tab_off(logr, st_n(logr) - 1); }
+__host__ __device__ __forceinline__ constexpr int st25_tab_words(int logr) {
+    return st25_tab_off(logr, st_n(logr) - 1);
+}
 
-// Copy the step tables of length 2^LOGR into shared memory (ends without a barrier).
-template <int LOGR>
+// Copy the step tables of length 2^LOGR (pairs) into shared memory at dst
+// (8-byte aligned; ends without a barrier).  NT: the threads that copy.
+template <int LOGR, int NT = kThreads>
 __device__ __forceinline__ void load_steps25(uint32_t *dst, const uint32_t *__restrict__ steps) {
-    const uint32_t *src = steps + (1 << LOGR);
-    for (int i = threadIdx.x; i < st25_tab_words(LOGR); i += kThreads) dst[i] = __ldg(src + i);
+    const uint2 *src = reinterpret_cast<const uint2 *>(steps) + (1 << LOGR);
+    uint2 *d = reinterpret_cast<uint2 *>(dst);
+    for (int i = threadIdx.x; i < st25_tab_words(LOGR); i += NT) d[i] = __ldg(src + i);
 }
+// Shared-memory words of the step tables of length 2^LOGR.
+__host__ __device__ __forceinline__ constexpr int st25_smem_words(int logr) { return 2 * st25_tab_words(logr); }
+
+// x times the root pair r = (w, floor(w 2^32 / q)) -> [0, 2q), any 32-bit x.
+__device__ __forceinline__ uint32_t shoup_pair(uint32_t x, uint2 r) { return f25_shoup(x, r.x, r.y); }
 
 // Padded shared-memory position of input i1 of an item whose first input is
 // element e0, inputs S elements apart: linear in i1 when S >= 32 (sp adds one
@@ -61,15 +76,16 @@ __device__ __forceinline__ int sp_at(int e0, int p0, int i1) {
 // Forward step J over NBUF buffers (see fwd_step_f for the item layout).
 // BITS0: step 0 has radix 16 and 0/1 inputs; its DFTs come from the bit table
 // (RootTablesT::bits16, in shared memory at tab16).
+// tid: this thread's index among the kThreads that share the step.
 template <int LOGR, int J, int NCOL_LG, int NBUF, bool BITS0 = false>
 __device__ __forceinline__ void fwd_step25(uint32_t *s0, uint32_t *s1, const uint32_t *tab,
-                                           const uint32_t *tab16 = nullptr) {
+                                           const uint32_t *tab16 = nullptr, int tid = threadIdx.x) {
     constexpr int OFF = st_off(LOGR, J), LQ = st_q(LOGR, J), RD = 1 << LQ;
     constexpr int LN = LOGR - OFF, LM = LN - LQ, M = 1 << LM;
     constexpr int ITEMS = (1 << (LOGR - LQ)) << NCOL_LG;
     constexpr int S = M << NCOL_LG;
-    const uint32_t *tJ = tab + st25_tab_off(LOGR, J);
-    for (int item = threadIdx.x; item < ITEMS * NBUF; item += kThreads) {
+    const uint2 *tJ = reinterpret_cast<const uint2 *>(tab) + st25_tab_off(LOGR, J);
+    for (int item = tid; item < ITEMS * NBUF; item += kThreads) {
         const int bi = (NBUF == 2 && item >= ITEMS) ? 1 : 0;
         const int it = item - bi * ITEMS;
         uint32_t *s = bi ? s1 : s0;
@@ -95,12 +111,12 @@ __device__ __forceinline__ void fwd_step25(uint32_t *s0, uint32_t *s1, const uin
             for (int i1 = 0; i1 < RD; ++i1) v[i1] = s[sp_at<S>(e0, p0, i1)];
             dft_reg_f25<LQ>(v);
         }
-        const uint32_t *tw = tJ + i2;
+        const uint2 *tw = tJ + i2;
 #pragma unroll
         for (int k1 = 0; k1 < RD; ++k1) {
             uint32_t x = v[bitrev_c(k1, LQ)];
             if (LM > 0 && k1 > 0) {
-                x = f25_mont(x, tw[(k1 - 1) * M]);
+                x = shoup_pair(x, tw[(k1 - 1) * M]);
             } else {
                 x = f25_red(x);
             }
@@ -112,13 +128,13 @@ __device__ __forceinline__ void fwd_step25(uint32_t *s0, uint32_t *s1, const uin
 // Step J of the inverse with every root inverted (forward roots, forward
 // register DFT, outputs in plain bit-reversed order).
 template <int LOGR, int J, int NCOL_LG, int NBUF>
-__device__ __forceinline__ void inv_step25(uint32_t *s0, uint32_t *s1, const uint32_t *tab) {
+__device__ __forceinline__ void inv_step25(uint32_t *s0, uint32_t *s1, const uint32_t *tab, int tid = threadIdx.x) {
     constexpr int OFF = st_off(LOGR, J), LQ = st_q(LOGR, J), RD = 1 << LQ;
     constexpr int LN = LOGR - OFF, LM = LN - LQ, M = 1 << LM;
     constexpr int ITEMS = (1 << (LOGR - LQ)) << NCOL_LG;
     constexpr int S = M << NCOL_LG;
-    const uint32_t *tJ = tab + st25_tab_off(LOGR, J);
-    for (int item = threadIdx.x; item < ITEMS * NBUF; item += kThreads) {
+    const uint2 *tJ = reinterpret_cast<const uint2 *>(tab) + st25_tab_off(LOGR, J);
+    for (int item = tid; item < ITEMS * NBUF; item += kThreads) {
         const int bi = (NBUF == 2 && item >= ITEMS) ? 1 : 0;
         const int it = item - bi * ITEMS;
         uint32_t *s = bi ? s1 : s0;
@@ -127,12 +143,12 @@ __device__ __forceinline__ void inv_step25(uint32_t *s0, uint32_t *s1, const uin
         const int i2 = rest & (M - 1);
         const int e0 = ((((rest >> LM) << LN) + i2) << NCOL_LG) + c;
         const int p0 = sp(e0);
-        const uint32_t *tw = tJ + i2;
+        const uint2 *tw = tJ + i2;
         uint32_t v[RD];
 #pragma unroll
         for (int k1 = 0; k1 < RD; ++k1) {
             const uint32_t x = s[sp_at<S>(e0, p0, k1)];
-            v[k1] = (LM > 0 && k1 > 0) ? f25_mont(x, tw[(k1 - 1) * M]) : f25_red(x);
+            v[k1] = (LM > 0 && k1 > 0) ? shoup_pair(x, tw[(k1 - 1) * M]) : f25_red(x);
         }
         dft_reg_f25<LQ>(v);
 #pragma unroll
@@ -171,69 +187,11 @@ __device__ __forceinline__ void ntt_inv25(uint32_t *s0, uint32_t *s1, const uint
     if constexpr (LOGR > 0) inv_from25<LOGR, st_n(LOGR) - 1, NCOL_LG, NBUF>(s0, s1, tab);
 }
 
-// a b L^-1 for a any 32-bit value and b < 12.8 q (DFT outputs) -> (0, 2q).
-__device__ __forceinline__ uint32_t prod25(uint32_t a, uint32_t b, uint32_t linv) {
-    return f25_mont(f25_mont(f25_red(a), b), linv);
-}
-
-// One fused middle row of B = 2^13 elements over F25 (see middle_row_13_f for
-// the sum modes): forward steps 0 and 1 of both operands in shared memory,
-// then per thread 16 rows in registers: step 2 of both, the product scaled by
-// linv, step 2 of the inverse; then inverse steps 1 and 0 (every root
-// inverted).  The result (any value below 12 q, index-negated as described at
-// the top) is left in sA.  Ends with a block barrier.
-__device__ __forceinline__ void middle_row25(uint32_t *sA, uint32_t *sB, const uint32_t *tab, uint32_t linv,
-                                             uint32_t *gC = nullptr, int mode = kMidAlone) {
-    static_assert(st_n(13) == 3 && st_q(13, 0) == 5 && st_q(13, 1) == 4 && st_q(13, 2) == 4, "schedule");
-    static_assert(kThreads == 512, "one 16-row group per thread in the fused step");
-    fwd_step25<13, 0, 0, 2>(sA, sB, tab);
-    __syncthreads();
-    fwd_step25<13, 1, 0, 2>(sA, sB, tab);
-    __syncwarp();
-    {
-        const int row0 = threadIdx.x << 4;
-        const int p0 = sp(row0);  // the 16 rows of a group do not cross a pad word
-        uint32_t a[16], b[16], c[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) a[i] = sA[p0 + i];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) b[i] = sB[p0 + i];
-        dft_reg_f25<4>(a);
-        dft_reg_f25<4>(b);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) c[k] = prod25(a[bitrev_c(k, 4)], b[bitrev_c(k, 4)], linv);
-        if (mode != kMidAlone) {
-            uint4 *g4 = reinterpret_cast<uint4 *>(gC + row0);
-            if (mode != kMidFirst) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint4 pc = __ldcg(g4 + q);
-                    c[4 * q + 0] = f25_add(c[4 * q + 0], pc.x);
-                    c[4 * q + 1] = f25_add(c[4 * q + 1], pc.y);
-                    c[4 * q + 2] = f25_add(c[4 * q + 2], pc.z);
-                    c[4 * q + 3] = f25_add(c[4 * q + 3], pc.w);
-                }
-            }
-            if (mode != kMidLast) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) g4[q] = make_uint4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
-            }
-        }
-        if (mode == kMidAlone || mode == kMidLast) {
-            dft_reg_f25<4>(c);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) sA[p0 + i] = c[bitrev_c(i, 4)];
-        }
-    }
-    if (mode == kMidFirst || mode == kMidInner) {
-        __syncthreads();  // sA / sB free for the next row
-        return;
-    }
-    __syncwarp();
-    inv_step25<13, 1, 0, 1>(sA, sA, tab);
-    __syncthreads();
-    inv_step25<13, 0, 0, 1>(sA, sA, tab);
-    __syncthreads();
+// a b L^-1 for any 32-bit a, b (DFT outputs) -> [0, 2q).  linv packs the
+// Shoup pair of L^-1 2^32 mod q (low word) and its quotient (high word):
+// mont(red a, red b) = a b 2^-32, and the Shoup product restores the 2^32.
+__device__ __forceinline__ uint32_t prod25(uint32_t a, uint32_t b, uint64_t linv) {
+    return f25_shoup(f25_mont(f25_red(a), f25_red(b)), (uint32_t)linv, (uint32_t)(linv >> 32));
 }
 
 }  // namespace cm

@@ -121,8 +121,10 @@ struct FieldF25 {
     __device__ static __forceinline__ T rot(T x, int lh, int pos) {
         return pos == 0 ? f25_red(x) : f25_shoup(x, kF25W32[(16 >> lh) * pos], kF25W32Q[(16 >> lh) * pos]);
     }
-    // a b L^-1 for any a and b < 12 q (a DFT output) -> (0, 2q)
-    __device__ static __forceinline__ T prod(T a, T b, T linv) { return f25_mont(f25_mont(f25_red(a), b), linv); }
+    // a b L^-1 for any a, b -> (0, 2q); linv = L^-1 2^64 mod q
+    __device__ static __forceinline__ T prod(T a, T b, T linv) {
+        return f25_mont(f25_mont(f25_red(a), f25_red(b)), linv);
+    }
     __device__ static __forceinline__ T red(T x) { return f25_red(x); }
     __device__ static __forceinline__ T canon(T x) { return f25_canon(x); }
 };
@@ -241,12 +243,14 @@ struct BitMap {
 // order (position -> frequency: pos_to_freq).  The inverse applies the exact
 // inverse of each step in reverse order, mapping that order back to natural.
 // ---------------------------------------------------------------------------
-__host__ __device__ constexpr int st_n(int logr) { return (logr + 4) / 5; }
-__host__ __device__ constexpr int st_q(int logr, int j) {
+__host__ __device__ __forceinline__ constexpr int st_n(int logr) { return (logr + 4) / 5; }
+__host__ __device__ __forceinline__ constexpr int st_q(int logr, int j) {
     return logr / st_n(logr) + (j < logr % st_n(logr) ? 1 : 0);
 }
-__host__ __device__ constexpr int st_off(int logr, int j) {
-    return j == 0 ? 0 : st_off(logr, j - 1) + st_q(logr, j - 1);
+__host__ __device__ __forceinline__ constexpr int st_off(int logr, int j) {
+    int o = 0;
+    for (int i = 0; i < j; ++i) o += st_q(logr, i);
+    return o;
 }
 
 __device__ __forceinline__ int bitrev_c(int k, int lg) {
@@ -264,13 +268,27 @@ __device__ __forceinline__ int bitrev_c(int k, int lg) {
 // modulo X^len - zeta and X^len + zeta, (lo, hi) -> (lo + zeta hi, lo - zeta hi),
 // where block b of the stage has zeta = omega_(2^(s+1))^bitrev_s(b); after the
 // last stage position b holds the residue modulo X - omega^bitrev(b), i.e.
-// X[bitrev(b)].  Inputs in [0, 2q); the first stage (zeta = 1) doubles the
-// bound to 4q, every later one adds 2q (t = zeta hi is brought to [0, 2q) by the
-// Shoup product, or by red when zeta = 1): outputs below (2 + 2 LQ) q <= 12 q.
+// X[bitrev(b)].  Inputs in [0, 2q).  A block with zeta != 1 brings
+// t = zeta hi to [0, 2q) by the Shoup product and adds 2q to the bound of its
+// inputs.  Block 0 (zeta = 1) adds hi unreduced, (lo + hi, lo - hi + B q) for
+// inputs below B q, doubling the bound, as long as a doubled bound plus 2q per
+// remaining stage stays within 24 q; otherwise it reduces hi (red) and adds 2q.
+// Outputs below (f25_dft_bound(LQ)) q: 4, 8, 16, 18, 20 for LQ = 1 .. 5.
+// block 0's input bound at stage s (in units of q; 2 at stage 0)
+__host__ __device__ __forceinline__ constexpr int f25_b0_bound(int lq, int s) {
+    int b = 2;
+    for (int j = 0; j < s; ++j) b = (2 * b + 2 * (lq - 1 - j) <= 24) ? 2 * b : b + 2;
+    return b;
+}
+__host__ __device__ __forceinline__ constexpr bool f25_b0_reduces(int lq, int s) {
+    return s > 0 && 2 * f25_b0_bound(lq, s) + 2 * (lq - 1 - s) > 24;
+}
+__host__ __device__ constexpr int f25_dft_bound(int lq) { return f25_b0_bound(lq, lq); }
 template <int LQ>
 __device__ __forceinline__ void dft_reg_f25(uint32_t *v) {
     constexpr int RD = 1 << LQ;
     static_assert(LQ >= 1 && LQ <= 5, "register sub-transforms of length 2 .. 32");
+    static_assert(f25_dft_bound(LQ) <= 24 && (uint64_t)f25_dft_bound(LQ) * F25_Q < (1ull << 32), "headroom");
 #pragma unroll
     for (int s = 0; s < LQ; ++s) {
         const int len = RD >> (s + 1);
@@ -281,16 +299,16 @@ __device__ __forceinline__ void dft_reg_f25(uint32_t *v) {
             for (int j = 0; j < len; ++j) {
                 const int i0 = b * 2 * len + j, i1 = i0 + len;
                 const uint32_t x = v[i0], y = v[i1];
-                uint32_t t;
-                if (s == 0) {
-                    t = y;
-                } else if (b == 0) {
-                    t = f25_red(y);
+                uint32_t t, add;
+                if (b == 0 && !f25_b0_reduces(LQ, s)) {
+                    t = y;  // zeta = 1, unreduced: both inputs below B q
+                    add = (uint32_t)f25_b0_bound(LQ, s) * F25_Q;
                 } else {
-                    t = f25_shoup(y, kF25W32[e], kF25W32Q[e]);
+                    t = b == 0 ? f25_red(y) : f25_shoup(y, kF25W32[e], kF25W32Q[e]);
+                    add = 2 * F25_Q;
                 }
                 v[i0] = x + t;
-                v[i1] = x - t + 2 * F25_Q;
+                v[i1] = x - t + add;
             }
         }
     }

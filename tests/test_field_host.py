@@ -51,12 +51,24 @@ def test_field25_routines(tmp_path):
     assert "field25_check: ok" in r.stdout
 
 
+def f25_b0_bound(lq, s):
+    # block 0's input bound (units of q) at stage s, as dft_reg_f25 plans it:
+    # double it (no reduction of hi) while a doubled bound plus 2 per remaining
+    # stage stays within 24, else reduce hi and add 2
+    b = 2
+    for j in range(s):
+        b = 2 * b if 2 * b + 2 * (lq - 1 - j) <= 24 else b + 2
+    return b
+
+
 def test_lazy_radix_dft_model():
     # The register sub-transform of the lazily reduced field (dft_reg_f25):
     # Cooley-Tukey butterflies on natural-order input, stage s splitting block
     # b with zeta = omega_(2^(s+1))^bitrev_s(b), give X[k] at position
-    # bitrev(k), and from inputs in [0, 2q) every intermediate stays below
-    # (2 + 2 LQ) q < 2^32.  Modelled step for step with exact integers.
+    # bitrev(k); block 0 (zeta = 1) adds hi unreduced while its bound allows.
+    # From inputs in [0, 2q) every intermediate stays below the planned bound
+    # (4, 8, 16, 18, 20 q for LQ = 1 .. 5) < 25 q < 2^32.  Modelled step for
+    # step with exact integers.
     import random
     q = 5 * 2 ** 25 + 1
     w32 = pow(243, 2 ** 20, q)
@@ -78,17 +90,25 @@ def test_lazy_radix_dft_model():
         for _ in range(300):
             v = [rng.choice([0, 1, q, 2 * q - 1, rng.randrange(2 * q)]) for _ in range(rd)]
             x = list(v)
+            final = f25_b0_bound(lq, lq)
+            assert final == [4, 8, 16, 18, 20][lq - 1]
             for s in range(lq):
                 ln = rd >> (s + 1)
+                bb = f25_b0_bound(lq, s)
+                reduce0 = s > 0 and 2 * bb + 2 * (lq - 1 - s) > 24
                 for b in range(1 << s):
                     zeta = pow(w32, (32 >> (s + 1)) * brv(b, s), q)
                     for j in range(ln):
                         i0 = b * 2 * ln + j
                         i1 = i0 + ln
-                        t = v[i1] if s == 0 else (red(v[i1]) if b == 0 else shoup(v[i1], zeta))
-                        assert t < 2 * q or s == 0
-                        v[i0], v[i1] = v[i0] + t, v[i0] - t + 2 * q
-                        assert 0 <= v[i1] and max(v[i0], v[i1]) < (2 + 2 * (s + 1)) * q < 2 ** 32
+                        if b == 0 and not reduce0:
+                            t, add = v[i1], bb * q
+                            assert max(v[i0], v[i1]) < bb * q
+                        else:
+                            t, add = (red(v[i1]) if b == 0 else shoup(v[i1], zeta)), 2 * q
+                            assert t < 2 * q
+                        v[i0], v[i1] = v[i0] + t, v[i0] - t + add
+                        assert 0 <= v[i1] and max(v[i0], v[i1]) < final * q < 2 ** 32
             for k in range(rd):
                 assert v[brv(k, lq)] % q == sum(x[j] * pow(wr, j * k, q) for j in range(rd)) % q
 

@@ -173,6 +173,44 @@ def test_dense_tail_dodis_precondition(ctxs):
         assert ctxs[15].device_status()[0] == native.CM_EPRECOND
 
 
+FUSED_CASES = [
+    # (kind, n, m, max_transform_lg, max_sum_blocks): products of 2^22 .. 2^25
+    # over q = 5 * 2^25 + 1 run the fused column passes (tiles of 2^9 .. 2^12
+    # rows); alone, summed in pairs, and in groups of three (inner sums)
+    (T, 2 ** 21, 2 ** 21, 22, 0),
+    (T, 3 * 2 ** 21 + 5, 2 ** 21 - 7, 23, 0),
+    (T, 2 ** 24 - 1000, 12_345, 24, 0),
+    (T, 9_000_001, 777_777, 22, 0),
+    (C, "P9000000", 0.3, 23, 3),
+    (D, "P12000000", 0.4, 24, 2),
+]
+
+
+@pytest.mark.parametrize("kind,n,m,lg,sums", FUSED_CASES)
+def test_fused_passes_sampled(kind, n, m, lg, sums):
+    n, m = resolve(kind, n, m)
+    ctx = native.Context(0, max_transform_lg=lg, max_sum_blocks=sums)
+    q30 = native.Context(0, max_transform_lg=lg, max_sum_blocks=sums, field=native.FIELD_Q30)
+    try:
+        xw = inputs.bernoulli_half(930 + n % 61, n)
+        if kind == D:
+            xw[0] = (xw[0] | np.uint64(1)) & ~np.uint64(2)
+        yw = inputs.bernoulli_half(931 + n % 59, ybits(kind, n, m))
+        z = run(ctx, kind, n, m, xw, yw)
+        # every bit equals the other field's kernels; sampled rows the oracle's
+        assert (z == run(q30, kind, n, m, xw, yw)).all()
+        rows = sample_rows(m, 48, 7)
+        rowf = {T: lambda: oracle.toeplitz_rows(xw, n, yw, m, rows),
+                C: lambda: oracle.circulant_rows(xw, n, yw, m, rows),
+                D: lambda: oracle.dodis_rows(xw, yw, n, m, rows)}[kind]
+        assert (out_bits(z, rows) == rowf()).all()
+        if m & 63:
+            assert int(z[-1]) >> (m & 63) == 0
+    finally:
+        ctx.close()
+        q30.close()
+
+
 def test_split_by_cost(cm_ctx):
     # K + m - 1 = 2^22 + 149: shorter products and a dense tail instead of one
     # 2^23 transform
