@@ -6,8 +6,9 @@
 // 2^13 on chip), arranged so that every element crosses shared memory as few
 // times as the steps need:
 //   k25_fwd  the tile's input bits are loaded once per row into shared memory
-//            (C <= 32 bits a row); step 0 reads its 0/1 inputs from there (a
-//            radix-16 step takes its DFTs from the bit table); the last step
+//            (C <= 32 bits a row); step 0 reads its 0/1 inputs from there
+//            into a register DFT (faster here than the radix-16 bit table,
+//            whose random lookups conflict on banks); the last step
 //            multiplies by the pass twiddle omega_N^(col freq) and stores
 //            straight from registers to HBM.
 //   k25_inv  the first step loads straight from HBM and multiplies by the pass
@@ -41,33 +42,80 @@ struct Pass25 {
     static constexpr int LAST = NST - 1;
     static constexpr int QL = st_q(LOGR, LAST), RDL = 1 << QL, OFFL = st_off(LOGR, LAST);
     static constexpr int Q0 = st_q(LOGR, 0), RD0 = 1 << Q0, M0 = R / RD0;
-    // the bit table where two CTAs still fit an SM (not at 2^12 rows, whose
-    // root pairs take 32 KiB)
-    static constexpr bool BTAB = Q0 == 4 && LOGR <= 11;
+    static constexpr int Q1 = st_q(LOGR, 1), RD1 = 1 << Q1, N1 = R / RD0, M1 = N1 / RD1;  // step 1 (of 3)
     using BitsT = std::conditional_t<(C <= 8), uint8_t, std::conditional_t<(C <= 16), uint16_t, uint32_t>>;
+    // The tile holds element e = row * C + col at word tile_at(e): e with the
+    // column bits above log2 C XORed by the last step's block index (mod 32 /
+    // C).  The last step's lanes take C columns of 32 / C consecutive blocks
+    // (stride RD_last C words): without the XOR they would share banks.  The
+    // other steps' lanes take 32 consecutive words, which the XOR (constant
+    // within an aligned group of 32, since RD_last C >= 64) only permutes.
+    static constexpr int SW_SHIFT = QL + NCOL_LG, SW_MASK = C >= 32 ? 0 : 32 / C - 1;
+    static_assert(SW_SHIFT >= 5, "XOR constant within 32-word groups");
     // shared memory layout (32-bit words): tile, step root pairs, P pairs,
-    // row bits, bit table
-    static constexpr int O_STEPS = (sp_size(1 << kTileLg) + 1) & ~1;
+    // row bits
+    static constexpr int O_STEPS = 1 << kTileLg;
     static constexpr int O_P = O_STEPS + st25_smem_words(LOGR);
     static constexpr int O_BITS = O_P + 2 * C * RDL;
-    static constexpr int O_TAB = (O_BITS + (int)(R * sizeof(BitsT) + 3) / 4 + 3) & ~3;
-    static constexpr int W_FWD = O_TAB + (BTAB ? kBitsTable : 0);
+    static constexpr int W_FWD = O_BITS + (int)(R * sizeof(BitsT) + 3) / 4;
     static constexpr int W_INV = O_BITS;
     static_assert(NST >= 2 && C * RDL <= kThreads, "two or more steps; one P entry per thread");
     static_assert(W_FWD * 4 <= 113 * 1024, "two CTAs per SM");
 };
 
-// P[c * RDL + k1] = omega_N^(col k1 2^OFFL) as a Shoup pair (plain root,
+template <int LOGR>
+__device__ __forceinline__ int tile_at(int e) {
+    using PS = Pass25<LOGR>;
+    return e ^ (((e >> PS::SW_SHIFT) & PS::SW_MASK) << PS::NCOL_LG);
+}
+
+// P[k1 * C + c] = omega_N^(col k1 2^OFFL) as a Shoup pair (plain root,
 // quotient), col = col0 + c; omega_N = g25^(2^esh).
 template <int LOGR>
 __device__ __forceinline__ void load_pass_p25(uint2 *P, uint32_t col0, int esh, const RootTables25 &rt) {
     using PS = Pass25<LOGR>;
     const int t = threadIdx.x;
     if (t < PS::C * PS::RDL) {
-        const uint64_t col = col0 + (uint32_t)(t / PS::RDL), k1 = (uint32_t)(t % PS::RDL);
+        const uint64_t col = col0 + (uint32_t)(t & (PS::C - 1)), k1 = (uint32_t)(t >> PS::NCOL_LG);
         const uint32_t E = (uint32_t)(((col * k1) << (PS::OFFL + esh)) & ((1ull << 25) - 1));
         const uint32_t w = f25_canon(f25_mont(big_root_f<FieldF25>(rt.big_lo_fwd, rt.big_hi_fwd, E), 1u));
         P[t] = make_uint2(w, f25_shoup_q(w));
+    }
+}
+
+// The middle step (step 1 of three) of the tile's columns: forward (roots on
+// the outputs) or with every root inverted (roots on the inputs).
+template <int LOGR, bool INV>
+__device__ __forceinline__ void tile_step1_25(uint32_t *tile, const uint32_t *steps) {
+    using PS = Pass25<LOGR>;
+    constexpr int C = PS::C, NCOL_LG = PS::NCOL_LG, RD = PS::RD1, M = PS::M1, N = PS::N1;
+    constexpr int LM = LOGR - PS::Q0 - PS::Q1;  // log2 M
+    const uint2 *tJ = reinterpret_cast<const uint2 *>(steps) + st25_tab_off(LOGR, 1);
+    for (int item = threadIdx.x; item < (PS::R / RD) * C; item += kThreads) {
+        const int c = item & (C - 1), rest = item >> NCOL_LG;
+        const int i2 = rest & (M - 1), blk = rest >> LM;
+        const int e0 = ((blk * N + i2) << NCOL_LG) + c;
+        const uint2 *tw = tJ + i2;
+        uint32_t v[RD];
+        if constexpr (!INV) {
+#pragma unroll
+            for (int i1 = 0; i1 < RD; ++i1) v[i1] = tile[tile_at<LOGR>(e0 + ((i1 * M) << NCOL_LG))];
+            dft_reg_f25<PS::Q1>(v);
+#pragma unroll
+            for (int k1 = 0; k1 < RD; ++k1) {
+                const uint32_t x = v[bitrev_c(k1, PS::Q1)];
+                tile[tile_at<LOGR>(e0 + ((k1 * M) << NCOL_LG))] = k1 ? shoup_pair(x, tw[(k1 - 1) * M]) : f25_red(x);
+            }
+        } else {
+#pragma unroll
+            for (int k1 = 0; k1 < RD; ++k1) {
+                const uint32_t x = tile[tile_at<LOGR>(e0 + ((k1 * M) << NCOL_LG))];
+                v[k1] = k1 ? shoup_pair(x, tw[(k1 - 1) * M]) : f25_red(x);
+            }
+            dft_reg_f25<PS::Q1>(v);
+#pragma unroll
+            for (int i1 = 0; i1 < RD; ++i1) tile[tile_at<LOGR>(e0 + ((i1 * M) << NCOL_LG))] = v[bitrev_c(i1, PS::Q1)];
+        }
     }
 }
 
@@ -87,7 +135,6 @@ k25_fwd(uint32_t *__restrict__ data1, BitMap map1, uint32_t *__restrict__ data2,
     uint32_t *steps = tile + PS::O_STEPS;
     uint2 *P = reinterpret_cast<uint2 *>(tile + PS::O_P);
     BitsT *sbits = reinterpret_cast<BitsT *>(tile + PS::O_BITS);
-    uint32_t *tab = tile + PS::O_TAB;
 
     const bool second = blockIdx.x >= ntiles;
     const uint32_t t_ = second ? blockIdx.x - ntiles : blockIdx.x;
@@ -101,10 +148,6 @@ k25_fwd(uint32_t *__restrict__ data1, BitMap map1, uint32_t *__restrict__ data2,
     const int esh = FieldF25::kAdicity - lgN;
 
     load_steps25<LOGR>(steps, rt.steps);
-    if constexpr (PS::BTAB) {
-        for (int i = threadIdx.x; i < kBitsTable / 4; i += kThreads)
-            reinterpret_cast<uint4 *>(tab)[i] = __ldg(reinterpret_cast<const uint4 *>(rt.bits16) + i);
-    }
     load_pass_p25<LOGR>(P, col0, esh, rt);
     for (int i = threadIdx.x; i < PS::R; i += kThreads) sbits[i] = (BitsT)map.get_run<C>(base + (uint64_t)i * S);
     __syncthreads();
@@ -115,52 +158,37 @@ k25_fwd(uint32_t *__restrict__ data1, BitMap map1, uint32_t *__restrict__ data2,
         for (int item = threadIdx.x; item < M0 * C; item += kThreads) {
             const int c = item & (C - 1), i2 = item >> NCOL_LG;
             uint32_t v[RD0];
-            if constexpr (PS::BTAB) {
-                uint32_t p = 0;
 #pragma unroll
-                for (int i1 = 0; i1 < RD0; ++i1) p |= (((uint32_t)sbits[i2 + M0 * i1] >> c) & 1u) << i1;
-                const uint32_t *tlo = tab + (p & 255u), *thi = tab + (p >> 8);
-#pragma unroll
-                for (int k = 0; k < RD0; ++k) {
-                    const uint32_t a = tlo[k << 8], b = thi[k << 8];
-                    v[bitrev_c(k, PS::Q0)] = (k & 1) ? f25_sub(a, b) : f25_add(a, b);
-                }
-            } else {
-#pragma unroll
-                for (int i1 = 0; i1 < RD0; ++i1) v[i1] = ((uint32_t)sbits[i2 + M0 * i1] >> c) & 1u;
-                dft_reg_f25<PS::Q0>(v);
-            }
+            for (int i1 = 0; i1 < RD0; ++i1) v[i1] = ((uint32_t)sbits[i2 + M0 * i1] >> c) & 1u;
+            dft_reg_f25<PS::Q0>(v);
             const uint2 *tw = tw0 + i2;
-            const int p0 = sp((i2 << NCOL_LG) + c);
-            constexpr int STRIDE = (M0 << NCOL_LG) + (M0 << NCOL_LG) / 32;  // M0 C >= 32
+            const int e0 = item;  // (i2 << NCOL_LG) + c
 #pragma unroll
             for (int k1 = 0; k1 < RD0; ++k1) {
-                uint32_t x = v[bitrev_c(k1, PS::Q0)];
-                x = k1 ? shoup_pair(x, tw[(k1 - 1) * M0]) : f25_red(x);
-                tile[p0 + k1 * STRIDE] = x;
+                const uint32_t x = v[bitrev_c(k1, PS::Q0)];
+                tile[tile_at<LOGR>(e0 + ((k1 * M0) << NCOL_LG))] = k1 ? shoup_pair(x, tw[(k1 - 1) * M0]) : f25_red(x);
             }
         }
     }
     __syncthreads();
     if constexpr (PS::NST == 3) {
-        fwd_step25<LOGR, 1, NCOL_LG, 1>(tile, tile, steps);
+        tile_step1_25<LOGR, false>(tile, steps);
         __syncthreads();
     }
     // last step (no step roots): pass twiddle, store to HBM
     for (int item = threadIdx.x; item < (PS::R / RDL) * C; item += kThreads) {
         const int c = item & (C - 1), blk = item >> NCOL_LG;
-        const int e0 = ((blk * RDL) << NCOL_LG) + c;
-        uint32_t v[RDL];
-#pragma unroll
-        for (int i1 = 0; i1 < RDL; ++i1) v[i1] = tile[sp(e0 + i1 * C)];
-        dft_reg_f25<PS::QL>(v);
         const uint32_t col = col0 + c;
         const uint32_t fb = pos_to_freq<LOGR>((uint32_t)(blk * RDL));
         const uint32_t beta = big_root_f<FieldF25>(rt.big_lo_fwd, rt.big_hi_fwd, (col * fb) << esh);
-        uint32_t *g = data + base + (uint32_t)(blk * RDL) * S + c;
-        const uint2 *pc = P + c * RDL;
+        const int e0 = ((blk * RDL) << NCOL_LG) + c;
+        uint32_t v[RDL];
 #pragma unroll
-        for (int k1 = 0; k1 < RDL; ++k1) g[(uint32_t)k1 * S] = f25_mont(shoup_pair(v[bitrev_c(k1, PS::QL)], pc[k1]), beta);
+        for (int i1 = 0; i1 < RDL; ++i1) v[i1] = tile[tile_at<LOGR>(e0 + (i1 << NCOL_LG))];
+        dft_reg_f25<PS::QL>(v);
+        uint32_t *g = data + base + (uint32_t)(blk * RDL) * S + c;
+#pragma unroll
+        for (int k1 = 0; k1 < RDL; ++k1) g[(uint32_t)k1 * S] = f25_mont(shoup_pair(v[bitrev_c(k1, PS::QL)], P[k1 * C + c]), beta);
     }
 }
 
@@ -193,22 +221,21 @@ k25_inv(const uint32_t *__restrict__ data, int lgN, int lgS, uint8_t *__restrict
     // first step (the forward's last): load from HBM, pass twiddle, DFT
     for (int item = threadIdx.x; item < (PS::R / RDL) * C; item += kThreads) {
         const int c = item & (C - 1), blk = item >> NCOL_LG;
-        const int e0 = ((blk * RDL) << NCOL_LG) + c;
         const uint32_t col = col0 + c;
         const uint32_t fb = pos_to_freq<LOGR>((uint32_t)(blk * RDL));
         const uint32_t beta = big_root_f<FieldF25>(rt.big_lo_fwd, rt.big_hi_fwd, (col * fb) << esh);
         const uint32_t *g = data + base + (uint32_t)(blk * RDL) * S + c;
-        const uint2 *pc = P + c * RDL;
         uint32_t v[RDL];
 #pragma unroll
-        for (int k1 = 0; k1 < RDL; ++k1) v[k1] = f25_mont(shoup_pair(g[(uint32_t)k1 * S], pc[k1]), beta);
+        for (int k1 = 0; k1 < RDL; ++k1) v[k1] = f25_mont(shoup_pair(g[(uint32_t)k1 * S], P[k1 * C + c]), beta);
         dft_reg_f25<PS::QL>(v);
+        const int e0 = ((blk * RDL) << NCOL_LG) + c;
 #pragma unroll
-        for (int i1 = 0; i1 < RDL; ++i1) tile[sp(e0 + i1 * C)] = v[bitrev_c(i1, PS::QL)];
+        for (int i1 = 0; i1 < RDL; ++i1) tile[tile_at<LOGR>(e0 + (i1 << NCOL_LG))] = v[bitrev_c(i1, PS::QL)];
     }
     __syncthreads();
     if constexpr (PS::NST == 3) {
-        inv_step25<LOGR, 1, NCOL_LG, 1>(tile, tile, steps);
+        tile_step1_25<LOGR, true>(tile, steps);
         __syncthreads();
     }
     // last step (the forward's step 0): parity of the window positions
@@ -218,12 +245,11 @@ k25_inv(const uint32_t *__restrict__ data, int lgN, int lgS, uint8_t *__restrict
         for (int item = threadIdx.x; item < M0 * C; item += kThreads) {
             const int c = item & (C - 1), i2 = item >> NCOL_LG;
             const uint2 *tw = tw0 + i2;
-            const int p0 = sp((i2 << NCOL_LG) + c);
-            constexpr int STRIDE = (M0 << NCOL_LG) + (M0 << NCOL_LG) / 32;
+            const int e0 = item;
             uint32_t v[RD0];
 #pragma unroll
             for (int k1 = 0; k1 < RD0; ++k1) {
-                const uint32_t x = tile[p0 + k1 * STRIDE];
+                const uint32_t x = tile[tile_at<LOGR>(e0 + ((k1 * M0) << NCOL_LG))];
                 v[k1] = k1 ? shoup_pair(x, tw[(k1 - 1) * M0]) : f25_red(x);
             }
             dft_reg_f25<PS::Q0>(v);
