@@ -203,7 +203,9 @@ cm_status cm_extract_host(cm_ctx *ctx, int kind, const uint64_t *x_host, uint64_
  * that device up: it looks up the arrays' device addresses and fills the root
  * tables with a kernel on the legacy default stream, then synchronizes.  Make
  * that first call before any stream capture.  Later calls only enqueue work
- * on `stream`.
+ * on `stream`.  A device reset gives the device a new CUDA context, in which
+ * the arrays start over: the first call after it sets the device up again
+ * (the set-up remembers the context it ran in).
  *
  * All calls on a device share the one scratch array, which keeps the last
  * call's contents (nothing in it needs to start at zero: every word is written

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <vector>
 
 #include "cm.h"
@@ -13,6 +14,25 @@ namespace cm {
 constexpr uint32_t kFlagPrecond = CM_FLAG_PRECOND;
 constexpr uint32_t kFlagTimeout = CM_FLAG_TIMEOUT;
 constexpr size_t kTableWords = 8192 + 4 * 65536;  // resident root tables
+
+// The unique id of the calling thread's current CUDA context (0 if there is
+// none or the driver cannot tell): it changes when a device reset replaces the
+// device's primary context, which drops every per-context setting.
+uint64_t current_ctx_id();
+
+// Raise KERN's dynamic shared-memory limit to `bytes` once per CUDA context
+// instead of on every launch (the runtime call costs host time that a short
+// extraction would wait for).  A new context (after a device reset) sets it
+// again.
+template <auto KERN>
+inline cudaError_t smem_attr_once(int bytes) {
+    static std::atomic<uint64_t> done_ctx{0};
+    const uint64_t id = current_ctx_id();
+    if (id && done_ctx.load(std::memory_order_acquire) == id) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(KERN, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && id) done_ctx.store(id, std::memory_order_release);
+    return e;
+}
 
 // Transform fields (see ntt_device.cuh).
 constexpr int kFieldGL = 0;   // Goldilocks, 64-bit elements, L <= 2^32

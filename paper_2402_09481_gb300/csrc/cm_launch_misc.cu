@@ -119,7 +119,7 @@ static cudaError_t launch_middle_f(void *A, const void *B, void *C, int mode, ui
                                    const RootTablesT<typename F::T> &rt, int nsm, cudaStream_t st) {
     using T = typename F::T;
     const size_t sm = (2 * sp_size(1 << kMidLgMax) + (1 << kMidLgMax)) * sizeof(T);
-    cudaError_t e = cudaFuncSetAttribute(k_middle<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = smem_attr_once<k_middle<F>>((int)sm);
     if (e != cudaSuccess) return e;
     const uint64_t rows = L >> kMidLgMax;
     const uint64_t per_sm = sizeof(T) == 4 ? 2 : 1;  // resident CTAs per SM (shared memory, registers)

@@ -27,7 +27,7 @@ static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st) {
         (BTAB ? pass_table_off<F, LOGR>() + kBitsTable : pass_tw_off<F, LOGR>() + pass_tw_words<F, LOGR>()) *
         sizeof(T);
     auto kern = k_pass<F, LOGR, INV, BITS_IN, PARITY_OUT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = smem_attr_once<k_pass<F, LOGR, INV, BITS_IN, PARITY_OUT>>((int)sm);
     if (e != cudaSuccess) return e;
     const uint64_t tiles = a.L >> TILE_LG;
     const uint64_t grid = a.data2 ? 2 * tiles : tiles;

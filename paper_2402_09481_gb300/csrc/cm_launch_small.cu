@@ -12,7 +12,7 @@ static cudaError_t launch_small_f(const Launch &q, const RootTablesT<typename F:
     const size_t tw = F::kLazy ? st25_smem_words(LG) : (1 << LG);
     const size_t sm = (2 * sp_size(1 << LG) + tw) * sizeof(typename F::T);
     auto kern = k_fused_small<F, LG>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = smem_attr_once<k_fused_small<F, LG>>((int)sm);
     if (e != cudaSuccess) return e;
     kern<<<1, kThreads, sm, q.stream>>>(q.amap, q.bmap, q.lo, q.m, q.linv, q.z, q.pre, q.status, rt);
     return cudaGetLastError();

@@ -29,6 +29,7 @@ static __device__ __align__(256) uint32_t g_noalloc_status[64];
 
 struct NoAllocDevice {
     bool ready;
+    uint64_t ctx_id;  // the CUDA context the set-up ran in (current_ctx_id)
     unsigned char *scratch;
     uint64_t *tables;
     uint32_t *status;
@@ -64,10 +65,15 @@ __global__ void k_noalloc_tables(uint64_t *t, uint64_t w, uint64_t g, uint64_t g
     }
 }
 
+// Set-up of device dev (current), once per CUDA context: a device reset
+// replaces the primary context, whose __device__ arrays start over (addresses
+// and root tables), so a new context runs the set-up again.
 cm_status setup_device(int dev, NoAllocDevice **out) {
     if (dev < 0 || dev >= kMaxDevices) return CM_EDEVICE;
     std::lock_guard<std::mutex> lock(g_setup_mu);
     NoAllocDevice &d = g_devices[dev];
+    const uint64_t ctx = current_ctx_id();
+    if (d.ready && (ctx == 0 || ctx != d.ctx_id)) d.ready = false;
     if (!d.ready) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return CM_EDEVICE;
@@ -85,6 +91,7 @@ cm_status setup_device(int dev, NoAllocDevice **out) {
         if (cudaGetLastError() != cudaSuccess) return CM_EDEVICE;
         if (cudaMemsetAsync(d.status, 0, sizeof(uint32_t) * 64, 0) != cudaSuccess) return CM_EDEVICE;
         if (cudaStreamSynchronize(0) != cudaSuccess) return CM_EDEVICE;
+        d.ctx_id = ctx;
         d.ready = true;
     }
     *out = &d;

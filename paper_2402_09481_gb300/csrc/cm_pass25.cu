@@ -401,7 +401,7 @@ static cudaError_t launch_fwd25_t(const PassArgs &a, cudaStream_t st) {
     using PS = Pass25<LOGR>;
     const size_t sm = PS::W_FWD * sizeof(uint32_t);
     auto kern = k25_fwd<LOGR>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = smem_attr_once<k25_fwd<LOGR>>((int)sm);
     if (e != cudaSuccess) return e;
     const uint32_t tiles = (uint32_t)(a.L >> kTileLg);
     const uint32_t grid = a.data2 ? 2 * tiles : tiles;
@@ -415,7 +415,7 @@ static cudaError_t launch_inv25_t(const PassArgs &a, cudaStream_t st) {
     using PS = Pass25<LOGR>;
     const size_t sm = PS::W_INV * sizeof(uint32_t);
     auto kern = k25_inv<LOGR>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = smem_attr_once<k25_inv<LOGR>>((int)sm);
     if (e != cudaSuccess) return e;
     const uint32_t tiles = (uint32_t)(a.L >> kTileLg);
     kern<<<tiles, kThreads, sm, st>>>(static_cast<const uint32_t *>(a.data), a.lgN, a.lgS, a.par, a.lo, a.m, a.rt25);
@@ -441,7 +441,7 @@ cudaError_t launch_pass25(const PassArgs &a, int logr, cudaStream_t st) {
 cudaError_t launch_middle25(void *A, const void *B, void *C, int mode, uint64_t L, uint64_t linv,
                             const RootTables25 &rt, int nsm, cudaStream_t st) {
     const size_t sm = 2 * kMid1Pairs * sizeof(uint32_t) + (kMid0Words + 2 * sp_size(1 << kMidLgMax)) * sizeof(uint32_t);
-    cudaError_t e = cudaFuncSetAttribute(k25_middle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = smem_attr_once<k25_middle>((int)sm);
     if (e != cudaSuccess) return e;
     const uint64_t rows = L >> kMidLgMax;
     const uint64_t grid = rows < 2ull * nsm ? rows : 2ull * nsm;
