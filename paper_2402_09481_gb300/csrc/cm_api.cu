@@ -152,17 +152,16 @@ bool make_plan(int kind, uint64_t n, uint64_t m, Plan *p, int fields) {
 // ---------------------------------------------------------------------------
 
 // Measured on one GB300 (SM clock 2070 MHz): ms per extraction of transform
-// length 2^lg (Toeplitz, K = L/2 + 1, m = L/4); below 2^16 launch latency
-// dominates and the figures are floors.
+// length 2^lg (Toeplitz, K = L/2 + 1, m = L/4, one transform); below 2^21
+// launch latency dominates and the figures are floors.
 static const double kCostF30[kF30MaxLg + 1] = {
-    0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,   0.02,   0.02,
+    0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,   0.02,   0.02,   0.02,   0.02,
     0.02,  0.02,  0.02,  0.080, 0.081, 0.0822, 0.0829, 0.0857, 0.0950, 0.0991, 0.1162,
     0.1907, 0.3389, 0.6710, 1.3995, 2.6839, 5.4039, 10.960, 22.246, 45.643};
-// F25: estimated from the F30 figures until measured (lazy butterflies).
 static const double kCostF25[kF25MaxLg + 1] = {
-    0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,  0.02,   0.02,   0.02,
-    0.02,  0.02,  0.02,  0.060, 0.061, 0.0620, 0.0625, 0.0640, 0.0700, 0.0720, 0.0800,
-    0.1200, 0.2000, 0.3900, 0.8000};
+    0.02,   0.02,   0.02,   0.02,   0.02,   0.02,   0.02,   0.02,   0.02,   0.02,   0.02,
+    0.02,   0.02,   0.02,   0.0551, 0.0582, 0.0579, 0.0598, 0.0616, 0.0632, 0.0653, 0.0824,
+    0.1060, 0.1668, 0.3264, 0.7317};
 static const double kCostGL[33] = {
     0.03,  0.03,  0.03,  0.03,  0.03,  0.03,  0.03,  0.03,  0.03,   0.03,   0.03,
     0.03,  0.03,  0.03,  0.130, 0.133, 0.1356, 0.1419, 0.1459, 0.1604, 0.1678, 0.2221,
