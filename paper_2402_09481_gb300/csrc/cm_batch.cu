@@ -79,8 +79,8 @@ __device__ void do_small(const BatchInst &I, const typename F::T *tw, typename F
     const uint64_t nwords = (I.m + 63) >> 6;
     for (uint64_t w = warp; w < nwords; w += kThreads / 32) {
         const uint64_t p0 = (w << 6) + lane, p1 = p0 + 32;
-        const uint32_t b0 = (p0 < I.m) ? (uint32_t)(sA[sp((int)(I.lo + p0))] & 1u) : 0u;
-        const uint32_t b1 = (p1 < I.m) ? (uint32_t)(sA[sp((int)(I.lo + p1))] & 1u) : 0u;
+        const uint32_t b0 = (p0 < I.m) ? (uint32_t)(F::canon(sA[sp((int)(I.lo + p0))]) & 1u) : 0u;
+        const uint32_t b1 = (p1 < I.m) ? (uint32_t)(F::canon(sA[sp((int)(I.lo + p1))]) & 1u) : 0u;
         const uint32_t w0 = __ballot_sync(0xffffffffu, b0);
         const uint32_t w1 = __ballot_sync(0xffffffffu, b1);
         if (lane == 0) I.z[w] = bad ? 0ull : ((uint64_t)w1 << 32 | w0);
@@ -103,7 +103,7 @@ __device__ void do_pass(const BatchInst &I, int operand, uint32_t tile, const ty
         const uint64_t g = col0 + ((uint64_t)i << lgS) + c;
         T v;
         if (INV) {
-            v = __ldcg(data + g);
+            v = F::red(__ldcg(data + g));  // lazy fields: below 2q before a product by a root below 2q
             const uint64_t k = pos_to_freq_rt(i, logr);
             const uint32_t E = (uint32_t)(((col0 + c) * k) << esh);
             if (E) v = F::twmul(v, big_root_f<F>(rt.big_lo_inv, rt.big_hi_inv, E));
@@ -123,7 +123,7 @@ __device__ void do_pass(const BatchInst &I, int operand, uint32_t tile, const ty
         const uint64_t g = col0 + ((uint64_t)i << lgS) + c;
         if (INV) {
             const uint64_t p = g - I.lo;
-            if (g >= I.lo && p < I.m) I.par[p] = (uint8_t)(v & 1u);
+            if (g >= I.lo && p < I.m) I.par[p] = (uint8_t)(F::canon(v) & 1u);
         } else {
             const uint64_t k = pos_to_freq_rt(i, logr);
             const uint32_t E = (uint32_t)(((col0 + c) * k) << esh);
@@ -259,8 +259,9 @@ k_batch(const BatchInst *__restrict__ insts, const WorkItem *__restrict__ items,
 }  // namespace
 
 static size_t round256(size_t v) { return (v + 255) & ~size_t(255); }
-// The work list runs every instance (L <= 2^25) over the 32-bit field.
-using BatchField = FieldF30;
+// The work list runs every instance (L <= 2^25) over the lazily reduced field
+// of 5 * 2^25 + 1 (exact: every count is at most K <= L <= 2^25 < q).
+using BatchField = FieldF25;
 using BatchT = BatchField::T;
 static const size_t kBatchSmem = (8192 + 2 * (size_t)sp_size(1 << kMidLgMax)) * sizeof(BatchT);
 
@@ -283,7 +284,7 @@ int batch_grid(int nsm) {
 }
 
 cudaError_t launch_k_batch(const BatchInst *insts, const WorkItem *items, uint32_t nitems, uint32_t *ctrl,
-                           uint32_t *status, const RootTables30 &rt, int grid, cudaStream_t st) {
+                           uint32_t *status, const RootTables25 &rt, int grid, cudaStream_t st) {
     k_batch<BatchField><<<grid, kThreads, kBatchSmem, st>>>(insts, items, nitems, ctrl, status, rt);
     return cudaGetLastError();
 }
@@ -312,7 +313,7 @@ void build_worklist(const cm_desc *descs, const Plan *plans, const uint32_t *idx
         I.z = d.z;
         I.lo = p.lo;
         I.m = p.m;
-        I.linv = f30_linv_mont2(p.L);
+        I.linv = f25_linv_mont2(p.L);
         I.nx = p.n;
         I.lg = p.lg;
         I.kind = p.kind;
@@ -419,7 +420,7 @@ static cm_status batch_enqueue(cm_batch *b, cudaStream_t st) {
         if (cudaMemsetAsync(b->d_ctrl, 0, b->ctrl_words * sizeof(uint32_t), st) != cudaSuccess) return CM_EDEVICE;
         ProfScope ps(ctx, "k_batch", st);
         k_batch<BatchField><<<b->grid, kThreads, kBatchSmem, st>>>(b->d_insts, b->d_items, b->nitems, b->d_ctrl,
-                                                         ctx->d_status, ctx->rt30);
+                                                         ctx->d_status, ctx->rt25);
         if (cudaGetLastError() != cudaSuccess) return CM_EDEVICE;
         b->kernel_launches += 1;
     }

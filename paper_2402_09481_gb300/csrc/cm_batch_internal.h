@@ -58,6 +58,6 @@ int batch_grid(int nsm);
 
 // One launch of the work-list kernel; ctrl holds 2 + 4 n zeroed words.
 cudaError_t launch_k_batch(const BatchInst *insts, const WorkItem *items, uint32_t nitems, uint32_t *ctrl,
-                           uint32_t *status, const RootTables30 &rt, int grid, cudaStream_t st);
+                           uint32_t *status, const RootTables25 &rt, int grid, cudaStream_t st);
 
 }  // namespace cm

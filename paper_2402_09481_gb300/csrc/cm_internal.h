@@ -193,8 +193,10 @@ struct PlanOptions {
 };
 // PlanOptions from cm_options (NULL: defaults); false if a value is invalid.
 bool plan_options(const cm_options *opt, PlanOptions *o);
-// The work-list kernel of batches and the server runs over F30: its instances
-// are planned over F30 (Goldilocks in a Goldilocks-only context).
+// Batches and the server plan their instances like single calls restricted to
+// one transform of at most 2^25 for the work-list kernel (which runs every such
+// instance over F25 whatever the plan's field tag); longer ones go through the
+// single-call planner.
 inline int worklist_fields(const PlanOptions &o) { return o.fields == kFieldsGL ? kFieldsGL : kFieldsQ30; }
 bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::vector<Block> *out);
 

@@ -288,7 +288,7 @@ cm_status launch_wave(cm_server *S, Slot &sl, const std::vector<uint64_t> &tk) {
             return CM_EDEVICE;
         ProfScope ps(ctx, "k_batch", sl.st);
         e = launch_k_batch(static_cast<BatchInst *>(sl.insts.dev), static_cast<WorkItem *>(sl.items.dev),
-                           (uint32_t)items.size(), static_cast<uint32_t *>(sl.ctrl.dev), dflags, ctx->rt30, S->grid,
+                           (uint32_t)items.size(), static_cast<uint32_t *>(sl.ctrl.dev), dflags, ctx->rt25, S->grid,
                            sl.st);
         if (e != cudaSuccess) return CM_EDEVICE;
     }

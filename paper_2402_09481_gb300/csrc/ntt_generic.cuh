@@ -1,5 +1,6 @@
 // Runtime-size on-chip transforms for the batched work-list kernel, over a
-// field policy F of ntt_device.cuh.
+// field policy F of ntt_device.cuh (lazily reduced fields: every step brings
+// its DFT inputs below 2q by the root product or F::red, as in ntt_device.cuh).
 //
 // Same mixed-radix decimation-in-frequency steps as ntt_device.cuh (the
 // four-step split of Def. ntt applied recursively over shared memory, with
@@ -47,14 +48,22 @@ __device__ __forceinline__ void step_rt(typename F::T *s0, typename F::T *s1, in
 #pragma unroll
             for (int k1 = 0; k1 < RD; ++k1) {
                 T x = v[bitrev_c(k1, LQ)];
-                if (k1 > 0 && i2 > 0) x = F::twmul(x, tw8192[tw_swz((i2 * k1) << tws)]);
+                if (k1 > 0 && i2 > 0) {
+                    x = F::twmul(x, tw8192[tw_swz((i2 * k1) << tws)]);
+                } else {
+                    x = F::red(x);  // lazy fields: back below 2q for the next step
+                }
                 s[sp(((row0 + (k1 << LM)) << ncol_lg) + c)] = x;
             }
         } else {
 #pragma unroll
             for (int k1 = 0; k1 < RD; ++k1) {
                 T x = s[sp(((row0 + (k1 << LM)) << ncol_lg) + c)];
-                if (k1 > 0 && i2 > 0) x = F::twmul(x, tw8192[tw_swz((8192 - ((i2 * k1) << tws)) & 8191)]);
+                if (k1 > 0 && i2 > 0) {
+                    x = F::twmul(x, tw8192[tw_swz((8192 - ((i2 * k1) << tws)) & 8191)]);
+                } else {
+                    x = F::red(x);
+                }
                 v[k1] = x;
             }
             dft_reg_f<F, LQ>(v);
