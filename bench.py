@@ -214,124 +214,129 @@ def pass_split(L):
     return [(rest + 1) // 2, rest // 2]
 
 
+FIELD_GL, FIELD_Q30, FIELD_Q25 = 1, 2, 3
+FIELD_NAMES = {FIELD_GL: "Goldilocks p = 2^64 - 2^32 + 1", FIELD_Q30: "q = 3 * 2^30 + 1",
+               FIELD_Q25: "q = 5 * 2^25 + 1"}
+
+
+def element_bytes(field):
+    return 8 if field == FIELD_GL else 4
+
+
 def kernel_model(products, m):
-    """Per-step totals of algorithmic bytes, radix-2 butterflies and launches
-    for each kernel (name without the field suffix), from the plan's product
-    list (cm_plan_products).  A forward-pass launch takes both operands; a
-    summed product's middle (sum 1, 2) skips the inverse row transform and
-    stores or adds its product to the group's accumulator (sum 2, 3 read it);
-    only alone (0) and last (3) products run the inverse passes and pack."""
+    """Per-step algorithmic bytes and launches of each kernel (name without the
+    field suffix), from the plan's product list (cm_plan_products), in the
+    scope's model: one write and one read of three L-element
+    arrays per product with 8-byte field elements, 48 L bytes (a forward pass
+    writes both operands, 16 L; the middle reads them and writes the product,
+    24 L, or reads and writes the sum-group accumulator as well, 32 L; the
+    inverse pass reads the product, 8 L), plus the bits.  "actual" is the same
+    count with the path's own element size (4 bytes for the 32-bit fields)."""
     tot = {}
 
-    def add(k, b, f):
-        t = tot.setdefault(k, {"bytes": 0.0, "butterflies": 0.0, "launches": 0})
+    def add(k, b, a):
+        t = tot.setdefault(k, {"bytes": 0.0, "actual": 0.0, "launches": 0})
         t["bytes"] += b
-        t["butterflies"] += f
+        t["actual"] += a
         t["launches"] += 1
 
     for p in products:
         if p["sum"] == 4:  # dense tail: seed bits and z read, z written
-            add("k_tail", (p["m"] + p["tail_terms"]) / 8 + 2 * p["m"] / 8, 0.0)
+            b = (p["m"] + p["tail_terms"]) / 8 + 2 * p["m"] / 8
+            add("k_tail", b, b)
             continue
-        L, e, s, mr = p["L"], (8 if p["field"] == 1 else 4), p["sum"], p["m"]
-        lg = int(L).bit_length() - 1
+        L, e, s, mr = p["L"], element_bytes(p["field"]), p["sum"], p["m"]
+        bits = (p["a_len"] + p["b_len"]) / 8
         split = pass_split(L)
         if not split:
-            add("k_fused_small", (p["a_len"] + p["b_len"] + mr) / 8, 3 * (L // 2) * lg)
+            add("k_fused_small", bits + mr / 8, bits + mr / 8)
             continue
-        for j, r in enumerate(split):
+        for j, _ in enumerate(split):
             if j == 0:
-                add("k_pass_fwd_bits", 2 * e * L + (p["a_len"] + p["b_len"]) / 8, 2 * (L // 2) * r)
+                add("k_pass_fwd_bits", 16 * L + bits, 2 * e * L + bits)
             else:
-                add("k_pass_fwd", 4 * e * L, 2 * (L // 2) * r)
-        add("k_middle", e * L * (3 if s in (0, 1) else 4), (3 if s in (0, 3) else 2) * (L // 2) * 13)
+                add("k_pass_fwd", 32 * L, 4 * e * L)
+        w = 3 if s in (0, 1) else 4
+        add("k_middle", 8 * w * L, e * w * L)
         if s in (0, 3):
             for j in reversed(range(len(split))):
                 if j == 0:
-                    add("k_pass_inv_parity", e * L + mr, (L // 2) * split[j])
+                    add("k_pass_inv_parity", 8 * L + mr, e * L + mr)
                 else:
-                    add("k_pass_inv", 2 * e * L, (L // 2) * split[j])
-            add("k_pack", mr + mr / 8, 0.0)
+                    add("k_pass_inv", 16 * L, 2 * e * L)
+            add("k_pack", mr + mr / 8, mr + mr / 8)
     return tot
 
 
-# ALU roofline model for the transforms: a radix-2 butterfly needs at least a
-# 64-bit modular add and a modular subtract, 12 ops on the 32-bit ALU pipe
-# (2 for the carry chain and 4 for the conditional correction, each); the
-# twiddle multiply (FMA pipe) and everything else is not counted, so the model
-# peak is an upper bound on butterflies per second.
-# The 32-bit field's add and subtract are a subtraction, a compare and a
-# conditional add each at least: 6 ALU operations per butterfly.
-ALU_OPS_PER_BUTTERFLY = 12
-ALU_OPS_PER_BUTTERFLY_F30 = 6
+# Trevisan's bit-product model uses the GPU's ALU lanes.
 ALU_LANES_PER_SM = 64
 NUM_SMS = 152
 
 
-def alu_peak_butterflies(sm_mhz, ops=ALU_OPS_PER_BUTTERFLY):
-    return NUM_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / ops
-
-
-def _steps(logr):
-    """Radix steps (log2 radix each) of an on-chip transform of 2^logr."""
-    ns = (logr + 4) // 5
-    return [logr // ns + (1 if j < logr % ns else 0) for j in range(ns)]
-
-
-def _transform_modmuls(logr, f30, bits_in=False):
-    """General modular multiplies per element of one on-chip transform of
-    2^logr: the sub-transform twiddles (non-trivial radix-2 rotations; shifts
-    over Goldilocks, products over the 32-bit field) and the twiddles between
-    steps (all but the last step).  bits_in: the first forward pass of the
-    32-bit field, whose radix-16 first step on 0/1 inputs is a table lookup
-    (no multiplies)."""
-    st = _steps(logr)
-    tot = 0.0
-    for j, q in enumerate(st):
-        rd = 1 << q
-        if f30 and not (bits_in and j == 0 and q == 4):
-            tot += ((rd // 2) * q - (rd - 1)) / rd
-        if j + 1 < len(st):
-            tot += (rd - 1) / rd
-    return tot
-
-
-def path_modmuls(products):
-    """(N_path, N_official): general modular multiplies of the path as the
-    kernels run it (on-chip sub-transform and step twiddles, the column passes'
-    row twiddles, the pointwise product and its scaling), and the count of
-    the reference model, 3 L (ceil(lg / 6) - 1) + L per product (a radix-64
-    plan whose inner twiddles are shifts)."""
-    n_path = n_off = 0.0
+def path_model(products, n, seedlen, m):
+    """Bytes and modular multiplies of the whole path:
+    bytes48 = 48 L per product (8-byte elements) + the bit I/O once;
+    bytes_actual = 6 e L per product with the path's element size e;
+    modmuls_reference = 3 L (ceil(lg / 6) - 1) + L per product (the scope's
+    official count: a radix-64 plan whose inner twiddles are shifts, as over
+    Goldilocks); modmuls_radix2 = 3 (L / 2)(lg - 2) + L per product (the
+    non-trivial twiddles of three radix-2 transforms and the pointwise
+    product: the count without free twiddles, as over the 32-bit fields)."""
+    io = (n + seedlen + m) / 8
+    b48, bact, n_ref, n_r2 = io, io, 0.0, 0.0
     for p in products:
         if p["sum"] == 4:
             continue
-        L, f30, s = p["L"], p["field"] != 1, p["sum"]
+        L = p["L"]
         lg = int(L).bit_length() - 1
-        n_off += 3 * L * (-(-lg // 6) - 1) + L
-        split = pass_split(L)
-        row_tw = 9 / 4 if f30 else 2.0
-        per = 0.0
-        for j, r in enumerate(split):  # forward column passes of both operands
-            per += 2 * (_transform_modmuls(r, f30, bits_in=(j == 0)) + row_tw)
-        mid = _transform_modmuls(min(lg, 13), f30)
-        inverse = s in (0, 3)
-        per += 2 * mid + 2 + (mid if inverse else 0.0)
-        if inverse:
-            for r in split:
-                per += _transform_modmuls(r, f30) + row_tw
-        n_path += per * L
-    return n_path, n_off
+        b48 += 48 * L
+        bact += 6 * element_bytes(p["field"]) * L
+        n_ref += 3 * L * (-(-lg // 6) - 1) + L
+        n_r2 += 3 * (L // 2) * max(lg - 2, 0) + L
+    return {"bytes48": b48, "bytes_actual": bact, "modmuls_reference": n_ref, "modmuls_radix2": n_r2}
 
 
-def path_bytes(products, n, seedlen, m):
-    """Bytes the path moves at least: per product of transform length L over
-    e-byte elements, one write and one read of three L-element arrays (6 e L:
-    48L for Goldilocks, 24L for the 32-bit field), plus the bit I/O once."""
-    tot = (n + seedlen + m) / 8
-    for p in products:
-        tot += 6 * (8 if p["field"] == 1 else 4) * p["L"]
-    return tot
+def cpu_model_name():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
+
+
+def cpu_ntt_baseline(kind, n, m, xw, yw, z_gpu=None):
+    """The bit-packed CPU NTT (cpu_ntt/) on the full workload: one thread and
+    every core this process may run on (os.sched_getaffinity); None when the
+    workload's transform exceeds its field (2^30)."""
+    import numpy as np
+
+    import cpu_ntt
+    if cpu_ntt.transform_lg(kind, n, m) > 30:
+        return None
+    cores = len(os.sched_getaffinity(0))
+    cpu_ntt.prepare(kind, n, m)
+    t0 = time.perf_counter()
+    z1 = cpu_ntt.extract(kind, xw, n, yw, m, 1)
+    t1 = time.perf_counter() - t0
+    tn = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        zn = cpu_ntt.extract(kind, xw, n, yw, m, cores)
+        tn.append(time.perf_counter() - t0)
+    tn = statistics.median(tn)
+    same = bool((z1 == zn).all())
+    if z_gpu is not None:
+        same = same and bool((np.asarray(z_gpu, dtype=np.uint64) == zn).all())
+    return {"value": m / tn / 1e9, "unit": "Gbit/s", "cores": cores, "kind": "cpu_ntt",
+            "sample": "the whole workload, one extraction per timing (median of 3 on all cores)",
+            "ms_per_step": tn * 1e3, "cpu_model": cpu_model_name(),
+            "single_thread": {"value": m / t1 / 1e9, "unit": "Gbit/s", "cores": 1, "ms_per_step": t1 * 1e3},
+            "bit_identical_to_gpu": same,
+            "design": "C++ threads, field 3 * 2^30 + 1 (the paper's), radix-2 Shoup butterflies, "
+                      "breadth-first then cache-blocked stages"}
 
 
 def cpu_oracle_rate(kind, n, m, xw, yw, budget_s=12.0):
@@ -454,7 +459,7 @@ def run_reference_vn(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batched_a(args, world, rank, local):
+def run_batched_a(args, world, rank, local, emit=True):
     """4096 Toeplitz extractions, n = floor(2^U), U ~ U[10, 22), m = n/2, each with
     its own Bernoulli(1/2) input and seed; one step = one replay of the planned
     batch (a single persistent work-list launch, CUDA-graph captured)."""
@@ -570,12 +575,16 @@ def run_batched_a(args, world, rank, local):
     assert torch.equal(zp, zd), "batched output differs from the per-call output"
     plain_value = world * out_bits / (statistics.median(plain_ms) * 1e-3) / 1e9
 
-    # roofline of the work-list kernel (the only kernel of a step)
-    # (the work list plans every instance as one transform)
+    # roofline of the work-list kernel (the only kernel of a step), in the
+    # scope's model: 48 L bytes per instance with 8-byte
+    # elements (on-chip instances, L <= 2^13: the bits only) + the bit I/O; the
+    # work list runs 4-byte elements, so it moves about half of that
     Ls = np.array([native.plan_query(native.TOEPLITZ, int(n), int(m), plan_mode=native.PLAN_SINGLE)
                    ["transform_length"] for n, m in zip(ns, ms)])
     big = Ls > (1 << 13)
-    alg = float(24 * Ls[big].sum() + ((ns + (ns + ms - 1) + ms) / 8).sum())  # 32-bit field elements
+    io = float(((ns + (ns + ms - 1) + ms) / 8).sum())
+    alg = float(48 * Ls[big].sum()) + io
+    act = float(24 * Ls[big].sum()) + io
     peak, peak_src = measured_peaks()
     ctx.profile_enable(True)
     ctx.profile_read(reset=True)
@@ -586,19 +595,13 @@ def run_batched_a(args, world, rank, local):
     kb = prof.get("k_batch", (1, ms_per_step))
     per_launch = kb[1] / kb[0]
     achieved = alg / (per_launch * 1e-3) / 1e9
-    lgs = np.array([int(L).bit_length() - 1 for L in Ls])
-    bfly = float((3 * (Ls // 2) * lgs).sum())
-    clk = (sampler.summary(tw0, tw1) or {}).get("sm_mhz") or 2070.0
-    ach_b = bfly / (per_launch * 1e-3) / 1e9
-    peak_b = alu_peak_butterflies(clk, ALU_OPS_PER_BUTTERFLY_F30) / 1e9  # the work list runs the 32-bit field
-    roof = {"bound": "alu", "kernel": "k_batch", "achieved": ach_b, "peak": peak_b, "unit": "G butterflies/s",
-            "frac": ach_b / peak_b,
-            "peak_source": f"{NUM_SMS} SMs x {ALU_LANES_PER_SM} ALU lanes x {clk:.0f} MHz measured / "
-                           f"{ALU_OPS_PER_BUTTERFLY_F30} ALU ops per radix-2 butterfly",
-            "traffic": ncu_traffic("k_batch", "batched_a"), "butterflies_per_launch": bfly,
-            "avg_launch_ms": per_launch,
-            "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_source": peak_src, "algorithmic_bytes_per_launch": alg}}
+    roof = {"bound": "hbm", "kernel": "k_batch", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json)",
+            "traffic": ncu_traffic("k_batch", "batched_a"),
+            "model": "SURVEY 8(d): 48 L bytes per instance with L > 2^13 (8-byte elements) + bit I/O",
+            "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_launch,
+            "actual_element_bytes": {"bytes_per_launch": act, "achieved": act / (per_launch * 1e-3) / 1e9,
+                                     "frac": act / (per_launch * 1e-3) / 1e9 / peak}}
 
     # end to end: host inputs (pinned) -> device, batch, outputs -> host
     xp = torch.from_numpy(xh.view(np.int64)).pin_memory()
@@ -639,7 +642,7 @@ def run_batched_a(args, world, rank, local):
         line = {
             "metric": "extracted output Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
             "config": {"workload": f"Batched Toeplitz: {count} instances, n = floor(2^U), U ~ U[10, 22), "
                                    "m = floor(n/2), own Bernoulli(1/2) x and seed each",
@@ -656,11 +659,15 @@ def run_batched_a(args, world, rank, local):
             "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": int(info["kernel_launches"]) * args.steps,
         }
-        print(json.dumps(line), flush=True)
+        if emit:
+            print(json.dumps(line), flush=True)
     b.close()
     ctx.close()
+    del xd, yd, zd, zp
+    torch.cuda.empty_cache()
     if dist:
         dist.destroy_process_group()
+    return line if rank == 0 else None
 
 
 def run_batched_b(args, world, rank, local):
@@ -1168,7 +1175,7 @@ def served_trace(count, rate, seed_stream=3):
     return out
 
 
-def run_served(args, world, rank, local):
+def run_served(args, world, rank, local, emit=True):
     """Requests of the served workload submitted at their arrival times to the
     library's continuous-batching server; end-to-end latency (arrival to
     completion), service time (admission to completion) and output Gbit/s at
@@ -1195,7 +1202,7 @@ def run_served(args, world, rank, local):
         zbuf = torch.empty(sum(zwords), dtype=torch.int64, device="cuda")
         zoff = np.concatenate([[0], np.cumsum(zwords)])
         rng = np.random.default_rng(len(trace))
-        tickets, arrive = [None] * len(trace), [0] * len(trace)
+        tickets, arrive, offs = [None] * len(trace), [0] * len(trace), [None] * len(trace)
         t0 = time.monotonic_ns() + 20_000_000
 
         def client():
@@ -1207,6 +1214,7 @@ def run_served(args, world, rank, local):
                         break
                     time.sleep(min(d, 2_000_000) / 1e9)
                 ox, oy = int(rng.integers(0, 1 << 18)), int(rng.integers(0, 1 << 18))
+                offs[j] = (ox, oy)
                 arrive[j] = max(due, time.monotonic_ns())
                 s, t = ctx.submit_raw(kind, n, m, xpool.data_ptr() + 8 * ox, ypool.data_ptr() + 8 * oy,
                                       zbuf.data_ptr() + 8 * int(zoff[j]))
@@ -1227,96 +1235,189 @@ def run_served(args, world, rank, local):
         svc = np.array([(r["t_done_ns"] - r["t_admit_ns"]) / 1e6 for r in res])
         span = (max(r["t_done_ns"] for r in res) - min(arrive)) / 1e9
         bits = sum(m for _, _, _, m in trace)
-        return {"requests": len(trace), "output_gbits": bits / 1e9, "span_s": span,
-                "gbit_per_s": bits / span / 1e9, "req_per_s": len(trace) / span,
-                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-                "service_ms": {"p50": float(np.percentile(svc, 50)), "p99": float(np.percentile(svc, 99))},
-                "waves": ctx.server_stats()["waves"]}
+        stats = {"requests": len(trace), "output_gbits": bits / 1e9, "span_s": span,
+                 "gbit_per_s": bits / span / 1e9, "req_per_s": len(trace) / span,
+                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                 "service_ms": {"p50": float(np.percentile(svc, 50)), "p99": float(np.percentile(svc, 99))},
+                 "waves": ctx.server_stats()["waves"], "_lat": lat.tolist()}
+        return stats, zbuf, zoff, offs
+
+    def plain(trace, zoff, offs, z):
+        """The same requests and inputs as plain single calls, back to back on one stream."""
+        Lb = native.lib()
+        sh = torch.cuda.current_stream().cuda_stream
+        for j, (_, kind, n, m) in enumerate(trace):
+            px, py = xpool.data_ptr() + 8 * offs[j][0], ypool.data_ptr() + 8 * offs[j][1]
+            pz = z.data_ptr() + 8 * int(zoff[j])
+            if kind == 0:
+                r = Lb.cm_toeplitz(ctx.handle, px, n, py, m, pz, sh)
+            elif kind == 1:
+                r = Lb.cm_circulant(ctx.handle, px, n, py, m, pz, sh)
+            else:
+                r = Lb.cm_dodis(ctx.handle, px, py, n, m, pz, sh)
+            if r != native.CM_OK:
+                raise native.CMError(r, "single call")
+
+    def alone_ms(trace, zoff, offs):
+        """Each request's time as a plain single call (CUDA events around it on
+        one stream), and whether those outputs equal the served ones."""
+        z = torch.zeros(int(zoff[-1]), dtype=torch.int64, device="cuda")
+        sh = torch.cuda.current_stream()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in trace]
+        for j in range(len(trace)):
+            ev[j][0].record(sh)
+            plain(trace[j:j + 1], zoff[j:j + 2] - zoff[j], [offs[j]], z[int(zoff[j]):])
+            ev[j][1].record(sh)
+        torch.cuda.synchronize()
+        return np.array([a.elapsed_time(b) for a, b in ev]), z
+
+    def slowdown(stats, trace, zs, zoff, offs):
+        """Served latency over the request's time alone, p50 / p99 (1 = no
+        waiting behind other requests)."""
+        t_alone, z = alone_ms(trace, zoff, offs)
+        assert torch.equal(z, zs), "served outputs differ from the per-call outputs"
+        r = np.array(stats.pop("_lat")) / np.maximum(t_alone, 1e-3)
+        stats["slowdown"] = {"p50": float(np.percentile(r, 50)), "p99": float(np.percentile(r, 99)),
+                             "alone_ms_p50": float(np.percentile(t_alone, 50)),
+                             "alone_ms_p99": float(np.percentile(t_alone, 99))}
+        return stats
 
     rate = float(os.environ.get("CM_SERVE_RATE", "20000"))
     count = int(os.environ.get("CM_SERVE_COUNT", "600"))
-    run(served_trace(max(8, args.warmup * 4), rate, seed_stream=90))   # warm-up
+    run(served_trace(max(8, args.warmup * 4), rate, seed_stream=90))   # warm-up (its outputs are not kept)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.25)
     tw0 = time.time()
-    main_run = run(served_trace(count, rate))
+    trace = served_trace(count, rate)
+    main_run, zs, zoff, offs = run(trace)
     tw1 = time.time()
     time.sleep(0.25)
     sampler.stop()
+    slowdown(main_run, trace, zs, zoff, offs)
+    # the plain per-call form on the same trace: outputs bit-identical, GPU
+    # time of the calls back to back (their host-side enqueue included)
+    zp = torch.zeros_like(zs)
+    plain(trace, zoff, offs, zp)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(zp, zs))
+    p_ms = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plain(trace, zoff, offs, zp)
+        e1.record()
+        torch.cuda.synchronize()
+        p_ms.append(e0.elapsed_time(e1))
+    bits = sum(m for _, _, _, m in trace)
+    plain_stats = {"value": bits / (min(p_ms) * 1e-3) / 1e9, "unit": "Gbit/s", "ms": min(p_ms),
+                   "bit_identical_to_served": same}
+    assert same, "served outputs differ from the per-call outputs"
     cap = main_run["req_per_s"]
     points = []
     for frac in (0.25, 0.5, 0.8):
         k = int(os.environ.get("CM_SERVE_SUB_COUNT", "120"))
-        pt = run(served_trace(k, frac * cap, seed_stream=30 + int(frac * 100)))
+        tr = served_trace(k, frac * cap, seed_stream=30 + int(frac * 100))
+        pt, zq, zoq, ofq = run(tr)
+        slowdown(pt, tr, zq, zoq, ofq)
         pt["offered_fraction_of_capacity"] = frac
         points.append(pt)
     st = ctx.server_stats()
     line = {
         "metric": "extracted output Gbit/s", "value": main_run["gbit_per_s"], "unit": "Gbit/s", "n_gpus": 1,
         "steps": 1, "warmup": args.warmup, "ms_per_step": main_run["span_s"] * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": f"Served: {count} requests, Poisson arrivals at {rate:g} req/s, Toeplitz/Circulant/"
                                "Dodis 50/25/25, n = floor(2^U), U ~ U[12, 28) (N_A-snapped), m = n/2, "
                                "Bernoulli(1/2) inputs", "slots": st["slots"],
                    "hbm_budget_bytes": st["budget_bytes"]},
-        "served": main_run, "sub_saturation": points,
+        "served": main_run, "plain_per_call": plain_stats, "sub_saturation": points,
         "latency_ms": main_run["latency_ms"], "max_inflight_bytes": st["max_inflight_bytes"],
         "clocks": sampler.summary(tw0, tw1),
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
     ctx.server_stop()
     ctx.close()
+    del xpool, ypool, zs, zp
+    torch.cuda.empty_cache()
+    return line
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
-    ap.add_argument("--impl", default="cm", choices=["cm", "reference"])
-    ap.add_argument("--workload", default="circulant",
-                    choices=sorted(WORKLOADS) + ["batched_a", "batched_b", "served", "von_neumann", "trevisan"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--field", default="auto", choices=["auto", "q30", "goldilocks"],
-                    help="transform fields of the single calls (cm_options.field)")
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
-    world, rank, local = dist_setup(args)
-    if args.impl == "reference":
-        run_reference(args, world, rank)
-        return
-    if args.workload == "batched_a":
-        run_batched_a(args, world, rank, local)
-        return
-    if args.workload == "batched_b":
-        run_batched_b(args, world, rank, local)
-        return
-    if args.workload == "served":
-        run_served(args, world, rank, local)
-        return
-    if args.workload == "von_neumann":
-        run_von_neumann(args, world, rank, local)
-        return
-    if args.workload == "trevisan":
-        run_trevisan(args, world, rank, local)
-        return
+def roofline_of(prof, products, m, peak, peak_src, workload):
+    """The dominant kernel's roofline: algorithmic bytes per launch (the scope's
+    48 L model, with the path's own element size beside it) over its average
+    launch time, against the measured HBM copy bandwidth."""
+    kernels = {k: {"launches": c, "avg_ms": t / c, "share": 0.0} for k, (c, t) in prof.items()}
+    tot = sum(t for _, t in prof.values()) or 1.0
+    for k, (c, t) in prof.items():
+        kernels[k]["share"] = t / tot
+    dom = max(prof, key=lambda k: prof[k][1])
+    per_launch = prof[dom][1] / prof[dom][0]
+    base = dom[:-4] if dom.endswith(("_f30", "_f25")) else dom
+    model = kernel_model(products, m).get(base)
+    if not model:
+        return None, kernels
+    alg = model["bytes"] / model["launches"]
+    act = model["actual"] / model["launches"]
+    achieved = alg / (per_launch * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": ncu_traffic(dom, workload),
+            "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json)",
+            "model": "SURVEY 8(d): 48 L bytes per product (three L-element arrays written and read once, "
+                     "8-byte elements) split over the kernels, per launch",
+            "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_launch,
+            "launches_per_step": model["launches"],
+            "actual_element_bytes": {"bytes_per_launch": act,
+                                     "achieved": act / (per_launch * 1e-3) / 1e9,
+                                     "frac": act / (per_launch * 1e-3) / 1e9 / peak}}
+    return roof, kernels
 
+
+def path_roofline_of(products, n, sb, m, ms_per_step, peak, rates):
+    """The scope's path roofline: max(T_hbm, T_int) against the measured step
+    time; T_hbm = the 48 L bytes (and the actual ones) over the measured HBM
+    copy bandwidth, T_int = modular multiplies over the measured rate of the
+    product of each product's own field (cm_modmul_rate)."""
+    pm = path_model(products, n, sb, m)
+    # modular multiplies per field
+    t_ref = t_r2 = 0.0
+    fields = set()
+    for p in products:
+        if p["sum"] == 4:
+            continue
+        L = p["L"]
+        lg = int(L).bit_length() - 1
+        r = rates[p["field"]]
+        fields.add(p["field"])
+        t_ref += (3 * L * (-(-lg // 6) - 1) + L) / r
+        t_r2 += (3 * (L // 2) * max(lg - 2, 0) + L) / r
+    t_hbm48 = pm["bytes48"] / (peak * 1e9) * 1e3
+    t_hbm_act = pm["bytes_actual"] / (peak * 1e9) * 1e3
+    t_ref *= 1e3
+    t_r2 *= 1e3
+    roof_ms = max(t_hbm48, t_ref)
+    return {"definition": "max(T_hbm(48 L + bit I/O at the measured HBM bandwidth), T_int(the scope's "
+                          "modular-multiply count at the measured rate of the path's field)) / measured step",
+            "frac": roof_ms / ms_per_step, "roofline_ms": roof_ms,
+            "bytes48": pm["bytes48"], "t_hbm48_ms": t_hbm48,
+            "achieved_gbs_48L": pm["bytes48"] / (ms_per_step * 1e-3) / 1e9,
+            "frac_of_8tbs_48L": pm["bytes48"] / (ms_per_step * 1e-3) / 1e9 / 8000.0,
+            "modmuls_reference": pm["modmuls_reference"], "t_int_reference_ms": t_ref,
+            "modmul_rate_per_s": {FIELD_NAMES[f]: rates[f] for f in sorted(fields)},
+            "actual_element_bytes": {"bytes": pm["bytes_actual"], "t_hbm_ms": t_hbm_act,
+                                     "frac": max(t_hbm_act, t_ref) / ms_per_step},
+            "radix2_modmuls": {"count": pm["modmuls_radix2"], "t_int_ms": t_r2,
+                               "frac": max(t_hbm48, t_r2) / ms_per_step}}
+
+
+def run_single(args, world, rank, local, dist):
+    """One single-extraction workload (WORKLOADS): the JSON line (rank 0)."""
     import numpy as np
     import torch
 
-    from paper_2402_09481_gb300 import build, inputs, native, replicas
-
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if rank == 0 or world == 1:
-        build.build()
-    if dist:
-        dist.barrier()
+    from paper_2402_09481_gb300 import inputs, native, replicas
 
     wl = WORKLOADS[args.workload]
     kind, n, m = wl["kind"], wl["n"], wl["m"]
@@ -1384,53 +1485,10 @@ def main():
         call()
     prof = ctx.profile_read(reset=True)
     ctx.profile_enable(False)
-    kernels = {k: {"launches": c, "avg_ms": t / c, "share": 0.0} for k, (c, t) in prof.items()}
-    tot = sum(t for _, t in prof.values()) or 1.0
-    for k, (c, t) in prof.items():
-        kernels[k]["share"] = t / tot
-    dom = max(prof, key=lambda k: prof[k][1])
-    per_launch = prof[dom][1] / prof[dom][0]
-    model = kernel_model(products, m)[field_of(dom)[0]]
-    # per launch: the step's totals over the kernel's launches in a step
-    alg = model["bytes"] / model["launches"]
-    bfly = model["butterflies"] / model["launches"]
     peak, peak_src = measured_peaks()
-    achieved = alg / (per_launch * 1e-3) / 1e9
-    clk = (sampler.summary(t_wall0, t_wall1) or {}).get("sm_mhz") or 2070.0
-    ops = ALU_OPS_PER_BUTTERFLY_F30 if dom.endswith(("_f30", "_f25")) else ALU_OPS_PER_BUTTERFLY
-    ach_b = bfly / (per_launch * 1e-3) / 1e9
-    peak_b = alu_peak_butterflies(clk, ops) / 1e9
-    roof = {"bound": "alu", "kernel": dom, "achieved": ach_b, "peak": peak_b, "unit": "G butterflies/s",
-            "frac": ach_b / peak_b,
-            "peak_source": f"{NUM_SMS} SMs x {ALU_LANES_PER_SM} ALU lanes x {clk:.0f} MHz measured / "
-                           f"{ops} ALU ops per radix-2 butterfly",
-            "traffic": ncu_traffic(dom, args.workload), "butterflies_per_launch": bfly,
-            "launches_per_step": model["launches"], "avg_launch_ms": per_launch,
-            "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_source": peak_src, "algorithmic_bytes_per_launch": alg}}
-    # path roofline: max(HBM time of the path bytes, integer-pipe time of its
-    # modular multiplies at the measured rate) against the measured step time
-    pb = path_bytes(products, n, sb, m)
-    n_path, n_off = path_modmuls(products)
-    r_gl = native.modmul_rate(local, native.FIELD_GOLDILOCKS)
-    r_q30 = native.modmul_rate(local, native.FIELD_Q30)
-    r_q25 = native.modmul_rate(local, native.FIELD_Q25)
-    r_path = {native.FIELD_Q30: r_q30, native.FIELD_Q25: r_q25}.get(plan["field"], r_gl)
-    t_hbm = pb / (peak * 1e9) * 1e3
-    t_int_off = n_off / r_gl * 1e3
-    t_int_path = n_path / r_path * 1e3
-    path_roof = {"model": "6 e L per product (e = element bytes) + bit I/O; modular multiplies at the "
-                          "measured rate (cm_modmul_rate)", "bytes": pb,
-                 "achieved_gbs": pb / (ms_per_step * 1e-3) / 1e9,
-                 "frac_of_measured_hbm": pb / (ms_per_step * 1e-3) / 1e9 / peak,
-                 "frac_of_8tbs": pb / (ms_per_step * 1e-3) / 1e9 / 8000.0,
-                 "t_hbm_ms": t_hbm, "t_hbm_8tbs_ms": pb / 8e12 * 1e3,
-                 "modmuls_reference_model": n_off, "modmul_rate_goldilocks_per_s": r_gl,
-                 "t_int_reference_model_ms": t_int_off,
-                 "roofline_ms": max(t_hbm, t_int_off), "frac": max(t_hbm, t_int_off) / ms_per_step,
-                 "modmuls_path": n_path, "modmul_rate_path_per_s": r_path, "t_int_path_ms": t_int_path,
-                 "roofline_path_ms": max(t_hbm, t_int_path),
-                 "frac_path": max(t_hbm, t_int_path) / ms_per_step}
+    roof, kernels = roofline_of(prof, products, m, peak, peak_src, args.workload)
+    rates = {f: native.modmul_rate(local, f) for f in (native.FIELD_GOLDILOCKS, native.FIELD_Q30, native.FIELD_Q25)}
+    path_roof = path_roofline_of(products, n, sb, m, ms_per_step, peak, rates)
 
     # the Dodis et al. workload as its configuration states it: one Goldilocks
     # transform of length 2^31 (single-transform plan); same bits
@@ -1473,42 +1531,172 @@ def main():
         t0 = time.perf_counter()
         ctx.extract_host(kind, xh, n, yh, m, zh)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    assert torch.equal(zh, zd.cpu()), "host-buffer result differs from device-buffer result"
+    z_gpu = zd.cpu()
+    assert torch.equal(zh, z_gpu), "host-buffer result differs from device-buffer result"
     e2e_mean = sum(e2e_ms) / len(e2e_ms)
     e2e = {"value": world * m / (e2e_mean * 1e-3) / 1e9, "unit": "Gbit/s",
            "h2d_bytes_per_step": 8 * (xw.size + yw.size), "d2h_bytes_per_step": 8 * native.words(m),
            "ms_per_step": e2e_mean}
+    ctx.close()
+    del xd, yd, zd, flush
+    torch.cuda.empty_cache()
 
-    cpu = None
+    # CPU baselines on the host cores: the bit-packed CPU NTT on the whole
+    # workload (one thread and every core) and the oracle on a bounded sample
+    cpu = cpu_ntt = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, rows, secs = cpu_oracle_rate(kind, n, m, xw, yw)
         cpu = {"value": rate / 1e9, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
                "sample": f"{rows} random output rows of the full-size workload in {secs:.1f} s "
                          f"(explicit GF(2) rows, numpy, one thread)"}
+        cpu_ntt = cpu_ntt_baseline(kind, n, m, xw, yw, z_gpu.numpy().view(np.uint64))
+        if cpu_ntt is None:
+            cpu_ntt = {"unavailable": "the CPU NTT's field (3 * 2^30 + 1) holds transforms up to 2^30 only"}
 
     clocks = sampler.summary(t_wall0, t_wall1)
-    if rank == 0:
-        line = {
-            "metric": "extracted output Gbit/s", "value": value, "unit": "Gbit/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": wl["name"], "n": n, "m": m, "seed_bits": sb,
-                       "plan": {"products": plan["products"], "windows": plan["windows"],
-                                "transform_length": L,
-                                "field": {2: "q = 3 * 2^30 + 1", 3: "q = 5 * 2^25 + 1"}.get(plan["field"], "Goldilocks"),
-                                "planner_estimate_ms": plan["est_ms"]},
-                       "l2": "flushed between timed steps (256 MiB write)",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "latency_ms": {"p50": statistics.median(step_ms),
-                           "p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},
-            "roofline": roof, "path_roofline": path_roof, "kernels": kernels,
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
-            **({"as_configured": as_configured} if as_configured else {}),
-            "gpu_launches": launches * args.steps,
-        }
-        print(json.dumps(line), flush=True)
+    if rank != 0:
+        return None
+    pf = plan["field"]
+    return {
+        "metric": "extracted output Gbit/s", "value": value, "unit": "Gbit/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64" if pf == FIELD_GL else "u32", "data": "synthetic",
+        "config": {"workload": wl["name"], "n": n, "m": m, "seed_bits": sb,
+                   "plan": {"products": plan["products"], "windows": plan["windows"],
+                            "transform_length": L, "field": FIELD_NAMES.get(pf, pf),
+                            "tail_terms": plan["tail_terms"], "planner_estimate_ms": plan["est_ms"]},
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "latency_ms": {"p50": statistics.median(step_ms),
+                       "p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},
+        "roofline": roof, "path_roofline": path_roof, "kernels": kernels,
+        "e2e": e2e, "cpu_baseline": cpu, **({"cpu_ntt": cpu_ntt} if cpu_ntt else {}), "clocks": clocks,
+        **({"as_configured": as_configured} if as_configured else {}),
+        "gpu_launches": launches * args.steps,
+    }
+
+
+def dodis_extra(local, steps=5):
+    """The Dodis et al. workload (n = 1073741789, m = floor(0.4 n)), Bernoulli(1/2)
+    sources and a second run with x 0.8-biased (drawn on the device: timing
+    only; the tests check this run's bits against the oracle)."""
+    import numpy as np
+    import torch
+
+    from paper_2402_09481_gb300 import inputs, native
+    n, m = 1073741789, 429496715
+    ctx = native.Context(local)
+    plan = native.plan_query(2, n, m)
+    products = native.plan_products(2, n, m)
+    nw = native.words(n)
+    xu = torch.from_numpy(inputs.bernoulli_half(31, n).view(np.int64)).cuda()
+    yd = torch.from_numpy(inputs.bernoulli_half(32, n).view(np.int64)).cuda()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2402)
+    bits = torch.rand((nw, 64), device="cuda", generator=g) < 0.8
+    xb = (bits.to(torch.int64) << torch.arange(64, device="cuda", dtype=torch.int64)).sum(dim=1)
+    del bits
+    zd = torch.empty(native.words(m), dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    peak, _ = measured_peaks()
+    rates = {f: native.modmul_rate(local, f) for f in (native.FIELD_GOLDILOCKS, native.FIELD_Q30, native.FIELD_Q25)}
+    out = {"workload": "Dodis et al.: n = 1073741789 (largest N_A prime <= 2^30), m = floor(0.4 n)",
+           "plan": {"products": plan["products"], "transform_length": plan["transform_length"],
+                    "field": FIELD_NAMES.get(plan["field"], plan["field"])}}
+    for name, xd in (("bernoulli_half", xu), ("x_0p8_biased", xb)):
+        for _ in range(2):
+            ctx.dodis(xd, yd, n, m, zd)
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.dodis(xd, yd, n, m, zd)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        st, fl = ctx.device_status()
+        assert st == native.CM_OK, native.STATUS.get(st)
+        ms_ = statistics.median(ts)
+        pr = path_roofline_of(products, n, n, m, ms_, peak, rates)
+        out[name] = {"ms_per_step": ms_, "value": m / (ms_ * 1e-3) / 1e9, "unit": "Gbit/s",
+                     "path_roofline_frac": pr["frac"], "frac_actual_element_bytes": pr["actual_element_bytes"]["frac"]}
     ctx.close()
+    del xu, xb, yd, zd, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="cm", choices=["cm", "reference"])
+    ap.add_argument("--workload", default="circulant",
+                    choices=sorted(WORKLOADS) + ["batched_a", "batched_b", "served", "von_neumann", "trevisan"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line only: skip the Dodis et al., batched (a) and served summaries")
+    ap.add_argument("--field", default="auto", choices=["auto", "q30", "goldilocks"],
+                    help="transform fields of the single calls (cm_options.field)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    if args.workload == "batched_a":
+        run_batched_a(args, world, rank, local)
+        return
+    if args.workload == "batched_b":
+        run_batched_b(args, world, rank, local)
+        return
+    if args.workload == "served":
+        run_served(args, world, rank, local)
+        return
+    if args.workload == "von_neumann":
+        run_von_neumann(args, world, rank, local)
+        return
+    if args.workload == "trevisan":
+        run_trevisan(args, world, rank, local)
+        return
+
+    import torch
+
+    from paper_2402_09481_gb300 import build
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    line = run_single(args, world, rank, local, dist)
+    # the scope's other targets, measured in the same run (one GPU): Dodis et
+    # al. at full size with both sources, the batched and served forms each
+    # against the plain per-call form on the same inputs
+    if (line is not None and world == 1 and args.workload == "circulant" and args.field == "auto"
+            and not args.no_extras):
+        t0 = time.time()
+        line["dodis"] = dodis_extra(local)
+        sub = argparse.Namespace(**vars(args))
+        sub.steps, sub.warmup, sub.no_cpu_baseline = 3, 3, True
+        ba = run_batched_a(sub, 1, 0, local, emit=False)
+        line["batched_a"] = {k: ba[k] for k in ("value", "unit", "ms_per_step", "plain_per_call", "config",
+                                               "roofline", "gpu_launches")}
+        line["batched_a"]["faster_than_plain"] = ba["value"] / ba["plain_per_call"]["value"]
+        sv = run_served(sub, 1, 0, local, emit=False)
+        line["served"] = {k: sv[k] for k in ("value", "unit", "served", "plain_per_call", "sub_saturation", "config")}
+        line["served"]["faster_than_plain"] = sv["value"] / sv["plain_per_call"]["value"]
+        line["extras_seconds"] = time.time() - t0
+    if line is not None:
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 

@@ -422,8 +422,10 @@ cm_status cm_field_selftest(int device, uint64_t count, uint64_t seed, uint64_t 
 
 /* Modular-multiply rate of `device` for `field` (CM_FIELD_GOLDILOCKS: the
  * 64-bit product and reduction of the transforms; CM_FIELD_Q30: the 32-bit
- * Montgomery product; CM_FIELD_Q25: the lazy Montgomery product of the field
- * of 5 * 2^25 + 1), measured by a kernel of independent register chains of
+ * Montgomery product; CM_FIELD_Q25: the Shoup product by a constant root with
+ * its precomputed quotient, the product the transforms of the field of
+ * 5 * 2^25 + 1 use for their roots), measured by a kernel of independent
+ * register chains of
  * products on every SM (8 chains a thread, 4 CTAs of 256 threads per SM) and
  * timed with CUDA events: *per_second receives products per second.  The
  * integer-pipe bound of a path is its number of general multiplies divided by

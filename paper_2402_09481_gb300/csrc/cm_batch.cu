@@ -369,7 +369,7 @@ struct cm_batch {
     std::vector<cm_desc> descs;
     std::vector<Plan> plans;
     std::vector<uint32_t> wl;       // instances on the work list
-    std::vector<uint32_t> solo;     // instances with L > 2^25 (per-call kernels)
+    std::vector<uint32_t> solo;     // instances with L > 2^21 (single-call kernels)
     std::vector<size_t> off_scratch;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -478,16 +478,15 @@ extern "C" cm_status cm_batch_create(cm_ctx *ctx, const cm_desc *descs, uint32_t
             delete b;
             return CM_EINVAL;
         }
-        const Plan &p = b->plans[i];
         b->off_scratch[i] = total;
-        if (p.npass == 1) {
+        if (on_worklist(b->plans[i])) {
             b->wl.push_back(i);
-            total += worklist_scratch_bytes(p);
-        } else if (p.npass == 0) {
-            b->wl.push_back(i);
+            total += worklist_scratch_bytes(b->plans[i]);
         } else {
+            // the single-call kernels, over the context's field set
+            make_plan(d.kind, d.n, d.m, &b->plans[i], ctx->popt.fields);
             b->solo.push_back(i);
-            total += round256(p.scratch_bytes);
+            total += round256(b->plans[i].scratch_bytes);
         }
     }
     if (total > ctx->budget) {

@@ -32,6 +32,13 @@ struct WorkItem {
     uint32_t pad;
 };
 
+// Instances with transforms up to 2^21 go on the work list; longer ones run
+// the single-call kernels (column passes fused with the products over F25 up
+// to 2^25), which are faster per element than the work list's runtime-size
+// steps once a transform fills the GPU on its own.
+constexpr int kWorklistMaxLg = 21;
+inline bool on_worklist(const Plan &p) { return p.npass <= 1 && p.lg <= kWorklistMaxLg; }
+
 // Scratch one work-list instance needs (0 for L <= 2^13): operands A and B
 // (L elements each of the work list's field, 4 bytes) and the parity bytes of
 // its window.

@@ -328,7 +328,9 @@ __global__ void k_field_selftest(uint64_t count, uint64_t seed, unsigned long lo
 namespace cm {
 
 // Independent chains x <- x w of the field's product, kChains per thread;
-// the chains' sum goes to *sink so that nothing is dead code.
+// the chains' sum goes to *sink so that nothing is dead code.  The lazily
+// reduced field times its Shoup product by a constant root (the product its
+// transforms use for constant and table roots).
 constexpr int kChains = 8;
 template <class F>
 __global__ void __launch_bounds__(256) k_modmul_rate(uint32_t iters, typename F::T w, typename F::T *sink) {
@@ -336,9 +338,15 @@ __global__ void __launch_bounds__(256) k_modmul_rate(uint32_t iters, typename F:
     T x[kChains];
 #pragma unroll
     for (int c = 0; c < kChains; ++c) x[c] = (T)(threadIdx.x + 977u * (c + 1) + blockIdx.x);
+    const uint32_t wq = F::kLazy ? f25_shoup_q((uint32_t)w) : 0u;
     for (uint32_t i = 0; i < iters; ++i) {
 #pragma unroll
-        for (int c = 0; c < kChains; ++c) x[c] = F::twmul(x[c], w);
+        for (int c = 0; c < kChains; ++c) {
+            if constexpr (F::kLazy)
+                x[c] = f25_shoup(x[c], (uint32_t)w, wq);
+            else
+                x[c] = F::twmul(x[c], w);
+        }
     }
     T s = 0;
 #pragma unroll
@@ -382,7 +390,7 @@ extern "C" cm_status cm_modmul_rate(int device, uint32_t field, double *per_seco
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return CM_EDEVICE;
     if (field == CM_FIELD_Q30) return cm::modmul_rate<cm::FieldF30>(nsm, f30_to_mont(12345u), per_second);
-    if (field == CM_FIELD_Q25) return cm::modmul_rate<cm::FieldF25>(nsm, f25_to_mont(12345u), per_second);
+    if (field == CM_FIELD_Q25) return cm::modmul_rate<cm::FieldF25>(nsm, 12345u, per_second);
     return cm::modmul_rate<cm::FieldGL>(nsm, 0x123456789ABCDEFull, per_second);
 }
 

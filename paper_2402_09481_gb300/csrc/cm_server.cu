@@ -2,20 +2,25 @@
 //
 // Clients submit single extractions of any kind and size; a worker thread
 // keeps a FIFO of pending requests and a few "slots" (CUDA streams).  Whenever
-// a slot is free it admits the longest prefix of the queue whose scratch fits
-// in the HBM budget still unclaimed by requests on the device, and launches
-// that wave as one work-list kernel on the slot's stream (instances needing
-// two column passes follow on the same stream through the single-call
-// kernels).  Waves on different slots run concurrently, so requests that
-// arrive while others are on the GPU start as soon as a slot and memory free
-// up.  Scratch comes from the context's stream-ordered pool and returns to it
-// at the end of the wave.  Each request's result (its own status, including
-// the Dodis et al. precondition, and submit / admit / completion times) is
-// collected with cm_poll.  The root tables stay resident in the context.
+// a slot is free it admits, in queue order, the requests whose scratch fits in
+// the HBM budget still unclaimed by requests on the device; a request that
+// does not fit yet is passed over by at most a fixed number of waves, after
+// which nothing behind it starts until it fits.  A wave runs as one work-list
+// kernel on the slot's stream (requests with transforms longer than 2^21
+// follow on the same stream through the single-call kernels).  Waves on
+// different slots run concurrently, so requests that arrive while others are
+// on the GPU start as soon as a slot and memory free up.  Admission holds the
+// server lock; planning, upload and launch run outside it, so submissions
+// and polls never wait for them.  Scratch comes from the context's
+// stream-ordered pool and returns to it at the end of the wave.  Each
+// request's result (its own status, including the Dodis et al.
+// precondition, and submit / admit / completion times) is collected with
+// cm_poll.  The root tables stay resident in the context.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -49,12 +54,13 @@ size_t r256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Req {
     cm_desc d;
-    Plan p;                     // one-transform plan (work-list requests: L <= 2^25)
+    Plan p;                     // one-transform plan (the work list takes L <= 2^21)
     std::vector<Block> blocks;  // longer requests: the single-call planner's products
     uint64_t tmp_off = 0, pre_off = 0;
     uint32_t flags = 0;
     uint64_t seed_id = 0;
     size_t foot = 0;  // scratch bytes while on the device
+    uint32_t passed = 0;  // waves admitted past it while it did not fit
     uint64_t t_submit = 0, t_admit = 0, t_done = 0, wave = 0;
     int status = CM_OK;
     bool done = false;
@@ -139,6 +145,52 @@ struct cm_server {
 
 namespace {
 
+// Drop the slot's references to seed transforms.  An entry this wave created
+// becomes ready when the wave succeeded and holds a buffer; otherwise it is
+// freed once no wave uses it.
+void release_seeds(cm_server *S, Slot &sl, bool ok) {
+    for (auto &kc : sl.seeds) {
+        auto it = S->seeds.find(kc.first);
+        if (it == S->seeds.end()) continue;
+        SeedEntry &e = it->second;
+        e.refs -= 1;
+        if (!kc.second) continue;
+        if (ok && e.buf) {
+            e.ready = true;
+        } else if (e.refs == 0) {
+            if (e.buf) cudaFreeAsync(e.buf, sl.st);
+            S->seed_bytes -= e.bytes;
+            S->seeds.erase(it);
+        }
+    }
+    sl.seeds.clear();
+}
+
+// Free the slot; its scratch claim returns to the budget.
+void vacate_slot(cm_server *S, Slot &sl) {
+    S->inflight -= sl.foot;
+    sl.foot = 0;
+    sl.tickets.clear();
+    sl.pre_index.clear();
+    sl.busy = false;
+}
+
+// Complete every request of the slot's wave with `status` (a launch that
+// failed, or a device error reported by the wave's event).
+void fail_wave(cm_server *S, Slot &sl, int status) {
+    const uint64_t t = now_ns();
+    for (uint64_t tk : sl.tickets) {
+        auto it = S->reqs.find(tk);
+        if (it == S->reqs.end()) continue;
+        it->second.status = status;
+        it->second.done = true;
+        it->second.t_done = t;
+        ++S->completed;
+    }
+    release_seeds(S, sl, false);
+    vacate_slot(S, sl);
+}
+
 // Finish a completed wave: per-request status from the copied-back flags.
 void finish_slot(cm_server *S, Slot &sl) {
     const uint32_t *f = static_cast<const uint32_t *>(sl.flags.host);
@@ -157,123 +209,174 @@ void finish_slot(cm_server *S, Slot &sl) {
         r.done = true;
         ++S->completed;
     }
-    const bool ok = !(st_word & CM_FLAG_TIMEOUT);
-    for (auto &kc : sl.seeds) {
-        auto it = S->seeds.find(kc.first);
-        if (it == S->seeds.end()) continue;
-        it->second.refs -= 1;
-        if (kc.second) {
-            if (ok) {
-                it->second.ready = true;
-            } else if (it->second.refs == 0) {
-                cudaFreeAsync(it->second.buf, sl.st);
-                S->seed_bytes -= it->second.bytes;
-                S->seeds.erase(it);
-            }
-        }
-    }
-    sl.seeds.clear();
-    S->inflight -= sl.foot;
-    sl.foot = 0;
-    sl.tickets.clear();
-    sl.pre_index.clear();
-    sl.busy = false;
+    release_seeds(S, sl, !(st_word & CM_FLAG_TIMEOUT));
+    vacate_slot(S, sl);
 }
 
-// Make room for `bytes` of seed transforms by dropping unused entries, least
-// recently used first; false if it cannot.
-bool seed_make_room(cm_server *S, size_t bytes, cudaStream_t st) {
-    while (S->seed_bytes + bytes > S->seed_limit) {
-        auto victim = S->seeds.end();
-        for (auto it = S->seeds.begin(); it != S->seeds.end(); ++it)
-            if (it->second.refs == 0 && it->second.ready && (victim == S->seeds.end() || it->second.last < victim->second.last))
-                victim = it;
-        if (victim == S->seeds.end()) return false;
-        cudaFreeAsync(victim->second.buf, st);
-        S->seed_bytes -= victim->second.bytes;
-        S->seeds.erase(victim);
-    }
+// Drop the least recently used seed transform that no wave uses; false if
+// there is none.
+bool seed_evict_one(cm_server *S, cudaStream_t st) {
+    auto victim = S->seeds.end();
+    for (auto it = S->seeds.begin(); it != S->seeds.end(); ++it)
+        if (it->second.refs == 0 && it->second.ready &&
+            (victim == S->seeds.end() || it->second.last < victim->second.last))
+            victim = it;
+    if (victim == S->seeds.end()) return false;
+    cudaFreeAsync(victim->second.buf, st);
+    S->seed_bytes -= victim->second.bytes;
+    S->seeds.erase(victim);
     return true;
 }
 
-// Launch the requests `tk` (already admitted) as one wave on slot sl.
-cm_status launch_wave(cm_server *S, Slot &sl, const std::vector<uint64_t> &tk) {
-    cm_ctx *ctx = S->ctx;
-    const uint32_t n = (uint32_t)tk.size();
-    std::vector<cm_desc> descs(n);
-    std::vector<Plan> plans(n);
-    std::vector<size_t> off(n, 0);
-    std::vector<uint32_t> wl, solo;
-    size_t total = 0;
-    for (uint32_t i = 0; i < n; ++i) {
-        const Req &r = S->reqs[tk[i]];
-        descs[i] = r.d;
-        plans[i] = r.p;
-        off[i] = total;
-        if (r.p.npass <= 1) {
-            wl.push_back(i);
-            total += worklist_scratch_bytes(r.p);
-        } else {
-            solo.push_back(i);
-            uint64_t t0, t1;
-            total += r256(blocks_scratch(r.blocks, &t0, &t1));
+// Make room for `bytes` of seed transforms within the cache limit.
+bool seed_make_room(cm_server *S, size_t bytes, cudaStream_t st) {
+    while (S->seed_bytes + bytes > S->seed_limit)
+        if (!seed_evict_one(S, st)) return false;
+    return true;
+}
+
+// What launching a wave needs, copied out of the request table under the lock
+// (the table changes while clients submit and poll).
+struct WaveReq {
+    cm_desc d;
+    Plan p;
+    std::vector<Block> blocks;
+    uint64_t tmp_off = 0, pre_off = 0;
+};
+struct Wave {
+    std::vector<WaveReq> r;
+    std::vector<void *> bext;       // per request: its resident seed transform, else null
+    std::vector<uint8_t> bready;    // it already holds the transform
+    std::vector<SeedEntry *> make;  // per request: a new entry whose buffer the launch allocates
+};
+
+// Waves that may pass a queued request whose scratch does not fit; after
+// that, nothing behind it is admitted until it fits.
+constexpr uint32_t kMaxPassed = 16;
+
+// Admit a wave for the free slot sl (under the lock).  The queue is taken in
+// order; a request whose scratch does not fit in the budget left is passed
+// over (at most kMaxPassed times), so small requests need not wait behind a
+// large one.  With nothing in flight, unused seed transforms give way to a
+// request that does not fit.  Marks the slot busy and copies what the launch
+// needs into w; false if nothing was admitted.
+bool admit_wave(cm_server *S, Slot &sl, Wave &w) {
+    std::vector<uint64_t> wave, passed;
+    std::vector<size_t> passed_at;
+    size_t foot = 0;
+    const size_t scan = std::max<size_t>(64, 4 * (size_t)S->opt.max_wave);
+    for (size_t seen = 0; seen < scan && !S->pending.empty() && wave.size() < S->opt.max_wave; ++seen) {
+        const uint64_t tk = S->pending.front();
+        const Req &r = S->reqs[tk];
+        auto fits = [&] { return S->inflight + foot + r.foot + S->seed_bytes <= S->budget; };
+        if (!fits() && S->inflight + foot == 0)
+            while (!fits() && seed_evict_one(S, sl.st)) {
+            }
+        if (!fits()) {
+            if (r.passed >= kMaxPassed) break;  // stays at the head of what is left
+            passed.push_back(tk);
+            passed_at.push_back(wave.size());
+            S->pending.pop_front();
+            continue;
         }
+        foot += r.foot;
+        wave.push_back(tk);
+        S->pending.pop_front();
     }
-    void *scratch = nullptr;
-    if (total && cudaMallocFromPoolAsync(&scratch, total, ctx->pool, sl.st) != cudaSuccess) {
-        cudaGetLastError();
-        return CM_ENOMEM;
+    for (size_t j = passed.size(); j-- > 0;) {
+        S->pending.push_front(passed[j]);
+        if (passed_at[j] < wave.size()) S->reqs[passed[j]].passed += 1;  // a later request went first
     }
-    // flags: status word, pad, then a pair per work-list instance (index k) and
-    // one per single-call request (index wl.size() + i)
-    const size_t flag_words = 2 + 2 * ((size_t)n + n);
-    if (!sl.flags.ensure(flag_words * 4)) return CM_ENOMEM;
-    uint32_t *dflags = static_cast<uint32_t *>(sl.flags.dev);
-    // resident seed transforms
-    std::vector<void *> bext(wl.size(), nullptr);
-    std::vector<uint8_t> bready(wl.size(), 0);
+    if (wave.empty()) return false;
+    const uint64_t t = now_ns(), wid = ++S->waves;
+    const uint32_t n = (uint32_t)wave.size();
+    w.r.resize(n);
+    w.bext.assign(n, nullptr);
+    w.bready.assign(n, 0);
+    w.make.assign(n, nullptr);
     sl.seeds.clear();
-    for (uint32_t k = 0; k < wl.size(); ++k) {
-        const Req &r = S->reqs[tk[wl[k]]];
-        if (!(r.flags & CM_REQ_SEED_CACHE) || r.p.npass != 1) continue;
+    for (uint32_t i = 0; i < n; ++i) {
+        Req &r = S->reqs[wave[i]];
+        r.t_admit = t;
+        r.wave = wid;
+        w.r[i].d = r.d;
+        w.r[i].p = r.p;
+        w.r[i].blocks = r.blocks;
+        w.r[i].tmp_off = r.tmp_off;
+        w.r[i].pre_off = r.pre_off;
+        // resident seed transforms (work-list requests with one column pass)
+        if (!(r.flags & CM_REQ_SEED_CACHE) || !on_worklist(r.p) || r.p.npass != 1) continue;
         const SeedKey key{r.seed_id, r.p.n, r.p.m, r.p.kind};
         auto it = S->seeds.find(key);
         if (it != S->seeds.end()) {
             if (!it->second.ready) continue;  // still being made by a wave in flight
             it->second.refs += 1;
             it->second.last = ++S->lru;
-            bext[k] = it->second.buf;
-            bready[k] = 1;
+            w.bext[i] = it->second.buf;
+            w.bready[i] = 1;
             sl.seeds.push_back({key, false});
             ++S->seed_hits;
             continue;
         }
         const size_t bytes = worklist_seed_bytes(r.p);
         if (!seed_make_room(S, bytes, sl.st)) continue;
-        void *buf = nullptr;
-        if (cudaMallocFromPoolAsync(&buf, bytes, ctx->pool, sl.st) != cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
         SeedEntry e;
-        e.buf = buf;
         e.bytes = bytes;
         e.refs = 1;
         e.last = ++S->lru;
-        S->seeds.emplace(key, e);
+        w.make[i] = &S->seeds.emplace(key, e).first->second;  // node addresses survive rehashing
         S->seed_bytes += bytes;
-        bext[k] = e.buf;
         sl.seeds.push_back({key, true});
         ++S->seed_misses;
     }
+    sl.tickets = wave;
+    sl.foot = foot;
+    sl.wave = wid;
+    sl.busy = true;
+    S->inflight += foot;
+    if (S->inflight > S->max_inflight) S->max_inflight = S->inflight;
+    return true;
+}
+
+// Plan, upload and launch an admitted wave on slot sl (without the lock: it
+// touches only the slot, the wave's copies and the seed entries it created,
+// which no other thread reads).
+cm_status enqueue_wave(cm_server *S, Slot &sl, Wave &w, uint8_t *scratch, const std::vector<size_t> &off,
+                       const std::vector<uint32_t> &wl, const std::vector<uint32_t> &solo) {
+    cm_ctx *ctx = S->ctx;
+    const uint32_t n = (uint32_t)w.r.size();
+    std::vector<cm_desc> descs(n);
+    std::vector<Plan> plans(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        descs[i] = w.r[i].d;
+        plans[i] = w.r[i].p;
+    }
+    // flags: status word, pad, then a pair per work-list instance (index k) and
+    // one per single-call request (index wl.size() + i)
+    const size_t flag_words = 2 + 2 * ((size_t)n + n);
+    if (!sl.flags.ensure(flag_words * 4)) return CM_ENOMEM;
+    uint32_t *dflags = static_cast<uint32_t *>(sl.flags.dev);
+    std::vector<void *> bext(wl.size(), nullptr);
+    std::vector<uint8_t> bready(wl.size(), 0);
+    for (uint32_t k = 0; k < wl.size(); ++k) {
+        const uint32_t i = wl[k];
+        if (SeedEntry *e = w.make[i]) {
+            if (cudaMallocFromPoolAsync(&e->buf, e->bytes, ctx->pool, sl.st) != cudaSuccess) {
+                cudaGetLastError();
+                e->buf = nullptr;  // no resident transform: the wave computes it in scratch
+            }
+            w.bext[i] = e->buf;
+        }
+        bext[k] = w.bext[i];
+        bready[k] = w.bready[i];
+    }
     std::vector<BatchInst> insts;
     std::vector<WorkItem> items;
-    build_worklist(descs.data(), plans.data(), wl.data(), (uint32_t)wl.size(), static_cast<uint8_t *>(scratch),
-                   off.data(), kTileLg, dflags + 2, insts, items, bext.data(), bready.data());
+    build_worklist(descs.data(), plans.data(), wl.data(), (uint32_t)wl.size(), scratch, off.data(), kTileLg,
+                   dflags + 2, insts, items, bext.data(), bready.data());
     sl.pre_index.assign(n, -1);
     for (uint32_t k = 0; k < wl.size(); ++k)
         if (plans[wl[k]].kind == CM_DODIS) sl.pre_index[wl[k]] = (int)k;
-    cudaError_t e = cudaSuccess;
     if (cudaMemsetAsync(dflags, 0xff, flag_words * 4, sl.st) != cudaSuccess) return CM_EDEVICE;  // pairs "ok"
     if (cudaMemsetAsync(dflags, 0, 4, sl.st) != cudaSuccess) return CM_EDEVICE;                 // status word
     if (!wl.empty() && !items.empty()) {
@@ -287,18 +390,17 @@ cm_status launch_wave(cm_server *S, Slot &sl, const std::vector<uint64_t> &tk) {
             cudaMemsetAsync(sl.ctrl.dev, 0, cb, sl.st) != cudaSuccess)
             return CM_EDEVICE;
         ProfScope ps(ctx, "k_batch", sl.st);
-        e = launch_k_batch(static_cast<BatchInst *>(sl.insts.dev), static_cast<WorkItem *>(sl.items.dev),
+        if (launch_k_batch(static_cast<BatchInst *>(sl.insts.dev), static_cast<WorkItem *>(sl.items.dev),
                            (uint32_t)items.size(), static_cast<uint32_t *>(sl.ctrl.dev), dflags, ctx->rt25, S->grid,
-                           sl.st);
-        if (e != cudaSuccess) return CM_EDEVICE;
+                           sl.st) != cudaSuccess)
+            return CM_EDEVICE;
     }
     for (uint32_t i : solo) {
-        const Req &r = S->reqs[tk[i]];
-        uint8_t *sc = static_cast<uint8_t *>(scratch) + off[i];
-        cm_status s = enqueue_blocks(ctx, r.blocks, descs[i].x, descs[i].y, descs[i].z, sc, r.tmp_off, r.pre_off,
-                                     sl.st);
+        const WaveReq &r = w.r[i];
+        uint8_t *sc = scratch + off[i];
+        cm_status s = enqueue_blocks(ctx, r.blocks, r.d.x, r.d.y, r.d.z, sc, r.tmp_off, r.pre_off, sl.st);
         if (s != CM_OK) return s;
-        if (plans[i].kind == CM_DODIS) {
+        if (r.p.kind == CM_DODIS) {
             // the single-call path keeps its flag pair at pre_off of its scratch
             const uint8_t *pf = sc + r.pre_off;
             sl.pre_index[i] = (int)(wl.size() + i);
@@ -309,9 +411,37 @@ cm_status launch_wave(cm_server *S, Slot &sl, const std::vector<uint64_t> &tk) {
     }
     if (cudaMemcpyAsync(sl.flags.host, dflags, flag_words * 4, cudaMemcpyDeviceToHost, sl.st) != cudaSuccess)
         return CM_EDEVICE;
-    if (scratch) cudaFreeAsync(scratch, sl.st);
-    if (cudaEventRecord(sl.ev, sl.st) != cudaSuccess) return CM_EDEVICE;
     return CM_OK;
+}
+
+// Scratch layout, allocation and launch of an admitted wave; the scratch goes
+// back to the pool (stream-ordered) whatever happens.
+cm_status launch_wave(cm_server *S, Slot &sl, Wave &w) {
+    const uint32_t n = (uint32_t)w.r.size();
+    std::vector<size_t> off(n, 0);
+    std::vector<uint32_t> wl, solo;
+    size_t total = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const WaveReq &r = w.r[i];
+        off[i] = total;
+        if (on_worklist(r.p)) {
+            wl.push_back(i);
+            total += worklist_scratch_bytes(r.p);
+        } else {
+            solo.push_back(i);
+            uint64_t t0, t1;
+            total += r256(blocks_scratch(r.blocks, &t0, &t1));
+        }
+    }
+    void *scratch = nullptr;
+    if (total && cudaMallocFromPoolAsync(&scratch, total, S->ctx->pool, sl.st) != cudaSuccess) {
+        cudaGetLastError();
+        return CM_ENOMEM;
+    }
+    cm_status s = enqueue_wave(S, sl, w, static_cast<uint8_t *>(scratch), off, wl, solo);
+    if (scratch) cudaFreeAsync(scratch, sl.st);
+    if (s == CM_OK && cudaEventRecord(sl.ev, sl.st) != cudaSuccess) s = CM_EDEVICE;
+    return s;
 }
 
 void worker_main(cm_server *S) {
@@ -327,18 +457,7 @@ void worker_main(cm_server *S) {
                 finish_slot(S, sl);
                 progress = true;
             } else if (q != cudaErrorNotReady) {
-                // device error: fail the wave's requests
-                for (uint64_t t : sl.tickets) {
-                    Req &r = S->reqs[t];
-                    r.status = CM_EDEVICE;
-                    r.done = true;
-                    r.t_done = now_ns();
-                    ++S->completed;
-                }
-                S->inflight -= sl.foot;
-                sl.foot = 0;
-                sl.tickets.clear();
-                sl.busy = false;
+                fail_wave(S, sl, CM_EDEVICE);
                 progress = true;
             } else {
                 any_busy = true;
@@ -348,52 +467,15 @@ void worker_main(cm_server *S) {
         if (S->stop && S->pending.empty() && !any_busy) break;
         for (Slot &sl : S->slots) {
             if (sl.busy || S->pending.empty()) continue;
-            std::vector<uint64_t> wave;
-            size_t foot = 0;
-            while (!S->pending.empty() && wave.size() < S->opt.max_wave) {
-                Req &r = S->reqs[S->pending.front()];
-                if (S->inflight + foot + r.foot + S->seed_bytes > S->budget) break;  // admitted when memory frees up
-                foot += r.foot;
-                wave.push_back(S->pending.front());
-                S->pending.pop_front();
-            }
-            if (wave.empty()) break;
-            const uint64_t t = now_ns(), w = ++S->waves;
-            for (uint64_t tk : wave) {
-                S->reqs[tk].t_admit = t;
-                S->reqs[tk].wave = w;
-            }
-            sl.tickets = wave;
-            sl.foot = foot;
-            sl.wave = w;
-            sl.busy = true;
-            S->inflight += foot;
-            if (S->inflight > S->max_inflight) S->max_inflight = S->inflight;
-            const cm_status s = launch_wave(S, sl, wave);
+            Wave w;
+            if (!admit_wave(S, sl, w)) break;
+            // submissions and polls proceed while the wave is planned and launched
+            lk.unlock();
+            cm_status s = launch_wave(S, sl, w);
+            if (s != CM_OK) cudaStreamSynchronize(sl.st);
+            lk.lock();
             if (s != CM_OK) {
-                cudaStreamSynchronize(sl.st);
-                for (auto &kc : sl.seeds) {
-                    auto it = S->seeds.find(kc.first);
-                    if (it == S->seeds.end()) continue;
-                    it->second.refs -= 1;
-                    if (kc.second && it->second.refs == 0) {
-                        cudaFreeAsync(it->second.buf, sl.st);
-                        S->seed_bytes -= it->second.bytes;
-                        S->seeds.erase(it);
-                    }
-                }
-                sl.seeds.clear();
-                for (uint64_t tk : wave) {
-                    Req &r = S->reqs[tk];
-                    r.status = s;
-                    r.done = true;
-                    r.t_done = now_ns();
-                    ++S->completed;
-                }
-                S->inflight -= foot;
-                sl.tickets.clear();
-                sl.foot = 0;
-                sl.busy = false;
+                fail_wave(S, sl, s);
                 S->cv_done.notify_all();
             }
             progress = true;
@@ -486,9 +568,9 @@ extern "C" cm_status cm_submit(cm_ctx *ctx, const cm_request *rq, uint64_t *tick
     r.seed_id = rq->seed_id;
     if (rq->flags & ~CM_REQ_SEED_CACHE) return CM_EINVAL;
     if (!rq->x || !rq->y || !rq->z || !make_plan(rq->kind, rq->n, rq->m, &r.p, worklist_fields(ctx->popt))) return CM_EINVAL;
-    if (r.p.npass > 1) {
-        // too long for the work list: the single-call planner (sums of shorter
-        // products, a dense tail) within the server's budget
+    if (!on_worklist(r.p)) {
+        // too long for the work list: the single-call planner (one product, or
+        // sums of shorter products and a dense tail) within the server's budget
         PlanOptions po = ctx->popt;
         po.budget = S->budget;
         if (!make_blocks(rq->kind, rq->n, rq->m, po, &r.blocks)) return CM_EINVAL;

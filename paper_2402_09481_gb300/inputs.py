@@ -84,16 +84,14 @@ def bernoulli(stream: int, nbits: int, threshold_u32: int = BIAS_08_THRESHOLD) -
     out = np.zeros(nw, dtype=np.uint64)
     step = 1 << 21  # words of output per chunk
     thr = np.uint64(threshold_u32)
-    weights = (np.uint64(1) << np.arange(64, dtype=np.uint64))
     for c in range(0, nw, step):
         cw = min(step, nw - c)
         g = stream_words(stream, 32 * cw, first=32 * c).reshape(cw, 32)
-        lo = (g & np.uint64(0xFFFFFFFF)) < thr
-        hi = (g >> np.uint64(32)) < thr
         bits = np.empty((cw, 64), dtype=bool)
-        bits[:, 0::2] = lo
-        bits[:, 1::2] = hi
-        out[c:c + cw] = (bits.astype(np.uint64) * weights).sum(axis=1, dtype=np.uint64)
+        bits[:, 0::2] = (g & np.uint64(0xFFFFFFFF)) < thr
+        bits[:, 1::2] = (g >> np.uint64(32)) < thr
+        # bit j of output word = bits[:, j] (little-endian bytes of the word)
+        out[c:c + cw] = np.packbits(bits, axis=1, bitorder="little").view("<u8").reshape(cw)
     return _mask_tail(out, nbits)
 
 

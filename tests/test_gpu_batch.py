@@ -62,7 +62,8 @@ def mixed_specs():
     return [(T, 1000, 500), (T, 4096, 4097), (T, 5000, 4000), (T, 20000, 10000), (T, 2 ** 17, 2 ** 16),
             (C, P[0] - 1, P[0] // 2), (C, P[2] - 1, P[2] - 1), (C, P[3] - 1, P[3] // 2),
             (D, P[1], (2 * P[1]) // 5), (D, P[4], P[4] // 2), (T, 3, 2), (C, 10, 3),
-            (T, 2 ** 25, 2 ** 24)]  # the last one (L = 2^26) needs two column passes (per-call path)
+            (T, 2 ** 21, 2 ** 20),  # L = 2^22: past the work list, the single-call kernels over F25
+            (T, 2 ** 25, 2 ** 24)]  # L = 2^26: two column passes (single-call path)
 
 
 def test_batch_mixed_matches_single_and_oracle(cm_ctx):
@@ -72,7 +73,7 @@ def test_batch_mixed_matches_single_and_oracle(cm_ctx):
     b.launch()
     torch.cuda.synchronize()
     info = b.info()
-    assert info["instances"] == len(specs) and info["solo_instances"] == 1 and info["graph"] == 1
+    assert info["instances"] == len(specs) and info["solo_instances"] == 2 and info["graph"] == 1
     for (kind, n, m, x, y, z), (xw, yw) in zip(items, host):
         assert torch.equal(z, single(cm_ctx, kind, n, m, x, y)), (kind, n, m)
         oracle_check(kind, n, m, xw, yw, z)

@@ -257,6 +257,21 @@ def test_dodis_workload_both_plans(cm_ctx):
 
 
 @pytest.mark.slow
+def test_dodis_workload_biased_source(cm_ctx):
+    # the configuration's second Dodis et al. run: x 0.8-biased (P(bit = 1) =
+    # 0.8), y Bernoulli(1/2), n = 2^30 - 35, m = floor(0.4 n); sampled rows
+    n = 1073741789
+    m = int(0.4 * n)
+    xw, yw = inputs.bernoulli(70, n), inputs.bernoulli_half(71, n)
+    z = run(cm_ctx, D, n, m, xw, yw)
+    assert cm_ctx.device_status()[0] == native.CM_OK
+    rows = sample_rows(m, 16, 8)
+    assert (out_bits(z, rows) == oracle.dodis_rows(xw, yw, n, m, rows)).all()
+    if m & 63:
+        assert int(z[-1]) >> (m & 63) == 0
+
+
+@pytest.mark.slow
 def test_qrng_example_toeplitz_sampled(cm_ctx):
     # n1 = 6.5e9, m = floor(k1 + 2 log2 1e-10) = 581294933, seed n1 + m - 1 bits
     n, m = 6_500_000_000, 581_294_933

@@ -123,7 +123,15 @@ def test_server_admission_by_footprint(sctx, cm_ctx):
     assert 0 < st["max_inflight_bytes"] <= budget
     for r in reqs:
         assert torch.equal(r["z"], alone(cm_ctx, r))
-    big = make(T, 2 ** 22, 2 ** 22, 999)   # L = 2^23: 64 MiB alone
+    # L = 2^23 alone needs 64 MiB: the single-call planner splits it into
+    # summed blocks that fit the budget
+    big = make(T, 2 ** 22, 2 ** 22, 999)
+    assert wait(sctx, submit(sctx, big))["status"] == native.CM_OK
+    assert sctx.server_stats()["max_inflight_bytes"] <= budget
+    assert torch.equal(big["z"], alone(cm_ctx, big))
+    sctx.server_stop()
+    # nothing fits 64 KiB: refused at submission
+    sctx.server_start(hbm_budget_bytes=64 << 10, slots=1)
     s, _ = sctx.submit_raw(T, big["n"], big["m"], big["x"].data_ptr(), big["y"].data_ptr(), big["z"].data_ptr())
     assert s == native.CM_ENOMEM
     sctx.server_stop()
