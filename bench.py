@@ -743,7 +743,8 @@ def run_batched_b(args, world, rank, local):
 
     others = {}
     compare = os.environ.get("CM_BENCH_NO_COMPARE") != "1"
-    for name, e in (("imma", native.ENGINE_IMMA), ("gf2", native.ENGINE_GF2)) if compare else ():
+    for name, e in ((("imma", native.ENGINE_IMMA), ("gf2", native.ENGINE_GF2), ("bmma", native.ENGINE_BMMA))
+                    if compare else ()):
         Z.zero_()
         t = statistics.median(timed(lambda e=e: step(e), max(3, min(args.steps, 10))))
         assert torch.equal(Z, z_ref), name
@@ -780,7 +781,7 @@ def run_batched_b(args, world, rank, local):
         step()
     prof = ctx.profile_read(reset=True)
     ctx.profile_enable(False)
-    kname = "k_ss_gf2" if engine == native.ENGINE_GF2 else "k_ss_imma"
+    kname = {native.ENGINE_GF2: "k_ss_gf2", native.ENGINE_BMMA: "k_ss_bmma"}.get(engine, "k_ss_imma")
     c_, t_ = prof[kname]
     per_launch = t_ / c_
     clocks = sampler.summary(tw0, tw1)
@@ -792,6 +793,17 @@ def run_batched_b(args, world, rank, local):
                 "peak": peak / 1e12, "unit": "T LOP3/s", "frac": ops / (per_launch * 1e-3) / peak,
                 "peak_source": "152 SMs x 64 ALU lanes x measured SM clock",
                 "traffic": ncu_traffic(kname, "batched_b"), "avg_launch_ms": per_launch}
+    elif engine == native.ENGINE_BMMA:
+        # algorithmic HBM bytes: the inputs once, the outputs once, the expanded matrix once
+        alg = 8 * X.size + 8 * Z.numel() + (m + 63) // 64 * 64 * ((n + 1023) // 1024 * 1024) // 8
+        hbm, hbm_src = measured_peaks()
+        roof = {"bound": "hbm", "kernel": kname, "achieved": alg / (per_launch * 1e-3) / 1e9, "peak": hbm,
+                "unit": "GB/s", "frac": alg / (per_launch * 1e-3) / 1e9 / hbm,
+                "peak_source": f"{hbm_src} HBM copy bandwidth (MEASURED_PEAKS.json)",
+                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_launch,
+                "traffic": ncu_traffic(kname, "batched_b"),
+                "b1_tensor_ops": {"value": count * m * n / (per_launch * 1e-3) / 1e12, "unit": "T bit-AND-POPC/s",
+                                  "note": "no measured or nominal peak for b1 MMA on this GPU"}}
     else:
         ops = 2 * count * m * n
         roof = {"bound": "tensor", "kernel": kname, "achieved": ops / (per_launch * 1e-3) / 1e12,
@@ -830,10 +842,11 @@ def run_batched_b(args, world, rank, local):
         line = {
             "metric": "extracted output Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 (GF(2) words)"
-            if engine == native.ENGINE_GF2 else "s8", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": {native.ENGINE_GF2: "u32 (GF(2) words)",
+                                                                 native.ENGINE_BMMA: "b1"}.get(engine, "s8"),
+            "data": "synthetic",
             "config": {"workload": f"Shared Toeplitz seed: {count} inputs of n = 4096 bits, m = 2048, "
-                                   "Bernoulli(1/2)", "engine": {1: "imma", 2: "gf2"}.get(engine),
+                                   "Bernoulli(1/2)", "engine": {1: "imma", 2: "gf2", 3: "bmma"}.get(engine),
                        "l2": "inputs (%d MB) larger than L2" % (8 * X.size >> 20),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "compare": others, "latency_ms": {"p50": statistics.median(step_ms), "p99": max(step_ms)},
@@ -1543,15 +1556,17 @@ def run_single(args, world, rank, local, dist):
 
     # CPU baselines on the host cores: the bit-packed CPU NTT on the whole
     # workload (one thread and every core) and the oracle on a bounded sample
-    cpu = cpu_ntt = None
+    cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, rows, secs = cpu_oracle_rate(kind, n, m, xw, yw)
         cpu = {"value": rate / 1e9, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
                "sample": f"{rows} random output rows of the full-size workload in {secs:.1f} s "
                          f"(explicit GF(2) rows, numpy, one thread)"}
+        # the competent CPU implementation, timed in the same run beside the oracle
         cpu_ntt = cpu_ntt_baseline(kind, n, m, xw, yw, z_gpu.numpy().view(np.uint64))
         if cpu_ntt is None:
             cpu_ntt = {"unavailable": "the CPU NTT's field (3 * 2^30 + 1) holds transforms up to 2^30 only"}
+        cpu["cpu_ntt"] = cpu_ntt
 
     clocks = sampler.summary(t_wall0, t_wall1)
     if rank != 0:
@@ -1571,7 +1586,7 @@ def run_single(args, world, rank, local, dist):
         "latency_ms": {"p50": statistics.median(step_ms),
                        "p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},
         "roofline": roof, "path_roofline": path_roof, "kernels": kernels,
-        "e2e": e2e, "cpu_baseline": cpu, **({"cpu_ntt": cpu_ntt} if cpu_ntt else {}), "clocks": clocks,
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
         **({"as_configured": as_configured} if as_configured else {}),
         "gpu_launches": launches * args.steps,
     }

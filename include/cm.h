@@ -163,6 +163,27 @@ cm_status cm_circulant(cm_ctx *ctx, const uint64_t *x, uint64_t n, const uint64_
 cm_status cm_dodis(cm_ctx *ctx, const uint64_t *x, const uint64_t *y, uint64_t n, uint64_t m,
                    uint64_t *z, cm_stream stream);
 
+/*
+ * Composed two-source extractor, Section "Composing extractors": a strong
+ * seeded extractor appended to a strong two-source extractor, the two-source
+ * output serving as the seed and the two-source weak seed as the input.
+ *   stage 1: s = Ext_kind1(x, y), m1 bits (x: n1 bits; y: the seed length of
+ *            kind1 for (n1, m1): n1 + m1 - 1, n1 + 1 or n1 bits);
+ *   stage 2: t = Ext_kind2(input = bits 0 .. n2-1 of y, seed = the first bits
+ *            of s), m2 bits; the seed takes n2 + m2 - 1 (Toeplitz), n2 + 1
+ *            (Circulant) or n2 (Dodis et al.) bits of s.
+ * z: m1 + m2 bits (ceil((m1 + m2)/64) words, written): s in bits 0 .. m1-1,
+ * t in bits m1 .. m1+m2-1.  The paper names neither the seeded extractor nor
+ * its lengths; the caller picks them (kind2 a cm_kind, n2 <= y's length,
+ * stage 2's seed length <= m1), each stage with the argument rules of its
+ * single call.  CM_EINVAL otherwise, before any work.  Device pointers,
+ * stream-ordered; scratch: ceil(m2/64) words from the context pool besides
+ * the stages' own.  A constant Dodis et al. input in either stage is reported
+ * by cm_device_status (CM_EPRECOND) as for cm_dodis.
+ */
+cm_status cm_compose(cm_ctx *ctx, int kind1, const uint64_t *x, uint64_t n1, const uint64_t *y, uint64_t m1,
+                     int kind2, uint64_t n2, uint64_t m2, uint64_t *z, cm_stream stream);
+
 /* Synchronize `stream`, then read and clear the context's device status bits.
  * *flags (may be NULL) receives the CM_FLAG_* bits.  Returns CM_EPRECOND if
  * CM_FLAG_PRECOND was set, CM_ETIMEDOUT if CM_FLAG_TIMEOUT was set, CM_EDEVICE
@@ -288,9 +309,10 @@ cm_status cm_batch_toeplitz(cm_ctx *ctx, const cm_desc *descs, uint32_t count, c
 
 /* ----- many inputs under one shared Toeplitz seed ------------------------- */
 
-#define CM_ENGINE_AUTO 0 /* faster of the two, timed on the first call of an (n, m) */
+#define CM_ENGINE_AUTO 0 /* fastest engine, timed on the first call of an (n, m) */
 #define CM_ENGINE_IMMA 1 /* INT8 tensor cores (mma.sync s8 x s8 -> s32), mod-2 epilogue */
 #define CM_ENGINE_GF2 2  /* CUDA cores: XOR of AND over packed words, parity epilogue */
+#define CM_ENGINE_BMMA 3 /* binary tensor cores (mma.sync b1 x b1 -> s32, AND-POPC), mod-2 epilogue */
 
 /*
  * Z_c = toep(y) X_c over GF(2) for c < count: the Toeplitz extractor of Eq.

@@ -83,6 +83,11 @@ static bool base_maps(int kind, uint64_t n, uint64_t m, Plan *p) {
     return true;
 }
 
+bool valid_args(int kind, uint64_t n, uint64_t m) {
+    Plan p;
+    return base_maps(kind, n, m, &p);
+}
+
 // Scratch of one product: the operands A and B (and the transform-domain sum C
 // of a summed window) and the parity bytes; one-CTA plans (lg <= 13) keep
 // everything on chip.  A single call's plan adds 256 bytes of Dodis et al.

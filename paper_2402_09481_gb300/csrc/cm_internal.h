@@ -145,6 +145,8 @@ inline int field_for(int fields, int lg) {
 // Validate (kind, n, m) and fill the plan; false if invalid or if K + m - 1
 // exceeds 2^32 (one transform).  fields: a field set (kFields*).
 bool make_plan(int kind, uint64_t n, uint64_t m, Plan *out, int fields = kFieldsGL);
+// (kind, n, m) satisfies the argument rules of the single calls.
+bool valid_args(int kind, uint64_t n, uint64_t m);
 
 // Longest bit string a blocked extraction takes (the paper's 2^40).
 constexpr uint64_t kMaxBits = 1ull << 40;

@@ -3,7 +3,7 @@
 //
 // The seed is expanded once into T, the m x n Toeplitz matrix of Eq. toep as
 // packed bit rows (T[i][j] = y[(i - j) mod (n + m - 1)], zero-padded to whole
-// tiles).  Two exact engines multiply T by the packed inputs:
+// tiles).  Three exact engines multiply T by the packed inputs:
 //
 //  * kImma: INT8 tensor cores (mma.sync m16n8k32, s8 x s8 -> s32).  Operand
 //    fragments are built in registers from the packed bits (4 bits -> 4 bytes of
@@ -14,15 +14,21 @@
 //    popcount(AND); the kernel accumulates XOR(T_word AND X_word) (one LOP3 per
 //    32 bit-products) and takes the parity once per output.
 //
-// Both give identical bits; the default picks the faster on the first call of a
-// shape (timed on that call) and remembers it.
+//  * kBmma: binary tensor cores (mma.sync m16n8k256, b1 x b1 -> s32 with
+//    AND-POPC): popcount(row AND column) over 256 bits per instruction from
+//    the packed words; exact int32 counts, bit 0 kept.
+//
+// All give identical bits; the default picks the fastest on the first call of
+// a shape (timed on that call) and remembers it.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
 
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
+#include <vector>
 
 #include "cm.h"
 #include "cm_ctx.h"
@@ -230,12 +236,123 @@ k_ss_imma(const uint32_t *__restrict__ T, uint32_t words_pad, const uint64_t *__
     }
 }
 
-std::mutex g_engine_mu;
-std::map<std::pair<uint64_t, uint64_t>, int> g_engine_choice;  // (n, m) -> engine variant
+// ---------------------------------------------------------------------------
+// Binary tensor-core engine: mma.sync m16n8k256 b1 x b1 -> s32 with AND-POPC,
+// i.e. popcount(row AND column) over 256 bits per instruction, straight from
+// the packed words (no byte expansion).  The counts are exact in int32 (at
+// most n) and the epilogue keeps bit 0.  Thread t of a quad holds, per row or
+// column, the words w + t and w + 4 + t of a 256-bit step in both operands, so
+// A and B cover the same bits of K in the same order and the popcount is the
+// dot product whatever the register's bit order.
+// CTA: ROWS x 128 instances, 8 warps of (ROWS / 2) rows x 32 instances.
+// ---------------------------------------------------------------------------
+constexpr int kBmPad = 4;  // row stride 36 words: fragment loads hit 32 distinct banks
 
-// Engine variants the autotuner times: the INT8 engine and the GF(2) engine
-// with 4 or 2 instances per thread.
-constexpr int kVarImma = 0, kVarGf2x4 = 1, kVarGf2x2 = 2;
+template <int ROWS>
+__global__ void __launch_bounds__(256)
+k_ss_bmma(const uint32_t *__restrict__ T, uint32_t rows_pad, uint32_t words_pad, const uint64_t *__restrict__ X,
+          uint64_t wx, uint64_t count, uint64_t *__restrict__ Z, uint64_t wz) {
+    constexpr int WM = ROWS / 2, AT = WM / 16;  // warp rows, 16-row A tiles per warp
+    static_assert(kImCols * ROWS <= ROWS * (kSsKw + kBmPad) * 4, "parity bytes reuse the T tile");
+    __shared__ __align__(16) uint32_t sT[ROWS][kSsKw + kBmPad];
+    __shared__ __align__(16) uint32_t sX[kImCols][kSsKw + kBmPad];
+    auto sPar = reinterpret_cast<uint8_t (*)[ROWS]>(&sT[0][0]);  // after the last K chunk
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int wr = warp & 1, wc = warp >> 1;  // warp tile: rows wr * WM .., instances wc * 32 ..
+    const uint32_t row0 = blockIdx.x * ROWS;
+    const uint64_t col0 = (uint64_t)blockIdx.y * kImCols;
+    int acc[AT][4][4];
+#pragma unroll
+    for (int a = 0; a < AT; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[a][b][k] = 0;
+    for (uint32_t w0 = 0; w0 < words_pad; w0 += kSsKw) {
+        // 16-byte loads: T rows (words_pad is a multiple of kSsKw), X instances (wx u64 words each)
+        for (int e = threadIdx.x; e < ROWS * (kSsKw / 4); e += 256) {
+            const int r = e / (kSsKw / 4), q = e % (kSsKw / 4);
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (row0 + r < rows_pad)
+                v = __ldg(reinterpret_cast<const uint4 *>(T + (uint64_t)(row0 + r) * words_pad + w0) + q);
+            *reinterpret_cast<uint4 *>(&sT[r][4 * q]) = v;
+        }
+        for (int e = threadIdx.x; e < kImCols * (kSsKw / 4); e += 256) {
+            const int cc = e / (kSsKw / 4), q = e % (kSsKw / 4);
+            const uint64_t c = col0 + cc, u = w0 / 2 + 2 * q;  // first u64 word of this 16 bytes
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (c < count) {
+                const uint64_t *src = X + c * wx + u;
+                const uint64_t lo = u < wx ? __ldg(src) : 0ull, hi = u + 1 < wx ? __ldg(src + 1) : 0ull;
+                v = make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+            }
+            *reinterpret_cast<uint4 *>(&sX[cc][4 * q]) = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < kSsKw; w += 8) {  // one k256 step per 8 words
+            uint32_t afr[AT][4], bfr[4][2];
+#pragma unroll
+            for (int a = 0; a < AT; ++a) {
+                const int r = wr * WM + a * 16 + g;
+                afr[a][0] = sT[r][w + t];
+                afr[a][1] = sT[r + 8][w + t];
+                afr[a][2] = sT[r][w + 4 + t];
+                afr[a][3] = sT[r + 8][w + 4 + t];
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int cc = wc * 32 + b * 8 + g;
+                bfr[b][0] = sX[cc][w + t];
+                bfr[b][1] = sX[cc][w + 4 + t];
+            }
+#pragma unroll
+            for (int a = 0; a < AT; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k256.row.col.s32.b1.b1.s32.and.popc {%0,%1,%2,%3}, "
+                        "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                        : "+r"(acc[a][b][0]), "+r"(acc[a][b][1]), "+r"(acc[a][b][2]), "+r"(acc[a][b][3])
+                        : "r"(afr[a][0]), "r"(afr[a][1]), "r"(afr[a][2]), "r"(afr[a][3]), "r"(bfr[b][0]),
+                          "r"(bfr[b][1]));
+        }
+        __syncthreads();
+    }
+    // mod-2 epilogue: accumulator (row g / g + 8, instances 2t, 2t + 1) -> parity bytes
+#pragma unroll
+    for (int a = 0; a < AT; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int r = wr * WM + a * 16 + g, cc = wc * 32 + b * 8 + 2 * t;
+            sPar[cc][r] = (uint8_t)(acc[a][b][0] & 1);
+            sPar[cc + 1][r] = (uint8_t)(acc[a][b][1] & 1);
+            sPar[cc][r + 8] = (uint8_t)(acc[a][b][2] & 1);
+            sPar[cc + 1][r + 8] = (uint8_t)(acc[a][b][3] & 1);
+        }
+    __syncthreads();
+    // pack: one warp per (instance, 64-row word) at a time
+    for (int e = warp; e < kImCols * (ROWS / 64); e += 8) {
+        const int cc = e / (ROWS / 64), h = e % (ROWS / 64);
+        const uint32_t lo = __ballot_sync(0xffffffffu, sPar[cc][64 * h + lane]);
+        const uint32_t hi = __ballot_sync(0xffffffffu, sPar[cc][64 * h + 32 + lane]);
+        const uint64_t c = col0 + cc, zw = (row0 >> 6) + h;
+        if (lane == 0 && c < count && zw < wz) Z[c * wz + zw] = ((uint64_t)hi << 32) | lo;
+    }
+}
+
+std::mutex g_engine_mu;
+// (n, m, engine asked for) -> the variant the first call of that shape timed fastest
+std::map<std::tuple<uint64_t, uint64_t, int>, int> g_engine_choice;
+
+// Engine variants the autotuner times: the INT8 engine, the GF(2) engine
+// with 4 or 2 instances per thread, and the binary engine with 64- or 128-row
+// tiles.
+constexpr int kVarImma = 0, kVarGf2x4 = 1, kVarGf2x2 = 2, kVarBmma64 = 3, kVarBmma128 = 4;
+inline int engine_of(int var) {
+    return var == kVarImma ? CM_ENGINE_IMMA : (var >= kVarBmma64 ? CM_ENGINE_BMMA : CM_ENGINE_GF2);
+}
 
 cm_status launch_variant(int var, const uint32_t *T, uint32_t rows_pad, uint32_t words_pad,
                          const uint64_t *X, uint64_t wx, uint64_t count, uint64_t *Z, uint64_t wz,
@@ -248,6 +365,14 @@ cm_status launch_variant(int var, const uint32_t *T, uint32_t rows_pad, uint32_t
         dim3 grid(rows_pad / kSsRows, (unsigned)((count + 127) / 128));
         ProfScope ps(ctx, "k_ss_gf2", st);
         k_ss_gf2<2><<<grid, 256, 0, st>>>(T, words_pad, X, wx, count, Z, wz);
+    } else if (var == kVarBmma64 || var == kVarBmma128) {
+        const int rows = var == kVarBmma64 ? 64 : 128;
+        dim3 grid((rows_pad + rows - 1) / rows, (unsigned)((count + kImCols - 1) / kImCols));
+        ProfScope ps(ctx, "k_ss_bmma", st);
+        if (var == kVarBmma64)
+            k_ss_bmma<64><<<grid, 256, 0, st>>>(T, rows_pad, words_pad, X, wx, count, Z, wz);
+        else
+            k_ss_bmma<128><<<grid, 256, 0, st>>>(T, rows_pad, words_pad, X, wx, count, Z, wz);
     } else {
         dim3 grid(rows_pad / kSsRows, (unsigned)((count + kImCols - 1) / kImCols));
         ProfScope ps(ctx, "k_ss_imma", st);
@@ -265,7 +390,8 @@ extern "C" cm_status cm_batch_toeplitz_shared_seed(cm_ctx *ctx, const uint64_t *
                                                    const uint64_t *X, uint64_t count, uint64_t *Z,
                                                    int engine, cm_stream stream) {
     if (!ctx || !y || !X || !Z || n == 0 || m == 0 || count == 0) return CM_EINVAL;
-    if (engine != CM_ENGINE_AUTO && engine != CM_ENGINE_IMMA && engine != CM_ENGINE_GF2) return CM_EINVAL;
+    if (engine != CM_ENGINE_AUTO && engine != CM_ENGINE_IMMA && engine != CM_ENGINE_GF2 && engine != CM_ENGINE_BMMA)
+        return CM_EINVAL;
     if (n > (1ull << 24) || m > (1ull << 24) || (n * m) > (1ull << 34) || count > (1ull << 31))
         return CM_EINVAL;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return CM_EDEVICE;
@@ -290,22 +416,31 @@ extern "C" cm_status cm_batch_toeplitz_shared_seed(cm_ctx *ctx, const uint64_t *
         k_toep_rows<<<(unsigned)blocks, 256, 0, st>>>(y, n, m, T, rows_pad, words_pad);
         if (cudaGetLastError() != cudaSuccess) s = CM_EDEVICE;
     }
-    int var = engine == CM_ENGINE_IMMA ? kVarImma : kVarGf2x4;
-    if (s == CM_OK && engine != CM_ENGINE_IMMA) {
-        // CM_ENGINE_GF2 and CM_ENGINE_AUTO use the tuned variant for (n, m);
-        // the first call of a shape times the candidates on its own data
+    // candidates of the engine asked for; the first call of a shape times them
+    // on its own data and later calls take the fastest
+    std::vector<int> cand;
+    if (engine == CM_ENGINE_AUTO || engine == CM_ENGINE_IMMA) cand.push_back(kVarImma);
+    if (engine == CM_ENGINE_AUTO || engine == CM_ENGINE_GF2) {
+        cand.push_back(kVarGf2x4);
+        cand.push_back(kVarGf2x2);
+    }
+    if (engine == CM_ENGINE_AUTO || engine == CM_ENGINE_BMMA) {
+        cand.push_back(kVarBmma64);
+        cand.push_back(kVarBmma128);
+    }
+    int var = cand[0];
+    if (s == CM_OK && cand.size() > 1) {
         std::lock_guard<std::mutex> lock(g_engine_mu);
-        auto it = g_engine_choice.find({n, m});
-        if (it != g_engine_choice.end() && (engine == CM_ENGINE_AUTO || it->second != kVarImma)) {
+        const auto key = std::make_tuple(n, m, engine);
+        auto it = g_engine_choice.find(key);
+        if (it != g_engine_choice.end()) {
             var = it->second;
         } else {
             float best = 1e30f;
-            int best_v = kVarGf2x4;
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
-            for (int v : {kVarImma, kVarGf2x4, kVarGf2x2}) {
-                if (engine == CM_ENGINE_GF2 && v == kVarImma) continue;
+            for (int v : cand) {
                 launch_variant(v, T, rows_pad, words_pad, X, wx, count, Z, wz, ctx, st);  // warm-up
                 cudaEventRecord(e0, st);
                 s = launch_variant(v, T, rows_pad, words_pad, X, wx, count, Z, wz, ctx, st);
@@ -313,15 +448,15 @@ extern "C" cm_status cm_batch_toeplitz_shared_seed(cm_ctx *ctx, const uint64_t *
                 cudaEventSynchronize(e1);
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
-                if (s == CM_OK && ms < best) {
+                if (s != CM_OK) break;
+                if (ms < best) {
                     best = ms;
-                    best_v = v;
+                    var = v;
                 }
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
-            if (engine == CM_ENGINE_AUTO || best_v != kVarImma) g_engine_choice[{n, m}] = best_v;
-            var = best_v;
+            if (s == CM_OK) g_engine_choice[key] = var;
         }
     }
     if (s == CM_OK) s = launch_variant(var, T, rows_pad, words_pad, X, wx, count, Z, wz, ctx, st);
@@ -331,7 +466,7 @@ extern "C" cm_status cm_batch_toeplitz_shared_seed(cm_ctx *ctx, const uint64_t *
 
 extern "C" int cm_shared_seed_engine(uint64_t n, uint64_t m) {
     std::lock_guard<std::mutex> lock(g_engine_mu);
-    auto it = g_engine_choice.find({n, m});
+    auto it = g_engine_choice.find(std::make_tuple(n, m, (int)CM_ENGINE_AUTO));
     if (it == g_engine_choice.end()) return CM_ENGINE_AUTO;
-    return it->second == kVarImma ? CM_ENGINE_IMMA : CM_ENGINE_GF2;
+    return engine_of(it->second);
 }

@@ -36,6 +36,7 @@ PROTOTYPES = {
     "cm_toeplitz": (_I, [_P, _P, _U64, _P, _U64, _P, _P]),
     "cm_circulant": (_I, [_P, _P, _U64, _P, _U64, _P, _P]),
     "cm_dodis": (_I, [_P, _P, _P, _U64, _U64, _P, _P]),
+    "cm_compose": (_I, [_P, _I, _P, _U64, _P, _U64, _I, _U64, _U64, _P, _P]),
     "cm_device_status": (_I, [_P, _P, ctypes.POINTER(_U32)]),
     "cm_extract_host": (_I, [_P, _I, _P, _U64, _P, _U64, _P, _P]),
     "cm_toeplitz_noalloc": (_I, [_P, _U64, _P, _U64, _P, _P]),
@@ -166,7 +167,7 @@ class ServerStats(ctypes.Structure):
 
 
 BATCH_AUTOTUNE, BATCH_NO_GRAPH, BATCH_TEST_STALL = 0x1, 0x2, 0x4
-ENGINE_AUTO, ENGINE_IMMA, ENGINE_GF2 = 0, 1, 2
+ENGINE_AUTO, ENGINE_IMMA, ENGINE_GF2, ENGINE_BMMA = 0, 1, 2, 3
 
 
 class CMError(RuntimeError):
@@ -405,6 +406,18 @@ class Context:
         z = self._out(z, m, x)
         _check(self._L.cm_dodis(self._h, px, py, n, m, z.data_ptr(), _stream_handle(stream)),
                "cm_dodis")
+        return z
+
+    def compose(self, kind1: int, x, n1: int, y, m1: int, kind2: int, n2: int, m2: int, z=None, stream=None):
+        """Composed extractor (cm_compose): s = Ext_kind1(x, y) (m1 bits), then
+        t = Ext_kind2(first n2 bits of y, seed = first bits of s) (m2 bits);
+        returns z = s followed by t (m1 + m2 bits)."""
+        ybits = {TOEPLITZ: n1 + m1 - 1, CIRCULANT: n1 + 1, DODIS: n1}.get(kind1, 0)
+        px = _dev_words(x, n1, "x")
+        py = _dev_words(y, ybits, "y")
+        z = self._out(z, m1 + m2, x)
+        _check(self._L.cm_compose(self._h, kind1, px, n1, py, m1, kind2, n2, m2, z.data_ptr(),
+                                  _stream_handle(stream)), "cm_compose")
         return z
 
     def von_neumann(self, x, n: int, z=None, m_out=None, stream=None):

@@ -1,5 +1,6 @@
-"""Many inputs under one Toeplitz seed: both dense engines (INT8 tensor cores
-and GF(2) CUDA cores) vs the single-call NTT path and the CPU oracle."""
+"""Many inputs under one Toeplitz seed: the three dense engines (INT8 and
+binary tensor cores, GF(2) CUDA cores) vs the single-call NTT path and the CPU
+oracle."""
 
 import numpy as np
 import pytest
@@ -32,12 +33,12 @@ def run_case(ctx, n, m, count, engine, seed):
     return Zh
 
 
-@pytest.mark.parametrize("engine", [native.ENGINE_IMMA, native.ENGINE_GF2])
+@pytest.mark.parametrize("engine", [native.ENGINE_IMMA, native.ENGINE_GF2, native.ENGINE_BMMA])
 def test_engines_config_shape(cm_ctx, engine):
     run_case(cm_ctx, 4096, 2048, 300, engine, 11)
 
 
-@pytest.mark.parametrize("engine", [native.ENGINE_IMMA, native.ENGINE_GF2])
+@pytest.mark.parametrize("engine", [native.ENGINE_IMMA, native.ENGINE_GF2, native.ENGINE_BMMA])
 @pytest.mark.parametrize("n,m,count", [(1000, 333, 257), (77, 1, 3), (1, 65, 129), (5000, 4000, 9)])
 def test_engines_ragged(cm_ctx, engine, n, m, count):
     run_case(cm_ctx, n, m, count, engine, 21)
@@ -47,7 +48,8 @@ def test_auto_engine_agrees(cm_ctx):
     a = run_case(cm_ctx, 3000, 1500, 200, native.ENGINE_AUTO, 31)
     b = run_case(cm_ctx, 3000, 1500, 200, native.ENGINE_GF2, 31)
     assert (a == b).all()
-    assert native.lib().cm_shared_seed_engine(3000, 1500) in (native.ENGINE_IMMA, native.ENGINE_GF2)
+    assert native.lib().cm_shared_seed_engine(3000, 1500) in (native.ENGINE_IMMA, native.ENGINE_GF2,
+                                                              native.ENGINE_BMMA)
 
 
 def test_shared_seed_invalid(cm_ctx):
@@ -64,7 +66,7 @@ def test_shared_seed_invalid(cm_ctx):
 
 def test_engines_full_count_sampled(cm_ctx):
     # the shared-seed workload at full size: 65536 inputs of 4096 bits under one
-    # 2048 x 4096 Toeplitz seed.  The two engines and the auto choice agree on
+    # 2048 x 4096 Toeplitz seed.  The three engines and the auto choice agree on
     # every output bit; 50 inputs against the oracle.
     n, m, count = 4096, 2048, 65536
     wx, wz = native.words(n), native.words(m)
@@ -73,8 +75,9 @@ def test_engines_full_count_sampled(cm_ctx):
     Xd, yd = to_dev(X), to_dev(yw)
     Zg = from_dev(cm_ctx.toeplitz_shared_seed(yd, n, m, Xd, count, engine=native.ENGINE_GF2)).reshape(count, wz)
     Zi = from_dev(cm_ctx.toeplitz_shared_seed(yd, n, m, Xd, count, engine=native.ENGINE_IMMA)).reshape(count, wz)
+    Zb = from_dev(cm_ctx.toeplitz_shared_seed(yd, n, m, Xd, count, engine=native.ENGINE_BMMA)).reshape(count, wz)
     Za = from_dev(cm_ctx.toeplitz_shared_seed(yd, n, m, Xd, count)).reshape(count, wz)
-    assert (Zg == Zi).all() and (Zg == Za).all()
+    assert (Zg == Zi).all() and (Zg == Zb).all() and (Zg == Za).all()
     picks = [0, count - 1] + np.random.default_rng(4098).choice(count, 48, replace=False).tolist()
     for c in picks:
         assert (Zg[c] == oracle.toeplitz_packed(X[c * wx:(c + 1) * wx], n, yw, m)).all(), c
