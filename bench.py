@@ -251,6 +251,10 @@ def kernel_model(products, m):
         if not split:
             add("k_fused_small", bits + mr / 8, bits + mr / 8)
             continue
+        if p["field"] == FIELD_Q25 and 2 ** 14 <= L <= 2 ** 17 and s == 0:
+            # one launch on a thread-block cluster: the arrays never leave the chip
+            add("k_cluster", 48 * L + bits + mr / 8, bits + mr / 8)
+            continue
         for j, _ in enumerate(split):
             if j == 0:
                 add("k_pass_fwd_bits", 16 * L + bits, 2 * e * L + bits)

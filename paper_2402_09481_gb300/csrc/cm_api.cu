@@ -123,8 +123,10 @@ static void finish_plan(Plan *p, int fields, int min_lg, bool summed) {
         p->pass_lg[1] = rest / 2;
     }
     p->scratch_bytes = plan_scratch(p->lg, p->m, p->field, summed) + flag_bytes(p->kind);
-    // forward passes (both operands per launch), middle, inverse passes, pack
-    p->launches = p->npass == 0 ? 1 : p->npass + 1 + p->npass + 1;
+    p->cluster = p->field == kFieldF25 && !summed && p->lg >= kClusterMinLg && p->lg <= kClusterMaxLg;
+    // forward passes (both operands per launch), middle, inverse passes, pack;
+    // one launch on chip or on a cluster
+    p->launches = (p->npass == 0 || p->cluster) ? 1 : p->npass + 1 + p->npass + 1;
     if (p->kind == CM_DODIS) p->launches += 1;  // precondition check
 }
 
@@ -164,9 +166,12 @@ static const double kCostF30[kF30MaxLg + 1] = {
     0.02,  0.02,  0.02,  0.080, 0.081, 0.0822, 0.0829, 0.0857, 0.0950, 0.0991, 0.1162,
     0.1907, 0.3389, 0.6710, 1.3995, 2.6839, 5.4039, 10.960, 22.246, 45.643};
 static const double kCostF25[kF25MaxLg + 1] = {
-    0.02,   0.02,   0.02,   0.02,   0.02,   0.02,   0.02,   0.02,   0.02,   0.02,   0.02,
-    0.02,   0.02,   0.02,   0.0551, 0.0582, 0.0579, 0.0598, 0.0616, 0.0632, 0.0653, 0.0824,
+    0.0106, 0.0106, 0.0106, 0.0106, 0.0106, 0.0106, 0.0106, 0.0106, 0.0106, 0.0106, 0.0106,
+    0.0126, 0.0188, 0.0328, 0.0551, 0.0582, 0.0579, 0.0598, 0.0616, 0.0632, 0.0653, 0.0824,
     0.1060, 0.1668, 0.3264, 0.7317};
+// A product standing alone at 2^14 .. 2^17 runs as one cluster launch
+// (cm_cluster25.cu); L2 flushed before each call as above.
+static const double kCostCluster25[kClusterMaxLg - kClusterMinLg + 1] = {0.0312, 0.0309, 0.0312, 0.0333};
 static const double kCostGL[33] = {
     0.03,  0.03,  0.03,  0.03,  0.03,  0.03,  0.03,  0.03,  0.03,   0.03,   0.03,
     0.03,  0.03,  0.03,  0.130, 0.133, 0.1356, 0.1419, 0.1459, 0.1604, 0.1678, 0.2221,
@@ -187,6 +192,11 @@ static uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 static double plan_cost(int field, int lg) {
     return field == kFieldF25 ? kCostF25[lg] : field == kFieldF30 ? kCostF30[lg] : kCostGL[lg];
 }
+// A product that is not summed with others (its own inverse transform).
+static double alone_cost(int field, int lg) {
+    if (field == kFieldF25 && lg >= kClusterMinLg && lg <= kClusterMaxLg) return kCostCluster25[lg - kClusterMinLg];
+    return plan_cost(field, lg);
+}
 
 // Input blocks whose products one sum may hold: the counts of G blocks add up
 // to at most G Kb, which must stay below the field's characteristic (the
@@ -206,7 +216,7 @@ static uint64_t group_size(int field, uint64_t Kb, uint64_t nin, uint32_t cap) {
 static double window_cost(int field, int lg, uint64_t nin, uint64_t G) {
     const double t = plan_cost(field, lg);
     const uint64_t ng = ceil_div(nin, G);
-    if (G == 1) return (double)nin * t + (double)(nin - 1) * kXorMs;
+    if (G == 1) return (double)nin * alone_cost(field, lg) + (double)(nin - 1) * kXorMs;
     return ((double)(nin - ng) * kSumShare + (double)ng) * t + (double)(ng - 1) * kXorMs;
 }
 
@@ -395,7 +405,7 @@ double blocks_cost_ms(const std::vector<Block> &bl) {
             c += tail_cost(b.p.m);
             continue;
         }
-        const double t = plan_cost(b.p.field, b.p.lg);
+        const double t = b.sum == kSumNone ? alone_cost(b.p.field, b.p.lg) : plan_cost(b.p.field, b.p.lg);
         c += (b.sum == kSumFirst || b.sum == kSumInner) ? kSumShare * t : t;
         if (b.xor_into) c += kXorMs;
     }
@@ -418,6 +428,23 @@ static cm_status cuda_status(cudaError_t e) {
     return CM_EDEVICE;
 }
 
+// Whether the one-launch cluster kernel for 2^lg runs on this context's device
+// (attributes set and the cluster size checked on first use).
+static bool cluster25_ready(cm_ctx *ctx, int lg) {
+    std::atomic<int> &st = ctx->cluster25[lg - kClusterMinLg];
+    int v = st.load(std::memory_order_acquire);
+    if (v < 0) {
+        bool fits = false;
+        if (cluster25_prepare(lg, &fits) != cudaSuccess) {
+            cudaGetLastError();
+            fits = false;
+        }
+        v = fits ? 1 : 0;
+        st.store(v, std::memory_order_release);
+    }
+    return v == 1;
+}
+
 // Enqueue the product of plan p (no precondition check; pre: the Dodis et al.
 // flags the pack kernel reads, or null).  scratch holds p.scratch_bytes; sum
 // (SumMode) says whether the product stands alone or joins its window's sum.
@@ -432,6 +459,24 @@ static cm_status enqueue_product(cm_ctx *ctx, const Plan &p, const uint64_t *x, 
     auto kname = [&](const char *gl, const char *k30, const char *k25) { return f25 ? k25 : f30 ? k30 : gl; };
     cudaError_t e;
     uint8_t *sc = static_cast<uint8_t *>(scratch);
+    if (p.cluster && sum == kSumNone && cluster25_ready(ctx, p.lg)) {
+        Launch q;
+        q.amap = am;
+        q.bmap = bm;
+        q.lo = p.lo;
+        q.m = p.m;
+        q.linv = linv;
+        q.z = z;
+        q.pre = pre;
+        q.status = ctx->d_status;
+        q.field = p.field;
+        q.rt = ctx->rt;
+        q.rt30 = ctx->rt30;
+        q.rt25 = ctx->rt25;
+        q.stream = st;
+        ProfScope ps(ctx, "k_cluster_f25", st);
+        return cuda_status(launch_cluster25(q, p.lg));
+    }
     if (p.npass == 0) {
         Launch q;
         q.amap = am;
@@ -901,7 +946,7 @@ static uint32_t blocks_launches(const std::vector<Block> &bl) {
     for (const Block &b : bl) {
         const Plan &p = b.p;
         if (b.sum == kSumTail) c += 1;
-        else if (p.npass == 0) c += 1;
+        else if (p.npass == 0 || (p.cluster && b.sum == kSumNone)) c += 1;  // on chip or on a cluster
         else if (b.sum == kSumFirst || b.sum == kSumInner) c += p.npass + 1;  // forward + middle
         else c += p.npass + 1 + p.npass + 1;                                   // + inverse + pack
         if (b.xor_into && b.sum != kSumTail) c += 1;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -28,6 +29,8 @@ struct cm_ctx {
     uint32_t *d_tables25 = nullptr;
     cm::RootTables25 rt25{};
     cm_server *server = nullptr;
+    // one-launch cluster kernel per length 2^14 .. 2^17: -1 not yet checked, 0 no, 1 yes
+    std::atomic<int> cluster25[4] = {-1, -1, -1, -1};
 
     // per-kernel tracing (cm_profile_*): events around each launch when on
     struct ProfRec {

@@ -78,6 +78,12 @@ struct PassArgs {
 };
 
 cudaError_t launch_small(const Launch &q, int lg);
+// Whole F25 extraction for 2^14 <= L <= 2^17 on one cluster of L / 2^13 CTAs
+// (cm_cluster25.cu).  cluster25_prepare sets the kernel's attributes in the
+// current CUDA context and reports whether one such cluster fits the device.
+constexpr int kClusterMinLg = 14, kClusterMaxLg = 17;
+cudaError_t cluster25_prepare(int lg, bool *fits);
+cudaError_t launch_cluster25(const Launch &q, int lg);
 cudaError_t launch_pass(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_fwd(const PassArgs &a, int logr, cudaStream_t st);
 cudaError_t launch_pass_inv(const PassArgs &a, int logr, cudaStream_t st);
@@ -125,6 +131,7 @@ struct Plan {
     uint32_t launches;
     int field;       // kFieldGL, kFieldF30 or kFieldF25
     bool summed;     // one of several products summed before one inverse transform
+    bool cluster;    // one launch on a thread-block cluster (F25, 2^14 .. 2^17, alone)
 };
 
 // Which fields a plan may take (cm_options.field):
@@ -195,10 +202,10 @@ struct PlanOptions {
 };
 // PlanOptions from cm_options (NULL: defaults); false if a value is invalid.
 bool plan_options(const cm_options *opt, PlanOptions *o);
-// Batches and the server plan their instances like single calls restricted to
-// one transform of at most 2^25 for the work-list kernel (which runs every such
-// instance over F25 whatever the plan's field tag); longer ones go through the
-// single-call planner.
+// Batches and the server plan their instances like single calls, restricted
+// to one transform for the work-list kernel (which runs every such instance
+// over F25 whatever the plan's field tag); instances past the work list's
+// lengths go through the single-call planner.
 inline int worklist_fields(const PlanOptions &o) { return o.fields == kFieldsGL ? kFieldsGL : kFieldsQ30; }
 bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::vector<Block> *out);
 

@@ -74,10 +74,13 @@ def test_scratch_and_launches(lib):
     assert native.scratch_bytes(T, 100, 50) == 0          # one CTA, no scratch
     assert native.launch_count(T, 100, 50) == 1
     L = 2 ** 17
-    # two operands of L 32-bit elements, then the parity bytes
+    # two operands of L 32-bit elements, then the parity bytes (held for the
+    # column-pass form, which runs where the cluster kernel cannot)
     assert native.scratch_bytes(T, 2 ** 16, 2 ** 15) == 8 * L + 2 ** 15
-    # one forward pass (both operands), middle, inverse pass, pack
-    assert native.launch_count(T, 2 ** 16, 2 ** 15) == 4
+    # one launch on a thread-block cluster of 16 CTAs
+    assert native.launch_count(T, 2 ** 16, 2 ** 15) == 1
+    # a longer transform: one forward pass (both operands), middle, inverse pass, pack
+    assert native.launch_count(T, 2 ** 18, 2 ** 17) == 4
     # Dodis et al. at 2^30: precondition, then two summed products of two
     # column passes each: 2 x (2 fwd + middle) + 2 inv + pack
     assert native.launch_count(D, 1073741789, 429496715) == 1 + 2 * 3 + 3
