@@ -73,19 +73,6 @@ __device__ __forceinline__ void cl_or(uint32_t a, uint32_t v) {
     asm volatile("red.shared::cluster.or.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
-// The step root pairs of length 2^13 into shared memory by asynchronous
-// 16-byte copies (cp.async); the caller waits with cp_async_wait_all.
-__device__ __forceinline__ void prefetch_steps13(uint32_t *dst, const uint32_t *__restrict__ steps) {
-    constexpr int kVec = st25_smem_words(kMidLgMax) / 4;
-    static_assert(st25_smem_words(kMidLgMax) % 4 == 0, "whole 16-byte vectors");
-    const uint4 *src = reinterpret_cast<const uint4 *>(steps + 2 * kClM);  // pair 2^13: 16-byte aligned
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    for (int e = threadIdx.x; e < kVec; e += kThreads)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16u * e), "l"(src + e) : "memory");
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // OR run R (bit b = output bit s + b) into the cluster's output bitmap, bits
 // outside [0, m) dropped.  Output bit i is bit i & 31 of word (i >> 5) % kClBits
 // of CTA (i >> 5) / kClBits; bits0 is the bitmap's shared::cluster address in
@@ -128,7 +115,7 @@ k25_cluster(BitMap amap, BitMap bmap, uint64_t lo, uint64_t m, uint64_t linv, ui
     for (int p = 0; p < CL; ++p) base[p] = cl_mapa(base0, (uint32_t)p);
     const uint32_t bits0 = base0 + 4u * kClBitsOff;
 
-    prefetch_steps13(tw, rt.steps);  // needed from phase 2 on
+    prefetch_steps25<kMidLgMax>(tw, rt.steps);  // needed from phase 2 on
     for (int i = threadIdx.x; i < kClBits; i += kThreads) bits[i] = 0u;
     // cross-step roots: the powers of omega_L^j for this thread's columns
     for (int jj = threadIdx.x; jj < J; jj += kThreads) {

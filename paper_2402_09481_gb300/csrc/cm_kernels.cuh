@@ -40,6 +40,16 @@ namespace cm {
 // ---------------------------------------------------------------------------
 // Whole extraction on one CTA (L = 2^LG <= 2^13).
 // ---------------------------------------------------------------------------
+// Shared memory (words of F::T): both operands, then the roots (F25: the step
+// root pairs, 16-byte aligned for the asynchronous copy).
+template <class F, int LG>
+__host__ __device__ constexpr int small_tw_off() {
+    return F::kLazy ? (2 * sp_size(1 << LG) + 3) & ~3 : 2 * sp_size(1 << LG);
+}
+template <class F, int LG>
+__host__ __device__ constexpr int small_smem_words() {
+    return small_tw_off<F, LG>() + (F::kLazy ? st25_smem_words(LG) : (1 << LG));
+}
 template <class F, int LG>
 __global__ void __launch_bounds__(kThreads, 1)
 k_fused_small(BitMap amap, BitMap bmap, uint64_t lo, uint64_t m, uint64_t linv_,
@@ -51,15 +61,29 @@ k_fused_small(BitMap amap, BitMap bmap, uint64_t lo, uint64_t m, uint64_t linv_,
     extern __shared__ __align__(16) uint8_t smem_raw[];
     T *sA = reinterpret_cast<T *>(smem_raw);
     T *sB = sA + sp_size(L);
-    T *tw = sB + sp_size(L);
+    T *tw = sA + small_tw_off<F, LG>();
     if constexpr (F::kLazy)
-        load_steps25<LG>(tw, rt.steps);
+        prefetch_steps25<LG>(tw, rt.steps);  // lands while the operands unpack
     else
         load_roots<LG>(tw, rt.small);
-    for (int i = threadIdx.x; i < L; i += kThreads) {
-        sA[sp(i)] = (T)amap.get(i);
-        sB[sp(i)] = (T)bmap.get(i);
+    if constexpr (LG >= 5) {
+        // one run of 32 positions per thread, read as one or two words; thread
+        // t of a warp writes run t at sp(32 t + i), bank (t + i) mod 32
+        for (int u = threadIdx.x; u < 2 * (L / 32); u += kThreads) {
+            const int op = u >= L / 32 ? 1 : 0;
+            const int run = u - op * (L / 32);
+            const uint32_t b = op ? bmap.get_run<32>(32 * (uint64_t)run) : amap.get_run<32>(32 * (uint64_t)run);
+            T *dst = (op ? sB : sA) + sp(32 * run);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) dst[i] = (T)((b >> i) & 1u);
+        }
+    } else {
+        for (int i = threadIdx.x; i < L; i += kThreads) {
+            sA[sp(i)] = (T)amap.get(i);
+            sB[sp(i)] = (T)bmap.get(i);
+        }
     }
+    if constexpr (F::kLazy) cp_async_wait_all();
     __syncthreads();
     if constexpr (F::kLazy) {
         ntt_fwd25<LG, 0, 2>(sA, sB, tw);

@@ -8,9 +8,7 @@ namespace cm {
 
 template <class F, int LG>
 static cudaError_t launch_small_f(const Launch &q, const RootTablesT<typename F::T> &rt) {
-    // F25: the step roots are pairs (2 sp_size(L) is even: 8-byte aligned)
-    const size_t tw = F::kLazy ? st25_smem_words(LG) : (1 << LG);
-    const size_t sm = (2 * sp_size(1 << LG) + tw) * sizeof(typename F::T);
+    const size_t sm = (size_t)small_smem_words<F, LG>() * sizeof(typename F::T);
     auto kern = k_fused_small<F, LG>;
     cudaError_t e = smem_attr_once<k_fused_small<F, LG>>((int)sm);
     if (e != cudaSuccess) return e;

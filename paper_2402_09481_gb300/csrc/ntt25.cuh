@@ -59,6 +59,22 @@ __device__ __forceinline__ void load_steps25(uint32_t *dst, const uint32_t *__re
 // Shared-memory words of the step tables of length 2^LOGR.
 __host__ __device__ __forceinline__ constexpr int st25_smem_words(int logr) { return 2 * st25_tab_words(logr); }
 
+// The step tables of length 2^LOGR into shared memory at dst (16-byte
+// aligned) by asynchronous 16-byte copies (cp.async, sm_80 and later), so that
+// other work proceeds while they land; the issuing thread waits with
+// cp_async_wait_all(), then a barrier publishes them.  NT: the threads that copy.
+template <int LOGR, int NT = kThreads>
+__device__ __forceinline__ void prefetch_steps25(uint32_t *dst, const uint32_t *__restrict__ steps) {
+    constexpr int kVec = st25_smem_words(LOGR) / 4;  // pair counts are even: whole vectors
+    static_assert(st25_smem_words(LOGR) % 4 == 0, "whole 16-byte vectors");
+    const uint4 *src = reinterpret_cast<const uint4 *>(steps + 2 * (1 << LOGR));  // pair 2^LOGR
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    for (int e = threadIdx.x; e < kVec; e += NT)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16u * e), "l"(src + e) : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // x times the root pair r = (w, floor(w 2^32 / q)) -> [0, 2q), any 32-bit x.
 __device__ __forceinline__ uint32_t shoup_pair(uint32_t x, uint2 r) { return f25_shoup(x, r.x, r.y); }
 
