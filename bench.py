@@ -269,6 +269,11 @@ def kernel_model(products, m):
                 else:
                     add("k_pass_inv", 16 * L, 2 * e * L)
             add("k_pack", mr + mr / 8, mr + mr / 8)
+    if "k_tail" in tot and tot.get("k_pack", {}).get("launches") == 1 and tot.get("k_middle"):
+        # one window packed in place: the library folds the tail into that pack
+        t, pk = tot.pop("k_tail"), tot.pop("k_pack")
+        tot["k_pack_tail"] = {"bytes": t["bytes"] + pk["bytes"], "actual": t["actual"] + pk["actual"],
+                              "launches": 1}
     return tot
 
 

@@ -449,7 +449,8 @@ static bool cluster25_ready(cm_ctx *ctx, int lg) {
 // flags the pack kernel reads, or null).  scratch holds p.scratch_bytes; sum
 // (SumMode) says whether the product stands alone or joins its window's sum.
 static cm_status enqueue_product(cm_ctx *ctx, const Plan &p, const uint64_t *x, const uint64_t *y,
-                                 uint64_t *z, void *scratch, const uint32_t *pre, int sum, cudaStream_t st) {
+                                 uint64_t *z, void *scratch, const uint32_t *pre, int sum, cudaStream_t st,
+                                 const TailArgs *tail = nullptr) {
     const BitMap am = bitmap(x, p.amode, p.alen, p.asrclen, p.aoff);
     const BitMap bm = bitmap(y, p.bmode, p.blen, p.bsrclen, p.boff);
     const bool f30 = p.field == kFieldF30, f25 = p.field == kFieldF25;
@@ -559,6 +560,10 @@ static cm_status enqueue_product(cm_ctx *ctx, const Plan &p, const uint64_t *x, 
                                  : kname("k_pass_inv", "k_pass_inv_f30", "k_pass_inv_f25"), st);
         if ((e = launch_pass(a, p.pass_lg[j], st)) != cudaSuccess) return cuda_status(e);
     }
+    if (tail) {  // the extraction's dense tail joins the pack of its only window
+        ProfScope ps(ctx, "k_pack_tail", st);
+        return cuda_status(launch_pack_tail(par, p.m, z, pre, ctx->d_status, *tail, ctx->nsm, st));
+    }
     ProfScope ps(ctx, "k_pack", st);
     return cuda_status(launch_pack(par, p.m, z, pre, ctx->d_status, ctx->nsm, st));
 }
@@ -602,6 +607,20 @@ uint64_t blocks_scratch(const std::vector<Block> &bl, uint64_t *tmp_off, uint64_
     return dodis ? *pre_off + kFlagBytes : *tmp_off + 8 * tmpw;
 }
 
+// Index of the product whose pack also applies the dense tail: the last
+// product, when the list ends in a tail, every product writes the one window
+// in place (word 0, no XOR temporary) and the last one packs through the
+// column-pass form; else -1.
+static int tail_fold(const std::vector<Block> &bl) {
+    if (bl.size() < 2 || bl.back().sum != kSumTail) return -1;
+    for (size_t i = 0; i + 1 < bl.size(); ++i)
+        if (bl[i].zword != 0 || bl[i].xor_into) return -1;
+    const Block &last = bl[bl.size() - 2];
+    if (last.sum != kSumNone && last.sum != kSumLast) return -1;
+    if (last.p.npass == 0 || (last.p.cluster && last.sum == kSumNone)) return -1;  // packs on chip
+    return (int)bl.size() - 2;
+}
+
 // Enqueue every block of an extraction; scratch holds blocks_scratch() bytes.
 cm_status enqueue_blocks(cm_ctx *ctx, const std::vector<Block> &bl, const uint64_t *x, const uint64_t *y,
                          uint64_t *z, uint8_t *scratch, uint64_t tmp_off, uint64_t pre_off, cudaStream_t st) {
@@ -611,8 +630,22 @@ cm_status enqueue_blocks(cm_ctx *ctx, const std::vector<Block> &bl, const uint64
         cm_status s = enqueue_precondition(ctx, x, bl[0].p.n, pre, st);
         if (s != CM_OK) return s;
     }
-    for (const Block &b : bl) {
+    // A dense tail folds into the pack of the last product when the extraction
+    // has one output window written in place and that product runs the
+    // column-pass form (its pack is a separate launch).
+    const int fold = tail_fold(bl);
+    TailArgs ta{};
+    if (fold >= 0) {
+        const Plan &tp = bl.back().p;
+        ta.amap = bitmap(x, tp.amode, tp.alen, tp.asrclen, tp.aoff);
+        ta.bmap = bitmap(y, tp.bmode, tp.blen, tp.bsrclen, tp.boff);
+        ta.K = tp.K;
+        ta.T = bl.back().tail;
+    }
+    for (size_t i = 0; i < bl.size(); ++i) {
+        const Block &b = bl[i];
         if (b.sum == kSumTail) {
+            if (fold >= 0) continue;  // done by the pack
             const Plan &p = b.p;
             ProfScope ps(ctx, "k_tail", st);
             if (launch_tail(bitmap(x, p.amode, p.alen, p.asrclen, p.aoff), bitmap(y, p.bmode, p.blen, p.bsrclen, p.boff),
@@ -621,7 +654,8 @@ cm_status enqueue_blocks(cm_ctx *ctx, const std::vector<Block> &bl, const uint64
             continue;
         }
         uint64_t *dst = b.xor_into ? reinterpret_cast<uint64_t *>(scratch + tmp_off) : z + b.zword;
-        cm_status s = enqueue_product(ctx, b.p, x, y, dst, b.p.scratch_bytes ? scratch : nullptr, pre, b.sum, st);
+        cm_status s = enqueue_product(ctx, b.p, x, y, dst, b.p.scratch_bytes ? scratch : nullptr, pre, b.sum, st,
+                                      (int)i == fold ? &ta : nullptr);
         if (s != CM_OK) return s;
         if (b.xor_into) {
             ProfScope ps(ctx, "k_xor_into", st);
@@ -943,9 +977,10 @@ extern "C" cm_status cm_device_status(cm_ctx *ctx, cm_stream stream, uint32_t *f
 
 static uint32_t blocks_launches(const std::vector<Block> &bl) {
     uint32_t c = (!bl.empty() && bl[0].p.kind == CM_DODIS) ? 1 : 0;  // precondition, once
+    const bool folded = tail_fold(bl) >= 0;
     for (const Block &b : bl) {
         const Plan &p = b.p;
-        if (b.sum == kSumTail) c += 1;
+        if (b.sum == kSumTail) c += folded ? 0 : 1;
         else if (p.npass == 0 || (p.cluster && b.sum == kSumNone)) c += 1;  // on chip or on a cluster
         else if (b.sum == kSumFirst || b.sum == kSumInner) c += p.npass + 1;  // forward + middle
         else c += p.npass + 1 + p.npass + 1;                                   // + inverse + pack

@@ -112,6 +112,17 @@ cudaError_t launch_allsame(const uint64_t *x, uint64_t n, uint32_t *flags, int n
 constexpr int kTailMax = 256;
 cudaError_t launch_tail(const BitMap &amap, const BitMap &bmap, uint64_t K, uint32_t T, uint64_t m, uint64_t *z,
                         const uint32_t *pre, int nsm, cudaStream_t st);
+// The dense tail of a one-window extraction, folded into the window's pack.
+struct TailArgs {
+    BitMap amap, bmap;
+    uint64_t K;
+    uint32_t T;
+};
+// launch_pack and launch_tail in one kernel: z = pack(par) ^ tail, words
+// past m written 0, z zero (and the status flag set) for a constant Dodis et
+// al. x.
+cudaError_t launch_pack_tail(const uint8_t *par, uint64_t m, uint64_t *z, const uint32_t *pre, uint32_t *status,
+                             const TailArgs &t, int nsm, cudaStream_t st);
 
 // The plan of one extraction: the middle-product form of the extractor and the
 // pass split of its transform.

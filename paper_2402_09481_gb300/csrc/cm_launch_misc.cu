@@ -202,13 +202,16 @@ k_tail(BitMap amap, BitMap bmap, uint64_t K, uint32_t T, uint64_t m, uint64_t *_
             const uint64_t v = (w << 6) + 64 * q;
             W[q] = (uint64_t)bmap.get_run<32>(v) | ((uint64_t)bmap.get_run<32>(v + 32) << 32);
         }
-        uint64_t acc = 0;
+        // four independent accumulators (terms t mod 4): no serial chain of
+        // dependent XORs; the tail bits are the same in every thread, so the
+        // branches do not diverge
+        uint64_t acc4[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int t = 0; t < 64 * NW; ++t) {
             const int q = t >> 6, s = t & 63;
-            const uint64_t run = s ? (W[q] >> s) | (W[q + 1] << (64 - s)) : W[q];
-            if ((al[q] >> s) & 1ull) acc ^= run;
+            if ((al[q] >> s) & 1ull) acc4[t & 3] ^= s ? (W[q] >> s) | (W[q + 1] << (64 - s)) : W[q];
         }
+        uint64_t acc = (acc4[0] ^ acc4[1]) ^ (acc4[2] ^ acc4[3]);
         if (w == nwords - 1 && (m & 63)) acc &= (1ull << (m & 63)) - 1;
         z[w] ^= acc;
     }
@@ -227,6 +230,82 @@ cudaError_t launch_tail(const BitMap &amap, const BitMap &bmap, uint64_t K, uint
         case 2: k_tail<2><<<(unsigned)blocks, kTailThreads, 0, st>>>(amap, bmap, K, T, m, z, pre); break;
         case 3: k_tail<3><<<(unsigned)blocks, kTailThreads, 0, st>>>(amap, bmap, K, T, m, z, pre); break;
         default: k_tail<4><<<(unsigned)blocks, kTailThreads, 0, st>>>(amap, bmap, K, T, m, z, pre); break;
+    }
+    return cudaGetLastError();
+}
+
+// k_pack and k_tail in one pass: one thread per output word packs its 64
+// parity bytes (four 16-byte loads when the word lies below m) and XORs in
+// the tail terms, computed as in k_tail.
+template <int NW>
+__global__ void __launch_bounds__(kTailThreads)
+k_pack_tail(const uint8_t *__restrict__ par, uint64_t m, uint64_t *__restrict__ z, const uint32_t *__restrict__ pre,
+            uint32_t *__restrict__ status, BitMap amap, BitMap bmap, uint64_t K, uint32_t T) {
+    const bool bad = pre && (pre[0] == 0u || pre[1] == 0u);
+    if (bad && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kFlagPrecond);
+    __shared__ uint32_t sal[kTailMax / 32];
+    {
+        const int t = threadIdx.x;  // one tail position per thread
+        const uint32_t bit = (uint32_t)t < T ? (uint32_t)amap.get(K - 1 - (uint64_t)t) : 0u;
+        const uint32_t w = __ballot_sync(0xffffffffu, bit);
+        if ((t & 31) == 0) sal[t >> 5] = w;
+    }
+    __syncthreads();
+    uint64_t al[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) al[q] = (uint64_t)sal[2 * q] | ((uint64_t)sal[2 * q + 1] << 32);
+    const bool vec = (reinterpret_cast<uintptr_t>(par) & 15) == 0;
+    const uint64_t nwords = (m + 63) >> 6;
+    for (uint64_t w = (uint64_t)blockIdx.x * kTailThreads + threadIdx.x; w < nwords;
+         w += (uint64_t)gridDim.x * kTailThreads) {
+        uint64_t W[NW + 1];  // seed bits 64 w .. 64 w + 64 (NW + 1) - 1
+#pragma unroll
+        for (int q = 0; q <= NW; ++q) {
+            const uint64_t v = (w << 6) + 64 * q;
+            W[q] = (uint64_t)bmap.get_run<32>(v) | ((uint64_t)bmap.get_run<32>(v + 32) << 32);
+        }
+        uint64_t packed = 0;
+        if (vec && (w << 6) + 64 <= m) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(par + (w << 6));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint4 v = __ldg(src + k);
+                const uint64_t u = ((v.x * 0x01020408u) >> 24) | (((v.y * 0x01020408u) >> 24) << 4) |
+                                   (((v.z * 0x01020408u) >> 24) << 8) | (((v.w * 0x01020408u) >> 24) << 12);
+                packed |= u << (16 * k);
+            }
+        } else {
+            for (int b = 0; b < 64; ++b) {
+                const uint64_t p = (w << 6) + b;
+                if (p < m) packed |= (uint64_t)(par[p] & 1u) << b;
+            }
+        }
+        uint64_t acc4[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int t = 0; t < 64 * NW; ++t) {
+            const int q = t >> 6, s = t & 63;
+            if ((al[q] >> s) & 1ull) acc4[t & 3] ^= s ? (W[q] >> s) | (W[q + 1] << (64 - s)) : W[q];
+        }
+        uint64_t acc = packed ^ (acc4[0] ^ acc4[1]) ^ (acc4[2] ^ acc4[3]);
+        if (w == nwords - 1 && (m & 63)) acc &= (1ull << (m & 63)) - 1;
+        z[w] = bad ? 0ull : acc;
+    }
+}
+
+cudaError_t launch_pack_tail(const uint8_t *par, uint64_t m, uint64_t *z, const uint32_t *pre, uint32_t *status,
+                             const TailArgs &a, int nsm, cudaStream_t st) {
+    if (a.T == 0 || a.T > (uint32_t)kTailMax || a.T > a.K) return cudaErrorInvalidValue;
+    const uint64_t nwords = (m + 63) >> 6;
+    uint64_t blocks = (nwords + kTailThreads - 1) / kTailThreads;
+    const uint64_t cap = (uint64_t)nsm * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) blocks = 1;
+    const dim3 g((unsigned)blocks), t(kTailThreads);
+    switch ((a.T + 63) / 64) {
+        case 1: k_pack_tail<1><<<g, t, 0, st>>>(par, m, z, pre, status, a.amap, a.bmap, a.K, a.T); break;
+        case 2: k_pack_tail<2><<<g, t, 0, st>>>(par, m, z, pre, status, a.amap, a.bmap, a.K, a.T); break;
+        case 3: k_pack_tail<3><<<g, t, 0, st>>>(par, m, z, pre, status, a.amap, a.bmap, a.K, a.T); break;
+        default: k_pack_tail<4><<<g, t, 0, st>>>(par, m, z, pre, status, a.amap, a.bmap, a.K, a.T); break;
     }
     return cudaGetLastError();
 }

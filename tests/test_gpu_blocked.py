@@ -173,6 +173,41 @@ def test_dense_tail_dodis_precondition(ctxs):
         assert ctxs[15].device_status()[0] == native.CM_EPRECOND
 
 
+FOLD_CASES = [
+    # (kind, n, m): two summed 2^14 products and a dense tail in one window:
+    # the tail runs inside the window's pack (71 and 241 terms)
+    (C, 16_420, 8_210),
+    (D, 17_011, 8_000),
+]
+
+
+@pytest.mark.parametrize("kind,n,m", FOLD_CASES)
+def test_tail_folded_into_pack(kind, n, m):
+    ctx = native.Context(0, max_transform_lg=14)
+    try:
+        info = native.plan_query(kind, n, m, max_transform_lg=14)
+        assert info["products"] == 2 and info["windows"] == 1 and info["tail_terms"] > 0
+        xw = inputs.bernoulli_half(80 + n % 7, n)
+        if kind == D:
+            xw[0] = (xw[0] | np.uint64(1)) & ~np.uint64(2)
+        yw = inputs.bernoulli_half(81 + n % 5, ybits(kind, n, m))
+        ctx.profile_enable(True)
+        ctx.profile_read(reset=True)
+        z = run(ctx, kind, n, m, xw, yw)
+        prof = ctx.profile_read(reset=True)
+        ctx.profile_enable(False)
+        assert "k_pack_tail" in prof and "k_tail" not in prof and "k_pack" not in prof, prof
+        assert sum(c for c, _ in prof.values()) == info["launches"]
+        assert (z == want(kind, n, m, xw, yw)).all()
+        if kind == D:  # a constant source still zeroes the output
+            for fill in (0, 1):
+                got = run(ctx, D, n, m, ex.pack_bits(np.full(n, fill, dtype=np.uint8)), yw)
+                assert not got.any()
+                assert ctx.device_status()[0] == native.CM_EPRECOND
+    finally:
+        ctx.close()
+
+
 FUSED_CASES = [
     # (kind, n, m, max_transform_lg, max_sum_blocks): products of 2^22 .. 2^25
     # over q = 5 * 2^25 + 1 run the fused column passes (tiles of 2^9 .. 2^12
