@@ -234,38 +234,27 @@ cudaError_t launch_tail(const BitMap &amap, const BitMap &bmap, uint64_t K, uint
     return cudaGetLastError();
 }
 
-// k_pack and k_tail in one pass: one thread per output word packs its 64
-// parity bytes (four 16-byte loads when the word lies below m) and XORs in
-// the tail terms, computed as in k_tail.
+// k_pack and k_tail in one pass: one thread per output word (the grid covers
+// every word) packs its 64 parity bytes (four 16-byte loads when the word lies
+// below m) and XORs in the tail terms, computed as in k_tail.
 template <int NW>
 __global__ void __launch_bounds__(kTailThreads)
 k_pack_tail(const uint8_t *__restrict__ par, uint64_t m, uint64_t *__restrict__ z, const uint32_t *__restrict__ pre,
             uint32_t *__restrict__ status, BitMap amap, BitMap bmap, uint64_t K, uint32_t T) {
-    const bool bad = pre && (pre[0] == 0u || pre[1] == 0u);
-    if (bad && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kFlagPrecond);
     __shared__ uint32_t sal[kTailMax / 32];
-    {
-        const int t = threadIdx.x;  // one tail position per thread
-        const uint32_t bit = (uint32_t)t < T ? (uint32_t)amap.get(K - 1 - (uint64_t)t) : 0u;
-        const uint32_t w = __ballot_sync(0xffffffffu, bit);
-        if ((t & 31) == 0) sal[t >> 5] = w;
-    }
-    __syncthreads();
-    uint64_t al[NW];
-#pragma unroll
-    for (int q = 0; q < NW; ++q) al[q] = (uint64_t)sal[2 * q] | ((uint64_t)sal[2 * q + 1] << 32);
-    const bool vec = (reinterpret_cast<uintptr_t>(par) & 15) == 0;
     const uint64_t nwords = (m + 63) >> 6;
-    for (uint64_t w = (uint64_t)blockIdx.x * kTailThreads + threadIdx.x; w < nwords;
-         w += (uint64_t)gridDim.x * kTailThreads) {
-        uint64_t W[NW + 1];  // seed bits 64 w .. 64 w + 64 (NW + 1) - 1
+    const uint64_t w = (uint64_t)blockIdx.x * kTailThreads + threadIdx.x;  // one word a thread (grid covers m)
+    // this word's seed bits and parity bytes first: their loads overlap the
+    // gather of the tail bits below
+    uint64_t W[NW + 1];  // seed bits 64 w .. 64 w + 64 (NW + 1) - 1
+    uint64_t packed = 0;
+    if (w < nwords) {
 #pragma unroll
         for (int q = 0; q <= NW; ++q) {
             const uint64_t v = (w << 6) + 64 * q;
             W[q] = (uint64_t)bmap.get_run<32>(v) | ((uint64_t)bmap.get_run<32>(v + 32) << 32);
         }
-        uint64_t packed = 0;
-        if (vec && (w << 6) + 64 <= m) {
+        if ((reinterpret_cast<uintptr_t>(par) & 15) == 0 && (w << 6) + 64 <= m) {
             const uint4 *src = reinterpret_cast<const uint4 *>(par + (w << 6));
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -280,26 +269,41 @@ k_pack_tail(const uint8_t *__restrict__ par, uint64_t m, uint64_t *__restrict__ 
                 if (p < m) packed |= (uint64_t)(par[p] & 1u) << b;
             }
         }
-        uint64_t acc4[4] = {0, 0, 0, 0};
+    } else {
 #pragma unroll
-        for (int t = 0; t < 64 * NW; ++t) {
-            const int q = t >> 6, s = t & 63;
-            if ((al[q] >> s) & 1ull) acc4[t & 3] ^= s ? (W[q] >> s) | (W[q + 1] << (64 - s)) : W[q];
-        }
-        uint64_t acc = packed ^ (acc4[0] ^ acc4[1]) ^ (acc4[2] ^ acc4[3]);
-        if (w == nwords - 1 && (m & 63)) acc &= (1ull << (m & 63)) - 1;
-        z[w] = bad ? 0ull : acc;
+        for (int q = 0; q <= NW; ++q) W[q] = 0;
     }
+    {
+        const int t = threadIdx.x;  // one tail position per thread
+        const uint32_t bit = (uint32_t)t < T ? (uint32_t)amap.get(K - 1 - (uint64_t)t) : 0u;
+        const uint32_t b = __ballot_sync(0xffffffffu, bit);
+        if ((t & 31) == 0) sal[t >> 5] = b;
+    }
+    const bool bad = pre && (pre[0] == 0u || pre[1] == 0u);
+    if (bad && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kFlagPrecond);
+    __syncthreads();
+    if (w >= nwords) return;
+    uint64_t al[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) al[q] = (uint64_t)sal[2 * q] | ((uint64_t)sal[2 * q + 1] << 32);
+    uint64_t acc4[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int t = 0; t < 64 * NW; ++t) {
+        const int q = t >> 6, s = t & 63;
+        if ((al[q] >> s) & 1ull) acc4[t & 3] ^= s ? (W[q] >> s) | (W[q + 1] << (64 - s)) : W[q];
+    }
+    uint64_t acc = packed ^ (acc4[0] ^ acc4[1]) ^ (acc4[2] ^ acc4[3]);
+    if (w == nwords - 1 && (m & 63)) acc &= (1ull << (m & 63)) - 1;
+    z[w] = bad ? 0ull : acc;
 }
 
 cudaError_t launch_pack_tail(const uint8_t *par, uint64_t m, uint64_t *z, const uint32_t *pre, uint32_t *status,
                              const TailArgs &a, int nsm, cudaStream_t st) {
     if (a.T == 0 || a.T > (uint32_t)kTailMax || a.T > a.K) return cudaErrorInvalidValue;
     const uint64_t nwords = (m + 63) >> 6;
-    uint64_t blocks = (nwords + kTailThreads - 1) / kTailThreads;
-    const uint64_t cap = (uint64_t)nsm * 8;
-    if (blocks > cap) blocks = cap;
-    if (blocks == 0) blocks = 1;
+    const uint64_t blocks = (nwords + kTailThreads - 1) / kTailThreads;  // one word a thread
+    if (blocks == 0 || blocks > 0x7fffffffull) return cudaErrorInvalidValue;
+    (void)nsm;
     const dim3 g((unsigned)blocks), t(kTailThreads);
     switch ((a.T + 63) / 64) {
         case 1: k_pack_tail<1><<<g, t, 0, st>>>(par, m, z, pre, status, a.amap, a.bmap, a.K, a.T); break;

@@ -63,6 +63,12 @@ struct Pass25 {
     static_assert(W_FWD * 4 <= 113 * 1024, "two CTAs per SM");
 };
 
+// Bulk prefetch of `bytes` (a multiple of 16) at a 16-byte aligned global
+// address into L2 (cp.async.bulk.prefetch, sm_90 and later; no completion).
+__device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <int LOGR>
 __device__ __forceinline__ int tile_at(int e) {
     using PS = Pass25<LOGR>;
@@ -288,6 +294,15 @@ k25_middle(uint32_t *__restrict__ A, const uint32_t *__restrict__ Bv, uint32_t *
     uint32_t *mont0 = reinterpret_cast<uint32_t *>(pairs1 + kMid1Pairs);  // kMid0Words
     uint32_t *sA = mont0 + kMid0Words;
     uint32_t *sB = sA + sp_size(Bn);
+    // rows r, r + grid, ... of both operands (and of the accumulator when it
+    // is read), into L2 one row ahead; the first while the tables load
+    auto prefetch_row = [&](uint32_t r) {
+        const uint32_t at = r << kMidLgMax;
+        l2_prefetch(A + at, sizeof(uint32_t) << kMidLgMax);
+        l2_prefetch(Bv + at, sizeof(uint32_t) << kMidLgMax);
+        if (mode == kMidInner || mode == kMidLast) l2_prefetch(Cacc + at, sizeof(uint32_t) << kMidLgMax);
+    };
+    if (threadIdx.x == 0 && blockIdx.x < nrows) prefetch_row(blockIdx.x);
     {
         const uint2 *src = reinterpret_cast<const uint2 *>(rt.steps) + (1 << 13) + kMid0Words;
         for (int i = threadIdx.x; i < kMid1Pairs; i += kThreads) pairs1[i] = __ldg(src + i);
@@ -307,6 +322,7 @@ k25_middle(uint32_t *__restrict__ A, const uint32_t *__restrict__ Bv, uint32_t *
     constexpr int STRIDE0 = 256 + 8;  // sp(i2 + 256 k) - sp(i2)
     for (uint32_t r = blockIdx.x; r < nrows; r += gridDim.x) {
         const uint32_t row = r << kMidLgMax;
+        if (t == 0 && r + gridDim.x < nrows) prefetch_row(r + gridDim.x);  // asynchronous: nothing waits
         {
             // step 0: threads 0 .. 255 take A, 256 .. 511 take B
             uint32_t v[32];
