@@ -242,6 +242,7 @@ struct WaveReq {
     Plan p;
     std::vector<Block> blocks;
     uint64_t tmp_off = 0, pre_off = 0;
+    bool solo = false;  // runs the single-call kernels (blocks) even where the work list could take it
 };
 struct Wave {
     std::vector<WaveReq> r;
@@ -304,6 +305,22 @@ bool admit_wave(cm_server *S, Slot &sl, Wave &w) {
         w.r[i].blocks = r.blocks;
         w.r[i].tmp_off = r.tmp_off;
         w.r[i].pre_off = r.pre_off;
+        w.r[i].solo = !on_worklist(r.p);
+        if (n == 1 && on_worklist(r.p) && !(r.flags & CM_REQ_SEED_CACHE)) {
+            // a wave of one: the single call's kernels (one to a few launches)
+            // instead of building and uploading a work list, within the same
+            // footprint
+            PlanOptions po = S->ctx->popt;
+            po.budget = S->budget;
+            std::vector<Block> bl;
+            uint64_t to = 0, pf = 0;
+            if (make_blocks(r.d.kind, r.d.n, r.d.m, po, &bl) && r256(blocks_scratch(bl, &to, &pf)) + 256 <= r.foot) {
+                w.r[i].blocks.swap(bl);
+                w.r[i].tmp_off = to;
+                w.r[i].pre_off = pf;
+                w.r[i].solo = true;
+            }
+        }
         // resident seed transforms (work-list requests with one column pass)
         if (!(r.flags & CM_REQ_SEED_CACHE) || !on_worklist(r.p) || r.p.npass != 1) continue;
         const SeedKey key{r.seed_id, r.p.n, r.p.m, r.p.kind};
@@ -424,7 +441,7 @@ cm_status launch_wave(cm_server *S, Slot &sl, Wave &w) {
     for (uint32_t i = 0; i < n; ++i) {
         const WaveReq &r = w.r[i];
         off[i] = total;
-        if (on_worklist(r.p)) {
+        if (!r.solo) {
             wl.push_back(i);
             total += worklist_scratch_bytes(r.p);
         } else {

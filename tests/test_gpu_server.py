@@ -138,13 +138,15 @@ def test_server_admission_by_footprint(sctx, cm_ctx):
 
 
 def test_server_queue_full_poll_timeout_unknown(sctx):
-    a = make(T, 2 ** 24, 2 ** 24, 41)     # L = 2^25: about 0.25 GiB of scratch
-    b = make(T, 2 ** 24, 2 ** 24, 43)
+    a = make(T, 2 ** 25, 2 ** 25, 41)     # L = 2^26: about 0.5 GiB of scratch, over a millisecond
+    b = make(T, 2 ** 25, 2 ** 25, 43)
     c = make(T, 1000, 500, 45)
-    foot = 8 * 2 ** 25 + 2 ** 24 + 4096   # room for one of them
+    one = native.plan_query(T, 2 ** 25, 2 ** 25)["scratch_bytes"]
+    foot = one + 4096                     # room for one of them (the planner keeps one product)
+    assert native.plan_query(T, 2 ** 25, 2 ** 25, hbm_budget_bytes=foot)["scratch_bytes"] == one
     sctx.server_start(hbm_budget_bytes=foot, slots=2, max_queue=1)
     ta = submit(sctx, a)                  # admitted at once
-    time.sleep(0.001)
+    time.sleep(0.0005)
     tb = submit(sctx, b)                  # waits for a's memory: the queue holds it
     s, _ = sctx.submit_raw(T, c["n"], c["m"], c["x"].data_ptr(), c["y"].data_ptr(), c["z"].data_ptr())
     assert s == native.CM_EAGAIN          # queue full
