@@ -1478,6 +1478,11 @@ def run_single(args, world, rank, local, dist):
     L = plan["transform_length"]
     launches = plan["launches"]
     ctx = native.Context(local, field=fopt)
+    tune_cache = os.environ.get("CM_TUNE_CACHE")
+    if tune_cache:
+        # the planner's figures timed on this GPU (or loaded from the cache);
+        # the plan keys below stay the built-in planner's
+        ctx.calibrate(tune_cache)
     stream = torch.cuda.current_stream()
 
     xw = inputs.bernoulli_half(1 + 1000 * rank, n)
@@ -1619,6 +1624,7 @@ def run_single(args, world, rank, local, dist):
                             "transform_length": L, "field": FIELD_NAMES.get(pf, pf),
                             "tail_terms": plan["tail_terms"], "planner_estimate_ms": plan["est_ms"]},
                    "l2": "flushed between timed steps (256 MiB write)",
+                   **({"calibrated_planner": os.environ.get("CM_TUNE_CACHE")} if os.environ.get("CM_TUNE_CACHE") else {}),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "latency_ms": {"p50": statistics.median(step_ms),
                        "p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},

@@ -514,6 +514,35 @@ typedef struct {
 cm_status cm_plan_products(int kind, uint64_t n, uint64_t m, const cm_options *opt, cm_product_desc *out,
                            uint64_t cap, uint64_t *count);
 
+/*
+ * Planner calibration on this context's GPU (the paper has no counterpart;
+ * the planner's cost model is this library's).  Times one Toeplitz extraction
+ * per transform length and field (K = L/2 + 1, m = L/4; one warm-up, the
+ * median of three, L2 flushed before each): 5 * 2^25 + 1 over 2^9 .. 2^25
+ * (2^14 .. 2^17 also as one cluster launch), 3 * 2^30 + 1 and Goldilocks from
+ * 2^14, each up to max_lg (0: 2^30) and within the context's HBM budget; for
+ * two-pass lengths it also picks the first column pass's length among the
+ * default split and its two neighbours.  The figures replace the built-in
+ * ones in this context's planner (single calls, batches, the server; not
+ * cm_plan_query, which has no context).  cache_path (may be NULL): a text
+ * file keyed by the device's name and SM count; when it exists and matches,
+ * its figures are loaded instead of measured (unless flags has
+ * CM_TUNE_FORCE), otherwise the new figures are written to it.  Runs
+ * synchronously (seconds) and must not overlap other calls on the context.
+ * CM_EINVAL for bad arguments or an unwritable cache file (the figures are in
+ * force regardless), CM_ENOMEM, CM_EDEVICE.
+ */
+#define CM_TUNE_FORCE 0x1u
+cm_status cm_calibrate(cm_ctx *ctx, const char *cache_path, uint32_t flags, uint32_t max_lg);
+
+/* The calibrated figures of a context for field (CM_FIELD_GOLDILOCKS,
+ * CM_FIELD_Q30, CM_FIELD_Q25) and transform length 2^lg: *ms the
+ * column-pass form's time, *cluster_ms the cluster form's (5 * 2^25 + 1,
+ * 2^14 .. 2^17), *split the first pass's log2 R of a two-pass plan; 0 where
+ * none was taken (any pointer may be NULL).  CM_EINVAL for bad arguments. */
+cm_status cm_tune_query(const cm_ctx *ctx, uint32_t field, uint32_t lg, double *ms, double *cluster_ms,
+                        int32_t *split);
+
 /* Transform length of the longest product of (kind, n, m) with default
  * options (cm_plan_query); 0 if the arguments are invalid for that kind. */
 uint64_t cm_ntt_length(int kind, uint64_t n, uint64_t m);

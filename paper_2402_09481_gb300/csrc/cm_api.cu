@@ -102,7 +102,7 @@ static uint64_t plan_scratch(int lg, uint64_t m, int field, bool summed) {
 
 // Transform length (at least 2^min_lg), field, pass split, scratch and launch
 // count for K + m - 1 <= 2^32.
-static void finish_plan(Plan *p, int fields, int min_lg, bool summed) {
+static void finish_plan(Plan *p, int fields, int min_lg, bool summed, const Tuning *tune = nullptr) {
     const uint64_t need = p->K + p->m - 1;
     p->lg = ceil_log2(need);
     if (p->lg < min_lg) p->lg = min_lg;
@@ -120,7 +120,9 @@ static void finish_plan(Plan *p, int fields, int min_lg, bool summed) {
     } else {
         p->npass = 2;
         p->pass_lg[0] = (rest + 1) / 2;
-        p->pass_lg[1] = rest / 2;
+        const int f = tune ? tune->split[p->field][p->lg] : 0;  // a calibrated split, if valid
+        if (f >= 1 && f <= 12 && rest - f >= 1 && rest - f <= 12) p->pass_lg[0] = f;
+        p->pass_lg[1] = rest - p->pass_lg[0];
     }
     p->scratch_bytes = plan_scratch(p->lg, p->m, p->field, summed) + flag_bytes(p->kind);
     p->cluster = p->field == kFieldF25 && !summed && p->lg >= kClusterMinLg && p->lg <= kClusterMaxLg;
@@ -130,10 +132,10 @@ static void finish_plan(Plan *p, int fields, int min_lg, bool summed) {
     if (p->kind == CM_DODIS) p->launches += 1;  // precondition check
 }
 
-bool make_plan(int kind, uint64_t n, uint64_t m, Plan *p, int fields) {
+bool make_plan(int kind, uint64_t n, uint64_t m, Plan *p, int fields, const Tuning *tune) {
     if (!base_maps(kind, n, m, p)) return false;
     if (p->K + m - 1 > (1ull << 32)) return false;
-    finish_plan(p, fields, 1, false);
+    finish_plan(p, fields, 1, false, tune);
     return true;
 }
 
@@ -189,13 +191,17 @@ constexpr int kSumMinLg = kMidLgMax + 1;  // summed windows need a column pass
 static uint64_t words_of(uint64_t bits) { return (bits + 63) / 64; }
 static uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 
-static double plan_cost(int field, int lg) {
+static double plan_cost(int field, int lg, const Tuning *tune = nullptr) {
+    if (tune && tune->cost[field][lg] > 0) return tune->cost[field][lg];
     return field == kFieldF25 ? kCostF25[lg] : field == kFieldF30 ? kCostF30[lg] : kCostGL[lg];
 }
 // A product that is not summed with others (its own inverse transform).
-static double alone_cost(int field, int lg) {
-    if (field == kFieldF25 && lg >= kClusterMinLg && lg <= kClusterMaxLg) return kCostCluster25[lg - kClusterMinLg];
-    return plan_cost(field, lg);
+static double alone_cost(int field, int lg, const Tuning *tune = nullptr) {
+    if (field == kFieldF25 && lg >= kClusterMinLg && lg <= kClusterMaxLg) {
+        if (tune && tune->cluster[lg - kClusterMinLg] > 0) return tune->cluster[lg - kClusterMinLg];
+        return kCostCluster25[lg - kClusterMinLg];
+    }
+    return plan_cost(field, lg, tune);
 }
 
 // Input blocks whose products one sum may hold: the counts of G blocks add up
@@ -213,10 +219,10 @@ static uint64_t group_size(int field, uint64_t Kb, uint64_t nin, uint32_t cap) {
 // inverse-transformed on its own and XORed): a group's last block costs a
 // whole extraction, the others their forward passes and the middle without
 // its inverse row transform.
-static double window_cost(int field, int lg, uint64_t nin, uint64_t G) {
-    const double t = plan_cost(field, lg);
+static double window_cost(int field, int lg, uint64_t nin, uint64_t G, const Tuning *tune) {
+    const double t = plan_cost(field, lg, tune);
     const uint64_t ng = ceil_div(nin, G);
-    if (G == 1) return (double)nin * alone_cost(field, lg) + (double)(nin - 1) * kXorMs;
+    if (G == 1) return (double)nin * alone_cost(field, lg, tune) + (double)(nin - 1) * kXorMs;
     return ((double)(nin - ng) * kSumShare + (double)ng) * t + (double)(ng - 1) * kXorMs;
 }
 
@@ -240,7 +246,7 @@ static int window_lg(const Shape &s, uint64_t mr) {
     return lg < 1 ? 1 : lg;
 }
 
-static void evaluate(int kind, uint64_t m, int fields, uint32_t max_sum, Shape *s) {
+static void evaluate(int kind, uint64_t m, int fields, uint32_t max_sum, const Tuning *tune, Shape *s) {
     const uint64_t mlast = m - (s->nout - 1) * s->Mb;
     s->cost = 0;
     s->scratch = 0;
@@ -251,7 +257,7 @@ static void evaluate(int kind, uint64_t m, int fields, uint32_t max_sum, Shape *
         const int lg = window_lg(*s, mr);
         const int field = field_for(fields, lg);
         const uint64_t G = s->summed ? group_size(field, s->Kb, s->nin, max_sum) : 1;
-        s->cost += (double)cnt * window_cost(field, lg, s->nin, G);
+        s->cost += (double)cnt * window_cost(field, lg, s->nin, G, tune);
         const uint64_t sc = plan_scratch(lg, mr, field, s->summed);
         if (sc > s->scratch) s->scratch = sc;
         xors = xors || G < s->nin;
@@ -335,7 +341,7 @@ bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::ve
                 if (c.nin > kMaxBlocks / c.nout) continue;  // (no overflow: both <= 2^40)
                 c.Kb = ceil_div(K - c.tail, c.nin);
                 c.summed = c.nin > 1 && max_lg > kMidLgMax;
-                evaluate(kind, m, fields, o.max_sum, &c);
+                evaluate(kind, m, fields, o.max_sum, o.tune, &c);
                 const bool single = c.nin == 1 && c.nout == 1 && c.tail == 0;
                 const bool fits = budget == 0 || c.scratch <= budget;
                 double cc = c.cost, bc = best.cost;
@@ -355,7 +361,7 @@ bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::ve
     if (!have) return false;
     const Shape &s = best;
     if (s.nin == 1 && s.nout == 1 && s.tail == 0) {
-        finish_plan(&b, fields, 1, false);
+        finish_plan(&b, fields, 1, false, o.tune);
         out->push_back({b, 0, kSumNone, false, 0});
         return true;
     }
@@ -382,7 +388,7 @@ bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::ve
             // B'_v = B_{v + T0 + I0 - (Kb - kb)}, kept in [0, bsrclen)
             const uint64_t src = b.bsrclen;
             q.boff = ((b.boff + T0 + I0) % src + src - (s.Kb - kb) % src) % src;
-            finish_plan(&q, fields, lg_r, s.summed);
+            finish_plan(&q, fields, lg_r, s.summed, o.tune);
             // sum group [g0, g1) of this window; a group of one stands alone
             const uint64_t g0 = j / G * G, g1 = (g0 + G < s.nin) ? g0 + G : s.nin;
             int sum = kSumNone;
@@ -398,14 +404,14 @@ bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::ve
     return true;
 }
 
-double blocks_cost_ms(const std::vector<Block> &bl) {
+double blocks_cost_ms(const std::vector<Block> &bl, const Tuning *tune) {
     double c = 0;
     for (const Block &b : bl) {
         if (b.sum == kSumTail) {
             c += tail_cost(b.p.m);
             continue;
         }
-        const double t = b.sum == kSumNone ? alone_cost(b.p.field, b.p.lg) : plan_cost(b.p.field, b.p.lg);
+        const double t = b.sum == kSumNone ? alone_cost(b.p.field, b.p.lg, tune) : plan_cost(b.p.field, b.p.lg, tune);
         c += (b.sum == kSumFirst || b.sum == kSumInner) ? kSumShare * t : t;
         if (b.xor_into) c += kXorMs;
     }

@@ -484,7 +484,7 @@ extern "C" cm_status cm_batch_create(cm_ctx *ctx, const cm_desc *descs, uint32_t
             total += worklist_scratch_bytes(b->plans[i]);
         } else {
             // the single-call kernels, over the context's field set
-            make_plan(d.kind, d.n, d.m, &b->plans[i], ctx->popt.fields);
+            make_plan(d.kind, d.n, d.m, &b->plans[i], ctx->popt.fields, ctx->popt.tune);
             b->solo.push_back(i);
             total += round256(b->plans[i].scratch_bytes);
         }

@@ -20,6 +20,7 @@ struct cm_ctx {
     int nsm = 0;
     uint64_t budget = 0;         // scratch bytes one call may take
     cm::PlanOptions popt;        // planner options of the single calls
+    cm::Tuning tune{};           // cm_calibrate's figures (popt.tune points here once taken)
     cudaMemPool_t pool = nullptr;
     uint64_t *d_tables = nullptr;
     uint32_t *d_status = nullptr;

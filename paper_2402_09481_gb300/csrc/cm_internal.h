@@ -162,7 +162,8 @@ inline int field_for(int fields, int lg) {
 
 // Validate (kind, n, m) and fill the plan; false if invalid or if K + m - 1
 // exceeds 2^32 (one transform).  fields: a field set (kFields*).
-bool make_plan(int kind, uint64_t n, uint64_t m, Plan *out, int fields = kFieldsGL);
+struct Tuning;  // planner figures taken on the device (below)
+bool make_plan(int kind, uint64_t n, uint64_t m, Plan *out, int fields = kFieldsGL, const Tuning *tune = nullptr);
 // (kind, n, m) satisfies the argument rules of the single calls.
 bool valid_args(int kind, uint64_t n, uint64_t m);
 
@@ -204,12 +205,22 @@ struct Block {
 // and block shapes by an estimate of GPU time; shapes whose scratch exceeds
 // budget (0 = no limit) are taken only if none fits.  False if invalid.
 // fields: the field set of the products (kFields*).
+// Planner figures taken on the device (cm_calibrate): ms per extraction of
+// each transform length and field (the column-pass form), of a product alone
+// on a cluster (2^14 .. 2^17), and the first column pass's length log2 R of
+// two-pass plans.  Zero entries fall back to the built-in tables.
+struct Tuning {
+    double cost[3][33];  // [kFieldGL, kFieldF30, kFieldF25][lg]
+    double cluster[kClusterMaxLg - kClusterMinLg + 1];
+    int8_t split[3][33];  // [field][lg]
+};
 struct PlanOptions {
     int max_lg = 32;          // longest transform of one product (log2), 8..32
     int fields = kFieldsAll;  // F25 up to 2^25, F30 up to 2^30, Goldilocks above
     uint64_t budget = 0;      // scratch cap for choosing a shape (0 = none)
     uint32_t max_sum = 0;     // cap on blocks per sum group (0 = the field's bound)
     bool single = false;      // one transform whenever it fits (no cost-based split)
+    const Tuning *tune = nullptr;  // the context's calibration, if any
 };
 // PlanOptions from cm_options (NULL: defaults); false if a value is invalid.
 bool plan_options(const cm_options *opt, PlanOptions *o);
@@ -221,7 +232,7 @@ inline int worklist_fields(const PlanOptions &o) { return o.fields == kFieldsGL 
 bool make_blocks(int kind, uint64_t n, uint64_t m, const PlanOptions &o, std::vector<Block> *out);
 
 // Estimated GPU time (ms) of a block list, from measured per-length times.
-double blocks_cost_ms(const std::vector<Block> &bl);
+double blocks_cost_ms(const std::vector<Block> &bl, const Tuning *tune = nullptr);
 
 // Scratch bytes of a block list: the largest block's scratch, then an XOR
 // temporary at *tmp_off (when blocks XOR), then 256 bytes of Dodis et al.

@@ -37,6 +37,9 @@ PROTOTYPES = {
     "cm_circulant": (_I, [_P, _P, _U64, _P, _U64, _P, _P]),
     "cm_dodis": (_I, [_P, _P, _P, _U64, _U64, _P, _P]),
     "cm_compose": (_I, [_P, _I, _P, _U64, _P, _U64, _I, _U64, _U64, _P, _P]),
+    "cm_calibrate": (_I, [_P, ctypes.c_char_p, _U32, _U32]),
+    "cm_tune_query": (_I, [_P, _U32, _U32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_int32)]),
     "cm_device_status": (_I, [_P, _P, ctypes.POINTER(_U32)]),
     "cm_extract_host": (_I, [_P, _I, _P, _U64, _P, _U64, _P, _P]),
     "cm_toeplitz_noalloc": (_I, [_P, _U64, _P, _U64, _P, _P]),
@@ -88,6 +91,7 @@ MODEL_SEEDED, MODEL_PRODUCT, MODEL_MARKOV = 0, 1, 2
 ADV_CLASSICAL, ADV_QUANTUM = 0, 1
 ADJUST_UP, ADJUST_DOWN, ADJUST_CLOSEST = 0, 1, 2
 FIELD_AUTO, FIELD_GOLDILOCKS, FIELD_Q30, FIELD_Q25 = 0, 1, 2, 3
+TUNE_FORCE = 1
 PLAN_COST, PLAN_SINGLE = 0, 1
 
 
@@ -419,6 +423,19 @@ class Context:
         _check(self._L.cm_compose(self._h, kind1, px, n1, py, m1, kind2, n2, m2, z.data_ptr(),
                                   _stream_handle(stream)), "cm_compose")
         return z
+
+    def calibrate(self, cache: str | None = None, force: bool = False, max_lg: int = 0):
+        """Time the planner's figures on this GPU (cm_calibrate), or load them
+        from `cache` when it matches the device."""
+        _check(self._L.cm_calibrate(self._h, cache.encode() if cache else None, TUNE_FORCE if force else 0,
+                                    max_lg), "cm_calibrate")
+
+    def tune_query(self, field: int, lg: int) -> tuple[float, float, int]:
+        """(ms, cluster_ms, split) of the calibration for field and 2^lg (0 where none)."""
+        ms, cl, sp = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_int32(0)
+        _check(self._L.cm_tune_query(self._h, field, lg, ctypes.byref(ms), ctypes.byref(cl), ctypes.byref(sp)),
+               "cm_tune_query")
+        return ms.value, cl.value, sp.value
 
     def von_neumann(self, x, n: int, z=None, m_out=None, stream=None):
         """Von Neumann extraction on the device (cm_von_neumann).  Returns
