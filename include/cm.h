@@ -367,10 +367,12 @@ typedef struct {
     uint32_t slots;            /* concurrent waves (CUDA streams); 0 = 2 */
     uint32_t max_queue;        /* pending requests before cm_submit says CM_EAGAIN; 0 = 2^20 */
     uint32_t max_wave;         /* requests per wave; 0 = 512 */
-    uint32_t reserved0;
+    uint32_t express_slots;    /* extra high-priority slots for work-list-sized requests; 0 = 1,
+                                  CM_SERVER_NO_EXPRESS = none */
     uint64_t seed_cache_bytes; /* resident seed transforms (within the budget); 0 = a quarter of it */
     uint32_t reserved[2];
 } cm_server_options;
+#define CM_SERVER_NO_EXPRESS 0xFFFFFFFFu
 
 typedef struct {
     uint64_t submitted, completed, rejected, waves;
@@ -381,16 +383,22 @@ typedef struct {
 
 /*
  * Start the request server of a context (one per context): a worker thread
- * that admits pending requests in arrival order into waves whenever a slot is
- * free, as long as their scratch fits in what the HBM budget leaves, and
- * launches each wave as one work-list kernel (the cm_batch_create machinery)
- * on the slot's stream; waves on different slots overlap on the device.
- * Requests flagged CM_REQ_SEED_CACHE (transform length 2^14 .. 2^25) keep the
- * forward transform of their seed operand resident, keyed by (seed_id, kind,
- * n, m); a later request with the same key skips that transform (reuse of the
- * seed is what the paper's strong extractors allow).  Least recently used
- * entries are dropped past seed_cache_bytes.  The paper has no serving layer;
- * each request computes exactly its single call.
+ * that admits pending requests in queue order into waves whenever a slot is
+ * free, as long as their scratch fits in what the HBM budget leaves (a request
+ * that does not fit yet is passed over by at most 16 waves, after which
+ * nothing behind it starts until it fits).  A wave runs its requests with
+ * transforms up to 2^21 as one work-list kernel (the cm_batch_create
+ * machinery) and longer ones through the single-call planner, on the slot's
+ * stream; a wave of one request runs the single-call kernels.  Waves on
+ * different slots overlap on the device.  Express slots (high stream
+ * priority) take only requests up to 2^21, so that short requests are not
+ * held behind long ones.  Requests flagged CM_REQ_SEED_CACHE (transform
+ * length 2^14 .. 2^21) keep the forward transform of their seed operand
+ * resident, keyed by (seed_id, kind, n, m); a later request with the same key
+ * skips that transform (reuse of the seed is what the paper's strong
+ * extractors allow).  Least recently used entries are dropped past
+ * seed_cache_bytes.  The paper has no serving layer; each request computes
+ * exactly its single call.
  */
 cm_status cm_server_start(cm_ctx *ctx, const cm_server_options *opt);
 

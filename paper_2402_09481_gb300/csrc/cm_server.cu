@@ -113,6 +113,7 @@ struct Slot {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
     bool busy = false;
+    bool express = false;  // high-priority stream; takes work-list requests only
     std::vector<uint64_t> tickets;
     std::vector<int> pre_index;  // per ticket: flag pair index, or -1
     size_t foot = 0;
@@ -262,13 +263,20 @@ constexpr uint32_t kMaxPassed = 16;
 // request that does not fit.  Marks the slot busy and copies what the launch
 // needs into w; false if nothing was admitted.
 bool admit_wave(cm_server *S, Slot &sl, Wave &w) {
-    std::vector<uint64_t> wave, passed;
-    std::vector<size_t> passed_at;
+    std::vector<uint64_t> wave, passed, other;
+    std::vector<size_t> passed_at, other_at;
     size_t foot = 0;
     const size_t scan = std::max<size_t>(64, 4 * (size_t)S->opt.max_wave);
     for (size_t seen = 0; seen < scan && !S->pending.empty() && wave.size() < S->opt.max_wave; ++seen) {
         const uint64_t tk = S->pending.front();
         const Req &r = S->reqs[tk];
+        if (sl.express && !on_worklist(r.p)) {
+            // not for this lane: stays queued for a normal slot (not a pass)
+            other.push_back(tk);
+            other_at.push_back(passed.size());
+            S->pending.pop_front();
+            continue;
+        }
         auto fits = [&] { return S->inflight + foot + r.foot + S->seed_bytes <= S->budget; };
         if (!fits() && S->inflight + foot == 0)
             while (!fits() && seed_evict_one(S, sl.st)) {
@@ -284,10 +292,20 @@ bool admit_wave(cm_server *S, Slot &sl, Wave &w) {
         wave.push_back(tk);
         S->pending.pop_front();
     }
-    for (size_t j = passed.size(); j-- > 0;) {
-        S->pending.push_front(passed[j]);
-        if (passed_at[j] < wave.size()) S->reqs[passed[j]].passed += 1;  // a later request went first
+    // put the skipped requests back at the front in their queue order: the
+    // passed ones (counted when a later request went first) and, for the
+    // express lane, the ones it does not take
+    std::vector<uint64_t> back;
+    back.reserve(passed.size() + other.size());
+    for (size_t i = 0, j = 0; i < passed.size() || j < other.size();) {
+        if (j < other.size() && (i >= passed.size() || other_at[j] <= i)) {
+            back.push_back(other[j++]);
+        } else {
+            if (passed_at[i] < wave.size() && !sl.express) S->reqs[passed[i]].passed += 1;  // a later one went first
+            back.push_back(passed[i++]);
+        }
     }
+    for (size_t j = back.size(); j-- > 0;) S->pending.push_front(back[j]);
     if (wave.empty()) return false;
     const uint64_t t = now_ns(), wid = ++S->waves;
     const uint32_t n = (uint32_t)wave.size();
@@ -549,9 +567,19 @@ extern "C" cm_status cm_server_start(cm_ctx *ctx, const cm_server_options *opt) 
         delete S;
         return CM_EDEVICE;
     }
-    S->slots.resize(S->opt.slots);
-    for (Slot &sl : S->slots) {
-        if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
+    const uint32_t express = S->opt.express_slots == CM_SERVER_NO_EXPRESS ? 0u
+                             : S->opt.express_slots ? S->opt.express_slots : 1u;
+    int prio_low = 0, prio_high = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+        delete S;
+        return CM_EDEVICE;
+    }
+    S->slots.resize(S->opt.slots + express);
+    for (size_t i = 0; i < S->slots.size(); ++i) {
+        Slot &sl = S->slots[i];
+        sl.express = i >= S->opt.slots;
+        if (cudaStreamCreateWithPriority(&sl.st, cudaStreamNonBlocking, sl.express ? prio_high : prio_low) !=
+                cudaSuccess ||
             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
             server_release(S);
             return CM_EDEVICE;

@@ -92,6 +92,7 @@ ADV_CLASSICAL, ADV_QUANTUM = 0, 1
 ADJUST_UP, ADJUST_DOWN, ADJUST_CLOSEST = 0, 1, 2
 FIELD_AUTO, FIELD_GOLDILOCKS, FIELD_Q30, FIELD_Q25 = 0, 1, 2, 3
 TUNE_FORCE = 1
+SERVER_NO_EXPRESS = 0xFFFFFFFF
 PLAN_COST, PLAN_SINGLE = 0, 1
 
 
@@ -156,7 +157,7 @@ class CmResult(ctypes.Structure):
 
 class ServerOptions(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32),
-                ("max_queue", ctypes.c_uint32), ("max_wave", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+                ("max_queue", ctypes.c_uint32), ("max_wave", ctypes.c_uint32), ("express_slots", ctypes.c_uint32),
                 ("seed_cache_bytes", ctypes.c_uint64), ("reserved", ctypes.c_uint32 * 2)]
 
 
@@ -553,8 +554,9 @@ class Context:
 
     # ----- serving -------------------------------------------------------------
     def server_start(self, hbm_budget_bytes: int = 0, slots: int = 0, max_queue: int = 0, max_wave: int = 0,
-                     seed_cache_bytes: int = 0):
-        o = ServerOptions(hbm_budget_bytes, slots, max_queue, max_wave, 0, seed_cache_bytes)
+                     seed_cache_bytes: int = 0, express_slots: int = 0):
+        """express_slots: 0 = one, SERVER_NO_EXPRESS = none."""
+        o = ServerOptions(hbm_budget_bytes, slots, max_queue, max_wave, express_slots, seed_cache_bytes)
         _check(self._L.cm_server_start(self._h, ctypes.byref(o)), "cm_server_start")
 
     def server_stop(self):

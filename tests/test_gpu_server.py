@@ -137,6 +137,31 @@ def test_server_admission_by_footprint(sctx, cm_ctx):
     sctx.server_stop()
 
 
+def test_server_express_slot(sctx, cm_ctx):
+    # one normal slot: a long request holds it; short requests that arrive
+    # meanwhile finish first through the express slot (high stream priority),
+    # and without it they wait behind the long one
+    big = make(T, 2 ** 26, 2 ** 25, 801)     # L = 2^27: milliseconds
+    smalls = [make(T, 3000 + 100 * j, 1500, 810 + 2 * j) for j in range(6)]
+    for express in (0, native.SERVER_NO_EXPRESS):
+        sctx.server_start(slots=1, express_slots=express)
+        tb = submit(sctx, big)
+        time.sleep(0.002)
+        ts = [submit(sctx, r) for r in smalls]
+        rs = [wait(sctx, t) for t in ts]
+        rb = wait(sctx, tb)
+        assert rb["status"] == native.CM_OK and all(r["status"] == native.CM_OK for r in rs)
+        if express == 0:
+            assert all(r["t_done_ns"] < rb["t_done_ns"] for r in rs)
+        else:
+            assert all(r["t_done_ns"] >= rb["t_done_ns"] for r in rs)
+        st = sctx.server_stats()
+        assert st["slots"] == (2 if express == 0 else 1)
+        sctx.server_stop()
+        for r in smalls + [big]:
+            assert torch.equal(r["z"], alone(cm_ctx, r))
+
+
 def test_server_queue_full_poll_timeout_unknown(sctx):
     a = make(T, 2 ** 25, 2 ** 25, 41)     # L = 2^26: about 0.5 GiB of scratch, over a millisecond
     b = make(T, 2 ** 25, 2 ** 25, 43)
