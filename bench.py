@@ -1381,6 +1381,7 @@ def run_served(args, world, rank, local, emit=True):
         "config": {"workload": f"Served: {count} requests, Poisson arrivals at {rate:g} req/s, Toeplitz/Circulant/"
                                "Dodis 50/25/25, n = floor(2^U), U ~ U[12, 28) (N_A-snapped), m = n/2, "
                                "Bernoulli(1/2) inputs", "slots": st["slots"],
+                   "express_slots": 1,
                    "hbm_budget_bytes": st["budget_bytes"]},
         "served": main_run, "plain_per_call": plain_stats, "sub_saturation": points,
         "latency_ms": main_run["latency_ms"], "max_inflight_bytes": st["max_inflight_bytes"],
