@@ -67,11 +67,17 @@ def seed_bits(kind, n, m):
     return n + m - 1 if kind == 0 else (n + 1 if kind == 1 else n)
 
 
-# Kernels compiled from a translation unit of their own: a capture of one of
-# them stays valid while only other units change.  Every other kernel (the
-# transforms, the tail, the batch kernels) is keyed on all remaining units.
-# Each unit counts with the headers it includes (transitively).
-OWN_UNITS = {"k_vn": "cm_vn.cu", "k_rsh": "cm_trevisan.cu", "k_ss": "cm_shared_seed.cu"}
+# The translation units a kernel's capture depends on: the unit that defines
+# and launches it and, for the NTT-path kernels, the planner that picks their
+# shapes (cm_api.cu).  A capture stays valid while only other units change.
+# Any other kernel is keyed on every unit but those of the stand-alone
+# extractors (Von Neumann, Trevisan, shared seed).  Each unit counts with the
+# headers it includes (transitively).
+OWN_UNITS = {"k_vn": ("cm_vn.cu",), "k_rsh": ("cm_trevisan.cu",), "k_ss": ("cm_shared_seed.cu",),
+             "k_pass_fwd_bits_f25": ("cm_pass25.cu", "cm_api.cu"), "k_middle_f25": ("cm_pass25.cu", "cm_api.cu"),
+             "k_pass_inv_parity_f25": ("cm_pass25.cu", "cm_api.cu"),
+             "k_pack_tail": ("cm_launch_misc.cu", "cm_api.cu"), "k_cluster_f25": ("cm_cluster25.cu", "cm_api.cu"),
+             "k_batch": ("cm_batch.cu", "cm_api.cu")}
 _INCLUDE = re.compile(r'^\s*#\s*include\s+"([^"]+)"', re.M)
 
 
@@ -101,8 +107,10 @@ def kernel_source_hash(kernel: str | None = None) -> str:
     own = next((u for pre, u in OWN_UNITS.items() if kernel and kernel.startswith(pre)), None)
     csrc = os.path.join(ROOT, "paper_2402_09481_gb300", "csrc")
     units = [f for f in sorted(os.listdir(csrc)) if f.endswith(".cu")]
-    if kernel is not None:
-        units = [f for f in units if f == own] if own else [f for f in units if f not in OWN_UNITS.values()]
+    if own:
+        units = [f for f in units if f in own]
+    elif kernel is not None:
+        units = [f for f in units if f not in ("cm_vn.cu", "cm_trevisan.cu", "cm_shared_seed.cu")]
     h = hashlib.sha256()
     for path in _source_closure([os.path.join(csrc, f) for f in units]):
         h.update(os.path.relpath(path, ROOT).encode())
@@ -226,7 +234,7 @@ def element_bytes(field):
 def kernel_model(products, m):
     """Per-step algorithmic bytes and launches of each kernel (name without the
     field suffix), from the plan's product list (cm_plan_products), in the
-    scope's model: one write and one read of three L-element
+    HBM model of the path: one write and one read of three L-element
     arrays per product with 8-byte field elements, 48 L bytes (a forward pass
     writes both operands, 16 L; the middle reads them and writes the product,
     24 L, or reads and writes the sum-group accumulator as well, 32 L; the
@@ -283,11 +291,11 @@ NUM_SMS = 152
 
 
 def path_model(products, n, seedlen, m):
-    """Bytes and modular multiplies of the whole path (SURVEY 8(d)):
+    """Bytes and modular multiplies of the whole path:
     bytes48 = 48 L per product (8-byte elements) + the bit I/O once;
     bytes_actual = 6 e L per product with the path's element size e;
-    modmuls_reference = 3 L (ceil(lg / 6) - 1) + L per product (the scope's
-    official count: a radix-64 plan whose inner twiddles are shifts, as over
+    modmuls_reference = 3 L (ceil(lg / 6) - 1) + L per product (the reference
+    count: a radix-64 plan whose inner twiddles are shifts, as over
     Goldilocks); modmuls_radix2 = 3 (L / 2)(lg - 2) + L per product (the
     non-trivial twiddles of three radix-2 transforms and the pointwise
     product: the count without free twiddles, as over the 32-bit fields)."""
@@ -585,7 +593,7 @@ def run_batched_a(args, world, rank, local, emit=True):
     plain_value = world * out_bits / (statistics.median(plain_ms) * 1e-3) / 1e9
 
     # roofline of the work-list kernel (the only kernel of a step), in the
-    # scope's model: 48 L bytes per instance with 8-byte
+    # path's HBM model: 48 L bytes per instance with 8-byte
     # elements (on-chip instances, L <= 2^13: the bits only) + the bit I/O; the
     # work list runs 4-byte elements, so it moves about half of that
     Ls = np.array([native.plan_query(native.TOEPLITZ, int(n), int(m), plan_mode=native.PLAN_SINGLE)
@@ -607,7 +615,7 @@ def run_batched_a(args, world, rank, local, emit=True):
     roof = {"bound": "hbm", "kernel": "k_batch", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json)",
             "traffic": ncu_traffic("k_batch", "batched_a"),
-            "model": "SURVEY 8(d): 48 L bytes per instance with L > 2^13 (8-byte elements) + bit I/O",
+            "model": "48 L bytes per instance with L > 2^13 (8-byte elements) + bit I/O",
             "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_launch,
             "actual_element_bytes": {"bytes_per_launch": act, "achieved": act / (per_launch * 1e-3) / 1e9,
                                      "frac": act / (per_launch * 1e-3) / 1e9 / peak}}
@@ -1416,7 +1424,7 @@ def roofline_of(prof, products, m, peak, peak_src, workload):
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": ncu_traffic(dom, workload),
             "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json)",
-            "model": "SURVEY 8(d): 48 L bytes per product (three L-element arrays written and read once, "
+            "model": "48 L bytes per product (three L-element arrays written and read once, "
                      "8-byte elements) split over the kernels, per launch",
             "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_launch,
             "launches_per_step": model["launches"],

@@ -69,6 +69,10 @@ __device__ __forceinline__ uint32_t cl_ld(uint32_t a) {
 __device__ __forceinline__ void cl_st(uint32_t a, uint32_t v) {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v));
 }
+// The two halves of a cluster barrier: every thread of the cluster arrives
+// once (its earlier shared-memory writes released), then waits for all.
+__device__ __forceinline__ void cl_arrive_release() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
+__device__ __forceinline__ void cl_wait_acquire() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
 __device__ __forceinline__ void cl_or(uint32_t a, uint32_t v) {
     asm volatile("red.shared::cluster.or.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
@@ -117,16 +121,6 @@ k25_cluster(BitMap amap, BitMap bmap, uint64_t lo, uint64_t m, uint64_t linv, ui
 
     prefetch_steps25<kMidLgMax>(tw, rt.steps);  // needed from phase 2 on
     for (int i = threadIdx.x; i < kClBits; i += kThreads) bits[i] = 0u;
-    // cross-step roots: the powers of omega_L^j for this thread's columns
-    for (int jj = threadIdx.x; jj < J; jj += kThreads) {
-        const uint32_t w = big_root_f<FieldF25>(rt.big_lo_fwd, rt.big_hi_fwd, (uint32_t)(r * J + jj) << ESH);
-        uint32_t wk = w;
-#pragma unroll
-        for (int k1 = 1; k1 < CL; ++k1) {
-            roots[(k1 - 1) * J + jj] = wk;
-            if (k1 + 1 < CL) wk = FieldF25::twmul(wk, w);
-        }
-    }
     // 0. operands: one run of 32 positions per thread (kClM / 32 runs each),
     //    read as one or two words; thread t of a warp writes run t at
     //    sp(32 t + i), bank (t + i) mod 32: no conflicts
@@ -138,7 +132,22 @@ k25_cluster(BitMap amap, BitMap bmap, uint64_t lo, uint64_t m, uint64_t linv, ui
 #pragma unroll
         for (int i = 0; i < 32; ++i) dst[i] = (bitsr >> i) & 1u;
     }
-    cluster.sync();  // every CTA of the cluster runs and its tables are in place
+    // the operands are what the other CTAs read in phase 1: publish them, and
+    // compute the cross-step roots while the other CTAs catch up (each root is
+    // written and read by one thread of this CTA only: the same jj mapping in
+    // phases 1 and 3)
+    cl_arrive_release();
+    // cross-step roots: the powers of omega_L^j for this thread's columns
+    for (int jj = threadIdx.x; jj < J; jj += kThreads) {
+        const uint32_t w = big_root_f<FieldF25>(rt.big_lo_fwd, rt.big_hi_fwd, (uint32_t)(r * J + jj) << ESH);
+        uint32_t wk = w;
+#pragma unroll
+        for (int k1 = 1; k1 < CL; ++k1) {
+            roots[(k1 - 1) * J + jj] = wk;
+            if (k1 + 1 < CL) wk = FieldF25::twmul(wk, w);
+        }
+    }
+    cl_wait_acquire();  // every CTA of the cluster runs and its operands are in place
 
     // 1. CL-point DFTs across the cluster, both operands of column j together
     //    (all 2 CL remote loads in flight); column j is read and written by

@@ -176,7 +176,78 @@ cudaError_t launch_xor_into(uint64_t *z, const uint64_t *t, uint64_t words, int 
 constexpr int kTailThreads = 256;
 static_assert(kTailMax == kTailThreads && kTailMax % 64 == 0, "one tail bit per thread");
 
-// NW = ceil(T / 64) words of tail bits (the loop runs over 64 NW terms).
+// One output word of the tail: the XOR over the set tail bits t of the 64
+// seed bits starting at offset t of W (W[q] = seed bits 64 q .. 64 q + 63 of
+// this word's run).  sal holds the tail bits, 32 a word; they are the same in
+// every thread, so the loop over the set ones does not diverge and runs about
+// T / 2 times; each 64-bit run is two 32-bit funnel shifts.
+template <int NW>
+__device__ __forceinline__ uint64_t tail_word(const uint32_t *sal, const uint64_t (&W)[NW + 1]) {
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int h = 0; h < 2 * NW; ++h) {
+        // offsets 32 h .. 32 h + 31: 32-bit words h, h + 1, h + 2 of the run
+        const uint32_t v0 = h & 1 ? (uint32_t)(W[h >> 1] >> 32) : (uint32_t)W[h >> 1];
+        const uint32_t v1 = h & 1 ? (uint32_t)W[(h >> 1) + 1] : (uint32_t)(W[h >> 1] >> 32);
+        const uint32_t v2 = h & 1 ? (uint32_t)(W[(h >> 1) + 1] >> 32) : (uint32_t)W[(h >> 1) + 1];
+        uint32_t l2 = 0, h2 = 0;  // a second pair of accumulators: two chains
+        uint32_t a = sal[h];
+        while (a) {
+            const int s = __ffs(a) - 1;
+            a &= a - 1;
+            lo ^= __funnelshift_r(v0, v1, s);
+            hi ^= __funnelshift_r(v1, v2, s);
+            if (!a) break;
+            const int u = __ffs(a) - 1;
+            a &= a - 1;
+            l2 ^= __funnelshift_r(v0, v1, u);
+            h2 ^= __funnelshift_r(v1, v2, u);
+        }
+        lo ^= l2;
+        hi ^= h2;
+    }
+    return (uint64_t)lo | ((uint64_t)hi << 32);
+}
+
+// Seed positions k .. k + 64 (NW + 1) - 1 of map b as NW + 1 words: when the
+// run maps to one run of source bits (no cut at len, no wrap, not reversed)
+// from NW + 1 or NW + 2 word loads; else position by position in a loop that
+// is not unrolled (runs at the ends of the window only), so that the code a
+// warp executes stays a few hundred instructions: these kernels run one short
+// wave, and their time goes to fetching the instructions they run.
+template <int NW>
+__device__ __forceinline__ void seed_words(const BitMap &b, uint64_t k, uint64_t (&W)[NW + 1]) {
+    constexpr uint64_t kSpan = 64 * (NW + 1);
+    if (k + kSpan <= b.len && b.mode != kReverse) {
+        uint64_t lo = k;
+        if (b.mode == kModForward) {
+            lo = k + b.off;
+            if (lo >= b.srclen) lo -= b.srclen;
+            if (lo >= b.srclen) lo -= b.srclen;
+        }
+        if (lo + kSpan <= b.srclen) {
+            const uint64_t *src = b.src + (lo >> 6);
+            const int sh = (int)(lo & 63);
+            uint64_t u[NW + 2];
+#pragma unroll
+            for (int q = 0; q <= NW; ++q) u[q] = __ldg(src + q);
+            // the word after the run's last is read only when the run reaches into it
+            u[NW + 1] = sh ? __ldg(src + NW + 1) : 0ull;
+#pragma unroll
+            for (int q = 0; q <= NW; ++q) W[q] = sh ? (u[q] >> sh) | (u[q + 1] << (64 - sh)) : u[q];
+            return;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q <= NW; ++q) {
+        uint64_t v = 0;
+#pragma unroll 1
+        for (int j = 0; j < 64; ++j) v |= b.get(k + 64 * q + j) << j;
+        W[q] = v;
+    }
+}
+
+// NW = ceil(T / 64) words of tail bits.
 template <int NW>
 __global__ void __launch_bounds__(kTailThreads)
 k_tail(BitMap amap, BitMap bmap, uint64_t K, uint32_t T, uint64_t m, uint64_t *__restrict__ z,
@@ -190,28 +261,12 @@ k_tail(BitMap amap, BitMap bmap, uint64_t K, uint32_t T, uint64_t m, uint64_t *_
         if ((t & 31) == 0) sal[t >> 5] = w;
     }
     __syncthreads();
-    uint64_t al[NW];
-#pragma unroll
-    for (int q = 0; q < NW; ++q) al[q] = (uint64_t)sal[2 * q] | ((uint64_t)sal[2 * q + 1] << 32);
     const uint64_t nwords = (m + 63) >> 6;
     for (uint64_t w = (uint64_t)blockIdx.x * kTailThreads + threadIdx.x; w < nwords;
          w += (uint64_t)gridDim.x * kTailThreads) {
         uint64_t W[NW + 1];  // seed bits 64 w .. 64 w + 64 (NW + 1) - 1
-#pragma unroll
-        for (int q = 0; q <= NW; ++q) {
-            const uint64_t v = (w << 6) + 64 * q;
-            W[q] = (uint64_t)bmap.get_run<32>(v) | ((uint64_t)bmap.get_run<32>(v + 32) << 32);
-        }
-        // four independent accumulators (terms t mod 4): no serial chain of
-        // dependent XORs; the tail bits are the same in every thread, so the
-        // branches do not diverge
-        uint64_t acc4[4] = {0, 0, 0, 0};
-#pragma unroll
-        for (int t = 0; t < 64 * NW; ++t) {
-            const int q = t >> 6, s = t & 63;
-            if ((al[q] >> s) & 1ull) acc4[t & 3] ^= s ? (W[q] >> s) | (W[q + 1] << (64 - s)) : W[q];
-        }
-        uint64_t acc = (acc4[0] ^ acc4[1]) ^ (acc4[2] ^ acc4[3]);
+        seed_words<NW>(bmap, w << 6, W);
+        uint64_t acc = tail_word<NW>(sal, W);
         if (w == nwords - 1 && (m & 63)) acc &= (1ull << (m & 63)) - 1;
         z[w] ^= acc;
     }
@@ -235,8 +290,12 @@ cudaError_t launch_tail(const BitMap &amap, const BitMap &bmap, uint64_t K, uint
 }
 
 // k_pack and k_tail in one pass: one thread per output word (the grid covers
-// every word) packs its 64 parity bytes (four 16-byte loads when the word lies
-// below m) and XORs in the tail terms, computed as in k_tail.
+// every word) XORs the tail terms (tail_word) into its 64 packed parity bytes
+// (four 16-byte loads when the word lies below m).  The tail depends on the
+// input bits only, the parity bytes on the kernel before (the inverse pass):
+// launched as its programmatic dependent, the kernel computes the tail while
+// that pass's last CTAs still run and waits for it (griddepcontrol.wait, which
+// returns at once in an ordinary launch) only before it reads the parity.
 template <int NW>
 __global__ void __launch_bounds__(kTailThreads)
 k_pack_tail(const uint8_t *__restrict__ par, uint64_t m, uint64_t *__restrict__ z, const uint32_t *__restrict__ pre,
@@ -244,31 +303,9 @@ k_pack_tail(const uint8_t *__restrict__ par, uint64_t m, uint64_t *__restrict__ 
     __shared__ uint32_t sal[kTailMax / 32];
     const uint64_t nwords = (m + 63) >> 6;
     const uint64_t w = (uint64_t)blockIdx.x * kTailThreads + threadIdx.x;  // one word a thread (grid covers m)
-    // this word's seed bits and parity bytes first: their loads overlap the
-    // gather of the tail bits below
     uint64_t W[NW + 1];  // seed bits 64 w .. 64 w + 64 (NW + 1) - 1
-    uint64_t packed = 0;
     if (w < nwords) {
-#pragma unroll
-        for (int q = 0; q <= NW; ++q) {
-            const uint64_t v = (w << 6) + 64 * q;
-            W[q] = (uint64_t)bmap.get_run<32>(v) | ((uint64_t)bmap.get_run<32>(v + 32) << 32);
-        }
-        if ((reinterpret_cast<uintptr_t>(par) & 15) == 0 && (w << 6) + 64 <= m) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(par + (w << 6));
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint4 v = __ldg(src + k);
-                const uint64_t u = ((v.x * 0x01020408u) >> 24) | (((v.y * 0x01020408u) >> 24) << 4) |
-                                   (((v.z * 0x01020408u) >> 24) << 8) | (((v.w * 0x01020408u) >> 24) << 12);
-                packed |= u << (16 * k);
-            }
-        } else {
-            for (int b = 0; b < 64; ++b) {
-                const uint64_t p = (w << 6) + b;
-                if (p < m) packed |= (uint64_t)(par[p] & 1u) << b;
-            }
-        }
+        seed_words<NW>(bmap, w << 6, W);
     } else {
 #pragma unroll
         for (int q = 0; q <= NW; ++q) W[q] = 0;
@@ -279,20 +316,32 @@ k_pack_tail(const uint8_t *__restrict__ par, uint64_t m, uint64_t *__restrict__ 
         const uint32_t b = __ballot_sync(0xffffffffu, bit);
         if ((t & 31) == 0) sal[t >> 5] = b;
     }
+    // the precondition flags come from a kernel that finished before the
+    // inverse pass began
     const bool bad = pre && (pre[0] == 0u || pre[1] == 0u);
     if (bad && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kFlagPrecond);
     __syncthreads();
     if (w >= nwords) return;
-    uint64_t al[NW];
+    uint64_t acc = tail_word<NW>(sal, W);
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // the parity bytes are complete and visible
+    uint64_t packed = 0;
+    if ((reinterpret_cast<uintptr_t>(par) & 15) == 0 && (w << 6) + 64 <= m) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(par + (w << 6));
 #pragma unroll
-    for (int q = 0; q < NW; ++q) al[q] = (uint64_t)sal[2 * q] | ((uint64_t)sal[2 * q + 1] << 32);
-    uint64_t acc4[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int t = 0; t < 64 * NW; ++t) {
-        const int q = t >> 6, s = t & 63;
-        if ((al[q] >> s) & 1ull) acc4[t & 3] ^= s ? (W[q] >> s) | (W[q + 1] << (64 - s)) : W[q];
+        for (int k = 0; k < 4; ++k) {
+            const uint4 v = __ldcg(src + k);  // L2, never a line an L1 kept from before the wait
+            const uint64_t u = ((v.x * 0x01020408u) >> 24) | (((v.y * 0x01020408u) >> 24) << 4) |
+                               (((v.z * 0x01020408u) >> 24) << 8) | (((v.w * 0x01020408u) >> 24) << 12);
+            packed |= u << (16 * k);
+        }
+    } else {
+#pragma unroll 1
+        for (int b = 0; b < 64; ++b) {
+            const uint64_t p = (w << 6) + b;
+            if (p < m) packed |= (uint64_t)(__ldcg(par + p) & 1u) << b;
+        }
     }
-    uint64_t acc = packed ^ (acc4[0] ^ acc4[1]) ^ (acc4[2] ^ acc4[3]);
+    acc ^= packed;
     if (w == nwords - 1 && (m & 63)) acc &= (1ull << (m & 63)) - 1;
     z[w] = bad ? 0ull : acc;
 }
@@ -304,14 +353,26 @@ cudaError_t launch_pack_tail(const uint8_t *par, uint64_t m, uint64_t *z, const 
     const uint64_t blocks = (nwords + kTailThreads - 1) / kTailThreads;  // one word a thread
     if (blocks == 0 || blocks > 0x7fffffffull) return cudaErrorInvalidValue;
     (void)nsm;
-    const dim3 g((unsigned)blocks), t(kTailThreads);
+    // a programmatic dependent of the kernel before it, except under stream
+    // capture (the graphs of a batch keep plain edges)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return cudaGetLastError();
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kTailThreads);
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = cap == cudaStreamCaptureStatusNone ? 1 : 0;
+    auto go = [&](auto kern) { return cudaLaunchKernelEx(&cfg, kern, par, m, z, pre, status, a.amap, a.bmap, a.K, a.T); };
     switch ((a.T + 63) / 64) {
-        case 1: k_pack_tail<1><<<g, t, 0, st>>>(par, m, z, pre, status, a.amap, a.bmap, a.K, a.T); break;
-        case 2: k_pack_tail<2><<<g, t, 0, st>>>(par, m, z, pre, status, a.amap, a.bmap, a.K, a.T); break;
-        case 3: k_pack_tail<3><<<g, t, 0, st>>>(par, m, z, pre, status, a.amap, a.bmap, a.K, a.T); break;
-        default: k_pack_tail<4><<<g, t, 0, st>>>(par, m, z, pre, status, a.amap, a.bmap, a.K, a.T); break;
+        case 1: return go(k_pack_tail<1>);
+        case 2: return go(k_pack_tail<2>);
+        case 3: return go(k_pack_tail<3>);
+        default: return go(k_pack_tail<4>);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_allsame(const uint64_t *x, uint64_t n, uint32_t *flags, int nsm, cudaStream_t st) {

@@ -219,6 +219,9 @@ k25_inv(const uint32_t *__restrict__ data, int lgN, int lgS, uint8_t *__restrict
     const uint32_t col0 = (blockIdx.x - blkN * tiles_per_blk) << NCOL_LG;
     const uint32_t base = (blkN << lgN) + col0;
     const int esh = FieldF25::kAdicity - lgN;
+    // a programmatic dependent (the pack with the tail) may start once every
+    // CTA of this grid has: its CTAs fill the SMs this grid's last wave leaves
+    asm volatile("griddepcontrol.launch_dependents;");
 
     load_steps25<LOGR>(steps, rt.steps);
     load_pass_p25<LOGR>(P, col0, esh, rt);

@@ -16,8 +16,12 @@ def _copy_tree(tmp_path):
     return dst
 
 
+KERNELS = ("k_pass", "k_middle_f30", "k_vn_write", "k_rsh", "k_ss_gf2", "k_middle_f25", "k_pass_fwd_bits_f25",
+           "k_pack_tail", "k_cluster_f25", "k_batch")
+
+
 def _hashes():
-    return {k: bench.kernel_source_hash(k) for k in ("k_pass", "k_middle_f30", "k_vn_write", "k_rsh", "k_ss_gf2")}
+    return {k: bench.kernel_source_hash(k) for k in KERNELS}
 
 
 def test_hash_follows_own_unit(tmp_path, monkeypatch):
@@ -25,7 +29,9 @@ def test_hash_follows_own_unit(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     before = _hashes()
     assert before["k_pass"] == before["k_middle_f30"]          # one family
-    assert len({before[k] for k in ("k_pass", "k_vn_write", "k_rsh", "k_ss_gf2")}) == 4
+    assert before["k_middle_f25"] == before["k_pass_fwd_bits_f25"]
+    assert len({before[k] for k in ("k_pass", "k_vn_write", "k_rsh", "k_ss_gf2", "k_middle_f25", "k_pack_tail",
+                                    "k_cluster_f25", "k_batch")}) == 8
 
     with open(csrc / "cm_trevisan.cu", "a") as f:
         f.write("\n// edit\n")
@@ -33,11 +39,24 @@ def test_hash_follows_own_unit(tmp_path, monkeypatch):
     assert after["k_rsh"] != before["k_rsh"]
     assert all(after[k] == before[k] for k in ("k_pass", "k_vn_write", "k_ss_gf2"))
 
-    with open(csrc / "cm_api.cu", "a") as f:                  # a transform unit
+    with open(csrc / "cm_api.cu", "a") as f:                  # the planner
         f.write("\n// edit\n")
     after2 = _hashes()
-    assert after2["k_pass"] != after["k_pass"]
+    assert all(after2[k] != after[k] for k in ("k_pass", "k_middle_f25", "k_pack_tail", "k_cluster_f25", "k_batch"))
     assert all(after2[k] == after[k] for k in ("k_rsh", "k_vn_write", "k_ss_gf2"))
+
+    with open(csrc / "cm_pass25.cu", "a") as f:               # the 5 * 2^25 + 1 column passes and middle
+        f.write("\n// edit\n")
+    after25 = _hashes()
+    assert after25["k_middle_f25"] != after2["k_middle_f25"] and after25["k_pass_fwd_bits_f25"] != after2[
+        "k_pass_fwd_bits_f25"]
+    assert all(after25[k] == after2[k] for k in ("k_pack_tail", "k_cluster_f25", "k_batch", "k_rsh", "k_vn_write"))
+    with open(csrc / "cm_batch.cu", "a") as f:                # the work list
+        f.write("\n// edit\n")
+    afterb = _hashes()
+    assert afterb["k_batch"] != after25["k_batch"] and afterb["k_pass"] != after25["k_pass"]
+    assert all(afterb[k] == after25[k] for k in ("k_middle_f25", "k_pack_tail", "k_cluster_f25", "k_ss_gf2"))
+    after2 = afterb
 
     with open(csrc / "cm_internal.h", "a") as f:              # a header every unit includes
         f.write("\n// edit\n")
