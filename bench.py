@@ -103,7 +103,8 @@ def _source_closure(units):
 
 
 def kernel_source_hash(kernel: str | None = None) -> str:
-    """Hash of the sources `kernel` is built from (every unit when None)."""
+    """Hash of the code of the sources `kernel` is built from (every unit when
+    None); comments do not count."""
     own = next((u for pre, u in OWN_UNITS.items() if kernel and kernel.startswith(pre)), None)
     csrc = os.path.join(ROOT, "paper_2402_09481_gb300", "csrc")
     units = [f for f in sorted(os.listdir(csrc)) if f.endswith(".cu")]
@@ -114,9 +115,20 @@ def kernel_source_hash(kernel: str | None = None) -> str:
     h = hashlib.sha256()
     for path in _source_closure([os.path.join(csrc, f) for f in units]):
         h.update(os.path.relpath(path, ROOT).encode())
-        with open(path, "rb") as fh:
-            h.update(fh.read())
+        with open(path, errors="replace") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
+
+
+_COMMENT = re.compile(r"//[^\n]*|/\*.*?\*/", re.S)
+
+
+def _code_only(text):
+    """The source without its comments, blank lines and trailing spaces: what
+    a comment edit leaves unchanged (no string literal in these sources holds
+    a comment marker)."""
+    lines = (ln.rstrip() for ln in _COMMENT.sub("", text).splitlines())
+    return "\n".join(ln for ln in lines if ln)
 
 
 def ncu_traffic(kernel: str, workload: str):
@@ -595,13 +607,20 @@ def run_batched_a(args, world, rank, local, emit=True):
     # roofline of the work-list kernel (the only kernel of a step), in the
     # path's HBM model: 48 L bytes per instance with 8-byte
     # elements (on-chip instances, L <= 2^13: the bits only) + the bit I/O; the
-    # work list runs 4-byte elements, so it moves about half of that
+    # work list runs 4-byte elements, so it moves about half of that.  k_batch
+    # runs the instances of the work list (L <= 2^21); the longer ones run the
+    # single-call kernels in the same graph and count in the step's figure only
     Ls = np.array([native.plan_query(native.TOEPLITZ, int(n), int(m), plan_mode=native.PLAN_SINGLE)
                    ["transform_length"] for n, m in zip(ns, ms)])
-    big = Ls > (1 << 13)
-    io = float(((ns + (ns + ms - 1) + ms) / 8).sum())
+    onlist = Ls <= (1 << 21)
+    if int((~onlist).sum()) != int(info["solo_instances"]):
+        raise RuntimeError("work-list split differs from the batch's own")
+    big = (Ls > (1 << 13)) & onlist
+    bits = (ns + (ns + ms - 1) + ms) / 8
+    io = float(bits[onlist].sum())
     alg = float(48 * Ls[big].sum()) + io
     act = float(24 * Ls[big].sum()) + io
+    alg_step = float(48 * Ls[Ls > (1 << 13)].sum() + bits.sum())
     peak, peak_src = measured_peaks()
     ctx.profile_enable(True)
     ctx.profile_read(reset=True)
@@ -615,10 +634,14 @@ def run_batched_a(args, world, rank, local, emit=True):
     roof = {"bound": "hbm", "kernel": "k_batch", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json)",
             "traffic": ncu_traffic("k_batch", "batched_a"),
-            "model": "48 L bytes per instance with L > 2^13 (8-byte elements) + bit I/O",
+            "model": "48 L bytes per work-list instance with 2^13 < L <= 2^21 (8-byte elements) + their bit I/O",
             "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_launch,
+            "work_list_instances": int(onlist.sum()), "single_call_instances": int((~onlist).sum()),
             "actual_element_bytes": {"bytes_per_launch": act, "achieved": act / (per_launch * 1e-3) / 1e9,
-                                     "frac": act / (per_launch * 1e-3) / 1e9 / peak}}
+                                     "frac": act / (per_launch * 1e-3) / 1e9 / peak},
+            "step": {"bytes": alg_step, "achieved": alg_step / (ms_per_step * 1e-3) / 1e9,
+                     "frac": alg_step / (ms_per_step * 1e-3) / 1e9 / peak,
+                     "model": "48 L bytes per instance with L > 2^13 + all bit I/O, over the whole step"}}
 
     # end to end: host inputs (pinned) -> device, batch, outputs -> host
     xp = torch.from_numpy(xh.view(np.int64)).pin_memory()
@@ -1222,7 +1245,10 @@ def run_served(args, world, rank, local, emit=True):
         return
     build.build()
     ctx = native.Context(local)
-    ctx.server_start(slots=int(os.environ.get("CM_SERVE_SLOTS", "2")))
+    express = int(os.environ.get("CM_SERVE_EXPRESS", "1"))
+    streams = int(os.environ.get("CM_SERVE_SLOTS", "0"))  # 0: the server's default, 3 streams
+    ctx.server_start(slots=streams,
+                     express_slots=express if express > 0 else native.SERVER_NO_EXPRESS)
     pool_bits = (1 << 29) + (1 << 24)
     xpool = torch.randint(-(1 << 62), 1 << 62, ((pool_bits + 63) // 64,), dtype=torch.int64, device="cuda")
     ypool = torch.randint(-(1 << 62), 1 << 62, ((pool_bits + 63) // 64,), dtype=torch.int64, device="cuda")
@@ -1388,8 +1414,9 @@ def run_served(args, world, rank, local, emit=True):
         "data": "synthetic",
         "config": {"workload": f"Served: {count} requests, Poisson arrivals at {rate:g} req/s, Toeplitz/Circulant/"
                                "Dodis 50/25/25, n = floor(2^U), U ~ U[12, 28) (N_A-snapped), m = n/2, "
-                               "Bernoulli(1/2) inputs", "slots": st["slots"],
-                   "express_slots": 1,
+                               "Bernoulli(1/2) inputs", "streams": (st["slots"] - max(express, 0)) // 2,
+                   "wave_slots": st["slots"],
+                   "express_slots": max(express, 0),
                    "hbm_budget_bytes": st["budget_bytes"]},
         "served": main_run, "plain_per_call": plain_stats, "sub_saturation": points,
         "latency_ms": main_run["latency_ms"], "max_inflight_bytes": st["max_inflight_bytes"],

@@ -364,7 +364,7 @@ typedef struct {
 
 typedef struct {
     uint64_t hbm_budget_bytes; /* scratch of requests on the device at once; 0 = half the context budget */
-    uint32_t slots;            /* concurrent waves (CUDA streams); 0 = 2 */
+    uint32_t slots;            /* CUDA streams of concurrent waves, two wave slots each; 0 = 3 */
     uint32_t max_queue;        /* pending requests before cm_submit says CM_EAGAIN; 0 = 2^20 */
     uint32_t max_wave;         /* requests per wave; 0 = 512 */
     uint32_t express_slots;    /* extra high-priority slots for work-list-sized requests; 0 = 1,
@@ -378,7 +378,7 @@ typedef struct {
     uint64_t submitted, completed, rejected, waves;
     uint64_t inflight_bytes, max_inflight_bytes, budget_bytes;
     uint64_t seed_cache_hits, seed_cache_misses, seed_cache_bytes, seed_cache_entries;
-    uint32_t queued, busy_slots, slots, reserved;
+    uint32_t queued, busy_slots, slots, reserved; /* slots: wave slots, two per stream plus the express ones */
 } cm_server_stats;
 
 /*
@@ -390,7 +390,8 @@ typedef struct {
  * transforms up to 2^21 as one work-list kernel (the cm_batch_create
  * machinery) and longer ones through the single-call planner, on the slot's
  * stream; a wave of one request runs the single-call kernels.  Waves on
- * different slots overlap on the device.  Express slots (high stream
+ * different streams overlap on the device; each stream has two slots, so the
+ * next wave is enqueued behind the running one.  Express slots (high stream
  * priority) take only requests up to 2^21, so that short requests are not
  * held behind long ones.  Requests flagged CM_REQ_SEED_CACHE (transform
  * length 2^14 .. 2^21) keep the forward transform of their seed operand

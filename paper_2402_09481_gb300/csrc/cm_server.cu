@@ -1,7 +1,9 @@
 // Continuous-batching request server (cm_submit / cm_poll).
 //
 // Clients submit single extractions of any kind and size; a worker thread
-// keeps a FIFO of pending requests and a few "slots" (CUDA streams).  Whenever
+// keeps a FIFO of pending requests and a few "slots" (two per CUDA stream: a
+// wave waits on the stream behind the running one, so that the stream never
+// idles between waves).  Whenever
 // a slot is free it admits, in queue order, the requests whose scratch fits in
 // the HBM budget still unclaimed by requests on the device; a request that
 // does not fit yet is passed over by at most a fixed number of waves, after
@@ -114,6 +116,7 @@ struct Slot {
     cudaEvent_t ev = nullptr;
     bool busy = false;
     bool express = false;  // high-priority stream; takes work-list requests only
+    bool borrowed = false;  // the stream belongs to another slot (the wave runs after that slot's)
     std::vector<uint64_t> tickets;
     std::vector<int> pre_index;  // per ticket: flag pair index, or -1
     size_t foot = 0;
@@ -136,6 +139,7 @@ struct cm_server {
     std::unordered_map<uint64_t, Req> reqs;
     uint64_t next_ticket = 1, waves = 0;
     std::vector<Slot> slots;
+    uint32_t express = 0;  // express slots (the last ones)
     size_t inflight = 0, max_inflight = 0;
     uint64_t submitted = 0, completed = 0, rejected = 0;
     bool stop = false;
@@ -267,11 +271,16 @@ bool admit_wave(cm_server *S, Slot &sl, Wave &w) {
     std::vector<size_t> passed_at, other_at;
     size_t foot = 0;
     const size_t scan = std::max<size_t>(64, 4 * (size_t)S->opt.max_wave);
+    // what the slot takes: an express slot work-list requests only; a slot
+    // whose wave would wait behind another on its stream, while express slots
+    // exist, the longer requests only (a short one waits for a stream of its
+    // own or the express lane, not behind a long wave); any other slot all
+    const bool longs_only = sl.borrowed && S->express > 0;
     for (size_t seen = 0; seen < scan && !S->pending.empty() && wave.size() < S->opt.max_wave; ++seen) {
         const uint64_t tk = S->pending.front();
         const Req &r = S->reqs[tk];
-        if (sl.express && !on_worklist(r.p)) {
-            // not for this lane: stays queued for a normal slot (not a pass)
+        if (sl.express ? !on_worklist(r.p) : longs_only && on_worklist(r.p)) {
+            // not for this lane: stays queued for another slot (not a pass)
             other.push_back(tk);
             other_at.push_back(passed.size());
             S->pending.pop_front();
@@ -293,8 +302,8 @@ bool admit_wave(cm_server *S, Slot &sl, Wave &w) {
         S->pending.pop_front();
     }
     // put the skipped requests back at the front in their queue order: the
-    // passed ones (counted when a later request went first) and, for the
-    // express lane, the ones it does not take
+    // passed ones (counted when a later request went first) and the ones this
+    // slot does not take
     std::vector<uint64_t> back;
     back.reserve(passed.size() + other.size());
     for (size_t i = 0, j = 0; i < passed.size() || j < other.size();) {
@@ -503,7 +512,7 @@ void worker_main(cm_server *S) {
         for (Slot &sl : S->slots) {
             if (sl.busy || S->pending.empty()) continue;
             Wave w;
-            if (!admit_wave(S, sl, w)) break;
+            if (!admit_wave(S, sl, w)) continue;  // another slot may take what this one does not
             // submissions and polls proceed while the wave is planned and launched
             lk.unlock();
             cm_status s = launch_wave(S, sl, w);
@@ -535,8 +544,9 @@ void server_release(cm_server *S) {
         sl.ctrl.release();
         sl.flags.release();
         if (sl.ev) cudaEventDestroy(sl.ev);
-        if (sl.st) cudaStreamDestroy(sl.st);
     }
+    for (Slot &sl : S->slots)
+        if (sl.st && !sl.borrowed) cudaStreamDestroy(sl.st);
     delete S;
 }
 
@@ -556,7 +566,7 @@ extern "C" cm_status cm_server_start(cm_ctx *ctx, const cm_server_options *opt) 
     cm_server *S = new cm_server();
     S->ctx = ctx;
     if (opt) S->opt = *opt;
-    if (!S->opt.slots) S->opt.slots = 2;
+    if (!S->opt.slots) S->opt.slots = 3;
     if (!S->opt.max_queue) S->opt.max_queue = 1u << 20;
     if (!S->opt.max_wave) S->opt.max_wave = 512;
     S->budget = S->opt.hbm_budget_bytes ? S->opt.hbm_budget_bytes : ctx->budget / 2;
@@ -574,13 +584,23 @@ extern "C" cm_status cm_server_start(cm_ctx *ctx, const cm_server_options *opt) 
         delete S;
         return CM_EDEVICE;
     }
-    S->slots.resize(S->opt.slots + express);
+    // Each regular stream carries two slots: the worker plans and enqueues a
+    // wave behind the one running there, so the stream does not idle while it
+    // notices a completion and launches the next wave.  Express slots have a
+    // stream each.
+    const uint32_t R = S->opt.slots;
+    S->express = express;
+    S->slots.resize(2 * (size_t)R + express);
     for (size_t i = 0; i < S->slots.size(); ++i) {
         Slot &sl = S->slots[i];
-        sl.express = i >= S->opt.slots;
-        if (cudaStreamCreateWithPriority(&sl.st, cudaStreamNonBlocking, sl.express ? prio_high : prio_low) !=
-                cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
+        sl.express = i >= 2 * (size_t)R;
+        sl.borrowed = i >= R && !sl.express;
+        cudaError_t e = sl.borrowed ? cudaSuccess
+                                    : cudaStreamCreateWithPriority(&sl.st, cudaStreamNonBlocking,
+                                                                   sl.express ? prio_high : prio_low);
+        if (sl.borrowed) sl.st = S->slots[i - R].st;
+        if (e != cudaSuccess || cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
+            if (sl.borrowed) sl.st = nullptr;
             server_release(S);
             return CM_EDEVICE;
         }

@@ -138,9 +138,9 @@ def test_server_admission_by_footprint(sctx, cm_ctx):
 
 
 def test_server_express_slot(sctx, cm_ctx):
-    # one normal slot: a long request holds it; short requests that arrive
+    # one normal stream: a long request holds it; short requests that arrive
     # meanwhile finish first through the express slot (high stream priority),
-    # and without it they wait behind the long one
+    # and without it they wait behind the long one (queued on its stream)
     big = make(T, 2 ** 26, 2 ** 25, 801)     # L = 2^27: milliseconds
     smalls = [make(T, 3000 + 100 * j, 1500, 810 + 2 * j) for j in range(6)]
     for express in (0, native.SERVER_NO_EXPRESS):
@@ -156,7 +156,7 @@ def test_server_express_slot(sctx, cm_ctx):
         else:
             assert all(r["t_done_ns"] >= rb["t_done_ns"] for r in rs)
         st = sctx.server_stats()
-        assert st["slots"] == (2 if express == 0 else 1)
+        assert st["slots"] == (3 if express == 0 else 2)   # two wave slots on the stream, and the express one
         sctx.server_stop()
         for r in smalls + [big]:
             assert torch.equal(r["z"], alone(cm_ctx, r))
