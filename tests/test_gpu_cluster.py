@@ -108,10 +108,64 @@ def test_cluster_path_equals_goldilocks_path(cm_ctx):
         gl.close()
 
 
-def test_cluster_path_dodis_precondition(cm_ctx):
-    P = na(20000)
+@pytest.mark.parametrize("P,m", [(20000, 7000), (70000, 40001)])
+def test_cluster_path_dodis_precondition(cm_ctx, P, m):
+    P = na(P)
     x = to_dev(np.zeros(native.words(P), dtype=np.uint64))
     y = to_dev(inputs.bernoulli_half(5, P))
-    z = cm_ctx.dodis(x, y, P, 7000)
+    z = cm_ctx.dodis(x, y, P, m)
     assert cm_ctx.device_status()[0] == native.CM_EPRECOND
     assert (from_dev(z) == 0).all()
+
+
+# 2^17 products (16-CTA clusters): every window position class (lo = 0, the
+# wrap at position 0, m = 1, m = L - K + 1, ragged ends)
+WINDOW_CASES = [
+    (T, 2 ** 16 + 1, 2 ** 16),            # lo = 2^16, m = 2^16: K + m - 1 = 2^17 exactly
+    (T, 65537, 1),                        # m = 1
+    (T, 70001, 20000),                    # ragged
+    (T, 1, 2 ** 17),                      # n = 1 (lo = 0): z = y
+    (C, na(66000) - 1, 33000),
+    (D, na(66000), 30001),
+]
+
+
+@pytest.mark.parametrize("kind,n,m", WINDOW_CASES)
+def test_2p17_window_cases_match_oracle(cm_ctx, kind, n, m):
+    info = native.plan_query(kind, n, m)
+    assert info["transform_length"] == 2 ** 17 and info["products"] == 1, info
+    xw, yw, z, prof = run(cm_ctx, kind, n, m, 7300 + n % 1000 + m % 71)
+    assert prof.get("k_cluster_f25", (0,))[0] == 1, prof
+    if m & 63:
+        assert int(z[-1]) >> (m & 63) == 0
+    if m <= 40000:
+        assert (z == want(kind, xw, n, yw, m)).all()
+    else:
+        rows = np.unique(np.concatenate([np.arange(200), np.arange(m - 200, m),
+                                         np.random.default_rng(m).integers(0, m, 200)]))
+        got = ((z[rows >> 6] >> (rows & 63).astype(np.uint64)) & np.uint64(1)).astype(np.uint8)
+        fn = {T: lambda r: oracle.toeplitz_rows(xw, n, yw, m, r),
+              C: lambda r: oracle.circulant_rows(xw, n, yw, m, r),
+              D: lambda r: oracle.dodis_rows(xw, yw, n, m, r)}[kind]
+        assert (got == fn(rows)).all()
+    assert cm_ctx.device_status() == (native.CM_OK, 0)
+
+
+def test_cluster_path_repeated_calls_and_streams(cm_ctx):
+    # back-to-back calls and calls on two streams give the same bits every time
+    import torch
+    n, m = 2 ** 16, 2 ** 15
+    xw, yw = inputs.bernoulli_half(7501, n), inputs.bernoulli_half(7502, n + m - 1)
+    x, y = to_dev(xw), to_dev(yw)
+    ref = from_dev(cm_ctx.toeplitz(x, n, y, m))
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for s in (s1, s2, s1, s2):
+        with torch.cuda.stream(s):
+            outs.append(cm_ctx.toeplitz(x, n, y, m))
+    torch.cuda.synchronize()
+    for z in outs:
+        assert (from_dev(z) == ref).all()
+    rows = np.arange(0, m, 97)
+    got = ((ref[rows >> 6] >> (rows & 63).astype(np.uint64)) & np.uint64(1)).astype(np.uint8)
+    assert (got == oracle.toeplitz_rows(xw, n, yw, m, rows)).all()
